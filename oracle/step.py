@@ -1,0 +1,113 @@
+"""One fractional-step time step (oracle, FP64): Eqs. (4)-(10) of §2.3.1, the
+immersed-boundary coupling of §2.3.3 and the rigid body of §2.3.2.
+
+Forward Euler (the scheme of every run in §3):
+  1. markers X_i = X_i^0 + w^n; solid / IB faces; u_s and u_c (ib.py)
+  2. predictor with direct forcing, Eqs. (4)-(5):
+        f  = eps [ -R(u^n) + (u_s - u^n) / dt ]
+        u* = u^n + dt (R(u^n) + f) = (1 - eps)(u^n + dt R) + eps u_s
+  3. pressure Poisson Eq. (9) and correction Eq. (10), with phi = dt p / rho:
+        L phi = D[(1 - eps) u* + eps u_c],   u^{n+1} = u* - G phi
+  4. q_i from f (Eq. 20), F = rho sum q_i dV_i, then the body by RK4 (Eq. 12)
+
+Runge-Kutta ("explicit Runge-Kutta", §2.5; tableau not given): the strong-
+stability-preserving three-stage scheme of Shu and Osher with a projection
+after every stage, for grids without a body or an outflow:
+  u1 = P(u^n + dt R(u^n)),  u2 = P(3/4 u^n + 1/4 (u1 + dt R(u1))),
+  u^{n+1} = P(1/3 u^n + 2/3 (u2 + dt R(u2))).
+
+The outflow face (zero gradient, flux-corrected) and the boundary values are
+applied to u* before the projection.
+
+Parity: the pieces are pinned in their own modules; the composition is
+pinned by Taylor-Green decay, Poiseuille flow, divergence-free projection and
+momentum conservation (tests/test_oracle_flows.py), and its autograd adjoint
+by central finite differences (tests/test_oracle_adjoint.py).
+"""
+import torch
+
+from . import body as body_mod
+from . import fluid, ib, poisson
+from .grid import F64
+
+SSPRK3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
+
+
+class State:
+    """u: list of velocity components; w, wd: body displacement and velocity (2,), or None."""
+
+    def __init__(self, u, w=None, wd=None):
+        self.u = u
+        self.w = w
+        self.wd = wd
+
+
+class Diagnostics:
+    def __init__(self):
+        self.f = None
+        self.q = None
+        self.F = None
+        self.torque = None
+        self.phi = None
+        self.eps = None
+
+
+def _predictor(g, u_in, dt, eps=None, ut=None):
+    """Eq. (4)-(5): returns (u*, f)."""
+    R = fluid.momentum_rhs(g, u_in)
+    ustar, f = [], []
+    for c in range(g.dim):
+        base = u_in[c] + dt * R[c]
+        if eps is None:
+            ustar.append(base)
+            f.append(torch.zeros_like(base))
+        else:
+            e = eps[c]
+            ustar.append(torch.where(e, ut[c], base))
+            f.append(torch.where(e, -R[c] + (ut[c] - u_in[c]) / dt, torch.zeros_like(base)))
+    return ustar, f
+
+
+def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
+    """Advance one step; returns (new State, Diagnostics)."""
+    dg = Diagnostics()
+    u = fluid.apply_boundary_values(g, st.u)
+    if scheme == "rk3":
+        assert body is None and not (not g.periodic(0) and g.bc[0][1] == fluid.OUTFLOW), \
+            "RK3 is provided for grids without a body or an outflow"
+        v = u
+        for a, b in SSPRK3:
+            ustar, _ = _predictor(g, v, dt)
+            ut = [a * u[c] + b * ustar[c] for c in range(g.dim)]
+            ut = fluid.apply_boundary_values(g, ut)
+            v, phi = poisson.project(g, ut)
+        dg.phi = phi
+        return State(v, st.w, st.wd), dg
+
+    eps = ut = ucl = masks = None
+    if body is not None:
+        masks = ib.classify(g, body, st.w)
+        ut, ucl = ib.target_velocity(g, body, kernel, st.w, st.wd, masks)
+        eps = [m[0] | m[1] for m in masks]
+        dg.eps = eps
+    ustar, f = _predictor(g, u, dt, eps, ut)
+    ustar = fluid.apply_boundary_values(g, ustar)
+    ustar = fluid.outflow_faces(g, u, ustar)
+    unew, phi = poisson.project(g, ustar, ucl, eps)
+    dg.phi = phi
+    dg.f = f
+    w_new, wd_new = st.w, st.wd
+    if body is not None:
+        q, F, torque = ib.marker_forces(g, body, kernel, st.w, f)
+        dg.q, dg.F, dg.torque = q, F, torque
+        if params is not None:
+            w_new, wd_new = body_mod.rk4(params, st.w, st.wd, F, dt)
+    return State(unew, w_new, wd_new), dg
+
+
+def kinetic_energy(g, u):
+    """1/2 sum over faces of u_c^2 times the face control volume."""
+    ke = torch.zeros((), dtype=F64)
+    for c in range(g.dim):
+        ke = ke + 0.5 * (u[c] * u[c] * g.face_volume(c)).sum()
+    return ke
