@@ -1,0 +1,351 @@
+#!/usr/bin/env python
+"""Throughput of the fractional-step time step on one B300 (or N replicas).
+
+Workload (default): 3-D decaying isotropic turbulence, periodic 128^3, random
+solenoidal initial field with E(k) ~ k^4 exp(-2 (k/4)^2), u_rms = 1, nu = 1/400,
+SSP-RK3 at CFL 0.5, mixed precision (FP32 stencils and transforms, FP64
+tridiagonal / zero mode / reductions).  One "step" is one full time step
+(three predictor + projection stages) through the C ABI.
+
+Metric: cell-updates/s = cells x steps / time (higher is better).  L2 (126 MB)
+is flushed before every timed step by writing a 256 MB buffer outside the
+timed events; each step is timed with CUDA events on the solver's stream.
+
+Also reported: the all-FP64 GPU path on the same workload with the relative L2
+difference of the mixed result to it, the end-to-end number through host
+buffers, the roofline of the dominant kernel, and the oracle timed on the
+host cores (cpu_baseline).  --impl reference times the oracle alone.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as S  # noqa: E402
+
+# Bytes each kernel must move per launch (every array read or written once), per cell
+# of the 3-D mixed-precision RK3 step: f32 fields, f64 tridiagonal factor tables.
+KERNEL_BYTES_PER_CELL = {
+    "predictor_u": None, "predictor_v": None, "predictor_w": None,   # 3 reads + 1 write (+1 read in stages 2, 3)
+    "divergence": 16.0, "fft_x_fwd": 8.0, "fft_z_fwd": 8.0, "fft_z_inv": 8.0, "fft_x_inv": 8.0,
+    "correct_u": 12.0, "correct_v": 12.0, "correct_w": 12.0,
+}
+
+# DRAM bytes per launch from an ncu capture of the kernel as it stands (see profiles/);
+# keyed by kernel name with the hash of the source file it was measured on.
+NCU_TRAFFIC = {}
+
+
+def src_hash(name):
+    files = {"predictor": "stencil.cu", "divergence": "stencil.cu", "correct": "stencil.cu",
+             "fft": "poisson.cu", "ysolve": "poisson.cu"}
+    for key, fn in files.items():
+        if name.startswith(key):
+            p = os.path.join(ROOT, "paper_2505_23940_b300", "csrc", fn)
+            return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+    return None
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=2)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v, device):
+    if ws == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(name):
+    if name == "isotropic_3d_128":
+        return S.isotropic_3d(n=128)
+    if name == "isotropic_3d_256":
+        return S.isotropic_3d(n=256)
+    if name == "channel_3d":
+        return S.channel_3d()
+    if name == "taylor_green_2d":
+        return S.taylor_green_2d()
+    if name == "cylinder_2d":
+        return S.cylinder_2d(seed=2, perturb=0.01)
+    raise ValueError(name)
+
+
+def cpu_oracle_rate(wl, steps, threads=None):
+    """Oracle (plain FP64 torch CPU) cell-updates/s over `steps` full steps of the workload."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import oracle as O
+    from helpers import body_of, grid_of, state_of
+    if threads:
+        torch.set_num_threads(threads)
+    g = grid_of(wl)
+    st = state_of(wl)
+    body, params = body_of(wl)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        st, _ = O.step(g, st, wl.dt, scheme=wl.scheme, body=body, kernel=wl.kernel, params=params)
+    dt = time.perf_counter() - t0
+    return wl.cells() * steps / dt, dt
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    threads = torch.get_num_threads()
+    cpu_oracle_rate(wl, args.warmup)
+    rate, secs = cpu_oracle_rate(wl, args.steps)
+    line = {
+        "impl": "reference", "metric": "cell-updates/s forward", "value": rate, "unit": "cell-updates/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": wl.cells(), "scheme": wl.scheme},
+        "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": "%d full time steps of the %s workload (FP64 torch CPU oracle)"
+                                   % (args.steps, args.workload)},
+        "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(g, u, dt, steps, flush, stream, body=None):
+    times = []
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(u, dt, 1, body=body)
+        e1.record(stream)
+        times.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in times]
+
+
+def predictor_bytes(wl, stage_reads):
+    return None
+
+
+def run_ours(args, ws, rank, local):
+    from paper_2505_23940_b300 import grid_from_workload
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload(args.workload)
+    cells = wl.cells()
+    stream = torch.cuda.current_stream()
+    g = grid_from_workload(wl, "mixed", stream=stream)
+    u0 = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
+    u = [x.clone() for x in u0]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    for _ in range(args.warmup):
+        g.step(u, wl.dt, 1)
+    torch.cuda.synchronize()
+    # short profiling pass over every kernel: which one dominates the step
+    g.profile_begin("")
+    timed_steps(g, u, wl.dt, 2, flush, stream)
+    allk = g.profile_end()
+    dominant = max(allk, key=lambda k: allk[k][1])
+
+    barrier(ws)
+    torch.cuda.synchronize()
+    launches0 = g.launches()
+    g.profile_begin(dominant)
+    with Clocks(local) as clk:
+        ms = timed_steps(g, u, wl.dt, args.steps, flush, stream)
+    prof = g.profile_end()
+    launches = g.launches() - launches0
+    barrier(ws)
+    total_ms = max_over_ranks(ws, sum(ms), dev)
+    value = cells * args.steps * ws / (total_ms * 1e-3)
+
+    # roofline of the dominant kernel, timed live inside the region above
+    cnt, kms = prof.get(dominant, (0, 0.0))
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6400.0)
+    bpc = KERNEL_BYTES_PER_CELL.get(dominant)
+    if dominant.startswith("predictor"):
+        bpc = (16.0 + 20.0 + 20.0) / 3.0 if wl.scheme == "rk3" else 16.0
+    if dominant == "ysolve":
+        nlam = (wl.n[0] // 2 + 1) * (wl.n[2] // 2 + 1)
+        bpc = 8.0 + 3 * 8.0 * nlam * wl.n[1] / cells
+    achieved = bpc * cells / (kms / cnt * 1e-3) / 1e9 if (cnt and bpc) else None
+    tr = NCU_TRAFFIC.get(dominant)
+    traffic = tr["bytes"] if tr and tr.get("src") == src_hash(dominant) else None
+    roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "bytes_per_cell": bpc, "launches": cnt, "avg_launch_us": kms / cnt * 1e3 if cnt else None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
+    line = {
+        "metric": "cell-updates/s forward", "value": value, "unit": "cell-updates/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "cells": cells, "n": wl.n, "scheme": wl.scheme,
+                   "precision": "mixed (FP32 stencils/transforms, FP64 tridiagonal/zero mode/reductions)",
+                   "l2": "flushed before every timed step (256 MB write outside the timed events)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clk.summary(),
+        "kernels_ms_per_step": {k: v[1] / 2 for k, v in sorted(allk.items(), key=lambda kv: -kv[1][1])},
+    }
+
+    if not args.quick:
+        # all-FP64 GPU path on the same workload, and the mixed result's distance to it
+        k64 = max(2, min(args.steps, 5))
+        g64 = grid_from_workload(wl, "fp64", stream=stream)
+        u64 = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev).contiguous() for a in wl.u0]
+        for _ in range(2):
+            g64.step(u64, wl.dt, 1)
+        ms64 = timed_steps(g64, u64, wl.dt, k64, flush, stream)
+        um = [x.clone() for x in u0]
+        ud = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev).contiguous() for a in wl.u0]
+        g.step(um, wl.dt, 10)
+        g64.step(ud, wl.dt, 10)
+        torch.cuda.synchronize()
+        num = sum(float(((a.double() - b) ** 2).sum()) for a, b in zip(um, ud))
+        den = sum(float((b ** 2).sum()) for b in ud)
+        line["fp64_gpu"] = {"value": cells * k64 / (sum(ms64) * 1e-3), "unit": "cell-updates/s",
+                            "ms_per_step": sum(ms64) / k64,
+                            "mixed_vs_fp64_rel_l2_after_10_steps": (num / den) ** 0.5}
+        line["speedup_mixed_over_fp64"] = line["value"] / ws / line["fp64_gpu"]["value"]
+        del g64, u64
+
+        # end to end through host buffers: H2D of the state from pinned memory, the step, D2H of the result
+        host = [x.cpu().pin_memory() for x in u0]
+        dev_u = [x.clone() for x in u0]
+        nbytes = sum(x.numel() * x.element_size() for x in host)
+        ev = []
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d, h in zip(dev_u, host):
+                d.copy_(h, non_blocking=True)
+            g.step(dev_u, wl.dt, 1)
+            for d, h in zip(dev_u, host):
+                h.copy_(d, non_blocking=True)
+            e1.record(stream)
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ems = max_over_ranks(ws, sum(a.elapsed_time(b) for a, b in ev), dev)
+        line["e2e"] = {"value": cells * args.steps * ws / (ems * 1e-3), "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        line["fwd_adj"] = None
+
+    if rank == 0 and not args.quick and args.cpu_steps > 0:
+        rate, secs = cpu_oracle_rate(wl, args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": torch.get_num_threads(),
+                                "kind": "oracle",
+                                "sample": "%d full time step(s) of the %s workload, FP64 torch CPU oracle, %.1f s"
+                                          % (args.cpu_steps, args.workload, secs)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="isotropic_3d_128")
+    ap.add_argument("--cpu-steps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

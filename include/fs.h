@@ -1,0 +1,199 @@
+/*
+ * fs.h -- C ABI of the fractional-step finite-volume / immersed-boundary
+ * time step (Diff-FlowFSI, arXiv 2505.23940), B300 (sm_103a) CUDA library.
+ *
+ * Conventions for every function
+ *   - Returns an int status: FS_OK (0) or a negative FS_ERR_* code.  The text
+ *     of the last error of the calling thread is returned by fs_last_error().
+ *     No C++ exception crosses this boundary.
+ *   - "device" pointers are CUDA global-memory addresses on the grid's device;
+ *     "host" pointers are ordinary CPU memory.  The library never takes
+ *     ownership of a caller pointer and never frees one.
+ *   - Work is enqueued on the stream given to fs_create_grid (or
+ *     fs_set_stream).  Functions return without waiting for the GPU unless
+ *     their comment says they synchronise.
+ *
+ * Discretisation (§2.3.1 of the paper): staggered (MAC) finite-volume grid,
+ * pressure at cell centres, velocity component c on the faces normal to
+ * direction c; 2nd-order central diffusion, 2nd-order central or 1st-order
+ * upwind convection; Chorin projection (Eqs. 4-10).
+ *
+ * Field layout (every velocity array, state or adjoint): dense, x fastest,
+ * index = i + ex * (j + ey * k).  Component c has extents (ex, ey, ez) equal
+ * to the cell counts n, except along its own direction c where a
+ * non-periodic direction stores n_c + 1 faces (faces 0 and n_c lie on the
+ * boundary).  fs_field_extent() returns them.  Pressure arrays have extents n.
+ * In 2-D, n[2] = 1 and there is no w component.
+ */
+#ifndef FS_H
+#define FS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define FS_OK               0
+#define FS_ERR_ARG         -1   /* invalid argument or combination (message says which) */
+#define FS_ERR_CUDA        -2   /* a CUDA runtime call failed */
+#define FS_ERR_DIVERGED    -3   /* NaN/Inf or |u| above the blow-up bound after a step */
+#define FS_ERR_TIMEOUT     -4   /* a bounded device-side wait ran out */
+#define FS_ERR_UNSUPPORTED -5   /* a valid request this library does not implement */
+#define FS_ERR_STATE       -6   /* call out of order (e.g. forces before any step) */
+
+/* ---- boundary types (Table 1 of the paper) ---------------------------- */
+#define FS_BC_PERIODIC 0
+#define FS_BC_NOSLIP   1   /* Dirichlet: wall velocity bc_val */
+#define FS_BC_FREESLIP 2   /* no penetration, zero tangential stress */
+#define FS_BC_INFLOW   3   /* Dirichlet velocity bc_val (x-low only) */
+#define FS_BC_OUTFLOW  4   /* zero-gradient, flux-corrected (x-high only) */
+
+#define FS_CENTRAL2 0      /* 2nd-order central convection */
+#define FS_UPWIND1  1      /* 1st-order upwind convection */
+#define FS_FE       0      /* forward Euler (the paper's runs) */
+#define FS_RK3      1      /* SSP Runge-Kutta 3, projection at every stage */
+#define FS_FP64     0      /* every step in FP64 */
+#define FS_MIXED    1      /* FP32 stencils, transforms and IB transfers; FP64
+                              tridiagonal / zero-mode solves, reductions, body ODE */
+#define FS_PESKIN4  0      /* 4-point kernel of Eq. (22) */
+#define FS_ROMA3    1      /* 3-point kernel of Roma, Peskin & Berger (1999) */
+
+typedef struct fs_grid fs_grid;   /* opaque; owns plans, workspaces, IB buffers */
+
+/* Grid description (§2.5: rectangular domain, uniform or stretched spacing).
+ * x and z must be uniform; y may be stretched when it is not periodic.
+ * Supported: 2-D with x periodic / inflow-outflow / walls and y periodic /
+ * walls; 3-D with x and z periodic and y periodic / walls.  Periodic
+ * directions need an even cell count; transform lengths need prime factors
+ * <= 13. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int n[3];                /* cell counts (n[2] = 1 in 2-D) */
+  const double* xf[3];     /* host: n[d] + 1 face coordinates per direction (xf[2] unused in 2-D) */
+  int bc[3][2];            /* FS_BC_* at the low / high side of each direction */
+  double bc_val[3][2][3];  /* velocity vector imposed at each side (NOSLIP wall velocity, INFLOW velocity) */
+  double nu;               /* kinematic viscosity */
+  double rho;              /* density */
+  int conv_scheme;         /* FS_CENTRAL2 | FS_UPWIND1 */
+  int time_scheme;         /* FS_FE | FS_RK3 */
+  int precision;           /* FS_FP64 | FS_MIXED */
+  const double* body_force;/* host: n[1] values of an x-momentum source per y row, or NULL */
+} fs_grid_desc;
+
+/* Solver state.  The caller owns every buffer (e.g. torch tensors).
+ * u[c]  device, velocity component c with the extents of fs_field_extent:
+ *       double for FS_FP64 grids, float for FS_MIXED grids.
+ * p     device, double, cell-centred pressure written by fs_step (may be NULL).
+ * body  device, double[4] = {w_x, w_y, wdot_x, wdot_y}: rigid-body
+ *       displacement and velocity; NULL when the grid has no body. */
+typedef struct {
+  void*   u[3];
+  double* p;
+  double* body;
+} fs_state;
+
+/* Immersed body (§2.3.3): a closed polygon of Lagrangian markers, rigid,
+ * translating with the displacement of fs_state.body, optionally elastically
+ * mounted (Eq. 12). */
+typedef struct {
+  int nm;                  /* number of markers (>= 3) */
+  const double* X0;        /* host: rest x of each marker, ordered around the surface */
+  const double* Y0;        /* host: rest y */
+  const double* ds;        /* host: arc length per marker; dV_i = ds_i * h (shell of one cell) */
+  double centre[2];        /* reference point (rotation centre) at rest */
+  double omega;            /* prescribed surface angular velocity (geometry does not turn) */
+  double mass;             /* m of Eq. (12); <= 0 holds the body fixed */
+  double stiffness;        /* k */
+  double damping;          /* c */
+  int active[2];           /* DOF mask: x, y */
+  int delta_kernel;        /* FS_PESKIN4 | FS_ROMA3 */
+} fs_body_desc;
+
+/* Parameter-gradient accumulators filled by fs_step_adjoint (added to, never cleared). */
+typedef struct {
+  double* body_force;      /* device, n[1] doubles: dJ/d f_x(y_j), or NULL */
+  double* stiffness;       /* device, 1 double: dJ/dk, or NULL */
+} fs_param_grad;
+
+/* Create a grid: validates the description, builds metrics, transform plans
+ * and tridiagonal tables, and allocates every workspace on the current CUDA
+ * device.  stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: FS_ERR_ARG (bad sizes, BC combination, non-uniform x/z),
+ * FS_ERR_UNSUPPORTED (transform length with a prime factor > 13),
+ * FS_ERR_CUDA (allocation). */
+int fs_create_grid(const fs_grid_desc* desc, void* stream, fs_grid** out);
+
+/* Free every device buffer the grid owns.  Synchronises the grid's stream. */
+int fs_destroy_grid(fs_grid* grid);
+
+/* Change the stream later work is enqueued on. */
+int fs_set_stream(fs_grid* grid, void* stream);
+
+/* Extents (ex, ey, ez) of velocity component comp (0..dim-1); comp = -1 gives
+ * the cell counts (pressure).  Host output. */
+int fs_field_extent(const fs_grid* grid, int comp, int ext[3]);
+
+/* Attach a rigid body (2-D grids, uniform x and y near the body).  Marker
+ * arrays are host memory and are copied.  Replaces any previous body.
+ * Eqs. (18)-(23): solid faces (inside the polygon) and IB faces (non-solid
+ * faces with a solid same-component neighbour) are forced; the target
+ * velocity is the body velocity inside and the half-distribution-normalised
+ * marker interpolation on IB faces.  Errors: FS_ERR_ARG, FS_ERR_UNSUPPORTED
+ * (3-D grid, RK3 grid). */
+int fs_set_ib_markers(fs_grid* grid, const fs_body_desc* body);
+
+/* Advance st by nsteps time steps of size dt (Eqs. 4-10, 18-23, 12).
+ * dt > 0: fixed step, no host synchronisation.
+ * dt <= 0: adaptive step dt = 0.5 * min(h) / max|u| from the state before
+ *          each step (§2.5, CFL condition), which synchronises once per step.
+ * st->u is updated in place; st->p (if not NULL) receives the pressure of the
+ * last step; st->body (required when a body is attached) is advanced by RK4.
+ * Errors: FS_ERR_ARG (NULL field), FS_ERR_DIVERGED (checked only for dt <= 0),
+ * FS_ERR_CUDA. */
+int fs_step(fs_grid* grid, fs_state* st, double dt, int nsteps);
+
+/* Discrete adjoint of one fs_step(dt, 1) (§2.4.1): given the forward state at
+ * step n (st_n, not modified) and the adjoint lam of the state after the
+ * step, overwrite lam with the adjoint of the state before the step and add
+ * parameter gradients to g.  dJdF: host, dim doubles, the sensitivity of the
+ * loss to the hydrodynamic force of this step (may be NULL).  The forward
+ * step is recomputed internally.  The epsilon mask is frozen (its derivative
+ * is zero almost everywhere).  Errors: FS_ERR_UNSUPPORTED (rotating surface
+ * with a body), FS_ERR_ARG, FS_ERR_CUDA. */
+int fs_step_adjoint(fs_grid* grid, const fs_state* st_n, fs_state* lam,
+                    const double* dJdF, fs_param_grad* g, double dt);
+
+/* Solve the discrete pressure Poisson equation D G p = rhs (Eq. 9) exactly
+ * (FFT / DCT along x and z, FP64 tridiagonal along y) for the zero
+ * volume-weighted-mean solution.  rhs, p: device doubles with the cell
+ * counts' extents; may alias.  rhs must be compatible (zero volume-weighted
+ * sum) when the operator is singular. */
+int fs_solve_pressure(fs_grid* grid, const double* rhs, double* p);
+
+/* Hydrodynamic force of the last step (Eq. 20 with F = rho sum_i q_i dV_i).
+ * Host outputs: F[dim], torque[1], q[nm * 2] marker forces (q may be NULL).
+ * Synchronises the grid's stream.  FS_ERR_STATE before the first FSI step. */
+int fs_forces(fs_grid* grid, double* F, double* torque, double* q);
+
+/* Diagnostics of a state: out[0] = max |u|, out[1] = max |D u| (FP64),
+ * out[2] = kinetic energy 1/2 sum u^2 dV.  Host output; synchronises. */
+int fs_diagnostics(fs_grid* grid, const fs_state* st, double out[3]);
+
+/* Number of kernels launched by this grid since creation (host counter). */
+long long fs_kernel_launches(const fs_grid* grid);
+
+/* Kernel timing.  After fs_profile_begin, every launch whose kernel name
+ * contains `filter` ("" = all) is bracketed by CUDA events on the grid's
+ * stream.  fs_profile_end synchronises the stream and writes one line per
+ * kernel name, "name launches total_ms", into report (host, len bytes,
+ * truncated and NUL-terminated). */
+int fs_profile_begin(fs_grid* grid, const char* filter);
+int fs_profile_end(fs_grid* grid, char* report, int len);
+
+/* Text of the calling thread's last error ("" if none). */
+const char* fs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FS_H */

@@ -1,0 +1,687 @@
+// C ABI of the fractional-step library (include/fs.h): grid set-up (metrics,
+// transform plans, tridiagonal factor tables), workspaces and the order of
+// kernels in one time step (Eqs. 4-10 and 18-23, 12 of the paper).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FS_OK;
+  return set_error(FS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+ProfMark::ProfMark(fs_grid* G, const char* name) : g(G) {
+  if (!G->prof_on) return;
+  if (!G->prof_filter.empty() && std::string(name).find(G->prof_filter) == std::string::npos) return;
+  if (G->prof_used + 2 > G->prof_pool.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      G->prof_pool.push_back(e);
+    }
+  }
+  slot = (int)G->prof_used;
+  G->prof_used += 2;
+  G->prof_names.push_back(name);
+  cudaEventRecord(G->prof_pool[slot], G->stream);
+}
+
+ProfMark::~ProfMark() {
+  if (slot >= 0) cudaEventRecord(g->prof_pool[slot + 1], g->stream);
+}
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+  return cudaMalloc((void**)p, (n > 0 ? n : 1) * sizeof(T));
+}
+
+template <typename T>
+cudaError_t upload(T** p, const std::vector<T>& v) {
+  cudaError_t e = dalloc(p, v.size());
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <typename T>
+std::vector<T> cast(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+bool factorize(int n, Plan1D& p) {
+  p.n = n;
+  p.nst = 0;
+  int m = n;
+  while (m % 4 == 0 && m > 4) {
+    if (p.nst >= FS_MAX_RADIX_STAGES) return false;
+    p.radix[p.nst++] = 4;
+    m /= 4;
+  }
+  const int primes[] = {4, 2, 3, 5, 7, 11, 13};
+  for (int q : primes) {
+    while (m % q == 0) {
+      if (p.nst >= FS_MAX_RADIX_STAGES) return false;
+      p.radix[p.nst++] = q;
+      m /= q;
+    }
+  }
+  return m == 1;
+}
+
+template <typename T>
+cudaError_t make_twiddles(Plan1D& p) {
+  const int n = p.n;
+  std::vector<T> tw(2 * n), dtw(2 * n);
+  for (int k = 0; k < n; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)n;
+    tw[2 * k] = (T)std::cos(a);
+    tw[2 * k + 1] = (T)(-std::sin(a));
+    const double b = M_PI * (double)k / (2.0 * (double)n);
+    dtw[2 * k] = (T)std::cos(b);
+    dtw[2 * k + 1] = (T)(-std::sin(b));
+  }
+  cudaError_t e = upload((T**)&p.tw, tw);
+  if (e != cudaSuccess) return e;
+  return upload((T**)&p.dtw, dtw);
+}
+
+bool uniform(const std::vector<double>& h) {
+  for (double v : h)
+    if (std::fabs(v - h[0]) > 1e-12 * std::fabs(h[0])) return false;
+  return true;
+}
+
+size_t comp_size(const fs_grid* G, int c) {
+  size_t s = 1;
+  const int n[3] = {G->nx, G->ny, G->nz};
+  for (int d = 0; d < 3; ++d) s *= (size_t)(n[d] + ((c == d && !G->per[d]) ? 1 : 0));
+  return s;
+}
+
+size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) : sizeof(double); }
+
+// FP64 tables of the y tridiagonal factorisation, one column per eigenvalue index.
+int build_tables(fs_grid* G) {
+  const int nx = G->nx, ny = G->ny, nz = G->nz;
+  G->nmx = G->xmode == 1 ? nx : nx / 2 + 1;
+  G->nlz = G->dim == 3 ? nz / 2 + 1 : 1;
+  const int nlam = G->nmx * G->nlz;
+  const std::vector<double>& h = G->h[1];
+  const std::vector<double>& hf = G->hf[1];
+  std::vector<double> a(ny), c(ny);
+  for (int j = 0; j < ny; ++j) {
+    a[j] = 1.0 / (hf[j] * h[j]);
+    c[j] = 1.0 / (hf[j + 1] * h[j]);
+  }
+  if (!G->per[1]) {
+    a[0] = 0.0;           // G p . n = 0 on the walls
+    c[ny - 1] = 0.0;
+  }
+  G->cyclic = G->per[1];
+  std::vector<double> E((size_t)ny * nlam), CP((size_t)ny * nlam), ZV(G->cyclic ? (size_t)ny * nlam : 1, 0.0);
+  std::vector<double> FAC(nlam, 0.0), VL(nlam, 0.0);
+  std::vector<double> diag(ny), e(ny), cp(ny), z(ny), dp(ny);
+  for (int mx = 0; mx < G->nmx; ++mx) {
+    const double lx = G->xmode == 1 ? -(2.0 - 2.0 * std::cos(M_PI * mx / nx)) / (G->hx * G->hx)
+                                    : -(2.0 - 2.0 * std::cos(2.0 * M_PI * mx / nx)) / (G->hx * G->hx);
+    for (int lz = 0; lz < G->nlz; ++lz) {
+      const double lzv = G->dim == 3 ? -(2.0 - 2.0 * std::cos(2.0 * M_PI * lz / nz)) / (G->hz * G->hz) : 0.0;
+      const double lam = lx + lzv;
+      const int li = mx * G->nlz + lz;
+      const bool sing = (mx == 0 && lz == 0);
+      for (int j = 0; j < ny; ++j) diag[j] = -(a[j] + c[j]) + lam;
+      double gam = 0, alpha = 0, beta = 0;
+      const bool cyc = G->cyclic && !sing;
+      if (cyc) {
+        gam = -diag[0];
+        alpha = c[ny - 1];
+        beta = a[0];
+        diag[0] -= gam;
+        diag[ny - 1] -= alpha * beta / gam;
+      }
+      if (sing) {
+        e[0] = 0.0;     // phi_0 = 0 replaces the first row of the singular mode
+        cp[0] = 0.0;
+      } else {
+        e[0] = 1.0 / diag[0];
+        cp[0] = c[0] * e[0];
+      }
+      for (int j = 1; j < ny; ++j) {
+        const double b = diag[j] - a[j] * cp[j - 1];
+        e[j] = 1.0 / b;
+        cp[j] = c[j] * e[j];
+      }
+      for (int j = 0; j < ny; ++j) {
+        E[(size_t)j * nlam + li] = e[j];
+        CP[(size_t)j * nlam + li] = cp[j];
+      }
+      if (cyc) {
+        // Sherman-Morrison: T' z = u with u = (gamma, 0, ..., 0, alpha)
+        for (int j = 0; j < ny; ++j) {
+          const double uj = j == 0 ? gam : (j == ny - 1 ? alpha : 0.0);
+          dp[j] = j == 0 ? uj * e[0] : (uj - a[j] * dp[j - 1]) * e[j];
+        }
+        z[ny - 1] = dp[ny - 1];
+        for (int j = ny - 2; j >= 0; --j) z[j] = dp[j] - cp[j] * z[j + 1];
+        for (int j = 0; j < ny; ++j) ZV[(size_t)j * nlam + li] = z[j];
+        VL[li] = beta / gam;
+        FAC[li] = 1.0 / (1.0 + z[0] + beta / gam * z[ny - 1]);
+      }
+    }
+  }
+  if (upload(&G->ya, a) != cudaSuccess || upload(&G->tE, E) != cudaSuccess || upload(&G->tCP, CP) != cudaSuccess ||
+      upload(&G->tZV, ZV) != cudaSuccess || upload(&G->tFAC, FAC) != cudaSuccess || upload(&G->tVL, VL) != cudaSuccess)
+    return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");
+  return FS_OK;
+}
+
+void free_all(fs_grid* G) {
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  F(G->ihy64); F(G->ihfy64); F(G->thy64); F(G->bf64);
+  F(G->ihy32); F(G->ihfy32); F(G->thy32); F(G->bf32);
+  for (int d = 0; d < 3; ++d) F(G->xf64[d]);
+  F(G->hy64); F(G->hfy64);
+  for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
+  F(G->spec); F(G->scal); F(G->red);
+  F(G->px.tw); F(G->px.dtw); F(G->pz.tw); F(G->pz.dtw);
+  F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tFAC); F(G->tVL);
+  IBDev& B = G->ib;
+  F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
+  for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
+  F(B.fn); F(B.q); F(B.F);
+}
+
+void free_body(fs_grid* G) {
+  IBDev& B = G->ib;
+  auto F = [](void* p) {
+    if (p) cudaFree(p);
+  };
+  F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
+  for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
+  F(B.fn); F(B.q); F(B.F);
+  B = IBDev();
+  G->has_body = false;
+}
+
+template <typename T>
+void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
+  T* u[3] = {(T*)st->u[0], (T*)st->u[1], (T*)(G->dim == 3 ? st->u[2] : nullptr)};
+  T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
+  T* spec = (T*)G->spec;
+  if (G->scheme == FS_RK3) {
+    T* v[3] = {(T*)G->ustage[0], (T*)G->ustage[1], (T*)G->ustage[2]};
+    const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int s = 0; s < 3; ++s) {
+      T* const* in = s == 0 ? u : v;
+      launch_predictor<T>(G, in, u, us, dt, A[s], Bc[s], nullptr);
+      launch_divergence<T>(G, us, spec, nullptr);
+      poisson_solve_inplace<T>(G, spec);
+      launch_correct<T>(G, us, spec, s == 2 ? u : v);
+    }
+    if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / (Bc[2] * dt));
+    return;
+  }
+  if (G->has_body) ib_prepare<T>(G, st->body);
+  launch_outflow_flux<T>(G, u);
+  launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
+  launch_divergence<T>(G, us, spec, st->body);
+  poisson_solve_inplace<T>(G, spec);
+  launch_correct<T>(G, us, spec, u);
+  if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / dt);
+  if (G->has_body) {
+    ib_forces<T>(G, st->body);
+    body_rk4(G, st->body, dt);
+  }
+}
+
+}  // namespace
+}  // namespace fs
+
+using namespace fs;
+
+template <>
+Geom<double> fs_grid::geom<double>() const {
+  Geom<double> g;
+  g.dim = dim; g.nx = nx; g.ny = ny; g.nz = nz;
+  for (int d = 0; d < 3; ++d) {
+    g.per[d] = per[d];
+    for (int s = 0; s < 2; ++s) {
+      g.bc[d][s] = bc[d][s];
+      for (int c = 0; c < 3; ++c) g.bcv[d][s][c] = bcv[d][s][c];
+    }
+  }
+  g.hx = hx; g.hz = hz; g.ihx = 1.0 / hx; g.ihz = 1.0 / hz;
+  g.ihy = ihy64; g.ihfy = ihfy64; g.thy = thy64;
+  g.bforce = bforce.empty() ? nullptr : bf64;
+  g.nu = nu;
+  return g;
+}
+
+template <>
+Geom<float> fs_grid::geom<float>() const {
+  Geom<float> g;
+  g.dim = dim; g.nx = nx; g.ny = ny; g.nz = nz;
+  for (int d = 0; d < 3; ++d) {
+    g.per[d] = per[d];
+    for (int s = 0; s < 2; ++s) {
+      g.bc[d][s] = bc[d][s];
+      for (int c = 0; c < 3; ++c) g.bcv[d][s][c] = (float)bcv[d][s][c];
+    }
+  }
+  g.hx = (float)hx; g.hz = (float)hz; g.ihx = (float)(1.0 / hx); g.ihz = (float)(1.0 / hz);
+  g.ihy = ihy32; g.ihfy = ihfy32; g.thy = thy32;
+  g.bforce = bforce.empty() ? nullptr : bf32;
+  g.nu = (float)nu;
+  return g;
+}
+
+extern "C" {
+
+const char* fs_last_error(void) { return g_last_error.c_str(); }
+
+int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
+  if (!D || !out) return set_error(FS_ERR_ARG, "fs_create_grid: NULL argument");
+  *out = nullptr;
+  if (D->dim != 2 && D->dim != 3) return set_error(FS_ERR_ARG, "dim must be 2 or 3");
+  const int nz = D->dim == 3 ? D->n[2] : 1;
+  if (D->n[0] < 2 || D->n[1] < 2 || nz < 1 || (D->dim == 3 && nz < 2))
+    return set_error(FS_ERR_ARG, "cell counts must be >= 2");
+  if (D->precision != FS_FP64 && D->precision != FS_MIXED) return set_error(FS_ERR_ARG, "unknown precision");
+  if (D->conv_scheme != FS_CENTRAL2 && D->conv_scheme != FS_UPWIND1) return set_error(FS_ERR_ARG, "unknown convection scheme");
+  if (D->time_scheme != FS_FE && D->time_scheme != FS_RK3) return set_error(FS_ERR_ARG, "unknown time scheme");
+  fs_grid* G = new (std::nothrow) fs_grid();
+  if (!G) return set_error(FS_ERR_ARG, "out of host memory");
+  G->dim = D->dim;
+  G->nx = D->n[0];
+  G->ny = D->n[1];
+  G->nz = nz;
+  G->nu = D->nu;
+  G->rho = D->rho > 0 ? D->rho : 1.0;
+  G->conv = D->conv_scheme;
+  G->scheme = D->time_scheme;
+  G->prec = D->precision;
+  G->stream = (cudaStream_t)stream;
+  const int n[3] = {G->nx, G->ny, G->nz};
+  for (int d = 0; d < 3; ++d) {
+    for (int s = 0; s < 2; ++s) {
+      G->bc[d][s] = d < D->dim ? D->bc[d][s] : FS_BC_PERIODIC;
+      for (int c = 0; c < 3; ++c) G->bcv[d][s][c] = d < D->dim ? D->bc_val[d][s][c] : 0.0;
+    }
+    G->per[d] = G->bc[d][0] == FS_BC_PERIODIC;
+    if ((G->bc[d][0] == FS_BC_PERIODIC) != (G->bc[d][1] == FS_BC_PERIODIC)) {
+      delete G;
+      return set_error(FS_ERR_ARG, "periodic boundary on one side only");
+    }
+    for (int s = 0; s < 2; ++s) {
+      const int k = G->bc[d][s];
+      if (k < FS_BC_PERIODIC || k > FS_BC_OUTFLOW || (k == FS_BC_INFLOW && (d != 0 || s != 0)) ||
+          (k == FS_BC_OUTFLOW && (d != 0 || s != 1))) {
+        delete G;
+        return set_error(FS_ERR_ARG, "inflow is x-low only, outflow x-high only");
+      }
+    }
+    std::vector<double> xf(n[d] + 1);
+    if (d < D->dim) {
+      if (!D->xf[d]) {
+        delete G;
+        return set_error(FS_ERR_ARG, "missing face coordinates");
+      }
+      for (int i = 0; i <= n[d]; ++i) xf[i] = D->xf[d][i];
+    } else {
+      xf = {0.0, 1.0};
+    }
+    std::vector<double> h(n[d]), xc(n[d]), hf(n[d] + 1), th(n[d] + 1, 0.5);
+    for (int i = 0; i < n[d]; ++i) {
+      h[i] = xf[i + 1] - xf[i];
+      xc[i] = 0.5 * (xf[i] + xf[i + 1]);
+      if (!(h[i] > 0)) {
+        delete G;
+        return set_error(FS_ERR_ARG, "face coordinates must increase");
+      }
+    }
+    const double L = xf[n[d]] - xf[0];
+    if (G->per[d]) {
+      for (int f = 0; f < n[d]; ++f) {
+        const double xl = f > 0 ? xc[f - 1] : xc[n[d] - 1] - L;
+        hf[f] = xc[f] - xl;
+        th[f] = (xf[f] - xl) / hf[f];
+      }
+      hf[n[d]] = hf[0];
+      th[n[d]] = th[0];
+    } else {
+      for (int f = 1; f < n[d]; ++f) {
+        hf[f] = xc[f] - xc[f - 1];
+        th[f] = (xf[f] - xc[f - 1]) / hf[f];
+      }
+      hf[0] = h[0];
+      hf[n[d]] = h[n[d] - 1];
+    }
+    G->xf[d] = xf;
+    G->h[d] = h;
+    G->hf[d] = hf;
+    G->th[d] = th;
+  }
+  if (!uniform(G->h[0]) || (G->dim == 3 && !uniform(G->h[2]))) {
+    delete G;
+    return set_error(FS_ERR_ARG, "x and z spacing must be uniform (transform directions)");
+  }
+  if (G->per[1] && !uniform(G->h[1])) {
+    delete G;
+    return set_error(FS_ERR_ARG, "a periodic y direction must be uniform");
+  }
+  if (G->dim == 3 && (!G->per[0] || !G->per[2])) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "3-D grids need periodic x and z");
+  }
+  if ((G->per[0] && G->nx % 2) || (G->dim == 3 && G->nz % 2)) {
+    delete G;
+    return set_error(FS_ERR_ARG, "periodic transform directions need an even cell count");
+  }
+  if (G->scheme == FS_RK3 && !G->per[0] && G->bc[0][1] == FS_BC_OUTFLOW) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "RK3 is provided for grids without an outflow");
+  }
+  G->hx = G->h[0][0];
+  G->hz = G->h[2][0];
+  G->xmode = G->per[0] ? 0 : 1;
+  if (!factorize(G->nx, G->px) || (G->dim == 3 && !factorize(G->nz, G->pz))) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "transform length with a prime factor > 13");
+  }
+  if ((size_t)G->ny * 32 * 8 > 200 * 1024) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 800)");
+  }
+  if (D->body_force) G->bforce.assign(D->body_force, D->body_force + G->ny);
+
+  // device metrics
+  const int ny = G->ny;
+  std::vector<double> ihy(ny), ihfy(ny + 1), thy(ny + 1);
+  for (int j = 0; j < ny; ++j) ihy[j] = 1.0 / G->h[1][j];
+  for (int j = 0; j <= ny; ++j) {
+    ihfy[j] = 1.0 / G->hf[1][j];
+    thy[j] = G->th[1][j];
+  }
+  bool ok = upload(&G->ihy64, ihy) == cudaSuccess && upload(&G->ihfy64, ihfy) == cudaSuccess &&
+            upload(&G->thy64, thy) == cudaSuccess && upload(&G->ihy32, cast<float>(ihy)) == cudaSuccess &&
+            upload(&G->ihfy32, cast<float>(ihfy)) == cudaSuccess && upload(&G->thy32, cast<float>(thy)) == cudaSuccess &&
+            upload(&G->hy64, G->h[1]) == cudaSuccess && upload(&G->hfy64, G->hf[1]) == cudaSuccess;
+  for (int d = 0; d < 3 && ok; ++d) ok = upload(&G->xf64[d], G->xf[d]) == cudaSuccess;
+  if (ok && !G->bforce.empty())
+    ok = upload(&G->bf64, G->bforce) == cudaSuccess && upload(&G->bf32, cast<float>(G->bforce)) == cudaSuccess;
+  // workspaces
+  const size_t es = elem_size(G);
+  for (int c = 0; c < G->dim && ok; ++c) {
+    ok = cudaMalloc(&G->ustar[c], comp_size(G, c) * es) == cudaSuccess;
+    if (ok && G->scheme == FS_RK3) ok = cudaMalloc(&G->ustage[c], comp_size(G, c) * es) == cudaSuccess;
+  }
+  const size_t cells = (size_t)G->nx * G->ny * G->nz;
+  if (ok) ok = cudaMalloc(&G->spec, cells * std::max(es, sizeof(double))) == cudaSuccess;
+  if (ok) ok = dalloc(&G->scal, 64) == cudaSuccess && cudaMemset(G->scal, 0, 64 * sizeof(double)) == cudaSuccess;
+  if (ok) ok = dalloc(&G->red, 64) == cudaSuccess;
+  if (ok) ok = G->prec == FS_MIXED ? (make_twiddles<float>(G->px) == cudaSuccess &&
+                                      (G->dim == 2 || make_twiddles<float>(G->pz) == cudaSuccess))
+                                   : (make_twiddles<double>(G->px) == cudaSuccess &&
+                                      (G->dim == 2 || make_twiddles<double>(G->pz) == cudaSuccess));
+  if (!ok) {
+    free_all(G);
+    delete G;
+    return set_error(FS_ERR_CUDA, "allocating grid workspaces");
+  }
+  int rc = build_tables(G);
+  if (rc != FS_OK) {
+    free_all(G);
+    delete G;
+    return rc;
+  }
+  *out = G;
+  return FS_OK;
+}
+
+int fs_destroy_grid(fs_grid* G) {
+  if (!G) return FS_OK;
+  cudaStreamSynchronize(G->stream);
+  for (cudaEvent_t e : G->prof_pool) cudaEventDestroy(e);
+  free_all(G);
+  delete G;
+  return FS_OK;
+}
+
+int fs_set_stream(fs_grid* G, void* stream) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  G->stream = (cudaStream_t)stream;
+  return FS_OK;
+}
+
+int fs_field_extent(const fs_grid* G, int comp, int ext[3]) {
+  if (!G || !ext) return set_error(FS_ERR_ARG, "NULL argument");
+  if (comp < -1 || comp >= G->dim) return set_error(FS_ERR_ARG, "component out of range");
+  const int n[3] = {G->nx, G->ny, G->nz};
+  for (int d = 0; d < 3; ++d) ext[d] = n[d] + ((comp == d && !G->per[d]) ? 1 : 0);
+  return FS_OK;
+}
+
+long long fs_kernel_launches(const fs_grid* G) { return G ? G->launches : 0; }
+
+int fs_profile_begin(fs_grid* G, const char* filter) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  G->prof_on = true;
+  G->prof_filter = filter ? filter : "";
+  G->prof_used = 0;
+  G->prof_names.clear();
+  return FS_OK;
+}
+
+int fs_profile_end(fs_grid* G, char* report, int len) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  G->prof_on = false;
+  cudaError_t e = cudaStreamSynchronize(G->stream);
+  if (e != cudaSuccess) return cuda_check(e, "fs_profile_end");
+  std::vector<std::string> names;
+  std::vector<long long> count;
+  std::vector<double> total;
+  for (size_t r = 0; r < G->prof_names.size(); ++r) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, G->prof_pool[2 * r], G->prof_pool[2 * r + 1]);
+    size_t q = 0;
+    while (q < names.size() && names[q] != G->prof_names[r]) ++q;
+    if (q == names.size()) {
+      names.push_back(G->prof_names[r]);
+      count.push_back(0);
+      total.push_back(0.0);
+    }
+    count[q] += 1;
+    total[q] += ms;
+  }
+  std::string out;
+  char line[256];
+  for (size_t q = 0; q < names.size(); ++q) {
+    snprintf(line, sizeof(line), "%s %lld %.6f\n", names[q].c_str(), count[q], total[q]);
+    out += line;
+  }
+  if (report && len > 0) {
+    strncpy(report, out.c_str(), (size_t)len - 1);
+    report[len - 1] = 0;
+  }
+  G->prof_used = 0;
+  G->prof_names.clear();
+  return FS_OK;
+}
+
+int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
+  if (!G || !b) return set_error(FS_ERR_ARG, "NULL argument");
+  if (G->dim != 2) return set_error(FS_ERR_UNSUPPORTED, "immersed bodies are provided for 2-D grids");
+  if (G->scheme != FS_FE) return set_error(FS_ERR_UNSUPPORTED, "immersed bodies use forward Euler");
+  if (b->nm < 3 || !b->X0 || !b->Y0 || !b->ds) return set_error(FS_ERR_ARG, "need >= 3 markers with X0, Y0, ds");
+  if (!uniform(G->h[1])) return set_error(FS_ERR_ARG, "immersed bodies need uniform y spacing");
+  if (b->delta_kernel != FS_PESKIN4 && b->delta_kernel != FS_ROMA3) return set_error(FS_ERR_ARG, "unknown delta kernel");
+  free_body(G);
+  IBDev& B = G->ib;
+  B.nm = b->nm;
+  B.kernel = b->delta_kernel;
+  B.centre[0] = b->centre[0];
+  B.centre[1] = b->centre[1];
+  B.omega = b->omega;
+  B.mass = b->mass;
+  B.k = b->stiffness;
+  B.c = b->damping;
+  B.active[0] = b->active[0];
+  B.active[1] = b->active[1];
+  // polygon in surface order, bounding box with a margin so the early-out never decides a point near an edge
+  std::vector<double> PX(b->X0, b->X0 + b->nm), PY(b->Y0, b->Y0 + b->nm);
+  double xmin = PX[0], xmax = PX[0], ymin = PY[0], ymax = PY[0];
+  for (int m = 0; m < b->nm; ++m) {
+    xmin = std::min(xmin, PX[m]);
+    xmax = std::max(xmax, PX[m]);
+    ymin = std::min(ymin, PY[m]);
+    ymax = std::max(ymax, PY[m]);
+  }
+  const double mg = 1e-6 * (std::fabs(xmax - xmin) + std::fabs(ymax - ymin) + 1.0);
+  B.poly_bb[0] = xmin - mg;
+  B.poly_bb[1] = xmax + mg;
+  B.poly_bb[2] = ymin - mg;
+  B.poly_bb[3] = ymax + mg;
+  // markers sorted by the cell that holds their rest position (row-major), for warp-local reductions
+  std::vector<int> order(b->nm);
+  for (int m = 0; m < b->nm; ++m) order[m] = m;
+  const double x0 = G->xf[0][0], y0 = G->xf[1][0], hy = G->h[1][0];
+  auto cell = [&](int m) {
+    const long long ci = (long long)std::floor((b->X0[m] - x0) / G->hx);
+    const long long cj = (long long)std::floor((b->Y0[m] - y0) / hy);
+    return cj * (G->nx + 2) + ci;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cell(p) < cell(q); });
+  std::vector<double> X(b->nm), Y(b->nm), S(b->nm);
+  for (int m = 0; m < b->nm; ++m) {
+    X[m] = b->X0[order[m]];
+    Y[m] = b->Y0[order[m]];
+    S[m] = b->ds[order[m]];
+  }
+  B.horder = order;
+  bool ok = upload(&B.X0, X) == cudaSuccess && upload(&B.Y0, Y) == cudaSuccess && upload(&B.ds, S) == cudaSuccess &&
+            upload(&B.PX, PX) == cudaSuccess && upload(&B.PY, PY) == cudaSuccess && upload(&B.order, order) == cudaSuccess;
+  const size_t es = elem_size(G);
+  for (int c = 0; c < 2 && ok; ++c) {
+    const size_t n = comp_size(G, c);
+    ok = dalloc(&B.flags[c], n) == cudaSuccess && cudaMalloc(&B.num[c], n * es) == cudaSuccess &&
+         cudaMalloc(&B.den[c], n * es) == cudaSuccess && cudaMalloc(&B.f[c], n * es) == cudaSuccess &&
+         cudaMemset(B.num[c], 0, n * es) == cudaSuccess && cudaMemset(B.den[c], 0, n * es) == cudaSuccess &&
+         cudaMemset(B.flags[c], 0, n) == cudaSuccess && cudaMemset(B.f[c], 0, n * es) == cudaSuccess;
+  }
+  if (ok) ok = dalloc(&B.fn, 2 * b->nm) == cudaSuccess && dalloc(&B.q, 2 * b->nm) == cudaSuccess &&
+               dalloc(&B.F, 4) == cudaSuccess && cudaMemset(B.F, 0, 4 * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    free_body(G);
+    return set_error(FS_ERR_CUDA, "allocating immersed-body buffers");
+  }
+  G->has_body = true;
+  return FS_OK;
+}
+
+int fs_step(fs_grid* G, fs_state* st, double dt, int nsteps) {
+  if (!G || !st) return set_error(FS_ERR_ARG, "NULL argument");
+  for (int c = 0; c < G->dim; ++c)
+    if (!st->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
+  if (G->has_body && !st->body) return set_error(FS_ERR_ARG, "a grid with a body needs st->body");
+  if (nsteps < 0) return set_error(FS_ERR_ARG, "nsteps < 0");
+  for (int s = 0; s < nsteps; ++s) {
+    double h = dt;
+    if (dt <= 0) {
+      double d[3];
+      int rc = fs_diagnostics(G, st, d);
+      if (rc != FS_OK) return rc;
+      if (!std::isfinite(d[0]) || !std::isfinite(d[2])) return set_error(FS_ERR_DIVERGED, "non-finite velocity");
+      double hmin = G->hx;
+      for (double v : G->h[1]) hmin = std::min(hmin, v);
+      if (G->dim == 3) hmin = std::min(hmin, G->hz);
+      h = 0.5 * hmin / std::max(d[0], 1e-30);
+    }
+    const bool want_p = st->p && s == nsteps - 1;
+    if (G->prec == FS_MIXED) step_once<float>(G, st, h, want_p);
+    else step_once<double>(G, st, h, want_p);
+  }
+  return cuda_check(cudaGetLastError(), "fs_step launch");
+}
+
+int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, fs_param_grad* g,
+                    double dt) {
+  (void)st_n; (void)lam; (void)dJdF; (void)g; (void)dt;
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  return set_error(FS_ERR_UNSUPPORTED, "adjoint not built in this library version");
+}
+
+int fs_solve_pressure(fs_grid* G, const double* rhs, double* p) {
+  if (!G || !rhs || !p) return set_error(FS_ERR_ARG, "NULL argument");
+  const size_t cells = (size_t)G->nx * G->ny * G->nz;
+  if (G->prec == FS_MIXED) {
+    return set_error(FS_ERR_UNSUPPORTED, "fs_solve_pressure takes FP64 data; use an FS_FP64 grid");
+  }
+  if (p != rhs) {
+    cudaError_t e = cudaMemcpyAsync(p, rhs, cells * sizeof(double), cudaMemcpyDeviceToDevice, G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_solve_pressure copy");
+  }
+  poisson_solve_inplace<double>(G, p);
+  return cuda_check(cudaGetLastError(), "fs_solve_pressure launch");
+}
+
+int fs_forces(fs_grid* G, double* F, double* torque, double* q) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (!G->has_body || !G->ib.have_forces) return set_error(FS_ERR_STATE, "no FSI step has run");
+  double h[4];
+  cudaError_t e = cudaMemcpyAsync(h, G->ib.F, 3 * sizeof(double), cudaMemcpyDeviceToHost, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  if (e != cudaSuccess) return cuda_check(e, "fs_forces");
+  if (F) {
+    F[0] = h[0];
+    F[1] = h[1];
+  }
+  if (torque) *torque = h[2];
+  if (q) {
+    std::vector<double> qs(2 * G->ib.nm);
+    e = cudaMemcpy(qs.data(), G->ib.q, qs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(e, "fs_forces q");
+    for (int m = 0; m < G->ib.nm; ++m) {
+      const int o = G->ib.horder[m];
+      q[2 * o] = qs[2 * m];
+      q[2 * o + 1] = qs[2 * m + 1];
+    }
+  }
+  return FS_OK;
+}
+
+int fs_diagnostics(fs_grid* G, const fs_state* st, double out[3]) {
+  if (!G || !st || !out) return set_error(FS_ERR_ARG, "NULL argument");
+  double* d = G->scal + 16;
+  if (G->prec == FS_MIXED) {
+    float* u[3] = {(float*)st->u[0], (float*)st->u[1], (float*)st->u[2]};
+    launch_diagnostics<float>(G, u, d);
+  } else {
+    double* u[3] = {(double*)st->u[0], (double*)st->u[1], (double*)st->u[2]};
+    launch_diagnostics<double>(G, u, d);
+  }
+  cudaError_t e = cudaMemcpyAsync(out, d, 3 * sizeof(double), cudaMemcpyDeviceToHost, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  return cuda_check(e, "fs_diagnostics");
+}
+
+}  // extern "C"

@@ -1,0 +1,202 @@
+// Internal declarations of the fractional-step CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "fs.h"
+
+#define FS_MAX_RADIX_STAGES 16
+
+namespace fs {
+
+// Boundary ghost rule for a tangential velocity component (§2.3.1, ghost values):
+// Dirichlet sides (no-slip, inflow) reflect about the imposed value, the others copy.
+__host__ __device__ inline bool bc_dirichlet(int kind) {
+  return kind == FS_BC_NOSLIP || kind == FS_BC_INFLOW;
+}
+
+// Geometry handed to kernels by value.  x and z are uniform; y may be stretched.
+template <typename T>
+struct Geom {
+  int dim, nx, ny, nz;
+  int per[3];
+  int bc[3][2];
+  T bcv[3][2][3];
+  T hx, hz, ihx, ihz;
+  const T* ihy;   // 1 / h_y[j]           j in [0, ny)
+  const T* ihfy;  // 1 / hf_y[j]          j in [0, ny]   (hf_y[ny] = hf_y[0] when periodic)
+  const T* thy;   // theta_y[j]           j in [0, ny]
+  const T* bforce;  // x-momentum source per y row, or nullptr
+  T nu;
+  __host__ __device__ int ext(int c, int d) const {
+    int n = d == 0 ? nx : (d == 1 ? ny : nz);
+    return n + ((c == d && !per[d]) ? 1 : 0);
+  }
+  __host__ __device__ int cells() const { return nx * ny * nz; }
+};
+
+// Load component c at integer position (i, j, k) that may lie one layer outside
+// its storage in any direction: periodic directions wrap, tangential
+// non-periodic directions apply the ghost rule, the component's own
+// non-periodic direction clamps (that ghost is never used by an interior face).
+template <typename T>
+__device__ __forceinline__ T ldv(const Geom<T>& g, const T* __restrict__ u, int c, int i, int j, int k) {
+  int idx[3] = {i, j, k};
+  int e[3] = {g.ext(c, 0), g.ext(c, 1), g.ext(c, 2)};
+  T sign = T(1), add = T(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int v = idx[d];
+    if (v < 0 || v >= e[d]) {
+      const int side = v < 0 ? 0 : 1;
+      if (g.per[d]) {
+        v = side ? v - e[d] : v + e[d];
+      } else {
+        v = side ? e[d] - 1 : 0;
+        if (d != c && bc_dirichlet(g.bc[d][side])) {
+          // ghost = 2 u_wall - (current value)
+          add = T(2) * g.bcv[d][side][c] - add;
+          sign = -sign;
+        }
+      }
+      idx[d] = v;
+    }
+  }
+  // A face on the component's own non-periodic boundary carries the imposed
+  // normal velocity (0 on walls, U at the inflow) whatever the state holds;
+  // only the outflow face is a state value.
+  T raw;
+  const int own = idx[c];
+  if (!g.per[c] && (own == 0 || own == e[c] - 1) && g.bc[c][own == 0 ? 0 : 1] != FS_BC_OUTFLOW) {
+    const int side = own == 0 ? 0 : 1;
+    raw = g.bc[c][side] == FS_BC_INFLOW ? g.bcv[c][side][c] : T(0);
+  } else {
+    raw = u[idx[0] + (size_t)e[0] * (idx[1] + (size_t)e[1] * idx[2])];
+  }
+  return sign * raw + add;
+}
+
+// Workspace and plans owned by a grid (host side).
+struct Plan1D {
+  int n = 0;
+  int nst = 0;
+  int radix[FS_MAX_RADIX_STAGES];
+  void* tw = nullptr;    // device twiddles exp(-2 pi i k / n), complex of the field precision
+  void* dtw = nullptr;   // device DCT post-twiddles exp(-i pi k / (2 n)), field precision
+};
+
+struct IBDev {
+  int nm = 0;
+  int kernel = FS_ROMA3;
+  double *X0 = nullptr, *Y0 = nullptr, *ds = nullptr;  // device, markers sorted by cell
+  double *PX = nullptr, *PY = nullptr;                 // device, polygon in surface order
+  int* order = nullptr;                                // device, sorted position -> caller index
+  std::vector<int> horder;
+  double centre[2] = {0, 0};
+  double omega = 0;
+  double mass = 0, k = 0, c = 0;
+  int active[2] = {0, 0};
+  uint8_t* flags[2] = {nullptr, nullptr};  // per face: bit0 solid, bit1 IB
+  void* num[2] = {nullptr, nullptr};       // IB interpolation accumulators (field precision)
+  void* den[2] = {nullptr, nullptr};
+  void* f[2] = {nullptr, nullptr};         // direct-forcing term f of Eq. (5) (field precision)
+  double* fn = nullptr;                    // F_N per marker and component (2 * nm)
+  double* q = nullptr;                     // marker forces (2 * nm)
+  double* F = nullptr;                     // [Fx, Fy, torque]
+  bool have_forces = false;
+  double poly_bb[4] = {0, 0, 0, 0};        // rest polygon bounding box xmin, xmax, ymin, ymax
+};
+
+}  // namespace fs
+
+struct fs_grid {
+  int dim = 2, nx = 1, ny = 1, nz = 1;
+  int per[3] = {1, 1, 1};
+  int bc[3][2];
+  double bcv[3][2][3];
+  double nu = 0, rho = 1;
+  int conv = FS_CENTRAL2, scheme = FS_FE, prec = FS_FP64;
+  double hx = 1, hz = 1;
+  std::vector<double> xf[3], h[3], hf[3], th[3];
+  std::vector<double> bforce;
+  cudaStream_t stream = nullptr;
+  long long launches = 0;
+
+  // device metrics (both precisions)
+  double *ihy64 = nullptr, *ihfy64 = nullptr, *thy64 = nullptr, *bf64 = nullptr;
+  float *ihy32 = nullptr, *ihfy32 = nullptr, *thy32 = nullptr, *bf32 = nullptr;
+  double *xf64[3] = {nullptr, nullptr, nullptr};   // face coordinates (IB positions)
+  double *hy64 = nullptr;                          // cell widths in y (FP64)
+  double *hfy64 = nullptr;                         // face spacings in y (FP64, ny + 1)
+
+  // workspace (field precision)
+  void* ustar[3] = {nullptr, nullptr, nullptr};
+  void* ustage[3] = {nullptr, nullptr, nullptr};
+  void* spec = nullptr;        // real-packed spectral / pressure work array (cells)
+  double* scal = nullptr;      // small device scalars (flux sums, reductions)
+  double* red = nullptr;       // reduction partials
+
+  // Poisson plans
+  fs::Plan1D px, pz;
+  int xmode = 0;               // 0: periodic DFT, 1: DCT-II
+  int nmx = 0, nlz = 1;        // eigenvalue table extents
+  int cyclic = 0;
+  double* ya = nullptr;        // a_j couplings (ny)
+  double *tE = nullptr, *tCP = nullptr, *tZV = nullptr;   // [ny][nmx*nlz]
+  double *tFAC = nullptr, *tVL = nullptr;                 // [nmx*nlz]
+
+  fs::IBDev ib;
+  bool has_body = false;
+
+  // optional per-kernel timing (fs_profile_begin / fs_profile_end)
+  bool prof_on = false;
+  std::string prof_filter;
+  std::vector<cudaEvent_t> prof_pool;
+  size_t prof_used = 0;
+  std::vector<std::string> prof_names;
+
+  template <typename T> fs::Geom<T> geom() const;
+};
+
+namespace fs {
+// kernels launchers (stencil.cu)
+template <typename T> void launch_predictor(fs_grid* g, T* const* uin, T* const* un, T* const* out,
+                                            double dt, double a, double b, const double* body_state);
+template <typename T> void launch_outflow_flux(fs_grid* g, T* const* uin);
+template <typename T> void launch_divergence(fs_grid* g, T* const* u, T* out, const double* body_state);
+template <typename T> void launch_correct(fs_grid* g, T* const* ustar, const T* phi, T* const* unew);
+template <typename T> void launch_to_pressure(fs_grid* g, const T* phi, double* p, double scale);
+template <typename T> void launch_diagnostics(fs_grid* g, T* const* u, double* out3);
+// poisson.cu
+template <typename T> void poisson_solve_inplace(fs_grid* g, T* data);
+// ib.cu
+template <typename T> void ib_prepare(fs_grid* g, const double* body_state);
+template <typename T> void ib_forces(fs_grid* g, const double* body_state);
+void body_rk4(fs_grid* g, double* body_state, double dt);
+// errors
+int set_error(int code, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+}  // namespace fs
+
+#define FS_LAUNCHED(g) ((g)->launches++)
+
+namespace fs {
+// Brackets one kernel launch with CUDA events on the grid's stream when
+// profiling is on and the kernel name contains the profile filter.
+struct ProfMark {
+  fs_grid* g;
+  int slot = -1;
+  ProfMark(fs_grid* G, const char* name);
+  ~ProfMark();
+};
+}  // namespace fs
+
+// Launch with accounting: FS_LAUNCH(grid, "name", kernel<<<...>>>(...));
+#define FS_LAUNCH(G, NAME, ...)        \
+  do {                                 \
+    fs::ProfMark fs_pm_((G), (NAME));  \
+    __VA_ARGS__;                       \
+    FS_LAUNCHED(G);                    \
+  } while (0)

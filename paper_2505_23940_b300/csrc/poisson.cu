@@ -1,0 +1,501 @@
+// Direct solve of the discrete pressure Poisson equation D G phi = b (Eq. 9 of
+// the paper).  The paper iterates with CG; every Krylov iteration converges to
+// the same unique zero-mean solution, which this solver computes directly:
+//
+//   x: real-to-complex DFT (periodic) or DCT-II (Neumann), two rows per complex
+//      FFT, output "real-packed" so the spectrum has exactly the cell count
+//        slot 0 = Re X_0, slot 1 = Re X_{n/2}, slots 2m, 2m+1 = Re, Im X_m
+//   z: (3-D) complex FFT of slot pairs (2m, 2m+1) along z; the pair m = 0 holds
+//      two real sequences and is split into two real-packed z spectra
+//   y: per wavenumber, the remaining tridiagonal system in FP64 (Thomas with
+//      factors precomputed per eigenvalue; Sherman-Morrison for periodic y;
+//      the singular zero mode pinned and shifted to zero mean)
+//   inverse z, inverse x.
+//
+// FFTs: mixed-radix (2, 3, 4, 5, 7, 11, 13) Stockham autosort in shared memory,
+// one complex line per group of butterflies, whole lines resident per CTA.
+// Precision: the field type T for transforms (FP32 in mixed mode), FP64 for the
+// tridiagonal elimination in both modes.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+
+template <typename T>
+struct cplx {
+  T x, y;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(cplx<T> a, cplx<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> cconj(cplx<T> a) {
+  return {a.x, -a.y};
+}
+
+struct Radices {
+  int nst;
+  int r[FS_MAX_RADIX_STAGES];
+};
+
+namespace {
+
+// One Stockham stage with compile-time radix R over `nlines` lines of length N.
+template <typename T, int R>
+__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int N,
+                                               int nlines, int Ns, const cplx<T>* __restrict__ tw, bool inv) {
+  const int NR = N / R;
+  const int nb = nlines * NR;
+  const int tws = N / (Ns * R);
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int line = t / NR;
+    const int jj = t - line * NR;
+    const cplx<T>* a = in + line * N;
+    cplx<T>* b = out + line * N;
+    const int k = jj % Ns;
+    cplx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[r] = a[jj + r * NR];
+      if (r > 0 && k > 0) {
+        cplx<T> w = tw[r * k * tws];
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    // R-point DFT
+    cplx<T> o[R];
+    if (R == 2) {
+      o[0] = {v[0].x + v[1].x, v[0].y + v[1].y};
+      o[1] = {v[0].x - v[1].x, v[0].y - v[1].y};
+    } else if (R == 4) {
+      const cplx<T> s02 = {v[0].x + v[2].x, v[0].y + v[2].y}, d02 = {v[0].x - v[2].x, v[0].y - v[2].y};
+      const cplx<T> s13 = {v[1].x + v[3].x, v[1].y + v[3].y}, d13 = {v[1].x - v[3].x, v[1].y - v[3].y};
+      // -i * d13 (forward) or +i * d13 (inverse)
+      const cplx<T> rot = inv ? cplx<T>{-d13.y, d13.x} : cplx<T>{d13.y, -d13.x};
+      o[0] = {s02.x + s13.x, s02.y + s13.y};
+      o[2] = {s02.x - s13.x, s02.y - s13.y};
+      o[1] = {d02.x + rot.x, d02.y + rot.y};
+      o[3] = {d02.x - rot.x, d02.y - rot.y};
+    } else {
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        cplx<T> s = v[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          cplx<T> w = tw[NR * ((q * r) % R)];
+          if (inv) w.y = -w.y;
+          const cplx<T> p = cmul(v[r], w);
+          s.x += p.x;
+          s.y += p.y;
+        }
+        o[q] = s;
+      }
+    }
+    const int idxD = (jj / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) b[idxD + r * Ns] = o[r];
+  }
+}
+
+// In-place (ping-pong) FFT of nlines lines of length N held in shared memory.
+// Returns the buffer holding the result.
+// BIG selects the instantiation that also carries radix 7, 11 and 13 stages;
+// lengths with prime factors <= 5 use the one without, whose register count
+// is not set by those large butterflies.
+template <typename T, bool BIG>
+__device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, int N, int nlines, const Radices& rad,
+                             const cplx<T>* __restrict__ tw, bool inv) {
+  int Ns = 1;
+  for (int s = 0; s < rad.nst; ++s) {
+    const int R = rad.r[s];
+    switch (R) {
+      case 2: stockham_stage<T, 2>(a, b, N, nlines, Ns, tw, inv); break;
+      case 3: stockham_stage<T, 3>(a, b, N, nlines, Ns, tw, inv); break;
+      case 4: stockham_stage<T, 4>(a, b, N, nlines, Ns, tw, inv); break;
+      case 5: stockham_stage<T, 5>(a, b, N, nlines, Ns, tw, inv); break;
+      default:
+        if constexpr (BIG) {
+          if (R == 7) stockham_stage<T, 7>(a, b, N, nlines, Ns, tw, inv);
+          else if (R == 11) stockham_stage<T, 11>(a, b, N, nlines, Ns, tw, inv);
+          else stockham_stage<T, 13>(a, b, N, nlines, Ns, tw, inv);
+        }
+        break;
+    }
+    __syncthreads();
+    cplx<T>* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+// ---------------------------------------------------------------------------
+// x transforms: rows of length N = nx, two rows per complex line.
+// mode 0: periodic DFT (real-packed output), mode 1: DCT-II.
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, int rows, int lpb, int mode, Radices rad,
+                            const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* B = A + (size_t)lpb * N;
+  const int line0 = blockIdx.x * lpb;
+  const int nl = min(lpb, (rows + 1) / 2 - line0);
+  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+    const int l = t / N, i = t - l * N;
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    const T va = data[(size_t)r0 * N + i];
+    const T vb = r1 < rows ? data[(size_t)r1 * N + i] : T(0);
+    int dst = i;
+    if (mode == 1) dst = (i & 1) ? N - 1 - (i >> 1) : (i >> 1);   // even samples forward, odd reversed
+    A[l * N + dst] = {va, vb};
+  }
+  __syncthreads();
+  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, nl, rad, tw, false);
+  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+    const int l = t / N, s = t - l * N;
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    int m;
+    bool im = false;
+    if (mode == 0) {
+      m = s == 0 ? 0 : (s == 1 ? N / 2 : s >> 1);
+      im = s >= 2 && (s & 1);
+    } else {
+      m = s;
+    }
+    const cplx<T> z = Z[l * N + m], zr = Z[l * N + (m == 0 ? 0 : N - m)];
+    // spectra of the two real rows: XA = (Z + conj Zr) / 2, XB = (Z - conj Zr) / (2 i)
+    const cplx<T> xa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};
+    const cplx<T> xb = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};
+    T oa, ob;
+    if (mode == 0) {
+      oa = im ? xa.y : xa.x;
+      ob = im ? xb.y : xb.x;
+    } else {
+      const cplx<T> w = dtw[m];   // exp(-i pi m / (2 N))
+      oa = w.x * xa.x - w.y * xa.y;
+      ob = w.x * xb.x - w.y * xb.y;
+    }
+    data[(size_t)r0 * N + s] = oa;
+    if (r1 < rows) data[(size_t)r1 * N + s] = ob;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> unpack_packed(const T* __restrict__ row, int N, int k) {
+  // Hermitian spectrum X[k] from a real-packed row
+  if (k == 0) return {row[0], T(0)};
+  if (2 * k == N) return {row[1], T(0)};
+  if (2 * k < N) return {row[2 * k], row[2 * k + 1]};
+  const int m = N - k;
+  return {row[2 * m], -row[2 * m + 1]};
+}
+
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, int rows, int lpb, int mode, Radices rad,
+                            const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* B = A + (size_t)lpb * N;
+  const int line0 = blockIdx.x * lpb;
+  const int nl = min(lpb, (rows + 1) / 2 - line0);
+  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+    const int l = t / N, k = t - l * N;
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    const T* ra = data + (size_t)r0 * N;
+    const T* rb = data + (size_t)r1 * N;
+    cplx<T> xa, xb;
+    if (mode == 0) {
+      xa = unpack_packed(ra, N, k);
+      xb = r1 < rows ? unpack_packed(rb, N, k) : cplx<T>{T(0), T(0)};
+    } else {
+      // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
+      const cplx<T> w = cconj(dtw[k]);
+      const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
+      const T b1 = r1 < rows ? rb[k] : T(0), b2 = (r1 < rows && k) ? rb[N - k] : T(0);
+      xa = cmul(w, cplx<T>{a1, -a2});
+      xb = cmul(w, cplx<T>{b1, -b2});
+    }
+    A[l * N + k] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
+  }
+  __syncthreads();
+  cplx<T>* z = fft_smem<T, BIG>(A, B, N, nl, rad, tw, true);
+  const T inv_n = T(1) / T(N);
+  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
+    const int l = t / N, i = t - l * N;
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    int src = i;
+    if (mode == 1) src = (i & 1) ? N - 1 - (i >> 1) : (i >> 1);
+    const cplx<T> v = z[l * N + src];
+    data[(size_t)r0 * N + i] = v.x * inv_n;
+    if (r1 < rows) data[(size_t)r1 * N + i] = v.y * inv_n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// z transforms (3-D, periodic z): complex lines of slot pairs (2m, 2m+1) along z.
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx, int ny, int N, int ppb, Radices rad,
+                            const cplx<T>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* B = A + (size_t)ppb * N;
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * ppb;
+  const int np = min(ppb, nx / 2 - pair0);
+  const size_t plane = (size_t)nx * ny;
+  T* base = data + (size_t)nx * j + 2 * pair0;
+  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
+    const int k = t / (2 * np), sl = t - k * (2 * np);
+    const T v = base[plane * k + sl];
+    T* dst = reinterpret_cast<T*>(&A[(sl >> 1) * N + k]);
+    dst[sl & 1] = v;
+  }
+  __syncthreads();
+  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, np, rad, tw, false);
+  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
+    const int p = t / (2 * np), sl = t - p * (2 * np);
+    const int line = sl >> 1;
+    const int m = pair0 + line;
+    T out;
+    if (m > 0) {
+      const cplx<T> z = Z[line * N + p];
+      out = (sl & 1) ? z.y : z.x;
+    } else {
+      // pair 0 holds two real sequences: split into two real-packed z spectra
+      const int l = p == 0 ? 0 : (p == 1 ? N / 2 : p >> 1);
+      const bool im = p >= 2 && (p & 1);
+      const cplx<T> z = Z[line * N + l], zr = Z[line * N + (l == 0 ? 0 : N - l)];
+      if ((sl & 1) == 0) out = im ? T(0.5) * (z.y - zr.y) : T(0.5) * (z.x + zr.x);
+      else out = im ? T(0.5) * (zr.x - z.x) : T(0.5) * (z.y + zr.y);
+    }
+    base[plane * p + sl] = out;
+  }
+}
+
+template <typename T, bool BIG>
+__global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx, int ny, int N, int ppb, Radices rad,
+                            const cplx<T>* __restrict__ tw) {
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* B = A + (size_t)ppb * N;
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * ppb;
+  const int np = min(ppb, nx / 2 - pair0);
+  const size_t plane = (size_t)nx * ny;
+  T* base = data + (size_t)nx * j + 2 * pair0;
+  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
+    const int k = t / (2 * np), sl = t - k * (2 * np);
+    const T v = base[plane * k + sl];
+    T* dst = reinterpret_cast<T*>(&B[(sl >> 1) * N + k]);
+    dst[sl & 1] = v;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
+    const int line = t / N, l = t - line * N;
+    const int m = pair0 + line;
+    if (m > 0) {
+      A[line * N + l] = B[line * N + l];
+    } else {
+      // rebuild Z = Y0 + i Y1 from the two real-packed spectra held in .x (slot 0) and .y (slot 1)
+      cplx<T> y0, y1;
+      const cplx<T>* P = B + line * N;
+      if (l == 0) { y0 = {P[0].x, T(0)}; y1 = {P[0].y, T(0)}; }
+      else if (2 * l == N) { y0 = {P[1].x, T(0)}; y1 = {P[1].y, T(0)}; }
+      else if (2 * l < N) { y0 = {P[2 * l].x, P[2 * l + 1].x}; y1 = {P[2 * l].y, P[2 * l + 1].y}; }
+      else { const int q = N - l; y0 = {P[2 * q].x, -P[2 * q + 1].x}; y1 = {P[2 * q].y, -P[2 * q + 1].y}; }
+      A[line * N + l] = {y0.x - y1.y, y0.y + y1.x};
+    }
+  }
+  __syncthreads();
+  cplx<T>* z = fft_smem<T, BIG>(A, B, N, np, rad, tw, true);
+  const T inv_n = T(1) / T(N);
+  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
+    const int k = t / (2 * np), sl = t - k * (2 * np);
+    const cplx<T> v = z[(sl >> 1) * N + k];
+    base[plane * k + sl] = ((sl & 1) ? v.y : v.x) * inv_n;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// y solve: one thread per (slot s, z position t) column; FP64 Thomas with
+// factors e_j = 1 / beta_j and c'_j tabulated per eigenvalue index.
+struct YArgs {
+  int nx, ny, nz, dim, xmode, nlz, cyclic;
+  const double* a;       // a_j
+  const double* E;       // [ny][nlam]
+  const double* CP;
+  const double* ZV;
+  const double* FAC;     // [nlam]
+  const double* VL;
+  const double* hy;      // cell widths (zero-mode mean)
+};
+
+__device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
+  int mx;
+  if (A.xmode == 1) mx = s;
+  else mx = s == 0 ? 0 : (s == 1 ? A.nx / 2 : (s >> 1));
+  if (A.dim == 2) return mx;
+  int l = (s >= 2 || A.xmode == 1) ? t : (t == 0 ? 0 : (t == 1 ? A.nz / 2 : (t >> 1)));
+  const int lz = min(l, A.nz - l);
+  return mx * A.nlz + lz;
+}
+
+template <typename T>
+__global__ void ysolve_kernel(T* __restrict__ data, const YArgs A) {
+  extern __shared__ double dp[];   // [ny][blockDim.x]
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = blockIdx.y;
+  const bool active = s < A.nx;
+  const int bw = blockDim.x;
+  const int nlam = (A.xmode == 1 ? A.nx : A.nx / 2 + 1) * A.nlz;
+  if (!active) return;
+  const int li = lam_index(A, s, t);
+  T* col = data + s + (size_t)A.nx * A.ny * t;
+  double prev = 0.0;
+  for (int j = 0; j < A.ny; ++j) {
+    const double d = (double)col[(size_t)A.nx * j];
+    const double e = A.E[(size_t)j * nlam + li];
+    prev = (j == 0) ? d * e : (d - A.a[j] * prev) * e;
+    dp[j * bw + threadIdx.x] = prev;
+  }
+  double x = prev;
+  for (int j = A.ny - 2; j >= 0; --j) {
+    x = dp[j * bw + threadIdx.x] - A.CP[(size_t)j * nlam + li] * x;
+    dp[j * bw + threadIdx.x] = x;
+  }
+  const bool singular = li == 0;
+  if (A.cyclic && !singular) {
+    const double f = (dp[threadIdx.x] + A.VL[li] * dp[(A.ny - 1) * bw + threadIdx.x]) * A.FAC[li];
+    for (int j = 0; j < A.ny; ++j) dp[j * bw + threadIdx.x] -= f * A.ZV[(size_t)j * nlam + li];
+  }
+  double mean = 0.0;
+  if (singular) {
+    double sw = 0.0, sx = 0.0;
+    for (int j = 0; j < A.ny; ++j) {
+      sx += dp[j * bw + threadIdx.x] * A.hy[j];
+      sw += A.hy[j];
+    }
+    mean = sx / sw;
+  }
+  for (int j = 0; j < A.ny; ++j) col[(size_t)A.nx * j] = (T)(dp[j * bw + threadIdx.x] - mean);
+}
+
+template <typename T>
+size_t fft_smem_bytes(int N, int lines) {
+  return 2ull * lines * N * sizeof(cplx<T>);
+}
+
+Radices radices_of(const Plan1D& p) {
+  Radices r;
+  r.nst = p.nst;
+  for (int i = 0; i < FS_MAX_RADIX_STAGES; ++i) r.r[i] = i < p.nst ? p.radix[i] : 1;
+  return r;
+}
+
+constexpr size_t kSmemBudget = 96 * 1024;
+
+template <typename T, bool BIG>
+void set_smem_attrs_big() {
+  cudaFuncSetAttribute(xfwd_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(xinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(zfwd_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(zinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+}
+
+template <typename T>
+void set_smem_attrs() {
+  static bool done = false;
+  if (done) return;
+  set_smem_attrs_big<T, false>();
+  set_smem_attrs_big<T, true>();
+  cudaFuncSetAttribute(ysolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  done = true;
+}
+
+bool has_big(const Plan1D& p) {
+  for (int i = 0; i < p.nst; ++i)
+    if (p.radix[i] > 5) return true;
+  return false;
+}
+
+}  // namespace
+
+int ysolve_threads(int ny) {
+  // dp staging: ny doubles per thread column
+  if ((size_t)ny * 64 * 8 <= 160 * 1024) return 64;
+  return 32;
+}
+
+template <typename T>
+void poisson_solve_inplace(fs_grid* G, T* data) {
+  set_smem_attrs<T>();
+  const int nx = G->nx, ny = G->ny, nz = G->nz;
+  const int rows = ny * nz;
+  // x forward
+  {
+    int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
+    lpb = lpb > 16 ? 16 : (lpb < 1 ? 1 : lpb);
+    const int lines = (rows + 1) / 2;
+    const int nb = (lines + lpb - 1) / lpb;
+    auto k = has_big(G->px) ? xfwd_kernel<T, true> : xfwd_kernel<T, false>;
+    FS_LAUNCH(G, "fft_x_fwd", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
+                                                          (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
+  }
+  int ppb = 0;
+  if (G->dim == 3) {
+    ppb = (int)(kSmemBudget / fft_smem_bytes<T>(nz, 1));
+    ppb = ppb > 16 ? 16 : (ppb < 1 ? 1 : ppb);
+    if (ppb > nx / 2) ppb = nx / 2;
+    dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
+    auto k = has_big(G->pz) ? zfwd_kernel<T, true> : zfwd_kernel<T, false>;
+    FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+                                                            (const cplx<T>*)G->pz.tw));
+  }
+  {
+    YArgs A;
+    A.nx = nx;
+    A.ny = ny;
+    A.nz = nz;
+    A.dim = G->dim;
+    A.xmode = G->xmode;
+    A.nlz = G->nlz;
+    A.cyclic = G->cyclic;
+    A.a = G->ya;
+    A.E = G->tE;
+    A.CP = G->tCP;
+    A.ZV = G->tZV;
+    A.FAC = G->tFAC;
+    A.VL = G->tVL;
+    A.hy = G->hy64;
+    const int th = ysolve_threads(ny);
+    dim3 grid((nx + th - 1) / th, G->dim == 3 ? nz : 1);
+    FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, th, (size_t)ny * th * sizeof(double), G->stream>>>(data, A));
+  }
+  if (G->dim == 3) {
+    dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
+    auto k = has_big(G->pz) ? zinv_kernel<T, true> : zinv_kernel<T, false>;
+    FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+                                                            (const cplx<T>*)G->pz.tw));
+  }
+  {
+    int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
+    lpb = lpb > 16 ? 16 : (lpb < 1 ? 1 : lpb);
+    const int lines = (rows + 1) / 2;
+    const int nb = (lines + lpb - 1) / lpb;
+    auto k = has_big(G->px) ? xinv_kernel<T, true> : xinv_kernel<T, false>;
+    FS_LAUNCH(G, "fft_x_inv", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
+                                                          (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
+  }
+}
+
+template void poisson_solve_inplace<float>(fs_grid*, float*);
+template void poisson_solve_inplace<double>(fs_grid*, double*);
+
+}  // namespace fs

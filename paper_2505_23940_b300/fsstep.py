@@ -1,0 +1,232 @@
+"""ctypes binding of the C ABI in include/fs.h (argument marshalling only).
+
+Every step of the solver runs in the CUDA library libfsstep.so; this module
+loads it (failing loudly when it is missing), mirrors the C structs, and keeps
+torch tensors as the caller-owned device buffers the ABI expects.  torch is
+used for device memory and streams only.
+"""
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int, c_longlong, c_void_p
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libfsstep.so")
+
+FS_OK, FS_ERR_ARG, FS_ERR_CUDA, FS_ERR_DIVERGED, FS_ERR_TIMEOUT, FS_ERR_UNSUPPORTED, FS_ERR_STATE = \
+    0, -1, -2, -3, -4, -5, -6
+PERIODIC, NOSLIP, FREESLIP, INFLOW, OUTFLOW = 0, 1, 2, 3, 4
+CENTRAL2, UPWIND1 = 0, 1
+FE, RK3 = 0, 1
+FP64, MIXED = 0, 1
+PESKIN4, ROMA3 = 0, 1
+
+
+class FsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fs error %d: %s" % (code, msg))
+        self.code = code
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("dim", c_int), ("n", c_int * 3), ("xf", POINTER(c_double) * 3), ("bc", (c_int * 2) * 3),
+                ("bc_val", ((c_double * 3) * 2) * 3), ("nu", c_double), ("rho", c_double),
+                ("conv_scheme", c_int), ("time_scheme", c_int), ("precision", c_int),
+                ("body_force", POINTER(c_double))]
+
+
+class State(ctypes.Structure):
+    _fields_ = [("u", c_void_p * 3), ("p", c_void_p), ("body", c_void_p)]
+
+
+class BodyDesc(ctypes.Structure):
+    _fields_ = [("nm", c_int), ("X0", POINTER(c_double)), ("Y0", POINTER(c_double)), ("ds", POINTER(c_double)),
+                ("centre", c_double * 2), ("omega", c_double), ("mass", c_double), ("stiffness", c_double),
+                ("damping", c_double), ("active", c_int * 2), ("delta_kernel", c_int)]
+
+
+class ParamGrad(ctypes.Structure):
+    _fields_ = [("body_force", c_void_p), ("stiffness", c_void_p)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load libfsstep.so once; raise if it has not been built (there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIBPATH):
+            raise ImportError("libfsstep.so is not built: run paper_2505_23940_b300/build.py")
+        L = ctypes.CDLL(LIBPATH)
+        L.fs_create_grid.argtypes = [POINTER(GridDesc), c_void_p, POINTER(c_void_p)]
+        L.fs_destroy_grid.argtypes = [c_void_p]
+        L.fs_set_stream.argtypes = [c_void_p, c_void_p]
+        L.fs_field_extent.argtypes = [c_void_p, c_int, POINTER(c_int)]
+        L.fs_set_ib_markers.argtypes = [c_void_p, POINTER(BodyDesc)]
+        L.fs_step.argtypes = [c_void_p, POINTER(State), c_double, c_int]
+        L.fs_step_adjoint.argtypes = [c_void_p, POINTER(State), POINTER(State), POINTER(c_double),
+                                      POINTER(ParamGrad), c_double]
+        L.fs_solve_pressure.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.fs_forces.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]
+        L.fs_diagnostics.argtypes = [c_void_p, POINTER(State), POINTER(c_double)]
+        L.fs_kernel_launches.argtypes = [c_void_p]
+        L.fs_kernel_launches.restype = c_longlong
+        L.fs_last_error.restype = ctypes.c_char_p
+        L.fs_profile_begin.argtypes = [c_void_p, ctypes.c_char_p]
+        L.fs_profile_end.argtypes = [c_void_p, ctypes.c_char_p, c_int]
+        _LIB = L
+    return _LIB
+
+
+def check(rc):
+    if rc != FS_OK:
+        raise FsError(rc, lib().fs_last_error().decode())
+    return rc
+
+
+def _dptr(arr):
+    import numpy as np
+    a = np.ascontiguousarray(arr, dtype=np.float64)
+    return a, a.ctypes.data_as(POINTER(c_double))
+
+
+class Grid:
+    """One solver grid on the current CUDA device (wraps fs_grid)."""
+
+    def __init__(self, dim, n, xf, bc, bc_val=None, nu=0.0, rho=1.0, conv=CENTRAL2, scheme=FE,
+                 precision=FP64, body_force=None, stream=None):
+        L = lib()
+        d = GridDesc()
+        d.dim = dim
+        n = list(n) + [1] * (3 - len(n))
+        for i in range(3):
+            d.n[i] = int(n[i])
+        self._keep = []
+        for i in range(dim):
+            a, p = _dptr(xf[i])
+            self._keep.append(a)
+            d.xf[i] = p
+        bc = list(bc) + [(PERIODIC, PERIODIC)] * (3 - len(bc))
+        for i in range(3):
+            for s in range(2):
+                d.bc[i][s] = int(bc[i][s])
+                vals = (bc_val[i][s] if bc_val is not None and i < len(bc_val) else [0.0, 0.0, 0.0])
+                vals = list(vals) + [0.0] * (3 - len(vals))
+                for c in range(3):
+                    d.bc_val[i][s][c] = float(vals[c])
+        d.nu, d.rho = float(nu), float(rho)
+        d.conv_scheme, d.time_scheme, d.precision = int(conv), int(scheme), int(precision)
+        if body_force is not None:
+            a, p = _dptr(body_force)
+            self._keep.append(a)
+            d.body_force = p
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = c_void_p()
+        check(L.fs_create_grid(byref(d), c_void_p(self.stream.cuda_stream), byref(h)))
+        self.h = h
+        self.dim = dim
+        self.n = n
+        self.precision = precision
+        self.dtype = torch.float64 if precision == FP64 else torch.float32
+        self.has_body = False
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) and _LIB is not None:
+                _LIB.fs_destroy_grid(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    def extent(self, comp):
+        e = (c_int * 3)()
+        check(lib().fs_field_extent(self.h, comp, e))
+        return tuple(e)
+
+    def shape(self, comp):
+        ex, ey, ez = self.extent(comp)
+        return (ez, ey, ex)
+
+    def zeros(self):
+        return [torch.zeros(self.shape(c), dtype=self.dtype, device="cuda") for c in range(self.dim)]
+
+    def set_body(self, X0, Y0, ds, centre, omega=0.0, mass=0.0, stiffness=0.0, damping=0.0,
+                 active=(False, False), kernel=ROMA3):
+        b = BodyDesc()
+        b.nm = len(X0)
+        ax, px = _dptr(X0)
+        ay, py = _dptr(Y0)
+        ad, pd = _dptr(ds)
+        b.X0, b.Y0, b.ds = px, py, pd
+        b.centre[0], b.centre[1] = float(centre[0]), float(centre[1])
+        b.omega, b.mass, b.stiffness, b.damping = float(omega), float(mass), float(stiffness), float(damping)
+        b.active[0], b.active[1] = int(bool(active[0])), int(bool(active[1]))
+        b.delta_kernel = int(kernel)
+        check(lib().fs_set_ib_markers(self.h, byref(b)))
+        self.has_body = True
+        self.nm = b.nm
+
+    def _state(self, u, p=None, body=None):
+        s = State()
+        for c in range(self.dim):
+            assert u[c].is_cuda and u[c].dtype == self.dtype and u[c].is_contiguous()
+            assert tuple(u[c].shape) == self.shape(c)
+            s.u[c] = u[c].data_ptr()
+        s.p = p.data_ptr() if p is not None else None
+        s.body = body.data_ptr() if body is not None else None
+        return s
+
+    def step(self, u, dt, nsteps=1, p=None, body=None):
+        s = self._state(u, p, body)
+        check(lib().fs_step(self.h, byref(s), float(dt), int(nsteps)))
+
+    def step_adjoint(self, u_n, lam, dt, body_n=None, lam_body=None, dJdF=None, g_body_force=None,
+                     g_stiffness=None):
+        sn = self._state(u_n, None, body_n)
+        sl = self._state(lam, None, lam_body)
+        g = ParamGrad()
+        g.body_force = g_body_force.data_ptr() if g_body_force is not None else None
+        g.stiffness = g_stiffness.data_ptr() if g_stiffness is not None else None
+        dj = None
+        if dJdF is not None:
+            dj = (c_double * 2)(*[float(x) for x in dJdF])
+        check(lib().fs_step_adjoint(self.h, byref(sn), byref(sl), dj, byref(g), float(dt)))
+
+    def solve_pressure(self, rhs, p=None):
+        p = torch.empty_like(rhs) if p is None else p
+        check(lib().fs_solve_pressure(self.h, c_void_p(rhs.data_ptr()), c_void_p(p.data_ptr())))
+        return p
+
+    def forces(self, with_q=False):
+        F = (c_double * 2)()
+        tq = c_double()
+        q = (c_double * (2 * self.nm))() if with_q else None
+        check(lib().fs_forces(self.h, F, byref(tq), q))
+        out = (F[0], F[1]), tq.value
+        if with_q:
+            return out + ([(q[2 * i], q[2 * i + 1]) for i in range(self.nm)],)
+        return out
+
+    def diagnostics(self, u):
+        s = self._state(u)
+        out = (c_double * 3)()
+        check(lib().fs_diagnostics(self.h, byref(s), out))
+        return {"umax": out[0], "divmax": out[1], "ke": out[2]}
+
+    def launches(self):
+        return int(lib().fs_kernel_launches(self.h))
+
+    def profile_begin(self, filter_=""):
+        check(lib().fs_profile_begin(self.h, filter_.encode()))
+
+    def profile_end(self):
+        """{kernel name: (launches, total ms)} of the launches since profile_begin (synchronises)."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        check(lib().fs_profile_end(self.h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split()
+            out[name] = (int(cnt), float(ms))
+        return out

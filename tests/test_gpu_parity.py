@@ -1,0 +1,158 @@
+"""GPU vs oracle parity of the forward step through the C ABI (Eqs. 4-10, 18-23, 12).
+
+Tolerances: relative L2 over all velocity components <= 1e-11 for FP64 grids,
+<= 1e-5 for mixed-precision grids (FP32 stencils / transforms, FP64 tridiagonal,
+reductions and body ODE), as the north star of this hot path states."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synthetic as S
+from gpu_util import field_err, run_gpu, run_oracle
+from helpers import grid_of
+
+pytestmark = pytest.mark.gpu
+P, NS, FS, IN, OUT = S.PERIODIC, S.NOSLIP, S.FREESLIP, S.INFLOW, S.OUTFLOW
+TOL64, TOLMIX = 1e-11, 1e-5
+
+
+def test_taylor_green_64_fp64_100_steps():
+    """The 2-D Taylor-Green workload: 64^2, nu = 0.01, CFL 0.5, 100 forward-Euler steps."""
+    wl = S.taylor_green_2d(64, 0.01)
+    gp = run_gpu(wl, 100)
+    st, _, g = run_oracle(wl, 100)
+    assert field_err(gp["u"], st.u) < TOL64
+    ex = [torch.tensor(a) for a in S.taylor_green_exact(64, 0.01, 100 * wl.dt)]
+    assert field_err(gp["u"], ex) < 5e-3
+    d = gp["grid"].diagnostics(gp["u_dev"])
+    assert d["divmax"] < 1e-10
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk3"])
+@pytest.mark.parametrize("conv", ["central", "upwind"])
+def test_periodic_3d_fp64(scheme, conv):
+    wl = S.box_3d(16, 12, 8, (P, P), (P, P), L=(1.0, 0.75, 0.5), nu=0.02)
+    wl.conv, wl.scheme, wl.dt = conv, scheme, 0.004
+    wl.u0 = S.random_fields(wl, 4, 0.5)
+    gp = run_gpu(wl, 8)
+    st, _, _ = run_oracle(wl, 8)
+    assert field_err(gp["u"], st.u) < TOL64
+
+
+def test_channel_stretched_fp64_with_pressure():
+    wl = S.box_3d(16, 12, 8, (P, P), (NS, NS), L=(2.0, 2.0, 1.0), stretched=1.5, nu=0.05)
+    wl.body_force = np.linspace(0.5, 1.5, 12)
+    wl.dt = 0.002
+    wl.u0 = S.random_fields(wl, 5, 1.0)
+    gp = run_gpu(wl, 10, want_p=True)
+    st, dg, g = run_oracle(wl, 10)
+    assert field_err(gp["u"], st.u) < TOL64
+    p_or = dg.phi * g.rho / wl.dt
+    assert float((gp["p"] - p_or).abs().max()) < 1e-9 * float(p_or.abs().max())
+
+
+@pytest.mark.parametrize("bcx,bcy,gamma,n", [
+    ((P, P), (NS, NS), 0.0, (16, 12)),
+    ((P, P), (FS, FS), 1.2, (12, 10)),
+    ((IN, OUT), (FS, FS), 0.0, (24, 12)),
+    ((NS, NS), (FS, FS), 0.0, (9, 10)),        # odd DCT length
+    ((FS, FS), (NS, NS), 1.1, (14, 8)),        # radix 7
+    ((P, P), (P, P), 0.0, (22, 26)),           # radices 11 and 13
+])
+def test_2d_boundary_combinations_fp64(bcx, bcy, gamma, n):
+    bc_val = [[[1.0, 0, 0], [0, 0, 0]], [[0.3, 0, 0], [0.0, 0, 0]]]
+    wl = S.box_2d(n[0], n[1], bcx, bcy, Lx=1.3, Ly=1.0, stretched=gamma, nu=0.02, bc_val=bc_val)
+    wl.dt = 0.002
+    wl.u0 = S.random_fields(wl, 6, 1.0)
+    gp = run_gpu(wl, 6)
+    st, _, _ = run_oracle(wl, 6)
+    assert field_err(gp["u"], st.u) < TOL64
+    assert gp["grid"].diagnostics(gp["u_dev"])["divmax"] < 1e-10
+
+
+@pytest.mark.parametrize("kind,wl", [
+    ("2d", S.box_2d(12, 10, (P, P), (NS, NS), stretched=1.3)),
+    ("2d", S.box_2d(9, 7, (IN, OUT), (FS, FS))),
+    ("2d", S.box_2d(28, 6, (P, P), (P, P))),
+    ("3d", S.box_3d(16, 12, 8, (P, P), (NS, NS), stretched=1.5)),
+    ("3d", S.box_3d(12, 8, 10, (P, P), (P, P))),
+])
+def test_solve_pressure_fp64(kind, wl):
+    from paper_2505_23940_b300 import grid_from_workload
+    from oracle import fluid, poisson
+    g = grid_of(wl)
+    rng = np.random.default_rng(8)
+    u = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(g.dim)]
+    u = fluid.apply_boundary_values(g, u)
+    u = fluid.outflow_faces(g, u, u)
+    b = fluid.divergence(g, u)
+    ref = poisson.solve(g, b)
+    G = grid_from_workload(wl, "fp64")
+    p = G.solve_pressure(b.cuda().contiguous())
+    torch.cuda.synchronize()
+    assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+
+
+def _small_cyl(kernel, precision="fp64", omega=0.0):
+    wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, kernel=kernel, centre_d=(2.0, 2.0),
+                       precision=precision, seed=3, perturb=0.05, omega=omega)
+    wl.body.w0 = (0.0, 0.05)
+    return wl
+
+
+@pytest.mark.parametrize("kernel", [S.ROMA3, S.PESKIN4])
+def test_cylinder_fsi_fp64(kernel):
+    wl = _small_cyl(kernel)
+    gp = run_gpu(wl, 10)
+    st, dg, _ = run_oracle(wl, 10)
+    assert field_err(gp["u"], st.u) < TOL64
+    assert float((gp["body"][:2] - st.w).abs().max()) < 1e-12
+    assert float((gp["body"][2:] - st.wd).abs().max()) < 1e-11
+    F, _ = gp["F"]
+    assert abs(F[0] - float(dg.F[0])) < 1e-10 * abs(float(dg.F[0]))
+    assert abs(F[1] - float(dg.F[1])) < 1e-9 * max(abs(float(dg.F[1])), 1e-3)
+
+
+def test_cylinder_rotating_surface_fp64():
+    wl = _small_cyl(S.ROMA3, omega=1.5)
+    gp = run_gpu(wl, 5)
+    st, _, _ = run_oracle(wl, 5)
+    assert field_err(gp["u"], st.u) < TOL64
+
+
+def test_mixed_taylor_green_100_steps():
+    wl = S.taylor_green_2d(64, 0.01)
+    gp = run_gpu(wl, 100, precision="mixed")
+    st, _, _ = run_oracle(wl, 100)
+    assert field_err(gp["u"], st.u) < TOLMIX
+
+
+def test_mixed_isotropic_32_rk3():
+    wl = S.isotropic_3d(n=32, steps=20)
+    gp = run_gpu(wl, 20, precision="mixed")
+    st, _, _ = run_oracle(wl, 20)
+    assert field_err(gp["u"], st.u) < TOLMIX
+
+
+def test_mixed_channel_small_100_steps():
+    wl = S.channel_3d(nx=24, ny=16, nz=16, steps=100)
+    gp = run_gpu(wl, 100, precision="mixed")
+    st, _, _ = run_oracle(wl, 100)
+    assert field_err(gp["u"], st.u) < TOLMIX
+
+
+def test_mixed_cylinder_small():
+    wl = _small_cyl(S.ROMA3, precision="mixed")
+    gp = run_gpu(wl, 20)
+    st, _, _ = run_oracle(wl, 20)
+    assert field_err(gp["u"], st.u) < TOLMIX
+    assert float((gp["body"][:2] - st.w).abs().max()) < 1e-7
+
+
+def test_zero_steps_is_identity():
+    wl = S.taylor_green_2d(16, 0.01)
+    gp = run_gpu(wl, 0)
+    assert field_err(gp["u"], [torch.tensor(a) for a in wl.u0]) == 0.0
