@@ -190,6 +190,30 @@ long long fs_kernel_launches(const fs_grid* grid);
 int fs_profile_begin(fs_grid* grid, const char* filter);
 int fs_profile_end(fs_grid* grid, char* report, int len);
 
+/* Allocation-free statistics of one velocity component (the paper has no
+ * counterpart; this is a library service).  For callers that may not call
+ * cudaMalloc -- e.g. a host application whose device memory belongs to its
+ * own pool allocator, or a loop where an allocation's implicit device
+ * synchronisation is not allowed -- and therefore cannot create an fs_grid.
+ * Computes, on `stream`, out[0] = sum over the field of 0.5 u^2 vol w_j and
+ * out[1] = max |u|, where w_j = wy[j] for the row index j of each element
+ * (wy: device, ext[1] doubles, or NULL for w_j = 1).
+ *   u          device, dense x-fastest array of ext[0] * ext[1] * ext[2]
+ *              elements, double (FS_FP64) or float (FS_MIXED)
+ *   out        device, 2 doubles, written by the GPU (read it after the stream)
+ * Allocates nothing: its reduction scratch is a fixed 64 KiB file-scope
+ * device array present on every device that loads the library, until exit.
+ * The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the scratch: calls that overlap on the GPU (different
+ * streams, no ordering between them) race and give wrong results.  Each call
+ * overwrites every scratch slot it reads, so nothing needs clearing.
+ * Errors: FS_ERR_ARG for NULL pointers, bad precision or extents, and for
+ * fields of more than 33,554,432 elements (the scratch holds 4096 partials of
+ * 8192 elements each); FS_ERR_CUDA for a failed launch. */
+int fs_component_stats_noalloc(const void* u, int precision, const int ext[3], double vol,
+                               const double* wy, double* out, void* stream);
+
 /* Text of the calling thread's last error ("" if none). */
 const char* fs_last_error(void);
 

@@ -76,6 +76,8 @@ def lib():
         L.fs_last_error.restype = ctypes.c_char_p
         L.fs_profile_begin.argtypes = [c_void_p, ctypes.c_char_p]
         L.fs_profile_end.argtypes = [c_void_p, ctypes.c_char_p, c_int]
+        L.fs_component_stats_noalloc.argtypes = [c_void_p, c_int, POINTER(c_int), c_double, c_void_p, c_void_p,
+                                                 c_void_p]
         _LIB = L
     return _LIB
 
