@@ -1,0 +1,849 @@
+// Discrete adjoint of one time step (fs_step_adjoint), §2.4.1 of the paper:
+// the paper differentiates its solver by reverse-mode AD; this file is the
+// hand-written transpose of every kernel of the forward step, so
+//   lam^n = (d step / d state^n)^T lam^{n+1}   (plus parameter gradients).
+//
+//   predictor   R'(u)^T mu: the exact reverse of the per-face forward flux
+//               computation, scattered to the faces it read (ghost rules
+//               transposed), plus the direct-forcing and RK terms
+//   projection  P^T = I - D^T V S V^-1 G^T (L = D G is symmetric in the
+//               cell-volume inner product), the same direct Poisson solver S
+//   outflow     transpose of the flux-balanced zero-gradient face
+//   IB          force spreading transposed (marker -> grid), the marker
+//               position derivative through phi'(r); the epsilon mask is
+//               frozen (its derivative is zero almost everywhere)
+//   body        reverse of the four RK4 stages, d/dk accumulated (FP64)
+//
+// Adjoint fields have the precision of the grid's fields; gradient
+// accumulators and body adjoints are FP64.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "fs_internal.cuh"
+
+namespace fs {
+
+namespace {
+
+constexpr int kT = 256;
+
+// Transpose of ldv: add v to the adjoint of the stored value that ldv would
+// read at (i, j, k) for component c; imposed boundary values absorb nothing.
+template <typename T>
+__device__ __forceinline__ void adj_add(const Geom<T>& g, T* __restrict__ lam, int c, int i, int j, int k, T v) {
+  int idx[3] = {i, j, k};
+  int e[3] = {g.ext(c, 0), g.ext(c, 1), g.ext(c, 2)};
+  T sign = T(1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int q = idx[d];
+    if (q < 0 || q >= e[d]) {
+      const int side = q < 0 ? 0 : 1;
+      if (g.per[d]) {
+        q = side ? q - e[d] : q + e[d];
+      } else {
+        q = side ? e[d] - 1 : 0;
+        if (d != c && bc_dirichlet(g.bc[d][side])) sign = -sign;
+      }
+      idx[d] = q;
+    }
+  }
+  const int own = idx[c];
+  if (!g.per[c] && (own == 0 || own == e[c] - 1) && g.bc[c][own == 0 ? 0 : 1] != FS_BC_OUTFLOW) return;
+  atomicAdd(lam + idx[0] + e[0] * (idx[1] + e[1] * idx[2]), sign * v);
+}
+
+// Reverse of momentum_rhs for the C-face (i, j, k): adds (dR/du)^T * gm to lam.
+template <typename T, int C>
+__device__ __forceinline__ void rhs_adjoint_face(const Geom<T>& g, const T* const* u, T* const* lam, int conv,
+                                                 int i, int j, int k, T gm) {
+  const int idx[3] = {i, j, k};
+  constexpr int cx = C == 0, cy = C == 1, cz = C == 2;
+  {
+    const T uW = ldv(g, u[C], C, i - cx, j - cy, k - cz);
+    const T u0 = ldv(g, u[C], C, i, j, k);
+    const T uE = ldv(g, u[C], C, i + cx, j + cy, k + cz);
+    const T TE = T(0.5) * (u0 + uE), TW = T(0.5) * (uW + u0);
+    T ihf, ihE, ihW;
+    if (C == 1) {
+      ihf = g.ihfy[j];
+      ihE = g.ihy[j < g.ny ? j : g.ny - 1];
+      ihW = g.ihy[j > 0 ? j - 1 : (g.per[1] ? g.ny - 1 : 0)];
+    } else {
+      ihf = ihE = ihW = (C == 0) ? g.ihx : g.ihz;
+    }
+    // R = -(TE QE - TW QW) ihf + nu ((uE - u0) ihE - (u0 - uW) ihW) ihf
+    const T gE = -gm * ihf, gW = gm * ihf;   // adjoints of TE*QE and TW*QW
+    T aW = T(0), a0 = T(0), aE = T(0);
+    if (conv == FS_UPWIND1) {
+      const T QE = TE > T(0) ? u0 : uE, QW = TW > T(0) ? uW : u0;
+      a0 += T(0.5) * gE * QE;
+      aE += T(0.5) * gE * QE;
+      if (TE > T(0)) a0 += gE * TE; else aE += gE * TE;
+      aW += T(0.5) * gW * QW;
+      a0 += T(0.5) * gW * QW;
+      if (TW > T(0)) aW += gW * TW; else a0 += gW * TW;
+    } else {
+      a0 += gE * TE + gW * TW;     // d(T^2) = 2 T dT, dT = (du0 + duE) / 2
+      aE += gE * TE;
+      aW += gW * TW;
+    }
+    const T nd = gm * g.nu * ihf;
+    aE += nd * ihE;
+    a0 -= nd * (ihE + ihW);
+    aW += nd * ihW;
+    adj_add(g, lam[C], C, i - cx, j - cy, k - cz, aW);
+    adj_add(g, lam[C], C, i, j, k, a0);
+    adj_add(g, lam[C], C, i + cx, j + cy, k + cz, aE);
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if (d == C || d >= g.dim) continue;
+    const int dx = d == 0, dy = d == 1, dz = d == 2;
+    const T thc = (C == 1) ? g.thy[j] : T(0.5);
+    const T A1 = ldv(g, u[d], d, i + dx - cx, j + dy - cy, k + dz - cz);
+    const T A2 = ldv(g, u[d], d, i + dx, j + dy, k + dz);
+    const T B1 = ldv(g, u[d], d, i - cx, j - cy, k - cz);
+    const T B2 = ldv(g, u[d], d, i, j, k);
+    const T TN = (T(1) - thc) * A1 + thc * A2;
+    const T TS = (T(1) - thc) * B1 + thc * B2;
+    const T uS = ldv(g, u[C], C, i - dx, j - dy, k - dz);
+    const T u0 = ldv(g, u[C], C, i, j, k);
+    const T uN = ldv(g, u[C], C, i + dx, j + dy, k + dz);
+    const int m = idx[d];
+    T thN, thS, ihd, ihfN, ihfS;
+    if (d == 1) {
+      thN = g.thy[m + 1];
+      thS = g.thy[m];
+      ihd = g.ihy[m];
+      ihfN = g.ihfy[m + 1];
+      ihfS = g.ihfy[m];
+    } else {
+      thN = thS = T(0.5);
+      ihd = ihfN = ihfS = (d == 0) ? g.ihx : g.ihz;
+    }
+    T QN, QS;
+    if (conv == FS_UPWIND1) {
+      QN = TN > T(0) ? u0 : uN;
+      QS = TS > T(0) ? uS : u0;
+    } else {
+      QN = (T(1) - thN) * u0 + thN * uN;
+      QS = (T(1) - thS) * uS + thS * u0;
+    }
+    // R = -(TN QN - TS QS) ihd + nu ((uN - u0) ihfN - (u0 - uS) ihfS) ihd
+    const T gN = -gm * ihd, gS = gm * ihd;
+    const T gTN = gN * QN, gQN = gN * TN, gTS = gS * QS, gQS = gS * TS;
+    adj_add(g, lam[d], d, i + dx - cx, j + dy - cy, k + dz - cz, (T(1) - thc) * gTN);
+    adj_add(g, lam[d], d, i + dx, j + dy, k + dz, thc * gTN);
+    adj_add(g, lam[d], d, i - cx, j - cy, k - cz, (T(1) - thc) * gTS);
+    adj_add(g, lam[d], d, i, j, k, thc * gTS);
+    T aS = T(0), a0 = T(0), aN = T(0);
+    if (conv == FS_UPWIND1) {
+      if (TN > T(0)) a0 += gQN; else aN += gQN;
+      if (TS > T(0)) aS += gQS; else a0 += gQS;
+    } else {
+      a0 += (T(1) - thN) * gQN + thS * gQS;
+      aN += thN * gQN;
+      aS += (T(1) - thS) * gQS;
+    }
+    const T nd = gm * g.nu * ihd;
+    aN += nd * ihfN;
+    a0 -= nd * (ihfN + ihfS);
+    aS += nd * ihfS;
+    adj_add(g, lam[C], C, i - dx, j - dy, k - dz, aS);
+    adj_add(g, lam[C], C, i, j, k, a0);
+    adj_add(g, lam[C], C, i + dx, j + dy, k + dz, aN);
+  }
+}
+
+template <typename T>
+struct RhsAdjArgs {
+  Geom<T> g;
+  const T* u[3];     // state the forward R was evaluated at
+  const T* mu[3];    // adjoint of R on each face (0 on boundary faces)
+  T* lam[3];         // receives R'(u)^T mu
+  int conv;
+  int X, Y;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kT) rhs_adjoint_kernel(const RhsAdjArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= A.X || j >= A.Y) return;
+  const Geom<T>& g = A.g;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (c >= g.dim) break;
+    const int ex = g.ext(c, 0), ey = g.ext(c, 1), ez = g.ext(c, 2);
+    if (i >= ex || j >= ey || k >= ez) continue;
+    const T gm = A.mu[c][i + ex * (j + ey * k)];
+    if (gm == T(0)) continue;
+    if (c == 0) rhs_adjoint_face<T, 0>(g, A.u, A.lam, A.conv, i, j, k, gm);
+    else if (c == 1) rhs_adjoint_face<T, 1>(g, A.u, A.lam, A.conv, i, j, k, gm);
+    else rhs_adjoint_face<T, 2>(g, A.u, A.lam, A.conv, i, j, k, gm);
+  }
+}
+
+// x = -(G^T lam) / V at every cell: the right-hand side of the adjoint Poisson solve.
+template <typename T>
+__global__ void __launch_bounds__(kT) adj_rhs_kernel(const Geom<T> g, const T* __restrict__ l0,
+                                                     const T* __restrict__ l1, const T* __restrict__ l2,
+                                                     const double* __restrict__ hy, T* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  const T* L[3] = {l0, l1, l2};
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int p[3] = {i, j, k};
+  T gt = T(0);
+  for (int c = 0; c < g.dim; ++c) {
+    const int ex = g.ext(c, 0), ey = g.ext(c, 1);
+    // face f = cell (left face) and f + 1 (right face) along c
+    const bool lo_in = g.per[c] || p[c] > 0;
+    const bool hi_in = g.per[c] || p[c] + 1 < n[c];
+    int q[3] = {i, j, k};
+    const T ihf_lo = c == 0 ? g.ihx : (c == 1 ? g.ihfy[j] : g.ihz);
+    if (lo_in) gt += L[c][q[0] + ex * (q[1] + ey * q[2])] * ihf_lo;
+    q[c] = p[c] + 1;
+    if (g.per[c] && q[c] == n[c]) q[c] = 0;
+    const T ihf_hi = c == 0 ? g.ihx : (c == 1 ? g.ihfy[j + 1] : g.ihz);
+    if (hi_in) gt -= L[c][q[0] + ex * (q[1] + ey * q[2])] * ihf_hi;
+  }
+  const double V = (double)g.hx * hy[j] * (g.dim == 3 ? (double)g.hz : 1.0);
+  out[i + g.nx * (j + g.ny * k)] = T(-(double)gt / V);
+}
+
+// lam~ on face f of component c: D^T (V y) = A(f-1) y[f-1] - A(f) y[f], A = V / h_c.
+template <typename T>
+__device__ __forceinline__ T adj_div_T(const Geom<T>& g, const T* __restrict__ y, const double* __restrict__ hy,
+                                       int c, int i, int j, int k) {
+  const int n[3] = {g.nx, g.ny, g.nz};
+  const int p[3] = {i, j, k};
+  const double hz = g.dim == 3 ? (double)g.hz : 1.0;
+  double r = 0.0;
+  // cell f - 1 (left of the face)
+  int q[3] = {i, j, k};
+  bool have = true;
+  if (p[c] == 0) {
+    if (g.per[c]) q[c] = n[c] - 1; else have = false;
+  } else {
+    q[c] = p[c] - 1;
+  }
+  auto area = [&](int jj) {
+    if (c == 0) return hy[jj] * hz;
+    if (c == 1) return (double)g.hx * hz;
+    return (double)g.hx * hy[jj];
+  };
+  if (have) r += area(q[1]) * (double)y[q[0] + g.nx * (q[1] + g.ny * q[2])];
+  if (p[c] < n[c]) r -= area(j) * (double)y[i + g.nx * (j + g.ny * k)];
+  return T(r);
+}
+
+// Per-face adjoint of projection + predictor (forward Euler, optional body).
+template <typename T>
+struct FaceAdjArgs {
+  Geom<T> g;
+  const T* lam1[3];      // lambda of u^{n+1}
+  const T* y;            // adjoint pressure (solved)
+  const double* hy;
+  T dt;
+  // forward Euler with body
+  const uint8_t* flags[2];
+  const T* lamf[2];      // adjoint of the forcing term f (forced faces)
+  double* wdsum;         // [2] accumulators: adjoint of the body velocity (FP64)
+  double* bfsum;         // [ny] accumulators: adjoint of the body-force profile, or null
+  T* mu[3];              // out: adjoint of R (0 on boundary faces)
+  T* lamn[3];            // out: direct part of lambda of u^n
+  T* lamout;             // out: lambda of u* on the outflow faces [nz][ny], or null
+  // RK stage: lam_acc += a lam~, lamn = b lam~, mu = b dt lam~
+  int rk;
+  T a, b;
+  T* lacc[3];
+  int X, Y;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kT) face_adj_kernel(const FaceAdjArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const Geom<T>& g = A.g;
+  double wsum[2] = {0.0, 0.0};
+  double bsum = 0.0;
+  const bool in = i < A.X && j < A.Y;
+  if (in) {
+    for (int c = 0; c < g.dim; ++c) {
+      const int ex = g.ext(c, 0), ey = g.ext(c, 1), ez = g.ext(c, 2);
+      if (i >= ex || j >= ey || k >= ez) continue;
+      const int t = i + ex * (j + ey * k);
+      const int p[3] = {i, j, k};
+      const int ec = c == 0 ? ex : (c == 1 ? ey : ez);
+      const bool boundary = !g.per[c] && (p[c] == 0 || p[c] == ec - 1);
+      const T lt = adj_div_T(g, A.y, A.hy, c, i, j, k);
+      const T l1 = A.lam1[c][t];
+      if (A.rk) {
+        // u_new = P(a u^n + b (v + dt R(v))): lam~ = P^T lam (boundary faces are imposed)
+        const T lw = boundary ? T(0) : l1 + lt;
+        A.lacc[c][t] += A.a * lw;
+        A.lamn[c][t] = A.b * lw;
+        A.mu[c][t] = A.b * A.dt * lw;
+        if (c == 0 && A.bfsum && !boundary) bsum += (double)(A.b * A.dt * lw);
+        continue;
+      }
+      if (boundary) {
+        A.mu[c][t] = T(0);
+        A.lamn[c][t] = T(0);
+        if (c == 0 && p[0] == ec - 1 && g.bc[0][1] == FS_BC_OUTFLOW && A.lamout)
+          A.lamout[j + g.ny * k] = l1 + lt;   // u^{n+1} = u* = u~ on the outflow face
+        continue;
+      }
+      const bool forced = c < 2 && A.flags[0] && A.flags[c][t];
+      T mu, direct;
+      if (forced) {
+        // u* = u_s, f = -R + (u_s - u)/dt, u~ = u_c on forced faces
+        const T lf = A.lamf[c][t];
+        mu = -lf;
+        direct = -lf / A.dt;
+        wsum[c] += (double)lt + (double)l1 + (double)lf / (double)A.dt;
+      } else {
+        const T ls = l1 + lt;
+        mu = A.dt * ls;
+        direct = ls;
+      }
+      A.mu[c][t] = mu;
+      A.lamn[c][t] = direct;
+      if (c == 0 && A.bfsum) bsum += (double)mu;
+    }
+  }
+  // body-velocity adjoint sums (2-D bodies): warp reduce, one atomic per warp
+  if (A.wdsum) {
+    for (int c = 0; c < 2; ++c) {
+      double v = wsum[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&A.wdsum[c], v);
+    }
+  }
+  // body-force profile: the 32 threads of a warp share the row j
+  if (A.bfsum) {
+    double v = bsum;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && in && v != 0.0) atomicAdd(&A.bfsum[j], v);
+  }
+}
+
+// Outflow face u*[n] = s u[n-1], s = Q_in / sum u[n-1] A: transpose into lam of u^n[n-1].
+template <typename T>
+__global__ void outflow_adj_kernel(const T* __restrict__ u0, const T* __restrict__ lamout, T* __restrict__ lamn0,
+                                   int ex, int ny, int nz, const double* __restrict__ hy, double hz, double q_in) {
+  __shared__ double s1[kT], s2[kT];
+  double qo = 0.0, lu = 0.0;
+  for (int t = threadIdx.x; t < ny * nz; t += blockDim.x) {
+    const int j = t % ny, k = t / ny;
+    const double v = (double)u0[(ex - 2) + ex * (j + ny * k)];
+    qo += v * hy[j] * hz;
+    lu += (double)lamout[t] * v;
+  }
+  s1[threadIdx.x] = qo;
+  s2[threadIdx.x] = lu;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  const double Qo = s1[0], LU = s2[0];
+  const double s = q_in / Qo;
+  for (int t = threadIdx.x; t < ny * nz; t += blockDim.x) {
+    const int j = t % ny, k = t / ny;
+    const int idx = (ex - 2) + ex * (j + ny * k);
+    const double area = hy[j] * hz;
+    lamn0[idx] += T(s * (double)lamout[t] - s * area / Qo * LU);
+  }
+}
+
+// ---- immersed boundary and body ------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T phi_val(int kind, T r) {
+  const T a = fabs(r);
+  if (kind == FS_PESKIN4) {
+    if (a <= T(1)) return (T(3) - T(2) * a + sqrt(fmax(T(1) + T(4) * a - T(4) * a * a, T(0)))) * T(0.125);
+    if (a <= T(2)) return (T(5) - T(2) * a - sqrt(fmax(T(-7) + T(12) * a - T(4) * a * a, T(0)))) * T(0.125);
+    return T(0);
+  }
+  if (a <= T(0.5)) return (T(1) + sqrt(fmax(T(1) - T(3) * a * a, T(0)))) / T(3);
+  if (a <= T(1.5)) {
+    const T b = T(1) - a;
+    return (T(5) - T(3) * a - sqrt(fmax(T(1) - T(3) * b * b, T(0)))) / T(6);
+  }
+  return T(0);
+}
+
+// d phi / d r of the same kernels (odd in r).
+template <typename T>
+__device__ __forceinline__ T phi_der(int kind, T r) {
+  const T a = fabs(r);
+  const T sg = r < T(0) ? T(-1) : T(1);
+  T d = T(0);
+  if (kind == FS_PESKIN4) {
+    if (a <= T(1)) {
+      const T q = T(1) + T(4) * a - T(4) * a * a;
+      d = (T(-2) + (q > T(0) ? (T(4) - T(8) * a) / (T(2) * sqrt(q)) : T(0))) * T(0.125);
+    } else if (a <= T(2)) {
+      const T q = T(-7) + T(12) * a - T(4) * a * a;
+      d = (T(-2) - (q > T(0) ? (T(12) - T(8) * a) / (T(2) * sqrt(q)) : T(0))) * T(0.125);
+    }
+  } else {
+    if (a <= T(0.5)) {
+      const T q = T(1) - T(3) * a * a;
+      d = (q > T(0) ? (T(-6) * a) / (T(2) * sqrt(q)) : T(0)) / T(3);
+    } else if (a <= T(1.5)) {
+      const T b = T(1) - a;
+      const T q = T(1) - T(3) * b * b;
+      // d/da of sqrt(1 - 3 (1 - a)^2) = 6 (1 - a) / (2 sqrt(q))
+      d = (T(-3) - (q > T(0) ? (T(6) * b) / (T(2) * sqrt(q)) : T(0))) / T(6);
+    }
+  }
+  return sg * d;
+}
+
+struct IBAdjGeom {
+  int ex[2], ey[2];
+  double x0c[2], y0c[2];
+  double hx, hy;
+  int kind, width;
+  const double* xf;
+  const double* yf;
+  const double* hyv;
+  const double* hfyv;
+};
+
+__device__ __forceinline__ int first_node_adj(const IBAdjGeom& G, double X, double x0, double h) {
+  const double s = (X - x0) / h;
+  return G.kind == FS_PESKIN4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+}
+__device__ __forceinline__ double nodex(const IBAdjGeom& G, int c, int i) {
+  return c == 0 ? G.xf[i] : __dmul_rn(0.5, __dadd_rn(G.xf[i], G.xf[i + 1]));
+}
+__device__ __forceinline__ double nodey(const IBAdjGeom& G, int c, int j) {
+  return c == 1 ? G.yf[j] : __dmul_rn(0.5, __dadd_rn(G.yf[j], G.yf[j + 1]));
+}
+
+// lam_f(x) = - sum_i lam_q_i delta(x - X_i) dv(x), lam_q_i = rho dV_i lam_F (Eq. 20 transposed);
+// lam_X_i = sum_c lam_q_ic sum_x f_c(x) dv(x) d delta / d r (x - X_i).
+template <typename T>
+__global__ void ib_force_adj_kernel(const IBAdjGeom G, int nm, const double* __restrict__ X0,
+                                    const double* __restrict__ Y0, const double* __restrict__ ds,
+                                    const double* __restrict__ body, const double* __restrict__ lamF, double rho,
+                                    const T* __restrict__ f0, const T* __restrict__ f1, T* lf0, T* lf1,
+                                    double* __restrict__ lamX) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * nm) return;
+  const int m = t >> 1, c = t & 1;
+  const double X = X0[m] + body[0], Y = Y0[m] + body[1];
+  const double lq = rho * ds[m] * G.hx * lamF[c];
+  const T* f = c == 0 ? f0 : f1;
+  T* lf = c == 0 ? lf0 : lf1;
+  const int i0 = first_node_adj(G, X, G.x0c[c], G.hx), j0 = first_node_adj(G, Y, G.y0c[c], G.hy);
+  double gx = 0.0, gy = 0.0;
+  for (int b = 0; b < G.width; ++b) {
+    const int j = j0 + b;
+    if (j < 0 || j >= G.ey[c]) continue;
+    const double ry = (nodey(G, c, j) - Y) / G.hy;
+    const T py = phi_val<T>(G.kind, T(ry)), dpy = phi_der<T>(G.kind, T(ry));
+    const double dvy = c == 0 ? G.hyv[j] : G.hfyv[j];
+    for (int a = 0; a < G.width; ++a) {
+      const int i = i0 + a;
+      if (i < 0 || i >= G.ex[c]) continue;
+      const double rx = (nodex(G, c, i) - X) / G.hx;
+      const T px = phi_val<T>(G.kind, T(rx)), dpx = phi_der<T>(G.kind, T(rx));
+      const double dv = G.hx * dvy;
+      const double inv = 1.0 / (G.hx * G.hy);
+      const size_t fi = (size_t)j * G.ex[c] + i;
+      atomicAdd(&lf[fi], T(-lq * (double)(px * py) * inv * dv));
+      const double fv = (double)f[fi] * dv;
+      gx += fv * (double)(dpx * py) * inv / G.hx;
+      gy += fv * (double)(px * dpy) * inv / G.hy;
+    }
+  }
+  lamX[2 * t] = lq * gx;
+  lamX[2 * t + 1] = lq * gy;
+}
+
+// Reverse of the RK4 step of Eq. (12) per active DOF; body state and adjoints in FP64.
+//   lamb:  in lam of (w, wdot)^{n+1}, out: lam of (w, wdot)^n from the ODE
+//   lamF:  out lam of F^n (plus the direct dJ/dF)
+__global__ void rk4_adj_kernel(const double* __restrict__ st, const double* __restrict__ F, double* __restrict__ lamb,
+                               double* __restrict__ lamF, const double* __restrict__ dJdF, double m, double k,
+                               double c, int ax, int ay, double dt, int dynamic, double* __restrict__ gk) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int act[2] = {ax, ay};
+  double dk = 0.0;
+  for (int d = 0; d < 2; ++d) {
+    const double lw1 = lamb[d], lv1 = lamb[2 + d];
+    double lF = dJdF[d];
+    if (!dynamic) {   // static body: state carried through unchanged
+      lamF[d] = lF;
+      continue;
+    }
+    if (!act[d]) {
+      lamb[d] = 0.0;
+      lamb[2 + d] = 0.0;
+      lamF[d] = lF;
+      continue;
+    }
+    const double f = F[d], h = dt;
+    const double x0 = st[d], v0 = st[2 + d];
+    auto acc = [&](double x, double v) { return (f - c * v - k * x) / m; };
+    // forward stages
+    const double k1x = v0, k1v = acc(x0, v0);
+    const double x1 = x0 + 0.5 * h * k1x, v1 = v0 + 0.5 * h * k1v;
+    const double k2x = v1, k2v = acc(x1, v1);
+    const double x2 = x0 + 0.5 * h * k2x, v2 = v0 + 0.5 * h * k2v;
+    const double k3x = v2, k3v = acc(x2, v2);
+    const double x3 = x0 + h * k3x, v3 = v0 + h * k3v;
+    (void)k3x;
+    // reverse
+    double lx0 = lw1, lv0 = lv1;
+    double lk1x = h / 6.0 * lw1, lk2x = h / 3.0 * lw1, lk3x = h / 3.0 * lw1, lk4x = h / 6.0 * lw1;
+    double lk1v = h / 6.0 * lv1, lk2v = h / 3.0 * lv1, lk3v = h / 3.0 * lv1, lk4v = h / 6.0 * lv1;
+    // k4v = acc(x3, v3), k4x = v3
+    double lx3 = -k / m * lk4v, lv3 = -c / m * lk4v + lk4x;
+    lF += lk4v / m;
+    dk += -x3 / m * lk4v;
+    lx0 += lx3;
+    lk3x += h * lx3;
+    lv0 += lv3;
+    lk3v += h * lv3;
+    // k3v = acc(x2, v2), k3x = v2
+    double lx2 = -k / m * lk3v, lv2 = -c / m * lk3v + lk3x;
+    lF += lk3v / m;
+    dk += -x2 / m * lk3v;
+    lx0 += lx2;
+    lk2x += 0.5 * h * lx2;
+    lv0 += lv2;
+    lk2v += 0.5 * h * lv2;
+    // k2v = acc(x1, v1), k2x = v1
+    double lx1 = -k / m * lk2v, lv1s = -c / m * lk2v + lk2x;
+    lF += lk2v / m;
+    dk += -x1 / m * lk2v;
+    lx0 += lx1;
+    lk1x += 0.5 * h * lx1;
+    lv0 += lv1s;
+    lk1v += 0.5 * h * lv1s;
+    // k1v = acc(x0, v0), k1x = v0
+    lx0 += -k / m * lk1v;
+    lv0 += -c / m * lk1v + lk1x;
+    lF += lk1v / m;
+    dk += -x0 / m * lk1v;
+    lamb[d] = lx0;
+    lamb[2 + d] = lv0;
+    lamF[d] = lF;
+  }
+  if (gk) *gk += dk;
+}
+
+// lam of (w, wdot)^n += position adjoint (sum over markers) + fluid sums of the body velocity.
+__global__ void body_adj_finish_kernel(int nm, const double* __restrict__ lamX, const double* __restrict__ wdsum,
+                                       double* __restrict__ lamb) {
+  __shared__ double sx[kT], sy[kT];
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < 2 * nm; t += blockDim.x) {
+    a += lamX[2 * t];
+    b += lamX[2 * t + 1];
+  }
+  sx[threadIdx.x] = a;
+  sy[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      sx[threadIdx.x] += sx[threadIdx.x + o];
+      sy[threadIdx.x] += sy[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    lamb[0] += sx[0];
+    lamb[1] += sy[0];
+    lamb[2] += wdsum[0];
+    lamb[3] += wdsum[1];
+  }
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* __restrict__ y, const T* __restrict__ x, long long n) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] += x[t];
+}
+
+IBAdjGeom make_ib_adj_geom(const fs_grid* G) {
+  IBAdjGeom g;
+  for (int c = 0; c < 2; ++c) {
+    g.ex[c] = G->nx + ((c == 0 && !G->per[0]) ? 1 : 0);
+    g.ey[c] = G->ny + ((c == 1 && !G->per[1]) ? 1 : 0);
+  }
+  g.hx = G->hx;
+  g.hy = G->h[1][0];
+  g.x0c[0] = G->xf[0][0];
+  g.x0c[1] = 0.5 * (G->xf[0][0] + G->xf[0][1]);
+  g.y0c[0] = 0.5 * (G->xf[1][0] + G->xf[1][1]);
+  g.y0c[1] = G->xf[1][0];
+  g.kind = G->ib.kernel;
+  g.width = G->ib.kernel == FS_PESKIN4 ? 4 : 3;
+  g.xf = G->xf64[0];
+  g.yf = G->xf64[1];
+  g.hyv = G->hy64;
+  g.hfyv = G->hfy64;
+  return g;
+}
+
+size_t comp_count(const fs_grid* G, int c) {
+  size_t s = 1;
+  const int n[3] = {G->nx, G->ny, G->nz};
+  for (int d = 0; d < 3; ++d) s *= (size_t)(n[d] + ((c == d && !G->per[d]) ? 1 : 0));
+  return s;
+}
+
+template <typename T>
+void launch_rhs_adjoint(fs_grid* G, T* const* u, T* const* mu, T* const* lam) {
+  RhsAdjArgs<T> A;
+  A.g = G->geom<T>();
+  for (int c = 0; c < 3; ++c) {
+    A.u[c] = c < G->dim ? u[c] : nullptr;
+    A.mu[c] = c < G->dim ? mu[c] : nullptr;
+    A.lam[c] = c < G->dim ? lam[c] : nullptr;
+  }
+  A.conv = G->conv;
+  A.X = G->nx + (G->per[0] ? 0 : 1);
+  A.Y = G->ny + (G->per[1] ? 0 : 1);
+  const dim3 blk(32, 8), grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+}
+
+// adjoint Poisson: spec = S (V^-1 (-G^T lam))
+template <typename T>
+void launch_projection_adjoint_solve(fs_grid* G, T* const* lam, T* spec) {
+  const Geom<T> g = G->geom<T>();
+  const dim3 blk(32, 8), grd((G->nx + 31) / 32, (G->ny + 7) / 8, G->nz);
+  FS_LAUNCH(G, "adj_rhs", adj_rhs_kernel<T><<<grd, blk, 0, G->stream>>>(g, lam[0], lam[1], G->dim == 3 ? lam[2] : lam[1],
+                                                                        G->hy64, spec));
+  poisson_solve_inplace<T>(G, spec);
+}
+
+}  // namespace
+
+// Adjoint work buffers (allocated on the first adjoint call of a grid).
+struct AdjBuffers {
+  void* mu[3] = {nullptr, nullptr, nullptr};
+  void* lamn[3] = {nullptr, nullptr, nullptr};
+  void* lacc[3] = {nullptr, nullptr, nullptr};
+  void* v1[3] = {nullptr, nullptr, nullptr};
+  void* v2[3] = {nullptr, nullptr, nullptr};
+  void* lamf[2] = {nullptr, nullptr};
+  void* lamout = nullptr;
+  double* scal = nullptr;   // [0..1] lamF, [2..3] wdsum, [4..5] dJdF, [8..] lamX (2 * 2 * nm)
+};
+
+int adj_buffers(fs_grid* G, AdjBuffers** out) {
+  if (G->adj) {
+    *out = (AdjBuffers*)G->adj;
+    return FS_OK;
+  }
+  AdjBuffers* B = new AdjBuffers();
+  const size_t es = G->prec == FS_MIXED ? 4 : 8;
+  bool ok = true;
+  for (int c = 0; c < G->dim && ok; ++c) {
+    const size_t n = comp_count(G, c) * es;
+    ok = cudaMalloc(&B->mu[c], n) == cudaSuccess && cudaMalloc(&B->lamn[c], n) == cudaSuccess &&
+         cudaMalloc(&B->lacc[c], n) == cudaSuccess;
+    if (ok && G->scheme == FS_RK3)
+      ok = cudaMalloc(&B->v1[c], n) == cudaSuccess && cudaMalloc(&B->v2[c], n) == cudaSuccess;
+  }
+  if (ok && G->has_body)
+    for (int c = 0; c < 2 && ok; ++c) ok = cudaMalloc(&B->lamf[c], comp_count(G, c) * es) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&B->lamout, (size_t)G->ny * G->nz * es) == cudaSuccess;
+  const size_t ns = 16 + 4 * (size_t)(G->has_body ? G->ib.nm : 0);
+  if (ok) ok = cudaMalloc(&B->scal, ns * sizeof(double)) == cudaSuccess;
+  if (!ok) {
+    free_adj_buffers(B);
+    return set_error(FS_ERR_CUDA, "allocating adjoint buffers");
+  }
+  G->adj = B;
+  *out = B;
+  return FS_OK;
+}
+
+void free_adj_buffers(void* p) {
+  AdjBuffers* B = (AdjBuffers*)p;
+  if (!B) return;
+  auto F = [](void* q) {
+    if (q) cudaFree(q);
+  };
+  for (int c = 0; c < 3; ++c) {
+    F(B->mu[c]);
+    F(B->lamn[c]);
+    F(B->lacc[c]);
+    F(B->v1[c]);
+    F(B->v2[c]);
+  }
+  F(B->lamf[0]);
+  F(B->lamf[1]);
+  F(B->lamout);
+  F(B->scal);
+  delete B;
+}
+
+template <typename T>
+int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJdF, fs_param_grad* pg, double dt) {
+  AdjBuffers* B = nullptr;
+  int rc = adj_buffers(G, &B);
+  if (rc != FS_OK) return rc;
+  const int dim = G->dim;
+  T* u[3] = {(T*)st->u[0], (T*)st->u[1], (T*)(dim == 3 ? st->u[2] : nullptr)};
+  T* L[3] = {(T*)lam->u[0], (T*)lam->u[1], (T*)(dim == 3 ? lam->u[2] : nullptr)};
+  T* mu[3] = {(T*)B->mu[0], (T*)B->mu[1], (T*)B->mu[2]};
+  T* ln[3] = {(T*)B->lamn[0], (T*)B->lamn[1], (T*)B->lamn[2]};
+  T* la[3] = {(T*)B->lacc[0], (T*)B->lacc[1], (T*)B->lacc[2]};
+  T* spec = (T*)G->spec;
+  const Geom<T> g = G->geom<T>();
+  const int X = G->nx + (G->per[0] ? 0 : 1), Y = G->ny + (G->per[1] ? 0 : 1);
+  const dim3 blk(32, 8), grd((X + 31) / 32, (Y + 7) / 8, G->nz);
+  double* bfsum = pg ? pg->body_force : nullptr;
+
+  if (G->scheme == FS_RK3) {
+    // recompute the stage states v1, v2 of the forward step
+    T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
+    T* v1[3] = {(T*)B->v1[0], (T*)B->v1[1], (T*)B->v1[2]};
+    T* v2[3] = {(T*)B->v2[0], (T*)B->v2[1], (T*)B->v2[2]};
+    const double Ac[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+    launch_predictor<T>(G, u, u, us, dt, Ac[0], Bc[0], nullptr);
+    poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
+    launch_correct<T>(G, us, spec, v1);
+    launch_predictor<T>(G, v1, u, us, dt, Ac[1], Bc[1], nullptr);
+    poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
+    launch_correct<T>(G, us, spec, v2);
+    T* const* vs[3] = {u, v1, v2};
+    for (int c = 0; c < dim; ++c) cudaMemsetAsync(la[c], 0, comp_count(G, c) * sizeof(T), G->stream);
+    // cur = lam of the stage output, starting from lam^{n+1}
+    T* cur[3] = {L[0], L[1], L[2]};
+    for (int s = 2; s >= 0; --s) {
+      launch_projection_adjoint_solve<T>(G, cur, spec);
+      FaceAdjArgs<T> A{};
+      A.g = g;
+      for (int c = 0; c < 3; ++c) {
+        A.lam1[c] = cur[c];
+        A.mu[c] = mu[c];
+        A.lamn[c] = ln[c];
+        A.lacc[c] = la[c];
+      }
+      A.y = spec;
+      A.hy = G->hy64;
+      A.dt = (T)dt;
+      A.rk = 1;
+      A.a = (T)Ac[s];
+      A.b = (T)Bc[s];
+      A.bfsum = bfsum;
+      A.X = X;
+      A.Y = Y;
+      FS_LAUNCH(G, "face_adjoint", face_adj_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+      // lam of v_s = b lam~ + R'(v_s)^T (b dt lam~)
+      launch_rhs_adjoint<T>(G, vs[s], mu, ln);
+      if (s > 0) {
+        for (int c = 0; c < dim; ++c) {
+          // the next stage reads cur; stage s-1 output adjoint becomes ln: swap buffers through lam->u
+          cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+          cur[c] = L[c];
+        }
+      }
+    }
+    // lam^n = lam_acc + lam of v_0 (= u^n)
+    for (int c = 0; c < dim; ++c) {
+      const long long n = (long long)comp_count(G, c);
+      FS_LAUNCH(G, "axpy", axpy_kernel<T><<<(int)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0,
+                                          G->stream>>>(la[c], ln[c], n));
+      cudaMemcpyAsync(L[c], la[c], n * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+    }
+    return cuda_check(cudaGetLastError(), "fs_step_adjoint (RK3)");
+  }
+
+  // ---- forward Euler (optional body) ------------------------------------------
+  IBDev& ib = G->ib;
+  double* sc = B->scal;
+  const bool body = G->has_body;
+  if (body) {
+    // recompute the classification, u*, f and F of the forward step from the state at n
+    T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
+    ib_prepare<T>(G, st->body);
+    launch_outflow_flux<T>(G, u);
+    launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
+    ib_forces<T>(G, st->body);
+    double h4[4] = {dJdF ? dJdF[0] : 0.0, dJdF ? dJdF[1] : 0.0, 0.0, 0.0};
+    cudaMemcpyAsync(sc + 4, h4, 2 * sizeof(double), cudaMemcpyHostToDevice, G->stream);
+    cudaMemsetAsync(sc + 2, 0, 2 * sizeof(double), G->stream);
+    // body ODE reverse: lam of (w, wdot)^{n+1} -> ODE part of lam^n, lam_F, dJ/dk
+    FS_LAUNCH(G, "rk4_adjoint", rk4_adj_kernel<<<1, 32, 0, G->stream>>>(
+                                    st->body, ib.F, lam->body, sc, sc + 4, ib.mass, ib.k, ib.c, ib.active[0],
+                                    ib.active[1], dt, ib.mass > 0 ? 1 : 0, pg ? pg->stiffness : nullptr));
+    // force reverse: lam_f on the grid, marker position adjoint
+    for (int c = 0; c < 2; ++c) cudaMemsetAsync(B->lamf[c], 0, comp_count(G, c) * sizeof(T), G->stream);
+    const IBAdjGeom ig = make_ib_adj_geom(G);
+    FS_LAUNCH(G, "ib_force_adjoint", ib_force_adj_kernel<T><<<(2 * ib.nm + 127) / 128, 128, 0, G->stream>>>(
+                                         ig, ib.nm, ib.X0, ib.Y0, ib.ds, st->body, sc, G->rho, (const T*)ib.f[0],
+                                         (const T*)ib.f[1], (T*)B->lamf[0], (T*)B->lamf[1], sc + 8));
+  } else if (G->bc[0][1] == FS_BC_OUTFLOW && !G->per[0]) {
+    launch_outflow_flux<T>(G, u);
+  }
+  launch_projection_adjoint_solve<T>(G, L, spec);
+  FaceAdjArgs<T> A{};
+  A.g = g;
+  for (int c = 0; c < 3; ++c) {
+    A.lam1[c] = L[c];
+    A.mu[c] = mu[c];
+    A.lamn[c] = ln[c];
+  }
+  A.y = spec;
+  A.hy = G->hy64;
+  A.dt = (T)dt;
+  A.rk = 0;
+  if (body) {
+    A.flags[0] = ib.flags[0];
+    A.flags[1] = ib.flags[1];
+    A.lamf[0] = (const T*)B->lamf[0];
+    A.lamf[1] = (const T*)B->lamf[1];
+    A.wdsum = sc + 2;
+  }
+  A.bfsum = bfsum;
+  A.lamout = (T*)B->lamout;
+  A.X = X;
+  A.Y = Y;
+  FS_LAUNCH(G, "face_adjoint", face_adj_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+  launch_rhs_adjoint<T>(G, u, mu, ln);
+  if (!G->per[0] && G->bc[0][1] == FS_BC_OUTFLOW) {
+    double q_in = 0.0;
+    if (G->bc[0][0] == FS_BC_INFLOW) {
+      double area = 0.0;
+      for (int j = 0; j < G->ny; ++j) area += G->h[1][j];
+      area *= (G->dim == 3 ? G->hz * G->nz : 1.0);
+      q_in = G->bcv[0][0][0] * area;
+    }
+    FS_LAUNCH(G, "outflow_adjoint", outflow_adj_kernel<T><<<1, kT, 0, G->stream>>>(
+                                        u[0], (const T*)B->lamout, ln[0], G->nx + 1, G->ny, G->nz, G->hy64,
+                                        G->dim == 3 ? G->hz : 1.0, q_in));
+  }
+  if (body)
+    FS_LAUNCH(G, "body_adjoint", body_adj_finish_kernel<<<1, kT, 0, G->stream>>>(ib.nm, sc + 8, sc + 2, lam->body));
+  for (int c = 0; c < dim; ++c)
+    cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+  return cuda_check(cudaGetLastError(), "fs_step_adjoint");
+}
+
+template int step_adjoint<float>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double);
+template int step_adjoint<double>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double);
+
+}  // namespace fs

@@ -145,7 +145,7 @@ int build_tables(fs_grid* G) {
     for (int lz = 0; lz < G->nlz; ++lz) {
       const double lzv = G->dim == 3 ? -(2.0 - 2.0 * std::cos(2.0 * M_PI * lz / nz)) / (G->hz * G->hz) : 0.0;
       const double lam = lx + lzv;
-      const int li = mx * G->nlz + lz;
+      const int li = lz * G->nmx + mx;   // [j][lz][mx] layout
       const bool sing = (mx == 0 && lz == 0);
       for (int j = 0; j < ny; ++j) diag[j] = -(a[j] + c[j]) + lam;
       double gam = 0, alpha = 0, beta = 0;
@@ -234,8 +234,7 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
     for (int s = 0; s < 3; ++s) {
       T* const* in = s == 0 ? u : v;
       launch_predictor<T>(G, in, u, us, dt, A[s], Bc[s], nullptr);
-      launch_divergence<T>(G, us, spec, nullptr);
-      poisson_solve_inplace<T>(G, spec);
+      poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
       launch_correct<T>(G, us, spec, s == 2 ? u : v);
     }
     if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / (Bc[2] * dt));
@@ -244,8 +243,7 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
   if (G->has_body) ib_prepare<T>(G, st->body);
   launch_outflow_flux<T>(G, u);
   launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
-  launch_divergence<T>(G, us, spec, st->body);
-  poisson_solve_inplace<T>(G, spec);
+  poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, st->body), spec);
   launch_correct<T>(G, us, spec, u);
   if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / dt);
   if (G->has_body) {
@@ -408,9 +406,13 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
     delete G;
     return set_error(FS_ERR_UNSUPPORTED, "transform length with a prime factor > 13");
   }
-  if ((size_t)G->ny * 32 * 8 > 200 * 1024) {
+  if ((double)(G->nx + 1) * (G->ny + 1) * (G->nz + 1) >= 2147483647.0) {
     delete G;
-    return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 800)");
+    return set_error(FS_ERR_UNSUPPORTED, "fields of 2^31 or more elements (32-bit kernel indexing)");
+  }
+  if ((size_t)G->ny * 8 * 8 > 160 * 1024) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 2560)");
   }
   if (D->body_force) G->bforce.assign(D->body_force, D->body_force + G->ny);
 
@@ -462,6 +464,7 @@ int fs_destroy_grid(fs_grid* G) {
   if (!G) return FS_OK;
   cudaStreamSynchronize(G->stream);
   for (cudaEvent_t e : G->prof_pool) cudaEventDestroy(e);
+  free_adj_buffers(G->adj);
   free_all(G);
   delete G;
   return FS_OK;
@@ -625,9 +628,18 @@ int fs_step(fs_grid* G, fs_state* st, double dt, int nsteps) {
 
 int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, fs_param_grad* g,
                     double dt) {
-  (void)st_n; (void)lam; (void)dJdF; (void)g; (void)dt;
-  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
-  return set_error(FS_ERR_UNSUPPORTED, "adjoint not built in this library version");
+  if (!G || !st_n || !lam) return set_error(FS_ERR_ARG, "NULL argument");
+  if (!(dt > 0)) return set_error(FS_ERR_ARG, "the adjoint needs the fixed step dt > 0 of the forward step");
+  for (int c = 0; c < G->dim; ++c)
+    if (!st_n->u[c] || !lam->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
+  if (G->has_body) {
+    if (!st_n->body || !lam->body) return set_error(FS_ERR_ARG, "a grid with a body needs st_n->body and lam->body");
+    if (G->ib.omega != 0.0)
+      return set_error(FS_ERR_UNSUPPORTED, "adjoint of a body with a prescribed surface rotation");
+  }
+  const int rc = G->prec == FS_MIXED ? step_adjoint<float>(G, st_n, lam, dJdF, g, dt)
+                                     : step_adjoint<double>(G, st_n, lam, dJdF, g, dt);
+  return rc;
 }
 
 int fs_solve_pressure(fs_grid* G, const double* rhs, double* p) {

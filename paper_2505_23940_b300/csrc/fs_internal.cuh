@@ -78,6 +78,72 @@ __device__ __forceinline__ T ldv(const Geom<T>& g, const T* __restrict__ u, int 
   return sign * raw + add;
 }
 
+// Rigid velocity V + omega x (r - r_c) at face position (px, py) (Eq. 23, solid points).
+__device__ __forceinline__ void rigid_velocity(const double* body, double omega, double cx, double cy,
+                                               double px, double py, double& vx, double& vy) {
+  const double wx = body[0], wy = body[1];
+  vx = body[2] - omega * (py - (cy + wy));
+  vy = body[3] + omega * (px - (cx + wx));
+}
+
+// Inputs of the divergence D[(1 - eps) u* + eps u_c] of Eq. (9).
+template <typename T>
+struct DivArgs {
+  Geom<T> g;
+  const T* u[3];
+  const uint8_t* flags[2];   // IB flags (2-D) or null
+  const double* body;
+  double omega, cx, cy;
+  const double* xf;
+  const double* yf;
+};
+
+// (1 - eps) u* + eps u_c on face t of component c: forced faces take the exact
+// solid velocity u_c (Eq. 9), the others u*.
+template <typename T>
+__device__ __forceinline__ T blended(const DivArgs<T>& A, int c, int t, int i, int j) {
+  if (A.flags[0] && c < 2 && A.flags[c][t]) {
+    double px, py, vx, vy;
+    if (c == 0) {
+      px = A.xf[i];
+      py = 0.5 * (A.yf[j] + A.yf[j + 1]);
+    } else {
+      px = 0.5 * (A.xf[i] + A.xf[i + 1]);
+      py = A.yf[j];
+    }
+    rigid_velocity(A.body, A.omega, A.cx, A.cy, px, py, vx, vy);
+    return T(c == 0 ? vx : vy);
+  }
+  return A.u[c][t];
+}
+
+// Right-hand side of Eq. (9) at cell (i, j, k): sum_d (u_d[m+1] - u_d[m]) / h_d[m].
+template <typename T>
+__device__ __forceinline__ T div_at(const DivArgs<T>& A, int i, int j, int k) {
+  const Geom<T>& g = A.g;
+  T s;
+  {
+    const int ex = g.ext(0, 0);
+    const int base = ex * (j + g.ny * k);
+    const int ip = (i + 1 < ex) ? i + 1 : 0;
+    s = (blended(A, 0, base + ip, ip, j) - blended(A, 0, base + i, i, j)) * g.ihx;
+  }
+  {
+    const int ey = g.ext(1, 1);
+    const int jp = (j + 1 < ey) ? j + 1 : 0;
+    const int b0 = i + g.nx * ey * k;
+    s += (blended(A, 1, b0 + g.nx * jp, i, jp) - blended(A, 1, b0 + g.nx * j, i, j)) * g.ihy[j];
+  }
+  if (g.dim == 3) {
+    const int ez = g.ext(2, 2);
+    const int kp = (k + 1 < ez) ? k + 1 : 0;
+    const int b0 = i + g.nx * j;
+    const int pl = g.nx * g.ny;
+    s += (__ldg(A.u[2] + b0 + pl * kp) - __ldg(A.u[2] + b0 + pl * k)) * g.ihz;
+  }
+  return s;
+}
+
 // Workspace and plans owned by a grid (host side).
 struct Plan1D {
   int n = 0;
@@ -144,11 +210,12 @@ struct fs_grid {
   int nmx = 0, nlz = 1;        // eigenvalue table extents
   int cyclic = 0;
   double* ya = nullptr;        // a_j couplings (ny)
-  double *tE = nullptr, *tCP = nullptr, *tZV = nullptr;   // [ny][nmx*nlz]
-  double *tFAC = nullptr, *tVL = nullptr;                 // [nmx*nlz]
+  double *tE = nullptr, *tCP = nullptr, *tZV = nullptr;   // [ny][nlz][nmx]
+  double *tFAC = nullptr, *tVL = nullptr;                 // [nlz][nmx]
 
   fs::IBDev ib;
   bool has_body = false;
+  void* adj = nullptr;         // adjoint work buffers (adjoint.cu), allocated on first use
 
   // optional per-kernel timing (fs_profile_begin / fs_profile_end)
   bool prof_on = false;
@@ -166,15 +233,22 @@ template <typename T> void launch_predictor(fs_grid* g, T* const* uin, T* const*
                                             double dt, double a, double b, const double* body_state);
 template <typename T> void launch_outflow_flux(fs_grid* g, T* const* uin);
 template <typename T> void launch_divergence(fs_grid* g, T* const* u, T* out, const double* body_state);
+template <typename T> fs::DivArgs<T> make_div_args(fs_grid* g, T* const* u, const double* body_state);
 template <typename T> void launch_correct(fs_grid* g, T* const* ustar, const T* phi, T* const* unew);
 template <typename T> void launch_to_pressure(fs_grid* g, const T* phi, double* p, double scale);
 template <typename T> void launch_diagnostics(fs_grid* g, T* const* u, double* out3);
 // poisson.cu
 template <typename T> void poisson_solve_inplace(fs_grid* g, T* data);
+// Solve with the right-hand side D[(1 - eps) u* + eps u_c] formed inside the x transform (out: phi).
+template <typename T> void poisson_solve_from_velocity(fs_grid* g, const fs::DivArgs<T>& div, T* data);
 // ib.cu
 template <typename T> void ib_prepare(fs_grid* g, const double* body_state);
 template <typename T> void ib_forces(fs_grid* g, const double* body_state);
 void body_rk4(fs_grid* g, double* body_state, double dt);
+// adjoint.cu
+template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state* lam, const double* dJdF,
+                                       fs_param_grad* pg, double dt);
+void free_adj_buffers(void* p);
 // errors
 int set_error(int code, const std::string& msg);
 int cuda_check(cudaError_t e, const char* what);

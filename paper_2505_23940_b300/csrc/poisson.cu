@@ -48,15 +48,15 @@ namespace {
 // One Stockham stage with compile-time radix R over `nlines` lines of length N.
 template <typename T, int R>
 __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int N,
-                                               int nlines, int Ns, const cplx<T>* __restrict__ tw, bool inv) {
+                                               int P, int nlines, int Ns, const cplx<T>* __restrict__ tw, bool inv) {
   const int NR = N / R;
   const int nb = nlines * NR;
   const int tws = N / (Ns * R);
   for (int t = threadIdx.x; t < nb; t += blockDim.x) {
     const int line = t / NR;
     const int jj = t - line * NR;
-    const cplx<T>* a = in + line * N;
-    cplx<T>* b = out + line * N;
+    const cplx<T>* a = in + line * P;
+    cplx<T>* b = out + line * P;
     const int k = jj % Ns;
     cplx<T> v[R];
 #pragma unroll
@@ -109,21 +109,21 @@ __device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, c
 // lengths with prime factors <= 5 use the one without, whose register count
 // is not set by those large butterflies.
 template <typename T, bool BIG>
-__device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, int N, int nlines, const Radices& rad,
+__device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, int N, int P, int nlines, const Radices& rad,
                              const cplx<T>* __restrict__ tw, bool inv) {
   int Ns = 1;
   for (int s = 0; s < rad.nst; ++s) {
     const int R = rad.r[s];
     switch (R) {
-      case 2: stockham_stage<T, 2>(a, b, N, nlines, Ns, tw, inv); break;
-      case 3: stockham_stage<T, 3>(a, b, N, nlines, Ns, tw, inv); break;
-      case 4: stockham_stage<T, 4>(a, b, N, nlines, Ns, tw, inv); break;
-      case 5: stockham_stage<T, 5>(a, b, N, nlines, Ns, tw, inv); break;
+      case 2: stockham_stage<T, 2>(a, b, N, P, nlines, Ns, tw, inv); break;
+      case 3: stockham_stage<T, 3>(a, b, N, P, nlines, Ns, tw, inv); break;
+      case 4: stockham_stage<T, 4>(a, b, N, P, nlines, Ns, tw, inv); break;
+      case 5: stockham_stage<T, 5>(a, b, N, P, nlines, Ns, tw, inv); break;
       default:
         if constexpr (BIG) {
-          if (R == 7) stockham_stage<T, 7>(a, b, N, nlines, Ns, tw, inv);
-          else if (R == 11) stockham_stage<T, 11>(a, b, N, nlines, Ns, tw, inv);
-          else stockham_stage<T, 13>(a, b, N, nlines, Ns, tw, inv);
+          if (R == 7) stockham_stage<T, 7>(a, b, N, P, nlines, Ns, tw, inv);
+          else if (R == 11) stockham_stage<T, 11>(a, b, N, P, nlines, Ns, tw, inv);
+          else stockham_stage<T, 13>(a, b, N, P, nlines, Ns, tw, inv);
         }
         break;
     }
@@ -139,9 +139,12 @@ __device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, int N, int nlines, const Ra
 // ---------------------------------------------------------------------------
 // x transforms: rows of length N = nx, two rows per complex line.
 // mode 0: periodic DFT (real-packed output), mode 1: DCT-II.
-template <typename T, bool BIG>
+// DIV: the rows are not read from `data` but formed on the fly as the
+// divergence D[(1 - eps) u* + eps u_c] of Eq. (9) (row r = j + ny k).
+template <typename T, bool BIG, bool DIV>
 __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, int rows, int lpb, int mode, Radices rad,
-                            const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw) {
+                            const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw,
+                            const DivArgs<T> dv) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* B = A + (size_t)lpb * N;
@@ -150,14 +153,21 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, 
   for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
     const int l = t / N, i = t - l * N;
     const int r0 = 2 * (line0 + l), r1 = r0 + 1;
-    const T va = data[(size_t)r0 * N + i];
-    const T vb = r1 < rows ? data[(size_t)r1 * N + i] : T(0);
+    T va, vb;
+    if constexpr (DIV) {
+      const int ny = dv.g.ny;
+      va = div_at(dv, i, r0 % ny, r0 / ny);
+      vb = r1 < rows ? div_at(dv, i, r1 % ny, r1 / ny) : T(0);
+    } else {
+      va = data[(size_t)r0 * N + i];
+      vb = r1 < rows ? data[(size_t)r1 * N + i] : T(0);
+    }
     int dst = i;
     if (mode == 1) dst = (i & 1) ? N - 1 - (i >> 1) : (i >> 1);   // even samples forward, odd reversed
     A[l * N + dst] = {va, vb};
   }
   __syncthreads();
-  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, nl, rad, tw, false);
+  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, false);
   for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
     const int l = t / N, s = t - l * N;
     const int r0 = 2 * (line0 + l), r1 = r0 + 1;
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, 
     A[l * N + k] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
   }
   __syncthreads();
-  cplx<T>* z = fft_smem<T, BIG>(A, B, N, nl, rad, tw, true);
+  cplx<T>* z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, true);
   const T inv_n = T(1) / T(N);
   for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
     const int l = t / N, i = t - l * N;
@@ -245,7 +255,8 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
                             const cplx<T>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* B = A + (size_t)ppb * N;
+  const int P = N + 1;   // padded line pitch: lines start in different banks
+  cplx<T>* B = A + (size_t)ppb * P;
   const int j = blockIdx.y;
   const int pair0 = blockIdx.x * ppb;
   const int np = min(ppb, nx / 2 - pair0);
@@ -254,24 +265,24 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int k = t / (2 * np), sl = t - k * (2 * np);
     const T v = base[plane * k + sl];
-    T* dst = reinterpret_cast<T*>(&A[(sl >> 1) * N + k]);
+    T* dst = reinterpret_cast<T*>(&A[(sl >> 1) * P + k]);
     dst[sl & 1] = v;
   }
   __syncthreads();
-  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, np, rad, tw, false);
+  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, P, np, rad, tw, false);
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int p = t / (2 * np), sl = t - p * (2 * np);
     const int line = sl >> 1;
     const int m = pair0 + line;
     T out;
     if (m > 0) {
-      const cplx<T> z = Z[line * N + p];
+      const cplx<T> z = Z[line * P + p];
       out = (sl & 1) ? z.y : z.x;
     } else {
       // pair 0 holds two real sequences: split into two real-packed z spectra
       const int l = p == 0 ? 0 : (p == 1 ? N / 2 : p >> 1);
       const bool im = p >= 2 && (p & 1);
-      const cplx<T> z = Z[line * N + l], zr = Z[line * N + (l == 0 ? 0 : N - l)];
+      const cplx<T> z = Z[line * P + l], zr = Z[line * P + (l == 0 ? 0 : N - l)];
       if ((sl & 1) == 0) out = im ? T(0.5) * (z.y - zr.y) : T(0.5) * (z.x + zr.x);
       else out = im ? T(0.5) * (zr.x - z.x) : T(0.5) * (z.y + zr.y);
     }
@@ -284,7 +295,8 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
                             const cplx<T>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* B = A + (size_t)ppb * N;
+  const int P = N + 1;   // padded line pitch: lines start in different banks
+  cplx<T>* B = A + (size_t)ppb * P;
   const int j = blockIdx.y;
   const int pair0 = blockIdx.x * ppb;
   const int np = min(ppb, nx / 2 - pair0);
@@ -293,7 +305,7 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int k = t / (2 * np), sl = t - k * (2 * np);
     const T v = base[plane * k + sl];
-    T* dst = reinterpret_cast<T*>(&B[(sl >> 1) * N + k]);
+    T* dst = reinterpret_cast<T*>(&B[(sl >> 1) * P + k]);
     dst[sl & 1] = v;
   }
   __syncthreads();
@@ -301,24 +313,24 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
     const int line = t / N, l = t - line * N;
     const int m = pair0 + line;
     if (m > 0) {
-      A[line * N + l] = B[line * N + l];
+      A[line * P + l] = B[line * P + l];
     } else {
       // rebuild Z = Y0 + i Y1 from the two real-packed spectra held in .x (slot 0) and .y (slot 1)
       cplx<T> y0, y1;
-      const cplx<T>* P = B + line * N;
-      if (l == 0) { y0 = {P[0].x, T(0)}; y1 = {P[0].y, T(0)}; }
-      else if (2 * l == N) { y0 = {P[1].x, T(0)}; y1 = {P[1].y, T(0)}; }
-      else if (2 * l < N) { y0 = {P[2 * l].x, P[2 * l + 1].x}; y1 = {P[2 * l].y, P[2 * l + 1].y}; }
-      else { const int q = N - l; y0 = {P[2 * q].x, -P[2 * q + 1].x}; y1 = {P[2 * q].y, -P[2 * q + 1].y}; }
-      A[line * N + l] = {y0.x - y1.y, y0.y + y1.x};
+      const cplx<T>* Q = B + line * P;
+      if (l == 0) { y0 = {Q[0].x, T(0)}; y1 = {Q[0].y, T(0)}; }
+      else if (2 * l == N) { y0 = {Q[1].x, T(0)}; y1 = {Q[1].y, T(0)}; }
+      else if (2 * l < N) { y0 = {Q[2 * l].x, Q[2 * l + 1].x}; y1 = {Q[2 * l].y, Q[2 * l + 1].y}; }
+      else { const int q = N - l; y0 = {Q[2 * q].x, -Q[2 * q + 1].x}; y1 = {Q[2 * q].y, -Q[2 * q + 1].y}; }
+      A[line * P + l] = {y0.x - y1.y, y0.y + y1.x};
     }
   }
   __syncthreads();
-  cplx<T>* z = fft_smem<T, BIG>(A, B, N, np, rad, tw, true);
+  cplx<T>* z = fft_smem<T, BIG>(A, B, N, P, np, rad, tw, true);
   const T inv_n = T(1) / T(N);
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int k = t / (2 * np), sl = t - k * (2 * np);
-    const cplx<T> v = z[(sl >> 1) * N + k];
+    const cplx<T> v = z[(sl >> 1) * P + k];
     base[plane * k + sl] = ((sl & 1) ? v.y : v.x) * inv_n;
   }
 }
@@ -327,7 +339,7 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
 // y solve: one thread per (slot s, z position t) column; FP64 Thomas with
 // factors e_j = 1 / beta_j and c'_j tabulated per eigenvalue index.
 struct YArgs {
-  int nx, ny, nz, dim, xmode, nlz, cyclic;
+  int nx, ny, nz, dim, xmode, nmx, nlz, cyclic;
   const double* a;       // a_j
   const double* E;       // [ny][nlam]
   const double* CP;
@@ -344,52 +356,112 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
   if (A.dim == 2) return mx;
   int l = (s >= 2 || A.xmode == 1) ? t : (t == 0 ? 0 : (t == 1 ? A.nz / 2 : (t >> 1)));
   const int lz = min(l, A.nz - l);
-  return mx * A.nlz + lz;
+  return lz * A.nmx + mx;   // tables are [j][lz][mx]: consecutive slots read consecutive entries
 }
 
+// One thread per column (slot s at one z position): FP64 Thomas with the
+// factors e_j = 1 / beta_j and c'_j of the column's eigenvalue.  The block
+// stages its data tile in shared memory with coalesced loads; the factor
+// tables are read 16 rows ahead of the recurrence.
 template <typename T>
 __global__ void ysolve_kernel(T* __restrict__ data, const YArgs A) {
-  extern __shared__ double dp[];   // [ny][blockDim.x]
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  const int t = blockIdx.y;
-  const bool active = s < A.nx;
+  extern __shared__ double dsm[];  // [ny][blockDim.x]: the column tile, then dp, then x
+  constexpr int U = 16;            // table rows whose loads are issued together
   const int bw = blockDim.x;
-  const int nlam = (A.xmode == 1 ? A.nx : A.nx / 2 + 1) * A.nlz;
-  if (!active) return;
-  const int li = lam_index(A, s, t);
-  T* col = data + s + (size_t)A.nx * A.ny * t;
-  double prev = 0.0;
-  for (int j = 0; j < A.ny; ++j) {
-    const double d = (double)col[(size_t)A.nx * j];
-    const double e = A.E[(size_t)j * nlam + li];
-    prev = (j == 0) ? d * e : (d - A.a[j] * prev) * e;
-    dp[j * bw + threadIdx.x] = prev;
+  const int s0 = blockIdx.x * bw;
+  const int t = blockIdx.y;
+  const int s = s0 + threadIdx.x;
+  const int ny = A.ny;
+  const int ncol = min(bw, A.nx - s0);
+  const int nlam = A.nmx * A.nlz;
+  T* tile = data + s0 + (size_t)A.nx * A.ny * t;
+  const size_t rs = (size_t)A.nx;
+  for (int e = threadIdx.x; e < ny * bw; e += bw) {
+    const int j = e / bw, q = e - j * bw;
+    dsm[e] = q < ncol ? (double)tile[rs * j + q] : 0.0;
   }
-  double x = prev;
-  for (int j = A.ny - 2; j >= 0; --j) {
-    x = dp[j * bw + threadIdx.x] - A.CP[(size_t)j * nlam + li] * x;
-    dp[j * bw + threadIdx.x] = x;
-  }
-  const bool singular = li == 0;
-  if (A.cyclic && !singular) {
-    const double f = (dp[threadIdx.x] + A.VL[li] * dp[(A.ny - 1) * bw + threadIdx.x]) * A.FAC[li];
-    for (int j = 0; j < A.ny; ++j) dp[j * bw + threadIdx.x] -= f * A.ZV[(size_t)j * nlam + li];
-  }
-  double mean = 0.0;
-  if (singular) {
-    double sw = 0.0, sx = 0.0;
-    for (int j = 0; j < A.ny; ++j) {
-      sx += dp[j * bw + threadIdx.x] * A.hy[j];
-      sw += A.hy[j];
+  __syncthreads();
+  if (s < A.nx) {
+    const int li = lam_index(A, s, t);
+    const double* E = A.E + li;
+    const double* CP = A.CP + li;
+    double* my = dsm + threadIdx.x;
+    // forward elimination: dp_j = (d_j - a_j dp_{j-1}) e_j
+    double prev = 0.0;
+    int j = 0;
+    for (; j + U <= ny; j += U) {
+      double e[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) e[q] = __ldg(E + (size_t)(j + q) * nlam);
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const double d = my[(j + q) * bw];
+        prev = (j + q == 0) ? d * e[q] : (d - __ldg(A.a + j + q) * prev) * e[q];
+        my[(j + q) * bw] = prev;
+      }
     }
-    mean = sx / sw;
+    for (; j < ny; ++j) {
+      const double d = my[j * bw];
+      prev = (j == 0) ? d * __ldg(E) : (d - __ldg(A.a + j) * prev) * __ldg(E + (size_t)j * nlam);
+      my[j * bw] = prev;
+    }
+    // back substitution: x_j = dp_j - c'_j x_{j+1}
+    double x = prev;
+    j = ny - 2;
+    for (; j - U + 1 >= 0; j -= U) {
+      double c[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) c[q] = __ldg(CP + (size_t)(j - q) * nlam);
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        x = my[(j - q) * bw] - c[q] * x;
+        my[(j - q) * bw] = x;
+      }
+    }
+    for (; j >= 0; --j) {
+      x = my[j * bw] - __ldg(CP + (size_t)j * nlam) * x;
+      my[j * bw] = x;
+    }
+    if (li == 0) {
+      // singular zero mode: shift to zero hy-weighted mean
+      double sw = 0.0, sx = 0.0;
+      for (int q = 0; q < ny; ++q) {
+        sx += my[q * bw] * A.hy[q];
+        sw += A.hy[q];
+      }
+      const double mean = sx / sw;
+      for (int q = 0; q < ny; ++q) my[q * bw] -= mean;
+    } else if (A.cyclic) {
+      // Sherman-Morrison correction of the periodic coupling
+      const double f = (my[0] + A.VL[li] * my[(ny - 1) * bw]) * A.FAC[li];
+      const double* ZV = A.ZV + li;
+      j = 0;
+      for (; j + U <= ny; j += U) {
+        double z[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) z[q] = __ldg(ZV + (size_t)(j + q) * nlam);
+#pragma unroll
+        for (int q = 0; q < U; ++q) my[(j + q) * bw] -= f * z[q];
+      }
+      for (; j < ny; ++j) my[j * bw] -= f * __ldg(ZV + (size_t)j * nlam);
+    }
   }
-  for (int j = 0; j < A.ny; ++j) col[(size_t)A.nx * j] = (T)(dp[j * bw + threadIdx.x] - mean);
+  __syncthreads();
+  for (int e = threadIdx.x; e < ny * bw; e += bw) {
+    const int j = e / bw, q = e - j * bw;
+    if (q < ncol) tile[rs * j + q] = (T)dsm[e];
+  }
 }
 
 template <typename T>
 size_t fft_smem_bytes(int N, int lines) {
   return 2ull * lines * N * sizeof(cplx<T>);
+}
+
+// z transforms use a padded line pitch N + 1
+template <typename T>
+size_t fft_smem_bytes_z(int N, int lines) {
+  return 2ull * lines * (N + 1) * sizeof(cplx<T>);
 }
 
 Radices radices_of(const Plan1D& p) {
@@ -403,7 +475,8 @@ constexpr size_t kSmemBudget = 96 * 1024;
 
 template <typename T, bool BIG>
 void set_smem_attrs_big() {
-  cudaFuncSetAttribute(xfwd_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(xfwd_kernel<T, BIG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(xfwd_kernel<T, BIG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(xinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(zfwd_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(zinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
@@ -427,14 +500,15 @@ bool has_big(const Plan1D& p) {
 
 }  // namespace
 
+// Threads per y-solve block: each thread stages one column of ny doubles.
 int ysolve_threads(int ny) {
-  // dp staging: ny doubles per thread column
-  if ((size_t)ny * 64 * 8 <= 160 * 1024) return 64;
-  return 32;
+  int nt = 64;
+  while (nt > 8 && (size_t)ny * nt * 8 > 160 * 1024) nt /= 2;
+  return nt;
 }
 
 template <typename T>
-void poisson_solve_inplace(fs_grid* G, T* data) {
+void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   set_smem_attrs<T>();
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int rows = ny * nz;
@@ -444,18 +518,23 @@ void poisson_solve_inplace(fs_grid* G, T* data) {
     lpb = lpb > 16 ? 16 : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
     const int nb = (lines + lpb - 1) / lpb;
-    auto k = has_big(G->px) ? xfwd_kernel<T, true> : xfwd_kernel<T, false>;
-    FS_LAUNCH(G, "fft_x_fwd", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
-                                                          (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
+    const bool big = has_big(G->px);
+    auto k = dv ? (big ? xfwd_kernel<T, true, true> : xfwd_kernel<T, false, true>)
+                : (big ? xfwd_kernel<T, true, false> : xfwd_kernel<T, false, false>);
+    const DivArgs<T> none{};
+    FS_LAUNCH(G, dv ? "fft_x_fwd_div" : "fft_x_fwd",
+              k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
+                                                                    (const cplx<T>*)G->px.tw,
+                                                                    (const cplx<T>*)G->px.dtw, dv ? *dv : none));
   }
   int ppb = 0;
   if (G->dim == 3) {
-    ppb = (int)(kSmemBudget / fft_smem_bytes<T>(nz, 1));
+    ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
     ppb = ppb > 16 ? 16 : (ppb < 1 ? 1 : ppb);
     if (ppb > nx / 2) ppb = nx / 2;
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
     auto k = has_big(G->pz) ? zfwd_kernel<T, true> : zfwd_kernel<T, false>;
-    FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+    FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
   {
@@ -465,6 +544,7 @@ void poisson_solve_inplace(fs_grid* G, T* data) {
     A.nz = nz;
     A.dim = G->dim;
     A.xmode = G->xmode;
+    A.nmx = G->nmx;
     A.nlz = G->nlz;
     A.cyclic = G->cyclic;
     A.a = G->ya;
@@ -481,7 +561,7 @@ void poisson_solve_inplace(fs_grid* G, T* data) {
   if (G->dim == 3) {
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
     auto k = has_big(G->pz) ? zinv_kernel<T, true> : zinv_kernel<T, false>;
-    FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+    FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
   {
@@ -495,7 +575,19 @@ void poisson_solve_inplace(fs_grid* G, T* data) {
   }
 }
 
+template <typename T>
+void poisson_solve_inplace(fs_grid* G, T* data) {
+  poisson_solve<T>(G, data, nullptr);
+}
+
+template <typename T>
+void poisson_solve_from_velocity(fs_grid* G, const DivArgs<T>& div, T* data) {
+  poisson_solve<T>(G, data, &div);
+}
+
 template void poisson_solve_inplace<float>(fs_grid*, float*);
 template void poisson_solve_inplace<double>(fs_grid*, double*);
+template void poisson_solve_from_velocity<float>(fs_grid*, const DivArgs<float>&, float*);
+template void poisson_solve_from_velocity<double>(fs_grid*, const DivArgs<double>&, double*);
 
 }  // namespace fs

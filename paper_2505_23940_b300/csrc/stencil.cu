@@ -30,14 +30,15 @@ template <typename T>
 struct PredArgs {
   Geom<T> g;
   const T* uin[3];
-  const T* un;
-  T* out;
+  const T* un[3];
+  T* out[3];
   T dt, a, b;
   int conv;
-  const uint8_t* flags;
-  T* num;
-  T* den;
-  T* fout;
+  int X, Y;                  // thread grid (largest component extents along x and y)
+  const uint8_t* flags[2];   // IB (2-D): per-face flags, accumulators and forcing output
+  T* num[2];
+  T* den[2];
+  T* fout[2];
   const double* body;
   double omega, cx, cy;
   const double* xf;
@@ -45,20 +46,63 @@ struct PredArgs {
   const double* oscale;
 };
 
+// Velocity access around the face (i, j, k) with every boundary rule (ldv).
+template <typename T>
+struct AccGhost {
+  const Geom<T>* g;
+  const T* const* u;
+  int i, j, k;
+  __device__ __forceinline__ T operator()(int c, int di, int dj, int dk) const {
+    return ldv(*g, u[c], c, i + di, j + dj, k + dk);
+  }
+};
+
+// Velocity access for a face whose whole stencil lies inside: the wrapped
+// neighbour indices are formed once per thread, every load is two 32-bit
+// multiply-adds away (field sizes are checked below 2^31 at grid creation).
+template <typename T>
+struct AccFast {
+  const T* const* u;
+  int xo[3], yo[3], zo[3];   // neighbour index for offsets -1, 0, +1 (periodic wrap applied)
+  int ex[3], exy[3];         // per component: x extent and plane size
+  __device__ __forceinline__ AccFast(const Geom<T>& g, const T* const* uu, int i, int j, int k) : u(uu) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    const int p[3] = {i, j, k};
+    int* o[3] = {xo, yo, zo};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      o[d][0] = p[d] - 1;
+      o[d][1] = p[d];
+      o[d][2] = p[d] + 1;
+      if (g.per[d]) {
+        if (p[d] == 0) o[d][0] = n[d] - 1;
+        if (p[d] == n[d] - 1) o[d][2] = 0;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ex[c] = g.ext(c, 0);
+      exy[c] = ex[c] * g.ext(c, 1);
+    }
+  }
+  __device__ __forceinline__ T operator()(int c, int di, int dj, int dk) const {
+    return __ldg(u[c] + (xo[di + 1] + ex[c] * yo[dj + 1] + exy[c] * zo[dk + 1]));
+  }
+};
+
 // R(u) of Eq. (4) on the C-face (i, j, k): -div(u u) + nu lap(u) + body force.
 // Same flux construction as the oracle (fluid.momentum_rhs), evaluated for one face.
-template <typename T, int C>
-__device__ __forceinline__ T momentum_rhs(const Geom<T>& g, const T* const* u, int conv, int i, int j, int k) {
+template <typename T, int C, typename Acc>
+__device__ __forceinline__ T momentum_rhs(const Geom<T>& g, const Acc& U, int conv, int i, int j, int k) {
   const int idx[3] = {i, j, k};
   T cv = T(0), df = T(0);
+  // unit offsets along C
+  constexpr int cx = C == 0, cy = C == 1, cz = C == 2;
   // d == C: fluxes at the cell centres east (cell f) and west (cell f-1) of the face
   {
-    int lo[3] = {i, j, k}, hi[3] = {i, j, k};
-    lo[C] -= 1;
-    hi[C] += 1;
-    const T uW = ldv(g, u[C], C, lo[0], lo[1], lo[2]);
-    const T u0 = ldv(g, u[C], C, i, j, k);
-    const T uE = ldv(g, u[C], C, hi[0], hi[1], hi[2]);
+    const T uW = U(C, -cx, -cy, -cz);
+    const T u0 = U(C, 0, 0, 0);
+    const T uE = U(C, cx, cy, cz);
     const T TE = T(0.5) * (u0 + uE), TW = T(0.5) * (uW + u0);
     T QE, QW;
     if (conv == FS_UPWIND1) {
@@ -82,18 +126,14 @@ __device__ __forceinline__ T momentum_rhs(const Geom<T>& g, const T* const* u, i
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     if (d == C || d >= g.dim) continue;
+    const int dx = d == 0, dy = d == 1, dz = d == 2;
     const T thc = (C == 1) ? g.thy[j] : T(0.5);
-    int p_cd[3] = {i, j, k}, p_d[3] = {i, j, k}, p_c[3] = {i, j, k}, p_dm[3] = {i, j, k};
-    p_cd[C] -= 1;
-    p_cd[d] += 1;  // c-cell f-1, d-face m+1
-    p_d[d] += 1;   // c-cell f,   d-face m+1
-    p_c[C] -= 1;   // c-cell f-1, d-face m
-    p_dm[d] -= 1;  // C component at d-cell m-1
-    const T TN = (T(1) - thc) * ldv(g, u[d], d, p_cd[0], p_cd[1], p_cd[2]) + thc * ldv(g, u[d], d, p_d[0], p_d[1], p_d[2]);
-    const T TS = (T(1) - thc) * ldv(g, u[d], d, p_c[0], p_c[1], p_c[2]) + thc * ldv(g, u[d], d, i, j, k);
-    const T uS = ldv(g, u[C], C, p_dm[0], p_dm[1], p_dm[2]);
-    const T u0 = ldv(g, u[C], C, i, j, k);
-    const T uN = ldv(g, u[C], C, p_d[0], p_d[1], p_d[2]);
+    // transport u_d at (c-cell f-1 | f, d-face m+1 | m); C component at d-cells m-1, m, m+1
+    const T TN = (T(1) - thc) * U(d, dx - cx, dy - cy, dz - cz) + thc * U(d, dx, dy, dz);
+    const T TS = (T(1) - thc) * U(d, -cx, -cy, -cz) + thc * U(d, 0, 0, 0);
+    const T uS = U(C, -dx, -dy, -dz);
+    const T u0 = U(C, 0, 0, 0);
+    const T uN = U(C, dx, dy, dz);
     const int m = idx[d];
     T thN, thS, ihd, ihfN, ihfS;
     if (d == 1) {
@@ -122,73 +162,87 @@ __device__ __forceinline__ T momentum_rhs(const Geom<T>& g, const T* const* u, i
   return R;
 }
 
-// Rigid velocity V + omega x (r - r_c) at face position (px, py) (Eq. 23, solid points).
-__device__ __forceinline__ void rigid_velocity(const double* body, double omega, double cx, double cy,
-                                               double px, double py, double& vx, double& vy) {
-  const double wx = body[0], wy = body[1];
-  vx = body[2] - omega * (py - (cy + wy));
-  vy = body[3] + omega * (px - (cx + wx));
-}
 
-template <typename T, int C>
-__global__ void __launch_bounds__(kThreads) predictor_kernel(const PredArgs<T> A) {
+// Predictor for the C-face (i, j, k): Eq. (4), the direct-forcing blend of
+// Eq. (5) on forced faces, the RK stage combination, and the imposed normal
+// velocity on boundary faces.
+template <typename T, int C, typename Acc>
+__device__ __forceinline__ void predict_face(const PredArgs<T>& A, const Acc& U, int i, int j, int k) {
   const Geom<T>& g = A.g;
   const int ex = g.ext(C, 0), ey = g.ext(C, 1), ez = g.ext(C, 2);
-  const long long total = (long long)ex * ey * ez;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex);
-    const long long r = t / ex;
-    const int j = (int)(r % ey);
-    const int k = (int)(r / ey);
-    const int idx[3] = {i, j, k};
-    const int ec = (C == 0) ? ex : (C == 1 ? ey : ez);
-    T res;
-    T fval = T(0);
-    if (!g.per[C] && (idx[C] == 0 || idx[C] == ec - 1)) {
-      // boundary face of a non-periodic direction: imposed normal velocity
-      const int side = idx[C] == 0 ? 0 : 1;
-      const int kind = g.bc[C][side];
-      if (kind == FS_BC_OUTFLOW) {
-        // u*[n] = s u[n-1], s from the flux balance (outflow_scale_kernel)
-        res = T(*A.oscale) * A.uin[C][t - 1];
-      } else if (kind == FS_BC_INFLOW) {
-        res = g.bcv[C][side][C];
-      } else {
-        res = T(0);
-      }
+  if (i >= ex || j >= ey || k >= ez) return;
+  const int t = i + ex * (j + ey * k);
+  const int idx[3] = {i, j, k};
+  const int ec = (C == 0) ? ex : (C == 1 ? ey : ez);
+  T res;
+  T fval = T(0);
+  if (!g.per[C] && (idx[C] == 0 || idx[C] == ec - 1)) {
+    const int side = idx[C] == 0 ? 0 : 1;
+    const int kind = g.bc[C][side];
+    if (kind == FS_BC_OUTFLOW) {
+      // u*[n] = s u[n-1], s from the flux balance (outflow_scale_kernel)
+      res = T(*A.oscale) * A.uin[C][t - 1];
+    } else if (kind == FS_BC_INFLOW) {
+      res = g.bcv[C][side][C];
     } else {
-      const T R = momentum_rhs<T, C>(g, A.uin, A.conv, i, j, k);
-      const T u0 = A.uin[C][t];
-      T v = u0 + A.dt * R;
-      if (A.flags) {
-        const uint8_t fl = A.flags[t];
-        if (fl) {
-          double px, py;
-          if (C == 0) {
-            px = A.xf[i];
-            py = 0.5 * (A.yf[j] + A.yf[j + 1]);
-          } else {
-            px = 0.5 * (A.xf[i] + A.xf[i + 1]);
-            py = A.yf[j];
-          }
-          double vx, vy;
-          rigid_velocity(A.body, A.omega, A.cx, A.cy, px, py, vx, vy);
-          T ut = T(C == 0 ? vx : vy);
-          if (fl & 2) {
-            const T dn = A.den[t];
-            if (dn > T(0)) ut = A.num[t] / dn;
-            A.num[t] = T(0);
-            A.den[t] = T(0);
-          }
-          fval = -R + (ut - u0) / A.dt;   // Eq. (5) with eps = 1
-          v = ut;                          // u* = u + dt (R + f) = u_s on forced faces
-        }
-      }
-      res = (A.a != T(0)) ? A.a * A.un[t] + A.b * v : A.b * v;
+      res = T(0);
     }
-    A.out[t] = res;
-    if (A.fout) A.fout[t] = fval;
+  } else {
+    const T R = momentum_rhs<T, C>(g, U, A.conv, i, j, k);
+    const T u0 = A.uin[C][t];
+    T v = u0 + A.dt * R;
+    if (C < 2 && A.flags[0]) {
+      const uint8_t fl = A.flags[C][t];
+      if (fl) {
+        double px, py;
+        if (C == 0) {
+          px = A.xf[i];
+          py = 0.5 * (A.yf[j] + A.yf[j + 1]);
+        } else {
+          px = 0.5 * (A.xf[i] + A.xf[i + 1]);
+          py = A.yf[j];
+        }
+        double vx, vy;
+        rigid_velocity(A.body, A.omega, A.cx, A.cy, px, py, vx, vy);
+        T ut = T(C == 0 ? vx : vy);
+        if (fl & 2) {
+          const T dn = A.den[C][t];
+          if (dn > T(0)) ut = A.num[C][t] / dn;
+          A.num[C][t] = T(0);
+          A.den[C][t] = T(0);
+        }
+        fval = -R + (ut - u0) / A.dt;   // Eq. (5) with eps = 1
+        v = ut;                          // u* = u + dt (R + f) = u_s on forced faces
+      }
+    }
+    res = (A.a != T(0)) ? A.a * A.un[C][t] + A.b * v : A.b * v;
+  }
+  A.out[C][t] = res;
+  if (C < 2 && A.fout[0]) A.fout[C][t] = fval;
+}
+
+// One thread per cell position (i, j, k) computes every component's face there.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) predictor_kernel(const PredArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= A.X || j >= A.Y) return;
+  const Geom<T>& g = A.g;
+  bool fast = true;
+  if (!g.per[0]) fast = fast && i >= 2 && i <= g.nx - 2;
+  if (!g.per[1]) fast = fast && j >= 2 && j <= g.ny - 2;
+  if (g.dim == 3 && !g.per[2]) fast = fast && k >= 2 && k <= g.nz - 2;
+  if (fast) {
+    const AccFast<T> U(g, A.uin, i, j, k);
+    predict_face<T, 0>(A, U, i, j, k);
+    predict_face<T, 1>(A, U, i, j, k);
+    if (g.dim == 3) predict_face<T, 2>(A, U, i, j, k);
+  } else {
+    const AccGhost<T> U{&g, A.uin, i, j, k};
+    predict_face<T, 0>(A, U, i, j, k);
+    predict_face<T, 1>(A, U, i, j, k);
+    if (g.dim == 3) predict_face<T, 2>(A, U, i, j, k);
   }
 }
 
@@ -211,94 +265,57 @@ __global__ void outflow_scale_kernel(const T* __restrict__ u0, int ex, int ny, i
 }
 
 template <typename T>
-struct DivArgs {
+__global__ void __launch_bounds__(kThreads) divergence_kernel(const DivArgs<T> A, T* __restrict__ out) {
+  const Geom<T>& g = A.g;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= g.nx || j >= g.ny) return;
+  out[i + g.nx * (j + g.ny * k)] = div_at(A, i, j, k);
+}
+
+template <typename T>
+struct CorrArgs {
   Geom<T> g;
-  const T* u[3];
-  T* out;
-  const uint8_t* flags[2];
-  const double* body;
-  double omega, cx, cy;
-  const double* xf;
-  const double* yf;
+  const T* us[3];
+  const T* phi;
+  T* un[3];
+  int X, Y;
 };
 
-template <typename T>
-__device__ __forceinline__ T blended(const DivArgs<T>& A, int c, size_t t, int i, int j) {
-  if (A.flags[0] && c < 2 && A.flags[c][t]) {
-    double px, py, vx, vy;
-    if (c == 0) {
-      px = A.xf[i];
-      py = 0.5 * (A.yf[j] + A.yf[j + 1]);
-    } else {
-      px = 0.5 * (A.xf[i] + A.xf[i + 1]);
-      py = A.yf[j];
-    }
-    rigid_velocity(A.body, A.omega, A.cx, A.cy, px, py, vx, vy);
-    return T(c == 0 ? vx : vy);   // u_c on forced faces (Eq. 9)
-  }
-  return A.u[c][t];
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) divergence_kernel(const DivArgs<T> A) {
-  const Geom<T>& g = A.g;
-  const long long total = (long long)g.nx * g.ny * g.nz;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % g.nx);
-    const long long r = t / g.nx;
-    const int j = (int)(r % g.ny);
-    const int k = (int)(r / g.ny);
-    T s = T(0);
-    {
-      const int ex = g.ext(0, 0);
-      const size_t base = (size_t)ex * (j + (size_t)g.ny * k);
-      const int ip = (i + 1 < ex) ? i + 1 : 0;
-      s += (blended(A, 0, base + ip, ip, j) - blended(A, 0, base + i, i, j)) * g.ihx;
-    }
-    {
-      const int ey = g.ext(1, 1);
-      const int jp = (j + 1 < ey) ? j + 1 : 0;
-      const size_t b0 = i + (size_t)g.nx * ((size_t)ey * k);
-      s += (blended(A, 1, b0 + (size_t)g.nx * jp, i, jp) - blended(A, 1, b0 + (size_t)g.nx * j, i, j)) * g.ihy[j];
-    }
-    if (g.dim == 3) {
-      const int ez = g.ext(2, 2);
-      const int kp = (k + 1 < ez) ? k + 1 : 0;
-      const size_t b0 = i + (size_t)g.nx * j;
-      const size_t pl = (size_t)g.nx * g.ny;
-      s += (A.u[2][b0 + pl * kp] - A.u[2][b0 + pl * k]) * g.ihz;
-    }
-    A.out[t] = s;
-  }
-}
-
 template <typename T, int C>
-__global__ void __launch_bounds__(kThreads) correct_kernel(const Geom<T> g, const T* __restrict__ us,
-                                                           const T* __restrict__ phi, T* __restrict__ un) {
+__device__ __forceinline__ void correct_face(const CorrArgs<T>& A, int i, int j, int k, const T phi0) {
+  const Geom<T>& g = A.g;
   const int ex = g.ext(C, 0), ey = g.ext(C, 1), ez = g.ext(C, 2);
-  const long long total = (long long)ex * ey * ez;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex);
-    const long long r = t / ex;
-    const int j = (int)(r % ey);
-    const int k = (int)(r / ey);
-    int idx[3] = {i, j, k};
-    const int ec = (C == 0) ? ex : (C == 1 ? ey : ez);
-    T v = us[t];
-    if (g.per[C] || (idx[C] > 0 && idx[C] < ec - 1)) {
-      // G phi at the face: (phi[cell f] - phi[cell f-1]) / hf
-      int lo[3] = {i, j, k};
-      const int nC = (C == 0) ? g.nx : (C == 1 ? g.ny : g.nz);
-      lo[C] = idx[C] > 0 ? idx[C] - 1 : nC - 1;
-      const size_t c0 = idx[0] + (size_t)g.nx * (idx[1] + (size_t)g.ny * idx[2]);
-      const size_t c1 = lo[0] + (size_t)g.nx * (lo[1] + (size_t)g.ny * lo[2]);
-      const T ihf = (C == 0) ? g.ihx : (C == 1 ? g.ihfy[j] : g.ihz);
-      v -= (phi[c0] - phi[c1]) * ihf;
-    }
-    un[t] = v;
+  if (i >= ex || j >= ey || k >= ez) return;
+  const int t = i + ex * (j + ey * k);
+  int idx[3] = {i, j, k};
+  const int nC = (C == 0) ? g.nx : (C == 1 ? g.ny : g.nz);
+  T v = A.us[C][t];
+  if (g.per[C] || (idx[C] > 0 && idx[C] < nC)) {
+    // G phi at the face: (phi[cell f] - phi[cell f-1]) / hf
+    int lo[3] = {i, j, k};
+    lo[C] = idx[C] > 0 ? idx[C] - 1 : nC - 1;
+    const int c1 = lo[0] + g.nx * (lo[1] + g.ny * lo[2]);
+    const T ihf = (C == 0) ? g.ihx : (C == 1 ? g.ihfy[j] : g.ihz);
+    v -= (phi0 - __ldg(A.phi + c1)) * ihf;
   }
+  A.un[C][t] = v;
+}
+
+// Eq. (10): u^{n+1} = u* - G phi on every interior face; one thread per cell position.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) correct_kernel(const CorrArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= A.X || j >= A.Y) return;
+  const Geom<T>& g = A.g;
+  const bool in_cells = i < g.nx && j < g.ny;
+  const T phi0 = in_cells ? __ldg(A.phi + i + g.nx * (j + g.ny * k)) : T(0);
+  correct_face<T, 0>(A, i, j, k, phi0);
+  correct_face<T, 1>(A, i, j, k, phi0);
+  if (g.dim == 3) correct_face<T, 2>(A, i, j, k, phi0);
 }
 
 template <typename T>
@@ -395,11 +412,25 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
                       const double* body_state) {
   PredArgs<T> A;
   A.g = G->geom<T>();
-  for (int c = 0; c < 3; ++c) A.uin[c] = c < G->dim ? uin[c] : nullptr;
+  for (int c = 0; c < 3; ++c) {
+    const bool on = c < G->dim;
+    A.uin[c] = on ? uin[c] : nullptr;
+    A.un[c] = (on && un) ? un[c] : nullptr;
+    A.out[c] = on ? out[c] : nullptr;
+  }
   A.dt = (T)dt;
   A.a = (T)a;
   A.b = (T)b;
   A.conv = G->conv;
+  A.X = G->nx + (G->per[0] ? 0 : 1);
+  A.Y = G->ny + (G->per[1] ? 0 : 1);
+  for (int c = 0; c < 2; ++c) {
+    const bool ibc = G->has_body;
+    A.flags[c] = ibc ? G->ib.flags[c] : nullptr;
+    A.num[c] = ibc ? (T*)G->ib.num[c] : nullptr;
+    A.den[c] = ibc ? (T*)G->ib.den[c] : nullptr;
+    A.fout[c] = ibc ? (T*)G->ib.f[c] : nullptr;
+  }
   A.body = body_state;
   A.omega = G->ib.omega;
   A.cx = G->ib.centre[0];
@@ -407,20 +438,9 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   A.xf = G->xf64[0];
   A.yf = G->xf64[1];
   A.oscale = G->scal;
-  for (int c = 0; c < G->dim; ++c) {
-    A.un = un ? un[c] : nullptr;
-    A.out = out[c];
-    const bool ibc = G->has_body && c < 2;
-    A.flags = ibc ? G->ib.flags[c] : nullptr;
-    A.num = ibc ? (T*)G->ib.num[c] : nullptr;
-    A.den = ibc ? (T*)G->ib.den[c] : nullptr;
-    A.fout = ibc ? (T*)G->ib.f[c] : nullptr;
-    const long long n = (long long)A.g.ext(c, 0) * A.g.ext(c, 1) * A.g.ext(c, 2);
-    const int nb = grid_blocks(n);
-    if (c == 0) FS_LAUNCH(G, "predictor_u", predictor_kernel<T, 0><<<nb, kThreads, 0, G->stream>>>(A));
-    else if (c == 1) FS_LAUNCH(G, "predictor_v", predictor_kernel<T, 1><<<nb, kThreads, 0, G->stream>>>(A));
-    else FS_LAUNCH(G, "predictor_w", predictor_kernel<T, 2><<<nb, kThreads, 0, G->stream>>>(A));
-  }
+  const dim3 blk(32, 8);
+  const dim3 grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  FS_LAUNCH(G, "predictor", predictor_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
 template <typename T>
@@ -438,11 +458,10 @@ void launch_outflow_flux(fs_grid* G, T* const* uin) {
 }
 
 template <typename T>
-void launch_divergence(fs_grid* G, T* const* u, T* out, const double* body_state) {
+DivArgs<T> make_div_args(fs_grid* G, T* const* u, const double* body_state) {
   DivArgs<T> A;
   A.g = G->geom<T>();
   for (int c = 0; c < 3; ++c) A.u[c] = c < G->dim ? u[c] : nullptr;
-  A.out = out;
   A.flags[0] = G->has_body ? G->ib.flags[0] : nullptr;
   A.flags[1] = G->has_body ? G->ib.flags[1] : nullptr;
   A.body = body_state;
@@ -451,19 +470,31 @@ void launch_divergence(fs_grid* G, T* const* u, T* out, const double* body_state
   A.cy = G->ib.centre[1];
   A.xf = G->xf64[0];
   A.yf = G->xf64[1];
-  FS_LAUNCH(G, "divergence", divergence_kernel<T><<<grid_blocks((long long)G->nx * G->ny * G->nz), kThreads, 0, G->stream>>>(A));
+  return A;
+}
+
+template <typename T>
+void launch_divergence(fs_grid* G, T* const* u, T* out, const double* body_state) {
+  const DivArgs<T> A = make_div_args<T>(G, u, body_state);
+  const dim3 blk(32, 8);
+  const dim3 grd((G->nx + 31) / 32, (G->ny + 7) / 8, G->nz);
+  FS_LAUNCH(G, "divergence", divergence_kernel<T><<<grd, blk, 0, G->stream>>>(A, out));
 }
 
 template <typename T>
 void launch_correct(fs_grid* G, T* const* ustar, const T* phi, T* const* unew) {
-  const Geom<T> g = G->geom<T>();
-  for (int c = 0; c < G->dim; ++c) {
-    const long long n = (long long)g.ext(c, 0) * g.ext(c, 1) * g.ext(c, 2);
-    const int nb = grid_blocks(n);
-    if (c == 0) FS_LAUNCH(G, "correct_u", correct_kernel<T, 0><<<nb, kThreads, 0, G->stream>>>(g, ustar[0], phi, unew[0]));
-    else if (c == 1) FS_LAUNCH(G, "correct_v", correct_kernel<T, 1><<<nb, kThreads, 0, G->stream>>>(g, ustar[1], phi, unew[1]));
-    else FS_LAUNCH(G, "correct_w", correct_kernel<T, 2><<<nb, kThreads, 0, G->stream>>>(g, ustar[2], phi, unew[2]));
+  CorrArgs<T> A;
+  A.g = G->geom<T>();
+  for (int c = 0; c < 3; ++c) {
+    A.us[c] = c < G->dim ? ustar[c] : nullptr;
+    A.un[c] = c < G->dim ? unew[c] : nullptr;
   }
+  A.phi = phi;
+  A.X = G->nx + (G->per[0] ? 0 : 1);
+  A.Y = G->ny + (G->per[1] ? 0 : 1);
+  const dim3 blk(32, 8);
+  const dim3 grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  FS_LAUNCH(G, "correct", correct_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
 template <typename T>
@@ -490,6 +521,7 @@ void launch_diagnostics(fs_grid* G, T* const* u, double* out3) {
                                     const double*);                                                              \
   template void launch_outflow_flux<T>(fs_grid*, T* const*);                                                     \
   template void launch_divergence<T>(fs_grid*, T* const*, T*, const double*);                                    \
+  template DivArgs<T> make_div_args<T>(fs_grid*, T* const*, const double*);                                     \
   template void launch_correct<T>(fs_grid*, T* const*, const T*, T* const*);                                     \
   template void launch_to_pressure<T>(fs_grid*, const T*, double*, double);                                      \
   template void launch_diagnostics<T>(fs_grid*, T* const*, double*);
