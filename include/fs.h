@@ -170,6 +170,18 @@ int fs_step_adjoint(fs_grid* grid, const fs_state* st_n, fs_state* lam,
  * sum) when the operator is singular. */
 int fs_solve_pressure(fs_grid* grid, const double* rhs, double* p);
 
+/* Replace the x-momentum source profile (n[1] values, device doubles) used by
+ * later steps, e.g. to make it a differentiable parameter.  The grid must
+ * have been created with a body_force profile.  Enqueued on the grid's stream. */
+int fs_set_body_force(fs_grid* grid, const double* fx);
+
+/* Replace the spring stiffness k of the attached body (Eq. 12). */
+int fs_set_stiffness(fs_grid* grid, double k);
+
+/* Copy the force of the last step, {F_x, F_y, torque}, to device memory
+ * (3 doubles) on the grid's stream, without synchronising. */
+int fs_forces_device(fs_grid* grid, double* F);
+
 /* Hydrodynamic force of the last step (Eq. 20 with F = rho sum_i q_i dV_i).
  * Host outputs: F[dim], torque[1], q[nm * 2] marker forces (q may be NULL).
  * Synchronises the grid's stream.  FS_ERR_STATE before the first FSI step. */

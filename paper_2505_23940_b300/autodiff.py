@@ -1,0 +1,199 @@
+"""Differentiable rollouts: binomial ("revolve") checkpointing of time steps around
+fs_step / fs_step_adjoint, and a torch.autograd.Function over a whole rollout.
+
+The paper differentiates long rollouts with reverse-mode AD plus gradient
+checkpointing (§2.4.1) and nested scans (§2.4.2).  Here the forward steps and
+their hand-written adjoints are CUDA kernels; this module only decides which
+states to keep, which segments to recompute, and in which order to call the
+adjoint step.  State snapshots live in HBM as device tensors.
+
+Schedule.  With s snapshot slots and t recomputation sweeps, at most
+beta(s, t) = C(s + t, s) steps can be reversed (Griewank, "Achieving
+logarithmic growth of temporal and spatial complexity in reverse automatic
+differentiation", 1992).  To reverse steps [a, b) from a stored state at a with
+s free slots, the schedule advances to a + d with d = beta(s, t - 1) for the
+smallest t with beta(s, t) >= b - a, stores that state, reverses [a + d, b)
+with s - 1 slots, releases the slot and reverses [a, a + d) with s slots.
+"""
+from math import comb
+
+import torch
+
+from . import fsstep as F
+
+
+def _beta(s, t):
+    return comb(s + t, s)
+
+
+def revolve_schedule(n, slots):
+    """Actions reversing n steps with `slots` snapshot slots (state 0 is always kept).
+
+    Returns a list of tuples:
+      ("advance", a, b)   run forward steps a .. b-1 from the working state at a
+      ("store", slot, a)  copy the working state (at step a) into slot
+      ("load", slot, a)   copy slot (holding the state at step a) into the working state
+      ("adjoint", a)      working state is the state at step a: run the adjoint of step a
+    Slot 0 holds the initial state.
+    """
+    ops = []
+
+    def rev(a, b, free, base_slot):
+        # the state at a is held in base_slot
+        n_ = b - a
+        if n_ <= 0:
+            return
+        if n_ == 1:
+            ops.append(("load", base_slot, a))
+            ops.append(("adjoint", a))
+            return
+        if not free:
+            for t in range(b - 1, a - 1, -1):
+                ops.append(("load", base_slot, a))
+                if t > a:
+                    ops.append(("advance", a, t))
+                ops.append(("adjoint", t))
+            return
+        s = len(free)
+        t = 1
+        while _beta(s, t) < n_:
+            t += 1
+        d = max(1, min(n_ - 1, _beta(s, t - 1)))
+        m = a + d
+        ops.append(("load", base_slot, a))
+        ops.append(("advance", a, m))
+        slot = free[0]
+        ops.append(("store", slot, m))
+        rev(m, b, free[1:], slot)
+        rev(a, m, free, base_slot)
+
+    rev(0, n, list(range(1, slots)), 0)
+    return ops
+
+
+def simulate(n, slots):
+    """Replay a schedule on integers: returns (adjoint step order, forward steps recomputed)."""
+    work, mem, order, fwd = None, {}, [], 0
+    mem[0] = 0
+    for op in revolve_schedule(n, slots):
+        if op[0] == "load":
+            assert mem.get(op[1]) == op[2], op
+            work = op[2]
+        elif op[0] == "advance":
+            assert work == op[1], op
+            fwd += op[2] - op[1]
+            work = op[2]
+        elif op[0] == "store":
+            assert work == op[2]
+            mem[op[1]] = work
+        elif op[0] == "adjoint":
+            assert work == op[1]
+            order.append(op[1])
+    return order, fwd
+
+
+class Rollout:
+    """n steps of a grid from (u0, body0), differentiable through revolve + fs_step_adjoint.
+
+    Keeps `slots` device copies of the state.  Forces of every step (FSI grids)
+    are recorded on the device so losses may depend on them.
+    """
+
+    def __init__(self, grid, dt, nsteps, slots=4):
+        self.g = grid
+        self.dt = float(dt)
+        self.n = int(nsteps)
+        self.slots = max(1, int(slots))
+
+    def _clone(self, u, body):
+        return [x.clone() for x in u], (body.clone() if body is not None else None)
+
+    def forward(self, u0, body0=None):
+        u, body = self._clone(u0, body0)
+        forces = None
+        if self.g.has_body:
+            forces = torch.zeros((self.n, 3), dtype=torch.float64, device=u[0].device)
+        for t in range(self.n):
+            self.g.step(u, self.dt, 1, body=body)
+            if forces is not None:
+                self.g.forces_device(forces[t])
+        return u, body, forces
+
+    def backward(self, u0, body0, lam_u, lam_body=None, lam_forces=None, g_body_force=None, g_stiffness=None):
+        """lam_* are the adjoints of the outputs; returns (lam_u0, lam_body0).  Parameter gradients
+        are accumulated into the given device tensors."""
+        mem = {0: self._clone(u0, body0)}
+        work_u, work_b = None, None
+        lam = [x.clone() for x in lam_u]
+        lb = lam_body.clone() if lam_body is not None else (
+            torch.zeros(4, dtype=torch.float64, device=lam[0].device) if self.g.has_body else None)
+        self.recomputed = 0
+        for op in revolve_schedule(self.n, self.slots):
+            if op[0] == "load":
+                su, sb = mem[op[1]]
+                if work_u is None:
+                    work_u, work_b = self._clone(su, sb)
+                else:
+                    for w, s in zip(work_u, su):
+                        w.copy_(s)
+                    if sb is not None:
+                        work_b.copy_(sb)
+            elif op[0] == "advance":
+                self.g.step(work_u, self.dt, op[2] - op[1], body=work_b)
+                self.recomputed += op[2] - op[1]
+            elif op[0] == "store":
+                mem[op[1]] = self._clone(work_u, work_b)
+            elif op[0] == "adjoint":
+                t = op[1]
+                dJdF = None
+                if lam_forces is not None:
+                    dJdF = [float(x) for x in lam_forces[t, :2].tolist()]
+                self.g.step_adjoint(work_u, lam, self.dt, body_n=work_b, lam_body=lb, dJdF=dJdF,
+                                    g_body_force=g_body_force, g_stiffness=g_stiffness)
+        return lam, lb
+
+
+class FsRollout(torch.autograd.Function):
+    """u_T, body_T, forces = FsRollout.apply(grid, dt, nsteps, slots, body_force, stiffness, body0, *u0).
+
+    body_force: float64 device tensor (ny) or None; stiffness: 1-element float64 tensor or None.
+    Gradients flow to u0, body0, body_force and stiffness.
+    """
+
+    @staticmethod
+    def forward(ctx, grid, dt, nsteps, slots, body_force, stiffness, body0, *u0):
+        if body_force is not None:
+            grid.set_body_force(body_force.detach())
+        if stiffness is not None:
+            grid.set_stiffness(float(stiffness.detach().reshape(-1)[0]))
+        ro = Rollout(grid, dt, nsteps, slots)
+        uT, bT, forces = ro.forward([x.detach() for x in u0], body0.detach() if body0 is not None else None)
+        ctx.ro = ro
+        ctx.has_bf = body_force is not None
+        ctx.has_k = stiffness is not None
+        ctx.save_for_backward(*( [x.detach() for x in u0] + ([body0.detach()] if body0 is not None else []) ))
+        ctx.has_body = body0 is not None
+        dummy = torch.zeros(0, device=uT[0].device)
+        return tuple(uT) + (bT if bT is not None else dummy, forces if forces is not None else dummy)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        ro = ctx.ro
+        saved = ctx.saved_tensors
+        dim = ro.g.dim
+        u0 = list(saved[:dim])
+        body0 = saved[dim] if ctx.has_body else None
+        lam_u = [g if g is not None else torch.zeros_like(x) for g, x in zip(grads[:dim], u0)]
+        lam_b = grads[dim] if ctx.has_body and grads[dim] is not None and grads[dim].numel() else None
+        lam_f = grads[dim + 1] if ro.g.has_body and grads[dim + 1] is not None and grads[dim + 1].numel() else None
+        dev = u0[0].device
+        gbf = torch.zeros(ro.g.n[1], dtype=torch.float64, device=dev) if ctx.has_bf else None
+        gk = torch.zeros(1, dtype=torch.float64, device=dev) if ctx.has_k else None
+        lam, lb = ro.backward(u0, body0, lam_u, lam_b, lam_f, gbf, gk)
+        return (None, None, None, None, gbf, gk, lb if ctx.has_body else None) + tuple(lam)
+
+
+def rollout(grid, u0, dt, nsteps, slots=4, body0=None, body_force=None, stiffness=None):
+    """Differentiable rollout: returns (u_T list, body_T or empty, forces (nsteps, 3) or empty)."""
+    out = FsRollout.apply(grid, dt, nsteps, slots, body_force, stiffness, body0, *u0)
+    return list(out[:grid.dim]), out[grid.dim], out[grid.dim + 1]

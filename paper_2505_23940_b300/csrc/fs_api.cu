@@ -656,6 +656,38 @@ int fs_solve_pressure(fs_grid* G, const double* rhs, double* p) {
   return cuda_check(cudaGetLastError(), "fs_solve_pressure launch");
 }
 
+namespace fs {
+__global__ void bf_convert_kernel(const double* __restrict__ src, double* __restrict__ d64, float* __restrict__ d32,
+                                  int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) {
+    d64[t] = src[t];
+    d32[t] = (float)src[t];
+  }
+}
+}  // namespace fs
+
+int fs_set_body_force(fs_grid* G, const double* fx) {
+  if (!G || !fx) return set_error(FS_ERR_ARG, "NULL argument");
+  if (G->bforce.empty()) return set_error(FS_ERR_STATE, "the grid was created without a body_force profile");
+  FS_LAUNCH(G, "set_body_force", bf_convert_kernel<<<(G->ny + 127) / 128, 128, 0, G->stream>>>(fx, G->bf64, G->bf32, G->ny));
+  return cuda_check(cudaGetLastError(), "fs_set_body_force");
+}
+
+int fs_set_stiffness(fs_grid* G, double k) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (!G->has_body) return set_error(FS_ERR_STATE, "no body attached");
+  G->ib.k = k;
+  return FS_OK;
+}
+
+int fs_forces_device(fs_grid* G, double* F) {
+  if (!G || !F) return set_error(FS_ERR_ARG, "NULL argument");
+  if (!G->has_body) return set_error(FS_ERR_STATE, "no body attached");
+  return cuda_check(cudaMemcpyAsync(F, G->ib.F, 3 * sizeof(double), cudaMemcpyDeviceToDevice, G->stream),
+                    "fs_forces_device");
+}
+
 int fs_forces(fs_grid* G, double* F, double* torque, double* q) {
   if (!G) return set_error(FS_ERR_ARG, "NULL grid");
   if (!G->has_body || !G->ib.have_forces) return set_error(FS_ERR_STATE, "no FSI step has run");

@@ -76,6 +76,9 @@ def lib():
         L.fs_last_error.restype = ctypes.c_char_p
         L.fs_profile_begin.argtypes = [c_void_p, ctypes.c_char_p]
         L.fs_profile_end.argtypes = [c_void_p, ctypes.c_char_p, c_int]
+        L.fs_set_body_force.argtypes = [c_void_p, c_void_p]
+        L.fs_set_stiffness.argtypes = [c_void_p, c_double]
+        L.fs_forces_device.argtypes = [c_void_p, c_void_p]
         L.fs_component_stats_noalloc.argtypes = [c_void_p, c_int, POINTER(c_int), c_double, c_void_p, c_void_p,
                                                  c_void_p]
         _LIB = L
@@ -210,6 +213,18 @@ class Grid:
         if with_q:
             return out + ([(q[2 * i], q[2 * i + 1]) for i in range(self.nm)],)
         return out
+
+    def set_body_force(self, fx):
+        """fx: device float64 tensor with ny values (makes the profile a parameter)."""
+        assert fx.is_cuda and fx.dtype == torch.float64 and fx.numel() == self.n[1]
+        check(lib().fs_set_body_force(self.h, c_void_p(fx.contiguous().data_ptr())))
+
+    def set_stiffness(self, k):
+        check(lib().fs_set_stiffness(self.h, float(k)))
+
+    def forces_device(self, out):
+        """Copy {F_x, F_y, torque} of the last step into the device float64 tensor out (3 values)."""
+        check(lib().fs_forces_device(self.h, c_void_p(out.data_ptr())))
 
     def diagnostics(self, u):
         s = self._state(u)
