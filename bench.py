@@ -207,6 +207,49 @@ def predictor_bytes(wl, stage_reads):
     return None
 
 
+def ensemble_leg(args, flush):
+    """Batched ensemble of 2-D cylinder flows of uneven size: K steps of every member through one
+    CUDA-graph launch, against the same members launched one by one (mixed precision)."""
+    import tempfile
+    from paper_2505_23940_b300.ensemble import Ensemble
+    os.environ.setdefault("FS_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "fsstep_tuning_bench.json"))
+    wls = S.ensemble_cylinders(members=args.ensemble, seed=2, precision="mixed")
+    ens = Ensemble(wls, "mixed", streams=16, tune=True)
+    cells = ens.cells()
+    k = args.steps
+    snap = ens.snapshot()
+    stream = torch.cuda.current_stream()
+    ens.step_sequential(2)
+    torch.cuda.synchronize()
+    ens.restore(snap)
+    flush.fill_(3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ens.step_sequential(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    ens.restore(snap)
+    ens.capture(k)
+    ens.restore(snap)
+    torch.cuda.synchronize()
+    flush.fill_(4)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    ens.replay()
+    e3.record(stream)
+    torch.cuda.synchronize()
+    g_ms = e2.elapsed_time(e3)
+    sizes = sorted({tuple(w.n[:2]) for w in wls})
+    return {"members": len(wls), "cells": cells, "steps": k, "grid_sizes": len(sizes),
+            "graph": {"value": cells * k / (g_ms * 1e-3), "unit": "cell-updates/s", "ms": g_ms,
+                      "launches": 1},
+            "one_by_one": {"value": cells * k / (seq_ms * 1e-3), "unit": "cell-updates/s", "ms": seq_ms},
+            "speedup": seq_ms / g_ms,
+            "note": "every member advanced by K steps; graph = one CUDA-graph launch with members on 16 "
+                    "parallel branches; launch parameters autotuned per grid size"}
+
+
 def run_ours(args, ws, rank, local):
     from paper_2505_23940_b300 import grid_from_workload
     torch.cuda.set_device(local)
@@ -339,6 +382,9 @@ def run_ours(args, ws, rank, local):
                            "forward_ms": fwd_ms, "reverse_ms": adj_ms,
                            "note": "K forward steps then the reverse sweep (recomputation + adjoint steps)"}
 
+    if not args.quick and args.ensemble > 0:
+        line["ensemble"] = ensemble_leg(args, flush)
+
     if rank == 0 and not args.quick and args.cpu_steps > 0:
         rate, secs = cpu_oracle_rate(wl, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": torch.get_num_threads(),
@@ -358,6 +404,7 @@ def main():
     ap.add_argument("--workload", default="isotropic_3d_128")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
+    ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -194,6 +194,13 @@ int fs_diagnostics(fs_grid* grid, const fs_state* st, double out[3]);
 /* Number of kernels launched by this grid since creation (host counter). */
 long long fs_kernel_launches(const fs_grid* grid);
 
+/* Launch parameters chosen by an autotuner (0 restores the default):
+ *   "stencil_bx"      x threads of the 256-thread stencil blocks: 32, 64, 128, 256
+ *   "fft_lines"       complex lines per FFT block: 1..16
+ *   "ysolve_threads"  threads per tridiagonal block: power of two in 8..128
+ * Results do not depend on them.  FS_ERR_ARG for an unknown key or value. */
+int fs_set_tuning(fs_grid* grid, const char* key, int value);
+
 /* Kernel timing.  After fs_profile_begin, every launch whose kernel name
  * contains `filter` ("" = all) is bracketed by CUDA events on the grid's
  * stream.  fs_profile_end synchronises the stream and writes one line per

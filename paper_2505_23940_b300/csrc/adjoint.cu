@@ -622,7 +622,7 @@ void launch_rhs_adjoint(fs_grid* G, T* const* u, T* const* mu, T* const* lam) {
   A.conv = G->conv;
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
-  const dim3 blk(32, 8), grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G), grd = stencil_grid(G, A.X, A.Y);
   FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
@@ -630,7 +630,7 @@ void launch_rhs_adjoint(fs_grid* G, T* const* u, T* const* mu, T* const* lam) {
 template <typename T>
 void launch_projection_adjoint_solve(fs_grid* G, T* const* lam, T* spec) {
   const Geom<T> g = G->geom<T>();
-  const dim3 blk(32, 8), grd((G->nx + 31) / 32, (G->ny + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G), grd = stencil_grid(G, G->nx, G->ny);
   FS_LAUNCH(G, "adj_rhs", adj_rhs_kernel<T><<<grd, blk, 0, G->stream>>>(g, lam[0], lam[1], G->dim == 3 ? lam[2] : lam[1],
                                                                         G->hy64, spec));
   poisson_solve_inplace<T>(G, spec);
@@ -713,7 +713,7 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
   T* spec = (T*)G->spec;
   const Geom<T> g = G->geom<T>();
   const int X = G->nx + (G->per[0] ? 0 : 1), Y = G->ny + (G->per[1] ? 0 : 1);
-  const dim3 blk(32, 8), grd((X + 31) / 32, (Y + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G), grd = stencil_grid(G, X, Y);
   double* bfsum = pg ? pg->body_force : nullptr;
 
   if (G->scheme == FS_RK3) {

@@ -486,6 +486,26 @@ int fs_field_extent(const fs_grid* G, int comp, int ext[3]) {
 
 long long fs_kernel_launches(const fs_grid* G) { return G ? G->launches : 0; }
 
+int fs_set_tuning(fs_grid* G, const char* key, int value) {
+  if (!G || !key) return set_error(FS_ERR_ARG, "NULL argument");
+  const std::string k(key);
+  if (k == "stencil_bx") {
+    if (value != 0 && value != 32 && value != 64 && value != 128 && value != 256)
+      return set_error(FS_ERR_ARG, "stencil_bx must be 32, 64, 128 or 256");
+    G->tune_stencil_bx = value;
+  } else if (k == "fft_lines") {
+    if (value < 0 || value > 16) return set_error(FS_ERR_ARG, "fft_lines must be in 1..16");
+    G->tune_fft_lines = value;
+  } else if (k == "ysolve_threads") {
+    if (value != 0 && (value < 8 || value > 128 || (value & (value - 1))))
+      return set_error(FS_ERR_ARG, "ysolve_threads must be a power of two in 8..128");
+    G->tune_ysolve = value;
+  } else {
+    return set_error(FS_ERR_ARG, "unknown tuning key " + k);
+  }
+  return FS_OK;
+}
+
 int fs_profile_begin(fs_grid* G, const char* filter) {
   if (!G) return set_error(FS_ERR_ARG, "NULL grid");
   G->prof_on = true;

@@ -217,6 +217,11 @@ struct fs_grid {
   bool has_body = false;
   void* adj = nullptr;         // adjoint work buffers (adjoint.cu), allocated on first use
 
+  // launch parameters (fs_set_tuning; 0 = built-in default)
+  int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads
+  int tune_fft_lines = 0;      // complex lines per FFT block (1..16)
+  int tune_ysolve = 0;         // threads per y-solve block (8..128)
+
   // optional per-kernel timing (fs_profile_begin / fs_profile_end)
   bool prof_on = false;
   std::string prof_filter;
@@ -255,6 +260,16 @@ int cuda_check(cudaError_t e, const char* what);
 }  // namespace fs
 
 #define FS_LAUNCHED(g) ((g)->launches++)
+
+// Block shape of the stencil kernels: bx threads along x, 256 / bx along y.
+inline dim3 stencil_block(const fs_grid* G) {
+  const int bx = G->tune_stencil_bx > 0 ? G->tune_stencil_bx : 32;
+  return dim3(bx, 256 / bx);
+}
+inline dim3 stencil_grid(const fs_grid* G, int X, int Y) {
+  const dim3 b = stencil_block(G);
+  return dim3((X + b.x - 1) / b.x, (Y + b.y - 1) / b.y, G->nz);
+}
 
 namespace fs {
 // Brackets one kernel launch with CUDA events on the grid's stream when

@@ -515,7 +515,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   // x forward
   {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
-    lpb = lpb > 16 ? 16 : (lpb < 1 ? 1 : lpb);
+    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
+    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
     const int nb = (lines + lpb - 1) / lpb;
     const bool big = has_big(G->px);
@@ -530,7 +531,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   int ppb = 0;
   if (G->dim == 3) {
     ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
-    ppb = ppb > 16 ? 16 : (ppb < 1 ? 1 : ppb);
+    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
+    ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
     if (ppb > nx / 2) ppb = nx / 2;
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
     auto k = has_big(G->pz) ? zfwd_kernel<T, true> : zfwd_kernel<T, false>;
@@ -554,7 +556,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.FAC = G->tFAC;
     A.VL = G->tVL;
     A.hy = G->hy64;
-    const int th = ysolve_threads(ny);
+    int th = ysolve_threads(ny);
+    if (G->tune_ysolve > 0 && G->tune_ysolve < th) th = G->tune_ysolve;
     dim3 grid((nx + th - 1) / th, G->dim == 3 ? nz : 1);
     FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, th, (size_t)ny * th * sizeof(double), G->stream>>>(data, A));
   }
@@ -566,7 +569,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   }
   {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
-    lpb = lpb > 16 ? 16 : (lpb < 1 ? 1 : lpb);
+    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
+    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
     const int nb = (lines + lpb - 1) / lpb;
     auto k = has_big(G->px) ? xinv_kernel<T, true> : xinv_kernel<T, false>;

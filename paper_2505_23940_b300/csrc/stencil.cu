@@ -438,8 +438,8 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   A.xf = G->xf64[0];
   A.yf = G->xf64[1];
   A.oscale = G->scal;
-  const dim3 blk(32, 8);
-  const dim3 grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G);
+  const dim3 grd = stencil_grid(G, A.X, A.Y);
   FS_LAUNCH(G, "predictor", predictor_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
@@ -476,8 +476,8 @@ DivArgs<T> make_div_args(fs_grid* G, T* const* u, const double* body_state) {
 template <typename T>
 void launch_divergence(fs_grid* G, T* const* u, T* out, const double* body_state) {
   const DivArgs<T> A = make_div_args<T>(G, u, body_state);
-  const dim3 blk(32, 8);
-  const dim3 grd((G->nx + 31) / 32, (G->ny + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G);
+  const dim3 grd = stencil_grid(G, G->nx, G->ny);
   FS_LAUNCH(G, "divergence", divergence_kernel<T><<<grd, blk, 0, G->stream>>>(A, out));
 }
 
@@ -492,8 +492,8 @@ void launch_correct(fs_grid* G, T* const* ustar, const T* phi, T* const* unew) {
   A.phi = phi;
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
-  const dim3 blk(32, 8);
-  const dim3 grd((A.X + 31) / 32, (A.Y + 7) / 8, G->nz);
+  const dim3 blk = stencil_block(G);
+  const dim3 grd = stencil_grid(G, A.X, A.Y);
   FS_LAUNCH(G, "correct", correct_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 

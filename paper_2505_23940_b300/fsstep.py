@@ -76,6 +76,7 @@ def lib():
         L.fs_last_error.restype = ctypes.c_char_p
         L.fs_profile_begin.argtypes = [c_void_p, ctypes.c_char_p]
         L.fs_profile_end.argtypes = [c_void_p, ctypes.c_char_p, c_int]
+        L.fs_set_tuning.argtypes = [c_void_p, ctypes.c_char_p, c_int]
         L.fs_set_body_force.argtypes = [c_void_p, c_void_p]
         L.fs_set_stiffness.argtypes = [c_void_p, c_double]
         L.fs_forces_device.argtypes = [c_void_p, c_void_p]
@@ -218,6 +219,14 @@ class Grid:
         """fx: device float64 tensor with ny values (makes the profile a parameter)."""
         assert fx.is_cuda and fx.dtype == torch.float64 and fx.numel() == self.n[1]
         check(lib().fs_set_body_force(self.h, c_void_p(fx.contiguous().data_ptr())))
+
+    def set_tuning(self, key, value):
+        check(lib().fs_set_tuning(self.h, key.encode(), int(value)))
+
+    def set_stream(self, stream):
+        """Enqueue later work on a torch.cuda.Stream (e.g. a graph-capture branch)."""
+        self.stream = stream
+        check(lib().fs_set_stream(self.h, c_void_p(stream.cuda_stream)))
 
     def set_stiffness(self, k):
         check(lib().fs_set_stiffness(self.h, float(k)))

@@ -240,6 +240,26 @@ def cylinder_2d(nx=640, ny=320, cells_per_d=40, nm=126, re=150.0, mass_ratio=2.0
                     precision=precision, kernel=kernel, body=body, u0=[u, v])
 
 
+def ensemble_cylinders(members=64, seed=2, steps=500, precision="mixed", kmin=128, kmax=512):
+    """Members of the batched-ensemble workload: 2-D cylinder flows (16 D x 8 D boxes) with
+    nx drawn uniformly from the multiples of 32 in [kmin, kmax], ny = nx / 2, D = nx / 16
+    cells, Re uniform in [50, 200], 1 % seeded noise on the initial cross-flow velocity,
+    elastically mounted (m* = 2, U_r = 5) as in the FSI workload, dt = 0.2 h."""
+    rng = np.random.default_rng(seed)
+    sizes = np.arange(kmin, kmax + 1, 32)
+    out = []
+    for m in range(members):
+        nx = int(rng.choice(sizes))
+        re = float(rng.uniform(50.0, 200.0))
+        cpd = nx // 16
+        nm = int(round(math.pi * cpd))
+        wl = cylinder_2d(nx=nx, ny=nx // 2, cells_per_d=cpd, nm=nm, re=re, dt=0.2 / cpd, steps=steps,
+                         precision=precision, seed=int(seed * 1000 + m), perturb=0.01)
+        wl.name = "cylinder_2d_member_%d" % m
+        out.append(wl)
+    return out
+
+
 def poiseuille_2d(nx=8, ny=16, nu=1.0, fx=1.0, dt=None, steps=2000, stretched=0.0, slip=False):
     """Periodic-in-x channel y in [-1, 1] with no-slip (or free-slip) walls and body force fx."""
     Lx = 1.0
