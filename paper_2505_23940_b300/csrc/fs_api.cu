@@ -118,8 +118,13 @@ size_t comp_size(const fs_grid* G, int c) {
 
 size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) : sizeof(double); }
 
-// FP64 tables of the y tridiagonal factorisation, one column per eigenvalue index.
+// FP64 tables of the partitioned y solve, one column per eigenvalue index:
+// for each of the 4 segments of every column, the local Thomas factors of the
+// segment's block (e_j = 1 / beta_j, c'_j) and its right / left spikes v, w
+// (the block's response to its coupling with the next / previous segment).
+// The singular zero mode replaces row 0 by phi_0 = 0 (e_0 = 0, no couplings).
 int build_tables(fs_grid* G) {
+  constexpr int NSEG = 4;
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   G->nmx = G->xmode == 1 ? nx : nx / 2 + 1;
   G->nlz = G->dim == 3 ? nz / 2 + 1 : 1;
@@ -128,17 +133,20 @@ int build_tables(fs_grid* G) {
   const std::vector<double>& hf = G->hf[1];
   std::vector<double> a(ny), c(ny);
   for (int j = 0; j < ny; ++j) {
-    a[j] = 1.0 / (hf[j] * h[j]);
-    c[j] = 1.0 / (hf[j + 1] * h[j]);
+    a[j] = 1.0 / (hf[j] * h[j]);        // coupling of row j to j - 1 (row 0: wraps to ny - 1)
+    c[j] = 1.0 / (hf[j + 1] * h[j]);    // coupling of row j to j + 1 (row ny - 1: wraps to 0)
   }
   if (!G->per[1]) {
     a[0] = 0.0;           // G p . n = 0 on the walls
     c[ny - 1] = 0.0;
   }
   G->cyclic = G->per[1];
-  std::vector<double> E((size_t)ny * nlam), CP((size_t)ny * nlam), ZV(G->cyclic ? (size_t)ny * nlam : 1, 0.0);
-  std::vector<double> FAC(nlam, 0.0), VL(nlam, 0.0);
-  std::vector<double> diag(ny), e(ny), cp(ny), z(ny), dp(ny);
+  constexpr int NRED = 2 * NSEG;
+  std::vector<double> E((size_t)ny * nlam), CP((size_t)ny * nlam), V((size_t)ny * nlam), W((size_t)ny * nlam);
+  std::vector<double> MI((size_t)NRED * NRED * nlam);
+  std::vector<double> aa(ny), cc(ny), dd(ny), e(ny), cp(ny), dp(ny), x(ny);
+  std::vector<double> acoef(ny);
+  for (int j = 0; j < ny; ++j) acoef[j] = a[j];
   for (int mx = 0; mx < G->nmx; ++mx) {
     const double lx = G->xmode == 1 ? -(2.0 - 2.0 * std::cos(M_PI * mx / nx)) / (G->hx * G->hx)
                                     : -(2.0 - 2.0 * std::cos(2.0 * M_PI * mx / nx)) / (G->hx * G->hx);
@@ -147,48 +155,76 @@ int build_tables(fs_grid* G) {
       const double lam = lx + lzv;
       const int li = lz * G->nmx + mx;   // [j][lz][mx] layout
       const bool sing = (mx == 0 && lz == 0);
-      for (int j = 0; j < ny; ++j) diag[j] = -(a[j] + c[j]) + lam;
-      double gam = 0, alpha = 0, beta = 0;
-      const bool cyc = G->cyclic && !sing;
-      if (cyc) {
-        gam = -diag[0];
-        alpha = c[ny - 1];
-        beta = a[0];
-        diag[0] -= gam;
-        diag[ny - 1] -= alpha * beta / gam;
-      }
-      if (sing) {
-        e[0] = 0.0;     // phi_0 = 0 replaces the first row of the singular mode
-        cp[0] = 0.0;
-      } else {
-        e[0] = 1.0 / diag[0];
-        cp[0] = c[0] * e[0];
-      }
-      for (int j = 1; j < ny; ++j) {
-        const double b = diag[j] - a[j] * cp[j - 1];
-        e[j] = 1.0 / b;
-        cp[j] = c[j] * e[j];
-      }
       for (int j = 0; j < ny; ++j) {
-        E[(size_t)j * nlam + li] = e[j];
-        CP[(size_t)j * nlam + li] = cp[j];
+        aa[j] = a[j];
+        cc[j] = c[j];
+        dd[j] = -(a[j] + c[j]) + lam;
       }
-      if (cyc) {
-        // Sherman-Morrison: T' z = u with u = (gamma, 0, ..., 0, alpha)
-        for (int j = 0; j < ny; ++j) {
-          const double uj = j == 0 ? gam : (j == ny - 1 ? alpha : 0.0);
-          dp[j] = j == 0 ? uj * e[0] : (uj - a[j] * dp[j - 1]) * e[j];
+      if (sing) {         // phi_0 = 0 replaces row 0; no coupling reaches row 0
+        aa[0] = 0.0;
+        cc[0] = 0.0;
+        if (G->cyclic) cc[ny - 1] = 0.0;
+      }
+      for (int g = 0; g < NSEG; ++g) {
+        const int r0 = (g * ny) / NSEG, r1 = ((g + 1) * ny) / NSEG;
+        if (r1 <= r0) continue;
+        for (int j = r0; j < r1; ++j) {
+          const double beta = dd[j] - (j > r0 ? acoef[j] * cp[j - 1] : 0.0);
+          e[j] = (sing && j == 0) ? 0.0 : 1.0 / beta;
+          cp[j] = j < r1 - 1 ? cc[j] * e[j] : 0.0;
         }
-        z[ny - 1] = dp[ny - 1];
-        for (int j = ny - 2; j >= 0; --j) z[j] = dp[j] - cp[j] * z[j + 1];
-        for (int j = 0; j < ny; ++j) ZV[(size_t)j * nlam + li] = z[j];
-        VL[li] = beta / gam;
-        FAC[li] = 1.0 / (1.0 + z[0] + beta / gam * z[ny - 1]);
+        // spikes: A_g^-1 (a_{r0} e_first), A_g^-1 (c_{r1-1} e_last)
+        for (int which = 0; which < 2; ++which) {
+          for (int j = r0; j < r1; ++j) {
+            const double rhs = which == 0 ? (j == r0 ? aa[r0] : 0.0) : (j == r1 - 1 ? cc[r1 - 1] : 0.0);
+            dp[j] = j == r0 ? rhs * e[j] : (rhs - acoef[j] * dp[j - 1]) * e[j];
+          }
+          x[r1 - 1] = dp[r1 - 1];
+          for (int j = r1 - 2; j >= r0; --j) x[j] = dp[j] - cp[j] * x[j + 1];
+          for (int j = r0; j < r1; ++j) (which == 0 ? W : V)[(size_t)j * nlam + li] = x[j];
+        }
+        for (int j = r0; j < r1; ++j) {
+          E[(size_t)j * nlam + li] = e[j];
+          CP[(size_t)j * nlam + li] = cp[j];
+        }
       }
+      // interface system X_p + v X_{p+1} + w Y_{p-1} = y_first, Y_p + v X_{p+1} + w Y_{p-1} = y_last
+      double M[NRED][2 * NRED];
+      for (int r = 0; r < NRED; ++r)
+        for (int q = 0; q < 2 * NRED; ++q) M[r][q] = (q == r || q == r + NRED) ? 1.0 : 0.0;
+      for (int g = 0; g < NSEG; ++g) {
+        const int r0 = (g * ny) / NSEG, r1 = ((g + 1) * ny) / NSEG;
+        if (r1 <= r0) continue;
+        const int gn = g + 1 < NSEG ? g + 1 : 0, gp = g > 0 ? g - 1 : NSEG - 1;
+        const bool hn = g + 1 < NSEG || G->cyclic, hp = g > 0 || G->cyclic;
+        const int rows[2] = {r0, r1 - 1};
+        for (int hh = 0; hh < 2; ++hh) {
+          const int row = 2 * g + hh;
+          if (hn) M[row][2 * gn] += V[(size_t)rows[hh] * nlam + li];
+          if (hp) M[row][2 * gp + 1] += W[(size_t)rows[hh] * nlam + li];
+        }
+      }
+      // Gauss-Jordan with partial pivoting on [M | I]
+      for (int k = 0; k < NRED; ++k) {
+        int piv = k;
+        for (int r = k + 1; r < NRED; ++r)
+          if (std::fabs(M[r][k]) > std::fabs(M[piv][k])) piv = r;
+        if (piv != k)
+          for (int q = 0; q < 2 * NRED; ++q) std::swap(M[k][q], M[piv][q]);
+        const double inv = 1.0 / M[k][k];
+        for (int q = 0; q < 2 * NRED; ++q) M[k][q] *= inv;
+        for (int r = 0; r < NRED; ++r) {
+          if (r == k || M[r][k] == 0.0) continue;
+          const double f = M[r][k];
+          for (int q = 0; q < 2 * NRED; ++q) M[r][q] -= f * M[k][q];
+        }
+      }
+      for (int r = 0; r < NRED; ++r)
+        for (int q = 0; q < NRED; ++q) MI[(size_t)(r * NRED + q) * nlam + li] = M[r][NRED + q];
     }
   }
-  if (upload(&G->ya, a) != cudaSuccess || upload(&G->tE, E) != cudaSuccess || upload(&G->tCP, CP) != cudaSuccess ||
-      upload(&G->tZV, ZV) != cudaSuccess || upload(&G->tFAC, FAC) != cudaSuccess || upload(&G->tVL, VL) != cudaSuccess)
+  if (upload(&G->ya, acoef) != cudaSuccess || upload(&G->tE, E) != cudaSuccess || upload(&G->tCP, CP) != cudaSuccess ||
+      upload(&G->tZV, V) != cudaSuccess || upload(&G->tWV, W) != cudaSuccess || upload(&G->tMI, MI) != cudaSuccess)
     return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");
   return FS_OK;
 }
@@ -204,7 +240,7 @@ void free_all(fs_grid* G) {
   for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
   F(G->spec); F(G->scal); F(G->red);
   F(G->px.tw); F(G->px.dtw); F(G->pz.tw); F(G->pz.dtw);
-  F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tFAC); F(G->tVL);
+  F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);
   IBDev& B = G->ib;
   F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
@@ -410,9 +446,9 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
     delete G;
     return set_error(FS_ERR_UNSUPPORTED, "fields of 2^31 or more elements (32-bit kernel indexing)");
   }
-  if ((size_t)G->ny * 8 * 8 > 160 * 1024) {
+  if ((size_t)G->ny * 32 * 8 > 200 * 1024) {
     delete G;
-    return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 2560)");
+    return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 800)");
   }
   if (D->body_force) G->bforce.assign(D->body_force, D->body_force + G->ny);
 

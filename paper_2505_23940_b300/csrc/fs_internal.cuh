@@ -210,8 +210,9 @@ struct fs_grid {
   int nmx = 0, nlz = 1;        // eigenvalue table extents
   int cyclic = 0;
   double* ya = nullptr;        // a_j couplings (ny)
-  double *tE = nullptr, *tCP = nullptr, *tZV = nullptr;   // [ny][nlz][nmx]
-  double *tFAC = nullptr, *tVL = nullptr;                 // [nlz][nmx]
+  double *tE = nullptr, *tCP = nullptr;   // [ny][nlz][nmx] segment factors e_j, c'_j
+  double *tZV = nullptr, *tWV = nullptr;  // [ny][nlz][nmx] right / left spikes of each segment
+  double *tMI = nullptr;                  // [64][nlz][nmx] inverse of the 8 x 8 interface system
 
   fs::IBDev ib;
   bool has_body = false;

@@ -150,21 +150,37 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, 
   cplx<T>* B = A + (size_t)lpb * N;
   const int line0 = blockIdx.x * lpb;
   const int nl = min(lpb, (rows + 1) / 2 - line0);
-  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
-    const int l = t / N, i = t - l * N;
-    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
-    T va, vb;
-    if constexpr (DIV) {
-      const int ny = dv.g.ny;
-      va = div_at(dv, i, r0 % ny, r0 / ny);
-      vb = r1 < rows ? div_at(dv, i, r1 % ny, r1 / ny) : T(0);
-    } else {
-      va = data[(size_t)r0 * N + i];
-      vb = r1 < rows ? data[(size_t)r1 * N + i] : T(0);
+  // loads are batched (KB elements per thread in flight) before the shared-memory stores
+  constexpr int KB = 4;
+  for (int t0 = threadIdx.x; t0 < nl * N; t0 += KB * blockDim.x) {
+    T va[KB], vb[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      va[q] = vb[q] = T(0);
+      if (t < nl * N) {
+        const int l = t / N, i = t - l * N;
+        const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+        if constexpr (DIV) {
+          const int ny = dv.g.ny;
+          va[q] = div_at(dv, i, r0 % ny, r0 / ny);
+          if (r1 < rows) vb[q] = div_at(dv, i, r1 % ny, r1 / ny);
+        } else {
+          va[q] = data[(size_t)r0 * N + i];
+          if (r1 < rows) vb[q] = data[(size_t)r1 * N + i];
+        }
+      }
     }
-    int dst = i;
-    if (mode == 1) dst = (i & 1) ? N - 1 - (i >> 1) : (i >> 1);   // even samples forward, odd reversed
-    A[l * N + dst] = {va, vb};
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      if (t < nl * N) {
+        const int l = t / N, i = t - l * N;
+        int dst = i;
+        if (mode == 1) dst = (i & 1) ? N - 1 - (i >> 1) : (i >> 1);   // even samples forward, odd reversed
+        A[l * N + dst] = {va[q], vb[q]};
+      }
+    }
   }
   __syncthreads();
   cplx<T>* Z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, false);
@@ -215,24 +231,41 @@ __global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, 
   cplx<T>* B = A + (size_t)lpb * N;
   const int line0 = blockIdx.x * lpb;
   const int nl = min(lpb, (rows + 1) / 2 - line0);
-  for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
-    const int l = t / N, k = t - l * N;
-    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
-    const T* ra = data + (size_t)r0 * N;
-    const T* rb = data + (size_t)r1 * N;
-    cplx<T> xa, xb;
-    if (mode == 0) {
-      xa = unpack_packed(ra, N, k);
-      xb = r1 < rows ? unpack_packed(rb, N, k) : cplx<T>{T(0), T(0)};
-    } else {
-      // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
-      const cplx<T> w = cconj(dtw[k]);
-      const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
-      const T b1 = r1 < rows ? rb[k] : T(0), b2 = (r1 < rows && k) ? rb[N - k] : T(0);
-      xa = cmul(w, cplx<T>{a1, -a2});
-      xb = cmul(w, cplx<T>{b1, -b2});
+  constexpr int KB = 4;
+  for (int t0 = threadIdx.x; t0 < nl * N; t0 += KB * blockDim.x) {
+    cplx<T> z[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      z[q] = {T(0), T(0)};
+      if (t < nl * N) {
+        const int l = t / N, k = t - l * N;
+        const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+        const T* ra = data + (size_t)r0 * N;
+        const T* rb = data + (size_t)r1 * N;
+        cplx<T> xa, xb;
+        if (mode == 0) {
+          xa = unpack_packed(ra, N, k);
+          xb = r1 < rows ? unpack_packed(rb, N, k) : cplx<T>{T(0), T(0)};
+        } else {
+          // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
+          const cplx<T> w = cconj(dtw[k]);
+          const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
+          const T b1 = r1 < rows ? rb[k] : T(0), b2 = (r1 < rows && k) ? rb[N - k] : T(0);
+          xa = cmul(w, cplx<T>{a1, -a2});
+          xb = cmul(w, cplx<T>{b1, -b2});
+        }
+        z[q] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
+      }
     }
-    A[l * N + k] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      if (t < nl * N) {
+        const int l = t / N, k = t - l * N;
+        A[l * N + k] = z[q];
+      }
+    }
   }
   __syncthreads();
   cplx<T>* z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, true);
@@ -262,11 +295,26 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
   const int np = min(ppb, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;
-  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
-    const int k = t / (2 * np), sl = t - k * (2 * np);
-    const T v = base[plane * k + sl];
-    T* dst = reinterpret_cast<T*>(&A[(sl >> 1) * P + k]);
-    dst[sl & 1] = v;
+  constexpr int KB = 8;
+  for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
+    T v[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      v[q] = T(0);
+      if (t < 2 * np * N) {
+        const int k = t / (2 * np), sl = t - k * (2 * np);
+        v[q] = base[plane * k + sl];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      if (t < 2 * np * N) {
+        const int k = t / (2 * np), sl = t - k * (2 * np);
+        reinterpret_cast<T*>(&A[(sl >> 1) * P + k])[sl & 1] = v[q];
+      }
+    }
   }
   __syncthreads();
   cplx<T>* Z = fft_smem<T, BIG>(A, B, N, P, np, rad, tw, false);
@@ -302,11 +350,26 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
   const int np = min(ppb, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;
-  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
-    const int k = t / (2 * np), sl = t - k * (2 * np);
-    const T v = base[plane * k + sl];
-    T* dst = reinterpret_cast<T*>(&B[(sl >> 1) * P + k]);
-    dst[sl & 1] = v;
+  constexpr int KB = 8;
+  for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
+    T v[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      v[q] = T(0);
+      if (t < 2 * np * N) {
+        const int k = t / (2 * np), sl = t - k * (2 * np);
+        v[q] = base[plane * k + sl];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = t0 + q * blockDim.x;
+      if (t < 2 * np * N) {
+        const int k = t / (2 * np), sl = t - k * (2 * np);
+        reinterpret_cast<T*>(&B[(sl >> 1) * P + k])[sl & 1] = v[q];
+      }
+    }
   }
   __syncthreads();
   for (int t = threadIdx.x; t < np * N; t += blockDim.x) {
@@ -343,9 +406,9 @@ struct YArgs {
   const double* a;       // a_j
   const double* E;       // [ny][nlam]
   const double* CP;
-  const double* ZV;
-  const double* FAC;     // [nlam]
-  const double* VL;
+  const double* ZV;      // right spikes v_j  [ny][nlam]
+  const double* WV;      // left spikes w_j   [ny][nlam]
+  const double* MI;      // inverse interface matrices [NRED * NRED][nlam]
   const double* hy;      // cell widths (zero-mode mean)
 };
 
@@ -359,97 +422,143 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
   return lz * A.nmx + mx;   // tables are [j][lz][mx]: consecutive slots read consecutive entries
 }
 
-// One thread per column (slot s at one z position): FP64 Thomas with the
-// factors e_j = 1 / beta_j and c'_j of the column's eigenvalue.  The block
-// stages its data tile in shared memory with coalesced loads; the factor
-// tables are read 16 rows ahead of the recurrence.
+// Partitioned (SPIKE) solve: every column is split into NSEG segments of
+// about ny / NSEG rows solved concurrently by NSEG threads.  Each segment's
+// local factors (e_j = 1 / beta_j, c'_j) and its two spikes (the response to
+// its coupling with the neighbouring segments, v_j and w_j) are tabulated per
+// eigenvalue on the host, so one step of the solve is
+//   1. y = A_p^-1 d on each segment (FP64 Thomas, local factors)
+//   2. the 2 NSEG interface values X_p = x[first of p], Y_p = x[last of p] from
+//        X_p + v_f X_{p+1} + w_f Y_{p-1} = y_f,   Y_p + v_l X_{p+1} + w_l Y_{p-1} = y_l
+//      (periodic y couples the last and first segments).  That 2 NSEG system
+//      depends on the eigenvalue only: its inverse is tabulated on the host and
+//      the four threads of a column each form two of its rows' products in FP64
+//   3. x_j = y_j - v_j X_{p+1} - w_j Y_{p-1} on every row.
+// The singular zero mode pins x_0 = 0 (e_0 = 0 in its table) and is shifted to
+// zero hy-weighted mean afterwards.
+constexpr int NSEG = 4;
+constexpr int YCOLS = 32;
+constexpr int NRED = 2 * NSEG;
+
 template <typename T>
-__global__ void ysolve_kernel(T* __restrict__ data, const YArgs A) {
-  extern __shared__ double dsm[];  // [ny][blockDim.x]: the column tile, then dp, then x
-  constexpr int U = 16;            // table rows whose loads are issued together
-  const int bw = blockDim.x;
-  const int s0 = blockIdx.x * bw;
-  const int t = blockIdx.y;
-  const int s = s0 + threadIdx.x;
+__global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ data, const YArgs A) {
+  extern __shared__ double sm[];
   const int ny = A.ny;
-  const int ncol = min(bw, A.nx - s0);
+  double* D = sm;                                  // [ny][YCOLS] data tile, then y, then x
+  double* Z = D + (size_t)ny * YCOLS;              // [YCOLS][NRED] interface values
+  double* R = Z + YCOLS * NRED;                    // [YCOLS][2 NSEG] mean partial sums
+  const int tx = threadIdx.x, p = threadIdx.y;
+  const int tid = tx + YCOLS * p;
+  const int s0 = blockIdx.x * YCOLS;
+  const int t = blockIdx.y;
+  const int s = s0 + tx;
+  const int ncol = min(YCOLS, A.nx - s0);
   const int nlam = A.nmx * A.nlz;
   T* tile = data + s0 + (size_t)A.nx * A.ny * t;
   const size_t rs = (size_t)A.nx;
-  for (int e = threadIdx.x; e < ny * bw; e += bw) {
-    const int j = e / bw, q = e - j * bw;
-    dsm[e] = q < ncol ? (double)tile[rs * j + q] : 0.0;
+  for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+    const int j = e / YCOLS, c = e - j * YCOLS;
+    D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
   }
   __syncthreads();
-  if (s < A.nx) {
-    const int li = lam_index(A, s, t);
-    const double* E = A.E + li;
-    const double* CP = A.CP + li;
-    double* my = dsm + threadIdx.x;
-    // forward elimination: dp_j = (d_j - a_j dp_{j-1}) e_j
+  const bool act = s < A.nx;
+  const int li = act ? lam_index(A, s, t) : 0;
+  const int r0 = (p * ny) / NSEG, r1 = ((p + 1) * ny) / NSEG;
+  const double* E = A.E + li;
+  const double* CP = A.CP + li;
+  const double* V = A.ZV + li;    // right spikes
+  const double* W = A.WV + li;    // left spikes
+  double* col = D + tx;
+  if (act && r1 > r0) {
+    // 1. segment Thomas
     double prev = 0.0;
-    int j = 0;
-    for (; j + U <= ny; j += U) {
-      double e[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) e[q] = __ldg(E + (size_t)(j + q) * nlam);
+    constexpr int U = 8;
+    int j = r0;
+    for (; j + U <= r1; j += U) {
+      double e[U], a[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        const double d = my[(j + q) * bw];
-        prev = (j + q == 0) ? d * e[q] : (d - __ldg(A.a + j + q) * prev) * e[q];
-        my[(j + q) * bw] = prev;
+        e[q] = __ldg(E + (size_t)(j + q) * nlam);
+        a[q] = __ldg(A.a + j + q);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const double d = col[(j + q) * YCOLS];
+        prev = (j + q == r0) ? d * e[q] : (d - a[q] * prev) * e[q];
+        col[(j + q) * YCOLS] = prev;
       }
     }
-    for (; j < ny; ++j) {
-      const double d = my[j * bw];
-      prev = (j == 0) ? d * __ldg(E) : (d - __ldg(A.a + j) * prev) * __ldg(E + (size_t)j * nlam);
-      my[j * bw] = prev;
+    for (; j < r1; ++j) {
+      const double d = col[j * YCOLS];
+      prev = (j == r0) ? d * __ldg(E + (size_t)j * nlam) : (d - __ldg(A.a + j) * prev) * __ldg(E + (size_t)j * nlam);
+      col[j * YCOLS] = prev;
     }
-    // back substitution: x_j = dp_j - c'_j x_{j+1}
     double x = prev;
-    j = ny - 2;
-    for (; j - U + 1 >= 0; j -= U) {
+    j = r1 - 2;
+    for (; j - U + 1 >= r0; j -= U) {
       double c[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) c[q] = __ldg(CP + (size_t)(j - q) * nlam);
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        x = my[(j - q) * bw] - c[q] * x;
-        my[(j - q) * bw] = x;
+        x = col[(j - q) * YCOLS] - c[q] * x;
+        col[(j - q) * YCOLS] = x;
       }
     }
-    for (; j >= 0; --j) {
-      x = my[j * bw] - __ldg(CP + (size_t)j * nlam) * x;
-      my[j * bw] = x;
-    }
-    if (li == 0) {
-      // singular zero mode: shift to zero hy-weighted mean
-      double sw = 0.0, sx = 0.0;
-      for (int q = 0; q < ny; ++q) {
-        sx += my[q * bw] * A.hy[q];
-        sw += A.hy[q];
-      }
-      const double mean = sx / sw;
-      for (int q = 0; q < ny; ++q) my[q * bw] -= mean;
-    } else if (A.cyclic) {
-      // Sherman-Morrison correction of the periodic coupling
-      const double f = (my[0] + A.VL[li] * my[(ny - 1) * bw]) * A.FAC[li];
-      const double* ZV = A.ZV + li;
-      j = 0;
-      for (; j + U <= ny; j += U) {
-        double z[U];
-#pragma unroll
-        for (int q = 0; q < U; ++q) z[q] = __ldg(ZV + (size_t)(j + q) * nlam);
-#pragma unroll
-        for (int q = 0; q < U; ++q) my[(j + q) * bw] -= f * z[q];
-      }
-      for (; j < ny; ++j) my[j * bw] -= f * __ldg(ZV + (size_t)j * nlam);
+    for (; j >= r0; --j) {
+      x = col[j * YCOLS] - __ldg(CP + (size_t)j * nlam) * x;
+      col[j * YCOLS] = x;
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < ny * bw; e += bw) {
-    const int j = e / bw, q = e - j * bw;
-    if (q < ncol) tile[rs * j + q] = (T)dsm[e];
+  // 2. interface values: z = Minv b, b = (y[first], y[last]) of every segment
+  if (act) {
+    double b[NRED];
+#pragma unroll
+    for (int g = 0; g < NSEG; ++g) {
+      const int a0 = (g * ny) / NSEG, a1 = ((g + 1) * ny) / NSEG;
+      b[2 * g] = a1 > a0 ? col[a0 * YCOLS] : 0.0;
+      b[2 * g + 1] = a1 > a0 ? col[(a1 - 1) * YCOLS] : 0.0;
+    }
+    double* z = Z + tx * NRED;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = 2 * p + h;
+      double v = 0.0;
+#pragma unroll
+      for (int q = 0; q < NRED; ++q) v += __ldg(A.MI + (size_t)(r * NRED + q) * nlam + li) * b[q];
+      z[r] = v;
+    }
+  }
+  __syncthreads();
+  // 3. spike correction
+  double part = 0.0;
+  if (act && r1 > r0) {
+    const bool cyc = A.cyclic != 0;
+    const double* z = Z + tx * NRED;
+    const int gn = p + 1 < NSEG ? p + 1 : 0, gp = p > 0 ? p - 1 : NSEG - 1;
+    const double Xn = (p + 1 < NSEG || cyc) ? z[2 * gn] : 0.0;
+    const double Yp = (p > 0 || cyc) ? z[2 * gp + 1] : 0.0;
+    for (int j = r0; j < r1; ++j) {
+      const double v = col[j * YCOLS] - __ldg(V + (size_t)j * nlam) * Xn - __ldg(W + (size_t)j * nlam) * Yp;
+      col[j * YCOLS] = v;
+      if (li == 0) part += v * A.hy[j];
+    }
+  }
+  // singular zero mode: shift to zero hy-weighted mean
+  if (li == 0 && act) R[tx * NSEG + p] = part;
+  __syncthreads();
+  if (li == 0 && act && r1 > r0) {
+    double sx = 0.0, sw = 0.0;
+    for (int g = 0; g < NSEG; ++g) sx += R[tx * NSEG + g];
+    for (int q = 0; q < ny; ++q) sw += A.hy[q];
+    const double mean = sx / sw;
+    for (int j = r0; j < r1; ++j) col[j * YCOLS] -= mean;
+  }
+  __syncthreads();
+  for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+    const int j = e / YCOLS, c = e - j * YCOLS;
+    if (c < ncol) tile[rs * j + c] = (T)D[e];
   }
 }
 
@@ -488,7 +597,7 @@ void set_smem_attrs() {
   if (done) return;
   set_smem_attrs_big<T, false>();
   set_smem_attrs_big<T, true>();
-  cudaFuncSetAttribute(ysolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   done = true;
 }
 
@@ -500,11 +609,8 @@ bool has_big(const Plan1D& p) {
 
 }  // namespace
 
-// Threads per y-solve block: each thread stages one column of ny doubles.
-int ysolve_threads(int ny) {
-  int nt = 64;
-  while (nt > 8 && (size_t)ny * nt * 8 > 160 * 1024) nt /= 2;
-  return nt;
+size_t ysolve_smem(int ny) {
+  return ((size_t)ny * YCOLS + YCOLS * NRED + YCOLS * NSEG) * sizeof(double);
 }
 
 template <typename T>
@@ -553,13 +659,11 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.E = G->tE;
     A.CP = G->tCP;
     A.ZV = G->tZV;
-    A.FAC = G->tFAC;
-    A.VL = G->tVL;
+    A.WV = G->tWV;
+    A.MI = G->tMI;
     A.hy = G->hy64;
-    int th = ysolve_threads(ny);
-    if (G->tune_ysolve > 0 && G->tune_ysolve < th) th = G->tune_ysolve;
-    dim3 grid((nx + th - 1) / th, G->dim == 3 ? nz : 1);
-    FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, th, (size_t)ny * th * sizeof(double), G->stream>>>(data, A));
+    dim3 grid((nx + YCOLS - 1) / YCOLS, G->dim == 3 ? nz : 1);
+    FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, dim3(YCOLS, NSEG), ysolve_smem(ny), G->stream>>>(data, A));
   }
   if (G->dim == 3) {
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
