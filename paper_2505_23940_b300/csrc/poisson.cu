@@ -46,9 +46,12 @@ struct Radices {
 namespace {
 
 // One Stockham stage with compile-time radix R over `nlines` lines of length N.
-template <typename T, int R>
-__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int N,
-                                               int P, int nlines, int Ns, const cplx<T>* __restrict__ tw, bool inv) {
+// NC, NSC: compile-time line length and sub-transform size (0: the runtime values).
+template <typename T, int R, int NC = 0, int NSC = 0>
+__device__ __forceinline__ void stockham_stage(const cplx<T>* __restrict__ in, cplx<T>* __restrict__ out, int Nrt,
+                                               int P, int nlines, int Nsrt, const cplx<T>* __restrict__ tw, bool inv) {
+  const int N = NC ? NC : Nrt;
+  const int Ns = NSC ? NSC : Nsrt;
   const int NR = N / R;
   const int nb = nlines * NR;
   const int tws = N / (Ns * R);
@@ -136,16 +139,64 @@ __device__ cplx<T>* fft_smem(cplx<T>* a, cplx<T>* b, int N, int P, int nlines, c
   return a;
 }
 
+// Compile-time plans for the line lengths used most (64, 128, 192, 256): the
+// radix sequence, stage sizes and every index division are constants.
+constexpr int ct_radix(int n, int s) {
+  int m = n, st = 0;
+  while (m % 4 == 0 && m > 4) {
+    if (st == s) return 4;
+    m /= 4;
+    ++st;
+  }
+  const int primes[7] = {4, 2, 3, 5, 7, 11, 13};
+  for (int q = 0; q < 7; ++q)
+    while (m % primes[q] == 0) {
+      if (st == s) return primes[q];
+      m /= primes[q];
+      ++st;
+    }
+  return 1;
+}
+
+constexpr int ct_nstages(int n) {
+  int st = 0;
+  while (ct_radix(n, st) > 1) ++st;
+  return st;
+}
+
+template <typename T, int N, int S, int NS>
+__device__ __forceinline__ cplx<T>* fft_ct(cplx<T>* a, cplx<T>* b, int P, int nlines, const cplx<T>* __restrict__ tw,
+                                          bool inv) {
+  if constexpr (S >= ct_nstages(N)) {
+    return a;
+  } else {
+    constexpr int R = ct_radix(N, S);
+    stockham_stage<T, R, N, NS>(a, b, N, P, nlines, NS, tw, inv);
+    __syncthreads();
+    return fft_ct<T, N, S + 1, NS * R>(b, a, P, nlines, tw, inv);
+  }
+}
+
+// PL: 0 generic plan with radices <= 5, 1 generic plan with radices up to 13,
+// >= 2 the compile-time plan of length PL.
+template <typename T, int PL>
+__device__ __forceinline__ cplx<T>* fft_any(cplx<T>* a, cplx<T>* b, int N, int P, int nlines, const Radices& rad,
+                                           const cplx<T>* __restrict__ tw, bool inv) {
+  if constexpr (PL >= 2) return fft_ct<T, PL, 0, 1>(a, b, P, nlines, tw, inv);
+  else return fft_smem<T, PL == 1>(a, b, N, P, nlines, rad, tw, inv);
+}
+
 // ---------------------------------------------------------------------------
 // x transforms: rows of length N = nx, two rows per complex line.
 // mode 0: periodic DFT (real-packed output), mode 1: DCT-II.
 // DIV: the rows are not read from `data` but formed on the fly as the
 // divergence D[(1 - eps) u* + eps u_c] of Eq. (9) (row r = j + ny k).
-template <typename T, bool BIG, bool DIV>
-__global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, int rows, int lpb, int mode, Radices rad,
+template <typename T, int PL, bool DIV>
+__global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int Nrt, int rows, int lpb, int mode, Radices rad,
                             const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw,
                             const DivArgs<T> dv) {
   extern __shared__ unsigned char smem_raw[];
+  const int N = PL >= 2 ? PL : Nrt;
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* B = A + (size_t)lpb * N;
   const int line0 = blockIdx.x * lpb;
@@ -183,7 +234,7 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int N, 
     }
   }
   __syncthreads();
-  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, false);
+  cplx<T>* Z = fft_any<T, PL>(A, B, N, N, nl, rad, tw, false);
   for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
     const int l = t / N, s = t - l * N;
     const int r0 = 2 * (line0 + l), r1 = r0 + 1;
@@ -223,10 +274,11 @@ __device__ __forceinline__ cplx<T> unpack_packed(const T* __restrict__ row, int 
   return {row[2 * m], -row[2 * m + 1]};
 }
 
-template <typename T, bool BIG>
-__global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, int rows, int lpb, int mode, Radices rad,
+template <typename T, int PL>
+__global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int Nrt, int rows, int lpb, int mode, Radices rad,
                             const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dtw) {
   extern __shared__ unsigned char smem_raw[];
+  const int N = PL >= 2 ? PL : Nrt;
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* B = A + (size_t)lpb * N;
   const int line0 = blockIdx.x * lpb;
@@ -268,7 +320,7 @@ __global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, 
     }
   }
   __syncthreads();
-  cplx<T>* z = fft_smem<T, BIG>(A, B, N, N, nl, rad, tw, true);
+  cplx<T>* z = fft_any<T, PL>(A, B, N, N, nl, rad, tw, true);
   const T inv_n = T(1) / T(N);
   for (int t = threadIdx.x; t < nl * N; t += blockDim.x) {
     const int l = t / N, i = t - l * N;
@@ -283,10 +335,11 @@ __global__ void __launch_bounds__(256) xinv_kernel(T* __restrict__ data, int N, 
 
 // ---------------------------------------------------------------------------
 // z transforms (3-D, periodic z): complex lines of slot pairs (2m, 2m+1) along z.
-template <typename T, bool BIG>
-__global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx, int ny, int N, int ppb, Radices rad,
+template <typename T, int PL>
+__global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx, int ny, int Nrt, int ppb, Radices rad,
                             const cplx<T>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
+  const int N = PL >= 2 ? PL : Nrt;
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
   const int P = N + 1;   // padded line pitch: lines start in different banks
   cplx<T>* B = A + (size_t)ppb * P;
@@ -317,7 +370,7 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
     }
   }
   __syncthreads();
-  cplx<T>* Z = fft_smem<T, BIG>(A, B, N, P, np, rad, tw, false);
+  cplx<T>* Z = fft_any<T, PL>(A, B, N, P, np, rad, tw, false);
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int p = t / (2 * np), sl = t - p * (2 * np);
     const int line = sl >> 1;
@@ -338,10 +391,11 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
   }
 }
 
-template <typename T, bool BIG>
-__global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx, int ny, int N, int ppb, Radices rad,
+template <typename T, int PL>
+__global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx, int ny, int Nrt, int ppb, Radices rad,
                             const cplx<T>* __restrict__ tw) {
   extern __shared__ unsigned char smem_raw[];
+  const int N = PL >= 2 ? PL : Nrt;
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);
   const int P = N + 1;   // padded line pitch: lines start in different banks
   cplx<T>* B = A + (size_t)ppb * P;
@@ -389,7 +443,7 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
     }
   }
   __syncthreads();
-  cplx<T>* z = fft_smem<T, BIG>(A, B, N, P, np, rad, tw, true);
+  cplx<T>* z = fft_any<T, PL>(A, B, N, P, np, rad, tw, true);
   const T inv_n = T(1) / T(N);
   for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
     const int k = t / (2 * np), sl = t - k * (2 * np);
@@ -582,21 +636,56 @@ Radices radices_of(const Plan1D& p) {
 
 constexpr size_t kSmemBudget = 96 * 1024;
 
-template <typename T, bool BIG>
-void set_smem_attrs_big() {
-  cudaFuncSetAttribute(xfwd_kernel<T, BIG, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(xfwd_kernel<T, BIG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(xinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(zfwd_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(zinv_kernel<T, BIG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+template <typename T, int PL>
+void set_smem_attrs_plan() {
+  cudaFuncSetAttribute(xfwd_kernel<T, PL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(xfwd_kernel<T, PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(xinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+}
+
+// Kernel instances by plan: compile-time lengths first, generic plans otherwise.
+template <typename T>
+struct FftKernels {
+  using XF = void (*)(T*, int, int, int, int, Radices, const cplx<T>*, const cplx<T>*, const DivArgs<T>);
+  using XI = void (*)(T*, int, int, int, int, Radices, const cplx<T>*, const cplx<T>*);
+  using ZK = void (*)(T*, int, int, int, int, Radices, const cplx<T>*);
+  XF xfwd, xfwd_div;
+  XI xinv;
+  ZK zfwd, zinv;
+};
+
+template <typename T, int PL>
+FftKernels<T> fft_kernels_of() {
+  return {xfwd_kernel<T, PL, false>, xfwd_kernel<T, PL, true>, xinv_kernel<T, PL>, zfwd_kernel<T, PL>,
+          zinv_kernel<T, PL>};
+}
+
+template <typename T>
+FftKernels<T> fft_kernels(const Plan1D& p) {
+  switch (p.n) {
+    case 64: return fft_kernels_of<T, 64>();
+    case 128: return fft_kernels_of<T, 128>();
+    case 192: return fft_kernels_of<T, 192>();
+    case 256: return fft_kernels_of<T, 256>();
+    default: break;
+  }
+  for (int i = 0; i < p.nst; ++i)
+    if (p.radix[i] > 5) return fft_kernels_of<T, 1>();
+  return fft_kernels_of<T, 0>();
 }
 
 template <typename T>
 void set_smem_attrs() {
   static bool done = false;
   if (done) return;
-  set_smem_attrs_big<T, false>();
-  set_smem_attrs_big<T, true>();
+  set_smem_attrs_plan<T, 0>();
+  set_smem_attrs_plan<T, 1>();
+  set_smem_attrs_plan<T, 64>();
+  set_smem_attrs_plan<T, 128>();
+  set_smem_attrs_plan<T, 192>();
+  set_smem_attrs_plan<T, 256>();
   cudaFuncSetAttribute(ysolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   done = true;
 }
@@ -625,9 +714,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
     const int nb = (lines + lpb - 1) / lpb;
-    const bool big = has_big(G->px);
-    auto k = dv ? (big ? xfwd_kernel<T, true, true> : xfwd_kernel<T, false, true>)
-                : (big ? xfwd_kernel<T, true, false> : xfwd_kernel<T, false, false>);
+    const FftKernels<T> K = fft_kernels<T>(G->px);
+    auto k = dv ? K.xfwd_div : K.xfwd;
     const DivArgs<T> none{};
     FS_LAUNCH(G, dv ? "fft_x_fwd_div" : "fft_x_fwd",
               k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
@@ -641,7 +729,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
     if (ppb > nx / 2) ppb = nx / 2;
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
-    auto k = has_big(G->pz) ? zfwd_kernel<T, true> : zfwd_kernel<T, false>;
+    auto k = fft_kernels<T>(G->pz).zfwd;
     FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
@@ -667,7 +755,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   }
   if (G->dim == 3) {
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
-    auto k = has_big(G->pz) ? zinv_kernel<T, true> : zinv_kernel<T, false>;
+    auto k = fft_kernels<T>(G->pz).zinv;
     FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
@@ -677,7 +765,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
     const int nb = (lines + lpb - 1) / lpb;
-    auto k = has_big(G->px) ? xinv_kernel<T, true> : xinv_kernel<T, false>;
+    auto k = fft_kernels<T>(G->px).xinv;
     FS_LAUNCH(G, "fft_x_inv", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
                                                           (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
   }
