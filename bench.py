@@ -35,16 +35,27 @@ sys.path.insert(0, ROOT)
 import synthetic as S  # noqa: E402
 
 # Bytes each kernel must move per launch (every array read or written once), per cell
-# of the 3-D mixed-precision RK3 step: f32 fields, f64 tridiagonal factor tables.
+# of the 3-D mixed-precision step: FP32 fields and spectrum.  The predictor reads
+# u (12) and writes u* (12), plus u^n (12) in RK3 stages 2 and 3; the y solve adds
+# its FP64 tables (computed in roofline()).
 KERNEL_BYTES_PER_CELL = {
-    "predictor_u": None, "predictor_v": None, "predictor_w": None,   # 3 reads + 1 write (+1 read in stages 2, 3)
-    "divergence": 16.0, "fft_x_fwd": 8.0, "fft_z_fwd": 8.0, "fft_z_inv": 8.0, "fft_x_inv": 8.0,
-    "correct_u": 12.0, "correct_v": 12.0, "correct_w": 12.0,
+    "fft_x_fwd_div": 12.0 + 4.0, "fft_x_fwd": 8.0, "fft_z_fwd": 8.0, "fft_z_inv": 8.0, "fft_x_inv": 8.0,
+    "correct": 12.0 + 4.0 + 12.0, "divergence": 16.0,
 }
 
-# DRAM bytes per launch from an ncu capture of the kernel as it stands (see profiles/);
-# keyed by kernel name with the hash of the source file it was measured on.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch from one ncu capture of the 128^3 mixed RK3
+# workload (ncu flushes caches before each captured launch; writes still resident
+# in L2 at kernel end are not counted), keyed by kernel with the hash of the source
+# file it was measured on: a changed kernel reports traffic null until re-captured.
+NCU_TRAFFIC = {
+    "predictor": {"bytes": 25234688 + 1075968, "src": "48fa61085730"},
+    "ysolve": {"bytes": 27757056, "src": "2d9c5f98a66a"},
+    "fft_x_fwd_div": {"bytes": 25207552, "src": "2d9c5f98a66a"},
+    "fft_z_fwd": {"bytes": 8411648, "src": "2d9c5f98a66a"},
+    "fft_z_inv": {"bytes": 8412160, "src": "2d9c5f98a66a"},
+    "fft_x_inv": {"bytes": 8405760, "src": "2d9c5f98a66a"},
+    "correct": {"bytes": 33559552 + 256, "src": "48fa61085730"},
+}
 
 
 def src_hash(name):
@@ -289,7 +300,7 @@ def run_ours(args, ws, rank, local):
     peak = peaks.get("hbm_gbs", 6400.0)
     bpc = KERNEL_BYTES_PER_CELL.get(dominant)
     if dominant.startswith("predictor"):
-        bpc = (16.0 + 20.0 + 20.0) / 3.0 if wl.scheme == "rk3" else 16.0
+        bpc = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
     if dominant == "ysolve":
         nlam = (wl.n[0] // 2 + 1) * (wl.n[2] // 2 + 1)
         bpc = 8.0 + 3 * 8.0 * nlam * wl.n[1] / cells
