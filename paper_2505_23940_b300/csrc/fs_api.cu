@@ -129,6 +129,25 @@ int build_tables(fs_grid* G) {
   G->nmx = G->xmode == 1 ? nx : nx / 2 + 1;
   G->nlz = G->dim == 3 ? nz / 2 + 1 : 1;
   const int nlam = G->nmx * G->nlz;
+  if (G->yspec) {
+    // periodic y is uniform: the y operator is circulant and diagonal in the DFT basis
+    const double hy = G->h[1][0];
+    std::vector<double> ly(ny), lxz(nlam);
+    for (int k = 0; k < ny; ++k) ly[k] = -(2.0 - 2.0 * std::cos(2.0 * M_PI * k / ny)) / (hy * hy);
+    for (int mx = 0; mx < G->nmx; ++mx)
+      for (int lz = 0; lz < G->nlz; ++lz) {
+        const double lx = G->xmode == 1 ? -(2.0 - 2.0 * std::cos(M_PI * mx / nx)) / (G->hx * G->hx)
+                                        : -(2.0 - 2.0 * std::cos(2.0 * M_PI * mx / nx)) / (G->hx * G->hx);
+        const double lzv = G->dim == 3 ? -(2.0 - 2.0 * std::cos(2.0 * M_PI * lz / nz)) / (G->hz * G->hz) : 0.0;
+        lxz[lz * G->nmx + mx] = lx + lzv;
+      }
+    const bool ok = G->prec == FS_MIXED
+                        ? (upload((float**)&G->lamy, cast<float>(ly)) == cudaSuccess &&
+                           upload((float**)&G->lamxz, cast<float>(lxz)) == cudaSuccess)
+                        : (upload((double**)&G->lamy, ly) == cudaSuccess &&
+                           upload((double**)&G->lamxz, lxz) == cudaSuccess);
+    return ok ? FS_OK : set_error(FS_ERR_CUDA, "allocating eigenvalue tables");
+  }
   const std::vector<double>& h = G->h[1];
   const std::vector<double>& hf = G->hf[1];
   std::vector<double> a(ny), c(ny);
@@ -239,7 +258,8 @@ void free_all(fs_grid* G) {
   F(G->hy64); F(G->hfy64);
   for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
   F(G->spec); F(G->scal); F(G->red);
-  F(G->px.tw); F(G->px.dtw); F(G->pz.tw); F(G->pz.dtw);
+  F(G->px.tw); F(G->px.dtw); F(G->py.tw); F(G->py.dtw); F(G->pz.tw); F(G->pz.dtw);
+  F(G->lamy); F(G->lamxz);
   F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);
   IBDev& B = G->ib;
   F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
@@ -438,7 +458,9 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
   G->hx = G->h[0][0];
   G->hz = G->h[2][0];
   G->xmode = G->per[0] ? 0 : 1;
-  if (!factorize(G->nx, G->px) || (G->dim == 3 && !factorize(G->nz, G->pz))) {
+  G->yspec = G->per[1];
+  if (!factorize(G->nx, G->px) || (G->dim == 3 && !factorize(G->nz, G->pz)) ||
+      (G->yspec && !factorize(G->ny, G->py))) {
     delete G;
     return set_error(FS_ERR_UNSUPPORTED, "transform length with a prime factor > 13");
   }
@@ -478,9 +500,11 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
   if (ok) ok = dalloc(&G->scal, 64) == cudaSuccess && cudaMemset(G->scal, 0, 64 * sizeof(double)) == cudaSuccess;
   if (ok) ok = dalloc(&G->red, 64) == cudaSuccess;
   if (ok) ok = G->prec == FS_MIXED ? (make_twiddles<float>(G->px) == cudaSuccess &&
-                                      (G->dim == 2 || make_twiddles<float>(G->pz) == cudaSuccess))
+                                      (G->dim == 2 || make_twiddles<float>(G->pz) == cudaSuccess) &&
+                                      (!G->yspec || make_twiddles<float>(G->py) == cudaSuccess))
                                    : (make_twiddles<double>(G->px) == cudaSuccess &&
-                                      (G->dim == 2 || make_twiddles<double>(G->pz) == cudaSuccess));
+                                      (G->dim == 2 || make_twiddles<double>(G->pz) == cudaSuccess) &&
+                                      (!G->yspec || make_twiddles<double>(G->py) == cudaSuccess));
   if (!ok) {
     free_all(G);
     delete G;

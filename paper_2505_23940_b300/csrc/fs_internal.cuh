@@ -205,8 +205,11 @@ struct fs_grid {
   double* red = nullptr;       // reduction partials
 
   // Poisson plans
-  fs::Plan1D px, pz;
+  fs::Plan1D px, py, pz;       // py: periodic y only
   int xmode = 0;               // 0: periodic DFT, 1: DCT-II
+  int yspec = 0;               // 1: periodic (uniform) y, solved spectrally along y as well
+  void* lamy = nullptr;        // field type: y eigenvalues -(2 - 2 cos(2 pi k / ny)) / hy^2 (ny)
+  void* lamxz = nullptr;       // field type: x + z eigenvalue of each [lz][mx] index
   int nmx = 0, nlz = 1;        // eigenvalue table extents
   int cyclic = 0;
   double* ya = nullptr;        // a_j couplings (ny)

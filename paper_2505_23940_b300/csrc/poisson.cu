@@ -7,9 +7,12 @@
 //        slot 0 = Re X_0, slot 1 = Re X_{n/2}, slots 2m, 2m+1 = Re, Im X_m
 //   z: (3-D) complex FFT of slot pairs (2m, 2m+1) along z; the pair m = 0 holds
 //      two real sequences and is split into two real-packed z spectra
-//   y: per wavenumber, the remaining tridiagonal system in FP64 (Thomas with
-//      factors precomputed per eigenvalue; Sherman-Morrison for periodic y;
-//      the singular zero mode pinned and shifted to zero mean)
+//   y: wall-bounded (possibly stretched) y: per wavenumber, the remaining
+//      tridiagonal system in FP64 (partitioned Thomas with factors precomputed
+//      per eigenvalue; the singular zero mode pinned and shifted to zero mean).
+//      Periodic y is uniform and its operator circulant: a complex DFT along y
+//      of slot pairs, division by the eigenvalue sum, inverse DFT, all in one
+//      kernel in the field precision; the zero mode is set to zero (zero mean).
 //   inverse z, inverse x.
 //
 // FFTs: mixed-radix (2, 3, 4, 5, 7, 11, 13) Stockham autosort in shared memory,
@@ -18,6 +21,7 @@
 // tridiagonal elimination in both modes.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "fs_internal.cuh"
@@ -616,6 +620,97 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   }
 }
 
+// ---------------------------------------------------------------------------
+// Periodic y: the columns (slot s, z position t) of the x/z spectrum are real
+// sequences along y to which the real symmetric circulant inverse
+// (A_y + Lambda_s)^-1 applies.  Two neighbouring slots (s, s+1) form one complex
+// line z = a + i b; after its DFT Z(k) = A(k) + i B(k), the solution spectrum is
+//   Z'(k) = A(k) / mu_a(k) + i B(k) / mu_b(k)
+//         = Z(k) (1/mu_a + 1/mu_b) / 2 + conj Z(-k) (1/mu_a - 1/mu_b) / 2,
+// mu(k) = lambda_y(k) + Lambda (both slots of a pair share Lambda except the
+// special slots 0 and 1 of the real-packed x spectrum and DCT slots).  1/mu is
+// taken as 0 for the one zero eigenvalue (k = 0 of the x/z zero mode), which
+// gives the zero-mean solution.
+struct YSpecArgs {
+  int nx, ny, nz, dim, xmode, nmx, spb;
+};
+
+template <typename T>
+__device__ __forceinline__ int lam_index_spec(const YSpecArgs& A, int s, int t) {
+  int mx;
+  if (A.xmode == 1) mx = s;
+  else mx = s == 0 ? 0 : (s == 1 ? A.nx / 2 : (s >> 1));
+  if (A.dim == 2) return mx;
+  const int l = (s >= 2 || A.xmode == 1) ? t : (t == 0 ? 0 : (t == 1 ? A.nz / 2 : (t >> 1)));
+  return min(l, A.nz - l) * A.nmx + mx;
+}
+
+template <typename T, int PL>
+__global__ void __launch_bounds__(256) yspec_kernel(T* __restrict__ data, const YSpecArgs A, Radices rad,
+                                                    const cplx<T>* __restrict__ tw, const T* __restrict__ lamy,
+                                                    const T* __restrict__ lamxz) {
+  extern __shared__ unsigned char smem_raw[];
+  const int N = PL >= 2 ? PL : A.ny;
+  const int P = N + 1;                          // padded line pitch
+  cplx<T>* B0 = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* B1 = B0 + (size_t)(A.spb / 2) * P;
+  const int s0 = blockIdx.x * A.spb;
+  const int t = blockIdx.y;
+  const int ns = min(A.spb, A.nx - s0);
+  const int nl = (ns + 1) / 2;
+  T* base = data + s0 + (size_t)A.nx * A.ny * t;
+  const size_t rs = (size_t)A.nx;
+  if (ns & 1)   // odd tail: the missing partner slot is zero
+    for (int j = threadIdx.x; j < N; j += blockDim.x) B0[(nl - 1) * P + j].y = T(0);
+  constexpr int KB = 8;
+  for (int e0 = threadIdx.x; e0 < ns * N; e0 += KB * blockDim.x) {
+    T v[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < ns * N) {
+        const int j = e / ns, c = e - j * ns;
+        v[q] = base[rs * j + c];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int e = e0 + q * blockDim.x;
+      if (e < ns * N) {
+        const int j = e / ns, c = e - j * ns;
+        reinterpret_cast<T*>(&B0[(c >> 1) * P + j])[c & 1] = v[q];
+      }
+    }
+  }
+  __syncthreads();
+  cplx<T>* Z = fft_any<T, PL>(B0, B1, N, P, nl, rad, tw, false);
+  const int nh = N / 2 + 1;
+  for (int e = threadIdx.x; e < nl * nh; e += blockDim.x) {
+    const int l = e / nh, k = e - l * nh;
+    const int kk = k == 0 ? 0 : N - k;
+    const int sa = s0 + 2 * l, sb = sa + 1;
+    const T La = lamxz[lam_index_spec<T>(A, sa, t)];
+    const T Lb = sb < A.nx ? lamxz[lam_index_spec<T>(A, sb, t)] : La;
+    const T ly = lamy[k];
+    const T ma = ly + La, mb = ly + Lb;
+    const T ia = ma != T(0) ? T(1) / ma : T(0);
+    const T ib = mb != T(0) ? T(1) / mb : T(0);
+    const T cp = T(0.5) * (ia + ib), cm = T(0.5) * (ia - ib);
+    cplx<T>* line = Z + l * P;
+    const cplx<T> z1 = line[k], z2 = line[kk];
+    line[k] = {cp * z1.x + cm * z2.x, cp * z1.y - cm * z2.y};
+    if (kk != k) line[kk] = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
+  }
+  __syncthreads();
+  cplx<T>* W = fft_any<T, PL>(Z, Z == B0 ? B1 : B0, N, P, nl, rad, tw, true);
+  const T inv_n = T(1) / T(N);
+  for (int e = threadIdx.x; e < ns * N; e += blockDim.x) {
+    const int j = e / ns, c = e - j * ns;
+    const cplx<T> v = W[(c >> 1) * P + j];
+    base[rs * j + c] = ((c & 1) ? v.y : v.x) * inv_n;
+  }
+}
+
 template <typename T>
 size_t fft_smem_bytes(int N, int lines) {
   return 2ull * lines * N * sizeof(cplx<T>);
@@ -635,6 +730,7 @@ Radices radices_of(const Plan1D& p) {
 }
 
 constexpr size_t kSmemBudget = 96 * 1024;
+constexpr size_t kYSpecBudget = 200 * 1024;
 
 template <typename T, int PL>
 void set_smem_attrs_plan() {
@@ -643,6 +739,7 @@ void set_smem_attrs_plan() {
   cudaFuncSetAttribute(xinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
 }
 
 // Kernel instances by plan: compile-time lengths first, generic plans otherwise.
@@ -651,15 +748,17 @@ struct FftKernels {
   using XF = void (*)(T*, int, int, int, int, Radices, const cplx<T>*, const cplx<T>*, const DivArgs<T>);
   using XI = void (*)(T*, int, int, int, int, Radices, const cplx<T>*, const cplx<T>*);
   using ZK = void (*)(T*, int, int, int, int, Radices, const cplx<T>*);
+  using YK = void (*)(T*, const YSpecArgs, Radices, const cplx<T>*, const T*, const T*);
   XF xfwd, xfwd_div;
   XI xinv;
   ZK zfwd, zinv;
+  YK yspec;
 };
 
 template <typename T, int PL>
 FftKernels<T> fft_kernels_of() {
   return {xfwd_kernel<T, PL, false>, xfwd_kernel<T, PL, true>, xinv_kernel<T, PL>, zfwd_kernel<T, PL>,
-          zinv_kernel<T, PL>};
+          zinv_kernel<T, PL>, yspec_kernel<T, PL>};
 }
 
 template <typename T>
@@ -733,7 +832,25 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
-  {
+  if (G->yspec) {
+    YSpecArgs A;
+    A.nx = nx;
+    A.ny = ny;
+    A.nz = nz;
+    A.dim = G->dim;
+    A.xmode = G->xmode;
+    A.nmx = G->nmx;
+    // slots per block: an even count whose two ping-pong buffers fit the budget
+    const size_t line_bytes = 2ull * (ny + 1) * sizeof(cplx<T>);
+    int spb = 2 * (int)std::min<size_t>(16, kYSpecBudget / line_bytes);
+    if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
+    A.spb = spb;
+    dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);
+    auto k = fft_kernels<T>(G->py).yspec;
+    FS_LAUNCH(G, "fft_y_solve", k<<<grid, 256, (size_t)(spb / 2) * line_bytes, G->stream>>>(
+                                    data, A, radices_of(G->py), (const cplx<T>*)G->py.tw, (const T*)G->lamy,
+                                    (const T*)G->lamxz));
+  } else {
     YArgs A;
     A.nx = nx;
     A.ny = ny;
