@@ -49,6 +49,8 @@ struct Radices {
 
 namespace {
 
+constexpr int kMaxLines = 16;   // complex lines per FFT block (upper bound; the compile-time lengths use exactly this)
+
 // One Stockham stage with compile-time radix R over `nlines` lines of length N.
 // NC, NSC: compile-time line length and sub-transform size (0: the runtime values).
 template <typename T, int R, int NC = 0, int NSC = 0>
@@ -205,6 +207,16 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int Nrt
   cplx<T>* B = A + (size_t)lpb * N;
   const int line0 = blockIdx.x * lpb;
   const int nl = min(lpb, (rows + 1) / 2 - line0);
+  // (j, k) of the block's rows, formed once (rows r = j + ny k)
+  __shared__ int rowj[2 * kMaxLines], rowk[2 * kMaxLines];
+  if constexpr (DIV) {
+    if (threadIdx.x < 2 * nl) {
+      const int r = 2 * line0 + threadIdx.x;
+      rowk[threadIdx.x] = r / dv.g.ny;
+      rowj[threadIdx.x] = r - rowk[threadIdx.x] * dv.g.ny;
+    }
+    __syncthreads();
+  }
   // loads are batched (KB elements per thread in flight) before the shared-memory stores
   constexpr int KB = 4;
   for (int t0 = threadIdx.x; t0 < nl * N; t0 += KB * blockDim.x) {
@@ -217,9 +229,8 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int Nrt
         const int l = t / N, i = t - l * N;
         const int r0 = 2 * (line0 + l), r1 = r0 + 1;
         if constexpr (DIV) {
-          const int ny = dv.g.ny;
-          va[q] = div_at(dv, i, r0 % ny, r0 / ny);
-          if (r1 < rows) vb[q] = div_at(dv, i, r1 % ny, r1 / ny);
+          va[q] = div_at(dv, i, rowj[2 * l], rowk[2 * l]);
+          if (r1 < rows) vb[q] = div_at(dv, i, rowj[2 * l + 1], rowk[2 * l + 1]);
         } else {
           va[q] = data[(size_t)r0 * N + i];
           if (r1 < rows) vb[q] = data[(size_t)r1 * N + i];
@@ -352,31 +363,45 @@ __global__ void __launch_bounds__(256) zfwd_kernel(T* __restrict__ data, int nx,
   const int np = min(ppb, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;
-  constexpr int KB = 8;
-  for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
-    T v[KB];
+  if constexpr (PL >= 2) {
+    // ppb == kMaxLines: thread = (slot sl of the block's 32, z row k0 + 8 q)
+    const int sl = threadIdx.x & 31, k0 = threadIdx.x >> 5;
+    const bool act = sl < 2 * np;
+    constexpr int NQ = PL / 8;
+    T v[NQ];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = t0 + q * blockDim.x;
-      v[q] = T(0);
-      if (t < 2 * np * N) {
-        const int k = t / (2 * np), sl = t - k * (2 * np);
-        v[q] = base[plane * k + sl];
+    for (int q = 0; q < NQ; ++q) v[q] = act ? base[plane * (k0 + 8 * q) + sl] : T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) reinterpret_cast<T*>(&A[(sl >> 1) * P + k0 + 8 * q])[sl & 1] = v[q];
+  } else {
+    constexpr int KB = 8;
+    for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int t = t0 + q * blockDim.x;
+        v[q] = T(0);
+        if (t < 2 * np * N) {
+          const int k = t / (2 * np), sl = t - k * (2 * np);
+          v[q] = base[plane * k + sl];
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = t0 + q * blockDim.x;
-      if (t < 2 * np * N) {
-        const int k = t / (2 * np), sl = t - k * (2 * np);
-        reinterpret_cast<T*>(&A[(sl >> 1) * P + k])[sl & 1] = v[q];
+      for (int q = 0; q < KB; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t < 2 * np * N) {
+          const int k = t / (2 * np), sl = t - k * (2 * np);
+          reinterpret_cast<T*>(&A[(sl >> 1) * P + k])[sl & 1] = v[q];
+        }
       }
     }
   }
   __syncthreads();
   cplx<T>* Z = fft_any<T, PL>(A, B, N, P, np, rad, tw, false);
-  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
-    const int p = t / (2 * np), sl = t - p * (2 * np);
+  const int tstride = PL >= 2 ? 32 : 2 * np;   // PL >= 2: the thread's slot is fixed
+  for (int t = threadIdx.x; t < tstride * N; t += blockDim.x) {
+    const int p = t / tstride, sl = t - p * tstride;
+    if (sl >= 2 * np) continue;
     const int line = sl >> 1;
     const int m = pair0 + line;
     T out;
@@ -408,24 +433,38 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
   const int np = min(ppb, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;
-  constexpr int KB = 8;
-  for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
-    T v[KB];
+  // pair 0 (first block only) arrives as two real-packed spectra and is rebuilt
+  // below; every other line is loaded straight into A
+  cplx<T>* dst = pair0 == 0 ? B : A;
+  if constexpr (PL >= 2) {
+    const int sl = threadIdx.x & 31, k0 = threadIdx.x >> 5;
+    const bool act = sl < 2 * np;
+    constexpr int NQ = PL / 8;
+    T v[NQ];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = t0 + q * blockDim.x;
-      v[q] = T(0);
-      if (t < 2 * np * N) {
-        const int k = t / (2 * np), sl = t - k * (2 * np);
-        v[q] = base[plane * k + sl];
+    for (int q = 0; q < NQ; ++q) v[q] = act ? base[plane * (k0 + 8 * q) + sl] : T(0);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) reinterpret_cast<T*>(&dst[(sl >> 1) * P + k0 + 8 * q])[sl & 1] = v[q];
+  } else {
+    constexpr int KB = 8;
+    for (int t0 = threadIdx.x; t0 < 2 * np * N; t0 += KB * blockDim.x) {
+      T v[KB];
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int t = t0 + q * blockDim.x;
+        v[q] = T(0);
+        if (t < 2 * np * N) {
+          const int k = t / (2 * np), sl = t - k * (2 * np);
+          v[q] = base[plane * k + sl];
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = t0 + q * blockDim.x;
-      if (t < 2 * np * N) {
-        const int k = t / (2 * np), sl = t - k * (2 * np);
-        reinterpret_cast<T*>(&B[(sl >> 1) * P + k])[sl & 1] = v[q];
+      for (int q = 0; q < KB; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t < 2 * np * N) {
+          const int k = t / (2 * np), sl = t - k * (2 * np);
+          reinterpret_cast<T*>(&dst[(sl >> 1) * P + k])[sl & 1] = v[q];
+        }
       }
     }
   }
@@ -434,7 +473,7 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
     const int line = t / N, l = t - line * N;
     const int m = pair0 + line;
     if (m > 0) {
-      A[line * P + l] = B[line * P + l];
+      if (pair0 == 0) A[line * P + l] = B[line * P + l];
     } else {
       // rebuild Z = Y0 + i Y1 from the two real-packed spectra held in .x (slot 0) and .y (slot 1)
       cplx<T> y0, y1;
@@ -449,10 +488,22 @@ __global__ void __launch_bounds__(256) zinv_kernel(T* __restrict__ data, int nx,
   __syncthreads();
   cplx<T>* z = fft_any<T, PL>(A, B, N, P, np, rad, tw, true);
   const T inv_n = T(1) / T(N);
-  for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
-    const int k = t / (2 * np), sl = t - k * (2 * np);
-    const cplx<T> v = z[(sl >> 1) * P + k];
-    base[plane * k + sl] = ((sl & 1) ? v.y : v.x) * inv_n;
+  if constexpr (PL >= 2) {
+    const int sl = threadIdx.x & 31, k0 = threadIdx.x >> 5;
+    if (sl < 2 * np) {
+#pragma unroll 4
+      for (int q = 0; q < PL / 8; ++q) {
+        const int k = k0 + 8 * q;
+        const cplx<T> v = z[(sl >> 1) * P + k];
+        base[plane * k + sl] = ((sl & 1) ? v.y : v.x) * inv_n;
+      }
+    }
+  } else {
+    for (int t = threadIdx.x; t < 2 * np * N; t += blockDim.x) {
+      const int k = t / (2 * np), sl = t - k * (2 * np);
+      const cplx<T> v = z[(sl >> 1) * P + k];
+      base[plane * k + sl] = ((sl & 1) ? v.y : v.x) * inv_n;
+    }
   }
 }
 
@@ -662,23 +713,36 @@ __global__ void __launch_bounds__(256) yspec_kernel(T* __restrict__ data, const 
   const size_t rs = (size_t)A.nx;
   if (ns & 1)   // odd tail: the missing partner slot is zero
     for (int j = threadIdx.x; j < N; j += blockDim.x) B0[(nl - 1) * P + j].y = T(0);
-  constexpr int KB = 8;
-  for (int e0 = threadIdx.x; e0 < ns * N; e0 += KB * blockDim.x) {
-    T v[KB];
+  if constexpr (PL >= 2) {
+    // spb == 32: thread = (slot c, rows j0 + 8 q)
+    const int c = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+    if (c < ns) {
+      constexpr int NQ = PL / 8;
+      T v[NQ];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < ns * N) {
-        const int j = e / ns, c = e - j * ns;
-        v[q] = base[rs * j + c];
-      }
+      for (int q = 0; q < NQ; ++q) v[q] = base[rs * (j0 + 8 * q) + c];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) reinterpret_cast<T*>(&B0[(c >> 1) * P + j0 + 8 * q])[c & 1] = v[q];
     }
+  } else {
+    constexpr int KB = 8;
+    for (int e0 = threadIdx.x; e0 < ns * N; e0 += KB * blockDim.x) {
+      T v[KB];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int e = e0 + q * blockDim.x;
-      if (e < ns * N) {
-        const int j = e / ns, c = e - j * ns;
-        reinterpret_cast<T*>(&B0[(c >> 1) * P + j])[c & 1] = v[q];
+      for (int q = 0; q < KB; ++q) {
+        const int e = e0 + q * blockDim.x;
+        if (e < ns * N) {
+          const int j = e / ns, c = e - j * ns;
+          v[q] = base[rs * j + c];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < KB; ++q) {
+        const int e = e0 + q * blockDim.x;
+        if (e < ns * N) {
+          const int j = e / ns, c = e - j * ns;
+          reinterpret_cast<T*>(&B0[(c >> 1) * P + j])[c & 1] = v[q];
+        }
       }
     }
   }
@@ -704,10 +768,22 @@ __global__ void __launch_bounds__(256) yspec_kernel(T* __restrict__ data, const 
   __syncthreads();
   cplx<T>* W = fft_any<T, PL>(Z, Z == B0 ? B1 : B0, N, P, nl, rad, tw, true);
   const T inv_n = T(1) / T(N);
-  for (int e = threadIdx.x; e < ns * N; e += blockDim.x) {
-    const int j = e / ns, c = e - j * ns;
-    const cplx<T> v = W[(c >> 1) * P + j];
-    base[rs * j + c] = ((c & 1) ? v.y : v.x) * inv_n;
+  if constexpr (PL >= 2) {
+    const int c = threadIdx.x & 31, j0 = threadIdx.x >> 5;
+    if (c < ns) {
+#pragma unroll 4
+      for (int q = 0; q < PL / 8; ++q) {
+        const int j = j0 + 8 * q;
+        const cplx<T> v = W[(c >> 1) * P + j];
+        base[rs * j + c] = ((c & 1) ? v.y : v.x) * inv_n;
+      }
+    }
+  } else {
+    for (int e = threadIdx.x; e < ns * N; e += blockDim.x) {
+      const int j = e / ns, c = e - j * ns;
+      const cplx<T> v = W[(c >> 1) * P + j];
+      base[rs * j + c] = ((c & 1) ? v.y : v.x) * inv_n;
+    }
   }
 }
 
@@ -730,15 +806,17 @@ Radices radices_of(const Plan1D& p) {
 }
 
 constexpr size_t kSmemBudget = 96 * 1024;
+constexpr size_t kFixedBudget = 200 * 1024;   // compile-time-length kernels always take kMaxLines lines
 constexpr size_t kYSpecBudget = 200 * 1024;
 
 template <typename T, int PL>
 void set_smem_attrs_plan() {
+  const int zb = (int)(PL >= 2 ? kFixedBudget : kSmemBudget);
   cudaFuncSetAttribute(xfwd_kernel<T, PL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(xfwd_kernel<T, PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
   cudaFuncSetAttribute(xinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
+  cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
 }
 
@@ -760,6 +838,8 @@ FftKernels<T> fft_kernels_of() {
   return {xfwd_kernel<T, PL, false>, xfwd_kernel<T, PL, true>, xinv_kernel<T, PL>, zfwd_kernel<T, PL>,
           zinv_kernel<T, PL>, yspec_kernel<T, PL>};
 }
+
+bool is_fixed_length(int n) { return n == 64 || n == 128 || n == 192 || n == 256; }
 
 template <typename T>
 FftKernels<T> fft_kernels(const Plan1D& p) {
@@ -823,10 +903,14 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   }
   int ppb = 0;
   if (G->dim == 3) {
-    ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
-    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
-    ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
-    if (ppb > nx / 2) ppb = nx / 2;
+    if (is_fixed_length(G->pz.n)) {
+      ppb = kMaxLines;   // the compile-time-length z kernels map 32 slots x 8 rows onto 256 threads
+    } else {
+      ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
+      const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : kMaxLines;
+      ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
+      if (ppb > nx / 2) ppb = nx / 2;
+    }
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
     auto k = fft_kernels<T>(G->pz).zfwd;
     FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
@@ -842,8 +926,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.nmx = G->nmx;
     // slots per block: an even count whose two ping-pong buffers fit the budget
     const size_t line_bytes = 2ull * (ny + 1) * sizeof(cplx<T>);
-    int spb = 2 * (int)std::min<size_t>(16, kYSpecBudget / line_bytes);
-    if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
+    int spb = 2 * (int)std::min<size_t>(kMaxLines, kYSpecBudget / line_bytes);
+    if (is_fixed_length(ny)) spb = 2 * kMaxLines;   // compile-time lengths map 32 slots x 8 rows onto 256 threads
+    else if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
     A.spb = spb;
     dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);
     auto k = fft_kernels<T>(G->py).yspec;
