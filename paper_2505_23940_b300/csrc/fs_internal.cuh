@@ -96,7 +96,30 @@ struct DivArgs {
   double omega, cx, cy;
   const double* xf;
   const double* yf;
+  int vec4;                  // 1: periodic x, nx % 4 == 0, no IB: rows read four faces at a time
 };
+
+// Four consecutive values of a row whose start is 16-byte (float) / 32-byte (double) aligned.
+template <typename T>
+struct Vec4 {
+  T v[4];
+};
+__device__ __forceinline__ Vec4<float> ld4(const float* __restrict__ p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return {{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Vec4<double> ld4(const double* __restrict__ p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const Vec4<float>& a) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.v[0], a.v[1], a.v[2], a.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const Vec4<double>& a) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a.v[0], a.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(a.v[2], a.v[3]);
+}
 
 // (1 - eps) u* + eps u_c on face t of component c: forced faces take the exact
 // solid velocity u_c (Eq. 9), the others u*.
@@ -140,6 +163,41 @@ __device__ __forceinline__ T div_at(const DivArgs<T>& A, int i, int j, int k) {
     const int b0 = i + g.nx * j;
     const int pl = g.nx * g.ny;
     s += (__ldg(A.u[2] + b0 + pl * kp) - __ldg(A.u[2] + b0 + pl * k)) * g.ihz;
+  }
+  return s;
+}
+
+// D u* at cells (i0 .. i0+3, j, k) for vec4 grids (periodic x, no IB).
+template <typename T>
+__device__ __forceinline__ Vec4<T> div4_at(const DivArgs<T>& A, int i0, int j, int k) {
+  const Geom<T>& g = A.g;
+  const int nx = g.nx;
+  Vec4<T> s;
+  {
+    const T* row = A.u[0] + (size_t)nx * (j + g.ny * k);
+    const Vec4<T> a = ld4(row + i0);
+    const T e = __ldg(row + (i0 + 4 < nx ? i0 + 4 : 0));
+    s.v[0] = (a.v[1] - a.v[0]) * g.ihx;
+    s.v[1] = (a.v[2] - a.v[1]) * g.ihx;
+    s.v[2] = (a.v[3] - a.v[2]) * g.ihx;
+    s.v[3] = (e - a.v[3]) * g.ihx;
+  }
+  {
+    const int ey = g.ext(1, 1);
+    const int jp = (j + 1 < ey) ? j + 1 : 0;
+    const T* pl = A.u[1] + (size_t)nx * ey * k + i0;
+    const Vec4<T> a = ld4(pl + (size_t)nx * j), b = ld4(pl + (size_t)nx * jp);
+    const T ih = g.ihy[j];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s.v[e] += (b.v[e] - a.v[e]) * ih;
+  }
+  if (g.dim == 3) {
+    const int kp = (k + 1 < g.nz) ? k + 1 : 0;
+    const size_t plane = (size_t)nx * g.ny;
+    const T* col = A.u[2] + (size_t)nx * j + i0;
+    const Vec4<T> a = ld4(col + plane * k), b = ld4(col + plane * kp);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s.v[e] += (b.v[e] - a.v[e]) * g.ihz;
   }
   return s;
 }

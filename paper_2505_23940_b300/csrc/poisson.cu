@@ -217,9 +217,25 @@ __global__ void __launch_bounds__(256) xfwd_kernel(T* __restrict__ data, int Nrt
     }
     __syncthreads();
   }
+  bool done = false;
+  if constexpr (DIV && PL >= 2 && PL % 4 == 0) {
+    if (dv.vec4 && mode == 0) {
+      // four cells per thread: row-vector loads of u*, v*, w*
+      constexpr int NQ = PL / 4;
+      for (int Q = threadIdx.x; Q < nl * NQ; Q += blockDim.x) {
+        const int l = Q / NQ, i0 = 4 * (Q - l * NQ);
+        const Vec4<T> da = div4_at(dv, i0, rowj[2 * l], rowk[2 * l]);
+        Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
+        if (2 * (line0 + l) + 1 < rows) db = div4_at(dv, i0, rowj[2 * l + 1], rowk[2 * l + 1]);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) A[l * N + i0 + e] = {da.v[e], db.v[e]};
+      }
+      done = true;
+    }
+  }
   // loads are batched (KB elements per thread in flight) before the shared-memory stores
   constexpr int KB = 4;
-  for (int t0 = threadIdx.x; t0 < nl * N; t0 += KB * blockDim.x) {
+  for (int t0 = threadIdx.x; !done && t0 < nl * N; t0 += KB * blockDim.x) {
     T va[KB], vb[KB];
 #pragma unroll
     for (int q = 0; q < KB; ++q) {

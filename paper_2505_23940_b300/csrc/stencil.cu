@@ -44,6 +44,7 @@ struct PredArgs {
   const double* xf;
   const double* yf;
   const double* oscale;
+  T ihy0;                    // 1 / h_y of a uniform periodic y (predictor3_kernel<T, true>)
 };
 
 // Velocity access around the face (i, j, k) with every boundary rule (ldv).
@@ -246,6 +247,122 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(const PredArgs<T> A
   }
 }
 
+// The same predictor for the common 3-D case -- x and z periodic, central
+// convection, no immersed body -- with the 27 distinct neighbour values of a
+// cell loaded once and shared by its three faces.  YPER: y periodic (uniform
+// metrics); otherwise y has walls and stretched metrics, and the rows whose
+// stencil reaches a wall (j < 2 or j > ny - 2; warp-uniform since blocks are at
+// least 32 wide in x) take the general path.  Arithmetic follows momentum_rhs.
+template <typename T, bool YPER>
+__global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i >= A.X || j >= A.Y) return;
+  const Geom<T>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (!YPER && (j < 2 || j > ny - 2)) {
+    const AccGhost<T> U{&g, A.uin, i, j, k};
+    predict_face<T, 0>(A, U, i, j, k);
+    predict_face<T, 1>(A, U, i, j, k);
+    predict_face<T, 2>(A, U, i, j, k);
+    return;
+  }
+  const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
+  const int km = k > 0 ? k - 1 : nz - 1, kp = k < nz - 1 ? k + 1 : 0;
+  const int jm = YPER ? (j > 0 ? j - 1 : ny - 1) : j - 1;
+  const int jp = YPER ? (j < ny - 1 ? j + 1 : 0) : j + 1;
+  const int eyv = YPER ? ny : ny + 1;
+  // row offsets of u, w (ny rows per plane) and v (eyv rows per plane)
+  const int r00 = nx * (j + ny * k), rm0 = nx * (jm + ny * k), rp0 = nx * (jp + ny * k);
+  const int r0m = nx * (j + ny * km), r0p = nx * (j + ny * kp), rmp = nx * (jm + ny * kp);
+  const int v00 = nx * (j + eyv * k), vm0 = nx * (jm + eyv * k), vp0 = nx * (jp + eyv * k);
+  const int v0m = nx * (j + eyv * km), v0p = nx * (j + eyv * kp), vpm = nx * (jp + eyv * km);
+  const T* __restrict__ U = A.uin[0];
+  const T* __restrict__ V = A.uin[1];
+  const T* __restrict__ W = A.uin[2];
+  const T u000 = __ldg(U + r00 + i), uM00 = __ldg(U + r00 + im), uP00 = __ldg(U + r00 + ip);
+  const T u0M0 = __ldg(U + rm0 + i), u0P0 = __ldg(U + rp0 + i), u00M = __ldg(U + r0m + i), u00P = __ldg(U + r0p + i);
+  const T uPM0 = __ldg(U + rm0 + ip), uP0M = __ldg(U + r0m + ip);
+  const T v000 = __ldg(V + v00 + i), vM00 = __ldg(V + v00 + im), vP00 = __ldg(V + v00 + ip);
+  const T v0M0 = __ldg(V + vm0 + i), v0P0 = __ldg(V + vp0 + i), v00M = __ldg(V + v0m + i), v00P = __ldg(V + v0p + i);
+  const T vMP0 = __ldg(V + vp0 + im), v0PM = __ldg(V + vpm + i);
+  const T w000 = __ldg(W + r00 + i), wM00 = __ldg(W + r00 + im), wP00 = __ldg(W + r00 + ip);
+  const T w0M0 = __ldg(W + rm0 + i), w0P0 = __ldg(W + rp0 + i), w00M = __ldg(W + r0m + i), w00P = __ldg(W + r0p + i);
+  const T wM0P = __ldg(W + r0p + im), w0MP = __ldg(W + rmp + i);
+  const T h = T(0.5);
+  const T ihx = g.ihx, ihz = g.ihz;
+  // y metrics at rows j (cells and faces)
+  T ihyj, ihyjm, ihfj, ihfjp, thj, thjp;
+  if (YPER) {
+    ihyj = ihyjm = ihfj = ihfjp = A.ihy0;
+    thj = thjp = h;
+  } else {
+    ihyj = g.ihy[j];
+    ihyjm = g.ihy[j - 1];
+    ihfj = g.ihfy[j];
+    ihfjp = g.ihfy[j + 1];
+    thj = g.thy[j];
+    thjp = g.thy[j + 1];
+  }
+  T Ru, Rv, Rw;
+  {  // u on the x-face (i, j, k)
+    const T TE = h * (u000 + uP00), TW = h * (uM00 + u000);
+    T cv = (TE * TE - TW * TW) * ihx;
+    T df = ((uP00 - u000) * ihx - (u000 - uM00) * ihx) * ihx;
+    const T TN = h * (vMP0 + v0P0), TS = h * (vM00 + v000);
+    const T QN = (T(1) - thjp) * u000 + thjp * u0P0, QS = (T(1) - thj) * u0M0 + thj * u000;
+    cv += (TN * QN - TS * QS) * ihyj;
+    df += ((u0P0 - u000) * ihfjp - (u000 - u0M0) * ihfj) * ihyj;
+    const T TT = h * (wM0P + w00P), TB = h * (wM00 + w000);
+    const T QT = h * (u000 + u00P), QB = h * (u00M + u000);
+    cv += (TT * QT - TB * QB) * ihz;
+    df += ((u00P - u000) * ihz - (u000 - u00M) * ihz) * ihz;
+    Ru = -cv + g.nu * df;
+    if (g.bforce) Ru += g.bforce[j];
+  }
+  {  // v on the y-face (i, j, k)
+    const T TE = h * (v000 + v0P0), TW = h * (v0M0 + v000);
+    T cv = (TE * TE - TW * TW) * ihfj;
+    T df = ((v0P0 - v000) * ihyj - (v000 - v0M0) * ihyjm) * ihfj;
+    const T TN = (T(1) - thj) * uPM0 + thj * uP00, TS = (T(1) - thj) * u0M0 + thj * u000;
+    const T QN = h * (v000 + vP00), QS = h * (vM00 + v000);
+    cv += (TN * QN - TS * QS) * ihx;
+    df += ((vP00 - v000) * ihx - (v000 - vM00) * ihx) * ihx;
+    const T TT = (T(1) - thj) * w0MP + thj * w00P, TB = (T(1) - thj) * w0M0 + thj * w000;
+    const T QT = h * (v000 + v00P), QB = h * (v00M + v000);
+    cv += (TT * QT - TB * QB) * ihz;
+    df += ((v00P - v000) * ihz - (v000 - v00M) * ihz) * ihz;
+    Rv = -cv + g.nu * df;
+  }
+  {  // w on the z-face (i, j, k)
+    const T TE = h * (w000 + w00P), TW = h * (w00M + w000);
+    T cv = (TE * TE - TW * TW) * ihz;
+    T df = ((w00P - w000) * ihz - (w000 - w00M) * ihz) * ihz;
+    const T TN = h * (uP0M + uP00), TS = h * (u00M + u000);
+    const T QN = h * (w000 + wP00), QS = h * (wM00 + w000);
+    cv += (TN * QN - TS * QS) * ihx;
+    df += ((wP00 - w000) * ihx - (w000 - wM00) * ihx) * ihx;
+    const T TT = h * (v0PM + v0P0), TB = h * (v00M + v000);
+    const T QT = (T(1) - thjp) * w000 + thjp * w0P0, QB = (T(1) - thj) * w0M0 + thj * w000;
+    cv += (TT * QT - TB * QB) * ihyj;
+    df += ((w0P0 - w000) * ihfjp - (w000 - w0M0) * ihfj) * ihyj;
+    Rw = -cv + g.nu * df;
+  }
+  const T a = A.a, b = A.b, dt = A.dt;
+  T ou = b * (u000 + dt * Ru), ov = b * (v000 + dt * Rv), ow = b * (w000 + dt * Rw);
+  if (a != T(0)) {
+    ou += a * A.un[0][r00 + i];
+    ov += a * A.un[1][v00 + i];
+    ow += a * A.un[2][r00 + i];
+  }
+  if (j < ny) {
+    A.out[0][r00 + i] = ou;
+    A.out[2][r00 + i] = ow;
+  }
+  A.out[1][v00 + i] = ov;
+}
+
 template <typename T>
 __global__ void outflow_scale_kernel(const T* __restrict__ u0, int ex, int ny, int nz, const double* __restrict__ hy,
                                      double hz, double q_in, double* scale) {
@@ -316,6 +433,52 @@ __global__ void __launch_bounds__(kThreads) correct_kernel(const CorrArgs<T> A) 
   correct_face<T, 0>(A, i, j, k, phi0);
   correct_face<T, 1>(A, i, j, k, phi0);
   if (g.dim == 3) correct_face<T, 2>(A, i, j, k, phi0);
+}
+
+// Eq. (10) for grids with periodic x and nx % 4 == 0: four cells per thread,
+// row-vector loads and stores (y faces on walls keep their imposed value).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) correct4_kernel(const CorrArgs<T> A) {
+  const Geom<T>& g = A.g;
+  const int nx = g.nx, ny = g.ny;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i0 >= nx || j >= A.Y) return;
+  const bool cell = j < ny;
+  const size_t rowc = (size_t)nx * (j + (size_t)ny * k);
+  Vec4<T> p0 = {{T(0), T(0), T(0), T(0)}};
+  if (cell) {
+    p0 = ld4(A.phi + rowc + i0);
+    const T pm = __ldg(A.phi + rowc + (i0 > 0 ? i0 - 1 : nx - 1));
+    Vec4<T> a = ld4(A.us[0] + rowc + i0);
+    a.v[0] -= (p0.v[0] - pm) * g.ihx;
+    a.v[1] -= (p0.v[1] - p0.v[0]) * g.ihx;
+    a.v[2] -= (p0.v[2] - p0.v[1]) * g.ihx;
+    a.v[3] -= (p0.v[3] - p0.v[2]) * g.ihx;
+    st4(A.un[0] + rowc + i0, a);
+  }
+  {
+    const int ey = g.ext(1, 1);
+    const size_t t = (size_t)nx * (j + (size_t)ey * k) + i0;
+    Vec4<T> a = ld4(A.us[1] + t);
+    if (g.per[1] || (j > 0 && j < ny)) {
+      const int jm = j > 0 ? j - 1 : ny - 1;
+      const Vec4<T> pm = ld4(A.phi + (size_t)nx * (jm + (size_t)ny * k) + i0);
+      const T ih = g.ihfy[j];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a.v[e] -= (p0.v[e] - pm.v[e]) * ih;
+    }
+    st4(A.un[1] + t, a);
+  }
+  if (g.dim == 3 && cell) {
+    const int km = k > 0 ? k - 1 : g.nz - 1;
+    const Vec4<T> pm = ld4(A.phi + (size_t)nx * (j + (size_t)ny * km) + i0);
+    Vec4<T> a = ld4(A.us[2] + rowc + i0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) a.v[e] -= (p0.v[e] - pm.v[e]) * g.ihz;
+    st4(A.un[2] + rowc + i0, a);
+  }
 }
 
 template <typename T>
@@ -438,8 +601,16 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   A.xf = G->xf64[0];
   A.yf = G->xf64[1];
   A.oscale = G->scal;
+  A.ihy0 = (T)(1.0 / G->h[1][0]);
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
+  if (G->dim == 3 && G->per[0] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body && G->ny >= 4) {
+    if (G->per[1])
+      FS_LAUNCH(G, "predictor", predictor3_kernel<T, true><<<grd, blk, 0, G->stream>>>(A));
+    else
+      FS_LAUNCH(G, "predictor", predictor3_kernel<T, false><<<grd, blk, 0, G->stream>>>(A));
+    return;
+  }
   FS_LAUNCH(G, "predictor", predictor_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
@@ -470,6 +641,9 @@ DivArgs<T> make_div_args(fs_grid* G, T* const* u, const double* body_state) {
   A.cy = G->ib.centre[1];
   A.xf = G->xf64[0];
   A.yf = G->xf64[1];
+  A.vec4 = (G->per[0] && G->nx % 4 == 0 && !G->has_body) ? 1 : 0;
+  for (int c = 0; c < G->dim; ++c)
+    if ((uintptr_t)u[c] % (4 * sizeof(T))) A.vec4 = 0;
   return A;
 }
 
@@ -492,6 +666,15 @@ void launch_correct(fs_grid* G, T* const* ustar, const T* phi, T* const* unew) {
   A.phi = phi;
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
+  bool vec = G->per[0] && G->nx % 4 == 0 && (uintptr_t)phi % (4 * sizeof(T)) == 0;
+  for (int c = 0; c < G->dim; ++c)
+    vec = vec && (uintptr_t)ustar[c] % (4 * sizeof(T)) == 0 && (uintptr_t)unew[c] % (4 * sizeof(T)) == 0;
+  if (vec) {
+    const dim3 blk(32, 8);
+    const dim3 grd((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, G->nz);
+    FS_LAUNCH(G, "correct", correct4_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+    return;
+  }
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
   FS_LAUNCH(G, "correct", correct_kernel<T><<<grd, blk, 0, G->stream>>>(A));
