@@ -1,0 +1,602 @@
+// Register-resident FFT kernels for the transform lengths 64, 128 and 256
+// (included by poisson.cu inside its anonymous namespace; uses cplx, cmul,
+// DivArgs, div_at, div4_at, YSpecArgs and lam_index_spec from there).
+//
+// A line of N = R1 * TPL complex values is transformed by TPL threads in two
+// passes with one warp-level exchange through shared memory (the four-step
+// decomposition n = t + TPL m, k = q + R1 s):
+//   pass 1: thread t takes x[t + TPL m], m < R1, forms the R1-point DFT over m
+//           and multiplies entry q by W_N^{t q};
+//   pass 2: for each q, the TPL-point DFT over t gives X[q + R1 s], s < TPL.
+// The small DFTs (4, 8, 16 points) are straight-line code with constant
+// twiddles.  Lines live in shared memory with one pad element every R1 entries
+// so that both passes are free of bank conflicts.  Each block holds kRegLines
+// lines; kRegLines * TPL of its threads run the transform (a line never spans
+// two warps, so the exchange needs only __syncwarp) and all kRegBlock threads
+// move data, as whole slot pairs or row vectors, so that more loads are in
+// flight than the transform threads alone could issue.
+#pragma once
+
+template <int N>
+struct RegPlan;
+template <>
+struct RegPlan<64> {
+  static constexpr int R1 = 8, TPL = 8;
+};
+template <>
+struct RegPlan<128> {
+  static constexpr int R1 = 16, TPL = 8;
+};
+template <>
+struct RegPlan<256> {
+  static constexpr int R1 = 16, TPL = 16;
+};
+
+constexpr int kRegLines = 16;
+constexpr int kRegBlock = 256;
+
+// Line pitch: the padded length plus one, so that the 16 lines of a block start
+// in 16 different bank pairs (2 * pitch = 2 mod 32 words up to a multiple of 16):
+// slot-pair tiles (line = slot / 2) are then written and read without conflicts.
+template <int N>
+__host__ __device__ constexpr int rpitch() {
+  return N + N / RegPlan<N>::R1 + 1;
+}
+template <int N>
+__device__ __forceinline__ int rpad(int i) {
+  return i + i / RegPlan<N>::R1;
+}
+template <int N>
+constexpr int reg_threads() {
+  return kRegLines * RegPlan<N>::TPL;
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cadd(cplx<T> a, cplx<T> b) {
+  return {a.x + b.x, a.y + b.y};
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> csub(cplx<T> a, cplx<T> b) {
+  return {a.x - b.x, a.y - b.y};
+}
+// a * (-i) for the forward transform, a * (+i) for the inverse
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> mul_mi(cplx<T> a) {
+  return INV ? cplx<T>{-a.y, a.x} : cplx<T>{a.y, -a.x};
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft4(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2, cplx<T>& a3) {
+  const cplx<T> s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  const cplx<T> s13 = cadd(a1, a3), d13 = mul_mi<T, INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// cos and sin of pi/8 and pi/4
+constexpr double kC8 = 0.92387953251128675613, kS8 = 0.38268343236508977173, kR2 = 0.70710678118654752440;
+
+// exp(-+ 2 pi i e / 16) for the products e = n2 k1 of the 16-point DFT
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> w16(int e) {
+  const T sg = INV ? T(1) : T(-1);
+  switch (e) {
+    case 1: return {T(kC8), sg * T(kS8)};
+    case 2: return {T(kR2), sg * T(kR2)};
+    case 3: return {T(kS8), sg * T(kC8)};
+    case 4: return {T(0), sg};
+    case 6: return {T(-kR2), sg * T(kR2)};
+    case 9: return {T(-kC8), -sg * T(kS8)};
+    default: return {T(1), T(0)};
+  }
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft8(cplx<T>* v) {
+  cplx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  cplx<T> o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<T, INV>(e0, e1, e2, e3);
+  dft4<T, INV>(o0, o1, o2, o3);
+  const T c = T(kR2), sg = INV ? T(1) : T(-1);
+  const cplx<T> t1 = cmul(o1, cplx<T>{c, sg * c});
+  const cplx<T> t2 = mul_mi<T, INV>(o2);
+  const cplx<T> t3 = cmul(o3, cplx<T>{-c, sg * c});
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void dft16(cplx<T>* v) {
+  cplx<T> a[4][4];   // a[n2][k1]
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    a[n2][0] = v[n2];
+    a[n2][1] = v[4 + n2];
+    a[n2][2] = v[8 + n2];
+    a[n2][3] = v[12 + n2];
+    dft4<T, INV>(a[n2][0], a[n2][1], a[n2][2], a[n2][3]);
+  }
+#pragma unroll
+  for (int n2 = 1; n2 < 4; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 4; ++k1) a[n2][k1] = cmul(a[n2][k1], w16<T, INV>(n2 * k1));
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    cplx<T> c0 = a[0][k1], c1 = a[1][k1], c2 = a[2][k1], c3 = a[3][k1];
+    dft4<T, INV>(c0, c1, c2, c3);
+    v[k1] = c0;
+    v[k1 + 4] = c1;
+    v[k1 + 8] = c2;
+    v[k1 + 12] = c3;
+  }
+}
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void dft_small(cplx<T>* v) {
+  if constexpr (R == 8) dft8<T, INV>(v);
+  else dft16<T, INV>(v);
+}
+
+// Transform the line L (padded layout) in place with the TPL threads t of its
+// group; tws holds exp(-2 pi i e / N), e < N.  Every thread of the warp calls it.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fft_reg_line(cplx<T>* L, int t, const cplx<T>* __restrict__ tws) {
+  constexpr int R1 = RegPlan<N>::R1, TPL = RegPlan<N>::TPL, G = R1 / TPL;
+  cplx<T> v[R1];
+#pragma unroll
+  for (int m = 0; m < R1; ++m) v[m] = L[rpad<N>(t + TPL * m)];
+  dft_small<T, R1, INV>(v);
+#pragma unroll
+  for (int q = 1; q < R1; ++q) {
+    cplx<T> w = tws[t * q];
+    if (INV) w.y = -w.y;
+    v[q] = cmul(v[q], w);
+  }
+#pragma unroll
+  for (int q = 0; q < R1; ++q) L[rpad<N>(t + TPL * q)] = v[q];
+  __syncwarp();
+  cplx<T> u[G][TPL];
+#pragma unroll
+  for (int c = 0; c < G; ++c)
+#pragma unroll
+    for (int tt = 0; tt < TPL; ++tt) u[c][tt] = L[rpad<N>(tt + TPL * (t * G + c))];
+  __syncwarp();
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    dft_small<T, TPL, INV>(u[c]);
+#pragma unroll
+    for (int s = 0; s < TPL; ++s) L[rpad<N>(t * G + c + R1 * s)] = u[c][s];
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void load_twiddles(cplx<T>* tws, const cplx<T>* __restrict__ tw) {
+  for (int e = threadIdx.x; e < N; e += blockDim.x) tws[e] = tw[e];
+}
+
+template <typename T, int N>
+size_t reg_smem_bytes(int extra_lines) {
+  return (size_t)((kRegLines + extra_lines) * rpitch<N>() + N) * sizeof(cplx<T>);
+}
+
+// The transform threads of the block run the line FFT of their line.
+template <typename T, int N, bool INV>
+__device__ __forceinline__ void fft_reg_block(cplx<T>* S, const cplx<T>* __restrict__ tws) {
+  constexpr int TPL = RegPlan<N>::TPL;
+  if (threadIdx.x < reg_threads<N>())
+    fft_reg_line<T, N, INV>(S + (threadIdx.x / TPL) * rpitch<N>(), threadIdx.x % TPL, tws);
+}
+
+template <typename T>
+struct Pair2;
+template <>
+struct Pair2<float> {
+  using V = float2;
+};
+template <>
+struct Pair2<double> {
+  using V = double2;
+};
+
+// Tile of 32 consecutive slots x N rows (row stride rs) <-> the 16 lines of S:
+// slot pair (2m, 2m + 1) is line m (.x, .y).  Thread = (pair m, rows r0 + 16 q);
+// pairs are read and written as one 8- (16-) byte vector.  nslots may be odd
+// (the missing partner reads as zero and is not written).
+template <typename T, int N>
+__device__ __forceinline__ void load_pair_tile(cplx<T>* S, const T* __restrict__ base, size_t rs, int nslots) {
+  constexpr int P = rpitch<N>(), NQ = N / 16;
+  const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+  if (2 * m >= nslots) return;
+  const bool whole = 2 * m + 1 < nslots;
+  using V = typename Pair2<T>::V;
+  cplx<T> v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const T* a = base + rs * (r0 + 16 * q) + 2 * m;
+    if (whole) {
+      const V w = *reinterpret_cast<const V*>(a);
+      v[q] = {w.x, w.y};
+    } else {
+      v[q] = {a[0], T(0)};
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) S[m * P + rpad<N>(r0 + 16 * q)] = v[q];
+}
+
+template <typename T, int N, typename F>
+__device__ __forceinline__ void store_pair_tile(T* __restrict__ base, size_t rs, int nslots, F&& value) {
+  constexpr int NQ = N / 16;
+  const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+  if (2 * m >= nslots) return;
+  const bool whole = 2 * m + 1 < nslots;
+  using V = typename Pair2<T>::V;
+#pragma unroll 4
+  for (int q = 0; q < NQ; ++q) {
+    const int r = r0 + 16 * q;
+    const cplx<T> o = value(m, r);
+    T* a = base + rs * r + 2 * m;
+    if (whole) {
+      V w;
+      w.x = o.x;
+      w.y = o.y;
+      *reinterpret_cast<V*>(a) = w;
+    } else {
+      a[0] = o.x;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// x forward (see xfwd_kernel): rows of length N, two rows per complex line.
+template <typename T, int N, bool DIV>
+__global__ void __launch_bounds__(kRegBlock) xfwd_reg_kernel(T* __restrict__ data, int rows, int mode,
+                                                           const cplx<T>* __restrict__ tw,
+                                                           const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
+  constexpr int P = rpitch<N>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kRegLines * P;
+  __shared__ int rowj[2 * kRegLines], rowk[2 * kRegLines];
+  const int line0 = blockIdx.x * kRegLines;
+  const int nl = min(kRegLines, (rows + 1) / 2 - line0);
+  load_twiddles<T, N>(tws, tw);
+  if constexpr (DIV) {
+    if (threadIdx.x < 2 * nl) {
+      const int r = 2 * line0 + threadIdx.x;
+      rowk[threadIdx.x] = r / dv.g.ny;
+      rowj[threadIdx.x] = r - rowk[threadIdx.x] * dv.g.ny;
+    }
+    __syncthreads();
+  }
+  bool done = false;
+  if constexpr (DIV) {
+    if (dv.vec4 && mode == 0) {
+      constexpr int NQ = N / 4;
+      constexpr int PER = kRegLines * NQ / kRegBlock;   // quads per thread
+#pragma unroll
+      for (int u = 0; u < PER; ++u) {
+        const int Q = threadIdx.x + kRegBlock * u;
+        const int l = Q / NQ, i0 = 4 * (Q - l * NQ);
+        if (l < nl) {
+          const Vec4<T> da = div4_at(dv, i0, rowj[2 * l], rowk[2 * l]);
+          Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
+          if (2 * (line0 + l) + 1 < rows) db = div4_at(dv, i0, rowj[2 * l + 1], rowk[2 * l + 1]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) S[l * P + rpad<N>(i0 + e)] = {da.v[e], db.v[e]};
+        }
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+    constexpr int KB = kRegLines * N / kRegBlock;
+    T va[KB], vb[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = threadIdx.x + q * kRegBlock;
+      const int l = t / N, i = t - l * N;
+      va[q] = vb[q] = T(0);
+      if (l < nl) {
+        const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+        if constexpr (DIV) {
+          va[q] = div_at(dv, i, rowj[2 * l], rowk[2 * l]);
+          if (r1 < rows) vb[q] = div_at(dv, i, rowj[2 * l + 1], rowk[2 * l + 1]);
+        } else {
+          va[q] = data[(size_t)r0 * N + i];
+          if (r1 < rows) vb[q] = data[(size_t)r1 * N + i];
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = threadIdx.x + q * kRegBlock;
+      const int l = t / N, i = t - l * N;
+      const int dst = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
+      S[l * P + rpad<N>(dst)] = {va[q], vb[q]};
+    }
+  }
+  __syncthreads();
+  fft_reg_block<T, N, false>(S, tws);
+  __syncthreads();
+  // real-packed (periodic) or DCT-II rows; two consecutive outputs per thread
+  constexpr int NH = N / 2;
+  for (int t = threadIdx.x; t < nl * NH; t += kRegBlock) {
+    const int l = t / NH, s0 = 2 * (t - l * NH);
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    T oa[2], ob[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = s0 + h;
+      int m;
+      bool im = false;
+      if (mode == 0) {
+        m = s == 0 ? 0 : (s == 1 ? N / 2 : s >> 1);
+        im = s >= 2 && (s & 1);
+      } else {
+        m = s;
+      }
+      const cplx<T> z = S[l * P + rpad<N>(m)], zr = S[l * P + rpad<N>(m == 0 ? 0 : N - m)];
+      const cplx<T> xa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};
+      const cplx<T> xb = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};
+      if (mode == 0) {
+        oa[h] = im ? xa.y : xa.x;
+        ob[h] = im ? xb.y : xb.x;
+      } else {
+        const cplx<T> w = dtw[m];
+        oa[h] = w.x * xa.x - w.y * xa.y;
+        ob[h] = w.x * xb.x - w.y * xb.y;
+      }
+    }
+    using V = typename Pair2<T>::V;
+    V wa, wb;
+    wa.x = oa[0];
+    wa.y = oa[1];
+    wb.x = ob[0];
+    wb.y = ob[1];
+    *reinterpret_cast<V*>(data + (size_t)r0 * N + s0) = wa;
+    if (r1 < rows) *reinterpret_cast<V*>(data + (size_t)r1 * N + s0) = wb;
+  }
+}
+
+// x inverse (see xinv_kernel)
+template <typename T, int N>
+__global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
+                                                           const cplx<T>* __restrict__ tw,
+                                                           const cplx<T>* __restrict__ dtw) {
+  constexpr int P = rpitch<N>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kRegLines * P;
+  const int line0 = blockIdx.x * kRegLines;
+  const int nl = min(kRegLines, (rows + 1) / 2 - line0);
+  load_twiddles<T, N>(tws, tw);
+  using V = typename Pair2<T>::V;
+  constexpr int KB = kRegLines * N / kRegBlock;
+  cplx<T> z[KB];
+  if (mode == 0) {
+    // Hermitian spectra from real-packed rows: slot pair (2k', 2k' + 1) read as one vector
+    V pa[KB], pb[KB];
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = threadIdx.x + q * kRegBlock;
+      const int l = t / N, k = t - l * N;
+      const int kk = 2 * k <= N ? k : N - k;
+      pa[q].x = pa[q].y = pb[q].x = pb[q].y = T(0);
+      if (l < nl) {
+        const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+        pa[q] = *reinterpret_cast<const V*>(data + (size_t)r0 * N + 2 * (2 * kk == N ? 0 : kk));
+        if (r1 < rows) pb[q] = *reinterpret_cast<const V*>(data + (size_t)r1 * N + 2 * (2 * kk == N ? 0 : kk));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = threadIdx.x + q * kRegBlock;
+      const int k = t - (t / N) * N;
+      cplx<T> xa, xb;
+      if (k == 0) {
+        xa = {pa[q].x, T(0)};
+        xb = {pb[q].x, T(0)};
+      } else if (2 * k == N) {
+        xa = {pa[q].y, T(0)};
+        xb = {pb[q].y, T(0)};
+      } else if (2 * k < N) {
+        xa = {pa[q].x, pa[q].y};
+        xb = {pb[q].x, pb[q].y};
+      } else {
+        xa = {pa[q].x, -pa[q].y};
+        xb = {pb[q].x, -pb[q].y};
+      }
+      z[q] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < KB; ++q) {
+      const int t = threadIdx.x + q * kRegBlock;
+      const int l = t / N, k = t - l * N;
+      z[q] = {T(0), T(0)};
+      if (l < nl) {
+        const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+        const T* ra = data + (size_t)r0 * N;
+        const T* rb = data + (size_t)r1 * N;
+        // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
+        const cplx<T> w = cconj(dtw[k]);
+        const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
+        const T b1 = r1 < rows ? rb[k] : T(0), b2 = (r1 < rows && k) ? rb[N - k] : T(0);
+        const cplx<T> xa = cmul(w, cplx<T>{a1, -a2});
+        const cplx<T> xb = cmul(w, cplx<T>{b1, -b2});
+        z[q] = {xa.x - xb.y, xa.y + xb.x};
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < KB; ++q) {
+    const int t = threadIdx.x + q * kRegBlock;
+    const int l = t / N, k = t - l * N;
+    S[l * P + rpad<N>(k)] = z[q];
+  }
+  __syncthreads();
+  fft_reg_block<T, N, true>(S, tws);
+  __syncthreads();
+  const T inv_n = T(1) / T(N);
+  constexpr int NH = N / 2;
+  for (int t = threadIdx.x; t < nl * NH; t += kRegBlock) {
+    const int l = t / NH, i0 = 2 * (t - l * NH);
+    const int r0 = 2 * (line0 + l), r1 = r0 + 1;
+    cplx<T> v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h;
+      const int src = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
+      v[h] = S[l * P + rpad<N>(src)];
+    }
+    V wa, wb;
+    wa.x = v[0].x * inv_n;
+    wa.y = v[1].x * inv_n;
+    wb.x = v[0].y * inv_n;
+    wb.y = v[1].y * inv_n;
+    *reinterpret_cast<V*>(data + (size_t)r0 * N + i0) = wa;
+    if (r1 < rows) *reinterpret_cast<V*>(data + (size_t)r1 * N + i0) = wb;
+  }
+}
+
+// z forward (see zfwd_kernel): complex lines of slot pairs along z at one y row.
+template <typename T, int N>
+__global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
+                                                           const cplx<T>* __restrict__ tw) {
+  constexpr int P = rpitch<N>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kRegLines * P;
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * kRegLines;
+  const int np = min(kRegLines, nx / 2 - pair0);
+  const size_t plane = (size_t)nx * ny;
+  T* base = data + (size_t)nx * j + 2 * pair0;
+  load_twiddles<T, N>(tws, tw);
+  load_pair_tile<T, N>(S, base, plane, 2 * np);
+  __syncthreads();
+  fft_reg_block<T, N, false>(S, tws);
+  __syncthreads();
+  store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int p) -> cplx<T> {
+    const cplx<T>* Z = S + line * P;
+    if (pair0 + line > 0) return Z[rpad<N>(p)];
+    // pair 0 holds two real sequences: split into two real-packed z spectra
+    const int l = p == 0 ? 0 : (p == 1 ? N / 2 : p >> 1);
+    const bool im = p >= 2 && (p & 1);
+    const cplx<T> z = Z[rpad<N>(l)], zr = Z[rpad<N>(l == 0 ? 0 : N - l)];
+    return im ? cplx<T>{T(0.5) * (z.y - zr.y), T(0.5) * (zr.x - z.x)}
+              : cplx<T>{T(0.5) * (z.x + zr.x), T(0.5) * (z.y + zr.y)};
+  });
+}
+
+// z inverse (see zinv_kernel).  Pair 0 arrives as two real-packed spectra in
+// slots 0 and 1; the first block stages that line in a scratch line and
+// rebuilds Z = Y0 + i Y1 into line 0.
+template <typename T, int N>
+__global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
+                                                           const cplx<T>* __restrict__ tw) {
+  constexpr int P = rpitch<N>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kRegLines * P;
+  cplx<T>* X = tws + N;   // scratch line (pair 0)
+  const int j = blockIdx.y;
+  const int pair0 = blockIdx.x * kRegLines;
+  const int np = min(kRegLines, nx / 2 - pair0);
+  const size_t plane = (size_t)nx * ny;
+  T* base = data + (size_t)nx * j + 2 * pair0;
+  load_twiddles<T, N>(tws, tw);
+  load_pair_tile<T, N>(S, base, plane, 2 * np);
+  __syncthreads();
+  if (pair0 == 0) {
+    for (int e = threadIdx.x; e < N; e += blockDim.x) X[rpad<N>(e)] = S[rpad<N>(e)];
+    __syncthreads();
+    for (int l = threadIdx.x; l < N; l += blockDim.x) {
+      cplx<T> y0, y1;
+      if (l == 0) {
+        const cplx<T> a = X[rpad<N>(0)];
+        y0 = {a.x, T(0)};
+        y1 = {a.y, T(0)};
+      } else if (2 * l == N) {
+        const cplx<T> a = X[rpad<N>(1)];
+        y0 = {a.x, T(0)};
+        y1 = {a.y, T(0)};
+      } else if (2 * l < N) {
+        const cplx<T> a = X[rpad<N>(2 * l)], b = X[rpad<N>(2 * l + 1)];
+        y0 = {a.x, b.x};
+        y1 = {a.y, b.y};
+      } else {
+        const int q = N - l;
+        const cplx<T> a = X[rpad<N>(2 * q)], b = X[rpad<N>(2 * q + 1)];
+        y0 = {a.x, -b.x};
+        y1 = {a.y, -b.y};
+      }
+      S[rpad<N>(l)] = {y0.x - y1.y, y0.y + y1.x};
+    }
+    __syncthreads();
+  }
+  fft_reg_block<T, N, true>(S, tws);
+  __syncthreads();
+  const T inv_n = T(1) / T(N);
+  store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int k) -> cplx<T> {
+    const cplx<T> v = S[line * P + rpad<N>(k)];
+    return {v.x * inv_n, v.y * inv_n};
+  });
+}
+
+// Periodic y (see yspec_kernel): y DFT of slot pairs, eigenvalue division, inverse DFT.
+template <typename T, int N>
+__global__ void __launch_bounds__(kRegBlock) yspec_reg_kernel(T* __restrict__ data, const YSpecArgs A,
+                                                            const cplx<T>* __restrict__ tw,
+                                                            const T* __restrict__ lamy,
+                                                            const T* __restrict__ lamxz) {
+  constexpr int P = rpitch<N>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kRegLines * P;
+  const int s0 = blockIdx.x * 32;
+  const int t = blockIdx.y;
+  const int ns = min(32, A.nx - s0);
+  const int nl = (ns + 1) / 2;
+  T* base = data + s0 + (size_t)A.nx * A.ny * t;
+  const size_t rs = (size_t)A.nx;
+  load_twiddles<T, N>(tws, tw);
+  load_pair_tile<T, N>(S, base, rs, ns);
+  __syncthreads();
+  fft_reg_block<T, N, false>(S, tws);
+  __syncthreads();
+  constexpr int NH = N / 2 + 1;
+  for (int e = threadIdx.x; e < nl * NH; e += blockDim.x) {
+    const int l = e / NH, k = e - l * NH;
+    const int kk = k == 0 ? 0 : N - k;
+    const int sa = s0 + 2 * l, sb = sa + 1;
+    const T La = lamxz[lam_index_spec<T>(A, sa, t)];
+    const T Lb = sb < A.nx ? lamxz[lam_index_spec<T>(A, sb, t)] : La;
+    const T ly = lamy[k];
+    const T ma = ly + La, mb = ly + Lb;
+    const T ia = ma != T(0) ? T(1) / ma : T(0);
+    const T ib = mb != T(0) ? T(1) / mb : T(0);
+    const T cp = T(0.5) * (ia + ib), cm = T(0.5) * (ia - ib);
+    cplx<T>* line = S + l * P;
+    const cplx<T> z1 = line[rpad<N>(k)], z2 = line[rpad<N>(kk)];
+    line[rpad<N>(k)] = {cp * z1.x + cm * z2.x, cp * z1.y - cm * z2.y};
+    if (kk != k) line[rpad<N>(kk)] = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
+  }
+  __syncthreads();
+  fft_reg_block<T, N, true>(S, tws);
+  __syncthreads();
+  const T inv_n = T(1) / T(N);
+  store_pair_tile<T, N>(base, rs, ns, [&](int line, int jj) -> cplx<T> {
+    const cplx<T> v = S[line * P + rpad<N>(jj)];
+    return {v.x * inv_n, v.y * inv_n};
+  });
+}

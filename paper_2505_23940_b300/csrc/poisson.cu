@@ -803,6 +803,8 @@ __global__ void __launch_bounds__(256) yspec_kernel(T* __restrict__ data, const 
   }
 }
 
+#include "fft_reg.cuh"
+
 template <typename T>
 size_t fft_smem_bytes(int N, int lines) {
   return 2ull * lines * N * sizeof(cplx<T>);
@@ -871,10 +873,69 @@ FftKernels<T> fft_kernels(const Plan1D& p) {
   return fft_kernels_of<T, 0>();
 }
 
+template <typename T, int N>
+void set_smem_attrs_reg() {
+  const int b = (int)reg_smem_bytes<T, N>(1);
+  cudaFuncSetAttribute(xfwd_reg_kernel<T, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(xfwd_reg_kernel<T, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(xinv_reg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(zfwd_reg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(zinv_reg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  cudaFuncSetAttribute(yspec_reg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+bool is_reg_length(int n) { return n == 64 || n == 128 || n == 256; }
+
+// Launches of the register-FFT kernels for a length known at compile time.
+template <typename T, int N>
+struct RegLaunch {
+  static void xfwd(fs_grid* G, T* data, int rows, const DivArgs<T>* dv) {
+    const int nb = ((rows + 1) / 2 + kRegLines - 1) / kRegLines;
+    const DivArgs<T> none{};
+    const size_t sm = reg_smem_bytes<T, N>(0);
+    if (dv)
+      FS_LAUNCH(G, "fft_x_fwd_div", xfwd_reg_kernel<T, N, true><<<nb, kRegBlock, sm, G->stream>>>(
+                                        data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, *dv));
+    else
+      FS_LAUNCH(G, "fft_x_fwd", xfwd_reg_kernel<T, N, false><<<nb, kRegBlock, sm, G->stream>>>(
+                                    data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, none));
+  }
+  static void xinv(fs_grid* G, T* data, int rows) {
+    const int nb = ((rows + 1) / 2 + kRegLines - 1) / kRegLines;
+    FS_LAUNCH(G, "fft_x_inv", xinv_reg_kernel<T, N><<<nb, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
+                                  data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
+  }
+  static void zfwd(fs_grid* G, T* data) {
+    const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
+    FS_LAUNCH(G, "fft_z_fwd", zfwd_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
+                                  data, G->nx, G->ny, (const cplx<T>*)G->pz.tw));
+  }
+  static void zinv(fs_grid* G, T* data) {
+    const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
+    FS_LAUNCH(G, "fft_z_inv", zinv_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(1), G->stream>>>(
+                                  data, G->nx, G->ny, (const cplx<T>*)G->pz.tw));
+  }
+  static void yspec(fs_grid* G, T* data, const YSpecArgs& A) {
+    const dim3 grid((G->nx + 31) / 32, G->dim == 3 ? G->nz : 1);
+    FS_LAUNCH(G, "fft_y_solve", yspec_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
+                                    data, A, (const cplx<T>*)G->py.tw, (const T*)G->lamy, (const T*)G->lamxz));
+  }
+};
+
+template <typename T, typename F>
+void with_reg_length(int n, F&& f) {
+  if (n == 64) f(RegLaunch<T, 64>());
+  else if (n == 128) f(RegLaunch<T, 128>());
+  else f(RegLaunch<T, 256>());
+}
+
 template <typename T>
 void set_smem_attrs() {
   static bool done = false;
   if (done) return;
+  set_smem_attrs_reg<T, 64>();
+  set_smem_attrs_reg<T, 128>();
+  set_smem_attrs_reg<T, 256>();
   set_smem_attrs_plan<T, 0>();
   set_smem_attrs_plan<T, 1>();
   set_smem_attrs_plan<T, 64>();
@@ -885,11 +946,6 @@ void set_smem_attrs() {
   done = true;
 }
 
-bool has_big(const Plan1D& p) {
-  for (int i = 0; i < p.nst; ++i)
-    if (p.radix[i] > 5) return true;
-  return false;
-}
 
 }  // namespace
 
@@ -903,7 +959,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int rows = ny * nz;
   // x forward
-  {
+  if (is_reg_length(nx)) {
+    with_reg_length<T>(nx, [&](auto L) { L.xfwd(G, data, rows, dv); });
+  } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
     const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
@@ -918,7 +976,10 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
                                                                     (const cplx<T>*)G->px.dtw, dv ? *dv : none));
   }
   int ppb = 0;
-  if (G->dim == 3) {
+  const bool zreg = G->dim == 3 && is_reg_length(nz);
+  if (zreg) {
+    with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data); });
+  } else if (G->dim == 3) {
     if (is_fixed_length(G->pz.n)) {
       ppb = kMaxLines;   // the compile-time-length z kernels map 32 slots x 8 rows onto 256 threads
     } else {
@@ -932,7 +993,17 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
-  if (G->yspec) {
+  if (G->yspec && is_reg_length(ny)) {
+    YSpecArgs A;
+    A.nx = nx;
+    A.ny = ny;
+    A.nz = nz;
+    A.dim = G->dim;
+    A.xmode = G->xmode;
+    A.nmx = G->nmx;
+    A.spb = 32;
+    with_reg_length<T>(ny, [&](auto L) { L.yspec(G, data, A); });
+  } else if (G->yspec) {
     YSpecArgs A;
     A.nx = nx;
     A.ny = ny;
@@ -971,13 +1042,17 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     dim3 grid((nx + YCOLS - 1) / YCOLS, G->dim == 3 ? nz : 1);
     FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, dim3(YCOLS, NSEG), ysolve_smem(ny), G->stream>>>(data, A));
   }
-  if (G->dim == 3) {
+  if (zreg) {
+    with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data); });
+  } else if (G->dim == 3) {
     dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
     auto k = fft_kernels<T>(G->pz).zinv;
     FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
-  {
+  if (is_reg_length(nx)) {
+    with_reg_length<T>(nx, [&](auto L) { L.xinv(G, data, rows); });
+  } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
     const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
