@@ -13,6 +13,8 @@
 
 #include <cmath>
 
+#include <type_traits>
+
 #include "fs_internal.cuh"
 
 namespace fs {
@@ -247,12 +249,106 @@ __global__ void __launch_bounds__(kThreads) predictor_kernel(const PredArgs<T> A
   }
 }
 
-// The same predictor for the common 3-D case -- x and z periodic, central
+// The 27 neighbour values of cell (i, j, k) that the three face updates of
+// Eq. (4) need in the 3-D central scheme; names give the offsets in x, y, z
+// (0, M = -1, P = +1).
+template <typename T>
+struct Nb27 {
+  T u000, uM00, uP00, u0M0, u0P0, u00M, u00P, uPM0, uP0M;
+  T v000, vM00, vP00, v0M0, v0P0, v00M, v00P, vMP0, v0PM;
+  T w000, wM00, wP00, w0M0, w0P0, w00M, w00P, wM0P, w0MP;
+};
+
+// y metrics at row j: 1/h_y[j], 1/h_y[j-1], 1/hf_y[j], 1/hf_y[j+1], theta_y[j], theta_y[j+1]
+template <typename T>
+struct YMet {
+  T ihyj, ihyjm, ihfj, ihfjp, thj, thjp;
+};
+
+template <typename T, bool YPER>
+__device__ __forceinline__ YMet<T> ymet(const PredArgs<T>& A, int j) {
+  YMet<T> m;
+  if (YPER) {
+    m.ihyj = m.ihyjm = m.ihfj = m.ihfjp = A.ihy0;
+    m.thj = m.thjp = T(0.5);
+  } else {
+    const Geom<T>& g = A.g;
+    m.ihyj = g.ihy[j];
+    m.ihyjm = g.ihy[j - 1];
+    m.ihfj = g.ihfy[j];
+    m.ihfjp = g.ihfy[j + 1];
+    m.thj = g.thy[j];
+    m.thjp = g.thy[j + 1];
+  }
+  return m;
+}
+
+// R(u) of Eq. (4) on the x-, y- and z-faces of one cell, central convection;
+// the arithmetic is that of momentum_rhs with the interior metrics.
+template <typename T>
+__device__ __forceinline__ void rhs3(const Nb27<T>& n, const YMet<T>& m, T ihx, T ihz, T nu, T bf, T& Ru, T& Rv,
+                                     T& Rw) {
+  const T h = T(0.5);
+  {  // u on the x-face
+    const T TE = h * (n.u000 + n.uP00), TW = h * (n.uM00 + n.u000);
+    T cv = (TE * TE - TW * TW) * ihx;
+    T df = ((n.uP00 - n.u000) * ihx - (n.u000 - n.uM00) * ihx) * ihx;
+    const T TN = h * (n.vMP0 + n.v0P0), TS = h * (n.vM00 + n.v000);
+    const T QN = (T(1) - m.thjp) * n.u000 + m.thjp * n.u0P0, QS = (T(1) - m.thj) * n.u0M0 + m.thj * n.u000;
+    cv += (TN * QN - TS * QS) * m.ihyj;
+    df += ((n.u0P0 - n.u000) * m.ihfjp - (n.u000 - n.u0M0) * m.ihfj) * m.ihyj;
+    const T TT = h * (n.wM0P + n.w00P), TB = h * (n.wM00 + n.w000);
+    const T QT = h * (n.u000 + n.u00P), QB = h * (n.u00M + n.u000);
+    cv += (TT * QT - TB * QB) * ihz;
+    df += ((n.u00P - n.u000) * ihz - (n.u000 - n.u00M) * ihz) * ihz;
+    Ru = -cv + nu * df + bf;
+  }
+  {  // v on the y-face
+    const T TE = h * (n.v000 + n.v0P0), TW = h * (n.v0M0 + n.v000);
+    T cv = (TE * TE - TW * TW) * m.ihfj;
+    T df = ((n.v0P0 - n.v000) * m.ihyj - (n.v000 - n.v0M0) * m.ihyjm) * m.ihfj;
+    const T TN = (T(1) - m.thj) * n.uPM0 + m.thj * n.uP00, TS = (T(1) - m.thj) * n.u0M0 + m.thj * n.u000;
+    const T QN = h * (n.v000 + n.vP00), QS = h * (n.vM00 + n.v000);
+    cv += (TN * QN - TS * QS) * ihx;
+    df += ((n.vP00 - n.v000) * ihx - (n.v000 - n.vM00) * ihx) * ihx;
+    const T TT = (T(1) - m.thj) * n.w0MP + m.thj * n.w00P, TB = (T(1) - m.thj) * n.w0M0 + m.thj * n.w000;
+    const T QT = h * (n.v000 + n.v00P), QB = h * (n.v00M + n.v000);
+    cv += (TT * QT - TB * QB) * ihz;
+    df += ((n.v00P - n.v000) * ihz - (n.v000 - n.v00M) * ihz) * ihz;
+    Rv = -cv + nu * df;
+  }
+  {  // w on the z-face
+    const T TE = h * (n.w000 + n.w00P), TW = h * (n.w00M + n.w000);
+    T cv = (TE * TE - TW * TW) * ihz;
+    T df = ((n.w00P - n.w000) * ihz - (n.w000 - n.w00M) * ihz) * ihz;
+    const T TN = h * (n.uP0M + n.uP00), TS = h * (n.u00M + n.u000);
+    const T QN = h * (n.w000 + n.wP00), QS = h * (n.wM00 + n.w000);
+    cv += (TN * QN - TS * QS) * ihx;
+    df += ((n.wP00 - n.w000) * ihx - (n.w000 - n.wM00) * ihx) * ihx;
+    const T TT = h * (n.v0PM + n.v0P0), TB = h * (n.v00M + n.v000);
+    const T QT = (T(1) - m.thjp) * n.w000 + m.thjp * n.w0P0, QB = (T(1) - m.thj) * n.w0M0 + m.thj * n.w000;
+    cv += (TT * QT - TB * QB) * m.ihyj;
+    df += ((n.w0P0 - n.w000) * m.ihfjp - (n.w000 - n.w0M0) * m.ihfj) * m.ihyj;
+    Rw = -cv + nu * df;
+  }
+}
+
+// The general per-face path for the rows of a wall-bounded y whose stencil
+// reaches a wall (j < 2 or j > ny - 2).
+template <typename T>
+__device__ __forceinline__ void predict_cell_general(const PredArgs<T>& A, int i, int j, int k) {
+  const AccGhost<T> U{&A.g, A.uin, i, j, k};
+  predict_face<T, 0>(A, U, i, j, k);
+  predict_face<T, 1>(A, U, i, j, k);
+  predict_face<T, 2>(A, U, i, j, k);
+}
+
+// The predictor for the common 3-D case -- x and z periodic, central
 // convection, no immersed body -- with the 27 distinct neighbour values of a
 // cell loaded once and shared by its three faces.  YPER: y periodic (uniform
 // metrics); otherwise y has walls and stretched metrics, and the rows whose
-// stencil reaches a wall (j < 2 or j > ny - 2; warp-uniform since blocks are at
-// least 32 wide in x) take the general path.  Arithmetic follows momentum_rhs.
+// stencil reaches a wall take the general path (j is warp-uniform: blocks are
+// at least 32 wide in x).
 template <typename T, bool YPER>
 __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> A) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -262,10 +358,7 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
   const Geom<T>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (!YPER && (j < 2 || j > ny - 2)) {
-    const AccGhost<T> U{&g, A.uin, i, j, k};
-    predict_face<T, 0>(A, U, i, j, k);
-    predict_face<T, 1>(A, U, i, j, k);
-    predict_face<T, 2>(A, U, i, j, k);
+    predict_cell_general(A, i, j, k);
     return;
   }
   const int im = i > 0 ? i - 1 : nx - 1, ip = i < nx - 1 ? i + 1 : 0;
@@ -281,76 +374,20 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
   const T* __restrict__ U = A.uin[0];
   const T* __restrict__ V = A.uin[1];
   const T* __restrict__ W = A.uin[2];
-  const T u000 = __ldg(U + r00 + i), uM00 = __ldg(U + r00 + im), uP00 = __ldg(U + r00 + ip);
-  const T u0M0 = __ldg(U + rm0 + i), u0P0 = __ldg(U + rp0 + i), u00M = __ldg(U + r0m + i), u00P = __ldg(U + r0p + i);
-  const T uPM0 = __ldg(U + rm0 + ip), uP0M = __ldg(U + r0m + ip);
-  const T v000 = __ldg(V + v00 + i), vM00 = __ldg(V + v00 + im), vP00 = __ldg(V + v00 + ip);
-  const T v0M0 = __ldg(V + vm0 + i), v0P0 = __ldg(V + vp0 + i), v00M = __ldg(V + v0m + i), v00P = __ldg(V + v0p + i);
-  const T vMP0 = __ldg(V + vp0 + im), v0PM = __ldg(V + vpm + i);
-  const T w000 = __ldg(W + r00 + i), wM00 = __ldg(W + r00 + im), wP00 = __ldg(W + r00 + ip);
-  const T w0M0 = __ldg(W + rm0 + i), w0P0 = __ldg(W + rp0 + i), w00M = __ldg(W + r0m + i), w00P = __ldg(W + r0p + i);
-  const T wM0P = __ldg(W + r0p + im), w0MP = __ldg(W + rmp + i);
-  const T h = T(0.5);
-  const T ihx = g.ihx, ihz = g.ihz;
-  // y metrics at rows j (cells and faces)
-  T ihyj, ihyjm, ihfj, ihfjp, thj, thjp;
-  if (YPER) {
-    ihyj = ihyjm = ihfj = ihfjp = A.ihy0;
-    thj = thjp = h;
-  } else {
-    ihyj = g.ihy[j];
-    ihyjm = g.ihy[j - 1];
-    ihfj = g.ihfy[j];
-    ihfjp = g.ihfy[j + 1];
-    thj = g.thy[j];
-    thjp = g.thy[j + 1];
-  }
+  Nb27<T> n;
+  n.u000 = __ldg(U + r00 + i); n.uM00 = __ldg(U + r00 + im); n.uP00 = __ldg(U + r00 + ip);
+  n.u0M0 = __ldg(U + rm0 + i); n.u0P0 = __ldg(U + rp0 + i); n.u00M = __ldg(U + r0m + i); n.u00P = __ldg(U + r0p + i);
+  n.uPM0 = __ldg(U + rm0 + ip); n.uP0M = __ldg(U + r0m + ip);
+  n.v000 = __ldg(V + v00 + i); n.vM00 = __ldg(V + v00 + im); n.vP00 = __ldg(V + v00 + ip);
+  n.v0M0 = __ldg(V + vm0 + i); n.v0P0 = __ldg(V + vp0 + i); n.v00M = __ldg(V + v0m + i); n.v00P = __ldg(V + v0p + i);
+  n.vMP0 = __ldg(V + vp0 + im); n.v0PM = __ldg(V + vpm + i);
+  n.w000 = __ldg(W + r00 + i); n.wM00 = __ldg(W + r00 + im); n.wP00 = __ldg(W + r00 + ip);
+  n.w0M0 = __ldg(W + rm0 + i); n.w0P0 = __ldg(W + rp0 + i); n.w00M = __ldg(W + r0m + i); n.w00P = __ldg(W + r0p + i);
+  n.wM0P = __ldg(W + r0p + im); n.w0MP = __ldg(W + rmp + i);
   T Ru, Rv, Rw;
-  {  // u on the x-face (i, j, k)
-    const T TE = h * (u000 + uP00), TW = h * (uM00 + u000);
-    T cv = (TE * TE - TW * TW) * ihx;
-    T df = ((uP00 - u000) * ihx - (u000 - uM00) * ihx) * ihx;
-    const T TN = h * (vMP0 + v0P0), TS = h * (vM00 + v000);
-    const T QN = (T(1) - thjp) * u000 + thjp * u0P0, QS = (T(1) - thj) * u0M0 + thj * u000;
-    cv += (TN * QN - TS * QS) * ihyj;
-    df += ((u0P0 - u000) * ihfjp - (u000 - u0M0) * ihfj) * ihyj;
-    const T TT = h * (wM0P + w00P), TB = h * (wM00 + w000);
-    const T QT = h * (u000 + u00P), QB = h * (u00M + u000);
-    cv += (TT * QT - TB * QB) * ihz;
-    df += ((u00P - u000) * ihz - (u000 - u00M) * ihz) * ihz;
-    Ru = -cv + g.nu * df;
-    if (g.bforce) Ru += g.bforce[j];
-  }
-  {  // v on the y-face (i, j, k)
-    const T TE = h * (v000 + v0P0), TW = h * (v0M0 + v000);
-    T cv = (TE * TE - TW * TW) * ihfj;
-    T df = ((v0P0 - v000) * ihyj - (v000 - v0M0) * ihyjm) * ihfj;
-    const T TN = (T(1) - thj) * uPM0 + thj * uP00, TS = (T(1) - thj) * u0M0 + thj * u000;
-    const T QN = h * (v000 + vP00), QS = h * (vM00 + v000);
-    cv += (TN * QN - TS * QS) * ihx;
-    df += ((vP00 - v000) * ihx - (v000 - vM00) * ihx) * ihx;
-    const T TT = (T(1) - thj) * w0MP + thj * w00P, TB = (T(1) - thj) * w0M0 + thj * w000;
-    const T QT = h * (v000 + v00P), QB = h * (v00M + v000);
-    cv += (TT * QT - TB * QB) * ihz;
-    df += ((v00P - v000) * ihz - (v000 - v00M) * ihz) * ihz;
-    Rv = -cv + g.nu * df;
-  }
-  {  // w on the z-face (i, j, k)
-    const T TE = h * (w000 + w00P), TW = h * (w00M + w000);
-    T cv = (TE * TE - TW * TW) * ihz;
-    T df = ((w00P - w000) * ihz - (w000 - w00M) * ihz) * ihz;
-    const T TN = h * (uP0M + uP00), TS = h * (u00M + u000);
-    const T QN = h * (w000 + wP00), QS = h * (wM00 + w000);
-    cv += (TN * QN - TS * QS) * ihx;
-    df += ((wP00 - w000) * ihx - (w000 - wM00) * ihx) * ihx;
-    const T TT = h * (v0PM + v0P0), TB = h * (v00M + v000);
-    const T QT = (T(1) - thjp) * w000 + thjp * w0P0, QB = (T(1) - thj) * w0M0 + thj * w000;
-    cv += (TT * QT - TB * QB) * ihyj;
-    df += ((w0P0 - w000) * ihfjp - (w000 - w0M0) * ihfj) * ihyj;
-    Rw = -cv + g.nu * df;
-  }
+  rhs3(n, ymet<T, YPER>(A, j), g.ihx, g.ihz, g.nu, g.bforce ? g.bforce[j] : T(0), Ru, Rv, Rw);
   const T a = A.a, b = A.b, dt = A.dt;
-  T ou = b * (u000 + dt * Ru), ov = b * (v000 + dt * Rv), ow = b * (w000 + dt * Rw);
+  T ou = b * (n.u000 + dt * Ru), ov = b * (n.v000 + dt * Rv), ow = b * (n.w000 + dt * Rw);
   if (a != T(0)) {
     ou += a * A.un[0][r00 + i];
     ov += a * A.un[1][v00 + i];
@@ -361,6 +398,104 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
     A.out[2][r00 + i] = ow;
   }
   A.out[1][v00 + i] = ov;
+}
+
+// Row segment of four values at x = i0 .. i0+3 with optional neighbours:
+// s[0] = x[i0 - 1] (LO), s[1..4] = x[i0 .. i0+3], s[5] = x[i0 + 4] (HI), periodic in x.
+template <bool LO, bool HI>
+__device__ __forceinline__ void ld_seg(const float* __restrict__ row, int i0, int nx, float* s) {
+  const Vec4<float> a = ld4(row + i0);
+  s[1] = a.v[0];
+  s[2] = a.v[1];
+  s[3] = a.v[2];
+  s[4] = a.v[3];
+  if (LO) s[0] = __ldg(row + (i0 > 0 ? i0 - 1 : nx - 1));
+  if (HI) s[5] = __ldg(row + (i0 + 4 < nx ? i0 + 4 : 0));
+}
+
+// Four cells per thread along x (FP32, nx % 4 == 0, 16-byte aligned fields):
+// 17 four-wide and 10 scalar loads feed the 3 x 4 face updates.
+template <bool YPER>
+__global__ void __launch_bounds__(kThreads) predictor3v_kernel(const PredArgs<float> A) {
+  const Geom<float>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i0 >= nx || j >= A.Y) return;
+  if (!YPER && (j < 2 || j > ny - 2)) {
+    for (int e = 0; e < 4; ++e) predict_cell_general(A, i0 + e, j, k);
+    return;
+  }
+  const int km = k > 0 ? k - 1 : nz - 1, kp = k < nz - 1 ? k + 1 : 0;
+  const int jm = YPER ? (j > 0 ? j - 1 : ny - 1) : j - 1;
+  const int jp = YPER ? (j < ny - 1 ? j + 1 : 0) : j + 1;
+  const int eyv = YPER ? ny : ny + 1;
+  const int r00 = nx * (j + ny * k), rm0 = nx * (jm + ny * k), rp0 = nx * (jp + ny * k);
+  const int r0m = nx * (j + ny * km), r0p = nx * (j + ny * kp), rmp = nx * (jm + ny * kp);
+  const int v00 = nx * (j + eyv * k), vm0 = nx * (jm + eyv * k), vp0 = nx * (jp + eyv * k);
+  const int v0m = nx * (j + eyv * km), v0p = nx * (j + eyv * kp), vpm = nx * (jp + eyv * km);
+  const float* __restrict__ U = A.uin[0];
+  const float* __restrict__ V = A.uin[1];
+  const float* __restrict__ W = A.uin[2];
+  // segments: index e + 1 is cell i0 + e
+  float U00[6], UM0[6], UP0[6], U0M[6], U0P[6];
+  float V00[6], VM0[6], VP0[6], V0M[6], V0P[6], VPM[6];
+  float W00[6], WM0[6], WP0[6], W0M[6], W0P[6], WMP[6];
+  ld_seg<true, true>(U + r00, i0, nx, U00);
+  ld_seg<false, true>(U + rm0, i0, nx, UM0);
+  ld_seg<false, false>(U + rp0, i0, nx, UP0);
+  ld_seg<false, true>(U + r0m, i0, nx, U0M);
+  ld_seg<false, false>(U + r0p, i0, nx, U0P);
+  ld_seg<true, true>(V + v00, i0, nx, V00);
+  ld_seg<false, false>(V + vm0, i0, nx, VM0);
+  ld_seg<true, false>(V + vp0, i0, nx, VP0);
+  ld_seg<false, false>(V + v0m, i0, nx, V0M);
+  ld_seg<false, false>(V + v0p, i0, nx, V0P);
+  ld_seg<false, false>(V + vpm, i0, nx, VPM);
+  ld_seg<true, true>(W + r00, i0, nx, W00);
+  ld_seg<false, false>(W + rm0, i0, nx, WM0);
+  ld_seg<false, false>(W + rp0, i0, nx, WP0);
+  ld_seg<false, false>(W + r0m, i0, nx, W0M);
+  ld_seg<true, false>(W + r0p, i0, nx, W0P);
+  ld_seg<false, false>(W + rmp, i0, nx, WMP);
+  const YMet<float> m = ymet<float, YPER>(A, j);
+  const float bf = g.bforce ? g.bforce[j] : 0.f;
+  const float a = A.a, b = A.b, dt = A.dt;
+  Vec4<float> ou, ov, ow;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int c = e + 1;
+    Nb27<float> n;
+    n.u000 = U00[c]; n.uM00 = U00[c - 1]; n.uP00 = U00[c + 1];
+    n.u0M0 = UM0[c]; n.uPM0 = UM0[c + 1]; n.u0P0 = UP0[c];
+    n.u00M = U0M[c]; n.uP0M = U0M[c + 1]; n.u00P = U0P[c];
+    n.v000 = V00[c]; n.vM00 = V00[c - 1]; n.vP00 = V00[c + 1];
+    n.v0M0 = VM0[c]; n.v0P0 = VP0[c]; n.vMP0 = VP0[c - 1];
+    n.v00M = V0M[c]; n.v00P = V0P[c]; n.v0PM = VPM[c];
+    n.w000 = W00[c]; n.wM00 = W00[c - 1]; n.wP00 = W00[c + 1];
+    n.w0M0 = WM0[c]; n.w0P0 = WP0[c]; n.w00M = W0M[c];
+    n.w00P = W0P[c]; n.wM0P = W0P[c - 1]; n.w0MP = WMP[c];
+    float Ru, Rv, Rw;
+    rhs3(n, m, g.ihx, g.ihz, g.nu, bf, Ru, Rv, Rw);
+    ou.v[e] = b * (n.u000 + dt * Ru);
+    ov.v[e] = b * (n.v000 + dt * Rv);
+    ow.v[e] = b * (n.w000 + dt * Rw);
+  }
+  if (a != 0.f) {
+    const Vec4<float> pu = ld4(A.un[0] + r00 + i0), pv = ld4(A.un[1] + v00 + i0), pw = ld4(A.un[2] + r00 + i0);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      ou.v[e] += a * pu.v[e];
+      ov.v[e] += a * pv.v[e];
+      ow.v[e] += a * pw.v[e];
+    }
+  }
+  if (j < ny) {
+    st4(A.out[0] + r00 + i0, ou);
+    st4(A.out[2] + r00 + i0, ow);
+  }
+  st4(A.out[1] + v00 + i0, ov);
 }
 
 template <typename T>
@@ -605,6 +740,22 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
   if (G->dim == 3 && G->per[0] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body && G->ny >= 4) {
+    if constexpr (std::is_same<T, float>::value) {
+      bool vec = G->nx % 4 == 0;
+      for (int c = 0; c < 3; ++c) {
+        vec = vec && (uintptr_t)uin[c] % 16 == 0 && (uintptr_t)out[c] % 16 == 0;
+        if (un) vec = vec && (uintptr_t)un[c] % 16 == 0;
+      }
+      if (vec) {
+        const dim3 vb(32, 8);
+        const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, G->nz);
+        if (G->per[1])
+          FS_LAUNCH(G, "predictor", predictor3v_kernel<true><<<vg, vb, 0, G->stream>>>(A));
+        else
+          FS_LAUNCH(G, "predictor", predictor3v_kernel<false><<<vg, vb, 0, G->stream>>>(A));
+        return;
+      }
+    }
     if (G->per[1])
       FS_LAUNCH(G, "predictor", predictor3_kernel<T, true><<<grd, blk, 0, G->stream>>>(A));
     else
