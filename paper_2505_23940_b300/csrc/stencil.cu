@@ -416,7 +416,7 @@ __device__ __forceinline__ void ld_seg(const float* __restrict__ row, int i0, in
 // Four cells per thread along x (FP32, nx % 4 == 0, 16-byte aligned fields):
 // 17 four-wide and 10 scalar loads feed the 3 x 4 face updates.
 template <bool YPER>
-__global__ void __launch_bounds__(kThreads) predictor3v_kernel(const PredArgs<float> A) {
+__global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs<float> A) {
   const Geom<float>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
