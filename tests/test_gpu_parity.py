@@ -137,6 +137,23 @@ def test_mixed_isotropic_32_rk3():
     assert field_err(gp["u"], st.u) < TOLMIX
 
 
+@pytest.mark.parametrize("n", [(64, 64, 64), (128, 64, 128), (64, 128, 64), (64, 256, 64), (256, 64, 64),
+                               (64, 64, 256)])
+def test_mixed_periodic_transform_shapes(n):
+    """Fully periodic 3-D mixed grids whose x, z and periodic-y transforms take
+    the register FFT kernels of lengths 64 / 128 / 256, against the FP64 oracle."""
+    L = (1.0, 0.8, 1.2)
+    wl = S.box_3d(*n, (P, P), (P, P), L=L, nu=0.001)
+    hmin = min(L[d] / n[d] for d in range(3))
+    wl.scheme, wl.dt, wl.precision = "rk3", 0.25 * hmin, "mixed"   # CFL 0.25 for |u| <= 1
+    wl.u0 = S.random_fields(wl, 11, 1.0)
+    gp = run_gpu(wl, 5, precision="mixed")
+    st, _, _ = run_oracle(wl, 5)
+    assert field_err(gp["u"], st.u) < TOLMIX
+    d = gp["grid"].diagnostics(gp["u_dev"])
+    assert d["divmax"] < 1e-3 * d["umax"] * max(n)
+
+
 def test_mixed_channel_small_100_steps():
     wl = S.channel_3d(nx=24, ny=16, nz=16, steps=100)
     gp = run_gpu(wl, 100, precision="mixed")
