@@ -198,6 +198,9 @@ long long fs_kernel_launches(const fs_grid* grid);
  *   "stencil_bx"      x threads of the 256-thread stencil blocks: 32, 64, 128, 256
  *   "fft_lines"       complex lines per FFT block: 1..16
  *   "ysolve_threads"  threads per tridiagonal block: power of two in 8..128
+ *   "pdl"             1 (default): step kernels use programmatic dependent
+ *                     launch (each starts while its predecessor drains);
+ *                     0: ordinary stream-ordered launches
  * Results do not depend on them.  FS_ERR_ARG for an unknown key or value. */
 int fs_set_tuning(fs_grid* grid, const char* key, int value);
 

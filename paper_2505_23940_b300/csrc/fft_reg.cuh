@@ -261,6 +261,7 @@ template <typename T, int N, bool DIV>
 __global__ void __launch_bounds__(kRegBlock) xfwd_reg_kernel(T* __restrict__ data, int rows, int mode,
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
+  pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(kRegBlock) xfwd_reg_kernel(T* __restrict__ dat
   __syncthreads();
   fft_reg_block<T, N, false>(S, tws);
   __syncthreads();
+  pdl_trigger();
   // real-packed (periodic) or DCT-II rows; two consecutive outputs per thread
   constexpr int NH = N / 2;
   for (int t = threadIdx.x; t < nl * NH; t += kRegBlock) {
@@ -372,6 +374,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw) {
+  pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -446,6 +449,7 @@ __global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ dat
   __syncthreads();
   fft_reg_block<T, N, true>(S, tws);
   __syncthreads();
+  pdl_trigger();
   const T inv_n = T(1) / T(N);
   constexpr int NH = N / 2;
   for (int t = threadIdx.x; t < nl * NH; t += kRegBlock) {
@@ -472,6 +476,7 @@ __global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ dat
 template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw) {
+  pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -486,6 +491,7 @@ __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ dat
   __syncthreads();
   fft_reg_block<T, N, false>(S, tws);
   __syncthreads();
+  pdl_trigger();
   store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int p) -> cplx<T> {
     const cplx<T>* Z = S + line * P;
     if (pair0 + line > 0) return Z[rpad<N>(p)];
@@ -504,6 +510,7 @@ __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ dat
 template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw) {
+  pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -546,6 +553,7 @@ __global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ dat
   }
   fft_reg_block<T, N, true>(S, tws);
   __syncthreads();
+  pdl_trigger();
   const T inv_n = T(1) / T(N);
   store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int k) -> cplx<T> {
     const cplx<T> v = S[line * P + rpad<N>(k)];
@@ -559,6 +567,7 @@ __global__ void __launch_bounds__(kRegBlock) yspec_reg_kernel(T* __restrict__ da
                                                             const cplx<T>* __restrict__ tw,
                                                             const T* __restrict__ lamy,
                                                             const T* __restrict__ lamxz) {
+  pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -594,6 +603,7 @@ __global__ void __launch_bounds__(kRegBlock) yspec_reg_kernel(T* __restrict__ da
   __syncthreads();
   fft_reg_block<T, N, true>(S, tws);
   __syncthreads();
+  pdl_trigger();
   const T inv_n = T(1) / T(N);
   store_pair_tile<T, N>(base, rs, ns, [&](int line, int jj) -> cplx<T> {
     const cplx<T> v = S[line * P + rpad<N>(jj)];

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "fs.h"
@@ -283,6 +284,7 @@ struct fs_grid {
   int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads
   int tune_fft_lines = 0;      // complex lines per FFT block (1..16)
   int tune_ysolve = 0;         // threads per y-solve block (8..128)
+  bool use_pdl = true;         // programmatic dependent launch of the step kernels
 
   // optional per-kernel timing (fs_profile_begin / fs_profile_end)
   bool prof_on = false;
@@ -342,6 +344,33 @@ struct ProfMark {
   ProfMark(fs_grid* G, const char* name);
   ~ProfMark();
 };
+}  // namespace fs
+
+namespace fs {
+// Programmatic dependent launch: a kernel launched by launch_pdl may start
+// while its predecessor on the stream drains; it must call pdl_wait() before
+// its first access to global memory (a no-op for ordinary launches).
+// pdl_trigger() lets the successor launch before this grid ends.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(fs_grid* G, const char* name, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                Args&&... args) {
+  ProfMark pm(G, name);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = G->stream;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = G->use_pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+  G->launches++;
+}
 }  // namespace fs
 
 // Launch with accounting: FS_LAUNCH(grid, "name", kernel<<<...>>>(...));

@@ -894,31 +894,31 @@ struct RegLaunch {
     const DivArgs<T> none{};
     const size_t sm = reg_smem_bytes<T, N>(0);
     if (dv)
-      FS_LAUNCH(G, "fft_x_fwd_div", xfwd_reg_kernel<T, N, true><<<nb, kRegBlock, sm, G->stream>>>(
-                                        data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, *dv));
+      launch_pdl(G, "fft_x_fwd_div", xfwd_reg_kernel<T, N, true>, dim3(nb), dim3(kRegBlock), sm, data, rows, G->xmode,
+                 (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, *dv);
     else
-      FS_LAUNCH(G, "fft_x_fwd", xfwd_reg_kernel<T, N, false><<<nb, kRegBlock, sm, G->stream>>>(
-                                    data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, none));
+      launch_pdl(G, "fft_x_fwd", xfwd_reg_kernel<T, N, false>, dim3(nb), dim3(kRegBlock), sm, data, rows, G->xmode,
+                 (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw, none);
   }
   static void xinv(fs_grid* G, T* data, int rows) {
     const int nb = ((rows + 1) / 2 + kRegLines - 1) / kRegLines;
-    FS_LAUNCH(G, "fft_x_inv", xinv_reg_kernel<T, N><<<nb, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
-                                  data, rows, G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
+    launch_pdl(G, "fft_x_inv", xinv_reg_kernel<T, N>, dim3(nb), dim3(kRegBlock), reg_smem_bytes<T, N>(0), data, rows,
+               G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw);
   }
   static void zfwd(fs_grid* G, T* data) {
     const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
-    FS_LAUNCH(G, "fft_z_fwd", zfwd_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
-                                  data, G->nx, G->ny, (const cplx<T>*)G->pz.tw));
+    launch_pdl(G, "fft_z_fwd", zfwd_reg_kernel<T, N>, grid, dim3(kRegBlock), reg_smem_bytes<T, N>(0), data, G->nx, G->ny,
+               (const cplx<T>*)G->pz.tw);
   }
   static void zinv(fs_grid* G, T* data) {
     const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
-    FS_LAUNCH(G, "fft_z_inv", zinv_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(1), G->stream>>>(
-                                  data, G->nx, G->ny, (const cplx<T>*)G->pz.tw));
+    launch_pdl(G, "fft_z_inv", zinv_reg_kernel<T, N>, grid, dim3(kRegBlock), reg_smem_bytes<T, N>(1), data, G->nx, G->ny,
+               (const cplx<T>*)G->pz.tw);
   }
   static void yspec(fs_grid* G, T* data, const YSpecArgs& A) {
     const dim3 grid((G->nx + 31) / 32, G->dim == 3 ? G->nz : 1);
-    FS_LAUNCH(G, "fft_y_solve", yspec_reg_kernel<T, N><<<grid, kRegBlock, reg_smem_bytes<T, N>(0), G->stream>>>(
-                                    data, A, (const cplx<T>*)G->py.tw, (const T*)G->lamy, (const T*)G->lamxz));
+    launch_pdl(G, "fft_y_solve", yspec_reg_kernel<T, N>, grid, dim3(kRegBlock), reg_smem_bytes<T, N>(0), data, A,
+               (const cplx<T>*)G->py.tw, (const T*)G->lamy, (const T*)G->lamxz);
   }
 };
 

@@ -227,6 +227,7 @@ __device__ __forceinline__ void predict_face(const PredArgs<T>& A, const Acc& U,
 // One thread per cell position (i, j, k) computes every component's face there.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) predictor_kernel(const PredArgs<T> A) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -351,6 +352,7 @@ __device__ __forceinline__ void predict_cell_general(const PredArgs<T>& A, int i
 // at least 32 wide in x).
 template <typename T, bool YPER>
 __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> A) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -417,6 +419,7 @@ __device__ __forceinline__ void ld_seg(const float* __restrict__ row, int i0, in
 // 17 four-wide and 10 scalar loads feed the 3 x 4 face updates.
 template <bool YPER>
 __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs<float> A) {
+  pdl_wait();
   const Geom<float>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -558,6 +561,7 @@ __device__ __forceinline__ void correct_face(const CorrArgs<T>& A, int i, int j,
 // Eq. (10): u^{n+1} = u* - G phi on every interior face; one thread per cell position.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) correct_kernel(const CorrArgs<T> A) {
+  pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -574,6 +578,7 @@ __global__ void __launch_bounds__(kThreads) correct_kernel(const CorrArgs<T> A) 
 // row-vector loads and stores (y faces on walls keep their imposed value).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) correct4_kernel(const CorrArgs<T> A) {
+  pdl_wait();
   const Geom<T>& g = A.g;
   const int nx = g.nx, ny = g.ny;
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
@@ -750,19 +755,19 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
         const dim3 vb(32, 8);
         const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, G->nz);
         if (G->per[1])
-          FS_LAUNCH(G, "predictor", predictor3v_kernel<true><<<vg, vb, 0, G->stream>>>(A));
+          launch_pdl(G, "predictor", predictor3v_kernel<true>, vg, vb, 0, A);
         else
-          FS_LAUNCH(G, "predictor", predictor3v_kernel<false><<<vg, vb, 0, G->stream>>>(A));
+          launch_pdl(G, "predictor", predictor3v_kernel<false>, vg, vb, 0, A);
         return;
       }
     }
     if (G->per[1])
-      FS_LAUNCH(G, "predictor", predictor3_kernel<T, true><<<grd, blk, 0, G->stream>>>(A));
+      launch_pdl(G, "predictor", predictor3_kernel<T, true>, grd, blk, 0, A);
     else
-      FS_LAUNCH(G, "predictor", predictor3_kernel<T, false><<<grd, blk, 0, G->stream>>>(A));
+      launch_pdl(G, "predictor", predictor3_kernel<T, false>, grd, blk, 0, A);
     return;
   }
-  FS_LAUNCH(G, "predictor", predictor_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+  launch_pdl(G, "predictor", predictor_kernel<T>, grd, blk, 0, A);
 }
 
 template <typename T>
@@ -823,12 +828,12 @@ void launch_correct(fs_grid* G, T* const* ustar, const T* phi, T* const* unew) {
   if (vec) {
     const dim3 blk(32, 8);
     const dim3 grd((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, G->nz);
-    FS_LAUNCH(G, "correct", correct4_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+    launch_pdl(G, "correct", correct4_kernel<T>, grd, blk, 0, A);
     return;
   }
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
-  FS_LAUNCH(G, "correct", correct_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+  launch_pdl(G, "correct", correct_kernel<T>, grd, blk, 0, A);
 }
 
 template <typename T>
