@@ -187,6 +187,92 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_kernel(const RhsAdjArgs<T> A) 
   }
 }
 
+// Gather form of rhs_adjoint for fully periodic 3-D grids with central
+// convection (uniform metrics): every thread forms lam(p) += (dR/du(p))^T mu
+// for the three faces at its cell p from the flux adjoints of all fluxes that
+// read u(p), so no atomics are needed.  With R_C(f) = -(F(f) - F(f - e)) i_e per
+// flux F on the interface between faces f and f + e, the flux adjoint is
+// aF(f) = i_e (mu_C(f + e) - mu_C(f)); the own-direction flux F = T^2,
+// T = (u_C(f) + u_C(f + e_C)) / 2, gives aF T to both faces, and the cross flux
+// E_Cd(f) = TN QN, TN = (u_d(f + e_d - e_C) + u_d(f + e_d)) / 2,
+// QN = (u_C(f) + u_C(f + e_d)) / 2, gives aE TN / 2 to the two u_C and aE QN / 2
+// to the two u_d it reads.  Diffusion is symmetric on a uniform periodic grid.
+template <typename T>
+__global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const RhsAdjArgs<T> A) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const Geom<T>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx || j >= ny) return;
+  const int xo[3] = {i > 0 ? i - 1 : nx - 1, i, i < nx - 1 ? i + 1 : 0};
+  const int yo[3] = {j > 0 ? j - 1 : ny - 1, j, j < ny - 1 ? j + 1 : 0};
+  const int zo[3] = {k > 0 ? k - 1 : nz - 1, k, k < nz - 1 ? k + 1 : 0};
+  auto at = [&](int di, int dj, int dk) { return xo[di + 1] + nx * (yo[dj + 1] + ny * zo[dk + 1]); };
+  const T* __restrict__ U = A.u[0];
+  const T* __restrict__ V = A.u[1];
+  const T* __restrict__ W = A.u[2];
+  const T* __restrict__ MU = A.mu[0];
+  const T* __restrict__ MV = A.mu[1];
+  const T* __restrict__ MW = A.mu[2];
+  auto u = [&](int a, int b, int c) { return __ldg(U + at(a, b, c)); };
+  auto v = [&](int a, int b, int c) { return __ldg(V + at(a, b, c)); };
+  auto w = [&](int a, int b, int c) { return __ldg(W + at(a, b, c)); };
+  auto mu = [&](int a, int b, int c) { return __ldg(MU + at(a, b, c)); };
+  auto mv = [&](int a, int b, int c) { return __ldg(MV + at(a, b, c)); };
+  auto mw = [&](int a, int b, int c) { return __ldg(MW + at(a, b, c)); };
+  const T h = T(0.5);
+  const T ihx = g.ihx, ihy = g.ihy[0], ihz = g.ihz, nu = g.nu;
+  // values shared by the three outputs
+  const T u0 = u(0, 0, 0), v0 = v(0, 0, 0), w0 = w(0, 0, 0);
+  const T mu0 = mu(0, 0, 0), mv0 = mv(0, 0, 0), mw0 = mw(0, 0, 0);
+  const T muPx = mu(1, 0, 0), mvPy = mv(0, 1, 0), mwPz = mw(0, 0, 1);
+  const T uPx = u(1, 0, 0), vPy = v(0, 1, 0), wPz = w(0, 0, 1);
+  const int p = at(0, 0, 0);
+  {  // lambda_u
+    const T uMx = u(-1, 0, 0);
+    const T vMxPy = v(-1, 1, 0), vMx = v(-1, 0, 0), wMxPz = w(-1, 0, 1), wMx = w(-1, 0, 0);
+    const T muMx = mu(-1, 0, 0), muPy = mu(0, 1, 0), muMy = mu(0, -1, 0), muPz = mu(0, 0, 1), muMz = mu(0, 0, -1);
+    const T mvMxPy = mv(-1, 1, 0), mvMx = mv(-1, 0, 0), mwMxPz = mw(-1, 0, 1), mwMx = mw(-1, 0, 0);
+    T l = ihx * (muPx - mu0) * h * (u0 + uPx) + ihx * (mu0 - muMx) * h * (uMx + u0);
+    l += h * (ihy * (muPy - mu0) * h * (vMxPy + vPy) + ihy * (mu0 - muMy) * h * (vMx + v0));
+    l += h * (ihz * (muPz - mu0) * h * (wMxPz + wPz) + ihz * (mu0 - muMz) * h * (wMx + w0));
+    l += h * (ihx * (mvPy - mvMxPy) * h * (vMxPy + vPy) + ihx * (mv0 - mvMx) * h * (vMx + v0));
+    l += h * (ihx * (mwPz - mwMxPz) * h * (wMxPz + wPz) + ihx * (mw0 - mwMx) * h * (wMx + w0));
+    l += nu * ((muPx - T(2) * mu0 + muMx) * ihx * ihx + (muPy - T(2) * mu0 + muMy) * ihy * ihy +
+               (muPz - T(2) * mu0 + muMz) * ihz * ihz);
+    A.lam[0][p] += l;
+  }
+  {  // lambda_v
+    const T vMy = v(0, -1, 0);
+    const T uPxMy = u(1, -1, 0), uMy = u(0, -1, 0), wMyPz = w(0, -1, 1), wMy = w(0, -1, 0);
+    const T mvMy = mv(0, -1, 0), mvPx = mv(1, 0, 0), mvMx = mv(-1, 0, 0), mvPz = mv(0, 0, 1), mvMz = mv(0, 0, -1);
+    const T muPxMy = mu(1, -1, 0), muMy = mu(0, -1, 0), mwMyPz = mw(0, -1, 1), mwMy = mw(0, -1, 0);
+    T l = ihy * (mvPy - mv0) * h * (v0 + vPy) + ihy * (mv0 - mvMy) * h * (vMy + v0);
+    l += h * (ihx * (mvPx - mv0) * h * (uPxMy + uPx) + ihx * (mv0 - mvMx) * h * (uMy + u0));
+    l += h * (ihz * (mvPz - mv0) * h * (wMyPz + wPz) + ihz * (mv0 - mvMz) * h * (wMy + w0));
+    l += h * (ihy * (muPx - muPxMy) * h * (uPxMy + uPx) + ihy * (mu0 - muMy) * h * (uMy + u0));
+    l += h * (ihy * (mwPz - mwMyPz) * h * (wMyPz + wPz) + ihy * (mw0 - mwMy) * h * (wMy + w0));
+    l += nu * ((mvPx - T(2) * mv0 + mvMx) * ihx * ihx + (mvPy - T(2) * mv0 + mvMy) * ihy * ihy +
+               (mvPz - T(2) * mv0 + mvMz) * ihz * ihz);
+    A.lam[1][p] += l;
+  }
+  {  // lambda_w
+    const T wMz = w(0, 0, -1);
+    const T uPxMz = u(1, 0, -1), uMz = u(0, 0, -1), vPyMz = v(0, 1, -1), vMz = v(0, 0, -1);
+    const T mwMz = mw(0, 0, -1), mwPx = mw(1, 0, 0), mwMx = mw(-1, 0, 0), mwPy = mw(0, 1, 0), mwMy = mw(0, -1, 0);
+    const T muPxMz = mu(1, 0, -1), muMz = mu(0, 0, -1), mvPyMz = mv(0, 1, -1), mvMz = mv(0, 0, -1);
+    T l = ihz * (mwPz - mw0) * h * (w0 + wPz) + ihz * (mw0 - mwMz) * h * (wMz + w0);
+    l += h * (ihx * (mwPx - mw0) * h * (uPxMz + uPx) + ihx * (mw0 - mwMx) * h * (uMz + u0));
+    l += h * (ihy * (mwPy - mw0) * h * (vPyMz + vPy) + ihy * (mw0 - mwMy) * h * (vMz + v0));
+    l += h * (ihz * (muPx - muPxMz) * h * (uPxMz + uPx) + ihz * (mu0 - muMz) * h * (uMz + u0));
+    l += h * (ihz * (mvPy - mvPyMz) * h * (vPyMz + vPy) + ihz * (mv0 - mvMz) * h * (vMz + v0));
+    l += nu * ((mwPx - T(2) * mw0 + mwMx) * ihx * ihx + (mwPy - T(2) * mw0 + mwMy) * ihy * ihy +
+               (mwPz - T(2) * mw0 + mwMz) * ihz * ihz);
+    A.lam[2][p] += l;
+  }
+}
+
 // x = -(G^T lam) / V at every cell: the right-hand side of the adjoint Poisson solve.
 template <typename T>
 __global__ void __launch_bounds__(kT) adj_rhs_kernel(const Geom<T> g, const T* __restrict__ l0,
@@ -623,6 +709,10 @@ void launch_rhs_adjoint(fs_grid* G, T* const* u, T* const* mu, T* const* lam) {
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
   const dim3 blk = stencil_block(G), grd = stencil_grid(G, A.X, A.Y);
+  if (G->dim == 3 && G->per[0] && G->per[1] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body) {
+    FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_gather_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+    return;
+  }
   FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
