@@ -421,6 +421,77 @@ __global__ void __launch_bounds__(kT) face_adj_kernel(const FaceAdjArgs<T> A) {
   }
 }
 
+// Projection adjoint and stage split on grids periodic in every direction
+// (uniform metrics, no body): there D^T V = -V G and the cell volume is
+// constant, so P^T lam = lam - G S D lam, the forward projection.  phi = S D lam
+// is solved by the forward path; this kernel forms lam~ = lam - G phi four
+// cells at a time and the stage outputs lam_acc += a lam~, lam_n = b lam~,
+// mu = b dt lam~ (forward Euler: a = 0, b = 1, no lam_acc).
+template <typename T>
+struct ProjAdjArgs {
+  Geom<T> g;
+  const T* lam[3];
+  const T* phi;
+  T* lacc[3];
+  T* lamn[3];
+  T* mu[3];
+  T a, b, dt;
+  int rk;
+  double* bfsum;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kT) proj_adj4_kernel(const ProjAdjArgs<T> A) {
+  const Geom<T>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  double bsum = 0.0;
+  const bool in = i0 < nx && j < ny;
+  if (in) {
+    const size_t row = (size_t)nx * (j + (size_t)ny * k);
+    const Vec4<T> p0 = ld4(A.phi + row + i0);
+    const T ih[3] = {g.ihx, g.ihfy[j], g.ihz};
+    for (int c = 0; c < g.dim; ++c) {
+      Vec4<T> pm;
+      if (c == 0) {
+        const T l = __ldg(A.phi + row + (i0 > 0 ? i0 - 1 : nx - 1));
+        pm = {{l, p0.v[0], p0.v[1], p0.v[2]}};
+      } else if (c == 1) {
+        pm = ld4(A.phi + (size_t)nx * ((j > 0 ? j - 1 : ny - 1) + (size_t)ny * k) + i0);
+      } else {
+        pm = ld4(A.phi + (size_t)nx * (j + (size_t)ny * (k > 0 ? k - 1 : nz - 1)) + i0);
+      }
+      Vec4<T> lw = ld4(A.lam[c] + row + i0);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) lw.v[e] -= (p0.v[e] - pm.v[e]) * ih[c];
+      Vec4<T> ln, m;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        ln.v[e] = A.b * lw.v[e];
+        m.v[e] = A.b * A.dt * lw.v[e];
+      }
+      if (A.rk) {
+        Vec4<T> la = ld4(A.lacc[c] + row + i0);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) la.v[e] += A.a * lw.v[e];
+        st4(A.lacc[c] + row + i0, la);
+      }
+      st4(A.lamn[c] + row + i0, ln);
+      st4(A.mu[c] + row + i0, m);
+      if (c == 0 && A.bfsum)
+        for (int e = 0; e < 4; ++e) bsum += (double)m.v[e];
+    }
+  }
+  // body-force profile: the 32 threads of a warp share the row j
+  if (A.bfsum) {
+    double v = bsum;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && in && v != 0.0) atomicAdd(&A.bfsum[j], v);
+  }
+}
+
 // Outflow face u*[n] = s u[n-1], s = Q_in / sum u[n-1] A: transpose into lam of u^n[n-1].
 template <typename T>
 __global__ void outflow_adj_kernel(const T* __restrict__ u0, const T* __restrict__ lamout, T* __restrict__ lamn0,
@@ -595,6 +666,7 @@ __global__ void rk4_adj_kernel(const double* __restrict__ st, const double* __re
     const double k3x = v2, k3v = acc(x2, v2);
     const double x3 = x0 + h * k3x, v3 = v0 + h * k3v;
     (void)k3x;
+    (void)v3;
     // reverse
     double lx0 = lw1, lv0 = lv1;
     double lk1x = h / 6.0 * lw1, lk2x = h / 3.0 * lw1, lk3x = h / 3.0 * lw1, lk4x = h / 6.0 * lw1;
@@ -726,6 +798,45 @@ void launch_projection_adjoint_solve(fs_grid* G, T* const* lam, T* spec) {
   poisson_solve_inplace<T>(G, spec);
 }
 
+// True when the projection adjoint may take the forward projection (all
+// directions periodic, no body, four-cell rows on 16/32-byte aligned arrays).
+template <typename T>
+bool proj_adj_fast(const fs_grid* G, T* const* lam, T* const* la, T* const* ln, T* const* mu) {
+  if (G->has_body || G->nx % 4) return false;
+  for (int d = 0; d < G->dim; ++d)
+    if (!G->per[d]) return false;
+  const uintptr_t al = 4 * sizeof(T);
+  if ((uintptr_t)G->spec % al) return false;
+  for (int c = 0; c < G->dim; ++c)
+    if ((uintptr_t)lam[c] % al || (uintptr_t)la[c] % al || (uintptr_t)ln[c] % al || (uintptr_t)mu[c] % al)
+      return false;
+  return true;
+}
+
+template <typename T>
+void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double dt, bool rk, double* bfsum,
+                          T* const* la, T* const* ln, T* const* mu) {
+  T* spec = (T*)G->spec;
+  poisson_solve_from_velocity<T>(G, make_div_args<T>(G, lam, nullptr), spec);
+  ProjAdjArgs<T> A;
+  A.g = G->geom<T>();
+  for (int c = 0; c < 3; ++c) {
+    const bool on = c < G->dim;
+    A.lam[c] = on ? lam[c] : nullptr;
+    A.lacc[c] = on ? la[c] : nullptr;
+    A.lamn[c] = on ? ln[c] : nullptr;
+    A.mu[c] = on ? mu[c] : nullptr;
+  }
+  A.phi = spec;
+  A.a = (T)a;
+  A.b = (T)b;
+  A.dt = (T)dt;
+  A.rk = rk ? 1 : 0;
+  A.bfsum = bfsum;
+  const dim3 blk(32, 8), grd((G->nx / 4 + 31) / 32, (G->ny + 7) / 8, G->nz);
+  FS_LAUNCH(G, "proj_adjoint", proj_adj4_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+}
+
 }  // namespace
 
 // Adjoint work buffers (allocated on the first adjoint call of a grid).
@@ -822,7 +933,18 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
     for (int c = 0; c < dim; ++c) cudaMemsetAsync(la[c], 0, comp_count(G, c) * sizeof(T), G->stream);
     // cur = lam of the stage output, starting from lam^{n+1}
     T* cur[3] = {L[0], L[1], L[2]};
+    const bool fast = proj_adj_fast<T>(G, L, la, ln, mu);
     for (int s = 2; s >= 0; --s) {
+      if (fast) {
+        launch_proj_adj_fast<T>(G, cur, Ac[s], Bc[s], dt, true, bfsum, la, ln, mu);
+        launch_rhs_adjoint<T>(G, vs[s], mu, ln);
+        if (s > 0)
+          for (int c = 0; c < dim; ++c) {
+            cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+            cur[c] = L[c];
+          }
+        continue;
+      }
       launch_projection_adjoint_solve<T>(G, cur, spec);
       FaceAdjArgs<T> A{};
       A.g = g;
@@ -888,6 +1010,12 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
                                          (const T*)ib.f[1], (T*)B->lamf[0], (T*)B->lamf[1], sc + 8));
   } else if (G->bc[0][1] == FS_BC_OUTFLOW && !G->per[0]) {
     launch_outflow_flux<T>(G, u);
+  } else if (proj_adj_fast<T>(G, L, la, ln, mu)) {
+    launch_proj_adj_fast<T>(G, L, 0.0, 1.0, dt, false, bfsum, la, ln, mu);
+    launch_rhs_adjoint<T>(G, u, mu, ln);
+    for (int c = 0; c < dim; ++c)
+      cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+    return cuda_check(cudaGetLastError(), "fs_step_adjoint");
   }
   launch_projection_adjoint_solve<T>(G, L, spec);
   FaceAdjArgs<T> A{};
