@@ -214,10 +214,6 @@ def timed_steps(g, u, dt, steps, flush, stream, body=None):
     return [a.elapsed_time(b) for a, b in times]
 
 
-def predictor_bytes(wl, stage_reads):
-    return None
-
-
 def ensemble_leg(args, flush):
     """Batched ensemble of 2-D cylinder flows of uneven size: K steps of every member through one
     CUDA-graph launch, against the same members launched one by one (mixed precision)."""
@@ -374,8 +370,9 @@ def run_ours(args, ws, rank, local):
         slots = 4
         ro = Rollout(g, wl.dt, args.steps, slots=slots)
         ua = [x.clone() for x in u0]
-        lam_T = [torch.ones_like(x) for x in ua]
-        ro.forward(ua)
+        # loss: final kinetic energy (1/2) sum u_T^2 h^3, whose adjoint is lam_T = u_T h^3
+        vol = (2.0 * np.pi / wl.n[0]) ** 3
+        lam_T = [x * vol for x in ro.forward(ua)[0]]
         ro.backward(ua, None, lam_T)        # warm-up of the adjoint kernels and buffers
         flush.fill_(7)
         torch.cuda.synchronize()
@@ -392,9 +389,33 @@ def run_ours(args, ws, rank, local):
                            "steps": args.steps, "slots": slots, "recomputed_steps": ro.recomputed,
                            "forward_ms": fwd_ms, "reverse_ms": adj_ms,
                            "note": "K forward steps then the reverse sweep (recomputation + adjoint steps)"}
+        # the same forward + adjoint on the all-FP64 path, and the distance of the mixed
+        # gradient dJ/du_0 to it
+        lam_mixed = ro.backward(ua, None, lam_T)[0]
+        g64 = grid_from_workload(wl, "fp64", stream=stream)
+        u64 = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev).contiguous() for a in wl.u0]
+        ro64 = Rollout(g64, wl.dt, args.steps, slots=slots)
+        lam64_T = [x * vol for x in ro64.forward(u64)[0]]
+        torch.cuda.synchronize()
+        ea.record(stream)
+        ro64.forward(u64)
+        lam64 = ro64.backward(u64, None, lam64_T)[0]
+        eb.record(stream)
+        torch.cuda.synchronize()
+        f64_ms = max_over_ranks(ws, ea.elapsed_time(eb), dev)
+        gnum = sum(float(((a.double() - b) ** 2).sum()) for a, b in zip(lam_mixed, lam64))
+        gden = sum(float((b ** 2).sum()) for b in lam64)
+        line["fwd_adj"]["fp64_gpu"] = {"value": cells * args.steps * ws / (f64_ms * 1e-3), "unit": "cell-updates/s",
+                                       "ms": f64_ms,
+                                       "mixed_vs_fp64_grad_rel_l2": (gnum / gden) ** 0.5}
+        line["fwd_adj"]["speedup_mixed_over_fp64"] = line["fwd_adj"]["value"] / line["fwd_adj"]["fp64_gpu"]["value"]
+        del g64, u64, ro64
 
     if not args.quick and args.ensemble > 0:
         line["ensemble"] = ensemble_leg(args, flush)
+
+    if not args.quick and args.sweep:
+        line["hbm_sweep"] = [sweep_leg(int(n), stream, flush) for n in args.sweep.split(",") if n]
 
     if rank == 0 and not args.quick and args.cpu_steps > 0:
         rate, secs = cpu_oracle_rate(wl, args.cpu_steps)
@@ -404,6 +425,47 @@ def run_ours(args, ws, rank, local):
                                           % (args.cpu_steps, args.workload, secs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def sweep_leg(n, stream, flush):
+    """The same RK3 step on an n^3 isotropic field whose working set exceeds L2:
+    per-kernel times and the predictor's achieved HBM bandwidth."""
+    from paper_2505_23940_b300 import grid_from_workload
+    dev = torch.device("cuda")
+    wl = S.isotropic_3d(n=n)
+    cells = n ** 3
+    g = grid_from_workload(wl, "mixed", stream=stream)
+    u = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
+    del wl.u0
+    for _ in range(2):
+        g.step(u, wl.dt, 1)
+    steps = 5
+    ms = timed_steps(g, u, wl.dt, steps, flush, stream)
+    g.profile_begin("")
+    timed_steps(g, u, wl.dt, 2, flush, stream)
+    prof = g.profile_end()
+    peak = measured_peaks().get("hbm_gbs", 6400.0)
+    kms = {k: v[1] / 2 for k, v in prof.items()}
+    cnt, tot = prof["predictor"]
+    bpc = (24.0 + 36.0 + 36.0) / 3.0
+    ach = bpc * cells / (tot / cnt * 1e-3) / 1e9
+    out = {"n": [n, n, n], "cells": cells, "ms_per_step": sum(ms) / steps,
+           "value": cells * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
+           "kernels_ms_per_step": dict(sorted(kms.items(), key=lambda kv: -kv[1])),
+           "predictor": {"avg_launch_us": tot / cnt * 1e3, "bytes_per_cell": bpc, "achieved_GBs": ach,
+                         "peak_GBs": peak, "frac": ach / peak}}
+    # every kernel's algorithmic bytes per cell (FP32 fields, FP32 spectrum)
+    per_kernel = {"predictor": bpc, "correct": 28.0, "fft_x_fwd_div": 16.0}
+    for k in kms:
+        if k.startswith("fft_") and k not in per_kernel:
+            per_kernel[k] = 8.0
+    step_bytes = sum(per_kernel.get(k, 0.0) * cells * prof[k][0] / 2 for k in kms)
+    out["step_algorithmic_bytes"] = step_bytes
+    out["step_GBs"] = step_bytes / (sum(ms) / steps * 1e-3) / 1e9
+    out["step_frac"] = out["step_GBs"] / peak
+    del g, u
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -416,6 +478,7 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")
+    ap.add_argument("--sweep", default="256", help="comma-separated n of the n^3 out-of-L2 leg ('' to skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":
