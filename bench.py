@@ -45,26 +45,29 @@ KERNEL_BYTES_PER_CELL = {
 
 # DRAM bytes (read + write) per launch from one ncu capture of the 128^3 mixed RK3
 # workload (ncu flushes caches before each captured launch; writes still resident
-# in L2 at kernel end are not counted), keyed by kernel with the hash of the source
-# file it was measured on: a changed kernel reports traffic null until re-captured.
+# in L2 at kernel end are not counted; the predictor launch is an RK3 stage 2 or 3,
+# which also reads u^n), keyed by kernel with the hash of the source files it was
+# measured on: a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 25234688 + 1075968, "src": "48fa61085730"},
-    "ysolve": {"bytes": 27757056, "src": "2d9c5f98a66a"},
-    "fft_x_fwd_div": {"bytes": 25207552, "src": "2d9c5f98a66a"},
-    "fft_z_fwd": {"bytes": 8411648, "src": "2d9c5f98a66a"},
-    "fft_z_inv": {"bytes": 8412160, "src": "2d9c5f98a66a"},
-    "fft_x_inv": {"bytes": 8405760, "src": "2d9c5f98a66a"},
-    "correct": {"bytes": 33559552 + 256, "src": "48fa61085730"},
+    "predictor": {"bytes": 50384384 + 1818880, "src": "70260af2c2e3"},
+    "fft_x_fwd_div": {"bytes": 25243648, "src": "064fb2dec636"},
+    "fft_z_fwd": {"bytes": 8406784, "src": "064fb2dec636"},
+    "fft_y_solve": {"bytes": 8433664, "src": "064fb2dec636"},
+    "fft_z_inv": {"bytes": 8410624, "src": "064fb2dec636"},
+    "fft_x_inv": {"bytes": 8414720, "src": "064fb2dec636"},
+    "correct": {"bytes": 33561088, "src": "70260af2c2e3"},
 }
 
 
 def src_hash(name):
-    files = {"predictor": "stencil.cu", "divergence": "stencil.cu", "correct": "stencil.cu",
-             "fft": "poisson.cu", "ysolve": "poisson.cu"}
-    for key, fn in files.items():
+    files = {"predictor": ["stencil.cu"], "divergence": ["stencil.cu"], "correct": ["stencil.cu"],
+             "fft": ["poisson.cu", "fft_reg.cuh"], "ysolve": ["poisson.cu"]}
+    for key, fns in files.items():
         if name.startswith(key):
-            p = os.path.join(ROOT, "paper_2505_23940_b300", "csrc", fn)
-            return hashlib.sha1(open(p, "rb").read()).hexdigest()[:12]
+            m = hashlib.sha1()
+            for fn in fns:
+                m.update(open(os.path.join(ROOT, "paper_2505_23940_b300", "csrc", fn), "rb").read())
+            return m.hexdigest()[:12]
     return None
 
 
