@@ -119,3 +119,38 @@ def test_projection_divergence_free():
         u = fluid.outflow_faces(g, u, u)
         un, _ = poisson.project(g, u)
         assert float(fluid.divergence(g, un).abs().max()) < 1e-10
+
+
+@pytest.mark.parametrize("jacobi", [False, True])
+@pytest.mark.parametrize("bcx,bcy,gamma", CASES_2D)
+def test_oracle_cg_matches_dense_lu_2d(bcx, bcy, gamma, jacobi):
+    """The paper's Krylov solver (CG, optionally Jacobi-preconditioned) reaches the same
+    zero volume-mean solution as the dense LU of the assembled operator."""
+    from oracle import krylov
+    wl = S.box_2d(8, 6, bcx, bcy, Lx=1.3, Ly=0.9, stretched=gamma)
+    g = grid_of(wl)
+    b = compatible_rhs(g, 3)
+    p, it, rel = krylov.cg_solve(g, b, tol=1e-14, jacobi=jacobi)
+    pd = dense_solve(g, b)
+    assert rel < 1e-14 and it <= 4 * b.numel()
+    assert float((p - pd).abs().max()) <= 1e-10 * float(pd.abs().max())
+
+
+@pytest.mark.parametrize("bcx,bcy,gamma", CASES_3D)
+def test_oracle_cg_matches_direct_3d(bcx, bcy, gamma):
+    from oracle import krylov
+    wl = S.box_3d(8, 8, 8, bcx, bcy, stretched=gamma)
+    g = grid_of(wl)
+    b = compatible_rhs(g, 4)
+    p, it, rel = krylov.cg_solve(g, b, tol=1e-14, jacobi=True)
+    pd = dense_solve(g, b)
+    assert float((p - pd).abs().max()) <= 1e-10 * float(pd.abs().max())
+
+
+def test_oracle_jacobi_diagonal_is_the_operator_diagonal():
+    from oracle import krylov
+    for wl in [S.box_2d(6, 5, (P, P), (NS, NS), stretched=1.2), S.box_3d(4, 6, 4, (FS, FS), (P, P)),
+               S.box_2d(5, 4, (IN, OUT), (FS, FS))]:
+        g = grid_of(wl)
+        A = -g.cell_volume().reshape(-1, 1) * assembled_L(g)
+        assert torch.allclose(krylov.diag_A(g).reshape(-1), torch.diagonal(A), rtol=1e-13, atol=0)
