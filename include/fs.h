@@ -170,6 +170,25 @@ int fs_step_adjoint(fs_grid* grid, const fs_state* st_n, fs_state* lam,
  * sum) when the operator is singular. */
 int fs_solve_pressure(fs_grid* grid, const double* rhs, double* p);
 
+/* Solve D G p = rhs (Eq. 9) with the paper's Krylov iteration (§2.5 and
+ * Table 1: conjugate gradients): CG on A = -V D G (symmetric positive
+ * semi-definite in the plain inner product, V the cell volumes), optionally
+ * Jacobi-preconditioned by diag(A), from p = 0 until ||r|| <= tol ||r_0|| or
+ * maxit iterations.  The right-hand side's plain mean is removed first (the
+ * constant null space when no pressure is imposed) and the result has zero
+ * volume-weighted mean, the gauge of fs_solve_pressure, which it matches to
+ * the tolerance.  FP64 grids only; every step runs in FP64.
+ *   rhs, p   device doubles with the cell counts' extents; must not alias
+ *   jacobi   0: plain CG (the paper's default), 1: Jacobi preconditioning
+ *   iters    host, iterations taken (may be NULL)
+ *   relres   host, final ||r|| / ||r_0|| (may be NULL)
+ * Synchronises the grid's stream every 8 iterations to test convergence; the
+ * first call allocates a workspace of 3 cells + 16 doubles kept by the grid.
+ * Errors: FS_ERR_ARG, FS_ERR_UNSUPPORTED (mixed grid), FS_ERR_DIVERGED (NaN
+ * residual), FS_ERR_CUDA. */
+int fs_solve_pressure_cg(fs_grid* grid, const double* rhs, double* p, double tol, int maxit, int jacobi,
+                         int* iters, double* relres);
+
 /* Replace the x-momentum source profile (n[1] values, device doubles) used by
  * later steps, e.g. to make it a differentiable parameter.  The grid must
  * have been created with a body_force profile.  Enqueued on the grid's stream. */

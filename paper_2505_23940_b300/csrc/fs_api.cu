@@ -257,7 +257,7 @@ void free_all(fs_grid* G) {
   for (int d = 0; d < 3; ++d) F(G->xf64[d]);
   F(G->hy64); F(G->hfy64);
   for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
-  F(G->spec); F(G->scal); F(G->red);
+  F(G->spec); F(G->scal); F(G->red); F(G->cg);
   F(G->px.tw); F(G->px.dtw); F(G->py.tw); F(G->py.dtw); F(G->pz.tw); F(G->pz.dtw);
   F(G->lamy); F(G->lamxz);
   F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);

@@ -279,6 +279,7 @@ struct fs_grid {
   fs::IBDev ib;
   bool has_body = false;
   void* adj = nullptr;         // adjoint work buffers (adjoint.cu), allocated on first use
+  void* cg = nullptr;          // conjugate-gradient workspace (cg.cu), allocated on first use
 
   // launch parameters (fs_set_tuning; 0 = built-in default)
   int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads

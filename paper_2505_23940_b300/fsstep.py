@@ -69,6 +69,8 @@ def lib():
         L.fs_step_adjoint.argtypes = [c_void_p, POINTER(State), POINTER(State), POINTER(c_double),
                                       POINTER(ParamGrad), c_double]
         L.fs_solve_pressure.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.fs_solve_pressure_cg.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, POINTER(c_int),
+                                           POINTER(c_double)]
         L.fs_forces.argtypes = [c_void_p, POINTER(c_double), POINTER(c_double), POINTER(c_double)]
         L.fs_diagnostics.argtypes = [c_void_p, POINTER(State), POINTER(c_double)]
         L.fs_kernel_launches.argtypes = [c_void_p]
@@ -204,6 +206,14 @@ class Grid:
         p = torch.empty_like(rhs) if p is None else p
         check(lib().fs_solve_pressure(self.h, c_void_p(rhs.data_ptr()), c_void_p(p.data_ptr())))
         return p
+
+    def solve_pressure_cg(self, rhs, p=None, tol=1e-12, maxit=100000, jacobi=False):
+        """Krylov (CG) solve of D G p = rhs on an FP64 grid: returns (p, iterations, relative residual)."""
+        p = torch.empty_like(rhs) if p is None else p
+        it, rel = c_int(0), c_double(0.0)
+        check(lib().fs_solve_pressure_cg(self.h, c_void_p(rhs.data_ptr()), c_void_p(p.data_ptr()), tol, maxit,
+                                         1 if jacobi else 0, byref(it), byref(rel)))
+        return p, it.value, rel.value
 
     def forces(self, with_q=False):
         F = (c_double * 2)()
