@@ -417,6 +417,9 @@ def run_ours(args, ws, rank, local):
     if not args.quick and args.ensemble > 0:
         line["ensemble"] = ensemble_leg(args, flush)
 
+    if not args.quick:
+        line["krylov"] = krylov_leg(wl, stream)
+
     if not args.quick and args.sweep:
         line["hbm_sweep"] = [sweep_leg(int(n), stream, flush) for n in args.sweep.split(",") if n]
 
@@ -428,6 +431,37 @@ def run_ours(args, ws, rank, local):
                                           % (args.cpu_steps, args.workload, secs)}
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def krylov_leg(wl, stream):
+    """The paper's CG pressure solve (fs_solve_pressure_cg, FP64) against the direct solve on
+    the workload's grid, for a seeded zero-mean right-hand side (compatible on periodic grids)."""
+    from paper_2505_23940_b300 import grid_from_workload
+    dev = torch.device("cuda")
+    g = grid_from_workload(wl, "fp64", stream=stream)
+    gen = torch.Generator(device="cpu").manual_seed(3)
+    b = torch.rand(tuple(reversed(wl.n)), dtype=torch.float64, generator=gen).to(dev)
+    b -= b.mean()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    out = {}
+    pd = g.solve_pressure(b)
+    ev[0].record(stream)
+    pd = g.solve_pressure(b)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    out["direct_ms"] = ev[0].elapsed_time(ev[1])
+    for jac in (False, True):
+        g.solve_pressure_cg(b, tol=1e-10, jacobi=jac, maxit=20000)
+        ev[0].record(stream)
+        p, it, rel = g.solve_pressure_cg(b, tol=1e-10, jacobi=jac, maxit=20000)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        out["jacobi_cg" if jac else "cg"] = {
+            "ms": ev[0].elapsed_time(ev[1]), "iterations": it, "relres": rel,
+            "max_diff_to_direct_rel": float((p - pd).abs().max() / pd.abs().max())}
+    out["note"] = "FP64 on the %s grid; tol 1e-10 on ||r|| / ||r0||" % wl.name
+    del g
+    return out
 
 
 def sweep_leg(n, stream, flush):

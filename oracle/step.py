@@ -105,6 +105,35 @@ def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
     return State(unew, w_new, wd_new), dg
 
 
+def step_coupled(g, st, dt, body, kernel=ib.ROMA3, params=None, max_iter=100, tol=1e-5):
+    """Strongly coupled FSI step: the sub-iteration of the paper's strong-coupling
+    procedure (§2.3.3, Algorithm 1), from the fluid state and body state of time level n.
+
+    Iterate k = 1, 2, ...: advance the fluid from u^n with the body kinematics of
+    the current iterate (iterate 0 = the body at level n), take the force of that
+    fluid step, advance the body ODE from its level-n state with that force, and
+    measure xi = |w_k - w_{k-1}|^2 / |w_{k-1}|^2 (the plain |w_k - w_{k-1}|^2 while
+    w_{k-1} = 0).  Stop when xi < tol or after max_iter fluid solves.  One
+    sub-iteration is the weakly coupled step.
+
+    Returns (new State, Diagnostics of the last fluid solve, sub-iterations, last xi).
+    """
+    w_it, wd_it = st.w, st.wd
+    xi = float("inf")
+    k = 0
+    while k < max_iter:
+        new, dg = step(g, State(st.u, w_it, wd_it), dt, "fe", body, kernel, params=None)
+        k += 1
+        w_new, wd_new = body_mod.rk4(params, st.w, st.wd, dg.F, dt)
+        den = float((w_it * w_it).sum())
+        num = float(((w_new - w_it) ** 2).sum())
+        xi = num / den if den > 0.0 else num
+        w_it, wd_it = w_new, wd_new
+        if xi < tol:
+            break
+    return State(new.u, w_it, wd_it), dg, k, xi
+
+
 def kinetic_energy(g, u):
     """1/2 sum over faces of u_c^2 times the face control volume."""
     ke = torch.zeros((), dtype=F64)
