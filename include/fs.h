@@ -194,6 +194,21 @@ int fs_solve_pressure_cg(fs_grid* grid, const double* rhs, double* p, double tol
  * have been created with a body_force profile.  Enqueued on the grid's stream. */
 int fs_set_body_force(fs_grid* grid, const double* fx);
 
+/* Strong fluid-structure coupling (§2.3.3, Algorithm 1).  With max_subiters > 1
+ * every forward-Euler step of a grid with an elastically mounted body
+ * sub-iterates: the fluid is advanced from u^n with the kinematics of the
+ * current body iterate (iterate 0 = the body at level n), the body ODE is
+ * advanced from its level-n state with the force of that fluid solve, until
+ * xi = |w_k - w_{k-1}|^2 / |w_{k-1}|^2 < tol (|w_k - w_{k-1}|^2 while w_{k-1} = 0)
+ * or max_subiters fluid solves.  max_subiters = 1 (the default) is the weakly
+ * coupled step.  Each sub-iteration reads xi on the host (one stream
+ * synchronisation).  fs_step_adjoint returns FS_ERR_UNSUPPORTED for a grid
+ * with max_subiters > 1.  Errors: FS_ERR_ARG (max_subiters < 1, tol <= 0). */
+int fs_set_coupling(fs_grid* grid, int max_subiters, double tol);
+
+/* Sub-iterations and final xi of the last strongly coupled step (host outputs, may be NULL). */
+int fs_coupling_stats(const fs_grid* grid, int* subiters, double* xi);
+
 /* Replace the spring stiffness k of the attached body (Eq. 12). */
 int fs_set_stiffness(fs_grid* grid, double k);
 

@@ -258,6 +258,8 @@ void free_all(fs_grid* G) {
   F(G->hy64); F(G->hfy64);
   for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
   F(G->spec); F(G->scal); F(G->red); F(G->cg);
+  for (int c = 0; c < 3; ++c) F(G->fsi_u[c]);
+  F(G->fsi_b);
   F(G->px.tw); F(G->px.dtw); F(G->py.tw); F(G->py.dtw); F(G->pz.tw); F(G->pz.dtw);
   F(G->lamy); F(G->lamxz);
   F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);
@@ -306,6 +308,71 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
     ib_forces<T>(G, st->body);
     body_rk4(G, st->body, dt);
   }
+}
+
+// xi = |w_new - w_it|^2 / |w_it|^2 (|w_new - w_it|^2 while w_it = 0); the iterate
+// st := the new body state.
+__global__ void couple_kernel(double* __restrict__ st, const double* __restrict__ nb, double* __restrict__ xi) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double num = 0.0, den = 0.0;
+  for (int d = 0; d < 2; ++d) {
+    const double dw = nb[d] - st[d];
+    num += dw * dw;
+    den += st[d] * st[d];
+  }
+  *xi = den > 0.0 ? num / den : num;
+  for (int q = 0; q < 4; ++q) st[q] = nb[q];
+}
+
+// Strongly coupled forward-Euler FSI step (§2.3.3, Algorithm 1): sub-iterate the
+// fluid solve (kinematics of the current body iterate, from u^n) and the body
+// ODE (from the body at level n, with the force of that solve) until the
+// relative change of the displacement falls below fsi_tol, at most fsi_iters
+// fluid solves.  The convergence test reads xi on the host once per
+// sub-iteration.
+template <typename T>
+int step_coupled(fs_grid* G, fs_state* st, double dt, bool want_p) {
+  const size_t es = sizeof(T);
+  size_t n[3];
+  for (int c = 0; c < G->dim; ++c) n[c] = comp_size(G, c);
+  if (!G->fsi_b) {
+    bool ok = cudaMalloc(&G->fsi_b, 16 * sizeof(double)) == cudaSuccess;
+    for (int c = 0; c < G->dim && ok; ++c) ok = cudaMalloc(&G->fsi_u[c], n[c] * es) == cudaSuccess;
+    if (!ok) return set_error(FS_ERR_CUDA, "allocating the coupling workspace");
+  }
+  cudaStream_t s = G->stream;
+  for (int c = 0; c < G->dim; ++c) cudaMemcpyAsync(G->fsi_u[c], st->u[c], n[c] * es, cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(G->fsi_b, st->body, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  T* u[3] = {(T*)st->u[0], (T*)st->u[1], (T*)(G->dim == 3 ? st->u[2] : nullptr)};
+  T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
+  T* spec = (T*)G->spec;
+  double* nb = G->fsi_b + 4;
+  int k = 0;
+  double xi = 0.0;
+  while (k < G->fsi_iters) {
+    if (k > 0)
+      for (int c = 0; c < G->dim; ++c)
+        cudaMemcpyAsync(st->u[c], G->fsi_u[c], n[c] * es, cudaMemcpyDeviceToDevice, s);
+    ib_prepare<T>(G, st->body);
+    launch_outflow_flux<T>(G, u);
+    launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
+    poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, st->body), spec);
+    launch_correct<T>(G, us, spec, u);
+    ib_forces<T>(G, st->body);
+    cudaMemcpyAsync(nb, G->fsi_b, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    body_rk4(G, nb, dt);
+    FS_LAUNCH(G, "couple", couple_kernel<<<1, 32, 0, s>>>(st->body, nb, G->fsi_b + 8));
+    ++k;
+    cudaError_t e = cudaMemcpyAsync(&xi, G->fsi_b + 8, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_check(e, "fs_step (strong coupling)");
+    if (!(xi == xi)) return set_error(FS_ERR_DIVERGED, "fs_step: NaN in the coupling iteration");
+    if (xi < G->fsi_tol) break;
+  }
+  if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / dt);
+  G->fsi_last_iters = k;
+  G->fsi_last_xi = xi;
+  return FS_OK;
 }
 
 }  // namespace
@@ -703,6 +770,11 @@ int fs_step(fs_grid* G, fs_state* st, double dt, int nsteps) {
       h = 0.5 * hmin / std::max(d[0], 1e-30);
     }
     const bool want_p = st->p && s == nsteps - 1;
+    if (G->has_body && G->fsi_iters > 1 && G->ib.mass > 0) {
+      const int rc = G->prec == FS_MIXED ? step_coupled<float>(G, st, h, want_p) : step_coupled<double>(G, st, h, want_p);
+      if (rc != FS_OK) return rc;
+      continue;
+    }
     if (G->prec == FS_MIXED) step_once<float>(G, st, h, want_p);
     else step_once<double>(G, st, h, want_p);
   }
@@ -717,6 +789,8 @@ int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const doubl
     if (!st_n->u[c] || !lam->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
   if (G->has_body) {
     if (!st_n->body || !lam->body) return set_error(FS_ERR_ARG, "a grid with a body needs st_n->body and lam->body");
+    if (G->fsi_iters > 1)
+      return set_error(FS_ERR_UNSUPPORTED, "adjoint of the strongly coupled (sub-iterated) FSI step");
     if (G->ib.omega != 0.0)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of a body with a prescribed surface rotation");
   }
@@ -755,6 +829,21 @@ int fs_set_body_force(fs_grid* G, const double* fx) {
   if (G->bforce.empty()) return set_error(FS_ERR_STATE, "the grid was created without a body_force profile");
   FS_LAUNCH(G, "set_body_force", bf_convert_kernel<<<(G->ny + 127) / 128, 128, 0, G->stream>>>(fx, G->bf64, G->bf32, G->ny));
   return cuda_check(cudaGetLastError(), "fs_set_body_force");
+}
+
+int fs_set_coupling(fs_grid* G, int max_subiters, double tol) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (max_subiters < 1 || !(tol > 0.0)) return set_error(FS_ERR_ARG, "fs_set_coupling: max_subiters >= 1, tol > 0");
+  G->fsi_iters = max_subiters;
+  G->fsi_tol = tol;
+  return FS_OK;
+}
+
+int fs_coupling_stats(const fs_grid* G, int* subiters, double* xi) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (subiters) *subiters = G->fsi_last_iters;
+  if (xi) *xi = G->fsi_last_xi;
+  return FS_OK;
 }
 
 int fs_set_stiffness(fs_grid* G, double k) {

@@ -280,6 +280,13 @@ struct fs_grid {
   bool has_body = false;
   void* adj = nullptr;         // adjoint work buffers (adjoint.cu), allocated on first use
   void* cg = nullptr;          // conjugate-gradient workspace (cg.cu), allocated on first use
+  // strong FSI coupling (fs_set_coupling): sub-iterations per step, tolerance, workspace
+  int fsi_iters = 1;
+  double fsi_tol = 1e-5;
+  void* fsi_u[3] = {nullptr, nullptr, nullptr};   // velocity at time level n
+  double* fsi_b = nullptr;     // [0..3] body at level n, [4..7] new iterate, [8] xi
+  int fsi_last_iters = 0;
+  double fsi_last_xi = 0.0;
 
   // launch parameters (fs_set_tuning; 0 = built-in default)
   int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads

@@ -81,6 +81,8 @@ def lib():
         L.fs_set_tuning.argtypes = [c_void_p, ctypes.c_char_p, c_int]
         L.fs_set_body_force.argtypes = [c_void_p, c_void_p]
         L.fs_set_stiffness.argtypes = [c_void_p, c_double]
+        L.fs_set_coupling.argtypes = [c_void_p, c_int, c_double]
+        L.fs_coupling_stats.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
         L.fs_forces_device.argtypes = [c_void_p, c_void_p]
         L.fs_component_stats_noalloc.argtypes = [c_void_p, c_int, POINTER(c_int), c_double, c_void_p, c_void_p,
                                                  c_void_p]
@@ -237,6 +239,15 @@ class Grid:
         """Enqueue later work on a torch.cuda.Stream (e.g. a graph-capture branch)."""
         self.stream = stream
         check(lib().fs_set_stream(self.h, c_void_p(stream.cuda_stream)))
+
+    def set_coupling(self, max_subiters, tol=1e-5):
+        """Strong FSI coupling: sub-iterate each step up to max_subiters fluid solves (1 = weak)."""
+        check(lib().fs_set_coupling(self.h, int(max_subiters), float(tol)))
+
+    def coupling_stats(self):
+        k, xi = c_int(0), c_double(0.0)
+        check(lib().fs_coupling_stats(self.h, byref(k), byref(xi)))
+        return k.value, xi.value
 
     def set_stiffness(self, k):
         check(lib().fs_set_stiffness(self.h, float(k)))

@@ -173,3 +173,33 @@ def test_zero_steps_is_identity():
     wl = S.taylor_green_2d(16, 0.01)
     gp = run_gpu(wl, 0)
     assert field_err(gp["u"], [torch.tensor(a) for a in wl.u0]) == 0.0
+
+
+@pytest.mark.parametrize("active", [(False, True), (True, True)])
+def test_strong_coupling_fp64(active):
+    """Strongly coupled FSI (Algorithm 1, 1-DOF and 2-DOF) against the oracle's sub-iteration:
+    fields, body state and the number of sub-iterations of every step."""
+    from oracle.step import step_coupled
+    from helpers import body_of
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, centre_d=(2.0, 2.0), precision="fp64",
+                       seed=3, perturb=0.05, mass_ratio=1.0)
+    wl.body.w0 = (0.02, 0.05)
+    wl.body.active = active
+    g = grid_of(wl)
+    body, params = body_of(wl)
+    st = O.State([torch.tensor(a, dtype=torch.float64) for a in wl.u0],
+                 torch.tensor(wl.body.w0, dtype=torch.float64), torch.tensor(wl.body.wd0, dtype=torch.float64))
+    G = grid_from_workload(wl, "fp64")
+    G.set_coupling(30, 1e-10)
+    u = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in wl.u0]
+    bt = body_tensor(wl)
+    for _ in range(4):
+        st, _, k, xi = step_coupled(g, st, wl.dt, body, wl.kernel, params, max_iter=30, tol=1e-10)
+        G.step(u, wl.dt, 1, body=bt)
+        kg, xig = G.coupling_stats()
+        assert kg == k and k > 1
+    torch.cuda.synchronize()
+    assert field_err([x.cpu() for x in u], st.u) < TOL64
+    assert float((bt[:2].cpu() - st.w).abs().max()) < 1e-12
+    assert float((bt[2:].cpu() - st.wd).abs().max()) < 1e-11
