@@ -9,6 +9,7 @@ Forward Euler (the scheme of every run in §3):
   3. pressure Poisson Eq. (9) and correction Eq. (10), with phi = dt p / rho:
         L phi = D[(1 - eps) u* + eps u_c],   u^{n+1} = u* - G phi
   4. q_i from f (Eq. 20), F = rho sum q_i dV_i, then the body by RK4 (Eq. 12)
+A static 3-D body (ib3d.Boxes) is forced the same way with u_s = u_c = 0.
 
 Runge-Kutta ("explicit Runge-Kutta", §2.5; tableau not given): the strong-
 stability-preserving three-stage scheme of Shu and Osher with a projection
@@ -27,7 +28,7 @@ by central finite differences (tests/test_oracle_adjoint.py).
 import torch
 
 from . import body as body_mod
-from . import fluid, ib, poisson
+from . import fluid, ib, ib3d, poisson
 from .grid import F64
 
 SSPRK3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
@@ -85,7 +86,15 @@ def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
         return State(v, st.w, st.wd), dg
 
     eps = ut = ucl = masks = None
-    if body is not None:
+    static3d = isinstance(body, ib3d.Boxes)
+    if static3d:
+        # body at rest: u_s = 0 on every forced face, u_c = 0
+        masks = ib3d.classify(g, body)
+        ut = [torch.zeros(g.shape(c), dtype=F64) for c in range(g.dim)]
+        ucl = ut
+        eps = [m[0] | m[1] for m in masks]
+        dg.eps = eps
+    elif body is not None:
         masks = ib.classify(g, body, st.w)
         ut, ucl = ib.target_velocity(g, body, kernel, st.w, st.wd, masks)
         eps = [m[0] | m[1] for m in masks]
@@ -97,7 +106,9 @@ def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
     dg.phi = phi
     dg.f = f
     w_new, wd_new = st.w, st.wd
-    if body is not None:
+    if static3d:
+        dg.q, dg.F = ib3d.marker_forces(g, body, kernel, f)
+    elif body is not None:
         q, F, torque = ib.marker_forces(g, body, kernel, st.w, f)
         dg.q, dg.F, dg.torque = q, F, torque
         if params is not None:
