@@ -419,6 +419,8 @@ def run_ours(args, ws, rank, local):
 
     if not args.quick:
         line["krylov"] = krylov_leg(wl, stream)
+    if not args.quick and args.ib_stress:
+        line["ib_stress"] = ib_stress_leg(stream, flush)
 
     if not args.quick and args.sweep:
         line["hbm_sweep"] = [sweep_leg(int(n), stream, flush) for n in args.sweep.split(",") if n]
@@ -461,6 +463,48 @@ def krylov_leg(wl, stream):
             "max_diff_to_direct_rel": float((p - pd).abs().max() / pd.abs().max())}
     out["note"] = "FP64 on the %s grid; tol 1e-10 on ||r|| / ||r0||" % wl.name
     del g
+    return out
+
+
+def ib_stress_leg(stream, flush):
+    """Static 3-D immersed boxes at scale: 256^3 rough-wall channel (cubes of 8 cells every 12 cells
+    on both walls, markers every h/2: about 1.35 M markers), mixed precision, forward Euler."""
+    from paper_2505_23940_b300 import grid_from_workload
+    dev = torch.device("cuda")
+    wl = S.rough_channel_3d(256, 256, 256, cube=8, pitch=12, both_walls=True, marker_spacing=0.5)
+    nm = wl.boxes.X.shape[0]
+    g = grid_from_workload(wl, "mixed", stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.set_boxes(wl.boxes.boxes, wl.boxes.X, wl.boxes.dV, wl.kernel)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    classify_ms = e0.elapsed_time(e1)
+    u = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
+    del wl.u0
+    for _ in range(2):
+        g.step(u, wl.dt, 1)
+    steps = 5
+    ms = timed_steps(g, u, wl.dt, steps, flush, stream)
+    g.profile_begin("")
+    timed_steps(g, u, wl.dt, 2, flush, stream)
+    prof = g.profile_end()
+    cnt, tot = prof["ib3_force_gather"]
+    gather_us = tot / cnt * 1e3
+    # algorithmic bytes of the gather: 27 four-byte reads of f per marker and component (3-point
+    # kernel), the marker position and volume (32 B) and q (24 B) per marker
+    gbytes = nm * (3 * 27 * 4 + 32 + 24)
+    F = g.box_forces()
+    out = {"n": [256, 256, 256], "cells": 256 ** 3, "markers": nm, "boxes": int(wl.boxes.boxes.shape[0]),
+           "classify_ms": classify_ms, "ms_per_step": sum(ms) / steps,
+           "value": 256 ** 3 * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
+           "force_gather_us": gather_us, "force_gather_markers_per_s": nm / (gather_us * 1e-6),
+           "force_gather_GBs": gbytes / (gather_us * 1e-6) / 1e9,
+           "kernels_ms_per_step": {k: v[1] / 2 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+           "F": list(F)}
+    del g, u
+    torch.cuda.empty_cache()
     return out
 
 
@@ -516,6 +560,7 @@ def main():
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")
     ap.add_argument("--sweep", default="256", help="comma-separated n of the n^3 out-of-L2 leg ('' to skip)")
+    ap.add_argument("--ib-stress", type=int, default=1, help="run the 256^3 static-box leg (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -142,6 +142,23 @@ int fs_field_extent(const fs_grid* grid, int comp, int ext[3]);
  * (3-D grid, RK3 grid). */
 int fs_set_ib_markers(fs_grid* grid, const fs_body_desc* body);
 
+/* Attach a static 3-D body made of axis-aligned boxes (the paper's cube
+ * roughness and obstacle cases, §3.4, forced as in §2.3.3): faces strictly
+ * inside a box are solid, non-solid faces with a solid same-component
+ * neighbour are IB faces, and both are forced to the velocity of a body at
+ * rest, u_s = u_c = 0 (Eqs. 5, 18, 23).  The markers only carry the force,
+ * q_i = -sum_faces f delta_h(x - X_i) dv (Eq. 20, 3-D tensor-product delta of
+ * the chosen kernel), F = rho sum_i q_i dV_i.  The classification is done once,
+ * here.  Replaces any previous box body.
+ *   boxes  host, nbox x 6 doubles: x0, x1, y0, y1, z0, z1 (x0 < x1 ...)
+ *   X      host, nm x 3 marker positions;  dV  host, nm marker volumes
+ * fs_forces then returns F[3], torque 0 and q (nm x 3).  Requirements: 3-D
+ * grid, forward Euler, uniform x, y and z.  fs_step_adjoint returns
+ * FS_ERR_UNSUPPORTED on such a grid.  Errors: FS_ERR_ARG, FS_ERR_UNSUPPORTED,
+ * FS_ERR_CUDA. */
+int fs_set_ib_boxes(fs_grid* grid, int nbox, const double* boxes, int nm, const double* X, const double* dV,
+                    int delta_kernel);
+
 /* Advance st by nsteps time steps of size dt (Eqs. 4-10, 18-23, 12).
  * dt > 0: fixed step, no host synchronisation.
  * dt <= 0: adaptive step dt = 0.5 * min(h) / max|u| from the state before
@@ -217,7 +234,8 @@ int fs_set_stiffness(fs_grid* grid, double k);
 int fs_forces_device(fs_grid* grid, double* F);
 
 /* Hydrodynamic force of the last step (Eq. 20 with F = rho sum_i q_i dV_i).
- * Host outputs: F[dim], torque[1], q[nm * 2] marker forces (q may be NULL).
+ * Host outputs: F[dim], torque[1], q[nm * 2] marker forces (q may be NULL);
+ * for a static 3-D box body F[3], torque 0 and q[nm * 3].
  * Synchronises the grid's stream.  FS_ERR_STATE before the first FSI step. */
 int fs_forces(fs_grid* grid, double* F, double* torque, double* q);
 

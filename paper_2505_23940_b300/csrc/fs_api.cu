@@ -308,6 +308,7 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
     ib_forces<T>(G, st->body);
     body_rk4(G, st->body, dt);
   }
+  if (G->has_ib3) ib3_forces<T>(G);
 }
 
 // xi = |w_new - w_it|^2 / |w_it|^2 (|w_new - w_it|^2 while w_it = 0); the iterate
@@ -592,6 +593,7 @@ int fs_destroy_grid(fs_grid* G) {
   cudaStreamSynchronize(G->stream);
   for (cudaEvent_t e : G->prof_pool) cudaEventDestroy(e);
   free_adj_buffers(G->adj);
+  free_ib3(G);
   free_all(G);
   delete G;
   return FS_OK;
@@ -791,6 +793,9 @@ int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const doubl
     if (!st_n->body || !lam->body) return set_error(FS_ERR_ARG, "a grid with a body needs st_n->body and lam->body");
     if (G->fsi_iters > 1)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of the strongly coupled (sub-iterated) FSI step");
+  }
+  if (G->has_ib3) {
+    return set_error(FS_ERR_UNSUPPORTED, "adjoint of a grid with a static 3-D box body");
     if (G->ib.omega != 0.0)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of a body with a prescribed surface rotation");
   }
@@ -855,6 +860,9 @@ int fs_set_stiffness(fs_grid* G, double k) {
 
 int fs_forces_device(fs_grid* G, double* F) {
   if (!G || !F) return set_error(FS_ERR_ARG, "NULL argument");
+  if (G->has_ib3)
+    return cuda_check(cudaMemcpyAsync(F, G->ib3.F, 3 * sizeof(double), cudaMemcpyDeviceToDevice, G->stream),
+                      "fs_forces_device");
   if (!G->has_body) return set_error(FS_ERR_STATE, "no body attached");
   return cuda_check(cudaMemcpyAsync(F, G->ib.F, 3 * sizeof(double), cudaMemcpyDeviceToDevice, G->stream),
                     "fs_forces_device");
@@ -862,6 +870,25 @@ int fs_forces_device(fs_grid* G, double* F) {
 
 int fs_forces(fs_grid* G, double* F, double* torque, double* q) {
   if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (G->has_ib3) {
+    if (!G->ib3.have_forces) return set_error(FS_ERR_STATE, "no step has run with the box body");
+    double h[3];
+    cudaError_t e = cudaMemcpyAsync(h, G->ib3.F, 3 * sizeof(double), cudaMemcpyDeviceToHost, G->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_forces");
+    if (F)
+      for (int d = 0; d < 3; ++d) F[d] = h[d];
+    if (torque) *torque = 0.0;
+    if (q) {
+      const int nm = G->ib3.nm;
+      std::vector<double> qs(3 * (size_t)nm);
+      e = cudaMemcpy(qs.data(), G->ib3.q, qs.size() * sizeof(double), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_check(e, "fs_forces q");
+      for (int m = 0; m < nm; ++m)
+        for (int d = 0; d < 3; ++d) q[3 * (size_t)m + d] = qs[(size_t)d * nm + m];
+    }
+    return FS_OK;
+  }
   if (!G->has_body || !G->ib.have_forces) return set_error(FS_ERR_STATE, "no FSI step has run");
   double h[4];
   cudaError_t e = cudaMemcpyAsync(h, G->ib.F, 3 * sizeof(double), cudaMemcpyDeviceToHost, G->stream);

@@ -234,6 +234,20 @@ struct IBDev {
   double poly_bb[4] = {0, 0, 0, 0};        // rest polygon bounding box xmin, xmax, ymin, ymax
 };
 
+// Static 3-D body made of axis-aligned boxes (ib3.cu): forced faces take zero velocity.
+struct IB3Dev {
+  int nbox = 0, nm = 0;
+  int kernel = FS_ROMA3;
+  double* boxes = nullptr;                  // device, nbox x 6
+  double* X = nullptr;                      // device, marker x, y, z (SoA, 3 * nm)
+  double* dV = nullptr;                     // device, marker volumes
+  uint8_t* flags[3] = {nullptr, nullptr, nullptr};   // per face: bit0 solid, bit1 IB
+  void* f[3] = {nullptr, nullptr, nullptr}; // direct-forcing term f of Eq. (5) (field precision)
+  double* q = nullptr;                      // marker forces (3 * nm, SoA)
+  double* F = nullptr;                      // [Fx, Fy, Fz]
+  bool have_forces = false;
+};
+
 }  // namespace fs
 
 struct fs_grid {
@@ -278,6 +292,8 @@ struct fs_grid {
 
   fs::IBDev ib;
   bool has_body = false;
+  fs::IB3Dev ib3;
+  bool has_ib3 = false;
   void* adj = nullptr;         // adjoint work buffers (adjoint.cu), allocated on first use
   void* cg = nullptr;          // conjugate-gradient workspace (cg.cu), allocated on first use
   // strong FSI coupling (fs_set_coupling): sub-iterations per step, tolerance, workspace
@@ -322,6 +338,9 @@ template <typename T> void poisson_solve_from_velocity(fs_grid* g, const fs::Div
 template <typename T> void ib_prepare(fs_grid* g, const double* body_state);
 template <typename T> void ib_forces(fs_grid* g, const double* body_state);
 void body_rk4(fs_grid* g, double* body_state, double dt);
+// ib3.cu
+template <typename T> void ib3_forces(fs_grid* g);
+void free_ib3(fs_grid* g);
 // adjoint.cu
 template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state* lam, const double* dJdF,
                                        fs_param_grad* pg, double dt);

@@ -47,6 +47,8 @@ struct PredArgs {
   const double* yf;
   const double* oscale;
   T ihy0;                    // 1 / h_y of a uniform periodic y (predictor3_kernel<T, true>)
+  const uint8_t* flags3[3];  // static 3-D body (boxes): per-face flags, forced faces take u_s = 0
+  T* fout3[3];               // and the forcing term f on every face (0 off forced faces)
 };
 
 // Velocity access around the face (i, j, k) with every boundary rule (ldv).
@@ -218,10 +220,15 @@ __device__ __forceinline__ void predict_face(const PredArgs<T>& A, const Acc& U,
         v = ut;                          // u* = u + dt (R + f) = u_s on forced faces
       }
     }
+    if (A.flags3[0] && A.flags3[C][t]) {   // static 3-D body: u_s = 0
+      fval = -R - u0 / A.dt;
+      v = T(0);
+    }
     res = (A.a != T(0)) ? A.a * A.un[C][t] + A.b * v : A.b * v;
   }
   A.out[C][t] = res;
   if (C < 2 && A.fout[0]) A.fout[C][t] = fval;
+  if (A.fout3[0]) A.fout3[C][t] = fval;
 }
 
 // One thread per cell position (i, j, k) computes every component's face there.
@@ -395,6 +402,15 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
     ov += a * A.un[1][v00 + i];
     ow += a * A.un[2][r00 + i];
   }
+  if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
+    T fu = T(0), fv = T(0), fw = T(0);
+    if (A.flags3[0][r00 + i]) { fu = -Ru - n.u000 / dt; ou = T(0); }
+    if (A.flags3[1][v00 + i]) { fv = -Rv - n.v000 / dt; ov = T(0); }
+    if (A.flags3[2][r00 + i]) { fw = -Rw - n.w000 / dt; ow = T(0); }
+    A.fout3[0][r00 + i] = fu;
+    A.fout3[1][v00 + i] = fv;
+    A.fout3[2][r00 + i] = fw;
+  }
   if (j < ny) {
     A.out[0][r00 + i] = ou;
     A.out[2][r00 + i] = ow;
@@ -492,6 +508,25 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
       ou.v[e] += a * pu.v[e];
       ov.v[e] += a * pv.v[e];
       ow.v[e] += a * pw.v[e];
+    }
+  }
+  if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
+    const uchar4 fl[3] = {*reinterpret_cast<const uchar4*>(A.flags3[0] + r00 + i0),
+                          *reinterpret_cast<const uchar4*>(A.flags3[1] + v00 + i0),
+                          *reinterpret_cast<const uchar4*>(A.flags3[2] + r00 + i0)};
+    Vec4<float>* o3[3] = {&ou, &ov, &ow};
+    const int rows[3] = {r00, v00, r00};
+    for (int c = 0; c < 3; ++c) {
+      const unsigned char f4[4] = {fl[c].x, fl[c].y, fl[c].z, fl[c].w};
+      Vec4<float> fo = {{0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (f4[e]) {
+          // u* = u + dt R, so R = (u* - u) / dt and f = -R - u / dt = -u* / dt
+          fo.v[e] = -o3[c]->v[e] / dt;
+          o3[c]->v[e] = 0.f;
+        }
+      st4(A.fout3[c] + rows[c] + i0, fo);
     }
   }
   if (j < ny) {
@@ -742,6 +777,10 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   A.yf = G->xf64[1];
   A.oscale = G->scal;
   A.ihy0 = (T)(1.0 / G->h[1][0]);
+  for (int c = 0; c < 3; ++c) {
+    A.flags3[c] = G->has_ib3 ? G->ib3.flags[c] : nullptr;
+    A.fout3[c] = G->has_ib3 ? (T*)G->ib3.f[c] : nullptr;
+  }
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
   if (G->dim == 3 && G->per[0] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body && G->ny >= 4) {

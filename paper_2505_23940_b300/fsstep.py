@@ -82,6 +82,8 @@ def lib():
         L.fs_set_body_force.argtypes = [c_void_p, c_void_p]
         L.fs_set_stiffness.argtypes = [c_void_p, c_double]
         L.fs_set_coupling.argtypes = [c_void_p, c_int, c_double]
+        L.fs_set_ib_boxes.argtypes = [c_void_p, c_int, POINTER(c_double), c_int, POINTER(c_double), POINTER(c_double),
+                                      c_int]
         L.fs_coupling_stats.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
         L.fs_forces_device.argtypes = [c_void_p, c_void_p]
         L.fs_component_stats_noalloc.argtypes = [c_void_p, c_int, POINTER(c_int), c_double, c_void_p, c_void_p,
@@ -217,6 +219,17 @@ class Grid:
                                          1 if jacobi else 0, byref(it), byref(rel)))
         return p, it.value, rel.value
 
+    def box_forces(self, with_q=False):
+        """Force of the last step on the static 3-D box body: (F_x, F_y, F_z) [, q (nm, 3)]."""
+        F = (c_double * 3)()
+        tq = c_double()
+        nm = self.n_box_markers
+        q = (c_double * (3 * nm))() if with_q else None
+        check(lib().fs_forces(self.h, F, byref(tq), q))
+        if with_q:
+            return (F[0], F[1], F[2]), [(q[3 * i], q[3 * i + 1], q[3 * i + 2]) for i in range(nm)]
+        return F[0], F[1], F[2]
+
     def forces(self, with_q=False):
         F = (c_double * 2)()
         tq = c_double()
@@ -239,6 +252,16 @@ class Grid:
         """Enqueue later work on a torch.cuda.Stream (e.g. a graph-capture branch)."""
         self.stream = stream
         check(lib().fs_set_stream(self.h, c_void_p(stream.cuda_stream)))
+
+    def set_boxes(self, boxes, X, dV, kernel):
+        """Static 3-D body: boxes (nb, 6), markers X (nm, 3), volumes dV (nm,), delta kernel."""
+        import numpy as np
+        b, bp = _dptr(np.asarray(boxes, dtype=np.float64).reshape(-1, 6))
+        x, xp = _dptr(np.asarray(X, dtype=np.float64).reshape(-1, 3))
+        v, vp = _dptr(np.asarray(dV, dtype=np.float64).reshape(-1))
+        check(lib().fs_set_ib_boxes(self.h, b.shape[0], bp, x.shape[0], xp, vp, int(kernel)))
+        self.n_box_markers = x.shape[0]
+        self.has_boxes = True
 
     def set_coupling(self, max_subiters, tol=1e-5):
         """Strong FSI coupling: sub-iterate each step up to max_subiters fluid solves (1 = weak)."""

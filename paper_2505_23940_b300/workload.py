@@ -16,6 +16,9 @@ def grid_from_workload(wl, precision=None, stream=None):
     if b is not None:
         g.set_body(b.X0, b.Y0, b.ds, b.centre, b.omega, b.mass, b.stiffness, b.damping, b.active,
                    kernel=wl.kernel)
+    bx = getattr(wl, "boxes", None)
+    if bx is not None:
+        g.set_boxes(bx.boxes, bx.X, bx.dV, wl.kernel)
     return g
 
 

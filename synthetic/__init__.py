@@ -43,6 +43,13 @@ class BodySpec:
 
 
 @dataclass
+class BoxSpec:
+    boxes: np.ndarray         # (nb, 6) x0, x1, y0, y1, z0, z1
+    X: np.ndarray             # (nm, 3) surface marker positions
+    dV: np.ndarray            # (nm,) marker volumes (surface area per marker x h)
+
+
+@dataclass
 class Workload:
     name: str
     dim: int
@@ -60,6 +67,7 @@ class Workload:
     kernel: int = ROMA3
     body_force: Optional[np.ndarray] = None
     body: Optional[BodySpec] = None
+    boxes: Optional[BoxSpec] = None
     u0: List[np.ndarray] = field(default_factory=list)   # (ez, ey, ex) arrays per component
 
     def cells(self):
@@ -298,3 +306,73 @@ def box_3d(nx, ny, nz, bcx, bcy, bcz=(PERIODIC, PERIODIC), L=(1.0, 1.0, 1.0), st
     yf = (L[1] / 2) * (1 + tanh_faces(ny, stretched)) if stretched > 0 else uniform_faces(ny, L[1])
     xf = [uniform_faces(nx, L[0]), yf, uniform_faces(nz, L[2])]
     return Workload("box_3d", 3, [nx, ny, nz], xf, [bcx, bcy, bcz], bc_val, nu)
+
+
+def box_markers(box, spacing, h):
+    """Markers on the six faces of a box at a lattice of the given spacing (cell-centred on each face);
+    dV = (area per marker) * h, the shell of one grid spacing."""
+    x0, x1, y0, y1, z0, z1 = box
+    pts, vol = [], []
+
+    def lattice(a0, a1):
+        n = max(1, int(round((a1 - a0) / spacing)))
+        return a0 + (np.arange(n) + 0.5) * (a1 - a0) / n, (a1 - a0) / n
+
+    ax, dx = lattice(x0, x1)
+    ay, dy = lattice(y0, y1)
+    az, dz = lattice(z0, z1)
+    for xv in (x0, x1):
+        Y, Z = np.meshgrid(ay, az, indexing="ij")
+        pts.append(np.stack([np.full(Y.size, xv), Y.ravel(), Z.ravel()], axis=1))
+        vol.append(np.full(Y.size, dy * dz * h))
+    for yv in (y0, y1):
+        X, Z = np.meshgrid(ax, az, indexing="ij")
+        pts.append(np.stack([X.ravel(), np.full(X.size, yv), Z.ravel()], axis=1))
+        vol.append(np.full(X.size, dx * dz * h))
+    for zv in (z0, z1):
+        X, Y = np.meshgrid(ax, ay, indexing="ij")
+        pts.append(np.stack([X.ravel(), Y.ravel(), np.full(X.size, zv)], axis=1))
+        vol.append(np.full(X.size, dx * dy * h))
+    return np.concatenate(pts), np.concatenate(vol)
+
+
+def rough_channel_3d(nx=32, ny=32, nz=32, L=(2.0, 2.0, 2.0), cube=4, pitch=8, nu=0.01, dt=None, seed=4,
+                     kernel=ROMA3, both_walls=False, noise=0.1, marker_spacing=1.0):
+    """Channel with cube roughness on the wall(s): uniform grid, x and z periodic, no-slip y walls,
+    constant x-momentum source f_x = 1, cubes of `cube` cells at a pitch of `pitch` cells
+    (the rough-wall case of §3.4 in miniature), surface markers every `marker_spacing` h.
+    Initial field: the laminar profile
+    u = (1 - y^2) (y in [-1, 1]) plus `noise` seeded uniform noise on every component."""
+    rng = np.random.default_rng(seed)
+    xf = [uniform_faces(nx, L[0]), uniform_faces(ny, L[1], -L[1] / 2), uniform_faces(nz, L[2])]
+    h = L[0] / nx
+    bc = [(PERIODIC, PERIODIC), (NOSLIP, NOSLIP), (PERIODIC, PERIODIC)]
+    boxes = []
+    walls = [(-L[1] / 2, 1)] + ([(L[1] / 2, -1)] if both_walls else [])
+    for i0 in range(pitch // 2, nx, pitch):
+        for k0 in range(pitch // 2, nz, pitch):
+            for yw, sgn in walls:
+                x0 = xf[0][0] + (i0 - cube / 2) * h
+                z0 = xf[2][0] + (k0 - cube / 2) * h
+                ya, yb = sorted((yw, yw + sgn * cube * h))
+                boxes.append([x0, x0 + cube * h, ya, yb, z0, z0 + cube * h])
+    X, dV = [], []
+    for b in boxes:
+        x, v = box_markers(b, marker_spacing * h, h)
+        X.append(x)
+        dV.append(v)
+    spec = BoxSpec(np.array(boxes), np.concatenate(X), np.concatenate(dV))
+    nn = [nx, ny, nz]
+    u0 = []
+    for c in range(3):
+        e = _ext(nn, c, bc)
+        shp = (e[2], e[1], e[0])
+        x, y, z = _face_positions(nn, xf, c, bc)
+        base = (1.0 - (2.0 * y / L[1]) ** 2) if c == 0 else 0.0
+        fld = base + noise * rng.uniform(-1.0, 1.0, size=shp)
+        if c == 1:
+            fld[:, 0, :] = 0.0
+            fld[:, -1, :] = 0.0
+        u0.append(np.ascontiguousarray(np.broadcast_to(fld, shp), dtype=np.float64))
+    return Workload("rough_channel_3d", 3, nn, xf, bc, None, nu, dt=dt if dt else 0.2 * h, steps=10,
+                    precision="fp64", kernel=kernel, body_force=np.ones(ny), boxes=spec, u0=u0)

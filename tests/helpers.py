@@ -22,6 +22,10 @@ def state_of(wl, u=None):
 
 
 def body_of(wl):
+    bx = getattr(wl, "boxes", None)
+    if bx is not None:
+        from oracle import ib3d
+        return ib3d.Boxes(bx.boxes, bx.X, bx.dV), None
     b = wl.body
     if b is None:
         return None, None

@@ -203,3 +203,27 @@ def test_strong_coupling_fp64(active):
     assert field_err([x.cpu() for x in u], st.u) < TOL64
     assert float((bt[:2].cpu() - st.w).abs().max()) < 1e-12
     assert float((bt[2:].cpu() - st.wd).abs().max()) < 1e-11
+
+
+@pytest.mark.parametrize("kernel", [S.ROMA3, S.PESKIN4])
+def test_rough_channel_static_boxes_fp64(kernel):
+    """Static 3-D box body (cube roughness on a channel wall): fields, the force on the body and
+    every marker force against the oracle."""
+    wl = S.rough_channel_3d(16, 16, 16, cube=4, pitch=8, kernel=kernel)
+    gp = run_gpu(wl, 10)
+    st, dg, _ = run_oracle(wl, 10)
+    assert field_err(gp["u"], st.u) < TOL64
+    F, q = gp["grid"].box_forces(with_q=True)
+    for d in range(3):
+        assert abs(F[d] - float(dg.F[d])) <= 1e-10 * float(dg.F.abs().max())
+    qo = dg.q.numpy()
+    assert np.abs(np.array(q) - qo).max() <= 1e-10 * np.abs(qo).max()
+
+
+def test_rough_channel_static_boxes_mixed():
+    wl = S.rough_channel_3d(32, 16, 32, cube=4, pitch=8, both_walls=True)
+    gp = run_gpu(wl, 10, precision="mixed")
+    st, dg, _ = run_oracle(wl, 10)
+    assert field_err(gp["u"], st.u) < TOLMIX
+    F = gp["grid"].box_forces()
+    assert abs(F[0] - float(dg.F[0])) <= 1e-4 * abs(float(dg.F[0]))
