@@ -84,20 +84,22 @@ __global__ void mark_ib_kernel(uint8_t* flags, int ex, int ey, int ez, int px, i
   }
 }
 
-// phi of Eq. (22) (Peskin 4-point) or the 3-point kernel of Roma, Peskin & Berger
-__device__ __forceinline__ double phi3(int kind, double r) {
-  const double a = fabs(r);
+// phi of Eq. (22) (Peskin 4-point) or the 3-point kernel of Roma, Peskin & Berger,
+// in the field precision (FP32 IB transfers in mixed mode)
+template <typename T>
+__device__ __forceinline__ T phi3(int kind, T r) {
+  const T a = fabs(r);
   if (kind == FS_PESKIN4) {
-    if (a <= 1.0) return (3.0 - 2.0 * a + sqrt(fmax(1.0 + 4.0 * a - 4.0 * a * a, 0.0))) / 8.0;
-    if (a <= 2.0) return (5.0 - 2.0 * a - sqrt(fmax(-7.0 + 12.0 * a - 4.0 * a * a, 0.0))) / 8.0;
-    return 0.0;
+    if (a <= T(1)) return (T(3) - T(2) * a + sqrt(fmax(T(1) + T(4) * a - T(4) * a * a, T(0)))) / T(8);
+    if (a <= T(2)) return (T(5) - T(2) * a - sqrt(fmax(T(-7) + T(12) * a - T(4) * a * a, T(0)))) / T(8);
+    return T(0);
   }
-  if (a <= 0.5) return (1.0 + sqrt(fmax(1.0 - 3.0 * a * a, 0.0))) / 3.0;
-  if (a <= 1.5) {
-    const double b = 1.0 - a;
-    return (5.0 - 3.0 * a - sqrt(fmax(1.0 - 3.0 * b * b, 0.0))) / 6.0;
+  if (a <= T(0.5)) return (T(1) + sqrt(fmax(T(1) - T(3) * a * a, T(0)))) / T(3);
+  if (a <= T(1.5)) {
+    const T b = T(1) - a;
+    return (T(5) - T(3) * a - sqrt(fmax(T(1) - T(3) * b * b, T(0)))) / T(6);
   }
-  return 0.0;
+  return T(0);
 }
 
 struct GatherArgs {
@@ -112,63 +114,77 @@ struct GatherArgs {
   double* F;
 };
 
-// One thread per (marker, component): q = -sum f delta_h dv over the support.
-template <typename T>
+// One thread per marker: the separable weights of the two face families of
+// every direction (a component's own faces, offset 0, and the faces across,
+// offset 1/2) are formed once and serve the three components; the support sums
+// run in the field precision, q and the body force in FP64.
+template <typename T, int W>
 __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs A, const T* __restrict__ f0,
                                                      const T* __restrict__ f1, const T* __restrict__ f2) {
   __shared__ double red[3][8];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int m = t / 3, c = t - 3 * (t / 3);
-  double contrib = 0.0;
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  double contrib[3] = {0.0, 0.0, 0.0};
   if (m < A.nm) {
-    const T* f = c == 0 ? f0 : (c == 1 ? f1 : f2);
-    const int* e = A.ext[c];
-    int base[3];
-    double wgt[3][4];
-    for (int d = 0; d < 3; ++d) {
-      // face positions along d: x0 + i h (own direction) or x0 + (i + 1/2) h
-      const double off = d == c ? 0.0 : 0.5;
-      const double s = (A.X[d * A.nm + m] - A.x0[d]) / A.h[d] - off;
-      // faces within the support |s - i| < w / 2
-      base[d] = A.w == 4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
-      for (int a = 0; a < A.w; ++a) wgt[d][a] = phi3(A.kind, s - (base[d] + a)) / A.h[d];
-    }
-    double sum = 0.0;
-    for (int cz = 0; cz < A.w; ++cz) {
-      int k = base[2] + cz;
-      if (k < 0 || k >= e[2]) {
-        if (!A.per[2]) continue;
-        k = (k % e[2] + e[2]) % e[2];
+    int base[3][2];
+    T wgt[3][2][W];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int fam = 0; fam < 2; ++fam) {
+        const double s = (A.X[d * A.nm + m] - A.x0[d]) / A.h[d] - (fam ? 0.5 : 0.0);
+        // faces within the support |s - i| < W / 2
+        const int b0 = W == 4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+        base[d][fam] = b0;
+        const T ih = T(1.0 / A.h[d]);
+#pragma unroll
+        for (int a = 0; a < W; ++a) wgt[d][fam][a] = phi3<T>(A.kind, T(s - (b0 + a))) * ih;
       }
-      for (int cy = 0; cy < A.w; ++cy) {
-        int j = base[1] + cy;
-        if (j < 0 || j >= e[1]) {
-          if (!A.per[1]) continue;
-          j = (j % e[1] + e[1]) % e[1];
+    const T* fs[3] = {f0, f1, f2};
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* f = fs[c];
+      const int* e = A.ext[c];
+      const int fx = c == 0 ? 0 : 1, fy = c == 1 ? 0 : 1, fz = c == 2 ? 0 : 1;
+      T sum = T(0);
+#pragma unroll
+      for (int cz = 0; cz < W; ++cz) {
+        int k = base[2][fz] + cz;
+        if (k < 0 || k >= e[2]) {
+          if (!A.per[2]) continue;
+          k = (k % e[2] + e[2]) % e[2];
         }
-        const double wyz = wgt[2][cz] * wgt[1][cy];
-        for (int cx = 0; cx < A.w; ++cx) {
-          int i = base[0] + cx;
-          if (i < 0 || i >= e[0]) {
-            if (!A.per[0]) continue;
-            i = (i % e[0] + e[0]) % e[0];
+#pragma unroll
+        for (int cy = 0; cy < W; ++cy) {
+          int j = base[1][fy] + cy;
+          if (j < 0 || j >= e[1]) {
+            if (!A.per[1]) continue;
+            j = (j % e[1] + e[1]) % e[1];
           }
-          sum += (double)f[i + (size_t)e[0] * (j + (size_t)e[1] * k)] * wyz * wgt[0][cx];
+          const T wyz = wgt[2][fz][cz] * wgt[1][fy][cy];
+          const T* row = f + (size_t)e[0] * (j + (size_t)e[1] * k);
+          T rs = T(0);
+#pragma unroll
+          for (int cx = 0; cx < W; ++cx) {
+            int i = base[0][fx] + cx;
+            if (i < 0 || i >= e[0]) {
+              if (!A.per[0]) continue;
+              i = (i % e[0] + e[0]) % e[0];
+            }
+            rs += __ldg(row + i) * wgt[0][fx][cx];
+          }
+          sum += rs * wyz;
         }
       }
+      const double qv = -(double)sum * A.dv;
+      A.q[c * A.nm + m] = qv;
+      contrib[c] = A.rho * qv * A.dV[m];
     }
-    const double qv = -sum * A.dv;
-    A.q[c * A.nm + m] = qv;
-    contrib = A.rho * qv * A.dV[m];
   }
-  // F: block sums per component (thread t carries component t % 3)
-  double s3[3] = {0.0, 0.0, 0.0};
-  s3[c] = contrib;
   for (int cc = 0; cc < 3; ++cc)
-    for (int o = 16; o > 0; o >>= 1) s3[cc] += __shfl_down_sync(0xffffffffu, s3[cc], o);
+    for (int o = 16; o > 0; o >>= 1) contrib[cc] += __shfl_down_sync(0xffffffffu, contrib[cc], o);
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   if (l == 0)
-    for (int cc = 0; cc < 3; ++cc) red[cc][w] = s3[cc];
+    for (int cc = 0; cc < 3; ++cc) red[cc][w] = contrib[cc];
   __syncthreads();
   if (threadIdx.x < 3) {
     double v = 0.0;
@@ -219,9 +235,13 @@ void ib3_forces(fs_grid* G) {
   A.q = B.q;
   A.F = B.F;
   cudaMemsetAsync(B.F, 0, 3 * sizeof(double), G->stream);
-  const int threads = 3 * B.nm;
-  FS_LAUNCH(G, "ib3_force_gather", gather_kernel<T><<<(threads + 255) / 256, 256, 0, G->stream>>>(
-                                       A, (const T*)B.f[0], (const T*)B.f[1], (const T*)B.f[2]));
+  const int nb = (B.nm + 255) / 256;
+  if (A.w == 4)
+    FS_LAUNCH(G, "ib3_force_gather", gather_kernel<T, 4><<<nb, 256, 0, G->stream>>>(
+                                         A, (const T*)B.f[0], (const T*)B.f[1], (const T*)B.f[2]));
+  else
+    FS_LAUNCH(G, "ib3_force_gather", gather_kernel<T, 3><<<nb, 256, 0, G->stream>>>(
+                                         A, (const T*)B.f[0], (const T*)B.f[1], (const T*)B.f[2]));
   B.have_forces = true;
 }
 
