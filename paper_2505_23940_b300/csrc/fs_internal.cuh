@@ -309,6 +309,7 @@ struct fs_grid {
   int tune_fft_lines = 0;      // complex lines per FFT block (1..16)
   int tune_ysolve = 0;         // threads per y-solve block (8..128)
   bool use_pdl = true;         // programmatic dependent launch of the step kernels
+  int tune_pred_vw = 0;        // cells per thread of the FP32 3-D predictor (2 or 4; 0 = 4)
 
   // optional per-kernel timing (fs_profile_begin / fs_profile_end)
   bool prof_on = false;

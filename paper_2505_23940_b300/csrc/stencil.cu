@@ -418,32 +418,45 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
   A.out[1][v00 + i] = ov;
 }
 
-// Row segment of four values at x = i0 .. i0+3 with optional neighbours:
-// s[0] = x[i0 - 1] (LO), s[1..4] = x[i0 .. i0+3], s[5] = x[i0 + 4] (HI), periodic in x.
-template <bool LO, bool HI>
-__device__ __forceinline__ void ld_seg(const float* __restrict__ row, int i0, int nx, float* s) {
-  const Vec4<float> a = ld4(row + i0);
-  s[1] = a.v[0];
-  s[2] = a.v[1];
-  s[3] = a.v[2];
-  s[4] = a.v[3];
-  if (LO) s[0] = __ldg(row + (i0 > 0 ? i0 - 1 : nx - 1));
-  if (HI) s[5] = __ldg(row + (i0 + 4 < nx ? i0 + 4 : 0));
+// VW consecutive floats (VW = 2 or 4) of a row whose start is 4 VW-byte aligned.
+template <int VW>
+__device__ __forceinline__ void ldw(const float* __restrict__ p, float* out) {
+  if constexpr (VW == 4) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = a.x; out[1] = a.y; out[2] = a.z; out[3] = a.w;
+  } else {
+    const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+    out[0] = a.x; out[1] = a.y;
+  }
+}
+template <int VW>
+__device__ __forceinline__ void stw(float* p, const float* in) {
+  if constexpr (VW == 4) *reinterpret_cast<float4*>(p) = make_float4(in[0], in[1], in[2], in[3]);
+  else *reinterpret_cast<float2*>(p) = make_float2(in[0], in[1]);
 }
 
-// Four cells per thread along x (FP32, nx % 4 == 0, 16-byte aligned fields):
-// 17 four-wide and 10 scalar loads feed the 3 x 4 face updates.
-template <bool YPER>
+// Row segment of VW values at x = i0 .. i0+VW-1 with optional neighbours:
+// s[0] = x[i0 - 1] (LO), s[1..VW] = x[i0 ..], s[VW + 1] = x[i0 + VW] (HI), periodic in x.
+template <bool LO, bool HI, int VW>
+__device__ __forceinline__ void ld_seg(const float* __restrict__ row, int i0, int nx, float* s) {
+  ldw<VW>(row + i0, s + 1);
+  if (LO) s[0] = __ldg(row + (i0 > 0 ? i0 - 1 : nx - 1));
+  if (HI) s[VW + 1] = __ldg(row + (i0 + VW < nx ? i0 + VW : 0));
+}
+
+// VW cells per thread along x (FP32, nx % VW == 0, 4 VW-byte aligned fields):
+// 17 VW-wide and 10 scalar loads feed the 3 x VW face updates.
+template <bool YPER, int VW>
 __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs<float> A) {
   pdl_wait();
   const Geom<float>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int i0 = VW * (blockIdx.x * blockDim.x + threadIdx.x);
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i0 >= nx || j >= A.Y) return;
   if (!YPER && (j < 2 || j > ny - 2)) {
-    for (int e = 0; e < 4; ++e) predict_cell_general(A, i0 + e, j, k);
+    for (int e = 0; e < VW; ++e) predict_cell_general(A, i0 + e, j, k);
     return;
   }
   const int km = k > 0 ? k - 1 : nz - 1, kp = k < nz - 1 ? k + 1 : 0;
@@ -457,33 +470,33 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
   const float* __restrict__ U = A.uin[0];
   const float* __restrict__ V = A.uin[1];
   const float* __restrict__ W = A.uin[2];
-  // segments: index e + 1 is cell i0 + e
-  float U00[6], UM0[6], UP0[6], U0M[6], U0P[6];
-  float V00[6], VM0[6], VP0[6], V0M[6], V0P[6], VPM[6];
-  float W00[6], WM0[6], WP0[6], W0M[6], W0P[6], WMP[6];
-  ld_seg<true, true>(U + r00, i0, nx, U00);
-  ld_seg<false, true>(U + rm0, i0, nx, UM0);
-  ld_seg<false, false>(U + rp0, i0, nx, UP0);
-  ld_seg<false, true>(U + r0m, i0, nx, U0M);
-  ld_seg<false, false>(U + r0p, i0, nx, U0P);
-  ld_seg<true, true>(V + v00, i0, nx, V00);
-  ld_seg<false, false>(V + vm0, i0, nx, VM0);
-  ld_seg<true, false>(V + vp0, i0, nx, VP0);
-  ld_seg<false, false>(V + v0m, i0, nx, V0M);
-  ld_seg<false, false>(V + v0p, i0, nx, V0P);
-  ld_seg<false, false>(V + vpm, i0, nx, VPM);
-  ld_seg<true, true>(W + r00, i0, nx, W00);
-  ld_seg<false, false>(W + rm0, i0, nx, WM0);
-  ld_seg<false, false>(W + rp0, i0, nx, WP0);
-  ld_seg<false, false>(W + r0m, i0, nx, W0M);
-  ld_seg<true, false>(W + r0p, i0, nx, W0P);
-  ld_seg<false, false>(W + rmp, i0, nx, WMP);
+  constexpr int L = VW + 2;   // segments: index e + 1 is cell i0 + e
+  float U00[L], UM0[L], UP0[L], U0M[L], U0P[L];
+  float V00[L], VM0[L], VP0[L], V0M[L], V0P[L], VPM[L];
+  float W00[L], WM0[L], WP0[L], W0M[L], W0P[L], WMP[L];
+  ld_seg<true, true, VW>(U + r00, i0, nx, U00);
+  ld_seg<false, true, VW>(U + rm0, i0, nx, UM0);
+  ld_seg<false, false, VW>(U + rp0, i0, nx, UP0);
+  ld_seg<false, true, VW>(U + r0m, i0, nx, U0M);
+  ld_seg<false, false, VW>(U + r0p, i0, nx, U0P);
+  ld_seg<true, true, VW>(V + v00, i0, nx, V00);
+  ld_seg<false, false, VW>(V + vm0, i0, nx, VM0);
+  ld_seg<true, false, VW>(V + vp0, i0, nx, VP0);
+  ld_seg<false, false, VW>(V + v0m, i0, nx, V0M);
+  ld_seg<false, false, VW>(V + v0p, i0, nx, V0P);
+  ld_seg<false, false, VW>(V + vpm, i0, nx, VPM);
+  ld_seg<true, true, VW>(W + r00, i0, nx, W00);
+  ld_seg<false, false, VW>(W + rm0, i0, nx, WM0);
+  ld_seg<false, false, VW>(W + rp0, i0, nx, WP0);
+  ld_seg<false, false, VW>(W + r0m, i0, nx, W0M);
+  ld_seg<true, false, VW>(W + r0p, i0, nx, W0P);
+  ld_seg<false, false, VW>(W + rmp, i0, nx, WMP);
   const YMet<float> m = ymet<float, YPER>(A, j);
   const float bf = g.bforce ? g.bforce[j] : 0.f;
   const float a = A.a, b = A.b, dt = A.dt;
-  Vec4<float> ou, ov, ow;
+  float o3[3][VW];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) {
+  for (int e = 0; e < VW; ++e) {
     const int c = e + 1;
     Nb27<float> n;
     n.u000 = U00[c]; n.uM00 = U00[c - 1]; n.uP00 = U00[c + 1];
@@ -497,43 +510,41 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
     n.w00P = W0P[c]; n.wM0P = W0P[c - 1]; n.w0MP = WMP[c];
     float Ru, Rv, Rw;
     rhs3(n, m, g.ihx, g.ihz, g.nu, bf, Ru, Rv, Rw);
-    ou.v[e] = b * (n.u000 + dt * Ru);
-    ov.v[e] = b * (n.v000 + dt * Rv);
-    ow.v[e] = b * (n.w000 + dt * Rw);
+    o3[0][e] = b * (n.u000 + dt * Ru);
+    o3[1][e] = b * (n.v000 + dt * Rv);
+    o3[2][e] = b * (n.w000 + dt * Rw);
   }
+  const int rows[3] = {r00, v00, r00};
   if (a != 0.f) {
-    const Vec4<float> pu = ld4(A.un[0] + r00 + i0), pv = ld4(A.un[1] + v00 + i0), pw = ld4(A.un[2] + r00 + i0);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      ou.v[e] += a * pu.v[e];
-      ov.v[e] += a * pv.v[e];
-      ow.v[e] += a * pw.v[e];
+    for (int c = 0; c < 3; ++c) {
+      float pn[VW];
+      ldw<VW>(A.un[c] + rows[c] + i0, pn);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) o3[c][e] += a * pn[e];
     }
   }
   if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
-    const uchar4 fl[3] = {*reinterpret_cast<const uchar4*>(A.flags3[0] + r00 + i0),
-                          *reinterpret_cast<const uchar4*>(A.flags3[1] + v00 + i0),
-                          *reinterpret_cast<const uchar4*>(A.flags3[2] + r00 + i0)};
-    Vec4<float>* o3[3] = {&ou, &ov, &ow};
-    const int rows[3] = {r00, v00, r00};
-    for (int c = 0; c < 3; ++c) {
-      const unsigned char f4[4] = {fl[c].x, fl[c].y, fl[c].z, fl[c].w};
-      Vec4<float> fo = {{0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
-        if (f4[e]) {
+    for (int c = 0; c < 3; ++c) {
+      float fo[VW];
+#pragma unroll
+      for (int e = 0; e < VW; ++e) {
+        fo[e] = 0.f;
+        if (A.flags3[c][rows[c] + i0 + e]) {
           // u* = u + dt R, so R = (u* - u) / dt and f = -R - u / dt = -u* / dt
-          fo.v[e] = -o3[c]->v[e] / dt;
-          o3[c]->v[e] = 0.f;
+          fo[e] = -o3[c][e] / dt;
+          o3[c][e] = 0.f;
         }
-      st4(A.fout3[c] + rows[c] + i0, fo);
+      }
+      stw<VW>(A.fout3[c] + rows[c] + i0, fo);
     }
   }
   if (j < ny) {
-    st4(A.out[0] + r00 + i0, ou);
-    st4(A.out[2] + r00 + i0, ow);
+    stw<VW>(A.out[0] + r00 + i0, o3[0]);
+    stw<VW>(A.out[2] + r00 + i0, o3[2]);
   }
-  st4(A.out[1] + v00 + i0, ov);
+  stw<VW>(A.out[1] + v00 + i0, o3[1]);
 }
 
 template <typename T>
@@ -785,18 +796,23 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   const dim3 grd = stencil_grid(G, A.X, A.Y);
   if (G->dim == 3 && G->per[0] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body && G->ny >= 4) {
     if constexpr (std::is_same<T, float>::value) {
-      bool vec = G->nx % 4 == 0;
+      const int vw = G->tune_pred_vw > 0 ? G->tune_pred_vw : 4;
+      bool vec = G->nx % vw == 0;
       for (int c = 0; c < 3; ++c) {
-        vec = vec && (uintptr_t)uin[c] % 16 == 0 && (uintptr_t)out[c] % 16 == 0;
-        if (un) vec = vec && (uintptr_t)un[c] % 16 == 0;
+        vec = vec && (uintptr_t)uin[c] % (4 * vw) == 0 && (uintptr_t)out[c] % (4 * vw) == 0;
+        if (un) vec = vec && (uintptr_t)un[c] % (4 * vw) == 0;
+        if (G->has_ib3) vec = vec && (uintptr_t)G->ib3.f[c] % (4 * vw) == 0;
       }
       if (vec) {
         const dim3 vb(32, 8);
-        const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, G->nz);
-        if (G->per[1])
-          launch_pdl(G, "predictor", predictor3v_kernel<true>, vg, vb, 0, A);
-        else
-          launch_pdl(G, "predictor", predictor3v_kernel<false>, vg, vb, 0, A);
+        const dim3 vg((G->nx / vw + 31) / 32, (A.Y + 7) / 8, G->nz);
+        if (vw == 4) {
+          if (G->per[1]) launch_pdl(G, "predictor", predictor3v_kernel<true, 4>, vg, vb, 0, A);
+          else launch_pdl(G, "predictor", predictor3v_kernel<false, 4>, vg, vb, 0, A);
+        } else {
+          if (G->per[1]) launch_pdl(G, "predictor", predictor3v_kernel<true, 2>, vg, vb, 0, A);
+          else launch_pdl(G, "predictor", predictor3v_kernel<false, 2>, vg, vb, 0, A);
+        }
         return;
       }
     }
