@@ -248,8 +248,8 @@ long long fs_kernel_launches(const fs_grid* grid);
 
 /* Launch parameters chosen by an autotuner (0 restores the default):
  *   "stencil_bx"      x threads of the 256-thread stencil blocks: 32, 64, 128, 256
- *   "fft_lines"       complex lines per FFT block: 1..16
- *   "ysolve_threads"  threads per tridiagonal block: power of two in 8..128
+ *   "fft_lines"       complex lines per block of the mixed-radix transforms
+ *                     (lengths other than 64, 128, 256): 1..16
  *   "predictor_cells" cells per thread of the FP32 3-D predictor: 2 or 4 (default)
  *   "pdl"             1 (default): step kernels use programmatic dependent
  *                     launch (each starts while its predecessor drains);

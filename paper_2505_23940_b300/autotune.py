@@ -14,7 +14,6 @@ import torch
 CANDIDATES = {
     "stencil_bx": [32, 64, 128],
     "fft_lines": [4, 8, 16],
-    "ysolve_threads": [16, 32, 64],
     "predictor_cells": [4, 2],
 }
 

@@ -625,10 +625,6 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "fft_lines") {
     if (value < 0 || value > 16) return set_error(FS_ERR_ARG, "fft_lines must be in 1..16");
     G->tune_fft_lines = value;
-  } else if (k == "ysolve_threads") {
-    if (value != 0 && (value < 8 || value > 128 || (value & (value - 1))))
-      return set_error(FS_ERR_ARG, "ysolve_threads must be a power of two in 8..128");
-    G->tune_ysolve = value;
   } else if (k == "predictor_cells") {
     if (value != 0 && value != 2 && value != 4) return set_error(FS_ERR_ARG, "predictor_cells must be 2 or 4");
     G->tune_pred_vw = value;

@@ -307,7 +307,6 @@ struct fs_grid {
   // launch parameters (fs_set_tuning; 0 = built-in default)
   int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads
   int tune_fft_lines = 0;      // complex lines per FFT block (1..16)
-  int tune_ysolve = 0;         // threads per y-solve block (8..128)
   bool use_pdl = true;         // programmatic dependent launch of the step kernels
   int tune_pred_vw = 0;        // cells per thread of the FP32 3-D predictor (2 or 4; 0 = 4)
 
