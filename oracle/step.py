@@ -28,7 +28,7 @@ by central finite differences (tests/test_oracle_adjoint.py).
 import torch
 
 from . import body as body_mod
-from . import fluid, ib, ib3d, poisson
+from . import fluid, ib, ib3d, les, poisson
 from .grid import F64
 
 SSPRK3 = ((0.0, 1.0), (0.75, 0.25), (1.0 / 3.0, 2.0 / 3.0))
@@ -53,9 +53,11 @@ class Diagnostics:
         self.eps = None
 
 
-def _predictor(g, u_in, dt, eps=None, ut=None):
-    """Eq. (4)-(5): returns (u*, f)."""
+def _predictor(g, u_in, dt, eps=None, ut=None, cs=0.0):
+    """Eq. (4)-(5): returns (u*, f).  cs > 0 adds the Smagorinsky subgrid term (les.py)."""
     R = fluid.momentum_rhs(g, u_in)
+    if cs > 0.0:
+        R = [a + b for a, b in zip(R, les.sgs_term(g, u_in, cs))]
     ustar, f = [], []
     for c in range(g.dim):
         base = u_in[c] + dt * R[c]
@@ -69,8 +71,8 @@ def _predictor(g, u_in, dt, eps=None, ut=None):
     return ustar, f
 
 
-def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
-    """Advance one step; returns (new State, Diagnostics)."""
+def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None, cs=0.0):
+    """Advance one step; returns (new State, Diagnostics).  cs: Smagorinsky constant (0: no model)."""
     dg = Diagnostics()
     u = fluid.apply_boundary_values(g, st.u)
     if scheme == "rk3":
@@ -78,7 +80,7 @@ def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
             "RK3 is provided for grids without a body or an outflow"
         v = u
         for a, b in SSPRK3:
-            ustar, _ = _predictor(g, v, dt)
+            ustar, _ = _predictor(g, v, dt, cs=cs)
             ut = [a * u[c] + b * ustar[c] for c in range(g.dim)]
             ut = fluid.apply_boundary_values(g, ut)
             v, phi = poisson.project(g, ut)
@@ -99,7 +101,7 @@ def step(g, st, dt, scheme="fe", body=None, kernel=ib.ROMA3, params=None):
         ut, ucl = ib.target_velocity(g, body, kernel, st.w, st.wd, masks)
         eps = [m[0] | m[1] for m in masks]
         dg.eps = eps
-    ustar, f = _predictor(g, u, dt, eps, ut)
+    ustar, f = _predictor(g, u, dt, eps, ut, cs=cs)
     ustar = fluid.apply_boundary_values(g, ustar)
     ustar = fluid.outflow_faces(g, u, ustar)
     unew, phi = poisson.project(g, ustar, ucl, eps)
