@@ -223,6 +223,16 @@ int fs_set_body_force(fs_grid* grid, const double* fx);
  * with max_subiters > 1.  Errors: FS_ERR_ARG (max_subiters < 1, tol <= 0). */
 int fs_set_coupling(fs_grid* grid, int max_subiters, double tol);
 
+/* Constant-coefficient Smagorinsky subgrid model (§2.5; the LES of §3.4):
+ * every later step adds d_j tau_ij, tau_ij = 2 nu_t S_ij, nu_t = (C_s Delta)^2
+ * sqrt(2 S_ij S_ij), Delta = (h_x h_y h_z)^(1/3), to R of Eq. (4); normal
+ * strains at cell centres, shear strains at cell edges, nu_t at centres and
+ * averaged to edges.  cs = 0 switches the model off.  Provided for 3-D grids
+ * periodic (hence uniform) in x, y and z with central convection and no body;
+ * fs_step_adjoint returns FS_ERR_UNSUPPORTED while it is on.
+ * Errors: FS_ERR_ARG (cs < 0), FS_ERR_UNSUPPORTED, FS_ERR_CUDA. */
+int fs_set_les(fs_grid* grid, double cs);
+
 /* Sub-iterations and final xi of the last strongly coupled step (host outputs, may be NULL). */
 int fs_coupling_stats(const fs_grid* grid, int* subiters, double* xi);
 

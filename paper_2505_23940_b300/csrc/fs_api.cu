@@ -260,6 +260,7 @@ void free_all(fs_grid* G) {
   F(G->spec); F(G->scal); F(G->red); F(G->cg);
   for (int c = 0; c < 3; ++c) F(G->fsi_u[c]);
   F(G->fsi_b);
+  for (int q = 0; q < 4; ++q) F(G->les_nu[q]);
   F(G->px.tw); F(G->px.dtw); F(G->py.tw); F(G->py.dtw); F(G->pz.tw); F(G->pz.dtw);
   F(G->lamy); F(G->lamxz);
   F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);
@@ -793,6 +794,7 @@ int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const doubl
     if (G->fsi_iters > 1)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of the strongly coupled (sub-iterated) FSI step");
   }
+  if (G->les_cs > 0.0) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a step with the Smagorinsky model");
   if (G->has_ib3) {
     return set_error(FS_ERR_UNSUPPORTED, "adjoint of a grid with a static 3-D box body");
     if (G->ib.omega != 0.0)
@@ -840,6 +842,24 @@ int fs_set_coupling(fs_grid* G, int max_subiters, double tol) {
   if (max_subiters < 1 || !(tol > 0.0)) return set_error(FS_ERR_ARG, "fs_set_coupling: max_subiters >= 1, tol > 0");
   G->fsi_iters = max_subiters;
   G->fsi_tol = tol;
+  return FS_OK;
+}
+
+int fs_set_les(fs_grid* G, double cs) {
+  if (!G) return set_error(FS_ERR_ARG, "NULL grid");
+  if (!(cs >= 0.0)) return set_error(FS_ERR_ARG, "fs_set_les: C_s must be >= 0");
+  if (cs > 0.0) {
+    if (G->dim != 3 || !G->per[0] || !G->per[1] || !G->per[2])
+      return set_error(FS_ERR_UNSUPPORTED, "the Smagorinsky model is provided for 3-D grids periodic in x, y and z");
+    if (G->conv != FS_CENTRAL2 || G->has_body || G->has_ib3)
+      return set_error(FS_ERR_UNSUPPORTED, "the Smagorinsky model is provided for central convection without bodies");
+    if (!G->les_nu[0]) {
+      const size_t n = (size_t)G->nx * G->ny * G->nz * elem_size(G);
+      for (int q = 0; q < 4; ++q)
+        if (cudaMalloc(&G->les_nu[q], n) != cudaSuccess) return set_error(FS_ERR_CUDA, "allocating nu_t");
+    }
+  }
+  G->les_cs = cs;
   return FS_OK;
 }
 

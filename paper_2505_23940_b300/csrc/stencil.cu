@@ -49,6 +49,7 @@ struct PredArgs {
   T ihy0;                    // 1 / h_y of a uniform periodic y (predictor3_kernel<T, true>)
   const uint8_t* flags3[3];  // static 3-D body (boxes): per-face flags, forced faces take u_s = 0
   T* fout3[3];               // and the forcing term f on every face (0 off forced faces)
+  const T* nut[4];           // Smagorinsky eddy viscosity: cell centres, xy, xz, yz edges (or null)
 };
 
 // Velocity access around the face (i, j, k) with every boundary rule (ldv).
@@ -341,6 +342,94 @@ __device__ __forceinline__ void rhs3(const Nb27<T>& n, const YMet<T>& m, T ihx, 
   }
 }
 
+// Divergence of the Smagorinsky subgrid stress tau_ij = 2 nu_t S_ij on the three
+// faces of a cell (uniform periodic grid): normal strains at the cell centres,
+// shear strains at the edges, nu_t at centres (c) and averaged to edges (e*).
+// nc: centres (i,j,k), (i-1), (j-1), (k-1); exy: edges (i,j), (i,j+1), (i+1,j);
+// exz: (i,k), (i,k+1), (i+1,k); eyz: (j,k), (j,k+1), (j+1,k).
+template <typename T>
+__device__ __forceinline__ void sgs3(const Nb27<T>& n, const T* nc, const T* exy, const T* exz, const T* eyz,
+                                     T ihx, T ihy, T ihz, T& Su, T& Sv, T& Sw) {
+  const T h = T(0.5), two = T(2);
+  // shear strains at the edges touching the cell's three faces
+  const T sxy_ij = h * ((n.u000 - n.u0M0) * ihy + (n.v000 - n.vM00) * ihx);
+  const T sxy_ijp = h * ((n.u0P0 - n.u000) * ihy + (n.v0P0 - n.vMP0) * ihx);
+  const T sxy_ipj = h * ((n.uP00 - n.uPM0) * ihy + (n.vP00 - n.v000) * ihx);
+  const T sxz_ik = h * ((n.u000 - n.u00M) * ihz + (n.w000 - n.wM00) * ihx);
+  const T sxz_ikp = h * ((n.u00P - n.u000) * ihz + (n.w00P - n.wM0P) * ihx);
+  const T sxz_ipk = h * ((n.uP00 - n.uP0M) * ihz + (n.wP00 - n.w000) * ihx);
+  const T syz_jk = h * ((n.v000 - n.v00M) * ihz + (n.w000 - n.w0M0) * ihy);
+  const T syz_jkp = h * ((n.v00P - n.v000) * ihz + (n.w00P - n.w0MP) * ihy);
+  const T syz_jpk = h * ((n.v0P0 - n.v0PM) * ihz + (n.w0P0 - n.w000) * ihy);
+  Su = (two * nc[0] * (n.uP00 - n.u000) * ihx - two * nc[1] * (n.u000 - n.uM00) * ihx) * ihx +
+       (two * exy[1] * sxy_ijp - two * exy[0] * sxy_ij) * ihy + (two * exz[1] * sxz_ikp - two * exz[0] * sxz_ik) * ihz;
+  Sv = (two * exy[2] * sxy_ipj - two * exy[0] * sxy_ij) * ihx +
+       (two * nc[0] * (n.v0P0 - n.v000) * ihy - two * nc[2] * (n.v000 - n.v0M0) * ihy) * ihy +
+       (two * eyz[1] * syz_jkp - two * eyz[0] * syz_jk) * ihz;
+  Sw = (two * exz[2] * sxz_ipk - two * exz[0] * sxz_ik) * ihx + (two * eyz[2] * syz_jpk - two * eyz[0] * syz_jk) * ihy +
+       (two * nc[0] * (n.w00P - n.w000) * ihz - two * nc[3] * (n.w000 - n.w00M) * ihz) * ihz;
+}
+
+// Eddy viscosity nu_t = (C_s Delta)^2 sqrt(2 S_ij S_ij) at cell (i, j, k) of a
+// uniform periodic grid, the shear strains averaged from the four edges around
+// the centre.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) les_nut_kernel(const Geom<T> g, const T* __restrict__ U,
+                                                           const T* __restrict__ V, const T* __restrict__ W,
+                                                           T coef, T* __restrict__ nut) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx || j >= ny) return;
+  const int xo[3] = {i > 0 ? i - 1 : nx - 1, i, i < nx - 1 ? i + 1 : 0};
+  const int yo[3] = {j > 0 ? j - 1 : ny - 1, j, j < ny - 1 ? j + 1 : 0};
+  const int zo[3] = {k > 0 ? k - 1 : nz - 1, k, k < nz - 1 ? k + 1 : 0};
+  auto at = [&](int a, int b, int c) { return xo[a + 1] + nx * (yo[b + 1] + ny * zo[c + 1]); };
+  const T ihx = g.ihx, ihy = g.ihy[0], ihz = g.ihz, h = T(0.5);
+  const T sxx = (__ldg(U + at(1, 0, 0)) - __ldg(U + at(0, 0, 0))) * ihx;
+  const T syy = (__ldg(V + at(0, 1, 0)) - __ldg(V + at(0, 0, 0))) * ihy;
+  const T szz = (__ldg(W + at(0, 0, 1)) - __ldg(W + at(0, 0, 0))) * ihz;
+  // edges (a, b) of a family at offsets a, b in {0, 1} from the cell's lower corner
+  T cxy = T(0), cxz = T(0), cyz = T(0);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      cxy += h * ((__ldg(U + at(a, b, 0)) - __ldg(U + at(a, b - 1, 0))) * ihy +
+                  (__ldg(V + at(a, b, 0)) - __ldg(V + at(a - 1, b, 0))) * ihx);
+      cxz += h * ((__ldg(U + at(a, 0, b)) - __ldg(U + at(a, 0, b - 1))) * ihz +
+                  (__ldg(W + at(a, 0, b)) - __ldg(W + at(a - 1, 0, b))) * ihx);
+      cyz += h * ((__ldg(V + at(0, a, b)) - __ldg(V + at(0, a, b - 1))) * ihz +
+                  (__ldg(W + at(0, a, b)) - __ldg(W + at(0, a - 1, b))) * ihy);
+    }
+  cxy *= T(0.25);
+  cxz *= T(0.25);
+  cyz *= T(0.25);
+  const T ss = sxx * sxx + syy * syy + szz * szz + T(2) * (cxy * cxy + cxz * cxz + cyz * cyz);
+  nut[at(0, 0, 0)] = coef * sqrt(T(2) * ss);
+}
+
+// nu_t averaged to the xy, xz and yz edges with the cell's index (lower corner).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) les_edge_kernel(const Geom<T> g, const T* __restrict__ nut,
+                                                            T* __restrict__ exy, T* __restrict__ exz,
+                                                            T* __restrict__ eyz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if (i >= nx || j >= ny) return;
+  const int im = i > 0 ? i - 1 : nx - 1, jm = j > 0 ? j - 1 : ny - 1, km = k > 0 ? k - 1 : nz - 1;
+  auto c = [&](int a, int b, int d) { return __ldg(nut + a + nx * (b + ny * d)); };
+  const T n0 = c(i, j, k), nxm = c(im, j, k), nym = c(i, jm, k), nzm = c(i, j, km);
+  const size_t p = i + (size_t)nx * (j + (size_t)ny * k);
+  exy[p] = T(0.25) * (n0 + nxm + nym + c(im, jm, k));
+  exz[p] = T(0.25) * (n0 + nxm + nzm + c(im, j, km));
+  eyz[p] = T(0.25) * (n0 + nym + nzm + c(i, jm, km));
+}
+
 // The general per-face path for the rows of a wall-bounded y whose stencil
 // reaches a wall (j < 2 or j > ny - 2).
 template <typename T>
@@ -395,6 +484,19 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
   n.wM0P = __ldg(W + r0p + im); n.w0MP = __ldg(W + rmp + i);
   T Ru, Rv, Rw;
   rhs3(n, ymet<T, YPER>(A, j), g.ihx, g.ihz, g.nu, g.bforce ? g.bforce[j] : T(0), Ru, Rv, Rw);
+  if (YPER && A.nut[0]) {   // Smagorinsky subgrid stress (uniform periodic grids)
+    const int c00 = r00 + i;
+    const T nc[4] = {__ldg(A.nut[0] + c00), __ldg(A.nut[0] + r00 + im), __ldg(A.nut[0] + rm0 + i),
+                     __ldg(A.nut[0] + r0m + i)};
+    const T exy[3] = {__ldg(A.nut[1] + c00), __ldg(A.nut[1] + rp0 + i), __ldg(A.nut[1] + r00 + ip)};
+    const T exz[3] = {__ldg(A.nut[2] + c00), __ldg(A.nut[2] + r0p + i), __ldg(A.nut[2] + r00 + ip)};
+    const T eyz[3] = {__ldg(A.nut[3] + c00), __ldg(A.nut[3] + r0p + i), __ldg(A.nut[3] + rp0 + i)};
+    T Su, Sv, Sw;
+    sgs3(n, nc, exy, exz, eyz, g.ihx, A.ihy0, g.ihz, Su, Sv, Sw);
+    Ru += Su;
+    Rv += Sv;
+    Rw += Sw;
+  }
   const T a = A.a, b = A.b, dt = A.dt;
   T ou = b * (n.u000 + dt * Ru), ov = b * (n.v000 + dt * Rv), ow = b * (n.w000 + dt * Rw);
   if (a != T(0)) {
@@ -792,9 +894,25 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
     A.flags3[c] = G->has_ib3 ? G->ib3.flags[c] : nullptr;
     A.fout3[c] = G->has_ib3 ? (T*)G->ib3.f[c] : nullptr;
   }
+  const bool les = G->les_cs > 0.0;
+  for (int q = 0; q < 4; ++q) A.nut[q] = les ? (const T*)G->les_nu[q] : nullptr;
+  if (les) {
+    const Geom<T> gg = G->geom<T>();
+    double delta = std::cbrt(G->hx * G->h[1][0] * G->hz);
+    const T coef = (T)(G->les_cs * delta * G->les_cs * delta);
+    const dim3 lb = stencil_block(G), lg = stencil_grid(G, G->nx, G->ny);
+    launch_pdl(G, "les_nut", les_nut_kernel<T>, lg, lb, 0, gg, (const T*)uin[0], (const T*)uin[1], (const T*)uin[2],
+               coef, (T*)G->les_nu[0]);
+    FS_LAUNCH(G, "les_nut", les_edge_kernel<T><<<lg, lb, 0, G->stream>>>(gg, (const T*)G->les_nu[0], (T*)G->les_nu[1],
+                                                                       (T*)G->les_nu[2], (T*)G->les_nu[3]));
+  }
   const dim3 blk = stencil_block(G);
   const dim3 grd = stencil_grid(G, A.X, A.Y);
   if (G->dim == 3 && G->per[0] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body && G->ny >= 4) {
+    if (les) {   // the one-cell kernel carries the subgrid term
+      launch_pdl(G, "predictor", predictor3_kernel<T, true>, grd, blk, 0, A);
+      return;
+    }
     if constexpr (std::is_same<T, float>::value) {
       const int vw = G->tune_pred_vw > 0 ? G->tune_pred_vw : 4;
       bool vec = G->nx % vw == 0;

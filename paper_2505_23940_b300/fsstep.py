@@ -82,6 +82,7 @@ def lib():
         L.fs_set_body_force.argtypes = [c_void_p, c_void_p]
         L.fs_set_stiffness.argtypes = [c_void_p, c_double]
         L.fs_set_coupling.argtypes = [c_void_p, c_int, c_double]
+        L.fs_set_les.argtypes = [c_void_p, c_double]
         L.fs_set_ib_boxes.argtypes = [c_void_p, c_int, POINTER(c_double), c_int, POINTER(c_double), POINTER(c_double),
                                       c_int]
         L.fs_coupling_stats.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
@@ -262,6 +263,10 @@ class Grid:
         check(lib().fs_set_ib_boxes(self.h, b.shape[0], bp, x.shape[0], xp, vp, int(kernel)))
         self.n_box_markers = x.shape[0]
         self.has_boxes = True
+
+    def set_les(self, cs):
+        """Constant-coefficient Smagorinsky model with constant cs (0: off)."""
+        check(lib().fs_set_les(self.h, float(cs)))
 
     def set_coupling(self, max_subiters, tol=1e-5):
         """Strong FSI coupling: sub-iterate each step up to max_subiters fluid solves (1 = weak)."""

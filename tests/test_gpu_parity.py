@@ -227,3 +227,30 @@ def test_rough_channel_static_boxes_mixed():
     assert field_err(gp["u"], st.u) < TOLMIX
     F = gp["grid"].box_forces()
     assert abs(F[0] - float(dg.F[0])) <= 1e-4 * abs(float(dg.F[0]))
+
+
+@pytest.mark.parametrize("scheme,precision", [("fe", "fp64"), ("rk3", "fp64"), ("rk3", "mixed")])
+def test_smagorinsky_les(scheme, precision):
+    """Constant-coefficient Smagorinsky LES on a periodic box against the oracle's subgrid term."""
+    from paper_2505_23940_b300 import FsError, grid_from_workload
+    wl = S.box_3d(16, 12, 8, (P, P), (P, P), L=(1.0, 0.75, 0.5), nu=0.002)
+    wl.scheme, wl.dt = scheme, 0.004
+    wl.u0 = S.random_fields(wl, 9, 1.0)
+    cs = 0.17
+    g = grid_of(wl)
+    st = O.State([torch.tensor(a) for a in wl.u0])
+    for _ in range(8):
+        st, _ = O.step(g, st, wl.dt, scheme=scheme, cs=cs)
+    G = grid_from_workload(wl, precision)
+    G.set_les(cs)
+    u = [torch.tensor(a, dtype=G.dtype, device="cuda") for a in wl.u0]
+    G.step(u, wl.dt, 8)
+    torch.cuda.synchronize()
+    assert field_err([x.double().cpu() for x in u], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
+    # the model changes the result (the comparison is not vacuous)
+    st0 = O.State([torch.tensor(a) for a in wl.u0])
+    for _ in range(8):
+        st0, _ = O.step(g, st0, wl.dt, scheme=scheme)
+    assert field_err(st.u, st0.u) > 1e-6
+    with pytest.raises(FsError):
+        G.step_adjoint(u, [torch.zeros_like(x) for x in u], wl.dt)
