@@ -197,8 +197,17 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_kernel(const RhsAdjArgs<T> A) 
 // E_Cd(f) = TN QN, TN = (u_d(f + e_d - e_C) + u_d(f + e_d)) / 2,
 // QN = (u_C(f) + u_C(f + e_d)) / 2, gives aE TN / 2 to the two u_C and aE QN / 2
 // to the two u_d it reads.  Diffusion is symmetric on a uniform periodic grid.
+// out = src + R'(u)^T (scale src): the gather below evaluated on mu = scale src.
 template <typename T>
-__global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const RhsAdjArgs<T> A) {
+struct GatherAdjArgs {
+  RhsAdjArgs<T> r;   // u, mu = src, g
+  T scale;
+  T* out[3];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const GatherAdjArgs<T> GA) {
+  const RhsAdjArgs<T>& A = GA.r;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
@@ -241,7 +250,7 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const RhsAdjArgs
     l += h * (ihx * (mwPz - mwMxPz) * h * (wMxPz + wPz) + ihx * (mw0 - mwMx) * h * (wMx + w0));
     l += nu * ((muPx - T(2) * mu0 + muMx) * ihx * ihx + (muPy - T(2) * mu0 + muMy) * ihy * ihy +
                (muPz - T(2) * mu0 + muMz) * ihz * ihz);
-    A.lam[0][p] += l;
+    GA.out[0][p] = mu0 + GA.scale * l;
   }
   {  // lambda_v
     const T vMy = v(0, -1, 0);
@@ -255,7 +264,7 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const RhsAdjArgs
     l += h * (ihy * (mwPz - mwMyPz) * h * (wMyPz + wPz) + ihy * (mw0 - mwMy) * h * (wMy + w0));
     l += nu * ((mvPx - T(2) * mv0 + mvMx) * ihx * ihx + (mvPy - T(2) * mv0 + mvMy) * ihy * ihy +
                (mvPz - T(2) * mv0 + mvMz) * ihz * ihz);
-    A.lam[1][p] += l;
+    GA.out[1][p] = mv0 + GA.scale * l;
   }
   {  // lambda_w
     const T wMz = w(0, 0, -1);
@@ -269,7 +278,7 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const RhsAdjArgs
     l += h * (ihz * (mvPy - mvPyMz) * h * (vPyMz + vPy) + ihz * (mv0 - mvMz) * h * (vMz + v0));
     l += nu * ((mwPx - T(2) * mw0 + mwMx) * ihx * ihx + (mwPy - T(2) * mw0 + mwMy) * ihy * ihy +
                (mwPz - T(2) * mw0 + mwMz) * ihz * ihz);
-    A.lam[2][p] += l;
+    GA.out[2][p] = mw0 + GA.scale * l;
   }
 }
 
@@ -425,8 +434,9 @@ __global__ void __launch_bounds__(kT) face_adj_kernel(const FaceAdjArgs<T> A) {
 // (uniform metrics, no body): there D^T V = -V G and the cell volume is
 // constant, so P^T lam = lam - G S D lam, the forward projection.  phi = S D lam
 // is solved by the forward path; this kernel forms lam~ = lam - G phi four
-// cells at a time and the stage outputs lam_acc += a lam~, lam_n = b lam~,
-// mu = b dt lam~ (forward Euler: a = 0, b = 1, no lam_acc).
+// cells at a time and the stage outputs lam_acc += a lam~, lam_n = b lam~
+// (the predictor adjoint's mu = b dt lam~ = dt lam_n; forward Euler: a = 0,
+// b = 1, no lam_acc).
 template <typename T>
 struct ProjAdjArgs {
   Geom<T> g;
@@ -434,7 +444,6 @@ struct ProjAdjArgs {
   const T* phi;
   T* lacc[3];
   T* lamn[3];
-  T* mu[3];
   T a, b, dt;
   int rk;
   double* bfsum;
@@ -466,12 +475,9 @@ __global__ void __launch_bounds__(kT) proj_adj4_kernel(const ProjAdjArgs<T> A) {
       Vec4<T> lw = ld4(A.lam[c] + row + i0);
 #pragma unroll
       for (int e = 0; e < 4; ++e) lw.v[e] -= (p0.v[e] - pm.v[e]) * ih[c];
-      Vec4<T> ln, m;
+      Vec4<T> ln;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        ln.v[e] = A.b * lw.v[e];
-        m.v[e] = A.b * A.dt * lw.v[e];
-      }
+      for (int e = 0; e < 4; ++e) ln.v[e] = A.b * lw.v[e];
       if (A.rk) {
         Vec4<T> la = ld4(A.lacc[c] + row + i0);
 #pragma unroll
@@ -479,9 +485,9 @@ __global__ void __launch_bounds__(kT) proj_adj4_kernel(const ProjAdjArgs<T> A) {
         st4(A.lacc[c] + row + i0, la);
       }
       st4(A.lamn[c] + row + i0, ln);
-      st4(A.mu[c] + row + i0, m);
+      // mu = b dt lam~ = dt lam_n is not stored: the gather transpose forms it
       if (c == 0 && A.bfsum)
-        for (int e = 0; e < 4; ++e) bsum += (double)m.v[e];
+        for (int e = 0; e < 4; ++e) bsum += (double)(A.dt * ln.v[e]);
     }
   }
   // body-force profile: the 32 threads of a warp share the row j
@@ -781,10 +787,6 @@ void launch_rhs_adjoint(fs_grid* G, T* const* u, T* const* mu, T* const* lam) {
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
   const dim3 blk = stencil_block(G), grd = stencil_grid(G, A.X, A.Y);
-  if (G->dim == 3 && G->per[0] && G->per[1] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body) {
-    FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_gather_kernel<T><<<grd, blk, 0, G->stream>>>(A));
-    return;
-  }
   FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
@@ -798,24 +800,29 @@ void launch_projection_adjoint_solve(fs_grid* G, T* const* lam, T* spec) {
   poisson_solve_inplace<T>(G, spec);
 }
 
+// Fully periodic 3-D grids with central convection and no body: the gather
+// transpose of the flux stencil applies.
+bool gather_fast(const fs_grid* G) {
+  return G->dim == 3 && G->per[0] && G->per[1] && G->per[2] && G->conv == FS_CENTRAL2 && !G->has_body;
+}
+
 // True when the projection adjoint may take the forward projection (all
 // directions periodic, no body, four-cell rows on 16/32-byte aligned arrays).
 template <typename T>
-bool proj_adj_fast(const fs_grid* G, T* const* lam, T* const* la, T* const* ln, T* const* mu) {
+bool proj_adj_fast(const fs_grid* G, T* const* lam, T* const* la, T* const* ln) {
   if (G->has_body || G->nx % 4) return false;
   for (int d = 0; d < G->dim; ++d)
     if (!G->per[d]) return false;
   const uintptr_t al = 4 * sizeof(T);
   if ((uintptr_t)G->spec % al) return false;
   for (int c = 0; c < G->dim; ++c)
-    if ((uintptr_t)lam[c] % al || (uintptr_t)la[c] % al || (uintptr_t)ln[c] % al || (uintptr_t)mu[c] % al)
-      return false;
+    if ((uintptr_t)lam[c] % al || (uintptr_t)la[c] % al || (uintptr_t)ln[c] % al) return false;
   return true;
 }
 
 template <typename T>
 void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double dt, bool rk, double* bfsum,
-                          T* const* la, T* const* ln, T* const* mu) {
+                          T* const* la, T* const* ln) {
   T* spec = (T*)G->spec;
   poisson_solve_from_velocity<T>(G, make_div_args<T>(G, lam, nullptr), spec);
   ProjAdjArgs<T> A;
@@ -825,7 +832,6 @@ void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double 
     A.lam[c] = on ? lam[c] : nullptr;
     A.lacc[c] = on ? la[c] : nullptr;
     A.lamn[c] = on ? ln[c] : nullptr;
-    A.mu[c] = on ? mu[c] : nullptr;
   }
   A.phi = spec;
   A.a = (T)a;
@@ -835,6 +841,25 @@ void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double 
   A.bfsum = bfsum;
   const dim3 blk(32, 8), grd((G->nx / 4 + 31) / 32, (G->ny + 7) / 8, G->nz);
   FS_LAUNCH(G, "proj_adjoint", proj_adj4_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+}
+
+// out = src + R'(u)^T (scale src) on a fully periodic grid (gather transpose).
+template <typename T>
+void launch_rhs_adjoint_gather(fs_grid* G, T* const* u, T* const* src, double scale, T* const* out) {
+  GatherAdjArgs<T> A;
+  A.r.g = G->geom<T>();
+  for (int c = 0; c < 3; ++c) {
+    A.r.u[c] = u[c];
+    A.r.mu[c] = src[c];
+    A.r.lam[c] = nullptr;
+    A.out[c] = out[c];
+  }
+  A.r.conv = G->conv;
+  A.r.X = G->nx;
+  A.r.Y = G->ny;
+  A.scale = (T)scale;
+  const dim3 blk = stencil_block(G), grd = stencil_grid(G, G->nx, G->ny);
+  FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_gather_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
 
 }  // namespace
@@ -933,18 +958,21 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
     for (int c = 0; c < dim; ++c) cudaMemsetAsync(la[c], 0, comp_count(G, c) * sizeof(T), G->stream);
     // cur = lam of the stage output, starting from lam^{n+1}
     T* cur[3] = {L[0], L[1], L[2]};
-    const bool fast = proj_adj_fast<T>(G, L, la, ln, mu);
-    for (int s = 2; s >= 0; --s) {
-      if (fast) {
-        launch_proj_adj_fast<T>(G, cur, Ac[s], Bc[s], dt, true, bfsum, la, ln, mu);
-        launch_rhs_adjoint<T>(G, vs[s], mu, ln);
-        if (s > 0)
-          for (int c = 0; c < dim; ++c) {
-            cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
-            cur[c] = L[c];
-          }
-        continue;
+    const bool fast = gather_fast(G) && proj_adj_fast<T>(G, L, la, ln);
+    if (fast) {
+      // lam of v_s = b lam~ + R'(v_s)^T (b dt lam~), written straight into lam->u
+      for (int s = 2; s >= 0; --s) {
+        launch_proj_adj_fast<T>(G, L, Ac[s], Bc[s], dt, true, bfsum, la, ln);
+        launch_rhs_adjoint_gather<T>(G, vs[s], ln, dt, L);
       }
+      for (int c = 0; c < dim; ++c) {
+        const long long n = (long long)comp_count(G, c);
+        FS_LAUNCH(G, "axpy", axpy_kernel<T><<<(int)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0,
+                                            G->stream>>>(L[c], la[c], n));
+      }
+      return cuda_check(cudaGetLastError(), "fs_step_adjoint (RK3)");
+    }
+    for (int s = 2; s >= 0; --s) {
       launch_projection_adjoint_solve<T>(G, cur, spec);
       FaceAdjArgs<T> A{};
       A.g = g;
@@ -1010,11 +1038,9 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
                                          (const T*)ib.f[1], (T*)B->lamf[0], (T*)B->lamf[1], sc + 8));
   } else if (G->bc[0][1] == FS_BC_OUTFLOW && !G->per[0]) {
     launch_outflow_flux<T>(G, u);
-  } else if (proj_adj_fast<T>(G, L, la, ln, mu)) {
-    launch_proj_adj_fast<T>(G, L, 0.0, 1.0, dt, false, bfsum, la, ln, mu);
-    launch_rhs_adjoint<T>(G, u, mu, ln);
-    for (int c = 0; c < dim; ++c)
-      cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+  } else if (gather_fast(G) && proj_adj_fast<T>(G, L, la, ln)) {
+    launch_proj_adj_fast<T>(G, L, 0.0, 1.0, dt, false, bfsum, la, ln);
+    launch_rhs_adjoint_gather<T>(G, u, ln, dt, L);
     return cuda_check(cudaGetLastError(), "fs_step_adjoint");
   }
   launch_projection_adjoint_solve<T>(G, L, spec);
