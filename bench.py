@@ -49,13 +49,13 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on: a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50384384 + 1818880, "src": "70260af2c2e3"},
-    "fft_x_fwd_div": {"bytes": 25243648, "src": "064fb2dec636"},
-    "fft_z_fwd": {"bytes": 8406784, "src": "064fb2dec636"},
-    "fft_y_solve": {"bytes": 8433664, "src": "064fb2dec636"},
-    "fft_z_inv": {"bytes": 8410624, "src": "064fb2dec636"},
-    "fft_x_inv": {"bytes": 8414720, "src": "064fb2dec636"},
-    "correct": {"bytes": 33561088, "src": "70260af2c2e3"},
+    "predictor": {"bytes": 50394624 + 1619712, "src": "0d59fe23c37e"},
+    "fft_x_fwd_div": {"bytes": 25243648 + 20480, "src": "064fb2dec636"},
+    "fft_z_fwd": {"bytes": 8407552, "src": "064fb2dec636"},
+    "fft_y_solve": {"bytes": 8432896, "src": "064fb2dec636"},
+    "fft_z_inv": {"bytes": 8419072, "src": "064fb2dec636"},
+    "fft_x_inv": {"bytes": 8414976, "src": "064fb2dec636"},
+    "correct": {"bytes": 33560576 + 3328, "src": "0d59fe23c37e"},
 }
 
 
