@@ -261,6 +261,8 @@ long long fs_kernel_launches(const fs_grid* grid);
  *   "fft_lines"       complex lines per block of the mixed-radix transforms
  *                     (lengths other than 64, 128, 256): 1..16
  *   "predictor_cells" cells per thread of the FP32 3-D predictor: 2 or 4 (default)
+ *   "predictor_zmarch" z planes per thread of the four-cell predictor: 1 (no
+ *                     march) .. 64; default 8
  *   "pdl"             1 (default): step kernels use programmatic dependent
  *                     launch (each starts while its predecessor drains);
  *                     0: ordinary stream-ordered launches

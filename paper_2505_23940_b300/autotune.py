@@ -15,6 +15,7 @@ CANDIDATES = {
     "stencil_bx": [32, 64, 128],
     "fft_lines": [4, 8, 16],
     "predictor_cells": [4, 2],
+    "predictor_zmarch": [8, 4, 1],
 }
 
 

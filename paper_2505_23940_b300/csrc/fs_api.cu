@@ -629,6 +629,9 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "predictor_cells") {
     if (value != 0 && value != 2 && value != 4) return set_error(FS_ERR_ARG, "predictor_cells must be 2 or 4");
     G->tune_pred_vw = value;
+  } else if (k == "predictor_zmarch") {
+    if (value < 0 || value > 64) return set_error(FS_ERR_ARG, "predictor_zmarch must be in 0..64");
+    G->tune_zmarch = value;
   } else if (k == "pdl") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "pdl must be 0 or 1");
     G->use_pdl = value == 1;

@@ -649,6 +649,128 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
   stw<VW>(A.out[1] + v00 + i0, o3[1]);
 }
 
+// The four-cell FP32 predictor marching in z: a thread computes the cells
+// (i0 .. i0+3, j) of KZ consecutive planes, keeping the rows shared by
+// neighbouring planes (the z neighbours of the stencil) in registers, so a plane
+// takes 9 four-wide and 7 scalar loads instead of 17 and 10.
+template <bool YPER>
+__global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs<float> A, int KZ) {
+  pdl_wait();
+  const Geom<float>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k0 = blockIdx.z * KZ;
+  const int k1 = min(k0 + KZ, nz);
+  if (i0 >= nx || j >= A.Y) return;
+  if (!YPER && (j < 2 || j > ny - 2)) {
+    for (int k = k0; k < k1; ++k)
+      for (int e = 0; e < 4; ++e) predict_cell_general(A, i0 + e, j, k);
+    return;
+  }
+  const int jm = YPER ? (j > 0 ? j - 1 : ny - 1) : j - 1;
+  const int jp = YPER ? (j < ny - 1 ? j + 1 : 0) : j + 1;
+  const int eyv = YPER ? ny : ny + 1;
+  auto ru = [&](int jj, int kk) { return nx * (jj + ny * kk); };
+  auto rv = [&](int jj, int kk) { return nx * (jj + eyv * kk); };
+  auto wrapk = [&](int kk) { return kk < 0 ? kk + nz : (kk >= nz ? kk - nz : kk); };
+  const float* __restrict__ U = A.uin[0];
+  const float* __restrict__ V = A.uin[1];
+  const float* __restrict__ W = A.uin[2];
+  constexpr int L = 6;
+  // rows carried from plane to plane
+  float Uc[L], Ukm[L], Vc[L], Vkm[L], Vpkm[L], Wc[L], Wmc[L], Wkm[L];
+  {
+    const int km = wrapk(k0 - 1);
+    ld_seg<true, true, 4>(U + ru(j, k0), i0, nx, Uc);
+    ld_seg<true, true, 4>(U + ru(j, km), i0, nx, Ukm);
+    ld_seg<true, true, 4>(V + rv(j, k0), i0, nx, Vc);
+    ld_seg<false, false, 4>(V + rv(j, km), i0, nx, Vkm);
+    ld_seg<false, false, 4>(V + rv(jp, km), i0, nx, Vpkm);
+    ld_seg<true, true, 4>(W + ru(j, k0), i0, nx, Wc);
+    ld_seg<false, false, 4>(W + ru(jm, k0), i0, nx, Wmc);
+    ld_seg<false, false, 4>(W + ru(j, km), i0, nx, Wkm);
+  }
+  const YMet<float> m = ymet<float, YPER>(A, j);
+  const float bf = g.bforce ? g.bforce[j] : 0.f;
+  const float a = A.a, b = A.b, dt = A.dt;
+  for (int k = k0; k < k1; ++k) {
+    const int kp = wrapk(k + 1);
+    float UM0[L], UP0[L], U0P[L], VM0[L], VP0[L], V0P[L], WP0[L], W0P[L], WMP[L];
+    ld_seg<false, true, 4>(U + ru(jm, k), i0, nx, UM0);
+    ld_seg<false, false, 4>(U + ru(jp, k), i0, nx, UP0);
+    ld_seg<true, true, 4>(U + ru(j, kp), i0, nx, U0P);
+    ld_seg<false, false, 4>(V + rv(jm, k), i0, nx, VM0);
+    ld_seg<true, false, 4>(V + rv(jp, k), i0, nx, VP0);
+    ld_seg<true, true, 4>(V + rv(j, kp), i0, nx, V0P);
+    ld_seg<false, false, 4>(W + ru(jp, k), i0, nx, WP0);
+    ld_seg<true, true, 4>(W + ru(j, kp), i0, nx, W0P);
+    ld_seg<false, false, 4>(W + ru(jm, kp), i0, nx, WMP);
+    float o3[3][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = e + 1;
+      Nb27<float> n;
+      n.u000 = Uc[c]; n.uM00 = Uc[c - 1]; n.uP00 = Uc[c + 1];
+      n.u0M0 = UM0[c]; n.uPM0 = UM0[c + 1]; n.u0P0 = UP0[c];
+      n.u00M = Ukm[c]; n.uP0M = Ukm[c + 1]; n.u00P = U0P[c];
+      n.v000 = Vc[c]; n.vM00 = Vc[c - 1]; n.vP00 = Vc[c + 1];
+      n.v0M0 = VM0[c]; n.v0P0 = VP0[c]; n.vMP0 = VP0[c - 1];
+      n.v00M = Vkm[c]; n.v00P = V0P[c]; n.v0PM = Vpkm[c];
+      n.w000 = Wc[c]; n.wM00 = Wc[c - 1]; n.wP00 = Wc[c + 1];
+      n.w0M0 = Wmc[c]; n.w0P0 = WP0[c]; n.w00M = Wkm[c];
+      n.w00P = W0P[c]; n.wM0P = W0P[c - 1]; n.w0MP = WMP[c];
+      float Ru, Rv, Rw;
+      rhs3(n, m, g.ihx, g.ihz, g.nu, bf, Ru, Rv, Rw);
+      o3[0][e] = b * (n.u000 + dt * Ru);
+      o3[1][e] = b * (n.v000 + dt * Rv);
+      o3[2][e] = b * (n.w000 + dt * Rw);
+    }
+    const int rows[3] = {ru(j, k), rv(j, k), ru(j, k)};
+    if (a != 0.f) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float pn[4];
+        ldw<4>(A.un[c] + rows[c] + i0, pn);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o3[c][e] += a * pn[e];
+      }
+    }
+    if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        float fo[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          fo[e] = 0.f;
+          if (A.flags3[c][rows[c] + i0 + e]) {
+            fo[e] = -o3[c][e] / dt;
+            o3[c][e] = 0.f;
+          }
+        }
+        stw<4>(A.fout3[c] + rows[c] + i0, fo);
+      }
+    }
+    if (j < ny) {
+      stw<4>(A.out[0] + rows[0] + i0, o3[0]);
+      stw<4>(A.out[2] + rows[2] + i0, o3[2]);
+    }
+    stw<4>(A.out[1] + rows[1] + i0, o3[1]);
+    // next plane: the centre rows move to k - 1, the k + 1 rows to the centre
+#pragma unroll
+    for (int q = 0; q < L; ++q) {
+      Ukm[q] = Uc[q];
+      Uc[q] = U0P[q];
+      Vkm[q] = Vc[q];
+      Vpkm[q] = VP0[q];
+      Vc[q] = V0P[q];
+      Wkm[q] = Wc[q];
+      Wc[q] = W0P[q];
+      Wmc[q] = WMP[q];
+    }
+  }
+}
+
 template <typename T>
 __global__ void outflow_scale_kernel(const T* __restrict__ u0, int ex, int ny, int nz, const double* __restrict__ hy,
                                      double hz, double q_in, double* scale) {
@@ -920,6 +1042,14 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
         vec = vec && (uintptr_t)uin[c] % (4 * vw) == 0 && (uintptr_t)out[c] % (4 * vw) == 0;
         if (un) vec = vec && (uintptr_t)un[c] % (4 * vw) == 0;
         if (G->has_ib3) vec = vec && (uintptr_t)G->ib3.f[c] % (4 * vw) == 0;
+      }
+      const int KZ = G->tune_zmarch > 0 ? G->tune_zmarch : 8;
+      if (vec && vw == 4 && KZ > 1) {
+        const dim3 vb(32, 8);
+        const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, (G->nz + KZ - 1) / KZ);
+        if (G->per[1]) launch_pdl(G, "predictor", predictor3z_kernel<true>, vg, vb, 0, A, KZ);
+        else launch_pdl(G, "predictor", predictor3z_kernel<false>, vg, vb, 0, A, KZ);
+        return;
       }
       if (vec) {
         const dim3 vb(32, 8);
