@@ -583,14 +583,21 @@ __global__ void __launch_bounds__(kRegBlock) yspec_reg_kernel(T* __restrict__ da
   __syncthreads();
   fft_reg_block<T, N, false>(S, tws);
   __syncthreads();
+  // x + z eigenvalues of the block's slot pairs and the y eigenvalues, staged once
+  __shared__ T Lab[2 * kRegLines], Ly[N / 2 + 1];
+  if (threadIdx.x < 2 * nl) {
+    const int sa = s0 + threadIdx.x;
+    const int sl = sa < A.nx ? sa : sa - 1;   // the odd tail's missing partner takes its neighbour's value
+    Lab[threadIdx.x] = lamxz[lam_index_spec<T>(A, sl, t)];
+  }
+  for (int k = threadIdx.x; k <= N / 2; k += blockDim.x) Ly[k] = lamy[k];
+  __syncthreads();
   constexpr int NH = N / 2 + 1;
   for (int e = threadIdx.x; e < nl * NH; e += blockDim.x) {
     const int l = e / NH, k = e - l * NH;
     const int kk = k == 0 ? 0 : N - k;
-    const int sa = s0 + 2 * l, sb = sa + 1;
-    const T La = lamxz[lam_index_spec<T>(A, sa, t)];
-    const T Lb = sb < A.nx ? lamxz[lam_index_spec<T>(A, sb, t)] : La;
-    const T ly = lamy[k];
+    const T La = Lab[2 * l], Lb = Lab[2 * l + 1];
+    const T ly = Ly[k];
     const T ma = ly + La, mb = ly + Lb;
     const T ia = ma != T(0) ? T(1) / ma : T(0);
     const T ib = mb != T(0) ? T(1) / mb : T(0);
