@@ -49,13 +49,13 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on: a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50394624 + 1619712, "src": "0d59fe23c37e"},
-    "fft_x_fwd_div": {"bytes": 25243648 + 20480, "src": "064fb2dec636"},
-    "fft_z_fwd": {"bytes": 8407552, "src": "064fb2dec636"},
-    "fft_y_solve": {"bytes": 8432896, "src": "064fb2dec636"},
-    "fft_z_inv": {"bytes": 8419072, "src": "064fb2dec636"},
-    "fft_x_inv": {"bytes": 8414976, "src": "064fb2dec636"},
-    "correct": {"bytes": 33560576 + 3328, "src": "0d59fe23c37e"},
+    "predictor": {"bytes": 50552320 + 1046784, "src": "8e74c07db183"},
+    "fft_x_fwd_div": {"bytes": 25244160 + 0, "src": "4b64e2a187d4"},
+    "fft_z_fwd": {"bytes": 8407296, "src": "4b64e2a187d4"},
+    "fft_y_solve": {"bytes": 8435712, "src": "4b64e2a187d4"},
+    "fft_z_inv": {"bytes": 8410368, "src": "4b64e2a187d4"},
+    "fft_x_inv": {"bytes": 8414720, "src": "4b64e2a187d4"},
+    "correct": {"bytes": 33560576 + 256, "src": "8e74c07db183"},
 }
 
 

@@ -266,7 +266,12 @@ long long fs_kernel_launches(const fs_grid* grid);
  *   "pdl"             1 (default): step kernels use programmatic dependent
  *                     launch (each starts while its predecessor drains);
  *                     0: ordinary stream-ordered launches
- * Results do not depend on them.  FS_ERR_ARG for an unknown key or value. */
+ *   "ysolve_segments" segments per column of the partitioned wall-bounded y
+ *                     solve: 4, 8 or 16 (default: 4, 8 when the grid has
+ *                     fewer 32-column blocks than two per SM); rebuilds the y tables
+ *                     (synchronises the stream; set it before capturing graphs)
+ * Results do not depend on them (ysolve_segments: up to rounding).
+ * FS_ERR_ARG for an unknown key or value. */
 int fs_set_tuning(fs_grid* grid, const char* key, int value);
 
 /* Kernel timing.  After fs_profile_begin, every launch whose kernel name

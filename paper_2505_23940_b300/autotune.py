@@ -16,6 +16,7 @@ CANDIDATES = {
     "fft_lines": [4, 8, 16],
     "predictor_cells": [4, 2],
     "predictor_zmarch": [8, 4, 1],
+    "ysolve_segments": [4, 8, 16],
 }
 
 

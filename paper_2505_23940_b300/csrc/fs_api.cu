@@ -119,13 +119,22 @@ size_t comp_size(const fs_grid* G, int c) {
 size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) : sizeof(double); }
 
 // FP64 tables of the partitioned y solve, one column per eigenvalue index:
-// for each of the 4 segments of every column, the local Thomas factors of the
+// for each of the NSEG segments of every column, the local Thomas factors of the
 // segment's block (e_j = 1 / beta_j, c'_j) and its right / left spikes v, w
 // (the block's response to its coupling with the next / previous segment).
 // The singular zero mode replaces row 0 by phi_0 = 0 (e_0 = 0, no couplings).
+// NSEG is 4 unless the grid has fewer 32-column blocks than two per SM (2-D
+// grids): then 8 shorter segments halve the sequential sweeps (16 segments
+// cost more in the denser interface solve than they save).
 int build_tables(fs_grid* G) {
-  constexpr int NSEG = 4;
   const int nx = G->nx, ny = G->ny, nz = G->nz;
+  if (G->tune_ynseg > 0) {
+    G->ynseg = G->tune_ynseg;
+  } else {
+    const long blocks = (long)((nx + 31) / 32) * (G->dim == 3 ? nz : 1);
+    G->ynseg = (blocks < 2 * 148 && ny >= 8 * 8) ? 8 : 4;
+  }
+  const int NSEG = G->ynseg;
   G->nmx = G->xmode == 1 ? nx : nx / 2 + 1;
   G->nlz = G->dim == 3 ? nz / 2 + 1 : 1;
   const int nlam = G->nmx * G->nlz;
@@ -150,6 +159,8 @@ int build_tables(fs_grid* G) {
   }
   const std::vector<double>& h = G->h[1];
   const std::vector<double>& hf = G->hf[1];
+  G->hysum = 0.0;
+  for (int j = 0; j < ny; ++j) G->hysum += h[j];
   std::vector<double> a(ny), c(ny);
   for (int j = 0; j < ny; ++j) {
     a[j] = 1.0 / (hf[j] * h[j]);        // coupling of row j to j - 1 (row 0: wraps to ny - 1)
@@ -160,7 +171,7 @@ int build_tables(fs_grid* G) {
     c[ny - 1] = 0.0;
   }
   G->cyclic = G->per[1];
-  constexpr int NRED = 2 * NSEG;
+  const int NRED = 2 * NSEG;
   std::vector<double> E((size_t)ny * nlam), CP((size_t)ny * nlam), V((size_t)ny * nlam), W((size_t)ny * nlam);
   std::vector<double> MI((size_t)NRED * NRED * nlam);
   std::vector<double> aa(ny), cc(ny), dd(ny), e(ny), cp(ny), dp(ny), x(ny);
@@ -208,7 +219,7 @@ int build_tables(fs_grid* G) {
         }
       }
       // interface system X_p + v X_{p+1} + w Y_{p-1} = y_first, Y_p + v X_{p+1} + w Y_{p-1} = y_last
-      double M[NRED][2 * NRED];
+      std::vector<std::vector<double>> M(NRED, std::vector<double>(2 * NRED));
       for (int r = 0; r < NRED; ++r)
         for (int q = 0; q < 2 * NRED; ++q) M[r][q] = (q == r || q == r + NRED) ? 1.0 : 0.0;
       for (int g = 0; g < NSEG; ++g) {
@@ -248,6 +259,14 @@ int build_tables(fs_grid* G) {
   return FS_OK;
 }
 
+void free_ytables(fs_grid* G) {
+  double** t[6] = {&G->ya, &G->tE, &G->tCP, &G->tZV, &G->tWV, &G->tMI};
+  for (double** p : t) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+}
+
 void free_all(fs_grid* G) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
@@ -263,7 +282,7 @@ void free_all(fs_grid* G) {
   for (int q = 0; q < 4; ++q) F(G->les_nu[q]);
   F(G->px.tw); F(G->px.dtw); F(G->py.tw); F(G->py.dtw); F(G->pz.tw); F(G->pz.dtw);
   F(G->lamy); F(G->lamxz);
-  F(G->ya); F(G->tE); F(G->tCP); F(G->tZV); F(G->tWV); F(G->tMI);
+  free_ytables(G);
   IBDev& B = G->ib;
   F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
@@ -635,6 +654,16 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "pdl") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "pdl must be 0 or 1");
     G->use_pdl = value == 1;
+  } else if (k == "ysolve_segments") {
+    if (value != 0 && value != 4 && value != 8 && value != 16)
+      return set_error(FS_ERR_ARG, "ysolve_segments must be 4, 8 or 16");
+    if (value == G->tune_ynseg) return FS_OK;
+    G->tune_ynseg = value;
+    if (G->yspec) return FS_OK;   // periodic y has no partitioned solve
+    const cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
+    free_ytables(G);
+    return build_tables(G);
   } else {
     return set_error(FS_ERR_ARG, "unknown tuning key " + k);
   }

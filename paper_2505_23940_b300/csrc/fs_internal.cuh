@@ -288,7 +288,10 @@ struct fs_grid {
   double* ya = nullptr;        // a_j couplings (ny)
   double *tE = nullptr, *tCP = nullptr;   // [ny][nlz][nmx] segment factors e_j, c'_j
   double *tZV = nullptr, *tWV = nullptr;  // [ny][nlz][nmx] right / left spikes of each segment
-  double *tMI = nullptr;                  // [64][nlz][nmx] inverse of the 8 x 8 interface system
+  double *tMI = nullptr;                  // [4 ynseg^2][nlz][nmx] inverse of the 2 ynseg interface system
+  int ynseg = 4;                          // segments per column of the partitioned y solve (4, 8 or 16)
+  double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
+  int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
 
   fs::IBDev ib;
   bool has_body = false;

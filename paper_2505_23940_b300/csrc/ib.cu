@@ -2,13 +2,18 @@
 //
 //   classify_solid   solid faces: crossing-number test of (face - w) against the
 //                    rest polygon, every FP64 operation rounded on its own
-//                    (__d*_rn) so the integer decision is the oracle's bit for bit
+//                    (__d*_rn) so the integer decision is the oracle's bit for bit;
+//                    one block per face row finds the edges crossing the row's
+//                    height once, then every face of the row counts the crossings
+//                    to its right (both components in one launch)
 //   classify_ib      IB faces: non-solid faces with a solid same-component neighbour
-//   fn_gather        F_N of Eq. (19) per marker and component (support nodes that are not solid)
+//   fn_gather        F_N of Eq. (19) per marker and component (support nodes that are
+//                    not solid); 16 lanes per (marker, component), one support node
+//                    each, summed by shuffles
 //   ib_scatter       Eq. (18), normalised: numerator / denominator of u_IB on IB faces;
 //                    markers are sorted by cell, contributions to the same face are
 //                    summed inside the warp (match_any + shuffles) before one atomicAdd
-//   force_gather     q_i of Eq. (20) per marker (FP64 sums)
+//   force_gather     q_i of Eq. (20) per marker (FP64 sums, 16 lanes per marker and component)
 //   force_reduce     F = rho sum q_i dV_i and torque, one CTA, fixed order (FP64)
 //   rk4              Eq. (12), classical RK4 with the force frozen (one thread, FP64)
 //
@@ -16,6 +21,7 @@
 // kernel phi in the field precision T.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "fs_internal.cuh"
@@ -60,20 +66,62 @@ __device__ __forceinline__ void face_pos(int c, int i, int j, const double* xf, 
   }
 }
 
-__global__ void classify_solid_kernel(uint8_t* __restrict__ flags, int c, int ex, int ey, const double* xf,
-                                      const double* yf, const double* body, Poly P) {
-  const long long total = (long long)ex * ey;
+constexpr int kRowCross = 1024;   // crossings of one face row held in shared memory
+
+struct Flags {
+  uint8_t* p[2];
+};
+
+// grid (rows, 2 components); face rows outside the polygon's displaced box are cleared.
+__global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0, int ey0, int ex1, int ey1,
+                                                             const double* __restrict__ xf,
+                                                             const double* __restrict__ yf,
+                                                             const double* __restrict__ body, Poly P) {
+  __shared__ double xs[kRowCross];
+  __shared__ int cnt;
+  const int c = blockIdx.y, j = blockIdx.x;
+  const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
+  if (j >= ey) return;
+  uint8_t* row = (c ? flags.p[1] : flags.p[0]) + (size_t)j * ex;
   const double wx = body[0], wy = body[1];
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex), j = (int)(t / ex);
-    double px, py;
-    face_pos(c, i, j, xf, yf, px, py);
-    flags[t] = inside_polygon(P, __dsub_rn(px, wx), __dsub_rn(py, wy)) ? 1 : 0;
+  const double py = __dsub_rn(c == 0 ? __dmul_rn(0.5, __dadd_rn(yf[j], yf[j + 1])) : yf[j], wy);
+  if (py < P.bb[2] || py > P.bb[3]) {
+    for (int i = threadIdx.x; i < ex; i += blockDim.x) row[i] = 0;
+    return;
+  }
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  // x where each edge crosses the row's height (the order of the crossings does not matter to the parity)
+  for (int e = threadIdx.x; e < P.n; e += blockDim.x) {
+    const double ax = P.X[e], ay = P.Y[e];
+    const int f = (e + 1 == P.n) ? 0 : e + 1;
+    const double bx = P.X[f], by = P.Y[f];
+    if ((ay > py) != (by > py)) {
+      const double xint = __dadd_rn(ax, __ddiv_rn(__dmul_rn(__dsub_rn(py, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
+      const int k = atomicAdd(&cnt, 1);
+      if (k < kRowCross) xs[k] = xint;
+    }
+  }
+  __syncthreads();
+  const int nc = cnt;
+  for (int i = threadIdx.x; i < ex; i += blockDim.x) {
+    const double px = __dsub_rn(c == 0 ? xf[i] : __dmul_rn(0.5, __dadd_rn(xf[i], xf[i + 1])), wx);
+    bool in = false;
+    if (nc > kRowCross) {
+      in = inside_polygon(P, px, py);
+    } else if (px >= P.bb[0] && px <= P.bb[1]) {
+      for (int k = 0; k < nc; ++k)
+        if (px < xs[k]) in = !in;
+    }
+    row[i] = in ? 1 : 0;
   }
 }
 
-__global__ void classify_ib_kernel(uint8_t* __restrict__ flags, int ex, int ey, int perx, int pery) {
+// grid (blocks, 2 components)
+__global__ void classify_ib_kernel(Flags F, int ex0, int ey0, int ex1, int ey1, int perx, int pery) {
+  const int c = blockIdx.y;
+  const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
+  uint8_t* __restrict__ flags = c ? F.p[1] : F.p[0];
   const long long total = (long long)ex * ey;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
@@ -115,14 +163,11 @@ __device__ __forceinline__ T phi_kernel(int kind, T r) {
   return T(0);
 }
 
-struct Flags {
-  uint8_t* p[2];
-};
-
 struct IBGeom {
   int ex[2], ey[2];
   double x0c[2], y0c[2];   // position of node (0, 0) of each component
   double hx, hy;
+  double ihx, ihy, ihxy;   // 1 / hx, 1 / hy, 1 / (hx hy)
   int kind;
   int width;               // support nodes per direction (3 Roma, 4 Peskin)
   const double* xf;
@@ -145,29 +190,50 @@ __device__ __forceinline__ double node_y(const IBGeom& G, int c, int j) {
   return c == 1 ? G.yf[j] : __dmul_rn(0.5, __dadd_rn(G.yf[j], G.yf[j + 1]));
 }
 
+// Support node of one lane: 16 lanes per (marker, component) pair, lane l -> node
+// (a, b) = (l mod width, l / width); lanes with b >= width hold no node.
+struct Lane {
+  int pair, m, c, a, b;
+  bool live;
+};
+
+__device__ __forceinline__ Lane lane_of(const IBGeom& G, int nm) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  Lane L;
+  L.pair = t >> 4;
+  const int l = t & 15;
+  L.m = L.pair >> 1;
+  L.c = L.pair & 1;
+  L.a = l % G.width;
+  L.b = l / G.width;
+  L.live = L.pair < 2 * nm;
+  return L;
+}
+
+__device__ __forceinline__ double sum16(double s) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 // F_N_i for both components (Eq. 19)
 template <typename T>
 __global__ void fn_gather_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
                                  const double* __restrict__ body, const Flags flags, double* __restrict__ fn) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * nm) return;
-  const int m = t >> 1, c = t & 1;
-  const double X = X0[m] + body[0], Y = Y0[m] + body[1];
-  const int i0 = first_node(G, X, G.x0c[c], G.hx), j0 = first_node(G, Y, G.y0c[c], G.hy);
+  const Lane L = lane_of(G, nm);
   double s = 0.0;
-  for (int b = 0; b < G.width; ++b) {
-    const int j = j0 + b;
-    if (j < 0 || j >= G.ey[c]) continue;
-    const T py = T(phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) / G.hy)));
-    for (int a = 0; a < G.width; ++a) {
-      const int i = i0 + a;
-      if (i < 0 || i >= G.ex[c]) continue;
-      if (flags.p[c][(size_t)j * G.ex[c] + i] & 1) continue;   // solid nodes excluded
-      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) / G.hx));
-      s += (double)(px * py) / (G.hx * G.hy);
+  if (L.live && L.b < G.width) {
+    const int c = L.c;
+    const double X = X0[L.m] + body[0], Y = Y0[L.m] + body[1];
+    const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
+    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c] && !((c ? flags.p[1] : flags.p[0])[(size_t)j * G.ex[c] + i] & 1)) {
+      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
+      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
+      s = (double)(px * py) * G.ihxy;
     }
   }
-  fn[t] = s;
+  s = sum16(s);
+  if (L.live && (threadIdx.x & 15) == 0) fn[L.pair] = s;
 }
 
 // Eq. (18): num += w_i wdot_i, den += w_i on IB faces, w_i = delta dV_i / F_N_i.
@@ -195,9 +261,9 @@ __global__ void ib_scatter_kernel(const IBGeom G, int nm, const double* __restri
       if (flags.p[c][f] & 2) {
         const double F = fn[2 * m + c];
         if (F > 0.0) {
-          const T d = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) / G.hx)) *
-                      phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) / G.hy));
-          w = T((double)d / (G.hx * G.hy) * (ds[m] * G.hx) / F);
+          const T d = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx)) *
+                      phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
+          w = T((double)d * G.ihxy * (ds[m] * G.hx) / F);
           // marker velocity: body translation plus surface rotation
           const double vm = c == 0 ? body[2] - omega * (Y - (cy + body[1])) : body[3] + omega * (X - (cx + body[0]));
           wv = w * T(vm);
@@ -236,27 +302,22 @@ template <typename T>
 __global__ void force_gather_kernel(const IBGeom G, int nm, const double* __restrict__ X0,
                                     const double* __restrict__ Y0, const double* __restrict__ body,
                                     const T* __restrict__ f0, const T* __restrict__ f1, double* __restrict__ q) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 2 * nm) return;
-  const int m = t >> 1, c = t & 1;
-  const T* f = c == 0 ? f0 : f1;
-  const double X = X0[m] + body[0], Y = Y0[m] + body[1];
-  const int i0 = first_node(G, X, G.x0c[c], G.hx), j0 = first_node(G, Y, G.y0c[c], G.hy);
+  const Lane L = lane_of(G, nm);
   double s = 0.0;
-  for (int b = 0; b < G.width; ++b) {
-    const int j = j0 + b;
-    if (j < 0 || j >= G.ey[c]) continue;
-    const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) / G.hy));
-    const double dvy = c == 0 ? G.hyv[j] : G.hfyv[j];
-    for (int a = 0; a < G.width; ++a) {
-      const int i = i0 + a;
-      if (i < 0 || i >= G.ex[c]) continue;
-      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) / G.hx));
-      const double d = (double)(px * py) / (G.hx * G.hy);
-      s += (double)f[(size_t)j * G.ex[c] + i] * d * (G.hfx * dvy);
+  if (L.live && L.b < G.width) {
+    const int c = L.c;
+    const T* f = c == 0 ? f0 : f1;
+    const double X = X0[L.m] + body[0], Y = Y0[L.m] + body[1];
+    const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
+    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
+      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
+      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
+      const double dvy = c == 0 ? G.hyv[j] : G.hfyv[j];
+      s = (double)f[(size_t)j * G.ex[c] + i] * ((double)(px * py) * G.ihxy) * (G.hfx * dvy);
     }
   }
-  q[t] = -s;
+  s = sum16(s);
+  if (L.live && (threadIdx.x & 15) == 0) q[L.pair] = -s;
 }
 
 // F = rho sum_i q_i dV_i, torque = rho sum_i dV_i (r_i x q_i); one CTA, fixed summation order.
@@ -324,6 +385,9 @@ IBGeom make_geom(const fs_grid* G) {
   }
   g.hx = G->hx;
   g.hy = G->h[1][0];
+  g.ihx = 1.0 / g.hx;
+  g.ihy = 1.0 / g.hy;
+  g.ihxy = 1.0 / (g.hx * g.hy);
   g.x0c[0] = G->xf[0][0];
   g.x0c[1] = 0.5 * (G->xf[0][0] + G->xf[0][1]);
   g.y0c[0] = 0.5 * (G->xf[1][0] + G->xf[1][1]);
@@ -348,25 +412,26 @@ void ib_prepare(fs_grid* G, const double* body_state) {
   P.Y = B.PY;
   P.n = B.nm;
   for (int q = 0; q < 4; ++q) P.bb[q] = B.poly_bb[q];
-  for (int c = 0; c < 2; ++c) {
-    const int ex = G->nx + ((c == 0 && !G->per[0]) ? 1 : 0), ey = G->ny + ((c == 1 && !G->per[1]) ? 1 : 0);
-    const long long n = (long long)ex * ey;
-    int nb = (int)((n + kT - 1) / kT);
-    if (nb > 148 * 16) nb = 148 * 16;
-    FS_LAUNCH(G, "classify_solid", classify_solid_kernel<<<nb, kT, 0, G->stream>>>(B.flags[c], c, ex, ey, G->xf64[0], G->xf64[1], body_state, P));
-  }
-  for (int c = 0; c < 2; ++c) {
-    const int ex = G->nx + ((c == 0 && !G->per[0]) ? 1 : 0), ey = G->ny + ((c == 1 && !G->per[1]) ? 1 : 0);
-    const long long n = (long long)ex * ey;
-    int nb = (int)((n + kT - 1) / kT);
-    if (nb > 148 * 16) nb = 148 * 16;
-    FS_LAUNCH(G, "classify_ib", classify_ib_kernel<<<nb, kT, 0, G->stream>>>(B.flags[c], ex, ey, G->per[0], G->per[1]));
-  }
-  const IBGeom g = make_geom(G);
   Flags dflags;
   dflags.p[0] = B.flags[0];
   dflags.p[1] = B.flags[1];
-  FS_LAUNCH(G, "fn_gather", fn_gather_kernel<T><<<(2 * B.nm + 127) / 128, 128, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state, dflags, B.fn));
+  int ex[2], ey[2];
+  for (int c = 0; c < 2; ++c) {
+    ex[c] = G->nx + ((c == 0 && !G->per[0]) ? 1 : 0);
+    ey[c] = G->ny + ((c == 1 && !G->per[1]) ? 1 : 0);
+  }
+  FS_LAUNCH(G, "classify_solid", classify_solid_kernel<<<dim3(std::max(ey[0], ey[1]), 2), kT, 0, G->stream>>>(
+                                     dflags, ex[0], ey[0], ex[1], ey[1], G->xf64[0], G->xf64[1], body_state, P));
+  {
+    const long long n = (long long)std::max(ex[0] * ey[0], ex[1] * ey[1]);
+    int nb = (int)((n + kT - 1) / kT);
+    if (nb > 148 * 8) nb = 148 * 8;
+    FS_LAUNCH(G, "classify_ib", classify_ib_kernel<<<dim3(nb, 2), kT, 0, G->stream>>>(dflags, ex[0], ey[0], ex[1], ey[1],
+                                                                                        G->per[0], G->per[1]));
+  }
+  const IBGeom g = make_geom(G);
+  const int nlane = 2 * B.nm * 16;
+  FS_LAUNCH(G, "fn_gather", fn_gather_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state, dflags, B.fn));
   const long long total = 2ll * B.nm * g.width * g.width;
   FS_LAUNCH(G, "ib_scatter", ib_scatter_kernel<T><<<(int)((total + kT - 1) / kT), kT, 0, G->stream>>>(
       g, B.nm, B.X0, B.Y0, B.ds, body_state, B.omega, B.centre[0], B.centre[1], dflags, B.fn, (T*)B.num[0],
@@ -377,7 +442,8 @@ template <typename T>
 void ib_forces(fs_grid* G, const double* body_state) {
   IBDev& B = G->ib;
   const IBGeom g = make_geom(G);
-  FS_LAUNCH(G, "force_gather", force_gather_kernel<T><<<(2 * B.nm + 127) / 128, 128, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state,
+  const int nlane = 2 * B.nm * 16;
+  FS_LAUNCH(G, "force_gather", force_gather_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state,
                                                                           (const T*)B.f[0], (const T*)B.f[1], B.q));
   FS_LAUNCH(G, "force_reduce", force_reduce_kernel<<<1, kT, 0, G->stream>>>(B.nm, B.X0, B.Y0, B.ds, body_state, B.centre[0], B.centre[1], G->hx,
                                                G->rho, B.q, B.F));

@@ -535,6 +535,7 @@ struct YArgs {
   const double* WV;      // left spikes w_j   [ny][nlam]
   const double* MI;      // inverse interface matrices [NRED * NRED][nlam]
   const double* hy;      // cell widths (zero-mode mean)
+  double hysum;          // sum of the cell widths
 };
 
 __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
@@ -548,7 +549,8 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
 }
 
 // Partitioned (SPIKE) solve: every column is split into NSEG segments of
-// about ny / NSEG rows solved concurrently by NSEG threads.  Each segment's
+// about ny / NSEG rows solved concurrently by NSEG threads (NSEG = 4, or 8
+// when the grid has too few columns to occupy every SM twice: 2-D grids).  Each segment's
 // local factors (e_j = 1 / beta_j, c'_j) and its two spikes (the response to
 // its coupling with the neighbouring segments, v_j and w_j) are tabulated per
 // eigenvalue on the host, so one step of the solve is
@@ -557,21 +559,20 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
 //        X_p + v_f X_{p+1} + w_f Y_{p-1} = y_f,   Y_p + v_l X_{p+1} + w_l Y_{p-1} = y_l
 //      (periodic y couples the last and first segments).  That 2 NSEG system
 //      depends on the eigenvalue only: its inverse is tabulated on the host and
-//      the four threads of a column each form two of its rows' products in FP64
+//      the NSEG threads of a column each form two of its rows' products in FP64
 //   3. x_j = y_j - v_j X_{p+1} - w_j Y_{p-1} on every row.
 // The singular zero mode pins x_0 = 0 (e_0 = 0 in its table) and is shifted to
 // zero hy-weighted mean afterwards.
-constexpr int NSEG = 4;
 constexpr int YCOLS = 32;
-constexpr int NRED = 2 * NSEG;
 
-template <typename T>
+template <typename T, int NSEG>
 __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ data, const YArgs A) {
+  constexpr int NRED = 2 * NSEG;
   extern __shared__ double sm[];
   const int ny = A.ny;
   double* D = sm;                                  // [ny][YCOLS] data tile, then y, then x
   double* Z = D + (size_t)ny * YCOLS;              // [YCOLS][NRED] interface values
-  double* R = Z + YCOLS * NRED;                    // [YCOLS][2 NSEG] mean partial sums
+  double* R = Z + YCOLS * NRED;                    // [YCOLS][NSEG] mean partial sums
   const int tx = threadIdx.x, p = threadIdx.y;
   const int tid = tx + YCOLS * p;
   const int s0 = blockIdx.x * YCOLS;
@@ -581,6 +582,7 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   const int nlam = A.nmx * A.nlz;
   T* tile = data + s0 + (size_t)A.nx * A.ny * t;
   const size_t rs = (size_t)A.nx;
+#pragma unroll 8
   for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
     const int j = e / YCOLS, c = e - j * YCOLS;
     D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
@@ -594,10 +596,10 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   const double* V = A.ZV + li;    // right spikes
   const double* W = A.WV + li;    // left spikes
   double* col = D + tx;
+  constexpr int U = 8;            // table rows fetched ahead of their use
   if (act && r1 > r0) {
     // 1. segment Thomas
     double prev = 0.0;
-    constexpr int U = 8;
     int j = r0;
     for (; j + U <= r1; j += U) {
       double e[U], a[U];
@@ -656,7 +658,7 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     }
   }
   __syncthreads();
-  // 3. spike correction
+  // 3. spike correction (rows independent: table loads batched like the sweeps)
   double part = 0.0;
   if (act && r1 > r0) {
     const bool cyc = A.cyclic != 0;
@@ -664,23 +666,38 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     const int gn = p + 1 < NSEG ? p + 1 : 0, gp = p > 0 ? p - 1 : NSEG - 1;
     const double Xn = (p + 1 < NSEG || cyc) ? z[2 * gn] : 0.0;
     const double Yp = (p > 0 || cyc) ? z[2 * gp + 1] : 0.0;
-    for (int j = r0; j < r1; ++j) {
-      const double v = col[j * YCOLS] - __ldg(V + (size_t)j * nlam) * Xn - __ldg(W + (size_t)j * nlam) * Yp;
-      col[j * YCOLS] = v;
-      if (li == 0) part += v * A.hy[j];
+    int j = r0;
+    for (; j + U <= r1; j += U) {
+      double v[U], w[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        v[q] = __ldg(V + (size_t)(j + q) * nlam);
+        w[q] = __ldg(W + (size_t)(j + q) * nlam);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const double r = col[(j + q) * YCOLS] - v[q] * Xn - w[q] * Yp;
+        col[(j + q) * YCOLS] = r;
+        if (li == 0) part += r * __ldg(A.hy + j + q);
+      }
+    }
+    for (; j < r1; ++j) {
+      const double r = col[j * YCOLS] - __ldg(V + (size_t)j * nlam) * Xn - __ldg(W + (size_t)j * nlam) * Yp;
+      col[j * YCOLS] = r;
+      if (li == 0) part += r * __ldg(A.hy + j);
     }
   }
   // singular zero mode: shift to zero hy-weighted mean
   if (li == 0 && act) R[tx * NSEG + p] = part;
   __syncthreads();
   if (li == 0 && act && r1 > r0) {
-    double sx = 0.0, sw = 0.0;
+    double sx = 0.0;
     for (int g = 0; g < NSEG; ++g) sx += R[tx * NSEG + g];
-    for (int q = 0; q < ny; ++q) sw += A.hy[q];
-    const double mean = sx / sw;
+    const double mean = sx / A.hysum;
     for (int j = r0; j < r1; ++j) col[j * YCOLS] -= mean;
   }
   __syncthreads();
+#pragma unroll 8
   for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
     const int j = e / YCOLS, c = e - j * YCOLS;
     if (c < ncol) tile[rs * j + c] = (T)D[e];
@@ -886,6 +903,17 @@ void set_smem_attrs_reg() {
 
 bool is_reg_length(int n) { return n == 64 || n == 128 || n == 256; }
 
+// Lines per block of the mixed-radix x transforms: up to 16, fewer when the
+// grid has too few lines to give every SM two blocks (2-D grids).
+int default_lines(int lines) { return std::max(1, std::min(kMaxLines, lines / (2 * 148))); }
+
+// The register x transforms hold kRegLines lines per block; 2-D grids with
+// fewer lines than one such block per SM take the mixed-radix kernels, whose
+// block size adapts to the line count.
+bool x_reg(const fs_grid* G) {
+  return is_reg_length(G->nx) && (G->dim == 3 || (G->ny + 1) / 2 >= kRegLines * 148);
+}
+
 // Launches of the register-FFT kernels for a length known at compile time.
 template <typename T, int N>
 struct RegLaunch {
@@ -942,15 +970,17 @@ void set_smem_attrs() {
   set_smem_attrs_plan<T, 128>();
   set_smem_attrs_plan<T, 192>();
   set_smem_attrs_plan<T, 256>();
-  cudaFuncSetAttribute(ysolve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   done = true;
 }
 
 
 }  // namespace
 
-size_t ysolve_smem(int ny) {
-  return ((size_t)ny * YCOLS + YCOLS * NRED + YCOLS * NSEG) * sizeof(double);
+size_t ysolve_smem(int ny, int nseg) {
+  return ((size_t)ny * YCOLS + (size_t)YCOLS * 3 * nseg) * sizeof(double);
 }
 
 template <typename T>
@@ -959,13 +989,13 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int rows = ny * nz;
   // x forward
-  if (is_reg_length(nx)) {
+  if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xfwd(G, data, rows, dv); });
   } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
-    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
-    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
+    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : default_lines(lines);
+    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int nb = (lines + lpb - 1) / lpb;
     const FftKernels<T> K = fft_kernels<T>(G->px);
     auto k = dv ? K.xfwd_div : K.xfwd;
@@ -1039,8 +1069,17 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.WV = G->tWV;
     A.MI = G->tMI;
     A.hy = G->hy64;
+    A.hysum = G->hysum;
     dim3 grid((nx + YCOLS - 1) / YCOLS, G->dim == 3 ? nz : 1);
-    FS_LAUNCH(G, "ysolve", ysolve_kernel<T><<<grid, dim3(YCOLS, NSEG), ysolve_smem(ny), G->stream>>>(data, A));
+    const int ns = G->ynseg;
+    const size_t sb = ysolve_smem(ny, ns);
+    if (ns == 16) {
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16><<<grid, dim3(YCOLS, 16), sb, G->stream>>>(data, A));
+    } else if (ns == 8) {
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8><<<grid, dim3(YCOLS, 8), sb, G->stream>>>(data, A));
+    } else {
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
+    }
   }
   if (zreg) {
     with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data); });
@@ -1050,13 +1089,13 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
                                                             (const cplx<T>*)G->pz.tw));
   }
-  if (is_reg_length(nx)) {
+  if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xinv(G, data, rows); });
   } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
-    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : 16;
-    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int lines = (rows + 1) / 2;
+    const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : default_lines(lines);
+    lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int nb = (lines + lpb - 1) / lpb;
     auto k = fft_kernels<T>(G->px).xinv;
     FS_LAUNCH(G, "fft_x_inv", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),

@@ -96,6 +96,31 @@ def test_solve_pressure_fp64(kind, wl):
     assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
 
 
+@pytest.mark.parametrize("segments", [4, 8, 16])
+@pytest.mark.parametrize("wl", [
+    S.box_2d(40, 70, (P, P), (NS, NS), stretched=1.3),
+    S.box_2d(24, 37, (IN, OUT), (FS, FS)),
+    S.box_3d(10, 66, 6, (P, P), (NS, NS), stretched=1.5),
+])
+def test_solve_pressure_segments_fp64(wl, segments):
+    """The partitioned wall-normal solve with 4, 8 and 16 segments per column
+    (ragged segment lengths) against the oracle's direct solve."""
+    from paper_2505_23940_b300 import grid_from_workload
+    from oracle import fluid, poisson
+    g = grid_of(wl)
+    rng = np.random.default_rng(11)
+    u = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(g.dim)]
+    u = fluid.apply_boundary_values(g, u)
+    u = fluid.outflow_faces(g, u, u)
+    b = fluid.divergence(g, u)
+    ref = poisson.solve(g, b)
+    G = grid_from_workload(wl, "fp64")
+    G.set_tuning("ysolve_segments", segments)
+    p = G.solve_pressure(b.cuda().contiguous())
+    torch.cuda.synchronize()
+    assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+
+
 def _small_cyl(kernel, precision="fp64", omega=0.0):
     wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, kernel=kernel, centre_d=(2.0, 2.0),
                        precision=precision, seed=3, perturb=0.05, omega=omega)
