@@ -49,13 +49,13 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on: a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50552320 + 1046784, "src": "8e74c07db183"},
-    "fft_x_fwd_div": {"bytes": 25244160 + 0, "src": "4b64e2a187d4"},
-    "fft_z_fwd": {"bytes": 8407296, "src": "4b64e2a187d4"},
-    "fft_y_solve": {"bytes": 8435712, "src": "4b64e2a187d4"},
-    "fft_z_inv": {"bytes": 8410368, "src": "4b64e2a187d4"},
-    "fft_x_inv": {"bytes": 8414720, "src": "4b64e2a187d4"},
-    "correct": {"bytes": 33560576 + 256, "src": "8e74c07db183"},
+    "predictor": {"bytes": 50362880 + 851712, "src": "220d445780dc"},
+    "fft_x_fwd_div": {"bytes": 25243904 + 0, "src": "4b64e2a187d4"},
+    "fft_z_fwd": {"bytes": 8407040, "src": "4b64e2a187d4"},
+    "fft_y_solve": {"bytes": 8434688, "src": "4b64e2a187d4"},
+    "fft_z_inv": {"bytes": 8410624, "src": "4b64e2a187d4"},
+    "fft_x_inv": {"bytes": 8414464, "src": "4b64e2a187d4"},
+    "correct": {"bytes": 33560576 + 512, "src": "220d445780dc"},
 }
 
 
@@ -217,6 +217,26 @@ def timed_steps(g, u, dt, steps, flush, stream, body=None):
     return [a.elapsed_time(b) for a, b in times]
 
 
+def kernel_times(g, u, dt, steps, flush, stream, filt, body=None):
+    """Per-kernel CUDA-event times over `steps` flushed steps: every launch whose
+    name starts with `filt` is bracketed by its own events on the grid's stream.
+    Programmatic dependent launch is off for this pass, so that a launch's events
+    enclose that launch alone (with it on, a kernel starts while its predecessor
+    drains).  A separate pass from the timed region: events between launches
+    would slow the step they measure."""
+    g.set_tuning("pdl", 0)
+    prof = None
+    for _ in range(2):   # the first pass sizes the grid's event pool; the second is measured
+        # a timed spin (about 50 ms) at the head of the stream: every instrumented launch is queued
+        # before the GPU reaches it, so that no event interval contains host enqueue time
+        torch.cuda._sleep(100_000_000)
+        g.profile_begin(filt)
+        timed_steps(g, u, dt, steps, flush, stream, body)
+        prof = g.profile_end()
+    g.set_tuning("pdl", 1)
+    return prof
+
+
 def ensemble_leg(args, flush):
     """Batched ensemble of 2-D cylinder flows of uneven size: K steps of every member through one
     CUDA-graph launch, against the same members launched one by one (mixed precision)."""
@@ -275,26 +295,21 @@ def run_ours(args, ws, rank, local):
     for _ in range(args.warmup):
         g.step(u, wl.dt, 1)
     torch.cuda.synchronize()
-    # short profiling pass over every kernel: which one dominates the step
-    g.profile_begin("")
-    timed_steps(g, u, wl.dt, 2, flush, stream)
-    allk = g.profile_end()
-    dominant = max(allk, key=lambda k: allk[k][1])
-
     barrier(ws)
     torch.cuda.synchronize()
     launches0 = g.launches()
-    g.profile_begin(dominant)
     with Clocks(local) as clk:
         ms = timed_steps(g, u, wl.dt, args.steps, flush, stream)
-    prof = g.profile_end()
     launches = g.launches() - launches0
     barrier(ws)
     total_ms = max_over_ranks(ws, sum(ms), dev)
     value = cells * args.steps * ws / (total_ms * 1e-3)
 
-    # roofline of the dominant kernel, timed live inside the region above
-    cnt, kms = prof.get(dominant, (0, 0.0))
+    # every kernel's launches timed by CUDA events on the grid's stream over the same K flushed
+    # steps again: the dominant kernel and its roofline
+    allk = kernel_times(g, u, wl.dt, args.steps, flush, stream, "")
+    dominant = max(allk, key=lambda k: allk[k][1])
+    cnt, kms = allk.get(dominant, (0, 0.0))
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6400.0)
     bpc = KERNEL_BYTES_PER_CELL.get(dominant)
@@ -309,6 +324,8 @@ def run_ours(args, ws, rank, local):
     roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "bytes_per_cell": bpc, "launches": cnt, "avg_launch_us": kms / cnt * 1e3 if cnt else None,
+                "timing": "CUDA events around every launch of the kernel over a second pass of the K timed "
+                          "steps (L2 flushed per step, programmatic dependent launch off in that pass)",
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     line = {
@@ -323,7 +340,7 @@ def run_ours(args, ws, rank, local):
         "gpu_launches": launches,
         "roofline": roofline,
         "clocks": clk.summary(),
-        "kernels_ms_per_step": {k: v[1] / 2 for k, v in sorted(allk.items(), key=lambda kv: -kv[1][1])},
+        "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(allk.items(), key=lambda kv: -kv[1][1])},
     }
 
     if not args.quick:
@@ -487,9 +504,7 @@ def ib_stress_leg(stream, flush):
         g.step(u, wl.dt, 1)
     steps = 5
     ms = timed_steps(g, u, wl.dt, steps, flush, stream)
-    g.profile_begin("")
-    timed_steps(g, u, wl.dt, 2, flush, stream)
-    prof = g.profile_end()
+    prof = kernel_times(g, u, wl.dt, 2, flush, stream, "")
     cnt, tot = prof["ib3_force_gather"]
     gather_us = tot / cnt * 1e3
     # algorithmic bytes of the gather: 27 four-byte reads of f per marker and component (3-point
@@ -522,9 +537,7 @@ def sweep_leg(n, stream, flush):
         g.step(u, wl.dt, 1)
     steps = 5
     ms = timed_steps(g, u, wl.dt, steps, flush, stream)
-    g.profile_begin("")
-    timed_steps(g, u, wl.dt, 2, flush, stream)
-    prof = g.profile_end()
+    prof = kernel_times(g, u, wl.dt, 2, flush, stream, "")
     peak = measured_peaks().get("hbm_gbs", 6400.0)
     kms = {k: v[1] / 2 for k, v in prof.items()}
     cnt, tot = prof["predictor"]

@@ -256,6 +256,11 @@ int fs_diagnostics(fs_grid* grid, const fs_state* st, double out[3]);
 /* Number of kernels launched by this grid since creation (host counter). */
 long long fs_kernel_launches(const fs_grid* grid);
 
+/* Device status bits set by kernels since the last call, then cleared:
+ * bit 0 = a bulk-copy wait of the staged predictor gave up after 2 s (the
+ * outputs of that step are invalid).  Host output; synchronises the stream. */
+int fs_device_status(fs_grid* grid, unsigned* bits);
+
 /* Launch parameters chosen by an autotuner (0 restores the default):
  *   "stencil_bx"      x threads of the 256-thread stencil blocks: 32, 64, 128, 256
  *   "fft_lines"       complex lines per block of the mixed-radix transforms
@@ -266,6 +271,10 @@ long long fs_kernel_launches(const fs_grid* grid);
  *   "pdl"             1 (default): step kernels use programmatic dependent
  *                     launch (each starts while its predecessor drains);
  *                     0: ordinary stream-ordered launches
+ *   "predictor_staged" 1 (default): on fully periodic FP32 grids with n_x =
+ *                     128 or 256 the predictor stages its input planes in
+ *                     shared memory with bulk asynchronous copies; 0: it reads
+ *                     them from global memory (four-cell z-marching kernel)
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 4, 8 when the grid has
  *                     fewer 32-column blocks than two per SM); rebuilds the y tables

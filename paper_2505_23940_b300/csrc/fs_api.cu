@@ -276,7 +276,7 @@ void free_all(fs_grid* G) {
   for (int d = 0; d < 3; ++d) F(G->xf64[d]);
   F(G->hy64); F(G->hfy64);
   for (int c = 0; c < 3; ++c) { F(G->ustar[c]); F(G->ustage[c]); }
-  F(G->spec); F(G->scal); F(G->red); F(G->cg);
+  F(G->spec); F(G->scal); F(G->red); F(G->cg); F(G->dstatus);
   for (int c = 0; c < 3; ++c) F(G->fsi_u[c]);
   F(G->fsi_b);
   for (int q = 0; q < 4; ++q) F(G->les_nu[q]);
@@ -587,6 +587,8 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
   if (ok) ok = cudaMalloc(&G->spec, cells * std::max(es, sizeof(double))) == cudaSuccess;
   if (ok) ok = dalloc(&G->scal, 64) == cudaSuccess && cudaMemset(G->scal, 0, 64 * sizeof(double)) == cudaSuccess;
   if (ok) ok = dalloc(&G->red, 64) == cudaSuccess;
+  if (ok) ok = cudaMalloc(&G->dstatus, sizeof(unsigned)) == cudaSuccess &&
+               cudaMemset(G->dstatus, 0, sizeof(unsigned)) == cudaSuccess;
   if (ok) ok = G->prec == FS_MIXED ? (make_twiddles<float>(G->px) == cudaSuccess &&
                                       (G->dim == 2 || make_twiddles<float>(G->pz) == cudaSuccess) &&
                                       (!G->yspec || make_twiddles<float>(G->py) == cudaSuccess))
@@ -654,6 +656,9 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "pdl") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "pdl must be 0 or 1");
     G->use_pdl = value == 1;
+  } else if (k == "predictor_staged") {
+    if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "predictor_staged must be 0 or 1");
+    G->tune_staged = value == 1;
   } else if (k == "ysolve_segments") {
     if (value != 0 && value != 4 && value != 8 && value != 16)
       return set_error(FS_ERR_ARG, "ysolve_segments must be 4, 8 or 16");
@@ -667,6 +672,15 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else {
     return set_error(FS_ERR_ARG, "unknown tuning key " + k);
   }
+  return FS_OK;
+}
+
+int fs_device_status(fs_grid* G, unsigned* bits) {
+  if (!G || !bits) return set_error(FS_ERR_ARG, "NULL argument");
+  cudaError_t e = cudaMemcpyAsync(bits, G->dstatus, sizeof(unsigned), cudaMemcpyDeviceToHost, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(G->dstatus, 0, sizeof(unsigned), G->stream);
+  if (e != cudaSuccess) return cuda_check(e, "fs_device_status");
   return FS_OK;
 }
 

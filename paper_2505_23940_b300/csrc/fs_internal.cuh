@@ -276,6 +276,7 @@ struct fs_grid {
   void* spec = nullptr;        // real-packed spectral / pressure work array (cells)
   double* scal = nullptr;      // small device scalars (flux sums, reductions)
   double* red = nullptr;       // reduction partials
+  unsigned* dstatus = nullptr; // device status bits, set by kernels (1: a staged copy wait timed out)
 
   // Poisson plans
   fs::Plan1D px, py, pz;       // py: periodic y only
@@ -291,7 +292,8 @@ struct fs_grid {
   double *tMI = nullptr;                  // [4 ynseg^2][nlz][nmx] inverse of the 2 ynseg interface system
   int ynseg = 4;                          // segments per column of the partitioned y solve (4, 8 or 16)
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
-  int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
+  int tune_ynseg = 0;
+  bool tune_staged = true;                // shared-memory staged predictor where it applies                     // requested segment count (0: chosen from the grid's shape)
 
   fs::IBDev ib;
   bool has_body = false;

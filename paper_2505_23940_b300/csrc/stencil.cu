@@ -16,6 +16,7 @@
 #include <type_traits>
 
 #include "fs_internal.cuh"
+#include "tma.cuh"
 
 namespace fs {
 
@@ -706,6 +707,13 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
     ld_seg<false, false, 4>(W + ru(jp, k), i0, nx, WP0);
     ld_seg<true, true, 4>(W + ru(j, kp), i0, nx, W0P);
     ld_seg<false, false, 4>(W + ru(jm, kp), i0, nx, WMP);
+    const int rows[3] = {ru(j, k), rv(j, k), ru(j, k)};
+    // the RK stage's u^n rows, issued with the stencil rows (one memory round trip per plane)
+    float pn[3][4];
+    if (a != 0.f) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ldw<4>(A.un[c] + rows[c] + i0, pn[c]);
+    }
     float o3[3][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -726,15 +734,11 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
       o3[1][e] = b * (n.v000 + dt * Rv);
       o3[2][e] = b * (n.w000 + dt * Rw);
     }
-    const int rows[3] = {ru(j, k), rv(j, k), ru(j, k)};
     if (a != 0.f) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        float pn[4];
-        ldw<4>(A.un[c] + rows[c] + i0, pn);
+      for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) o3[c][e] += a * pn[e];
-      }
+        for (int e = 0; e < 4; ++e) o3[c][e] += a * pn[c][e];
     }
     if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
 #pragma unroll
@@ -769,6 +773,242 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
       Wmc[q] = WMP[q];
     }
   }
+}
+
+// Staged z-marching predictor: fully periodic uniform FP32 grids with nx = NX
+// (128 or 256).  A block owns the whole x extent of BY = 1024 / NX rows
+// j0 .. j0+BY-1 and KZ consecutive planes.  One thread streams each plane's U,
+// V and W rows j0-1 .. j0+BY (periodic y halo) from global to shared memory with
+// bulk asynchronous copies into a ring of plane slots, up to four planes
+// ahead of the compute; a staged plane serves the iterations of its own plane
+// and of its two z neighbours.  Each thread computes four cells of one row from
+// shared memory (x neighbours wrap inside the row); the RK stage's u^n and the
+// outputs go through plain vector loads and stores.
+//
+// Arithmetic: the central divergence-form convection of Eq. (4) on a uniform
+// grid, written with the face sums s = u_a + u_b (the halves of Eq. 4's
+// interpolations folded into the factor 1/4) and one product per cell edge.
+// The product at an edge serves the two faces that share it: the lower xy edge
+// of cell e is the x flux of v at e and e - 1 and the lower y flux of u; the
+// products of the x edges are shared by the four cells of a thread, and those
+// of the z-upper edges and faces are carried to the next plane as its lower
+// ones.  Diffusion is the uniform second difference.
+template <int NX>
+struct StageGeo {
+  static constexpr int TX = NX / 4;       // threads per row
+  static constexpr int BY = 1024 / NX;    // rows per block (256 threads)
+  static constexpr int RR = BY + 2;       // rows per staged slab (y halo)
+  static constexpr int FIELD = RR * NX;   // floats per field in a slot
+  static constexpr int SLOT = 3 * FIELD;  // floats per slot
+  static constexpr int RING = NX == 128 ? 7 : 5;   // plane slots: RING - 3 planes in flight ahead
+};
+
+template <int NX>
+constexpr size_t stage_smem() {
+  return (size_t)StageGeo<NX>::RING * StageGeo<NX>::SLOT * sizeof(float);
+}
+
+// s[0] = row[i0 - 1] (LO), s[1..4] = row[i0 .. i0+3], s[5] = row[i0 + 4] (HI), periodic in x
+template <bool LO, bool HI, int NX>
+__device__ __forceinline__ void lds_seg(const float* row, int i0, float* s) {
+  const float4 a = *reinterpret_cast<const float4*>(row + i0);
+  s[1] = a.x; s[2] = a.y; s[3] = a.z; s[4] = a.w;
+  if (LO) s[0] = row[(i0 - 1) & (NX - 1)];
+  if (HI) s[5] = row[(i0 + 4) & (NX - 1)];
+}
+
+template <int NX>
+__global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs<float> A, int KZ,
+                                                                   unsigned* status) {
+  using SG = StageGeo<NX>;
+  extern __shared__ __align__(16) float stg[];
+  constexpr int kStageRing = SG::RING;
+  __shared__ uint64_t bars[kStageRing];
+  pdl_wait();
+  const Geom<float>& g = A.g;
+  const int ny = g.ny, nz = g.nz;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int j0 = blockIdx.x * SG::BY;
+  const int k0 = blockIdx.y * KZ;
+  const int kz = min(KZ, nz - k0);   // planes computed
+  const int nplanes = kz + 2;        // planes staged: k0 - 1 .. k0 + kz
+  const bool leader = tx == 0 && ty == 0;
+  if (leader) {
+    for (int s = 0; s < kStageRing; ++s) mbar_init(&bars[s], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // slab row r holds y row (j0 - 1 + r) mod ny: at most two contiguous runs (ny >= RR)
+  const int g0 = j0 == 0 ? ny - 1 : j0 - 1;
+  const int run1 = min(SG::RR, ny - g0);
+  auto issue = [&](int rel) {   // stage plane k0 - 1 + rel (leader only)
+    int p = k0 - 1 + rel;
+    p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
+    const int s = rel % kStageRing;
+    float* slot = stg + (size_t)s * SG::SLOT;
+    mbar_expect_tx(&bars[s], SG::SLOT * sizeof(float));
+    for (int f = 0; f < 3; ++f) {
+      const float* src = A.uin[f] + (size_t)p * ny * NX;
+      float* dst = slot + f * SG::FIELD;
+      bulk_g2s(dst, src + (size_t)g0 * NX, run1 * NX * sizeof(float), &bars[s]);
+      if (run1 < SG::RR) bulk_g2s(dst + run1 * NX, src, (SG::RR - run1) * NX * sizeof(float), &bars[s]);
+    }
+  };
+  if (leader)
+    for (int rel = 0; rel < kStageRing - 1 && rel < nplanes; ++rel) issue(rel);
+  bool ok = true;
+  auto wait = [&](int rel) { ok = mbar_wait(&bars[rel % kStageRing], (rel / kStageRing) & 1) && ok; };
+  const int j = j0 + ty;
+  const bool act = j < ny;
+  const int i0 = 4 * tx;
+  const int rm = ty * NX, r0 = (ty + 1) * NX, rp = (ty + 2) * NX;
+  const float a = A.a, b = A.b, dt = A.dt, nu = g.nu;
+  const float ihx = g.ihx, ihy = A.ihy0, ihz = g.ihz;
+  const float qx = 0.25f * ihx, qy = 0.25f * ihy, qz = 0.25f * ihz;
+  const float dx2 = ihx * ihx, dy2 = ihy * ihy, dz2 = ihz * ihz, d0 = -2.f * (dx2 + dy2 + dz2);
+  const float bf = g.bforce ? g.bforce[act ? j : 0] : 0.f;
+  // products of the lower z edges / faces of the current plane, carried from plane to plane
+  float Exz[5], Eyz[4], Szz[4];
+  wait(0);
+  wait(1);
+  {
+    const float* Pm = stg;                 // plane k0 - 1
+    const float* P0 = stg + SG::SLOT;      // plane k0
+    float Ukm[6], Uc[6], Wc[6], Vkm[6], Vc[6], Wmc[6], Wkm[6];
+    lds_seg<false, true, NX>(Pm + r0, i0, Ukm);
+    lds_seg<false, true, NX>(P0 + r0, i0, Uc);
+    lds_seg<true, true, NX>(P0 + 2 * SG::FIELD + r0, i0, Wc);
+    lds_seg<false, false, NX>(Pm + SG::FIELD + r0, i0, Vkm);
+    lds_seg<false, false, NX>(P0 + SG::FIELD + r0, i0, Vc);
+    lds_seg<false, false, NX>(P0 + 2 * SG::FIELD + rm, i0, Wmc);
+    lds_seg<false, false, NX>(Pm + 2 * SG::FIELD + r0, i0, Wkm);
+#pragma unroll
+    for (int e = 0; e < 5; ++e) Exz[e] = (Ukm[e + 1] + Uc[e + 1]) * (Wc[e] + Wc[e + 1]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      Eyz[e] = (Vkm[e + 1] + Vc[e + 1]) * (Wmc[e + 1] + Wc[e + 1]);
+      const float t = Wkm[e + 1] + Wc[e + 1];
+      Szz[e] = t * t;
+    }
+  }
+  for (int kk = 0; kk < kz; ++kk) {
+    const int k = k0 + kk;
+    __syncthreads();   // the slot of plane kk - 1 is free
+    if (leader && kk + kStageRing - 1 < nplanes) issue(kk + kStageRing - 1);
+    const size_t row = (size_t)NX * (j + (size_t)ny * k);
+    float pn[3][4];
+    if (a != 0.f && act) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) ldw<4>(A.un[c] + row + i0, pn[c]);
+    }
+    wait(kk + 2);
+    const float* Pm = stg + (size_t)(kk % kStageRing) * SG::SLOT;         // plane k - 1
+    const float* P0 = stg + (size_t)((kk + 1) % kStageRing) * SG::SLOT;   // plane k
+    const float* Pp = stg + (size_t)((kk + 2) % kStageRing) * SG::SLOT;   // plane k + 1
+    const float* U0 = P0;
+    const float* V0 = P0 + SG::FIELD;
+    const float* W0 = P0 + 2 * SG::FIELD;
+    float Uc[6], UM0[6], UP0[6], Ukm[6], U0P[6];
+    float Vc[6], VM0[6], VP0[6], Vkm[6], V0P[6], Vpkm[6];
+    float Wc[6], Wmc[6], WP0[6], Wkm[6], W0P[6], WMP[6];
+    lds_seg<true, true, NX>(U0 + r0, i0, Uc);
+    lds_seg<false, true, NX>(U0 + rm, i0, UM0);
+    lds_seg<false, false, NX>(U0 + rp, i0, UP0);
+    lds_seg<false, false, NX>(Pm + r0, i0, Ukm);
+    lds_seg<false, true, NX>(Pp + r0, i0, U0P);
+    lds_seg<true, true, NX>(V0 + r0, i0, Vc);
+    lds_seg<false, false, NX>(V0 + rm, i0, VM0);
+    lds_seg<true, false, NX>(V0 + rp, i0, VP0);
+    lds_seg<false, false, NX>(Pm + SG::FIELD + r0, i0, Vkm);
+    lds_seg<false, false, NX>(Pp + SG::FIELD + r0, i0, V0P);
+    lds_seg<false, false, NX>(Pm + SG::FIELD + rp, i0, Vpkm);
+    lds_seg<true, true, NX>(W0 + r0, i0, Wc);
+    lds_seg<false, false, NX>(W0 + rm, i0, Wmc);
+    lds_seg<false, false, NX>(W0 + rp, i0, WP0);
+    lds_seg<false, false, NX>(Pm + 2 * SG::FIELD + r0, i0, Wkm);
+    lds_seg<true, true, NX>(Pp + 2 * SG::FIELD + r0, i0, W0P);
+    lds_seg<false, false, NX>(Pp + 2 * SG::FIELD + rm, i0, WMP);
+    // edge and face products of this plane (x edges: five for four cells) and of the z-upper ones
+    float sq[5], Exy[5], Exz_up[5], Eyz_up[4], Szz_up[4];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+      const float su = Uc[e] + Uc[e + 1];
+      sq[e] = su * su;
+      Exy[e] = (UM0[e + 1] + Uc[e + 1]) * (Vc[e] + Vc[e + 1]);
+      Exz_up[e] = (Uc[e + 1] + U0P[e + 1]) * (W0P[e] + W0P[e + 1]);
+    }
+    float o3[3][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int c = e + 1;
+      Eyz_up[e] = (Vc[c] + V0P[c]) * (WMP[c] + W0P[c]);
+      const float tz = Wc[c] + W0P[c];
+      Szz_up[e] = tz * tz;
+      const float Nxy = (VP0[e] + VP0[c]) * (Uc[c] + UP0[c]);
+      const float Nyz = (Vpkm[c] + VP0[c]) * (Wc[c] + WP0[c]);
+      const float vn = Vc[c] + VP0[c], vs = VM0[c] + Vc[c];
+      // u on the x face
+      float cv = qx * (sq[c] - sq[e]);
+      cv = fmaf(qy, Nxy - Exy[e], cv);
+      cv = fmaf(qz, Exz_up[e] - Exz[e], cv);
+      float df = fmaf(d0, Uc[c], dx2 * (Uc[e] + Uc[c + 1]));
+      df = fmaf(dy2, UM0[c] + UP0[c], df);
+      df = fmaf(dz2, Ukm[c] + U0P[c], df);
+      const float Ru = fmaf(nu, df, bf - cv);
+      // v on the y face
+      cv = qy * (vn * vn - vs * vs);
+      cv = fmaf(qx, Exy[c] - Exy[e], cv);
+      cv = fmaf(qz, Eyz_up[e] - Eyz[e], cv);
+      df = fmaf(d0, Vc[c], dx2 * (Vc[e] + Vc[c + 1]));
+      df = fmaf(dy2, VM0[c] + VP0[c], df);
+      df = fmaf(dz2, Vkm[c] + V0P[c], df);
+      const float Rv = fmaf(nu, df, -cv);
+      // w on the z face
+      cv = qz * (Szz_up[e] - Szz[e]);
+      cv = fmaf(qx, Exz[c] - Exz[e], cv);
+      cv = fmaf(qy, Nyz - Eyz[e], cv);
+      df = fmaf(d0, Wc[c], dx2 * (Wc[e] + Wc[c + 1]));
+      df = fmaf(dy2, Wmc[c] + WP0[c], df);
+      df = fmaf(dz2, Wkm[c] + W0P[c], df);
+      const float Rw = fmaf(nu, df, -cv);
+      o3[0][e] = b * fmaf(dt, Ru, Uc[c]);
+      o3[1][e] = b * fmaf(dt, Rv, Vc[c]);
+      o3[2][e] = b * fmaf(dt, Rw, Wc[c]);
+    }
+#pragma unroll
+    for (int e = 0; e < 5; ++e) Exz[e] = Exz_up[e];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      Eyz[e] = Eyz_up[e];
+      Szz[e] = Szz_up[e];
+    }
+    if (act) {
+      if (a != 0.f) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) o3[c][e] = fmaf(a, pn[c][e], o3[c][e]);
+      }
+      if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          float fo[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            fo[e] = 0.f;
+            if (A.flags3[c][row + i0 + e]) {
+              fo[e] = -o3[c][e] / dt;
+              o3[c][e] = 0.f;
+            }
+          }
+          stw<4>(A.fout3[c] + row + i0, fo);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) stw<4>(A.out[c] + row + i0, o3[c]);
+    }
+  }
+  if (!ok) atomicOr(status, 1u);   // a staged plane never arrived: results of this block are invalid
 }
 
 template <typename T>
@@ -1044,6 +1284,24 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
         if (G->has_ib3) vec = vec && (uintptr_t)G->ib3.f[c] % (4 * vw) == 0;
       }
       const int KZ = G->tune_zmarch > 0 ? G->tune_zmarch : 8;
+      const int nx = G->nx;
+      if (vec && vw == 4 && G->tune_staged && G->per[1] && (nx == 128 || nx == 256) && G->ny >= 1024 / nx + 2) {
+        static bool attr = false;
+        if (!attr) {
+          cudaFuncSetAttribute(predictor3t_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stage_smem<128>());
+          cudaFuncSetAttribute(predictor3t_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)stage_smem<256>());
+          attr = true;
+        }
+        const int by = 1024 / nx;
+        const dim3 sg((G->ny + by - 1) / by, (G->nz + KZ - 1) / KZ);
+        if (nx == 128)
+          launch_pdl(G, "predictor", predictor3t_kernel<128>, sg, dim3(32, 8), stage_smem<128>(), A, KZ, G->dstatus);
+        else
+          launch_pdl(G, "predictor", predictor3t_kernel<256>, sg, dim3(64, 4), stage_smem<256>(), A, KZ, G->dstatus);
+        return;
+      }
       if (vec && vw == 4 && KZ > 1) {
         const dim3 vb(32, 8);
         const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, (G->nz + KZ - 1) / KZ);

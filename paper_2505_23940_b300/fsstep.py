@@ -87,6 +87,7 @@ def lib():
                                       c_int]
         L.fs_coupling_stats.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
         L.fs_forces_device.argtypes = [c_void_p, c_void_p]
+        L.fs_device_status.argtypes = [c_void_p, POINTER(ctypes.c_uint)]
         L.fs_component_stats_noalloc.argtypes = [c_void_p, c_int, POINTER(c_int), c_double, c_void_p, c_void_p,
                                                  c_void_p]
         _LIB = L
@@ -292,6 +293,12 @@ class Grid:
 
     def launches(self):
         return int(lib().fs_kernel_launches(self.h))
+
+    def device_status(self):
+        """Status bits set by kernels since the last call (0: nothing to report); synchronises."""
+        v = ctypes.c_uint(0)
+        check(lib().fs_device_status(self.h, byref(v)))
+        return int(v.value)
 
     def profile_begin(self, filter_=""):
         check(lib().fs_profile_begin(self.h, filter_.encode()))
