@@ -19,6 +19,7 @@ host cores (cpu_baseline).  --impl reference times the oracle alone.
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -385,10 +386,10 @@ def run_ours(args, ws, rank, local):
         ems = max_over_ranks(ws, sum(a.elapsed_time(b) for a, b in ev), dev)
         line["e2e"] = {"value": cells * args.steps * ws / (ems * 1e-3), "unit": "cell-updates/s",
                        "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
-        # forward + adjoint: K forward steps, then the revolve-checkpointed reverse sweep
+        # forward + adjoint: K forward steps keeping snapshots, then the reverse sweep; the snapshot
+        # count is chosen from free HBM (one per step here: no recomputation)
         from paper_2505_23940_b300.autodiff import Rollout
-        slots = 4
-        ro = Rollout(g, wl.dt, args.steps, slots=slots)
+        ro = Rollout(g, wl.dt, args.steps)
         ua = [x.clone() for x in u0]
         # loss: final kinetic energy (1/2) sum u_T^2 h^3, whose adjoint is lam_T = u_T h^3
         vol = (2.0 * np.pi / wl.n[0]) ** 3
@@ -405,10 +406,25 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         fwd_ms, adj_ms = ea.elapsed_time(eb), eb.elapsed_time(ec)
         fa_ms = max_over_ranks(ws, fwd_ms + adj_ms, dev)
+        slots = ro.used_slots
         line["fwd_adj"] = {"value": cells * args.steps * ws / (fa_ms * 1e-3), "unit": "cell-updates/s",
                            "steps": args.steps, "slots": slots, "recomputed_steps": ro.recomputed,
                            "forward_ms": fwd_ms, "reverse_ms": adj_ms,
-                           "note": "K forward steps then the reverse sweep (recomputation + adjoint steps)"}
+                           "note": "K forward steps keeping snapshots, then the reverse sweep "
+                                   "(recomputation + adjoint steps)"}
+        # the same with 4 snapshot slots: binomial recomputation in the reverse sweep
+        ro4 = Rollout(g, wl.dt, args.steps, slots=4)
+        lam4_T = [x * vol for x in ro4.forward(ua)[0]]
+        torch.cuda.synchronize()
+        ea.record(stream)
+        ro4.forward(ua)
+        ro4.backward(ua, None, lam4_T)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        r4_ms = max_over_ranks(ws, ea.elapsed_time(eb), dev)
+        line["fwd_adj"]["revolve_4_slots"] = {"value": cells * args.steps * ws / (r4_ms * 1e-3),
+                                              "unit": "cell-updates/s", "recomputed_steps": ro4.recomputed}
+        del ro4, lam4_T
         # the same forward + adjoint on the all-FP64 path, and the distance of the mixed
         # gradient dJ/du_0 to it
         lam_mixed = ro.backward(ua, None, lam_T)[0]
@@ -440,7 +456,7 @@ def run_ours(args, ws, rank, local):
         line["ib_stress"] = ib_stress_leg(stream, flush)
 
     if not args.quick and args.sweep:
-        line["hbm_sweep"] = [sweep_leg(int(n), stream, flush) for n in args.sweep.split(",") if n]
+        line["hbm_sweep"] = [sweep_leg(n, stream, flush) for n in args.sweep.split(",") if n]
 
     if rank == 0 and not args.quick and args.cpu_steps > 0:
         rate, secs = cpu_oracle_rate(wl, args.cpu_steps)
@@ -523,13 +539,34 @@ def ib_stress_leg(stream, flush):
     return out
 
 
-def sweep_leg(n, stream, flush):
-    """The same RK3 step on an n^3 isotropic field whose working set exceeds L2:
-    per-kernel times and the predictor's achieved HBM bandwidth."""
+def sweep_leg(spec, stream, flush):
+    """The RK3 step on a periodic grid whose working set exceeds L2: per-kernel times and the
+    predictor's achieved HBM bandwidth.  spec "n": n^3 (the isotropic field up to 256^3, uniform
+    random faces beyond, where the spectral generator costs minutes on the host); "AxB": a 2-D
+    A x B box with uniform random faces."""
     from paper_2505_23940_b300 import grid_from_workload
     dev = torch.device("cuda")
-    wl = S.isotropic_3d(n=n)
-    cells = n ** 3
+    if "x" in spec:
+        nx, ny = (int(a) for a in spec.split("x"))
+        wl = S.box_2d(nx, ny, (S.PERIODIC, S.PERIODIC), (S.PERIODIC, S.PERIODIC), Lx=2 * math.pi,
+                      Ly=2 * math.pi * ny / nx, nu=1.0 / 400.0)
+        dims, field = [nx, ny, 1], "uniform random faces"
+    else:
+        n = int(spec)
+        if n <= 256:
+            wl = S.isotropic_3d(n=n)
+            field = "isotropic spectrum"
+        else:
+            wl = S.box_3d(n, n, n, (S.PERIODIC, S.PERIODIC), (S.PERIODIC, S.PERIODIC),
+                          L=(2 * math.pi,) * 3, nu=1.0 / 400.0)
+            field = "uniform random faces"
+        dims = [n, n, n]
+    if field != "isotropic spectrum":
+        wl.u0 = S.random_fields(wl, 5, 1.0)
+        wl.scheme = "rk3"
+        wl.dt = 0.25 * 2 * math.pi / dims[0]
+    dim = wl.dim
+    cells = dims[0] * dims[1] * dims[2]
     g = grid_from_workload(wl, "mixed", stream=stream)
     u = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
     del wl.u0
@@ -541,15 +578,16 @@ def sweep_leg(n, stream, flush):
     peak = measured_peaks().get("hbm_gbs", 6400.0)
     kms = {k: v[1] / 2 for k, v in prof.items()}
     cnt, tot = prof["predictor"]
-    bpc = (24.0 + 36.0 + 36.0) / 3.0
+    vb = 4.0 * dim   # bytes of one FP32 velocity field per cell
+    bpc = (2 * vb + 3 * vb + 3 * vb) / 3.0
     ach = bpc * cells / (tot / cnt * 1e-3) / 1e9
-    out = {"n": [n, n, n], "cells": cells, "ms_per_step": sum(ms) / steps,
+    out = {"n": dims, "cells": cells, "field": field, "ms_per_step": sum(ms) / steps,
            "value": cells * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
            "kernels_ms_per_step": dict(sorted(kms.items(), key=lambda kv: -kv[1])),
            "predictor": {"avg_launch_us": tot / cnt * 1e3, "bytes_per_cell": bpc, "achieved_GBs": ach,
                          "peak_GBs": peak, "frac": ach / peak}}
     # every kernel's algorithmic bytes per cell (FP32 fields, FP32 spectrum)
-    per_kernel = {"predictor": bpc, "correct": 28.0, "fft_x_fwd_div": 16.0}
+    per_kernel = {"predictor": bpc, "correct": 2 * vb + 4.0, "fft_x_fwd_div": vb + 4.0}
     for k in kms:
         if k.startswith("fft_") and k not in per_kernel:
             per_kernel[k] = 8.0
@@ -572,7 +610,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")
-    ap.add_argument("--sweep", default="256", help="comma-separated n of the n^3 out-of-L2 leg ('' to skip)")
+    ap.add_argument("--sweep", default="256,384,512,4096x4096",
+                    help="comma-separated out-of-L2 grids: n for n^3, AxB for a 2-D A x B box ('' to skip)")
     ap.add_argument("--ib-stress", type=int, default=1, help="run the 256^3 static-box leg (0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()

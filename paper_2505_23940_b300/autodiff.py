@@ -71,6 +71,18 @@ def revolve_schedule(n, slots):
     return ops
 
 
+def split_schedule(n, slots):
+    """(stores, rest): the forward prefix of the schedule (everything before its first
+    adjoint) as {step: slot} for the states it stores, and the remaining actions.  A
+    forward pass that keeps those states and the state at step n - 1 (the working state
+    of the first remaining action, the adjoint of step n - 1) needs no recomputation
+    until the schedule's first reload."""
+    ops = revolve_schedule(n, slots)
+    i = next(k for k, op in enumerate(ops) if op[0] == "adjoint")
+    stores = {op[2]: op[1] for op in ops[:i] if op[0] == "store"}
+    return stores, ops[i:]
+
+
 def simulate(n, slots):
     """Replay a schedule on integers: returns (adjoint step order, forward steps recomputed)."""
     work, mem, order, fwd = None, {}, [], 0
@@ -95,40 +107,74 @@ def simulate(n, slots):
 class Rollout:
     """n steps of a grid from (u0, body0), differentiable through revolve + fs_step_adjoint.
 
-    Keeps `slots` device copies of the state.  Forces of every step (FSI grids)
-    are recorded on the device so losses may depend on them.
+    Keeps `slots` device copies of the state; slots=None takes as many as half of
+    the free device memory holds, up to one per step (no recomputation at all:
+    500 steps of a 128^3 FP32 field are 12.6 GB).  The forward pass already keeps
+    the states the schedule stores before its first adjoint, so a backward after
+    a forward starts reversing at once.  Forces of every step (FSI grids) are
+    recorded on the device so losses may depend on them.
     """
 
-    def __init__(self, grid, dt, nsteps, slots=4):
+    def __init__(self, grid, dt, nsteps, slots=None):
         self.g = grid
         self.dt = float(dt)
         self.n = int(nsteps)
-        self.slots = max(1, int(slots))
+        self.slots = None if slots is None else max(1, int(slots))
+        self.used_slots = self.slots
+        self.recomputed = 0
+        self._kept = None
 
     def _clone(self, u, body):
         return [x.clone() for x in u], (body.clone() if body is not None else None)
 
+    def _slots_for(self, u, body):
+        if self.slots is not None:
+            return self.slots
+        free, _ = torch.cuda.mem_get_info(u[0].device)
+        per = sum(x.numel() * x.element_size() for x in u) + (body.numel() * body.element_size() if body is not None else 0)
+        return max(2, min(self.n, int(0.5 * free) // max(per, 1)))
+
     def forward(self, u0, body0=None):
         u, body = self._clone(u0, body0)
+        slots = self._slots_for(u, body)
+        self.used_slots = slots
+        stores, _ = split_schedule(self.n, slots)
+        mem = {0: self._clone(u0, body0)}
+        work = None
         forces = None
         if self.g.has_body:
             forces = torch.zeros((self.n, 3), dtype=torch.float64, device=u[0].device)
         for t in range(self.n):
+            if t == self.n - 1:
+                work = self._clone(u, body)
             self.g.step(u, self.dt, 1, body=body)
             if forces is not None:
                 self.g.forces_device(forces[t])
+            if t + 1 in stores:
+                mem[stores[t + 1]] = self._clone(u, body)
+        self._kept = (mem, work, slots)
         return u, body, forces
 
     def backward(self, u0, body0, lam_u, lam_body=None, lam_forces=None, g_body_force=None, g_stiffness=None):
         """lam_* are the adjoints of the outputs; returns (lam_u0, lam_body0).  Parameter gradients
-        are accumulated into the given device tensors."""
-        mem = {0: self._clone(u0, body0)}
-        work_u, work_b = None, None
+        are accumulated into the given device tensors.  Right after forward() the states it kept
+        are used (u0 and body0 must be the forward's inputs); otherwise the schedule starts from
+        (u0, body0)."""
+        if self._kept is not None:
+            mem, (work_u, work_b), slots = self._kept
+            self._kept = None
+            ops = split_schedule(self.n, slots)[1]
+        else:
+            slots = self._slots_for(u0, body0)
+            mem = {0: self._clone(u0, body0)}
+            work_u, work_b = None, None
+            ops = revolve_schedule(self.n, slots)
+        self.used_slots = slots
         lam = [x.clone() for x in lam_u]
         lb = lam_body.clone() if lam_body is not None else (
             torch.zeros(4, dtype=torch.float64, device=lam[0].device) if self.g.has_body else None)
         self.recomputed = 0
-        for op in revolve_schedule(self.n, self.slots):
+        for op in ops:
             if op[0] == "load":
                 su, sb = mem[op[1]]
                 if work_u is None:
@@ -193,7 +239,7 @@ class FsRollout(torch.autograd.Function):
         return (None, None, None, None, gbf, gk, lb if ctx.has_body else None) + tuple(lam)
 
 
-def rollout(grid, u0, dt, nsteps, slots=4, body0=None, body_force=None, stiffness=None):
+def rollout(grid, u0, dt, nsteps, slots=None, body0=None, body_force=None, stiffness=None):
     """Differentiable rollout: returns (u_T list, body_T or empty, forces (nsteps, 3) or empty)."""
     out = FsRollout.apply(grid, dt, nsteps, slots, body_force, stiffness, body0, *u0)
     return list(out[:grid.dim]), out[grid.dim], out[grid.dim + 1]

@@ -556,7 +556,11 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
     delete G;
     return set_error(FS_ERR_UNSUPPORTED, "fields of 2^31 or more elements (32-bit kernel indexing)");
   }
-  if ((size_t)G->ny * 32 * 8 > 200 * 1024) {
+  if (G->yspec && 2ull * (G->ny + 1) * 2 * elem_size(G) > 200 * 1024) {
+    delete G;
+    return set_error(FS_ERR_UNSUPPORTED, "periodic ny too large for one slot pair's line in shared memory");
+  }
+  if (!G->yspec && (size_t)G->ny * 32 * 8 > 200 * 1024) {
     delete G;
     return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 800)");
   }

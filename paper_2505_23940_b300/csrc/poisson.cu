@@ -582,10 +582,19 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   const int nlam = A.nmx * A.nlz;
   T* tile = data + s0 + (size_t)A.nx * A.ny * t;
   const size_t rs = (size_t)A.nx;
+  // tile in (unrolled for the short columns of the 8- and 16-segment forms; the 4-segment
+  // form of large 3-D grids runs faster with the plain loop)
+  if constexpr (NSEG >= 8) {
 #pragma unroll 8
-  for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-    const int j = e / YCOLS, c = e - j * YCOLS;
-    D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
+    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+      const int j = e / YCOLS, c = e - j * YCOLS;
+      D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
+    }
+  } else {
+    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+      const int j = e / YCOLS, c = e - j * YCOLS;
+      D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
+    }
   }
   __syncthreads();
   const bool act = s < A.nx;
@@ -658,7 +667,7 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     }
   }
   __syncthreads();
-  // 3. spike correction (rows independent: table loads batched like the sweeps)
+  // 3. spike correction
   double part = 0.0;
   if (act && r1 > r0) {
     const bool cyc = A.cyclic != 0;
@@ -666,22 +675,7 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     const int gn = p + 1 < NSEG ? p + 1 : 0, gp = p > 0 ? p - 1 : NSEG - 1;
     const double Xn = (p + 1 < NSEG || cyc) ? z[2 * gn] : 0.0;
     const double Yp = (p > 0 || cyc) ? z[2 * gp + 1] : 0.0;
-    int j = r0;
-    for (; j + U <= r1; j += U) {
-      double v[U], w[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        v[q] = __ldg(V + (size_t)(j + q) * nlam);
-        w[q] = __ldg(W + (size_t)(j + q) * nlam);
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const double r = col[(j + q) * YCOLS] - v[q] * Xn - w[q] * Yp;
-        col[(j + q) * YCOLS] = r;
-        if (li == 0) part += r * __ldg(A.hy + j + q);
-      }
-    }
-    for (; j < r1; ++j) {
+    for (int j = r0; j < r1; ++j) {
       const double r = col[j * YCOLS] - __ldg(V + (size_t)j * nlam) * Xn - __ldg(W + (size_t)j * nlam) * Yp;
       col[j * YCOLS] = r;
       if (li == 0) part += r * __ldg(A.hy + j);
@@ -697,10 +691,17 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     for (int j = r0; j < r1; ++j) col[j * YCOLS] -= mean;
   }
   __syncthreads();
+  if constexpr (NSEG >= 8) {
 #pragma unroll 8
-  for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-    const int j = e / YCOLS, c = e - j * YCOLS;
-    if (c < ncol) tile[rs * j + c] = (T)D[e];
+    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+      const int j = e / YCOLS, c = e - j * YCOLS;
+      if (c < ncol) tile[rs * j + c] = (T)D[e];
+    }
+  } else {
+    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
+      const int j = e / YCOLS, c = e - j * YCOLS;
+      if (c < ncol) tile[rs * j + c] = (T)D[e];
+    }
   }
 }
 
