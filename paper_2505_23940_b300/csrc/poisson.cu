@@ -875,16 +875,42 @@ FftKernels<T> fft_kernels_of() {
           zinv_kernel<T, PL>, yspec_kernel<T, PL>};
 }
 
-bool is_fixed_length(int n) { return n == 64 || n == 128 || n == 192 || n == 256; }
+// Lengths with compile-time plans: the powers of two and the multiples of 32 up to
+// 512 met by the benchmark grids, and 640.  The z and periodic-y kernels of a
+// compile-time length stage kMaxLines lines of two buffers in shared memory, so
+// a length takes its compile-time plan only where those fit (FP64: n <= 399).
+template <typename T>
+bool is_fixed_length(int n) {
+  switch (n) {
+    case 64: case 128: case 160: case 192: case 224: case 256: case 288: case 320: case 352: case 384:
+    case 416: case 448: case 480: case 512: case 640:
+      return 2ull * kMaxLines * (n + 1) * sizeof(cplx<T>) <= kFixedBudget;
+    default:
+      return false;
+  }
+}
 
 template <typename T>
 FftKernels<T> fft_kernels(const Plan1D& p) {
-  switch (p.n) {
-    case 64: return fft_kernels_of<T, 64>();
-    case 128: return fft_kernels_of<T, 128>();
-    case 192: return fft_kernels_of<T, 192>();
-    case 256: return fft_kernels_of<T, 256>();
-    default: break;
+  if (is_fixed_length<T>(p.n)) {
+    switch (p.n) {
+      case 64: return fft_kernels_of<T, 64>();
+      case 128: return fft_kernels_of<T, 128>();
+      case 160: return fft_kernels_of<T, 160>();
+      case 192: return fft_kernels_of<T, 192>();
+      case 224: return fft_kernels_of<T, 224>();
+      case 256: return fft_kernels_of<T, 256>();
+      case 288: return fft_kernels_of<T, 288>();
+      case 320: return fft_kernels_of<T, 320>();
+      case 352: return fft_kernels_of<T, 352>();
+      case 384: return fft_kernels_of<T, 384>();
+      case 416: return fft_kernels_of<T, 416>();
+      case 448: return fft_kernels_of<T, 448>();
+      case 480: return fft_kernels_of<T, 480>();
+      case 512: return fft_kernels_of<T, 512>();
+      case 640: return fft_kernels_of<T, 640>();
+      default: break;
+    }
   }
   for (int i = 0; i < p.nst; ++i)
     if (p.radix[i] > 5) return fft_kernels_of<T, 1>();
@@ -969,8 +995,19 @@ void set_smem_attrs() {
   set_smem_attrs_plan<T, 1>();
   set_smem_attrs_plan<T, 64>();
   set_smem_attrs_plan<T, 128>();
+  set_smem_attrs_plan<T, 160>();
   set_smem_attrs_plan<T, 192>();
+  set_smem_attrs_plan<T, 224>();
   set_smem_attrs_plan<T, 256>();
+  set_smem_attrs_plan<T, 288>();
+  set_smem_attrs_plan<T, 320>();
+  set_smem_attrs_plan<T, 352>();
+  set_smem_attrs_plan<T, 384>();
+  set_smem_attrs_plan<T, 416>();
+  set_smem_attrs_plan<T, 448>();
+  set_smem_attrs_plan<T, 480>();
+  set_smem_attrs_plan<T, 512>();
+  set_smem_attrs_plan<T, 640>();
   cudaFuncSetAttribute(ysolve_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -1011,7 +1048,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   if (zreg) {
     with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data); });
   } else if (G->dim == 3) {
-    if (is_fixed_length(G->pz.n)) {
+    if (is_fixed_length<T>(G->pz.n)) {
       ppb = kMaxLines;   // the compile-time-length z kernels map 32 slots x 8 rows onto 256 threads
     } else {
       ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
@@ -1045,7 +1082,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     // slots per block: an even count whose two ping-pong buffers fit the budget
     const size_t line_bytes = 2ull * (ny + 1) * sizeof(cplx<T>);
     int spb = 2 * (int)std::min<size_t>(kMaxLines, kYSpecBudget / line_bytes);
-    if (is_fixed_length(ny)) spb = 2 * kMaxLines;   // compile-time lengths map 32 slots x 8 rows onto 256 threads
+    if (is_fixed_length<T>(ny)) spb = 2 * kMaxLines;   // compile-time lengths map 32 slots x 8 rows onto 256 threads
     else if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
     A.spb = spb;
     dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);

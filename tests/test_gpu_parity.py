@@ -121,6 +121,46 @@ def test_solve_pressure_segments_fp64(wl, segments):
     assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
 
 
+_CT_CASES = {
+    "x320": lambda: S.box_2d(320, 6, (P, P), (NS, NS), stretched=1.2),   # x DFT, compile-time 320
+    "x160dct": lambda: S.box_2d(160, 8, (IN, OUT), (FS, FS)),            # x DCT-II, 160
+    "z224": lambda: S.box_3d(8, 6, 224, (P, P), (NS, NS)),               # z, 224 (radix 7)
+    "y352": lambda: S.box_3d(6, 352, 4, (P, P), (P, P)),                 # periodic y, 352 (radix 11)
+    "x640dct": lambda: S.box_2d(640, 8, (IN, OUT), (FS, FS)),            # x DCT-II, 640 (FP32 plan only)
+    "z512": lambda: S.box_3d(4, 4, 512, (P, P), (P, P)),                 # z, 512 (FP32 plan only)
+}
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", sorted(_CT_CASES))
+def test_solve_pressure_compile_time_lengths(case, precision):
+    """Transform lengths with compile-time plans (and, in FP64, the generic plans of the
+    lengths whose compile-time kernels would not fit in shared memory) against the
+    oracle's direct solve; in mixed precision, two steps against the oracle's."""
+    from paper_2505_23940_b300 import grid_from_workload
+    wl = _CT_CASES[case]()
+    from oracle import fluid, poisson
+    if precision == "mixed":   # FP32 transforms inside the step (the pressure entry point is FP64)
+        hmin = min(float(np.diff(wl.xf[d]).min()) for d in range(wl.dim))
+        wl.dt = 0.1 * hmin
+        wl.u0 = S.random_fields(wl, 9, 1.0)
+        gp = run_gpu(wl, 2, precision="mixed")
+        st, _, _ = run_oracle(wl, 2)
+        assert field_err(gp["u"], st.u) < TOLMIX
+        return
+    g = grid_of(wl)
+    rng = np.random.default_rng(9)
+    u = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(g.dim)]
+    u = fluid.apply_boundary_values(g, u)
+    u = fluid.outflow_faces(g, u, u)
+    b = fluid.divergence(g, u)
+    ref = poisson.solve(g, b)
+    G = grid_from_workload(wl, precision)
+    p = G.solve_pressure(b.cuda().contiguous())
+    torch.cuda.synchronize()
+    assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
+
+
 def _small_cyl(kernel, precision="fp64", omega=0.0):
     wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, kernel=kernel, centre_d=(2.0, 2.0),
                        precision=precision, seed=3, perturb=0.05, omega=omega)
