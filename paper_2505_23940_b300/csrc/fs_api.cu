@@ -286,7 +286,7 @@ void free_all(fs_grid* G) {
   IBDev& B = G->ib;
   F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
-  F(B.fn); F(B.q); F(B.F);
+  F(B.fn); F(B.q); F(B.F); F(B.ticket);
 }
 
 void free_body(fs_grid* G) {
@@ -296,7 +296,7 @@ void free_body(fs_grid* G) {
   };
   F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
-  F(B.fn); F(B.q); F(B.F);
+  F(B.fn); F(B.q); F(B.F); F(B.ticket);
   B = IBDev();
   G->has_body = false;
 }
@@ -325,8 +325,7 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
   launch_correct<T>(G, us, spec, u);
   if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / dt);
   if (G->has_body) {
-    ib_forces<T>(G, st->body);
-    body_rk4(G, st->body, dt);
+    ib_forces<T>(G, st->body, st->body, dt);
   }
   if (G->has_ib3) ib3_forces<T>(G);
 }
@@ -794,7 +793,8 @@ int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
          cudaMemset(B.flags[c], 0, n) == cudaSuccess && cudaMemset(B.f[c], 0, n * es) == cudaSuccess;
   }
   if (ok) ok = dalloc(&B.fn, 2 * b->nm) == cudaSuccess && dalloc(&B.q, 2 * b->nm) == cudaSuccess &&
-               dalloc(&B.F, 4) == cudaSuccess && cudaMemset(B.F, 0, 4 * sizeof(double)) == cudaSuccess;
+               dalloc(&B.F, 4) == cudaSuccess && cudaMemset(B.F, 0, 4 * sizeof(double)) == cudaSuccess &&
+               dalloc(&B.ticket, 1) == cudaSuccess && cudaMemset(B.ticket, 0, sizeof(unsigned)) == cudaSuccess;
   if (!ok) {
     free_body(G);
     return set_error(FS_ERR_CUDA, "allocating immersed-body buffers");

@@ -230,6 +230,7 @@ struct IBDev {
   double* fn = nullptr;                    // F_N per marker and component (2 * nm)
   double* q = nullptr;                     // marker forces (2 * nm)
   double* F = nullptr;                     // [Fx, Fy, torque]
+  unsigned* ticket = nullptr;              // blocks finished in the force kernel (reset by its last block)
   bool have_forces = false;
   double poly_bb[4] = {0, 0, 0, 0};        // rest polygon bounding box xmin, xmax, ymin, ymax
 };
@@ -345,7 +346,9 @@ template <typename T> void poisson_solve_inplace(fs_grid* g, T* data);
 template <typename T> void poisson_solve_from_velocity(fs_grid* g, const fs::DivArgs<T>& div, T* data);
 // ib.cu
 template <typename T> void ib_prepare(fs_grid* g, const double* body_state);
-template <typename T> void ib_forces(fs_grid* g, const double* body_state);
+// Marker forces, F and torque (Eq. 20); with `advance`, also the body ODE step
+// (Eq. 12) of that state with the new force.
+template <typename T> void ib_forces(fs_grid* g, double* body_state, double* advance = nullptr, double dt = 0.0);
 void body_rk4(fs_grid* g, double* body_state, double dt);
 // ib3.cu
 template <typename T> void ib3_forces(fs_grid* g);

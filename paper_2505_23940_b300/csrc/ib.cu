@@ -7,15 +7,16 @@
 //                    height once, then every face of the row counts the crossings
 //                    to its right (both components in one launch)
 //   classify_ib      IB faces: non-solid faces with a solid same-component neighbour
-//   fn_gather        F_N of Eq. (19) per marker and component (support nodes that are
-//                    not solid); 16 lanes per (marker, component), one support node
-//                    each, summed by shuffles
-//   ib_scatter       Eq. (18), normalised: numerator / denominator of u_IB on IB faces;
-//                    markers are sorted by cell, contributions to the same face are
-//                    summed inside the warp (match_any + shuffles) before one atomicAdd
-//   force_gather     q_i of Eq. (20) per marker (FP64 sums, 16 lanes per marker and component)
-//   force_reduce     F = rho sum q_i dV_i and torque, one CTA, fixed order (FP64)
-//   rk4              Eq. (12), classical RK4 with the force frozen (one thread, FP64)
+//   ib_target        F_N of Eq. (19) per marker and component (support nodes that are
+//                    not solid) and the normalised scatter of Eq. (18): numerator and
+//                    denominator of u_IB on IB faces; 16 lanes per (marker, component),
+//                    one support node each, F_N summed by shuffles, one atomicAdd per
+//                    IB node
+//   ib_force         q_i of Eq. (20) per marker (FP64 sums, 16 lanes per marker and
+//                    component); the last block to finish forms F = rho sum q_i dV_i and
+//                    the torque in a fixed order (FP64) and, in a forward step, the
+//                    Eq. (12) RK4 update of the body with the force frozen
+//   rk4              the same body update on its own (coupling sub-iterations)
 //
 // Kernel evaluation: node offsets from markers are formed in FP64, the
 // kernel phi in the field precision T.
@@ -216,92 +217,93 @@ __device__ __forceinline__ double sum16(double s) {
   return s;
 }
 
-// F_N_i for both components (Eq. 19)
+// F_N_i of Eq. (19) and the scatter of Eq. (18) in one pass: the 16 lanes of a
+// (marker, component) pair evaluate delta_h at their support node once, sum
+// F_N over the non-solid nodes by shuffles (every lane receives the sum), and
+// the lanes whose node is an IB face add w = delta dV_i / F_N_i and w times the
+// marker velocity to the numerator and denominator of u_IB.
 template <typename T>
-__global__ void fn_gather_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
-                                 const double* __restrict__ body, const Flags flags, double* __restrict__ fn) {
+__global__ void ib_target_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
+                                 const double* __restrict__ ds, const double* __restrict__ body, double omega,
+                                 double cx, double cy, const Flags flags, double* __restrict__ fn, T* num0, T* den0,
+                                 T* num1, T* den1) {
   const Lane L = lane_of(G, nm);
   double s = 0.0;
+  T d = T(0);
+  long long face = -1;
+  double X = 0.0, Y = 0.0;
   if (L.live && L.b < G.width) {
     const int c = L.c;
-    const double X = X0[L.m] + body[0], Y = Y0[L.m] + body[1];
+    X = X0[L.m] + body[0];
+    Y = Y0[L.m] + body[1];
     const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
-    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c] && !((c ? flags.p[1] : flags.p[0])[(size_t)j * G.ex[c] + i] & 1)) {
-      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
-      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
-      s = (double)(px * py) * G.ihxy;
-    }
-  }
-  s = sum16(s);
-  if (L.live && (threadIdx.x & 15) == 0) fn[L.pair] = s;
-}
-
-// Eq. (18): num += w_i wdot_i, den += w_i on IB faces, w_i = delta dV_i / F_N_i.
-template <typename T>
-__global__ void ib_scatter_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
-                                  const double* __restrict__ ds, const double* __restrict__ body, double omega,
-                                  double cx, double cy, const Flags flags, const double* __restrict__ fn,
-                                  T* num0, T* den0, T* num1, T* den1) {
-  const int nn = G.width * G.width;
-  const long long total = 2ll * nm * nn;
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long key = -1;
-  T wv = T(0), w = T(0);
-  int c = 0;
-  if (t < total) {
-    // thread order: component, node, marker (consecutive lanes = consecutive sorted markers)
-    c = (int)(t / ((long long)nm * nn));
-    const int r = (int)(t - (long long)c * nm * nn);
-    const int node = r / nm, m = r - node * nm;
-    const int a = node % G.width, b = node / G.width;
-    const double X = X0[m] + body[0], Y = Y0[m] + body[1];
-    const int i = first_node(G, X, G.x0c[c], G.hx) + a, j = first_node(G, Y, G.y0c[c], G.hy) + b;
     if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
       const size_t f = (size_t)j * G.ex[c] + i;
-      if (flags.p[c][f] & 2) {
-        const double F = fn[2 * m + c];
-        if (F > 0.0) {
-          const T d = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx)) *
-                      phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
-          w = T((double)d * G.ihxy * (ds[m] * G.hx) / F);
-          // marker velocity: body translation plus surface rotation
-          const double vm = c == 0 ? body[2] - omega * (Y - (cy + body[1])) : body[3] + omega * (X - (cx + body[0]));
-          wv = w * T(vm);
-          key = (long long)c << 40 | (long long)f;
-        }
-      }
+      const uint8_t fl = (c ? flags.p[1] : flags.p[0])[f];
+      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
+      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
+      d = px * py;
+      if (!(fl & 1)) s = (double)d * G.ihxy;   // solid nodes are excluded from F_N
+      if (fl & 2) face = (long long)f;
     }
   }
-  // warp-level reduction of contributions that hit the same face, then one atomic per face
-  const unsigned full = 0xffffffffu;
-  const unsigned grp = __match_any_sync(full, key);
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(grp) - 1;
-  T sw = T(0), swv = T(0);
-  for (int src = 0; src < 32; ++src) {
-    const T a = __shfl_sync(full, w, src), b = __shfl_sync(full, wv, src);
-    if ((grp >> src) & 1u) {
-      sw += a;
-      swv += b;
-    }
-  }
-  if (key >= 0 && lane == leader) {
-    const size_t f = (size_t)(key & ((1ll << 40) - 1));
-    if ((key >> 40) == 0) {
-      atomicAdd(&num0[f], swv);
-      atomicAdd(&den0[f], sw);
-    } else {
-      atomicAdd(&num1[f], swv);
-      atomicAdd(&den1[f], sw);
-    }
+  const double F = sum16(s);
+  if (L.live && (threadIdx.x & 15) == 0) fn[L.pair] = F;
+  if (face >= 0 && F > 0.0) {
+    const int c = L.c;
+    const T w = T((double)d * G.ihxy * (ds[L.m] * G.hx) / F);
+    // marker velocity: body translation plus surface rotation
+    const double vm = c == 0 ? body[2] - omega * (Y - (cy + body[1])) : body[3] + omega * (X - (cx + body[0]));
+    atomicAdd(c ? &num1[face] : &num0[face], w * T(vm));
+    atomicAdd(c ? &den1[face] : &den0[face], w);
   }
 }
 
-// q_i = - sum_x f(x) delta_h(x - X_i) dv(x)   (Eq. 20), per marker and component
+// Eq. (12) with F frozen over the step: classical RK4 per active DOF (one thread).
+__device__ void rk4_body(double* __restrict__ st, const double* __restrict__ F, double m, double k, double c, int ax,
+                         int ay, double dt) {
+  const int act[2] = {ax, ay};
+  for (int d = 0; d < 2; ++d) {
+    double w = st[d], v = st[2 + d];
+    if (!act[d]) {
+      st[d] = 0.0;
+      st[2 + d] = 0.0;
+      continue;
+    }
+    const double f = F[d];
+    auto acc = [&](double x, double u) { return (f - c * u - k * x) / m; };
+    const double k1x = v, k1v = acc(w, v);
+    const double k2x = v + 0.5 * dt * k1v, k2v = acc(w + 0.5 * dt * k1x, v + 0.5 * dt * k1v);
+    const double k3x = v + 0.5 * dt * k2v, k3v = acc(w + 0.5 * dt * k2x, v + 0.5 * dt * k2v);
+    const double k4x = v + dt * k3v, k4v = acc(w + dt * k3x, v + dt * k3v);
+    st[d] = w + dt / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
+    st[2 + d] = v + dt / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+  }
+}
+
+__global__ void rk4_kernel(double* __restrict__ st, const double* __restrict__ F, double m, double k, double c,
+                           int ax, int ay, double dt) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) rk4_body(st, F, m, k, c, ax, ay, dt);
+}
+
+struct BodyODE {
+  double* st;   // body state to advance after the force, or null
+  double m, k, c, dt;
+  int ax, ay;
+};
+
+// q_i = - sum_x f(x) delta_h(x - X_i) dv(x)   (Eq. 20), 16 lanes per marker and
+// component; then F = rho sum_i q_i dV_i and the torque rho sum_i dV_i (r_i x q_i)
+// by the block that finishes last (the other blocks publish their q before
+// taking a ticket; no block waits), in a fixed summation order, and, when asked,
+// the body ODE step with that force.
 template <typename T>
-__global__ void force_gather_kernel(const IBGeom G, int nm, const double* __restrict__ X0,
-                                    const double* __restrict__ Y0, const double* __restrict__ body,
-                                    const T* __restrict__ f0, const T* __restrict__ f1, double* __restrict__ q) {
+__global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const double* __restrict__ X0,
+                                                   const double* __restrict__ Y0, const double* __restrict__ ds,
+                                                   const double* body, const T* __restrict__ f0,
+                                                   const T* __restrict__ f1, double cx, double cy, double rho,
+                                                   double* __restrict__ q, double* __restrict__ F,
+                                                   unsigned* __restrict__ ticket, const BodyODE ode) {
   const Lane L = lane_of(G, nm);
   double s = 0.0;
   if (L.live && L.b < G.width) {
@@ -318,21 +320,23 @@ __global__ void force_gather_kernel(const IBGeom G, int nm, const double* __rest
   }
   s = sum16(s);
   if (L.live && (threadIdx.x & 15) == 0) q[L.pair] = -s;
-}
-
-// F = rho sum_i q_i dV_i, torque = rho sum_i dV_i (r_i x q_i); one CTA, fixed summation order.
-__global__ void force_reduce_kernel(int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
-                                    const double* __restrict__ ds, const double* __restrict__ body, double cx,
-                                    double cy, double hx, double rho, const double* __restrict__ q,
-                                    double* __restrict__ F) {
+  // the last block to finish reduces
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   __shared__ double s0[kT], s1[kT], s2[kT];
+  const double bx = body[0], by = body[1];
   double a = 0, b = 0, tq = 0;
   for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-    const double dV = ds[m] * hx;
-    const double qx = q[2 * m], qy = q[2 * m + 1];
+    const double dV = ds[m] * G.hx;
+    const double qx = __ldcg(q + 2 * m), qy = __ldcg(q + 2 * m + 1);
     a += qx * dV;
     b += qy * dV;
-    const double rx = X0[m] + body[0] - (cx + body[0]), ry = Y0[m] + body[1] - (cy + body[1]);
+    const double rx = X0[m] + bx - (cx + bx), ry = Y0[m] + by - (cy + by);
     tq += dV * (rx * qy - ry * qx);
   }
   s0[threadIdx.x] = a;
@@ -351,29 +355,8 @@ __global__ void force_reduce_kernel(int nm, const double* __restrict__ X0, const
     F[0] = rho * s0[0];
     F[1] = rho * s1[0];
     F[2] = rho * s2[0];
-  }
-}
-
-// Eq. (12) with F frozen over the step: classical RK4 per active DOF.
-__global__ void rk4_kernel(double* __restrict__ st, const double* __restrict__ F, double m, double k, double c,
-                           int ax, int ay, double dt) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int act[2] = {ax, ay};
-  for (int d = 0; d < 2; ++d) {
-    double w = st[d], v = st[2 + d];
-    if (!act[d]) {
-      st[d] = 0.0;
-      st[2 + d] = 0.0;
-      continue;
-    }
-    const double f = F[d];
-    auto acc = [&](double x, double u) { return (f - c * u - k * x) / m; };
-    const double k1x = v, k1v = acc(w, v);
-    const double k2x = v + 0.5 * dt * k1v, k2v = acc(w + 0.5 * dt * k1x, v + 0.5 * dt * k1v);
-    const double k3x = v + 0.5 * dt * k2v, k3v = acc(w + 0.5 * dt * k2x, v + 0.5 * dt * k2v);
-    const double k4x = v + dt * k3v, k4v = acc(w + dt * k3x, v + dt * k3v);
-    st[d] = w + dt / 6.0 * (k1x + 2.0 * k2x + 2.0 * k3x + k4x);
-    st[2 + d] = v + dt / 6.0 * (k1v + 2.0 * k2v + 2.0 * k3v + k4v);
+    *ticket = 0u;
+    if (ode.st) rk4_body(ode.st, F, ode.m, ode.k, ode.c, ode.ax, ode.ay, ode.dt);
   }
 }
 
@@ -431,22 +414,21 @@ void ib_prepare(fs_grid* G, const double* body_state) {
   }
   const IBGeom g = make_geom(G);
   const int nlane = 2 * B.nm * 16;
-  FS_LAUNCH(G, "fn_gather", fn_gather_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state, dflags, B.fn));
-  const long long total = 2ll * B.nm * g.width * g.width;
-  FS_LAUNCH(G, "ib_scatter", ib_scatter_kernel<T><<<(int)((total + kT - 1) / kT), kT, 0, G->stream>>>(
-      g, B.nm, B.X0, B.Y0, B.ds, body_state, B.omega, B.centre[0], B.centre[1], dflags, B.fn, (T*)B.num[0],
-      (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
+  FS_LAUNCH(G, "ib_target", ib_target_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
+                                g, B.nm, B.X0, B.Y0, B.ds, body_state, B.omega, B.centre[0], B.centre[1], dflags, B.fn,
+                                (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
 }
 
 template <typename T>
-void ib_forces(fs_grid* G, const double* body_state) {
+void ib_forces(fs_grid* G, double* body_state, double* advance, double dt) {
   IBDev& B = G->ib;
   const IBGeom g = make_geom(G);
   const int nlane = 2 * B.nm * 16;
-  FS_LAUNCH(G, "force_gather", force_gather_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state,
-                                                                          (const T*)B.f[0], (const T*)B.f[1], B.q));
-  FS_LAUNCH(G, "force_reduce", force_reduce_kernel<<<1, kT, 0, G->stream>>>(B.nm, B.X0, B.Y0, B.ds, body_state, B.centre[0], B.centre[1], G->hx,
-                                               G->rho, B.q, B.F));
+  BodyODE ode{nullptr, B.mass, B.k, B.c, dt, B.active[0], B.active[1]};
+  if (advance && B.mass > 0) ode.st = advance;
+  FS_LAUNCH(G, "ib_force", force_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
+                               g, B.nm, B.X0, B.Y0, B.ds, body_state, (const T*)B.f[0], (const T*)B.f[1], B.centre[0],
+                               B.centre[1], G->rho, B.q, B.F, B.ticket, ode));
   B.have_forces = true;
 }
 
@@ -458,7 +440,7 @@ void body_rk4(fs_grid* G, double* body_state, double dt) {
 
 template void ib_prepare<float>(fs_grid*, const double*);
 template void ib_prepare<double>(fs_grid*, const double*);
-template void ib_forces<float>(fs_grid*, const double*);
-template void ib_forces<double>(fs_grid*, const double*);
+template void ib_forces<float>(fs_grid*, double*, double*, double);
+template void ib_forces<double>(fs_grid*, double*, double*, double);
 
 }  // namespace fs
