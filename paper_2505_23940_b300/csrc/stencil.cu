@@ -38,6 +38,7 @@ struct PredArgs {
   T dt, a, b;
   int conv;
   int X, Y;                  // thread grid (largest component extents along x and y)
+  int jlo;                   // first row of the vector kernels (walls: 2; the wall rows run apart)
   const uint8_t* flags[2];   // IB (2-D): per-face flags, accumulators and forcing output
   T* num[2];
   T* den[2];
@@ -49,7 +50,7 @@ struct PredArgs {
   const double* oscale;
   T ihy0;                    // 1 / h_y of a uniform periodic y (predictor3_kernel<T, true>)
   const uint8_t* flags3[3];  // static 3-D body (boxes): per-face flags, forced faces take u_s = 0
-  T* fout3[3];               // and the forcing term f on every face (0 off forced faces)
+  T* fout3[3];               // and the forcing term f on forced faces (zero from the start elsewhere)
   const T* nut[4];           // Smagorinsky eddy viscosity: cell centres, xy, xz, yz edges (or null)
 };
 
@@ -230,7 +231,7 @@ __device__ __forceinline__ void predict_face(const PredArgs<T>& A, const Acc& U,
   }
   A.out[C][t] = res;
   if (C < 2 && A.fout[0]) A.fout[C][t] = fval;
-  if (A.fout3[0]) A.fout3[C][t] = fval;
+  if (A.fout3[0] && A.flags3[C][t]) A.fout3[C][t] = fval;   // off forced faces f stays 0 (static body)
 }
 
 // One thread per cell position (i, j, k) computes every component's face there.
@@ -441,6 +442,22 @@ __device__ __forceinline__ void predict_cell_general(const PredArgs<T>& A, int i
   predict_face<T, 2>(A, U, i, j, k);
 }
 
+// The rows of a wall-bounded grid whose stencil reaches a wall (j = 0, 1, ny - 1,
+// ny): one cell per thread through the general path, launched beside the vector
+// kernels, which then cover rows 2 .. ny - 2 only (a wall row inside a z-marching
+// block would hold the whole block to the general path's pace).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) predictor_wall_rows_kernel(const PredArgs<T> A) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int r = blockIdx.y;   // 0, 1, 2, 3 -> j = 0, 1, ny - 1, ny
+  const int k = blockIdx.z;
+  const int ny = A.g.ny;
+  const int j = r < 2 ? r : ny - 3 + r;
+  if (i >= A.X || j >= A.Y) return;
+  predict_cell_general(A, i, j, k);
+}
+
 // The predictor for the common 3-D case -- x and z periodic, central
 // convection, no immersed body -- with the 27 distinct neighbour values of a
 // cell loaded once and shared by its three faces.  YPER: y periodic (uniform
@@ -507,12 +524,10 @@ __global__ void __launch_bounds__(kThreads) predictor3_kernel(const PredArgs<T> 
   }
   if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
     T fu = T(0), fv = T(0), fw = T(0);
-    if (A.flags3[0][r00 + i]) { fu = -Ru - n.u000 / dt; ou = T(0); }
-    if (A.flags3[1][v00 + i]) { fv = -Rv - n.v000 / dt; ov = T(0); }
-    if (A.flags3[2][r00 + i]) { fw = -Rw - n.w000 / dt; ow = T(0); }
-    A.fout3[0][r00 + i] = fu;
-    A.fout3[1][v00 + i] = fv;
-    A.fout3[2][r00 + i] = fw;
+    // the body is static: f is written on forced faces only and stays 0 elsewhere
+    if (A.flags3[0][r00 + i]) { fu = -Ru - n.u000 / dt; ou = T(0); A.fout3[0][r00 + i] = fu; }
+    if (A.flags3[1][v00 + i]) { fv = -Rv - n.v000 / dt; ov = T(0); A.fout3[1][v00 + i] = fv; }
+    if (A.flags3[2][r00 + i]) { fw = -Rw - n.w000 / dt; ow = T(0); A.fout3[2][r00 + i] = fw; }
   }
   if (j < ny) {
     A.out[0][r00 + i] = ou;
@@ -555,10 +570,11 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
   const Geom<float>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int i0 = VW * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = A.jlo + blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i0 >= nx || j >= A.Y) return;
   if (!YPER && (j < 2 || j > ny - 2)) {
+    if (A.jlo > 0) return;   // the wall-row kernel has them
     for (int e = 0; e < VW; ++e) predict_cell_general(A, i0 + e, j, k);
     return;
   }
@@ -630,17 +646,15 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
   if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      float fo[VW];
+      // u* = u + dt R, so R = (u* - u) / dt and f = -R - u / dt = -u* / dt; the body is
+      // static, so f is written on forced faces only and stays 0 elsewhere
 #pragma unroll
       for (int e = 0; e < VW; ++e) {
-        fo[e] = 0.f;
         if (A.flags3[c][rows[c] + i0 + e]) {
-          // u* = u + dt R, so R = (u* - u) / dt and f = -R - u / dt = -u* / dt
-          fo[e] = -o3[c][e] / dt;
+          A.fout3[c][rows[c] + i0 + e] = -o3[c][e] / dt;
           o3[c][e] = 0.f;
         }
       }
-      stw<VW>(A.fout3[c] + rows[c] + i0, fo);
     }
   }
   if (j < ny) {
@@ -660,11 +674,12 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
   const Geom<float>& g = A.g;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int j = A.jlo + blockIdx.y * blockDim.y + threadIdx.y;
   const int k0 = blockIdx.z * KZ;
   const int k1 = min(k0 + KZ, nz);
   if (i0 >= nx || j >= A.Y) return;
   if (!YPER && (j < 2 || j > ny - 2)) {
+    if (A.jlo > 0) return;   // the wall-row kernel has them
     for (int k = k0; k < k1; ++k)
       for (int e = 0; e < 4; ++e) predict_cell_general(A, i0 + e, j, k);
     return;
@@ -743,16 +758,15 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
     if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        float fo[4];
+        const uchar4 fl = *reinterpret_cast<const uchar4*>(A.flags3[c] + rows[c] + i0);
+        const bool on[4] = {fl.x != 0, fl.y != 0, fl.z != 0, fl.w != 0};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          fo[e] = 0.f;
-          if (A.flags3[c][rows[c] + i0 + e]) {
-            fo[e] = -o3[c][e] / dt;
+          if (on[e]) {   // f on forced faces only (static body: 0 elsewhere from the start)
+            A.fout3[c][rows[c] + i0 + e] = -o3[c][e] / dt;
             o3[c][e] = 0.f;
           }
         }
-        stw<4>(A.fout3[c] + rows[c] + i0, fo);
       }
     }
     if (j < ny) {
@@ -992,16 +1006,15 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs
       if (A.flags3[0]) {   // static 3-D body (forward Euler): u* = u_s = 0 and f on forced faces
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          float fo[4];
+          const uchar4 fl = *reinterpret_cast<const uchar4*>(A.flags3[c] + row + i0);
+          const bool on[4] = {fl.x != 0, fl.y != 0, fl.z != 0, fl.w != 0};
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            fo[e] = 0.f;
-            if (A.flags3[c][row + i0 + e]) {
-              fo[e] = -o3[c][e] / dt;
+            if (on[e]) {   // f on forced faces only (static body: 0 elsewhere from the start)
+              A.fout3[c][row + i0 + e] = -o3[c][e] / dt;
               o3[c][e] = 0.f;
             }
           }
-          stw<4>(A.fout3[c] + row + i0, fo);
         }
       }
 #pragma unroll
@@ -1237,6 +1250,7 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
   A.conv = G->conv;
   A.X = G->nx + (G->per[0] ? 0 : 1);
   A.Y = G->ny + (G->per[1] ? 0 : 1);
+  A.jlo = 0;
   for (int c = 0; c < 2; ++c) {
     const bool ibc = G->has_body;
     A.flags[c] = ibc ? G->ib.flags[c] : nullptr;
@@ -1302,16 +1316,24 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
           launch_pdl(G, "predictor", predictor3t_kernel<256>, sg, dim3(64, 4), stage_smem<256>(), A, KZ, G->dstatus);
         return;
       }
+      // walls: the four rows that reach a wall run in their own kernel, the vector kernels take rows 2 .. ny - 2
+      int rows = A.Y;
+      if (vec && !G->per[1] && G->ny >= 5) {
+        A.jlo = 2;
+        rows = G->ny - 3;
+        launch_pdl(G, "predictor_walls", predictor_wall_rows_kernel<T>, dim3((A.X + kThreads - 1) / kThreads, 4, G->nz),
+                   dim3(kThreads), 0, A);
+      }
       if (vec && vw == 4 && KZ > 1) {
         const dim3 vb(32, 8);
-        const dim3 vg((G->nx / 4 + 31) / 32, (A.Y + 7) / 8, (G->nz + KZ - 1) / KZ);
+        const dim3 vg((G->nx / 4 + 31) / 32, (rows + 7) / 8, (G->nz + KZ - 1) / KZ);
         if (G->per[1]) launch_pdl(G, "predictor", predictor3z_kernel<true>, vg, vb, 0, A, KZ);
         else launch_pdl(G, "predictor", predictor3z_kernel<false>, vg, vb, 0, A, KZ);
         return;
       }
       if (vec) {
         const dim3 vb(32, 8);
-        const dim3 vg((G->nx / vw + 31) / 32, (A.Y + 7) / 8, G->nz);
+        const dim3 vg((G->nx / vw + 31) / 32, (rows + 7) / 8, G->nz);
         if (vw == 4) {
           if (G->per[1]) launch_pdl(G, "predictor", predictor3v_kernel<true, 4>, vg, vb, 0, A);
           else launch_pdl(G, "predictor", predictor3v_kernel<false, 4>, vg, vb, 0, A);
