@@ -409,9 +409,11 @@ def run_ours(args, ws, rank, local):
         slots = ro.used_slots
         line["fwd_adj"] = {"value": cells * args.steps * ws / (fa_ms * 1e-3), "unit": "cell-updates/s",
                            "steps": args.steps, "slots": slots, "recomputed_steps": ro.recomputed,
+                           "recorded_stages": ro.recorded,
                            "forward_ms": fwd_ms, "reverse_ms": adj_ms,
-                           "note": "K forward steps keeping snapshots, then the reverse sweep "
-                                   "(recomputation + adjoint steps)"}
+                           "note": "K forward steps keeping snapshots (and, with recorded_stages, each "
+                                   "step's RK3 stage states), then the reverse sweep (recomputation + adjoint "
+                                   "steps)"}
         # the same with 4 snapshot slots: binomial recomputation in the reverse sweep
         ro4 = Rollout(g, wl.dt, args.steps, slots=4)
         lam4_T = [x * vol for x in ro4.forward(ua)[0]]
@@ -430,7 +432,7 @@ def run_ours(args, ws, rank, local):
         lam_mixed = ro.backward(ua, None, lam_T)[0]
         g64 = grid_from_workload(wl, "fp64", stream=stream)
         u64 = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev).contiguous() for a in wl.u0]
-        ro64 = Rollout(g64, wl.dt, args.steps, slots=slots)
+        ro64 = Rollout(g64, wl.dt, args.steps)   # the same snapshot policy as the mixed run
         lam64_T = [x * vol for x in ro64.forward(u64)[0]]
         torch.cuda.synchronize()
         ea.record(stream)

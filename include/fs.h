@@ -180,6 +180,19 @@ int fs_step(fs_grid* grid, fs_state* st, double dt, int nsteps);
 int fs_step_adjoint(fs_grid* grid, const fs_state* st_n, fs_state* lam,
                     const double* dJdF, fs_param_grad* g, double dt);
 
+/* One RK3 step (fs_step with nsteps = 1 and a fixed dt > 0) that leaves its two
+ * intermediate stage states in v1[dim], v2[dim]: caller-owned device arrays
+ * shaped like st->u, in the grid's precision.  st->p, if not NULL, receives the
+ * pressure.  Errors: FS_ERR_ARG (NULL arrays, dt <= 0, a forward-Euler grid),
+ * FS_ERR_UNSUPPORTED (body, static boxes or Smagorinsky model), FS_ERR_CUDA. */
+int fs_step_record(fs_grid* grid, fs_state* st, double dt, void* const* v1, void* const* v2);
+
+/* fs_step_adjoint of a step recorded by fs_step_record from st_n, with its
+ * stage states v1, v2 (device, not modified): nothing of the forward step is
+ * recomputed.  The result equals fs_step_adjoint's.  Errors as fs_step_record. */
+int fs_step_adjoint_recorded(fs_grid* grid, const fs_state* st_n, void* const* v1, void* const* v2,
+                             fs_state* lam, fs_param_grad* g, double dt);
+
 /* Solve the discrete pressure Poisson equation D G p = rhs (Eq. 9) exactly
  * (FFT / DCT along x and z, FP64 tridiagonal along y) for the zero
  * volume-weighted-mean solution.  rhs, p: device doubles with the cell
@@ -276,8 +289,9 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     shared memory with bulk asynchronous copies; 0: it reads
  *                     them from global memory (four-cell z-marching kernel)
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
- *                     solve: 4, 8 or 16 (default: 4, 8 when the grid has
- *                     fewer 32-column blocks than two per SM); rebuilds the y tables
+ *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
+ *                     grid has fewer 32-column blocks than two per SM, else 4);
+ *                     rebuilds the y tables
  *                     (synchronises the stream; set it before capturing graphs)
  * Results do not depend on them (ysolve_segments: up to rounding).
  * FS_ERR_ARG for an unknown key or value. */

@@ -109,7 +109,9 @@ class Rollout:
 
     Keeps `slots` device copies of the state; slots=None takes as many as half of
     the free device memory holds, up to one per step (no recomputation at all:
-    500 steps of a 128^3 FP32 field are 12.6 GB).  The forward pass already keeps
+    500 steps of a 128^3 FP32 field are 12.6 GB), and on RK3 grids without a body
+    also each step's two stage states when they fit (fs_step_record /
+    fs_step_adjoint_recorded: not even the stages are recomputed).  The forward pass already keeps
     the states the schedule stores before its first adjoint, so a backward after
     a forward starts reversing at once.  Forces of every step (FSI grids) are
     recorded on the device so losses may depend on them.
@@ -122,7 +124,18 @@ class Rollout:
         self.slots = None if slots is None else max(1, int(slots))
         self.used_slots = self.slots
         self.recomputed = 0
+        self.recorded = False
         self._kept = None
+
+    def _recordable(self, u, body):
+        """RK3 grids without a body keep, when memory allows, every step's state and its two
+        stage states: the reverse sweep then recomputes nothing of any step."""
+        g = self.g
+        if self.slots is not None or g.scheme != F.RK3 or g.has_body or g.has_boxes or g.les_cs > 0.0:
+            return False
+        free, _ = torch.cuda.mem_get_info(u[0].device)
+        per = sum(x.numel() * x.element_size() for x in u)
+        return 3 * per * self.n <= 0.5 * free
 
     def _clone(self, u, body):
         return [x.clone() for x in u], (body.clone() if body is not None else None)
@@ -136,6 +149,19 @@ class Rollout:
 
     def forward(self, u0, body0=None):
         u, body = self._clone(u0, body0)
+        if self._recordable(u, body):
+            tape = []
+            for t in range(self.n):
+                un = [x.clone() for x in u]
+                v1 = [torch.empty_like(x) for x in u]
+                v2 = [torch.empty_like(x) for x in u]
+                self.g.step_record(u, self.dt, v1, v2)
+                tape.append((un, v1, v2))
+            self.recorded = True
+            self.used_slots = self.n
+            self._kept = ("tape", tape)
+            return u, None, None
+        self.recorded = False
         slots = self._slots_for(u, body)
         self.used_slots = slots
         stores, _ = split_schedule(self.n, slots)
@@ -160,6 +186,15 @@ class Rollout:
         are accumulated into the given device tensors.  Right after forward() the states it kept
         are used (u0 and body0 must be the forward's inputs); otherwise the schedule starts from
         (u0, body0)."""
+        if self._kept is not None and self._kept[0] == "tape":
+            tape = self._kept[1]
+            self._kept = None
+            lam = [x.clone() for x in lam_u]
+            self.recomputed = 0
+            for t in range(self.n - 1, -1, -1):
+                un, v1, v2 = tape[t]
+                self.g.step_adjoint_recorded(un, v1, v2, lam, self.dt, g_body_force=g_body_force)
+            return lam, None
         if self._kept is not None:
             mem, (work_u, work_b), slots = self._kept
             self._kept = None

@@ -926,7 +926,8 @@ void free_adj_buffers(void* p) {
 }
 
 template <typename T>
-int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJdF, fs_param_grad* pg, double dt) {
+int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJdF, fs_param_grad* pg, double dt,
+                 void* const* rv1, void* const* rv2) {
   AdjBuffers* B = nullptr;
   int rc = adj_buffers(G, &B);
   if (rc != FS_OK) return rc;
@@ -943,17 +944,24 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
   double* bfsum = pg ? pg->body_force : nullptr;
 
   if (G->scheme == FS_RK3) {
-    // recompute the stage states v1, v2 of the forward step
+    // the stage states v1, v2 of the forward step: recorded by it, or recomputed here
     T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
     T* v1[3] = {(T*)B->v1[0], (T*)B->v1[1], (T*)B->v1[2]};
     T* v2[3] = {(T*)B->v2[0], (T*)B->v2[1], (T*)B->v2[2]};
     const double Ac[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
-    launch_predictor<T>(G, u, u, us, dt, Ac[0], Bc[0], nullptr);
-    poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
-    launch_correct<T>(G, us, spec, v1);
-    launch_predictor<T>(G, v1, u, us, dt, Ac[1], Bc[1], nullptr);
-    poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
-    launch_correct<T>(G, us, spec, v2);
+    if (rv1 && rv2) {
+      for (int c = 0; c < 3; ++c) {
+        v1[c] = c < dim ? (T*)rv1[c] : nullptr;
+        v2[c] = c < dim ? (T*)rv2[c] : nullptr;
+      }
+    } else {
+      launch_predictor<T>(G, u, u, us, dt, Ac[0], Bc[0], nullptr);
+      poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
+      launch_correct<T>(G, us, spec, v1);
+      launch_predictor<T>(G, v1, u, us, dt, Ac[1], Bc[1], nullptr);
+      poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
+      launch_correct<T>(G, us, spec, v2);
+    }
     T* const* vs[3] = {u, v1, v2};
     for (int c = 0; c < dim; ++c) cudaMemsetAsync(la[c], 0, comp_count(G, c) * sizeof(T), G->stream);
     // cur = lam of the stage output, starting from lam^{n+1}
@@ -1087,7 +1095,9 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
   return cuda_check(cudaGetLastError(), "fs_step_adjoint");
 }
 
-template int step_adjoint<float>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double);
-template int step_adjoint<double>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double);
+template int step_adjoint<float>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double,
+                                  void* const*, void* const*);
+template int step_adjoint<double>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double,
+                                   void* const*, void* const*);
 
 }  // namespace fs

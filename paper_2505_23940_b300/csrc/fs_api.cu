@@ -123,16 +123,18 @@ size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) 
 // segment's block (e_j = 1 / beta_j, c'_j) and its right / left spikes v, w
 // (the block's response to its coupling with the next / previous segment).
 // The singular zero mode replaces row 0 by phi_0 = 0 (e_0 = 0, no couplings).
-// NSEG is 4 unless the grid has fewer 32-column blocks than two per SM (2-D
-// grids): then 8 shorter segments halve the sequential sweeps (16 segments
-// cost more in the denser interface solve than they save).
+// NSEG is 4, or 8 for ny >= 192 and for grids with fewer 32-column blocks than
+// two per SM (2-D grids): shorter sequential sweeps (16 segments cost more in
+// the denser interface solve than they save).
 int build_tables(fs_grid* G) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   if (G->tune_ynseg > 0) {
     G->ynseg = G->tune_ynseg;
   } else {
     const long blocks = (long)((nx + 31) / 32) * (G->dim == 3 ? nz : 1);
-    G->ynseg = (blocks < 2 * 148 && ny >= 8 * 8) ? 8 : 4;
+    // sweeps of about 32 rows: 8 segments from ny = 192 on (256^3 channel: 296 against 382 us),
+    // and on grids with too few columns for two blocks per SM (2-D: latency-bound)
+    G->ynseg = ((blocks < 2 * 148 && ny >= 8 * 8) || ny >= 192) ? 8 : 4;
   }
   const int NSEG = G->ynseg;
   G->nmx = G->xmode == 1 ? nx : nx / 2 + 1;
@@ -301,19 +303,28 @@ void free_body(fs_grid* G) {
   G->has_body = false;
 }
 
+// rec1, rec2: where an RK3 step leaves its two stage states (null: the grid's stage buffer)
 template <typename T>
-void step_once(fs_grid* G, fs_state* st, double dt, bool want_p) {
+void step_once(fs_grid* G, fs_state* st, double dt, bool want_p, void* const* rec1 = nullptr,
+               void* const* rec2 = nullptr) {
   T* u[3] = {(T*)st->u[0], (T*)st->u[1], (T*)(G->dim == 3 ? st->u[2] : nullptr)};
   T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
   T* spec = (T*)G->spec;
   if (G->scheme == FS_RK3) {
     T* v[3] = {(T*)G->ustage[0], (T*)G->ustage[1], (T*)G->ustage[2]};
+    T* v1[3] = {v[0], v[1], v[2]};
+    T* v2[3] = {v[0], v[1], v[2]};
+    if (rec1 && rec2)
+      for (int c = 0; c < G->dim; ++c) {
+        v1[c] = (T*)rec1[c];
+        v2[c] = (T*)rec2[c];
+      }
     const double A[3] = {0.0, 0.75, 1.0 / 3.0}, Bc[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int s = 0; s < 3; ++s) {
-      T* const* in = s == 0 ? u : v;
+      T* const* in = s == 0 ? u : (s == 1 ? v1 : v2);
       launch_predictor<T>(G, in, u, us, dt, A[s], Bc[s], nullptr);
       poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
-      launch_correct<T>(G, us, spec, s == 2 ? u : v);
+      launch_correct<T>(G, us, spec, s == 2 ? u : (s == 0 ? v1 : v2));
     }
     if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / (Bc[2] * dt));
     return;
@@ -843,16 +854,50 @@ int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const doubl
     if (!st_n->body || !lam->body) return set_error(FS_ERR_ARG, "a grid with a body needs st_n->body and lam->body");
     if (G->fsi_iters > 1)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of the strongly coupled (sub-iterated) FSI step");
-  }
-  if (G->les_cs > 0.0) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a step with the Smagorinsky model");
-  if (G->has_ib3) {
-    return set_error(FS_ERR_UNSUPPORTED, "adjoint of a grid with a static 3-D box body");
     if (G->ib.omega != 0.0)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of a body with a prescribed surface rotation");
   }
+  if (G->les_cs > 0.0) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a step with the Smagorinsky model");
+  if (G->has_ib3) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a grid with a static 3-D box body");
   const int rc = G->prec == FS_MIXED ? step_adjoint<float>(G, st_n, lam, dJdF, g, dt)
                                      : step_adjoint<double>(G, st_n, lam, dJdF, g, dt);
   return rc;
+}
+
+namespace {
+int check_recordable(const fs_grid* G, void* const* v1, void* const* v2) {
+  if (!v1 || !v2) return set_error(FS_ERR_ARG, "NULL stage arrays");
+  for (int c = 0; c < G->dim; ++c)
+    if (!v1[c] || !v2[c]) return set_error(FS_ERR_ARG, "NULL stage component");
+  if (G->scheme != FS_RK3) return set_error(FS_ERR_ARG, "stage states exist for the RK3 scheme only");
+  if (G->has_body || G->has_ib3) return set_error(FS_ERR_UNSUPPORTED, "recorded stages of a grid with a body");
+  if (G->les_cs > 0.0) return set_error(FS_ERR_UNSUPPORTED, "recorded stages with the Smagorinsky model");
+  return FS_OK;
+}
+}  // namespace
+
+int fs_step_record(fs_grid* G, fs_state* st, double dt, void* const* v1, void* const* v2) {
+  if (!G || !st) return set_error(FS_ERR_ARG, "NULL argument");
+  for (int c = 0; c < G->dim; ++c)
+    if (!st->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
+  if (!(dt > 0)) return set_error(FS_ERR_ARG, "a recorded step needs a fixed dt > 0");
+  int rc = check_recordable(G, v1, v2);
+  if (rc != FS_OK) return rc;
+  if (G->prec == FS_MIXED) step_once<float>(G, st, dt, st->p != nullptr, v1, v2);
+  else step_once<double>(G, st, dt, st->p != nullptr, v1, v2);
+  return cuda_check(cudaGetLastError(), "fs_step_record launch");
+}
+
+int fs_step_adjoint_recorded(fs_grid* G, const fs_state* st_n, void* const* v1, void* const* v2, fs_state* lam,
+                             fs_param_grad* g, double dt) {
+  if (!G || !st_n || !lam) return set_error(FS_ERR_ARG, "NULL argument");
+  if (!(dt > 0)) return set_error(FS_ERR_ARG, "the adjoint needs the fixed step dt > 0 of the forward step");
+  for (int c = 0; c < G->dim; ++c)
+    if (!st_n->u[c] || !lam->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
+  int rc = check_recordable(G, v1, v2);
+  if (rc != FS_OK) return rc;
+  return G->prec == FS_MIXED ? step_adjoint<float>(G, st_n, lam, nullptr, g, dt, v1, v2)
+                             : step_adjoint<double>(G, st_n, lam, nullptr, g, dt, v1, v2);
 }
 
 int fs_solve_pressure(fs_grid* G, const double* rhs, double* p) {

@@ -354,8 +354,10 @@ void body_rk4(fs_grid* g, double* body_state, double dt);
 template <typename T> void ib3_forces(fs_grid* g);
 void free_ib3(fs_grid* g);
 // adjoint.cu
+// rv1, rv2: the RK3 stage states recorded by the forward step (then nothing is recomputed), or null
 template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state* lam, const double* dJdF,
-                                       fs_param_grad* pg, double dt);
+                                       fs_param_grad* pg, double dt, void* const* rv1 = nullptr,
+                                       void* const* rv2 = nullptr);
 void free_adj_buffers(void* p);
 // errors
 int set_error(int code, const std::string& msg);

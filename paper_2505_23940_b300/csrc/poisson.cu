@@ -549,8 +549,8 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
 }
 
 // Partitioned (SPIKE) solve: every column is split into NSEG segments of
-// about ny / NSEG rows solved concurrently by NSEG threads (NSEG = 4, or 8
-// when the grid has too few columns to occupy every SM twice: 2-D grids).  Each segment's
+// about ny / NSEG rows solved concurrently by NSEG threads (NSEG = 4, or 8 for
+// ny >= 192 and for grids with too few columns to occupy every SM twice).  Each segment's
 // local factors (e_j = 1 / beta_j, c'_j) and its two spikes (the response to
 // its coupling with the neighbouring segments, v_j and w_j) are tabulated per
 // eigenvalue on the host, so one step of the solve is

@@ -66,6 +66,9 @@ def lib():
         L.fs_field_extent.argtypes = [c_void_p, c_int, POINTER(c_int)]
         L.fs_set_ib_markers.argtypes = [c_void_p, POINTER(BodyDesc)]
         L.fs_step.argtypes = [c_void_p, POINTER(State), c_double, c_int]
+        L.fs_step_record.argtypes = [c_void_p, POINTER(State), c_double, POINTER(c_void_p), POINTER(c_void_p)]
+        L.fs_step_adjoint_recorded.argtypes = [c_void_p, POINTER(State), POINTER(c_void_p), POINTER(c_void_p),
+                                               POINTER(State), POINTER(ParamGrad), c_double]
         L.fs_step_adjoint.argtypes = [c_void_p, POINTER(State), POINTER(State), POINTER(c_double),
                                       POINTER(ParamGrad), c_double]
         L.fs_solve_pressure.argtypes = [c_void_p, c_void_p, c_void_p]
@@ -142,6 +145,9 @@ class Grid:
         self.h = h
         self.dim = dim
         self.n = n
+        self.scheme = int(scheme)
+        self.has_boxes = False
+        self.les_cs = 0.0
         self.precision = precision
         self.dtype = torch.float64 if precision == FP64 else torch.float32
         self.has_body = False
@@ -208,6 +214,25 @@ class Grid:
             dj = (c_double * 2)(*[float(x) for x in dJdF])
         check(lib().fs_step_adjoint(self.h, byref(sn), byref(sl), dj, byref(g), float(dt)))
 
+    @staticmethod
+    def _ptrs(fields):
+        return (c_void_p * 3)(*[c_void_p(x.data_ptr()) for x in fields], *([None] * (3 - len(fields))))
+
+    def step_record(self, u, dt, v1, v2, p=None):
+        """One RK3 step of u that leaves its two stage states in v1, v2 (lists shaped like u)."""
+        s = self._state(u, p, None)
+        check(lib().fs_step_record(self.h, byref(s), float(dt), self._ptrs(v1), self._ptrs(v2)))
+
+    def step_adjoint_recorded(self, u_n, v1, v2, lam, dt, g_body_force=None):
+        """step_adjoint of a step recorded by step_record from u_n (no recomputation)."""
+        sn = self._state(u_n, None, None)
+        sl = self._state(lam, None, None)
+        g = ParamGrad()
+        g.body_force = g_body_force.data_ptr() if g_body_force is not None else None
+        g.stiffness = None
+        check(lib().fs_step_adjoint_recorded(self.h, byref(sn), self._ptrs(v1), self._ptrs(v2), byref(sl),
+                                             byref(g), float(dt)))
+
     def solve_pressure(self, rhs, p=None):
         p = torch.empty_like(rhs) if p is None else p
         check(lib().fs_solve_pressure(self.h, c_void_p(rhs.data_ptr()), c_void_p(p.data_ptr())))
@@ -268,6 +293,7 @@ class Grid:
     def set_les(self, cs):
         """Constant-coefficient Smagorinsky model with constant cs (0: off)."""
         check(lib().fs_set_les(self.h, float(cs)))
+        self.les_cs = float(cs)
 
     def set_coupling(self, max_subiters, tol=1e-5):
         """Strong FSI coupling: sub-iterate each step up to max_subiters fluid solves (1 = weak)."""

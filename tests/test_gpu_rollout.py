@@ -18,7 +18,7 @@ def face_volumes(wl, dev):
     return [g.face_volume(c).contiguous().to(dev) for c in range(wl.dim)]
 
 
-@pytest.mark.parametrize("slots", [1, 3])
+@pytest.mark.parametrize("slots", [1, 3, None])
 def test_rollout_gradient_initial_field_rk3(slots):
     from paper_2505_23940_b300 import grid_from_workload
     from paper_2505_23940_b300.autodiff import rollout
@@ -94,3 +94,30 @@ def test_rollout_gradient_stiffness_fsi():
     assert abs(float(Jg) - float(J)) < 1e-10 * abs(float(J))
     assert abs(float(gg[0]) - float(go[0])) < 1e-9 * abs(float(go[0]))
     assert rel_l2([x.cpu() for x in gg[1:]], list(go[1:])) < 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_recorded_stages_match_recomputed_adjoint(precision):
+    """fs_step_record leaves the state fs_step gives, and fs_step_adjoint_recorded on its
+    stage states gives fs_step_adjoint's result (same kernels on the same stage values)."""
+    from paper_2505_23940_b300 import grid_from_workload
+    wl = S.isotropic_3d(n=16, steps=3)
+    G = grid_from_workload(wl, precision)
+    dt_ = G.dtype
+    u0 = [torch.tensor(np.asarray(a), dtype=dt_, device="cuda").contiguous() for a in wl.u0]
+    ua = [x.clone() for x in u0]
+    ub = [x.clone() for x in u0]
+    G.step(ua, wl.dt, 1)
+    v1 = [torch.empty_like(x) for x in u0]
+    v2 = [torch.empty_like(x) for x in u0]
+    G.step_record(ub, wl.dt, v1, v2)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(ua, ub))
+    rng = np.random.default_rng(4)
+    lam = [torch.tensor(rng.standard_normal(tuple(x.shape)), dtype=dt_, device="cuda") for x in u0]
+    la = [x.clone() for x in lam]
+    lb = [x.clone() for x in lam]
+    G.step_adjoint(u0, la, wl.dt)
+    G.step_adjoint_recorded(u0, v1, v2, lb, wl.dt)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(la, lb))
