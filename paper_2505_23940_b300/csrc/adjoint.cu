@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 #include "fs_internal.cuh"
 
@@ -203,7 +204,55 @@ struct GatherAdjArgs {
   RhsAdjArgs<T> r;   // u, mu = src, g
   T scale;
   T* out[3];
+  const T* add[3];   // added to out (the RK stage accumulator of the last stage), or null
 };
+
+// The neighbour values one cell's gather reads (u, v, w: linearisation point; m*: mu).
+template <typename T>
+struct AdjNb {
+  T u0, uPx, uMx, uMy, uPxMy, uMz, uPxMz;
+  T v0, vPy, vMx, vMxPy, vMy, vMz, vPyMz;
+  T w0, wPz, wMx, wMxPz, wMy, wMyPz, wMz;
+  T mu0, muPx, muMx, muPy, muMy, muPz, muMz, muPxMy, muPxMz;
+  T mv0, mvPy, mvPx, mvMx, mvMxPy, mvMy, mvPz, mvMz, mvPyMz;
+  T mw0, mwPz, mwPx, mwMx, mwMxPz, mwPy, mwMy, mwMyPz, mwMz;
+};
+
+// (dR/du)^T mu at the three faces of one cell (see rhs_adjoint_gather_kernel).
+template <typename T>
+__device__ __forceinline__ void gather_adj_cell(const AdjNb<T>& n, T ihx, T ihy, T ihz, T nu, T& lu, T& lv, T& lw) {
+  const T h = T(0.5);
+  {  // lambda_u
+    T l = ihx * (n.muPx - n.mu0) * h * (n.u0 + n.uPx) + ihx * (n.mu0 - n.muMx) * h * (n.uMx + n.u0);
+    l += h * (ihy * (n.muPy - n.mu0) * h * (n.vMxPy + n.vPy) + ihy * (n.mu0 - n.muMy) * h * (n.vMx + n.v0));
+    l += h * (ihz * (n.muPz - n.mu0) * h * (n.wMxPz + n.wPz) + ihz * (n.mu0 - n.muMz) * h * (n.wMx + n.w0));
+    l += h * (ihx * (n.mvPy - n.mvMxPy) * h * (n.vMxPy + n.vPy) + ihx * (n.mv0 - n.mvMx) * h * (n.vMx + n.v0));
+    l += h * (ihx * (n.mwPz - n.mwMxPz) * h * (n.wMxPz + n.wPz) + ihx * (n.mw0 - n.mwMx) * h * (n.wMx + n.w0));
+    l += nu * ((n.muPx - T(2) * n.mu0 + n.muMx) * ihx * ihx + (n.muPy - T(2) * n.mu0 + n.muMy) * ihy * ihy +
+               (n.muPz - T(2) * n.mu0 + n.muMz) * ihz * ihz);
+    lu = l;
+  }
+  {  // lambda_v
+    T l = ihy * (n.mvPy - n.mv0) * h * (n.v0 + n.vPy) + ihy * (n.mv0 - n.mvMy) * h * (n.vMy + n.v0);
+    l += h * (ihx * (n.mvPx - n.mv0) * h * (n.uPxMy + n.uPx) + ihx * (n.mv0 - n.mvMx) * h * (n.uMy + n.u0));
+    l += h * (ihz * (n.mvPz - n.mv0) * h * (n.wMyPz + n.wPz) + ihz * (n.mv0 - n.mvMz) * h * (n.wMy + n.w0));
+    l += h * (ihy * (n.muPx - n.muPxMy) * h * (n.uPxMy + n.uPx) + ihy * (n.mu0 - n.muMy) * h * (n.uMy + n.u0));
+    l += h * (ihy * (n.mwPz - n.mwMyPz) * h * (n.wMyPz + n.wPz) + ihy * (n.mw0 - n.mwMy) * h * (n.wMy + n.w0));
+    l += nu * ((n.mvPx - T(2) * n.mv0 + n.mvMx) * ihx * ihx + (n.mvPy - T(2) * n.mv0 + n.mvMy) * ihy * ihy +
+               (n.mvPz - T(2) * n.mv0 + n.mvMz) * ihz * ihz);
+    lv = l;
+  }
+  {  // lambda_w
+    T l = ihz * (n.mwPz - n.mw0) * h * (n.w0 + n.wPz) + ihz * (n.mw0 - n.mwMz) * h * (n.wMz + n.w0);
+    l += h * (ihx * (n.mwPx - n.mw0) * h * (n.uPxMz + n.uPx) + ihx * (n.mw0 - n.mwMx) * h * (n.uMz + n.u0));
+    l += h * (ihy * (n.mwPy - n.mw0) * h * (n.vPyMz + n.vPy) + ihy * (n.mw0 - n.mwMy) * h * (n.vMz + n.v0));
+    l += h * (ihz * (n.muPx - n.muPxMz) * h * (n.uPxMz + n.uPx) + ihz * (n.mu0 - n.muMz) * h * (n.uMz + n.u0));
+    l += h * (ihz * (n.mvPy - n.mvPyMz) * h * (n.vPyMz + n.vPy) + ihz * (n.mv0 - n.mvMz) * h * (n.vMz + n.v0));
+    l += nu * ((n.mwPx - T(2) * n.mw0 + n.mwMx) * ihx * ihx + (n.mwPy - T(2) * n.mw0 + n.mwMy) * ihy * ihy +
+               (n.mwPz - T(2) * n.mw0 + n.mwMz) * ihz * ihz);
+    lw = l;
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const GatherAdjArgs<T> GA) {
@@ -218,68 +267,132 @@ __global__ void __launch_bounds__(kT) rhs_adjoint_gather_kernel(const GatherAdjA
   const int yo[3] = {j > 0 ? j - 1 : ny - 1, j, j < ny - 1 ? j + 1 : 0};
   const int zo[3] = {k > 0 ? k - 1 : nz - 1, k, k < nz - 1 ? k + 1 : 0};
   auto at = [&](int di, int dj, int dk) { return xo[di + 1] + nx * (yo[dj + 1] + ny * zo[dk + 1]); };
-  const T* __restrict__ U = A.u[0];
-  const T* __restrict__ V = A.u[1];
-  const T* __restrict__ W = A.u[2];
-  const T* __restrict__ MU = A.mu[0];
-  const T* __restrict__ MV = A.mu[1];
-  const T* __restrict__ MW = A.mu[2];
-  auto u = [&](int a, int b, int c) { return __ldg(U + at(a, b, c)); };
-  auto v = [&](int a, int b, int c) { return __ldg(V + at(a, b, c)); };
-  auto w = [&](int a, int b, int c) { return __ldg(W + at(a, b, c)); };
-  auto mu = [&](int a, int b, int c) { return __ldg(MU + at(a, b, c)); };
-  auto mv = [&](int a, int b, int c) { return __ldg(MV + at(a, b, c)); };
-  auto mw = [&](int a, int b, int c) { return __ldg(MW + at(a, b, c)); };
-  const T h = T(0.5);
-  const T ihx = g.ihx, ihy = g.ihy[0], ihz = g.ihz, nu = g.nu;
-  // values shared by the three outputs
-  const T u0 = u(0, 0, 0), v0 = v(0, 0, 0), w0 = w(0, 0, 0);
-  const T mu0 = mu(0, 0, 0), mv0 = mv(0, 0, 0), mw0 = mw(0, 0, 0);
-  const T muPx = mu(1, 0, 0), mvPy = mv(0, 1, 0), mwPz = mw(0, 0, 1);
-  const T uPx = u(1, 0, 0), vPy = v(0, 1, 0), wPz = w(0, 0, 1);
+  auto ld = [&](const T* f, int a, int b, int c) { return __ldg(f + at(a, b, c)); };
+  const T *U = A.u[0], *V = A.u[1], *W = A.u[2], *MU = A.mu[0], *MV = A.mu[1], *MW = A.mu[2];
+  AdjNb<T> n;
+  n.u0 = ld(U, 0, 0, 0); n.uPx = ld(U, 1, 0, 0); n.uMx = ld(U, -1, 0, 0); n.uMy = ld(U, 0, -1, 0);
+  n.uPxMy = ld(U, 1, -1, 0); n.uMz = ld(U, 0, 0, -1); n.uPxMz = ld(U, 1, 0, -1);
+  n.v0 = ld(V, 0, 0, 0); n.vPy = ld(V, 0, 1, 0); n.vMx = ld(V, -1, 0, 0); n.vMxPy = ld(V, -1, 1, 0);
+  n.vMy = ld(V, 0, -1, 0); n.vMz = ld(V, 0, 0, -1); n.vPyMz = ld(V, 0, 1, -1);
+  n.w0 = ld(W, 0, 0, 0); n.wPz = ld(W, 0, 0, 1); n.wMx = ld(W, -1, 0, 0); n.wMxPz = ld(W, -1, 0, 1);
+  n.wMy = ld(W, 0, -1, 0); n.wMyPz = ld(W, 0, -1, 1); n.wMz = ld(W, 0, 0, -1);
+  n.mu0 = ld(MU, 0, 0, 0); n.muPx = ld(MU, 1, 0, 0); n.muMx = ld(MU, -1, 0, 0); n.muPy = ld(MU, 0, 1, 0);
+  n.muMy = ld(MU, 0, -1, 0); n.muPz = ld(MU, 0, 0, 1); n.muMz = ld(MU, 0, 0, -1); n.muPxMy = ld(MU, 1, -1, 0);
+  n.muPxMz = ld(MU, 1, 0, -1);
+  n.mv0 = ld(MV, 0, 0, 0); n.mvPy = ld(MV, 0, 1, 0); n.mvPx = ld(MV, 1, 0, 0); n.mvMx = ld(MV, -1, 0, 0);
+  n.mvMxPy = ld(MV, -1, 1, 0); n.mvMy = ld(MV, 0, -1, 0); n.mvPz = ld(MV, 0, 0, 1); n.mvMz = ld(MV, 0, 0, -1);
+  n.mvPyMz = ld(MV, 0, 1, -1);
+  n.mw0 = ld(MW, 0, 0, 0); n.mwPz = ld(MW, 0, 0, 1); n.mwPx = ld(MW, 1, 0, 0); n.mwMx = ld(MW, -1, 0, 0);
+  n.mwMxPz = ld(MW, -1, 0, 1); n.mwPy = ld(MW, 0, 1, 0); n.mwMy = ld(MW, 0, -1, 0); n.mwMyPz = ld(MW, 0, -1, 1);
+  n.mwMz = ld(MW, 0, 0, -1);
+  T lu, lv, lw;
+  gather_adj_cell(n, g.ihx, g.ihy[0], g.ihz, g.nu, lu, lv, lw);
   const int p = at(0, 0, 0);
-  {  // lambda_u
-    const T uMx = u(-1, 0, 0);
-    const T vMxPy = v(-1, 1, 0), vMx = v(-1, 0, 0), wMxPz = w(-1, 0, 1), wMx = w(-1, 0, 0);
-    const T muMx = mu(-1, 0, 0), muPy = mu(0, 1, 0), muMy = mu(0, -1, 0), muPz = mu(0, 0, 1), muMz = mu(0, 0, -1);
-    const T mvMxPy = mv(-1, 1, 0), mvMx = mv(-1, 0, 0), mwMxPz = mw(-1, 0, 1), mwMx = mw(-1, 0, 0);
-    T l = ihx * (muPx - mu0) * h * (u0 + uPx) + ihx * (mu0 - muMx) * h * (uMx + u0);
-    l += h * (ihy * (muPy - mu0) * h * (vMxPy + vPy) + ihy * (mu0 - muMy) * h * (vMx + v0));
-    l += h * (ihz * (muPz - mu0) * h * (wMxPz + wPz) + ihz * (mu0 - muMz) * h * (wMx + w0));
-    l += h * (ihx * (mvPy - mvMxPy) * h * (vMxPy + vPy) + ihx * (mv0 - mvMx) * h * (vMx + v0));
-    l += h * (ihx * (mwPz - mwMxPz) * h * (wMxPz + wPz) + ihx * (mw0 - mwMx) * h * (wMx + w0));
-    l += nu * ((muPx - T(2) * mu0 + muMx) * ihx * ihx + (muPy - T(2) * mu0 + muMy) * ihy * ihy +
-               (muPz - T(2) * mu0 + muMz) * ihz * ihz);
-    GA.out[0][p] = mu0 + GA.scale * l;
+  T o0 = n.mu0 + GA.scale * lu, o1 = n.mv0 + GA.scale * lv, o2 = n.mw0 + GA.scale * lw;
+  if (GA.add[0]) {
+    o0 += GA.add[0][p];
+    o1 += GA.add[1][p];
+    o2 += GA.add[2][p];
   }
-  {  // lambda_v
-    const T vMy = v(0, -1, 0);
-    const T uPxMy = u(1, -1, 0), uMy = u(0, -1, 0), wMyPz = w(0, -1, 1), wMy = w(0, -1, 0);
-    const T mvMy = mv(0, -1, 0), mvPx = mv(1, 0, 0), mvMx = mv(-1, 0, 0), mvPz = mv(0, 0, 1), mvMz = mv(0, 0, -1);
-    const T muPxMy = mu(1, -1, 0), muMy = mu(0, -1, 0), mwMyPz = mw(0, -1, 1), mwMy = mw(0, -1, 0);
-    T l = ihy * (mvPy - mv0) * h * (v0 + vPy) + ihy * (mv0 - mvMy) * h * (vMy + v0);
-    l += h * (ihx * (mvPx - mv0) * h * (uPxMy + uPx) + ihx * (mv0 - mvMx) * h * (uMy + u0));
-    l += h * (ihz * (mvPz - mv0) * h * (wMyPz + wPz) + ihz * (mv0 - mvMz) * h * (wMy + w0));
-    l += h * (ihy * (muPx - muPxMy) * h * (uPxMy + uPx) + ihy * (mu0 - muMy) * h * (uMy + u0));
-    l += h * (ihy * (mwPz - mwMyPz) * h * (wMyPz + wPz) + ihy * (mw0 - mwMy) * h * (wMy + w0));
-    l += nu * ((mvPx - T(2) * mv0 + mvMx) * ihx * ihx + (mvPy - T(2) * mv0 + mvMy) * ihy * ihy +
-               (mvPz - T(2) * mv0 + mvMz) * ihz * ihz);
-    GA.out[1][p] = mv0 + GA.scale * l;
+  GA.out[0][p] = o0;
+  GA.out[1][p] = o1;
+  GA.out[2][p] = o2;
+}
+
+// Four cells per thread along x (FP32, n_x % 4 == 0, 16-byte aligned fields): the
+// rows of the 30 neighbour segments are read as float4 vectors plus the x
+// neighbours they need, then the per-cell gather above.
+__device__ __forceinline__ void ld4s(const float* __restrict__ row, int i0, int nx, float* s, bool lo, bool hi) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(row + i0));
+  s[1] = a.x; s[2] = a.y; s[3] = a.z; s[4] = a.w;
+  s[0] = lo ? __ldg(row + (i0 > 0 ? i0 - 1 : nx - 1)) : 0.f;
+  s[5] = hi ? __ldg(row + (i0 + 4 < nx ? i0 + 4 : 0)) : 0.f;
+}
+
+__global__ void __launch_bounds__(kT, 2) rhs_adjoint_gather4_kernel(const GatherAdjArgs<float> GA) {
+  const RhsAdjArgs<float>& A = GA.r;
+  const Geom<float>& g = A.g;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i0 >= nx || j >= ny) return;
+  const int jm = j > 0 ? j - 1 : ny - 1, jp = j < ny - 1 ? j + 1 : 0;
+  const int km = k > 0 ? k - 1 : nz - 1, kp = k < nz - 1 ? k + 1 : 0;
+  auto row = [&](const float* f, int jj, int kk) { return f + (size_t)nx * (jj + (size_t)ny * kk); };
+  const float *U = A.u[0], *V = A.u[1], *W = A.u[2], *MU = A.mu[0], *MV = A.mu[1], *MW = A.mu[2];
+  float u00[6], um0[6], u0m[6];
+  float v00[6], vp0[6], vm0[6], v0m[6], vpm[6];
+  float w00[6], w0p[6], wm0[6], wmp[6], w0m[6];
+  float mu00[6], mup0[6], mum0[6], mu0p[6], mu0m[6];
+  float mv00[6], mvp0[6], mvm0[6], mv0p[6], mv0m[6], mvpm[6];
+  float mw00[6], mw0p[6], mwp0[6], mwmp[6], mwm0[6], mw0m[6];
+  ld4s(row(U, j, k), i0, nx, u00, true, true);
+  ld4s(row(U, jm, k), i0, nx, um0, false, true);
+  ld4s(row(U, j, km), i0, nx, u0m, false, true);
+  ld4s(row(V, j, k), i0, nx, v00, true, false);
+  ld4s(row(V, jp, k), i0, nx, vp0, true, false);
+  ld4s(row(V, jm, k), i0, nx, vm0, false, false);
+  ld4s(row(V, j, km), i0, nx, v0m, false, false);
+  ld4s(row(V, jp, km), i0, nx, vpm, false, false);
+  ld4s(row(W, j, k), i0, nx, w00, true, false);
+  ld4s(row(W, j, kp), i0, nx, w0p, true, false);
+  ld4s(row(W, jm, k), i0, nx, wm0, false, false);
+  ld4s(row(W, jm, kp), i0, nx, wmp, false, false);
+  ld4s(row(W, j, km), i0, nx, w0m, false, false);
+  ld4s(row(MU, j, k), i0, nx, mu00, true, true);
+  ld4s(row(MU, jp, k), i0, nx, mup0, false, false);
+  ld4s(row(MU, jm, k), i0, nx, mum0, false, true);
+  ld4s(row(MU, j, kp), i0, nx, mu0p, false, false);
+  ld4s(row(MU, j, km), i0, nx, mu0m, false, true);
+  ld4s(row(MV, j, k), i0, nx, mv00, true, true);
+  ld4s(row(MV, jp, k), i0, nx, mvp0, true, false);
+  ld4s(row(MV, jm, k), i0, nx, mvm0, false, false);
+  ld4s(row(MV, j, kp), i0, nx, mv0p, false, false);
+  ld4s(row(MV, j, km), i0, nx, mv0m, false, false);
+  ld4s(row(MV, jp, km), i0, nx, mvpm, false, false);
+  ld4s(row(MW, j, k), i0, nx, mw00, true, true);
+  ld4s(row(MW, j, kp), i0, nx, mw0p, true, false);
+  ld4s(row(MW, jp, k), i0, nx, mwp0, false, false);
+  ld4s(row(MW, jm, kp), i0, nx, mwmp, false, false);
+  ld4s(row(MW, jm, k), i0, nx, mwm0, false, false);
+  ld4s(row(MW, j, km), i0, nx, mw0m, false, false);
+  float o[3][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const int c = e + 1;
+    AdjNb<float> n;
+    n.u0 = u00[c]; n.uPx = u00[c + 1]; n.uMx = u00[c - 1]; n.uMy = um0[c]; n.uPxMy = um0[c + 1];
+    n.uMz = u0m[c]; n.uPxMz = u0m[c + 1];
+    n.v0 = v00[c]; n.vPy = vp0[c]; n.vMx = v00[c - 1]; n.vMxPy = vp0[c - 1]; n.vMy = vm0[c]; n.vMz = v0m[c];
+    n.vPyMz = vpm[c];
+    n.w0 = w00[c]; n.wPz = w0p[c]; n.wMx = w00[c - 1]; n.wMxPz = w0p[c - 1]; n.wMy = wm0[c]; n.wMyPz = wmp[c];
+    n.wMz = w0m[c];
+    n.mu0 = mu00[c]; n.muPx = mu00[c + 1]; n.muMx = mu00[c - 1]; n.muPy = mup0[c]; n.muMy = mum0[c];
+    n.muPz = mu0p[c]; n.muMz = mu0m[c]; n.muPxMy = mum0[c + 1]; n.muPxMz = mu0m[c + 1];
+    n.mv0 = mv00[c]; n.mvPy = mvp0[c]; n.mvPx = mv00[c + 1]; n.mvMx = mv00[c - 1]; n.mvMxPy = mvp0[c - 1];
+    n.mvMy = mvm0[c]; n.mvPz = mv0p[c]; n.mvMz = mv0m[c]; n.mvPyMz = mvpm[c];
+    n.mw0 = mw00[c]; n.mwPz = mw0p[c]; n.mwPx = mw00[c + 1]; n.mwMx = mw00[c - 1]; n.mwMxPz = mw0p[c - 1];
+    n.mwPy = mwp0[c]; n.mwMy = mwm0[c]; n.mwMyPz = mwmp[c]; n.mwMz = mw0m[c];
+    float lu, lv, lw;
+    gather_adj_cell(n, g.ihx, g.ihy[0], g.ihz, g.nu, lu, lv, lw);
+    o[0][e] = n.mu0 + GA.scale * lu;
+    o[1][e] = n.mv0 + GA.scale * lv;
+    o[2][e] = n.mw0 + GA.scale * lw;
   }
-  {  // lambda_w
-    const T wMz = w(0, 0, -1);
-    const T uPxMz = u(1, 0, -1), uMz = u(0, 0, -1), vPyMz = v(0, 1, -1), vMz = v(0, 0, -1);
-    const T mwMz = mw(0, 0, -1), mwPx = mw(1, 0, 0), mwMx = mw(-1, 0, 0), mwPy = mw(0, 1, 0), mwMy = mw(0, -1, 0);
-    const T muPxMz = mu(1, 0, -1), muMz = mu(0, 0, -1), mvPyMz = mv(0, 1, -1), mvMz = mv(0, 0, -1);
-    T l = ihz * (mwPz - mw0) * h * (w0 + wPz) + ihz * (mw0 - mwMz) * h * (wMz + w0);
-    l += h * (ihx * (mwPx - mw0) * h * (uPxMz + uPx) + ihx * (mw0 - mwMx) * h * (uMz + u0));
-    l += h * (ihy * (mwPy - mw0) * h * (vPyMz + vPy) + ihy * (mw0 - mwMy) * h * (vMz + v0));
-    l += h * (ihz * (muPx - muPxMz) * h * (uPxMz + uPx) + ihz * (mu0 - muMz) * h * (uMz + u0));
-    l += h * (ihz * (mvPy - mvPyMz) * h * (vPyMz + vPy) + ihz * (mv0 - mvMz) * h * (vMz + v0));
-    l += nu * ((mwPx - T(2) * mw0 + mwMx) * ihx * ihx + (mwPy - T(2) * mw0 + mwMy) * ihy * ihy +
-               (mwPz - T(2) * mw0 + mwMz) * ihz * ihz);
-    GA.out[2][p] = mw0 + GA.scale * l;
+  const size_t p = (size_t)nx * (j + (size_t)ny * k) + i0;
+  if (GA.add[0]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(GA.add[c] + p));
+      o[c][0] += a.x;
+      o[c][1] += a.y;
+      o[c][2] += a.z;
+      o[c][3] += a.w;
+    }
   }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) *reinterpret_cast<float4*>(GA.out[c] + p) = make_float4(o[c][0], o[c][1], o[c][2], o[c][3]);
 }
 
 // x = -(G^T lam) / V at every cell: the right-hand side of the adjoint Poisson solve.
@@ -845,7 +958,8 @@ void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double 
 
 // out = src + R'(u)^T (scale src) on a fully periodic grid (gather transpose).
 template <typename T>
-void launch_rhs_adjoint_gather(fs_grid* G, T* const* u, T* const* src, double scale, T* const* out) {
+void launch_rhs_adjoint_gather(fs_grid* G, T* const* u, T* const* src, double scale, T* const* out,
+                               T* const* add = nullptr) {
   GatherAdjArgs<T> A;
   A.r.g = G->geom<T>();
   for (int c = 0; c < 3; ++c) {
@@ -853,11 +967,23 @@ void launch_rhs_adjoint_gather(fs_grid* G, T* const* u, T* const* src, double sc
     A.r.mu[c] = src[c];
     A.r.lam[c] = nullptr;
     A.out[c] = out[c];
+    A.add[c] = add ? add[c] : nullptr;
   }
   A.r.conv = G->conv;
   A.r.X = G->nx;
   A.r.Y = G->ny;
   A.scale = (T)scale;
+  if constexpr (std::is_same<T, float>::value) {
+    bool vec = G->nx % 4 == 0;
+    for (int c = 0; c < 3; ++c)
+      vec = vec && (uintptr_t)u[c] % 16 == 0 && (uintptr_t)src[c] % 16 == 0 && (uintptr_t)out[c] % 16 == 0 &&
+          (!add || (uintptr_t)add[c] % 16 == 0);
+    if (vec) {
+      const dim3 vb(32, 8), vg((G->nx / 4 + 31) / 32, (G->ny + 7) / 8, G->nz);
+      FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_gather4_kernel<<<vg, vb, 0, G->stream>>>(A));
+      return;
+    }
+  }
   const dim3 blk = stencil_block(G), grd = stencil_grid(G, G->nx, G->ny);
   FS_LAUNCH(G, "rhs_adjoint", rhs_adjoint_gather_kernel<T><<<grd, blk, 0, G->stream>>>(A));
 }
@@ -969,14 +1095,10 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
     const bool fast = gather_fast(G) && proj_adj_fast<T>(G, L, la, ln);
     if (fast) {
       // lam of v_s = b lam~ + R'(v_s)^T (b dt lam~), written straight into lam->u
+      // (the last stage's gather also adds the stage accumulator: lam^n = lam of v_0 + lam_acc)
       for (int s = 2; s >= 0; --s) {
         launch_proj_adj_fast<T>(G, L, Ac[s], Bc[s], dt, true, bfsum, la, ln);
-        launch_rhs_adjoint_gather<T>(G, vs[s], ln, dt, L);
-      }
-      for (int c = 0; c < dim; ++c) {
-        const long long n = (long long)comp_count(G, c);
-        FS_LAUNCH(G, "axpy", axpy_kernel<T><<<(int)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0,
-                                            G->stream>>>(L[c], la[c], n));
+        launch_rhs_adjoint_gather<T>(G, vs[s], ln, dt, L, s == 0 ? la : nullptr);
       }
       return cuda_check(cudaGetLastError(), "fs_step_adjoint (RK3)");
     }
