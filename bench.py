@@ -50,13 +50,13 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on: a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50362880 + 851712, "src": "220d445780dc"},
-    "fft_x_fwd_div": {"bytes": 25243904 + 0, "src": "4b64e2a187d4"},
-    "fft_z_fwd": {"bytes": 8407040, "src": "4b64e2a187d4"},
-    "fft_y_solve": {"bytes": 8434688, "src": "4b64e2a187d4"},
-    "fft_z_inv": {"bytes": 8410624, "src": "4b64e2a187d4"},
-    "fft_x_inv": {"bytes": 8414464, "src": "4b64e2a187d4"},
-    "correct": {"bytes": 33560576 + 512, "src": "220d445780dc"},
+    "predictor": {"bytes": 50366208 + 860416, "src": "5ae02b068f73"},
+    "fft_x_fwd_div": {"bytes": 25243904 + 0, "src": "f9fff980db2d"},
+    "fft_z_fwd": {"bytes": 8406784, "src": "f9fff980db2d"},
+    "fft_y_solve": {"bytes": 8443648, "src": "f9fff980db2d"},
+    "fft_z_inv": {"bytes": 8410624, "src": "f9fff980db2d"},
+    "fft_x_inv": {"bytes": 8414976, "src": "f9fff980db2d"},
+    "correct": {"bytes": 33560064 + 5632, "src": "5ae02b068f73"},
 }
 
 

@@ -1,12 +1,14 @@
 """Summarise an ncu --csv launch list (gpu__time_duration.sum per launch) by kernel:
-launches, total time and share.  Usage: python launch_summary.py launches.csv"""
+launches, total time and share.  Usage: python launch_summary.py launches.csv [--exclude name,...]
+(excluded kernels, e.g. the benchmark's L2 flush fill and its timed spin, are left out of
+the shares)."""
 import collections
 import csv
 import re
 import sys
 
 
-def summarise(path):
+def summarise(path, exclude=()):
     rows = list(csv.reader(open(path)))
     start = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
     hdr = rows[start]
@@ -18,6 +20,8 @@ def summarise(path):
             continue
         name = re.sub(r"^void ", "", r[ki].split("(")[0])
         name = re.sub(r"<.*", "", name.replace("<unnamed>", "anon")).split("::")[-1]
+        if name in exclude:
+            continue
         v = float(r[mi].replace(",", "")) * scale.get(r[ui], 1.0)
         a = agg.setdefault(name, [0, 0.0])
         a[0] += 1
@@ -30,4 +34,7 @@ def summarise(path):
 
 
 if __name__ == "__main__":
-    print(summarise(sys.argv[1]))
+    ex = ()
+    if "--exclude" in sys.argv:
+        ex = tuple(sys.argv[sys.argv.index("--exclude") + 1].split(","))
+    print(summarise(sys.argv[1], ex))
