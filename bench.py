@@ -245,7 +245,7 @@ def ensemble_leg(args, flush):
     from paper_2505_23940_b300.ensemble import Ensemble
     os.environ.setdefault("FS_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "fsstep_tuning_bench.json"))
     wls = S.ensemble_cylinders(members=args.ensemble, seed=2, precision="mixed")
-    ens = Ensemble(wls, "mixed", streams=16, tune=True)
+    ens = Ensemble(wls, "mixed", streams=32, tune=True)
     cells = ens.cells()
     k = args.steps
     snap = ens.snapshot()
@@ -263,6 +263,8 @@ def ensemble_leg(args, flush):
     ens.restore(snap)
     ens.capture(k)
     ens.restore(snap)
+    ens.replay()   # the first replay uploads the graph: untimed, like any reused graph's
+    ens.restore(snap)
     torch.cuda.synchronize()
     flush.fill_(4)
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -277,8 +279,9 @@ def ensemble_leg(args, flush):
                       "launches": 1},
             "one_by_one": {"value": cells * k / (seq_ms * 1e-3), "unit": "cell-updates/s", "ms": seq_ms},
             "speedup": seq_ms / g_ms,
-            "note": "every member advanced by K steps; graph = one CUDA-graph launch with members on 16 "
-                    "parallel branches; launch parameters autotuned per grid size"}
+            "note": "every member advanced by K steps; graph = one CUDA-graph launch (after one untimed "
+                    "upload replay) with members on 32 parallel branches; launch parameters autotuned per "
+                    "grid size"}
 
 
 def run_ours(args, ws, rank, local):

@@ -28,7 +28,7 @@ class Member:
 
 
 class Ensemble:
-    def __init__(self, workloads, precision="mixed", streams=8, tune=False):
+    def __init__(self, workloads, precision="mixed", streams=32, tune=False):
         self.members = [Member(wl, precision) for wl in workloads]
         self.nstreams = max(1, int(streams))
         self.graph = None
