@@ -443,19 +443,22 @@ __device__ __forceinline__ void predict_cell_general(const PredArgs<T>& A, int i
 }
 
 // The rows of a wall-bounded grid whose stencil reaches a wall (j = 0, 1, ny - 1,
-// ny): one cell per thread through the general path, launched beside the vector
+// ny): one face per thread through the general path, launched beside the vector
 // kernels, which then cover rows 2 .. ny - 2 only (a wall row inside a z-marching
 // block would hold the whole block to the general path's pace).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) predictor_wall_rows_kernel(const PredArgs<T> A) {
+__global__ void __launch_bounds__(64) predictor_wall_rows_kernel(const PredArgs<T> A) {
   pdl_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int r = blockIdx.y;   // 0, 1, 2, 3 -> j = 0, 1, ny - 1, ny
+  const int r = blockIdx.y / 3, c = blockIdx.y - 3 * r;   // row 0, 1, 2, 3 -> j = 0, 1, ny - 1, ny; component
   const int k = blockIdx.z;
   const int ny = A.g.ny;
   const int j = r < 2 ? r : ny - 3 + r;
   if (i >= A.X || j >= A.Y) return;
-  predict_cell_general(A, i, j, k);
+  const AccGhost<T> U{&A.g, A.uin, i, j, k};   // one face per thread
+  if (c == 0) predict_face<T, 0>(A, U, i, j, k);
+  else if (c == 1) predict_face<T, 1>(A, U, i, j, k);
+  else predict_face<T, 2>(A, U, i, j, k);
 }
 
 // The predictor for the common 3-D case -- x and z periodic, central
@@ -1321,8 +1324,8 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
       if (vec && !G->per[1] && G->ny >= 5) {
         A.jlo = 2;
         rows = G->ny - 3;
-        launch_pdl(G, "predictor_walls", predictor_wall_rows_kernel<T>, dim3((A.X + kThreads - 1) / kThreads, 4, G->nz),
-                   dim3(kThreads), 0, A);
+        launch_pdl(G, "predictor_walls", predictor_wall_rows_kernel<T>, dim3((A.X + 63) / 64, 12, G->nz), dim3(64), 0,
+                   A);
       }
       if (vec && vw == 4 && KZ > 1) {
         const dim3 vb(32, 8);
