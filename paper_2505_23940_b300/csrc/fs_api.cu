@@ -255,6 +255,25 @@ int build_tables(fs_grid* G) {
         for (int q = 0; q < NRED; ++q) MI[(size_t)(r * NRED + q) * nlam + li] = M[r][NRED + q];
     }
   }
+  // grids with too few 32-column blocks to fill the SMs solve in 8-column blocks that copy their
+  // columns' tables into shared memory: those tables are stored eigenvalue-major, one contiguous
+  // (padded) column per eigenvalue index
+  const long blocks32 = (long)((nx + 31) / 32) * (G->dim == 3 ? nz : 1);
+  G->ypitch = ny + (ny & 1);
+  G->ynarrow = blocks32 < 148 && ysolve_smem(ny, NSEG, 8) <= 200 * 1024;
+  if (G->ynarrow) {
+    auto transpose = [&](const std::vector<double>& t) {
+      std::vector<double> o((size_t)nlam * G->ypitch, 0.0);
+      for (int j = 0; j < ny; ++j)
+        for (int l = 0; l < nlam; ++l) o[(size_t)l * G->ypitch + j] = t[(size_t)j * nlam + l];
+      return o;
+    };
+    E = transpose(E);
+    CP = transpose(CP);
+    V = transpose(V);
+    W = transpose(W);
+    acoef.resize(G->ypitch, 0.0);
+  }
   if (upload(&G->ya, acoef) != cudaSuccess || upload(&G->tE, E) != cudaSuccess || upload(&G->tCP, CP) != cudaSuccess ||
       upload(&G->tZV, V) != cudaSuccess || upload(&G->tWV, W) != cudaSuccess || upload(&G->tMI, MI) != cudaSuccess)
     return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");

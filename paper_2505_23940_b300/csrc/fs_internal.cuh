@@ -292,6 +292,8 @@ struct fs_grid {
   double *tZV = nullptr, *tWV = nullptr;  // [ny][nlz][nmx] right / left spikes of each segment
   double *tMI = nullptr;                  // [4 ynseg^2][nlz][nmx] inverse of the 2 ynseg interface system
   int ynseg = 4;                          // segments per column of the partitioned y solve (4, 8 or 16)
+  int ynarrow = 0;                        // 1: 8-column blocks; tE, tCP, tZV, tWV are then [nlam][ypitch]
+  int ypitch = 0;                         // row count of the eigenvalue-major tables (ny rounded up to even)
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
   int tune_ynseg = 0;
   bool tune_staged = true;                // shared-memory staged predictor where it applies                     // requested segment count (0: chosen from the grid's shape)
@@ -359,6 +361,8 @@ template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state*
                                        fs_param_grad* pg, double dt, void* const* rv1 = nullptr,
                                        void* const* rv2 = nullptr);
 void free_adj_buffers(void* p);
+// poisson.cu
+size_t ysolve_smem(int ny, int nseg, int yc);
 // errors
 int set_error(int code, const std::string& msg);
 int cuda_check(cudaError_t e, const char* what);

@@ -25,6 +25,7 @@
 #include <cmath>
 
 #include "fs_internal.cuh"
+#include "tma.cuh"
 
 namespace fs {
 
@@ -536,6 +537,8 @@ struct YArgs {
   const double* MI;      // inverse interface matrices [NRED * NRED][nlam]
   const double* hy;      // cell widths (zero-mode mean)
   double hysum;          // sum of the cell widths
+  int pitch;             // 8-column blocks: E, CP, ZV, WV are [nlam][pitch] (eigenvalue-major)
+  unsigned* status;      // device status word (bit 0: a staged copy wait gave up)
 };
 
 __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
@@ -563,22 +566,27 @@ __device__ __forceinline__ int lam_index(const YArgs& A, int s, int t) {
 //   3. x_j = y_j - v_j X_{p+1} - w_j Y_{p-1} on every row.
 // The singular zero mode pins x_0 = 0 (e_0 = 0 in its table) and is shifted to
 // zero hy-weighted mean afterwards.
-constexpr int YCOLS = 32;
+constexpr int YCOLS = 32;   // columns per block (8, with staged tables, on grids with few columns)
 
-template <typename T, int NSEG>
-__global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ data, const YArgs A) {
+// YC = 8 (grids with few columns) also stages the block's table columns and the
+// couplings a_j in shared memory, so that the sequential sweeps wait on shared
+// rather than global loads.
+template <typename T, int NSEG, int YC>
+__global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data, const YArgs A) {
   constexpr int NRED = 2 * NSEG;
-  extern __shared__ double sm[];
+  constexpr bool STG = YC == 8;
+  extern __shared__ __align__(16) double sm[];
   const int ny = A.ny;
-  double* D = sm;                                  // [ny][YCOLS] data tile, then y, then x
-  double* Z = D + (size_t)ny * YCOLS;              // [YCOLS][NRED] interface values
-  double* R = Z + YCOLS * NRED;                    // [YCOLS][NSEG] mean partial sums
+  double* D = sm;                                  // [ny][YC] data tile, then y, then x
+  double* Z = D + (size_t)ny * YC;              // [YC][NRED] interface values
+  double* R = Z + YC * NRED;                    // [YC][NSEG] mean partial sums
+  double* ST = R + YC * NSEG;                   // STG: [4 tables][YC][ny + 1], then a_j [ny]
   const int tx = threadIdx.x, p = threadIdx.y;
-  const int tid = tx + YCOLS * p;
-  const int s0 = blockIdx.x * YCOLS;
+  const int tid = tx + YC * p;
+  const int s0 = blockIdx.x * YC;
   const int t = blockIdx.y;
   const int s = s0 + tx;
-  const int ncol = min(YCOLS, A.nx - s0);
+  const int ncol = min(YC, A.nx - s0);
   const int nlam = A.nmx * A.nlz;
   T* tile = data + s0 + (size_t)A.nx * A.ny * t;
   const size_t rs = (size_t)A.nx;
@@ -586,17 +594,36 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   // form of large 3-D grids runs faster with the plain loop)
   if constexpr (NSEG >= 8) {
 #pragma unroll 8
-    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-      const int j = e / YCOLS, c = e - j * YCOLS;
+    for (int e = tid; e < ny * YC; e += YC * NSEG) {
+      const int j = e / YC, c = e - j * YC;
       D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
     }
   } else {
-    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-      const int j = e / YCOLS, c = e - j * YCOLS;
+    for (int e = tid; e < ny * YC; e += YC * NSEG) {
+      const int j = e / YC, c = e - j * YC;
       D[e] = c < ncol ? (double)tile[rs * j + c] : 0.0;
     }
   }
+  // STG: the block's 8 table columns and a_j land in shared memory by bulk copies while the tile loads
+  const int sp = A.pitch + 2;   // padded slot pitch (16-byte multiple, odd in 16-byte units)
+  __shared__ uint64_t tbar;
+  bool tok = true;
+  if constexpr (STG) {
+    if (tid == 0) {
+      mbar_init(&tbar, 1);
+      mbar_init_fence();
+      const uint32_t col = (uint32_t)A.pitch * sizeof(double);
+      mbar_expect_tx(&tbar, (4 * YC + 1) * col);
+      const double* tabs[4] = {A.E, A.CP, A.ZV, A.WV};
+      for (int c = 0; c < YC; ++c) {
+        const int lc = s0 + c < A.nx ? lam_index(A, s0 + c, t) : 0;
+        for (int q = 0; q < 4; ++q) bulk_g2s(ST + (q * YC + c) * sp, tabs[q] + (size_t)lc * A.pitch, col, &tbar);
+      }
+      bulk_g2s(ST + 4 * YC * sp, A.a, col, &tbar);
+    }
+  }
   __syncthreads();
+  if constexpr (STG) tok = mbar_wait(&tbar, 0);
   const bool act = s < A.nx;
   const int li = act ? lam_index(A, s, t) : 0;
   const int r0 = (p * ny) / NSEG, r1 = ((p + 1) * ny) / NSEG;
@@ -604,6 +631,27 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
   const double* CP = A.CP + li;
   const double* V = A.ZV + li;    // right spikes
   const double* W = A.WV + li;    // left spikes
+  // table entries of this thread's column (shared-memory copies when staged)
+  auto fE = [&](int j) -> double {
+    if constexpr (STG) return ST[(0 * YC + tx) * sp + j];
+    else return __ldg(E + (size_t)j * nlam);
+  };
+  auto fCP = [&](int j) -> double {
+    if constexpr (STG) return ST[(1 * YC + tx) * sp + j];
+    else return __ldg(CP + (size_t)j * nlam);
+  };
+  auto fV = [&](int j) -> double {
+    if constexpr (STG) return ST[(2 * YC + tx) * sp + j];
+    else return __ldg(V + (size_t)j * nlam);
+  };
+  auto fW = [&](int j) -> double {
+    if constexpr (STG) return ST[(3 * YC + tx) * sp + j];
+    else return __ldg(W + (size_t)j * nlam);
+  };
+  auto fa = [&](int j) -> double {
+    if constexpr (STG) return ST[4 * YC * sp + j];
+    else return __ldg(A.a + j);
+  };
   double* col = D + tx;
   constexpr int U = 8;            // table rows fetched ahead of their use
   if (act && r1 > r0) {
@@ -614,36 +662,36 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
       double e[U], a[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        e[q] = __ldg(E + (size_t)(j + q) * nlam);
-        a[q] = __ldg(A.a + j + q);
+        e[q] = fE(j + q);
+        a[q] = fa(j + q);
       }
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        const double d = col[(j + q) * YCOLS];
+        const double d = col[(j + q) * YC];
         prev = (j + q == r0) ? d * e[q] : (d - a[q] * prev) * e[q];
-        col[(j + q) * YCOLS] = prev;
+        col[(j + q) * YC] = prev;
       }
     }
     for (; j < r1; ++j) {
-      const double d = col[j * YCOLS];
-      prev = (j == r0) ? d * __ldg(E + (size_t)j * nlam) : (d - __ldg(A.a + j) * prev) * __ldg(E + (size_t)j * nlam);
-      col[j * YCOLS] = prev;
+      const double d = col[j * YC];
+      prev = (j == r0) ? d * fE(j) : (d - fa(j) * prev) * fE(j);
+      col[j * YC] = prev;
     }
     double x = prev;
     j = r1 - 2;
     for (; j - U + 1 >= r0; j -= U) {
       double c[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) c[q] = __ldg(CP + (size_t)(j - q) * nlam);
+      for (int q = 0; q < U; ++q) c[q] = fCP(j - q);
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        x = col[(j - q) * YCOLS] - c[q] * x;
-        col[(j - q) * YCOLS] = x;
+        x = col[(j - q) * YC] - c[q] * x;
+        col[(j - q) * YC] = x;
       }
     }
     for (; j >= r0; --j) {
-      x = col[j * YCOLS] - __ldg(CP + (size_t)j * nlam) * x;
-      col[j * YCOLS] = x;
+      x = col[j * YC] - fCP(j) * x;
+      col[j * YC] = x;
     }
   }
   __syncthreads();
@@ -653,8 +701,8 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
 #pragma unroll
     for (int g = 0; g < NSEG; ++g) {
       const int a0 = (g * ny) / NSEG, a1 = ((g + 1) * ny) / NSEG;
-      b[2 * g] = a1 > a0 ? col[a0 * YCOLS] : 0.0;
-      b[2 * g + 1] = a1 > a0 ? col[(a1 - 1) * YCOLS] : 0.0;
+      b[2 * g] = a1 > a0 ? col[a0 * YC] : 0.0;
+      b[2 * g + 1] = a1 > a0 ? col[(a1 - 1) * YC] : 0.0;
     }
     double* z = Z + tx * NRED;
 #pragma unroll
@@ -676,8 +724,8 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     const double Xn = (p + 1 < NSEG || cyc) ? z[2 * gn] : 0.0;
     const double Yp = (p > 0 || cyc) ? z[2 * gp + 1] : 0.0;
     for (int j = r0; j < r1; ++j) {
-      const double r = col[j * YCOLS] - __ldg(V + (size_t)j * nlam) * Xn - __ldg(W + (size_t)j * nlam) * Yp;
-      col[j * YCOLS] = r;
+      const double r = col[j * YC] - fV(j) * Xn - fW(j) * Yp;
+      col[j * YC] = r;
       if (li == 0) part += r * __ldg(A.hy + j);
     }
   }
@@ -688,21 +736,22 @@ __global__ void __launch_bounds__(YCOLS * NSEG) ysolve_kernel(T* __restrict__ da
     double sx = 0.0;
     for (int g = 0; g < NSEG; ++g) sx += R[tx * NSEG + g];
     const double mean = sx / A.hysum;
-    for (int j = r0; j < r1; ++j) col[j * YCOLS] -= mean;
+    for (int j = r0; j < r1; ++j) col[j * YC] -= mean;
   }
   __syncthreads();
   if constexpr (NSEG >= 8) {
 #pragma unroll 8
-    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-      const int j = e / YCOLS, c = e - j * YCOLS;
+    for (int e = tid; e < ny * YC; e += YC * NSEG) {
+      const int j = e / YC, c = e - j * YC;
       if (c < ncol) tile[rs * j + c] = (T)D[e];
     }
   } else {
-    for (int e = tid; e < ny * YCOLS; e += YCOLS * NSEG) {
-      const int j = e / YCOLS, c = e - j * YCOLS;
+    for (int e = tid; e < ny * YC; e += YC * NSEG) {
+      const int j = e / YC, c = e - j * YC;
       if (c < ncol) tile[rs * j + c] = (T)D[e];
     }
   }
+  if (!tok) atomicOr(A.status, 1u);   // the staged tables never arrived: this block's columns are invalid
 }
 
 // ---------------------------------------------------------------------------
@@ -1008,17 +1057,22 @@ void set_smem_attrs() {
   set_smem_attrs_plan<T, 480>();
   set_smem_attrs_plan<T, 512>();
   set_smem_attrs_plan<T, 640>();
-  cudaFuncSetAttribute(ysolve_kernel<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaFuncSetAttribute(ysolve_kernel<T, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-  cudaFuncSetAttribute(ysolve_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 4, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 8, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 16, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ysolve_kernel<T, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   done = true;
 }
 
 
 }  // namespace
 
-size_t ysolve_smem(int ny, int nseg) {
-  return ((size_t)ny * YCOLS + (size_t)YCOLS * 3 * nseg) * sizeof(double);
+size_t ysolve_smem(int ny, int nseg, int yc) {
+  const size_t pitch = ny + (ny & 1);
+  const size_t staged = yc == 8 ? (size_t)(4 * yc + 1) * (pitch + 2) : 0;
+  return ((size_t)ny * yc + (size_t)yc * 3 * nseg + staged) * sizeof(double);
 }
 
 template <typename T>
@@ -1108,15 +1162,24 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.MI = G->tMI;
     A.hy = G->hy64;
     A.hysum = G->hysum;
-    dim3 grid((nx + YCOLS - 1) / YCOLS, G->dim == 3 ? nz : 1);
+    A.pitch = G->ypitch;
+    A.status = G->dstatus;
+    // narrow blocks with staged tables when 32-column blocks would leave SMs idle
+    const int tz = G->dim == 3 ? nz : 1;
+    const int yc = G->ynarrow ? 8 : YCOLS;
+    const dim3 grid((nx + yc - 1) / yc, tz);
     const int ns = G->ynseg;
-    const size_t sb = ysolve_smem(ny, ns);
-    if (ns == 16) {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16><<<grid, dim3(YCOLS, 16), sb, G->stream>>>(data, A));
+    const size_t sb = ysolve_smem(ny, ns, yc);
+    if (yc == 8) {
+      if (ns == 16) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, 8><<<grid, dim3(8, 16), sb, G->stream>>>(data, A));
+      else if (ns == 8) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, 8><<<grid, dim3(8, 8), sb, G->stream>>>(data, A));
+      else FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, 8><<<grid, dim3(8, 4), sb, G->stream>>>(data, A));
+    } else if (ns == 16) {
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, YCOLS><<<grid, dim3(YCOLS, 16), sb, G->stream>>>(data, A));
     } else if (ns == 8) {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8><<<grid, dim3(YCOLS, 8), sb, G->stream>>>(data, A));
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, YCOLS><<<grid, dim3(YCOLS, 8), sb, G->stream>>>(data, A));
     } else {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
+      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, YCOLS><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
     }
   }
   if (zreg) {
