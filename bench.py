@@ -48,26 +48,38 @@ KERNEL_BYTES_PER_CELL = {
 # workload (ncu flushes caches before each captured launch; writes still resident
 # in L2 at kernel end are not counted; the predictor launch is an RK3 stage 2 or 3,
 # which also reads u^n), keyed by kernel with the hash of the source files it was
-# measured on: a changed kernel reports traffic null until re-captured.
+# measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50366208 + 860416, "src": "5ae02b068f73"},
-    "fft_x_fwd_div": {"bytes": 25243904 + 0, "src": "f9fff980db2d"},
-    "fft_z_fwd": {"bytes": 8406784, "src": "f9fff980db2d"},
-    "fft_y_solve": {"bytes": 8443648, "src": "f9fff980db2d"},
-    "fft_z_inv": {"bytes": 8410624, "src": "f9fff980db2d"},
-    "fft_x_inv": {"bytes": 8414976, "src": "f9fff980db2d"},
-    "correct": {"bytes": 33560064 + 5632, "src": "5ae02b068f73"},
+    "predictor": {"bytes": 50367232 + 864768, "src": "8165a552c6a7"},
+    "fft_x_fwd_div": {"bytes": 25243392 + 0, "src": "7895d4f893d7"},
+    "fft_z_fwd": {"bytes": 8407040 + 0, "src": "7895d4f893d7"},
+    "fft_y_solve": {"bytes": 8435200 + 0, "src": "7895d4f893d7"},
+    "fft_z_inv": {"bytes": 8410880 + 0, "src": "7895d4f893d7"},
+    "fft_x_inv": {"bytes": 8414720 + 0, "src": "7895d4f893d7"},
+    "correct": {"bytes": 33560576 + 256, "src": "96276b6b63ca"},
+}
+
+
+# The source a kernel's captured traffic was measured on: the text of the kernel
+# (from a start marker to the end of its body) and the headers it builds on.
+KERNEL_SOURCES = {
+    "predictor": ("stencil.cu", "// Staged z-marching predictor", "if (!ok) atomicOr(status, 1u);", ["tma.cuh"]),
+    "correct": ("stencil.cu", "__global__ void __launch_bounds__(kThreads) correct4_kernel", "\n}\n", []),
+    "fft": ("fft_reg.cuh", "", "", []),
 }
 
 
 def src_hash(name):
-    files = {"predictor": ["stencil.cu"], "divergence": ["stencil.cu"], "correct": ["stencil.cu"],
-             "fft": ["poisson.cu", "fft_reg.cuh"], "ysolve": ["poisson.cu"]}
-    for key, fns in files.items():
+    for key, (fn, start, end, extra) in KERNEL_SOURCES.items():
         if name.startswith(key):
-            m = hashlib.sha1()
-            for fn in fns:
-                m.update(open(os.path.join(ROOT, "paper_2505_23940_b300", "csrc", fn), "rb").read())
+            csrc = os.path.join(ROOT, "paper_2505_23940_b300", "csrc")
+            text = open(os.path.join(csrc, fn)).read()
+            if start:
+                i = text.index(start)
+                text = text[i:text.index(end, i) + len(end)]
+            m = hashlib.sha1(text.encode())
+            for e in extra:
+                m.update(open(os.path.join(csrc, e), "rb").read())
             return m.hexdigest()[:12]
     return None
 
