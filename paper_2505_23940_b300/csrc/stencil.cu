@@ -793,8 +793,10 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3z_kernel(const PredArgs
 }
 
 // Staged z-marching predictor: fully periodic uniform FP32 grids with nx = NX
-// (128 or 256).  A block owns the whole x extent of BY = 1024 / NX rows
-// j0 .. j0+BY-1 and KZ consecutive planes.  One thread streams each plane's U,
+// (128 or 256).  A block works on the whole x extent of BY = 1024 / NX rows
+// j0 .. j0+BY-1 and a run of consecutive planes: the launch holds two blocks per
+// SM and gives each an equal share of the (row block, plane) units, a run split
+// where it crosses into the next row block.  One thread streams each plane's U,
 // V and W rows j0-1 .. j0+BY (periodic y halo) from global to shared memory with
 // bulk asynchronous copies into a ring of plane slots, up to four planes
 // ahead of the compute; a staged plane serves the iterations of its own plane
@@ -835,8 +837,7 @@ __device__ __forceinline__ void lds_seg(const float* row, int i0, float* s) {
 }
 
 template <int NX>
-__global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs<float> A, int KZ,
-                                                                   unsigned* status) {
+__global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs<float> A, unsigned* status) {
   using SG = StageGeo<NX>;
   extern __shared__ __align__(16) float stg[];
   constexpr int kStageRing = SG::RING;
@@ -845,23 +846,39 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs
   const Geom<float>& g = A.g;
   const int ny = g.ny, nz = g.nz;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int j0 = blockIdx.x * SG::BY;
-  const int k0 = blockIdx.y * KZ;
-  const int kz = min(KZ, nz - k0);   // planes computed
-  const int nplanes = kz + 2;        // planes staged: k0 - 1 .. k0 + kz
   const bool leader = tx == 0 && ty == 0;
   if (leader) {
     for (int s = 0; s < kStageRing; ++s) mbar_init(&bars[s], 1);
     mbar_init_fence();
   }
-  __syncthreads();
+  // the block's share of the (row block, plane) units, in row-block-major order: a
+  // contiguous run of planes, split where it crosses into the next row block
+  const int nyb = (ny + SG::BY - 1) / SG::BY;
+  const long long total = (long long)nyb * nz;
+  const int u0 = (int)(total * blockIdx.x / gridDim.x), u1 = (int)(total * (blockIdx.x + 1) / gridDim.x);
+  const int i0 = 4 * tx;
+  const int rm = ty * NX, r0 = (ty + 1) * NX, rp = (ty + 2) * NX;
+  const float a = A.a, b = A.b, dt = A.dt, nu = g.nu;
+  const float ihx = g.ihx, ihy = A.ihy0, ihz = g.ihz;
+  const float qx = 0.25f * ihx, qy = 0.25f * ihy, qz = 0.25f * ihz;
+  const float dx2 = ihx * ihx, dy2 = ihy * ihy, dz2 = ihz * ihz, d0 = -2.f * (dx2 + dy2 + dz2);
+  bool ok = true;
+  int base = 0;   // planes this block has staged so far: ring slot and phase of the next one
+  for (int u = u0; u < u1;) {
+  const int yb = u / nz;
+  const int k0 = u - yb * nz;
+  const int kz = min(nz - k0, u1 - u);   // planes computed in this run
+  u += kz;
+  const int j0 = yb * SG::BY;
+  const int nplanes = kz + 2;        // planes staged: k0 - 1 .. k0 + kz
+  __syncthreads();   // barriers initialised; every slot of the previous run consumed
   // slab row r holds y row (j0 - 1 + r) mod ny: at most two contiguous runs (ny >= RR)
   const int g0 = j0 == 0 ? ny - 1 : j0 - 1;
   const int run1 = min(SG::RR, ny - g0);
   auto issue = [&](int rel) {   // stage plane k0 - 1 + rel (leader only)
     int p = k0 - 1 + rel;
     p = p < 0 ? p + nz : (p >= nz ? p - nz : p);
-    const int s = rel % kStageRing;
+    const int s = (base + rel) % kStageRing;
     float* slot = stg + (size_t)s * SG::SLOT;
     mbar_expect_tx(&bars[s], SG::SLOT * sizeof(float));
     for (int f = 0; f < 3; ++f) {
@@ -873,24 +890,20 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs
   };
   if (leader)
     for (int rel = 0; rel < kStageRing - 1 && rel < nplanes; ++rel) issue(rel);
-  bool ok = true;
-  auto wait = [&](int rel) { ok = mbar_wait(&bars[rel % kStageRing], (rel / kStageRing) & 1) && ok; };
+  auto wait = [&](int rel) {
+    ok = mbar_wait(&bars[(base + rel) % kStageRing], ((base + rel) / kStageRing) & 1) && ok;
+  };
+  auto slotp = [&](int rel) { return stg + (size_t)((base + rel) % kStageRing) * SG::SLOT; };
   const int j = j0 + ty;
   const bool act = j < ny;
-  const int i0 = 4 * tx;
-  const int rm = ty * NX, r0 = (ty + 1) * NX, rp = (ty + 2) * NX;
-  const float a = A.a, b = A.b, dt = A.dt, nu = g.nu;
-  const float ihx = g.ihx, ihy = A.ihy0, ihz = g.ihz;
-  const float qx = 0.25f * ihx, qy = 0.25f * ihy, qz = 0.25f * ihz;
-  const float dx2 = ihx * ihx, dy2 = ihy * ihy, dz2 = ihz * ihz, d0 = -2.f * (dx2 + dy2 + dz2);
   const float bf = g.bforce ? g.bforce[act ? j : 0] : 0.f;
   // products of the lower z edges / faces of the current plane, carried from plane to plane
   float Exz[5], Eyz[4], Szz[4];
   wait(0);
   wait(1);
   {
-    const float* Pm = stg;                 // plane k0 - 1
-    const float* P0 = stg + SG::SLOT;      // plane k0
+    const float* Pm = slotp(0);   // plane k0 - 1
+    const float* P0 = slotp(1);   // plane k0
     float Ukm[6], Uc[6], Wc[6], Vkm[6], Vc[6], Wmc[6], Wkm[6];
     lds_seg<false, true, NX>(Pm + r0, i0, Ukm);
     lds_seg<false, true, NX>(P0 + r0, i0, Uc);
@@ -919,9 +932,9 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs
       for (int c = 0; c < 3; ++c) ldw<4>(A.un[c] + row + i0, pn[c]);
     }
     wait(kk + 2);
-    const float* Pm = stg + (size_t)(kk % kStageRing) * SG::SLOT;         // plane k - 1
-    const float* P0 = stg + (size_t)((kk + 1) % kStageRing) * SG::SLOT;   // plane k
-    const float* Pp = stg + (size_t)((kk + 2) % kStageRing) * SG::SLOT;   // plane k + 1
+    const float* Pm = slotp(kk);       // plane k - 1
+    const float* P0 = slotp(kk + 1);   // plane k
+    const float* Pp = slotp(kk + 2);   // plane k + 1
     const float* U0 = P0;
     const float* V0 = P0 + SG::FIELD;
     const float* W0 = P0 + 2 * SG::FIELD;
@@ -1023,6 +1036,8 @@ __global__ void __launch_bounds__(kThreads, 2) predictor3t_kernel(const PredArgs
 #pragma unroll
       for (int c = 0; c < 3; ++c) stw<4>(A.out[c] + row + i0, o3[c]);
     }
+  }
+  base += nplanes;
   }
   if (!ok) atomicOr(status, 1u);   // a staged plane never arrived: results of this block are invalid
 }
@@ -1311,12 +1326,16 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
                                (int)stage_smem<256>());
           attr = true;
         }
+        // two resident blocks per SM, each with an equal share of the (row block, plane) units
+        static int nsm = 0;
+        if (!nsm) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
         const int by = 1024 / nx;
-        const dim3 sg((G->ny + by - 1) / by, (G->nz + KZ - 1) / KZ);
+        const long long units = (long long)((G->ny + by - 1) / by) * G->nz;
+        const dim3 sg((unsigned)std::min<long long>(units, 2LL * std::max(nsm, 1)));
         if (nx == 128)
-          launch_pdl(G, "predictor", predictor3t_kernel<128>, sg, dim3(32, 8), stage_smem<128>(), A, KZ, G->dstatus);
+          launch_pdl(G, "predictor", predictor3t_kernel<128>, sg, dim3(32, 8), stage_smem<128>(), A, G->dstatus);
         else
-          launch_pdl(G, "predictor", predictor3t_kernel<256>, sg, dim3(64, 4), stage_smem<256>(), A, KZ, G->dstatus);
+          launch_pdl(G, "predictor", predictor3t_kernel<256>, sg, dim3(64, 4), stage_smem<256>(), A, G->dstatus);
         return;
       }
       // walls: the four rows that reach a wall run in their own kernel, the vector kernels take rows 2 .. ny - 2
