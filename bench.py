@@ -304,6 +304,11 @@ def run_ours(args, ws, rank, local):
     cells = wl.cells()
     stream = torch.cuda.current_stream()
     g = grid_from_workload(wl, "mixed", stream=stream)
+    # "FP32 stencils / FP64 Poisson": on a periodic y the y part of the Poisson solve is the FP64
+    # cyclic tridiagonal per x/z wavenumber (x and z transforms in FP32, zero mode exact)
+    fp64_y = args.y_solve == "fp64" and wl.bc[1][0] == S.PERIODIC
+    if fp64_y:
+        g.set_tuning("y_spectral", 0)
     u0 = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
     u = [x.clone() for x in u0]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -331,18 +336,35 @@ def run_ours(args, ws, rank, local):
     bpc = KERNEL_BYTES_PER_CELL.get(dominant)
     if dominant.startswith("predictor"):
         bpc = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
+    timing = ("CUDA events around every launch of the kernel over a second pass of the K timed "
+              "steps (L2 flushed per step, programmatic dependent launch off in that pass)")
+
+    def hbm_roofline(name):
+        c, t = allk.get(name, (0, 0.0))
+        b = KERNEL_BYTES_PER_CELL.get(name)
+        if name.startswith("predictor"):
+            b = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
+        ach = b * cells / (t / c * 1e-3) / 1e9 if (c and b) else None
+        tr = NCU_TRAFFIC.get(name)
+        return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak if ach else None,
+                "traffic": tr["bytes"] if tr and tr.get("src") == src_hash(name) else None,
+                "bytes_per_cell": b, "launches": c, "avg_launch_us": t / c * 1e3 if c else None,
+                "timing": timing, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+
     if dominant == "ysolve":
-        nlam = (wl.n[0] // 2 + 1) * (wl.n[2] // 2 + 1)
-        bpc = 8.0 + 3 * 8.0 * nlam * wl.n[1] / cells
-    achieved = bpc * cells / (kms / cnt * 1e-3) / 1e9 if (cnt and bpc) else None
-    tr = NCU_TRAFFIC.get(dominant)
-    traffic = tr["bytes"] if tr and tr.get("src") == src_hash(dominant) else None
-    roofline = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "bytes_per_cell": bpc, "launches": cnt, "avg_launch_us": kms / cnt * 1e3 if cnt else None,
-                "timing": "CUDA events around every launch of the kernel over a second pass of the K timed "
-                          "steps (L2 flushed per step, programmatic dependent launch off in that pass)",
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
+        # the FP64 partitioned tridiagonal is bound by the FP64 rate: 9 flops per cell (forward sweep
+        # 3, backward 2, spike correction 4) against the B300's nominal 1.25 TFLOP/s FP64 (no FP64
+        # peak is measured on this machine)
+        flops = 9.0
+        ach = flops * cells / (kms / cnt * 1e-3) / 1e12 if cnt else None
+        roofline = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": ach / 1.25 if ach else None, "traffic": None, "flops_per_cell": flops,
+                    "launches": cnt, "avg_launch_us": kms / cnt * 1e3 if cnt else None, "timing": timing,
+                    "peak_source": "nominal FP64 rate (1.25 TFLOP/s)"}
+    else:
+        roofline = hbm_roofline(dominant)
+    stencil_roofline = hbm_roofline("predictor") if dominant != "predictor" else None
 
     line = {
         "metric": "cell-updates/s forward", "value": value, "unit": "cell-updates/s", "n_gpus": ws,
@@ -350,14 +372,30 @@ def run_ours(args, ws, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "cells": cells, "n": wl.n, "scheme": wl.scheme,
-                   "precision": "mixed (FP32 stencils/transforms, FP64 tridiagonal/zero mode/reductions)",
+                   "precision": ("mixed: FP32 stencils and x/z transforms; FP64 Poisson along y (cyclic "
+                                 "tridiagonal per wavenumber), zero mode and reductions" if fp64_y else
+                                 "mixed (FP32 stencils/transforms, FP64 tridiagonal/zero mode/reductions)"),
                    "l2": "flushed before every timed step (256 MB write outside the timed events)",
                    "parallelism": "replicas" if ws > 1 else "single"},
         "gpu_launches": launches,
         "roofline": roofline,
+        "stencil_roofline": stencil_roofline,
         "clocks": clk.summary(),
         "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(allk.items(), key=lambda kv: -kv[1][1])},
     }
+
+    if not args.quick and fp64_y:
+        # the same step with the y part of the Poisson solve as an FP32 DFT (zero mode exact)
+        gs = grid_from_workload(wl, "mixed", stream=stream)
+        us = [x.clone() for x in u0]
+        for _ in range(args.warmup):
+            gs.step(us, wl.dt, 1)
+        mss = timed_steps(gs, us, wl.dt, args.steps, flush, stream)
+        line["spectral_y"] = {"value": cells * args.steps / (sum(mss) * 1e-3), "unit": "cell-updates/s",
+                              "ms_per_step": sum(mss) / args.steps,
+                              "note": "the y part of the Poisson solve as an FP32 DFT with the exact zero mode "
+                                      "(the same discrete solution; FP32 rounding in y)"}
+        del gs, us
 
     if not args.quick:
         # all-FP64 GPU path on the same workload, and the mixed result's distance to it
@@ -624,6 +662,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="isotropic_3d_128")
+    ap.add_argument("--y-solve", default="fp64", choices=["fp64", "spectral"],
+                    help="periodic y: FP64 cyclic tridiagonal (the FP64 Poisson of the 128^3 configuration) "
+                         "or the FP32 DFT (also reported as the spectral_y leg)")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")

@@ -288,12 +288,16 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     128 or 256 the predictor stages its input planes in
  *                     shared memory with bulk asynchronous copies; 0: it reads
  *                     them from global memory (four-cell z-marching kernel)
+ *   "y_spectral"      periodic y only: 1 (default) DFT along y in the grid's
+ *                     field precision, zero mode exact; 0: the FP64 cyclic
+ *                     partitioned tridiagonal solve per x/z wavenumber (rebuilds
+ *                     the y tables; synchronises).  Same discrete solution.
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
  *                     grid has fewer 32-column blocks than two per SM, else 4);
  *                     rebuilds the y tables
  *                     (synchronises the stream; set it before capturing graphs)
- * Results do not depend on them (ysolve_segments: up to rounding).
+ * Results do not depend on them (ysolve_segments, y_spectral: up to rounding).
  * FS_ERR_ARG for an unknown key or value. */
 int fs_set_tuning(fs_grid* grid, const char* key, int value);
 

@@ -692,6 +692,22 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "predictor_staged") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "predictor_staged must be 0 or 1");
     G->tune_staged = value == 1;
+  } else if (k == "y_spectral") {
+    // periodic y: 1 (default) DFT along y in the field precision with the exact zero mode;
+    // 0 the FP64 cyclic partitioned tridiagonal solve per x/z wavenumber (the wall-normal path)
+    if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "y_spectral must be 0 or 1");
+    if (!G->per[1]) return value == 1 ? FS_OK : set_error(FS_ERR_ARG, "y_spectral applies to a periodic y");
+    if ((value == 1) == (G->yspec != 0)) return FS_OK;
+    if (value == 0 && (size_t)G->ny * 32 * 8 > 200 * 1024)
+      return set_error(FS_ERR_UNSUPPORTED, "ny too large for the shared-memory tridiagonal staging (max 800)");
+    const cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
+    free_ytables(G);
+    if (G->lamy) cudaFree(G->lamy);
+    if (G->lamxz) cudaFree(G->lamxz);
+    G->lamy = G->lamxz = nullptr;
+    G->yspec = value;
+    return build_tables(G);
   } else if (k == "ysolve_segments") {
     if (value != 0 && value != 4 && value != 8 && value != 16)
       return set_error(FS_ERR_ARG, "ysolve_segments must be 4, 8 or 16");

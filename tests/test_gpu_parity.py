@@ -161,6 +161,46 @@ def test_solve_pressure_compile_time_lengths(case, precision):
     assert float((p.cpu() - ref).abs().max()) < 1e-12 * float(ref.abs().max())
 
 
+@pytest.mark.parametrize("wl", [
+    S.box_3d(12, 16, 10, (P, P), (P, P)),
+    S.box_3d(8, 70, 6, (P, P), (P, P)),          # ragged segments, 8 segments (narrow 8-column blocks)
+    S.box_2d(24, 40, (P, P), (P, P)),
+])
+def test_periodic_y_cyclic_tridiagonal_fp64(wl):
+    """Periodic y solved by the FP64 cyclic partitioned tridiagonal (y_spectral = 0)
+    against the oracle's direct solve and against the spectral y solve."""
+    from paper_2505_23940_b300 import grid_from_workload
+    from oracle import fluid, poisson
+    g = grid_of(wl)
+    rng = np.random.default_rng(12)
+    u = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(g.dim)]
+    b = fluid.divergence(g, u)
+    ref = poisson.solve(g, b)
+    out = []
+    for spectral in (0, 1):
+        G = grid_from_workload(wl, "fp64")
+        G.set_tuning("y_spectral", spectral)
+        out.append(G.solve_pressure(b.cuda().contiguous()).cpu())
+    torch.cuda.synchronize()
+    scale = float(ref.abs().max())
+    assert float((out[0] - ref).abs().max()) < 1e-12 * scale
+    assert float((out[0] - out[1]).abs().max()) < 1e-12 * scale
+
+
+def test_mixed_isotropic_fp64_y_solve():
+    """The isotropic RK3 step in mixed precision with the FP64 cyclic tridiagonal y solve
+    (FP32 stencils and x/z transforms, FP64 Poisson along y) against the FP64 oracle."""
+    from paper_2505_23940_b300 import grid_from_workload
+    wl = S.isotropic_3d(n=32, steps=5)
+    st, _, _ = run_oracle(wl, 5)
+    G = grid_from_workload(wl, "mixed")
+    G.set_tuning("y_spectral", 0)
+    u = [torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous() for a in wl.u0]
+    G.step(u, wl.dt, 5)
+    torch.cuda.synchronize()
+    assert field_err([x.double().cpu() for x in u], st.u) < TOLMIX
+
+
 def _small_cyl(kernel, precision="fp64", omega=0.0):
     wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, kernel=kernel, centre_d=(2.0, 2.0),
                        precision=precision, seed=3, perturb=0.05, omega=omega)
