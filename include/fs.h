@@ -290,14 +290,19 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     them from global memory (four-cell z-marching kernel)
  *   "y_spectral"      periodic y only: 1 (default) DFT along y in the grid's
  *                     field precision, zero mode exact; 0: the FP64 cyclic
- *                     partitioned tridiagonal solve per x/z wavenumber (rebuilds
- *                     the y tables; synchronises).  Same discrete solution.
+ *                     tridiagonal solve per x/z wavenumber (rebuilds the y
+ *                     tables; synchronises).  Same discrete solution.
+ *   "ysolve_twisted"  FP64 tridiagonal y solve form: 1 twisted factorisation,
+ *                     two threads per column (where ny <= 586); 0 the
+ *                     partitioned form; -1 (default) twisted when the grid has
+ *                     at least 148 * 64 columns (n_x n_z).  Rebuilds the y
+ *                     tables (synchronises the stream)
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
  *                     grid has fewer 32-column blocks than two per SM, else 4);
  *                     rebuilds the y tables
  *                     (synchronises the stream; set it before capturing graphs)
- * Results do not depend on them (ysolve_segments, y_spectral: up to rounding).
+ * Results do not depend on them (ysolve_*, y_spectral: up to rounding).
  * FS_ERR_ARG for an unknown key or value. */
 int fs_set_tuning(fs_grid* grid, const char* key, int value);
 

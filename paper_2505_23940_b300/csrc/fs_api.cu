@@ -118,6 +118,122 @@ size_t comp_size(const fs_grid* G, int c) {
 
 size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) : sizeof(double); }
 
+// FP64 tables of the twisted y solve (poisson.cu: ytwist_kernel), per eigenvalue
+// index li = lz * nmx + mx, from the couplings a_j (row j to j - 1) and c_j (row j
+// to j + 1; both wrap around on periodic y) and the diagonal b_j = lambda - a_j - c_j.
+// Chain rows 0..L-1 (L = ny, or ny - 1 on periodic y where row ny - 1 is bordered
+// off); the upper elimination runs over rows 0..k, the lower over L-1..k+1:
+//   upper: beta_j = b_j - a_j c_{j-1} / beta_{j-1},  M_j = -a_j / beta_{j-1}   (j = 1..k)
+//          E_j = 1 / beta_j,  C_j = -c_j / beta_j                            (j = 0..k-1)
+//   lower: beta'_j = b_j - c_j a_{j+1} / beta'_{j+1},  M_j = -c_j / beta'_{j+1} (j = L-2..k+1)
+//          E_j = 1 / beta'_j,  C_j = -a_j / beta'_j                          (j = k+2..L-1)
+//   P = inverse of [[beta_k, c_k], [a_{k+1}, beta'_{k+1}]]
+// The singular zero mode pins x_0 = 0: 1 / beta_0 taken as 0, no coupling into row 0
+// (the corner couplings of row 0 and row ny - 1 vanish).
+// Periodic y also stores z = A''^-1 u (u_0 = a_0, u_{L-1} = c_{L-1}: the coupling
+// column of x_{ny-1}), computed with the same tables, and S = (c_{ny-1}, a_{ny-1},
+// 1 / (b_{ny-1} - c_{ny-1} z_0 - a_{ny-1} z_{ny-2})).
+// Layout: M, E, C, Z eigenvalue-major [nlam][pitch] in position order
+// p(j) = j (j <= k), L + k - j (k < j < L); P and S [nlam][4].
+int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::vector<double>& c) {
+  const int nx = G->nx, ny = G->ny, nz = G->nz;
+  const int nlam = G->nmx * G->nlz;
+  const bool cyc = G->cyclic != 0;
+  const int L = cyc ? ny - 1 : ny, k = (L - 1) / 2;
+  const int pitch = ny + (ny & 1);
+  G->ytw_L = L;
+  G->ytw_k = k;
+  G->ytw_pitch = pitch;
+  auto pos = [&](int j) { return j <= k ? j : L + k - j; };
+  std::vector<double> M((size_t)nlam * pitch, 0.0), E((size_t)nlam * pitch, 0.0), C((size_t)nlam * pitch, 0.0);
+  std::vector<double> P((size_t)4 * nlam, 0.0), Z, S;
+  if (cyc) {
+    Z.assign((size_t)nlam * pitch, 0.0);
+    S.assign((size_t)4 * nlam, 0.0);
+  }
+  std::vector<double> aa(ny), cc(ny), bb(ny), beta(ny), e(ny), rhs(ny), x(ny), gh(ny);
+  std::vector<double> m(ny), ee(ny), cm(ny);
+  for (int mx = 0; mx < G->nmx; ++mx) {
+    const double lx = G->xmode == 1 ? -(2.0 - 2.0 * std::cos(M_PI * mx / nx)) / (G->hx * G->hx)
+                                    : -(2.0 - 2.0 * std::cos(2.0 * M_PI * mx / nx)) / (G->hx * G->hx);
+    for (int lz = 0; lz < G->nlz; ++lz) {
+      const double lzv = G->dim == 3 ? -(2.0 - 2.0 * std::cos(2.0 * M_PI * lz / nz)) / (G->hz * G->hz) : 0.0;
+      const double lam = lx + lzv;
+      const int li = lz * G->nmx + mx;
+      const bool sing = (mx == 0 && lz == 0);
+      for (int j = 0; j < ny; ++j) {
+        aa[j] = a[j];
+        cc[j] = c[j];
+        bb[j] = -(a[j] + c[j]) + lam;
+      }
+      if (sing) {
+        aa[0] = 0.0;
+        cc[0] = 0.0;
+        if (cyc) cc[ny - 1] = 0.0;
+      }
+      // upper elimination
+      e[0] = sing ? 0.0 : 1.0 / bb[0];
+      beta[0] = bb[0];
+      m[0] = 0.0;
+      for (int j = 1; j <= k; ++j) {
+        beta[j] = bb[j] - aa[j] * cc[j - 1] * e[j - 1];
+        e[j] = 1.0 / beta[j];
+        m[j] = -aa[j] * e[j - 1];
+      }
+      for (int j = 0; j < k; ++j) {
+        ee[j] = e[j];
+        cm[j] = -cc[j] * e[j];
+      }
+      // lower elimination
+      beta[L - 1] = bb[L - 1];
+      e[L - 1] = 1.0 / beta[L - 1];
+      m[L - 1] = 0.0;
+      for (int j = L - 2; j > k; --j) {
+        beta[j] = bb[j] - cc[j] * aa[j + 1] * e[j + 1];
+        e[j] = 1.0 / beta[j];
+        m[j] = -cc[j] * e[j + 1];
+      }
+      for (int j = k + 2; j < L; ++j) {
+        ee[j] = e[j];
+        cm[j] = -aa[j] * e[j];
+      }
+      ee[k] = ee[k + 1] = cm[k] = cm[k + 1] = 0.0;
+      const double det = beta[k] * beta[k + 1] - cc[k] * aa[k + 1];
+      const double p[4] = {beta[k + 1] / det, -cc[k] / det, -aa[k + 1] / det, beta[k] / det};
+      for (int q = 0; q < 4; ++q) P[(size_t)li * 4 + q] = p[q];
+      for (int j = 0; j < L; ++j) {
+        const size_t o = (size_t)li * pitch + pos(j);
+        M[o] = m[j];
+        E[o] = ee[j];
+        C[o] = cm[j];
+      }
+      if (cyc) {
+        // z = A''^-1 u by the same two-sided sweeps
+        for (int j = 0; j < L; ++j) rhs[j] = 0.0;
+        rhs[0] += aa[0];
+        rhs[L - 1] += cc[L - 1];
+        gh[0] = rhs[0];
+        for (int j = 1; j <= k; ++j) gh[j] = rhs[j] + m[j] * gh[j - 1];
+        gh[L - 1] = rhs[L - 1];
+        for (int j = L - 2; j > k; --j) gh[j] = rhs[j] + m[j] * gh[j + 1];
+        x[k] = p[0] * gh[k] + p[1] * gh[k + 1];
+        x[k + 1] = p[2] * gh[k] + p[3] * gh[k + 1];
+        for (int j = k - 1; j >= 0; --j) x[j] = ee[j] * gh[j] + cm[j] * x[j + 1];
+        for (int j = k + 2; j < L; ++j) x[j] = ee[j] * gh[j] + cm[j] * x[j - 1];
+        for (int j = 0; j < L; ++j) Z[(size_t)li * pitch + pos(j)] = x[j];
+        const double sigma = bb[ny - 1] - cc[ny - 1] * x[0] - aa[ny - 1] * x[L - 1];
+        S[(size_t)li * 4 + 0] = cc[ny - 1];
+        S[(size_t)li * 4 + 1] = aa[ny - 1];
+        S[(size_t)li * 4 + 2] = 1.0 / sigma;
+      }
+    }
+  }
+  if (upload(&G->twM, M) != cudaSuccess || upload(&G->twE, E) != cudaSuccess || upload(&G->twC, C) != cudaSuccess ||
+      upload(&G->twP, P) != cudaSuccess || (cyc && (upload(&G->twZ, Z) != cudaSuccess || upload(&G->twS, S) != cudaSuccess)))
+    return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");
+  return FS_OK;
+}
+
 // FP64 tables of the partitioned y solve, one column per eigenvalue index:
 // for each of the NSEG segments of every column, the local Thomas factors of the
 // segment's block (e_j = 1 / beta_j, c'_j) and its right / left spikes v, w
@@ -128,6 +244,7 @@ size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) 
 // the denser interface solve than they save).
 int build_tables(fs_grid* G) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
+  G->ytwist = 0;
   if (G->tune_ynseg > 0) {
     G->ynseg = G->tune_ynseg;
   } else {
@@ -173,6 +290,16 @@ int build_tables(fs_grid* G) {
     c[ny - 1] = 0.0;
   }
   G->cyclic = G->per[1];
+  {
+    const long columns = (long)nx * (G->dim == 3 ? nz : 1);
+    const int L = G->cyclic ? ny - 1 : ny;
+    const bool want = G->tune_ytwist < 0 ? columns >= 148L * 64 : G->tune_ytwist == 1;
+    // shared memory holds the block's columns in FP64 plus their FP32 copy: 64 columns while two
+    // blocks fit an SM (ny <= 146), else 32 (ny <= 586)
+    G->ytw_cols = (size_t)ny * 64 * 12 <= 112 * 1024 ? 64 : 32;
+    G->ytwist = L >= 4 && (size_t)ny * G->ytw_cols * 12 <= 220 * 1024 && want;
+    if (G->ytwist) return build_twisted_tables(G, a, c);
+  }
   const int NRED = 2 * NSEG;
   std::vector<double> E((size_t)ny * nlam), CP((size_t)ny * nlam), V((size_t)ny * nlam), W((size_t)ny * nlam);
   std::vector<double> MI((size_t)NRED * NRED * nlam);
@@ -281,7 +408,8 @@ int build_tables(fs_grid* G) {
 }
 
 void free_ytables(fs_grid* G) {
-  double** t[6] = {&G->ya, &G->tE, &G->tCP, &G->tZV, &G->tWV, &G->tMI};
+  double** t[12] = {&G->ya, &G->tE, &G->tCP, &G->tZV, &G->tWV, &G->tMI,
+                    &G->twM, &G->twE, &G->twC, &G->twP, &G->twZ, &G->twS};
   for (double** p : t) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -694,7 +822,7 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     G->tune_staged = value == 1;
   } else if (k == "y_spectral") {
     // periodic y: 1 (default) DFT along y in the field precision with the exact zero mode;
-    // 0 the FP64 cyclic partitioned tridiagonal solve per x/z wavenumber (the wall-normal path)
+    // 0 the FP64 cyclic tridiagonal solve per x/z wavenumber (the wall-normal path)
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "y_spectral must be 0 or 1");
     if (!G->per[1]) return value == 1 ? FS_OK : set_error(FS_ERR_ARG, "y_spectral applies to a periodic y");
     if ((value == 1) == (G->yspec != 0)) return FS_OK;
@@ -714,6 +842,15 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     if (value == G->tune_ynseg) return FS_OK;
     G->tune_ynseg = value;
     if (G->yspec) return FS_OK;   // periodic y has no partitioned solve
+    const cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
+    free_ytables(G);
+    return build_tables(G);
+  } else if (k == "ysolve_twisted") {
+    if (value < -1 || value > 1) return set_error(FS_ERR_ARG, "ysolve_twisted must be -1, 0 or 1");
+    if (value == G->tune_ytwist) return FS_OK;
+    G->tune_ytwist = value;
+    if (G->yspec) return FS_OK;
     const cudaError_t e = cudaStreamSynchronize(G->stream);
     if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
     free_ytables(G);

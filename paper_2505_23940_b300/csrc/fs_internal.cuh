@@ -295,8 +295,18 @@ struct fs_grid {
   int ynarrow = 0;                        // 1: 8-column blocks; tE, tCP, tZV, tWV are then [nlam][ypitch]
   int ypitch = 0;                         // row count of the eigenvalue-major tables (ny rounded up to even)
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
-  int tune_ynseg = 0;
-  bool tune_staged = true;                // shared-memory staged predictor where it applies                     // requested segment count (0: chosen from the grid's shape)
+  int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
+  bool tune_staged = true;                // shared-memory staged predictor where it applies
+  // twisted y solve (grids with many columns): two threads per column, tables per eigenvalue
+  int ytwist = 0;                         // 1: the twisted solve runs instead of the partitioned one
+  int tune_ytwist = -1;                   // -1: chosen from the grid's shape, 0: off, 1: on where it fits
+  int ytw_cols = 64;                      // columns per block (64 or 32)
+  int ytw_L = 0, ytw_k = 0;               // chain rows 0..L-1, upper thread rows 0..k
+  int ytw_pitch = 0;                      // row pitch of the eigenvalue-major tables
+  double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [nlz * nmx][pitch], position order
+  double *twP = nullptr;                  // [nlz * nmx][4]
+  double *twZ = nullptr;                  // [nlz * nmx][pitch] (periodic y)
+  double *twS = nullptr;                  // [nlz * nmx][4] (periodic y)
 
   fs::IBDev ib;
   bool has_body = false;

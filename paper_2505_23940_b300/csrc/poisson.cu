@@ -23,8 +23,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "fs_internal.cuh"
+#include "fpconv.cuh"
 #include "tma.cuh"
 
 namespace fs {
@@ -755,6 +757,367 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 }
 
 // ---------------------------------------------------------------------------
+// y solve for grids with many columns: twisted (two-sided) factorisation, two
+// threads per column and no partition corrections.
+//
+// The chain of rows 0..L-1 (L = ny; with periodic y, L = ny - 1 and row ny - 1
+// is bordered off, below) is eliminated from both ends at once: the upper
+// thread runs forward elimination over rows 0..k, the lower thread backward
+// elimination over rows L-1..k+1,
+//   g_j = d_j + M_j g_{j-1}   (upper),      h_j = d_j + M_j h_{j+1}   (lower),
+// which leaves the 2x2 system of rows k, k+1, solved with its tabulated
+// inverse P after one shuffle between the two threads; each thread then
+// substitutes outward,
+//   x_j = E_j g_j + C_j x_{j+1}   (upper),  x_j = E_j h_j + C_j x_{j-1}   (lower).
+// That is one FP64 multiply-add per row forward and a multiply plus a
+// multiply-add backward: the FP64 work of a plain Thomas solve, spread over
+// twice the threads.  M, E, C are tabulated per eigenvalue (M and C negated).
+//
+// Periodic y (cyclic): with xi = x_{ny-1}, rows 0..ny-2 read A'' x' = d' - xi u,
+// u the coupling column of x_{ny-1}; so x' = y - xi z with A'' y = d' (the solve
+// above) and z = A''^-1 u (tabulated), and row ny-1 gives
+//   xi = (d_{ny-1} - S0 y_0 - S1 y_{ny-2}) S2,   S2 = 1 / (b_{ny-1} - S0 z_0 - S1 z_{ny-2}),
+// S0, S1 its couplings to x_0 and x_{ny-2}: one more multiply-add per row.
+//
+// Rows are held in "position" order p(j) = j (j <= k), L + k - j (k < j < L),
+// ny - 1 (the bordered row): both threads of a column then sweep the same
+// direction (positions ascending while eliminating, descending while
+// substituting), so the shared-memory tile and the eigenvalue-major tables
+// ([nlam][pitch], position order) are read at fixed offsets from one base, the
+// tables a chunk of U rows ahead of their use.  The tile's rows arrive by bulk
+// asynchronous copies straight into their positions and leave the same way.
+// FP32 fields stay FP32 in shared memory: each thread widens its next chunk of
+// the spectrum and narrows its solution with integer field arithmetic
+// (fpconv.cuh) inside its sweeps, where those instructions issue while the FP64
+// pipe, the kernel's bound (one warp instruction per ~73 cycles per SM
+// sub-partition on B300, conversions included), works on the chain.
+//
+// The singular zero mode pins x_0 = 0 through its tables (E_0 = C_0 = 0,
+// M_1 = 0, no coupling to row 0) and is shifted to zero hy-weighted mean (with
+// FP32 fields the shift, a constant invisible to the pressure gradient, is
+// applied after narrowing).
+//
+// Block: W columns (16 per warp, lanes 0..15 the upper and 16..31 the lower
+// threads); 3-D blocks are ordered so that the z positions t and nz - t, which
+// share every eigenvalue, run next to each other.
+struct YTwArgs {
+  int nx, ny, nz, dim, xmode, nmx, nlz;
+  int L, k;              // chain rows 0..L-1; the upper thread owns rows 0..k
+  int pitch;             // table row pitch (>= ny, even)
+  int bulk;              // rows move by bulk copies (16-byte aligned rows and widths)
+  const double* M;       // [nlam][pitch] forward multipliers (negated), position order
+  const double* E;       // [nlam][pitch] inverse pivots
+  const double* C;       // [nlam][pitch] outward multipliers (negated)
+  const double* Z;       // [nlam][pitch] cyclic: z = A''^-1 u
+  const double* P;       // [nlam][4] inverse of the middle 2x2 system
+  const double* S;       // [nlam][4] cyclic: S0, S1, S2
+  const double* hy;      // cell widths (zero-mode mean)
+  double hysum;
+  unsigned* status;      // device status word (bit 0: a bulk copy wait gave up)
+};
+
+__device__ __forceinline__ int lam_of(int nx, int nz, int dim, int xmode, int nmx, int s, int t) {
+  int mx;
+  if (xmode == 1) mx = s;
+  else mx = s == 0 ? 0 : (s == 1 ? nx / 2 : (s >> 1));
+  if (dim == 2) return mx;
+  const int l = (s >= 2 || xmode == 1) ? t : (t == 0 ? 0 : (t == 1 ? nz / 2 : (t >> 1)));
+  return min(l, nz - l) * nmx + mx;
+}
+
+template <typename T>
+__device__ __forceinline__ double widen(T v) {
+  if constexpr (sizeof(T) == 4) return fsconv_widen(v);
+  else return v;
+}
+template <typename T>
+__device__ __forceinline__ T narrow(double v) {
+  if constexpr (sizeof(T) == 4) return fsconv_narrow(v);
+  else return v;
+}
+
+template <typename T>
+size_t ytwist_smem(int ny, int w) {
+  return (size_t)ny * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0));
+}
+
+template <typename T, bool CYC, int W>
+__global__ void __launch_bounds__(2 * W) ytwist_kernel(T* __restrict__ data, const YTwArgs A) {
+  constexpr bool F32 = sizeof(T) == 4;
+  constexpr int U = 16;                          // rows per chunk (tables fetched a chunk ahead)
+  constexpr int NG = 4;                          // tile row groups, each on its own barrier
+  constexpr unsigned FULL = 0xffffffffu;
+  extern __shared__ __align__(16) unsigned char ytw_raw[];
+  const int ny = A.ny, L = A.L, k = A.k;
+  double* sg = reinterpret_cast<double*>(ytw_raw);   // [ny][W] FP64 eliminated / solved values, position order
+  T* st = F32 ? reinterpret_cast<T*>(ytw_raw + (size_t)ny * W * sizeof(double)) : reinterpret_cast<T*>(sg);
+  __shared__ uint64_t bar[NG];
+  const int tid = threadIdx.x, lane = tid & 31, half = lane >> 4;
+  const int cb = (tid >> 5) * 16 + (lane & 15);
+  const int s0 = blockIdx.x * W;
+  const int ncol = min(W, A.nx - s0);
+  int t = 0;
+  if (A.dim == 3) {
+    const int b = blockIdx.y;
+    t = (b & 1) ? A.nz - ((b + 1) >> 1) : (b >> 1);
+  }
+  const size_t rs = (size_t)A.nx;
+  T* tile = data + (size_t)A.nx * ny * t + s0;
+  auto pos = [&](int j) { return j <= k ? j : (j < L ? L + k - j : j); };
+  const int s = s0 + cb;
+  const bool act = cb < ncol;
+  const int li = act ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s, t) : 0;
+  const int P0 = half ? k + 1 : 0;             // first position of this thread
+  const int R = half ? L - 1 - k : k + 1;      // positions of this thread's elimination
+  const int RW = k + 1;                        // the upper thread's count (>= the lower's): warp-uniform trips
+  const size_t tb = (size_t)li * A.pitch + P0;
+  const double* __restrict__ Mt = A.M + tb;
+  // group of a row: by its offset from the first position of its thread (upper rows 0..k, lower
+  // rows from position k + 1; the bordered row last), cut at offsets 17, 33, 49 so that group g
+  // holds the chunk the elimination widens g-th
+  auto group = [&](int j) {
+    const int p = pos(j);
+    const int off = p >= L ? RW : (p <= k ? p : p - (k + 1));
+    return off < 17 ? 0 : min(NG - 1, (off - 1) >> 4);
+  };
+  // the first multipliers while the tile is in flight (tables do not depend on the predecessor)
+  double mn[U];
+#pragma unroll
+  for (int q = 0; q < U; ++q) mn[q] = (1 + q < R) ? __ldg(Mt + 1 + q) : 0.0;
+  bool ok = true;
+  if (A.bulk && tid == 0) {
+    for (int g = 0; g < NG; ++g) mbar_init(&bar[g], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  pdl_wait();
+  const uint32_t rb = (uint32_t)(ncol * sizeof(T));
+  if (A.bulk) {
+    if (tid < 32) {
+      if (lane < NG) {
+        // rows of group g: offsets [lo, hi) of the upper (RW rows) and lower (L - RW rows) threads,
+        // and the bordered row (offset RW) in the group that holds offset RW
+        const int lo = lane == 0 ? 0 : 1 + 16 * lane, hi = lane == NG - 1 ? 1 << 30 : 17 + 16 * lane;
+        auto cnt = [&](int n) { return max(0, min(hi, n) - lo); };
+        int rows = cnt(RW) + cnt(L - RW);
+        if (CYC && RW >= lo && RW < hi) ++rows;
+        mbar_expect_tx(&bar[lane], rb * (uint32_t)rows);
+      }
+      __syncwarp();
+      // issue in group order so that the first rows needed land first
+      for (int g = 0; g < NG; ++g)
+        for (int j = lane; j < ny; j += 32)
+          if (group(j) == g) bulk_g2s(st + (size_t)pos(j) * W, tile + rs * j, rb, &bar[g]);
+    }
+  } else {
+#pragma unroll 8
+    for (int e = tid; e < ny * W; e += 2 * W) {
+      const int j = e / W, c = e - j * W;
+      if (c < ncol) st[pos(j) * W + c] = tile[rs * j + c];
+    }
+    __syncthreads();
+  }
+  auto wait_group = [&](int g) {
+    if (A.bulk) ok &= mbar_wait(&bar[min(g, NG - 1)], 0);
+  };
+  T* op = st + P0 * W + cb;                    // this thread's column of the tile, from its first position
+  double* gp = sg + P0 * W + cb;
+  // d at positions i0 .. i0 + U - 1 by the integer fast path (positions past R and inactive columns
+  // read as zero); `sp` collects the values outside it
+  auto widen_fast = [&](int i0, double (&out)[U], uint32_t& sp) {
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int i = i0 + q;
+      if constexpr (F32) {
+        const uint32_t u = (act && i < R) ? __float_as_uint(op[i * W]) : 0u;
+        uint32_t hi, lo;
+        fsconv_widen_fast(u, &hi, &lo, &sp);
+        out[q] = __hiloint2double((int)hi, (int)lo);
+      } else {
+        out[q] = (act && i < R) ? (double)op[i * W] : 0.0;
+      }
+    }
+  };
+  auto widen_fix = [&](int i0, double (&out)[U], uint32_t sp) {
+    if constexpr (F32) {
+      if (__any_sync(FULL, sp)) {
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          const int i = i0 + q;
+          out[q] = (act && i < R) ? fsconv_widen(op[i * W]) : 0.0;
+        }
+      }
+    }
+  };
+  // FP64 value v of position i narrowed into the tile by the fast path
+  auto narrow_fast = [&](int i, double v, uint32_t& sp) {
+    if constexpr (F32) {
+      const uint32_t r = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
+      if (i >= 0 && i < R) op[i * W] = __uint_as_float(r);
+    } else {
+      if (i >= 0 && i < R) op[i * W] = v;
+    }
+  };
+  // 1. elimination towards the middle; the next chunk is widened (fast path) and its multipliers
+  // fetched while the chain runs, its exceptional values redone after
+  wait_group(0);
+  double gv = act ? widen<T>(op[0]) : 0.0;
+  gp[0] = gv;
+  double dn[U];
+  {
+    uint32_t sp = 0;
+    widen_fast(1, dn, sp);
+    widen_fix(1, dn, sp);
+  }
+  int c = 0;
+  for (int i0 = 1; i0 < RW; i0 += U, ++c) {
+    double mc[U], dc[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      mc[q] = mn[q];
+      dc[q] = dn[q];
+      mn[q] = (i0 + U + q < R) ? __ldg(Mt + i0 + U + q) : 0.0;
+    }
+    const bool more = i0 + U < RW;
+    if (more) wait_group(c + 1);
+    uint32_t sp = 0;
+    if (more) widen_fast(i0 + U, dn, sp);
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int i = i0 + q;
+      if (i < R) {
+        gv = fma(mc[q], gv, dc[q]);
+        gp[i * W] = gv;
+      }
+    }
+    if (more) widen_fix(i0 + U, dn, sp);
+  }
+  // 2. the middle rows k (upper's last position) and k+1 (lower's last)
+  const double oth = __shfl_xor_sync(FULL, gv, 16);
+  const double gk = half ? oth : gv, hk = half ? gv : oth;
+  const double* Pt = A.P + (size_t)li * 4 + 2 * half;
+  double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
+  gp[(R - 1) * W] = xv;
+  // 3. outward substitution, step m at position R - 2 - m (walls: narrowed as they are solved)
+  {
+    const double* __restrict__ Et = A.E + tb;
+    const double* __restrict__ Ct = A.C + tb;
+    double en[U], cn[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int i = R - 2 - q;
+      en[q] = i >= 0 ? __ldg(Et + i) : 0.0;
+      cn[q] = i >= 0 ? __ldg(Ct + i) : 0.0;
+    }
+    for (int m0 = 0; m0 < RW - 1; m0 += U) {
+      double ec[U], cc[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        ec[q] = en[q];
+        cc[q] = cn[q];
+        const int i = R - 2 - (m0 + U + q);
+        en[q] = i >= 0 ? __ldg(Et + i) : 0.0;
+        cn[q] = i >= 0 ? __ldg(Ct + i) : 0.0;
+      }
+      uint32_t sp = 0;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int i = R - 2 - (m0 + q);
+        if (i >= 0) {
+          const double eg = ec[q] * gp[i * W];
+          xv = fma(cc[q], xv, eg);
+          gp[i * W] = xv;
+        }
+        if constexpr (!CYC && F32) narrow_fast(i, xv, sp);
+      }
+      if constexpr (!CYC && F32) {
+        if (__any_sync(FULL, sp)) {
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            const int i = R - 2 - (m0 + q);
+            if (i >= 0) op[i * W] = fsconv_narrow(gp[i * W]);
+          }
+        }
+      }
+    }
+  }
+  pdl_trigger();
+  if constexpr (CYC) {
+    // 4. the bordered row ny - 1 (position ny - 1), then x = y - xi z, narrowed
+    for (int g = 1; g < NG; ++g) wait_group(g);   // the bordered row's group (already complete but for short columns)
+    const double o2 = __shfl_xor_sync(FULL, xv, 16);
+    const double y0 = half ? o2 : xv, yl = half ? xv : o2;   // positions 0 and k + 1
+    const double* St = A.S + (size_t)li * 4;
+    T* lastp = st + (size_t)(ny - 1) * W + cb;
+    const double dl = act ? widen<T>(*lastp) : 0.0;
+    const double xi = fma(-__ldg(St + 1), yl, fma(-__ldg(St), y0, dl)) * __ldg(St + 2);
+    const double* __restrict__ Zt = A.Z + tb;
+    double zn[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) zn[q] = q < R ? __ldg(Zt + q) : 0.0;
+    for (int i0 = 0; i0 < RW; i0 += U) {
+      double zc[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        zc[q] = zn[q];
+        zn[q] = i0 + U + q < R ? __ldg(Zt + i0 + U + q) : 0.0;
+      }
+      uint32_t sp = 0;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int i = i0 + q;
+        narrow_fast(i, fma(-xi, zc[q], i < R ? gp[i * W] : 0.0), sp);
+      }
+      if constexpr (F32) {
+        if (__any_sync(FULL, sp)) {
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            const int i = i0 + q;
+            if (i < R) op[i * W] = fsconv_narrow(fma(-xi, zc[q], gp[i * W]));
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (half) *lastp = narrow<T>(xi);
+  } else {
+    // walls: the middle position, which the outward sweep does not cover
+    if constexpr (F32) op[(R - 1) * W] = fsconv_narrow(gp[(R - 1) * W]);
+  }
+  // 5. zero mode: hy-weighted mean of its column (column 0 of the block holding s = 0, t = 0),
+  // subtracted in the field precision
+  const bool zb = s0 == 0 && (A.dim == 2 || t == 0);
+  __syncthreads();
+  if (zb) {
+    if (tid < 32) {
+      T part = 0;
+      for (int j = lane; j < ny; j += 32) part += (T)__ldg(A.hy + j) * st[pos(j) * W];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      const T zm = part / (T)A.hysum;
+      for (int p = lane; p < ny; p += 32) st[p * W] -= zm;
+    }
+    __syncthreads();
+  }
+  if (A.bulk) {
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid < 32) {
+      for (int j = lane; j < ny; j += 32) bulk_s2g(tile + rs * j, st + (size_t)pos(j) * W, rb);
+      bulk_s2g_commit();
+      bulk_s2g_wait();
+    }
+  } else {
+#pragma unroll 8
+    for (int e = tid; e < ny * W; e += 2 * W) {
+      const int j = e / W, c2 = e - j * W;
+      if (c2 < ncol) tile[rs * j + c2] = st[pos(j) * W + c2];
+    }
+  }
+  if (!ok) atomicOr(A.status, 1u);   // part of the tile never arrived: this block's columns are invalid
+}
+
+// ---------------------------------------------------------------------------
 // Periodic y: the columns (slot s, z position t) of the x/z spectrum are real
 // sequences along y to which the real symmetric circulant inverse
 // (A_y + Lambda_s)^-1 applies.  Two neighbouring slots (s, s+1) form one complex
@@ -1063,6 +1426,10 @@ void set_smem_attrs() {
   cudaFuncSetAttribute(ysolve_kernel<T, 4, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 16, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ytwist_kernel<T, true, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ytwist_kernel<T, false, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ytwist_kernel<T, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaFuncSetAttribute(ytwist_kernel<T, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   done = true;
 }
 
@@ -1144,6 +1511,39 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     FS_LAUNCH(G, "fft_y_solve", k<<<grid, 256, (size_t)(spb / 2) * line_bytes, G->stream>>>(
                                     data, A, radices_of(G->py), (const cplx<T>*)G->py.tw, (const T*)G->lamy,
                                     (const T*)G->lamxz));
+  } else if (G->ytwist) {
+    YTwArgs A;
+    A.nx = nx;
+    A.ny = ny;
+    A.nz = nz;
+    A.dim = G->dim;
+    A.xmode = G->xmode;
+    A.nmx = G->nmx;
+    A.nlz = G->nlz;
+    A.L = G->ytw_L;
+    A.k = G->ytw_k;
+    A.pitch = G->ytw_pitch;
+    A.M = G->twM;
+    A.E = G->twE;
+    A.C = G->twC;
+    A.P = G->twP;
+    A.Z = G->twZ;
+    A.S = G->twS;
+    A.hy = G->hy64;
+    A.hysum = G->hysum;
+    A.status = G->dstatus;
+    // rows move by bulk copies when every row start and width is a multiple of 16 bytes
+    A.bulk = (nx * (int)sizeof(T)) % 16 == 0 && reinterpret_cast<uintptr_t>(data) % 16 == 0;
+    const int w = G->ytw_cols;
+    const dim3 grid((nx + w - 1) / w, G->dim == 3 ? nz : 1);
+    const size_t sb = ytwist_smem<T>(ny, w);
+    if (w == 64) {
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(128), sb, data, A);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(128), sb, data, A);
+    } else {
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(64), sb, data, A);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(64), sb, data, A);
+    }
   } else {
     YArgs A;
     A.nx = nx;

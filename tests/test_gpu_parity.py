@@ -187,6 +187,71 @@ def test_periodic_y_cyclic_tridiagonal_fp64(wl):
     assert float((out[0] - out[1]).abs().max()) < 1e-12 * scale
 
 
+_TWIST_CASES = [
+    S.box_2d(40, 70, (P, P), (NS, NS), stretched=1.3),     # walls, stretched, 40 of 64 columns active
+    S.box_2d(24, 37, (IN, OUT), (FS, FS)),                 # x DCT-II, odd chain length
+    S.box_3d(10, 66, 6, (P, P), (NS, NS), stretched=1.5),
+    S.box_3d(12, 16, 10, (P, P), (P, P)),                  # periodic y: cyclic, chain of 15
+    S.box_2d(24, 6, (P, P), (P, P)),                       # shortest cyclic chain (5 rows)
+    S.box_2d(18, 5, (P, P), (NS, NS)),                     # walls, 5 rows
+    S.box_2d(20, 300, (P, P), (NS, NS), stretched=1.1),    # 300 rows
+    S.box_2d(16, 400, (P, P), (P, P)),                     # largest twisted column (200 KB tile), cyclic
+]
+
+
+@pytest.mark.parametrize("wl", _TWIST_CASES)
+def test_solve_pressure_twisted_fp64(wl):
+    """The twisted two-thread y solve (forced on small grids) against the oracle's direct
+    solve and against the partitioned solve of the same grid."""
+    from paper_2505_23940_b300 import grid_from_workload
+    from oracle import fluid, poisson
+    g = grid_of(wl)
+    rng = np.random.default_rng(13)
+    u = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(g.dim)]
+    u = fluid.apply_boundary_values(g, u)
+    u = fluid.outflow_faces(g, u, u)
+    b = fluid.divergence(g, u)
+    ref = poisson.solve(g, b)
+    out = []
+    for tw in (1, 0):
+        G = grid_from_workload(wl, "fp64")
+        if wl.bc[1][0] == P:
+            G.set_tuning("y_spectral", 0)
+        G.set_tuning("ysolve_twisted", tw)
+        out.append(G.solve_pressure(b.cuda().contiguous()).cpu())
+    torch.cuda.synchronize()
+    # the FP64 field tolerance (1e-11): the 400-row cyclic column, condition number ~ (400 / pi)^2,
+    # lands near 1e-12 with either solve form
+    scale = float(ref.abs().max())
+    assert float((out[0] - ref).abs().max()) < 1e-11 * scale
+    assert float((out[0] - out[1]).abs().max()) < 1e-11 * scale
+
+
+@pytest.mark.parametrize("wl", [
+    S.isotropic_3d(n=32, steps=5),
+    S.box_3d(16, 24, 8, (P, P), (NS, NS), stretched=1.2),
+    S.box_2d(18, 24, (P, P), (NS, NS), stretched=1.2),    # rows not 16-byte multiples: plain loads
+])
+def test_mixed_twisted_y_solve(wl):
+    """Mixed precision with the twisted FP64 y solve (integer-pipe FP32 <-> FP64
+    conversions, FP32 gauge of the zero mode) against the FP64 oracle over steps."""
+    from paper_2505_23940_b300 import grid_from_workload
+    if not wl.u0:
+        hmin = min(float(np.diff(wl.xf[d]).min()) for d in range(wl.dim))
+        wl.dt = 0.1 * hmin
+        wl.u0 = S.random_fields(wl, 14, 1.0)
+    n = 5
+    st, _, _ = run_oracle(wl, n)
+    G = grid_from_workload(wl, "mixed")
+    if wl.bc[1][0] == P:
+        G.set_tuning("y_spectral", 0)
+    G.set_tuning("ysolve_twisted", 1)
+    u = [torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous() for a in wl.u0]
+    G.step(u, wl.dt, n)
+    torch.cuda.synchronize()
+    assert field_err([x.double().cpu() for x in u], st.u) < TOLMIX
+
+
 def test_mixed_isotropic_fp64_y_solve():
     """The isotropic RK3 step in mixed precision with the FP64 cyclic tridiagonal y solve
     (FP32 stencils and x/z transforms, FP64 Poisson along y) against the FP64 oracle."""
