@@ -294,9 +294,10 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     tables; synchronises).  Same discrete solution.
  *   "ysolve_twisted"  FP64 tridiagonal y solve form: 1 twisted factorisation,
  *                     two threads per column (where ny <= 586); 0 the
- *                     partitioned form; -1 (default) twisted when the grid has
- *                     at least 148 * 64 columns (n_x n_z).  Rebuilds the y
- *                     tables (synchronises the stream)
+ *                     partitioned form; -1 (default) twisted on periodic y
+ *                     (y_spectral = 0) when the grid has at least 148 * 64
+ *                     columns (n_x n_z) and ny <= 148.  Rebuilds the y tables
+ *                     (synchronises the stream)
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
  *                     grid has fewer 32-column blocks than two per SM, else 4);

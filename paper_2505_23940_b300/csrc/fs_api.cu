@@ -133,22 +133,30 @@ size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) 
 // Periodic y also stores z = A''^-1 u (u_0 = a_0, u_{L-1} = c_{L-1}: the coupling
 // column of x_{ny-1}), computed with the same tables, and S = (c_{ny-1}, a_{ny-1},
 // 1 / (b_{ny-1} - c_{ny-1} z_0 - a_{ny-1} z_{ny-2})).
-// Layout: M, E, C, Z eigenvalue-major [nlam][pitch] in position order
-// p(j) = j (j <= k), L + k - j (k < j < L); P and S [nlam][4].
+// Layout: M, E, C, Z position-major [rows][nlp]: each thread of a column owns R = ceil(L / 2)
+// positions, the upper rows 0..R-1 (k = R - 1), the lower from position R: when L is odd first
+// an inert slot (M = 0, E = 1, C = 0, z = 0; it carries the bordered row ny - 1 on periodic y),
+// then rows L-1 down to R.  The rows are 2 kTwChunk zero rows, the 2 R positions, 2 kTwChunk
+// zero rows; nlp >= nlam + 72 leaves room for the kernel's L2 prefetch of a block's segment.
+// P and S are [nlam][4].
 int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::vector<double>& c) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int nlam = G->nmx * G->nlz;
   const bool cyc = G->cyclic != 0;
-  const int L = cyc ? ny - 1 : ny, k = (L - 1) / 2;
-  const int pitch = ny + (ny & 1);
+  const int L = cyc ? ny - 1 : ny, R = (L + 1) / 2, k = R - 1;
+  const bool odd = (L & 1) != 0;
+  const int front = 2 * kTwChunk;
+  const int rows = 2 * R + 4 * kTwChunk;
+  const int nlp = (nlam + 72 + 1) & ~1;
   G->ytw_L = L;
-  G->ytw_k = k;
-  G->ytw_pitch = pitch;
-  auto pos = [&](int j) { return j <= k ? j : L + k - j; };
-  std::vector<double> M((size_t)nlam * pitch, 0.0), E((size_t)nlam * pitch, 0.0), C((size_t)nlam * pitch, 0.0);
+  G->ytw_R = R;
+  G->ytw_nlp = nlp;
+  auto at = [&](int p, int li) { return (size_t)(front + p) * nlp + li; };
+  auto pos = [&](int j) { return j < R ? j : R + (odd ? 1 : 0) + (L - 1 - j); };
+  std::vector<double> M((size_t)rows * nlp, 0.0), E((size_t)rows * nlp, 0.0), C((size_t)rows * nlp, 0.0);
   std::vector<double> P((size_t)4 * nlam, 0.0), Z, S;
   if (cyc) {
-    Z.assign((size_t)nlam * pitch, 0.0);
+    Z.assign((size_t)rows * nlp, 0.0);
     S.assign((size_t)4 * nlam, 0.0);
   }
   std::vector<double> aa(ny), cc(ny), bb(ny), beta(ny), e(ny), rhs(ny), x(ny), gh(ny);
@@ -202,11 +210,12 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
       const double p[4] = {beta[k + 1] / det, -cc[k] / det, -aa[k + 1] / det, beta[k] / det};
       for (int q = 0; q < 4; ++q) P[(size_t)li * 4 + q] = p[q];
       for (int j = 0; j < L; ++j) {
-        const size_t o = (size_t)li * pitch + pos(j);
+        const size_t o = at(pos(j), li);
         M[o] = m[j];
         E[o] = ee[j];
         C[o] = cm[j];
       }
+      if (odd) E[at(R, li)] = 1.0;   // the inert slot keeps its value
       if (cyc) {
         // z = A''^-1 u by the same two-sided sweeps
         for (int j = 0; j < L; ++j) rhs[j] = 0.0;
@@ -220,7 +229,7 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
         x[k + 1] = p[2] * gh[k] + p[3] * gh[k + 1];
         for (int j = k - 1; j >= 0; --j) x[j] = ee[j] * gh[j] + cm[j] * x[j + 1];
         for (int j = k + 2; j < L; ++j) x[j] = ee[j] * gh[j] + cm[j] * x[j - 1];
-        for (int j = 0; j < L; ++j) Z[(size_t)li * pitch + pos(j)] = x[j];
+        for (int j = 0; j < L; ++j) Z[at(pos(j), li)] = x[j];
         const double sigma = bb[ny - 1] - cc[ny - 1] * x[0] - aa[ny - 1] * x[L - 1];
         S[(size_t)li * 4 + 0] = cc[ny - 1];
         S[(size_t)li * 4 + 1] = aa[ny - 1];
@@ -293,11 +302,16 @@ int build_tables(fs_grid* G) {
   {
     const long columns = (long)nx * (G->dim == 3 ? nz : 1);
     const int L = G->cyclic ? ny - 1 : ny;
-    const bool want = G->tune_ytwist < 0 ? columns >= 148L * 64 : G->tune_ytwist == 1;
-    // shared memory holds the block's columns in FP64 plus their FP32 copy: 64 columns while two
-    // blocks fit an SM (ny <= 146), else 32 (ny <= 586)
-    G->ytw_cols = (size_t)ny * 64 * 12 <= 112 * 1024 ? 64 : 32;
-    G->ytwist = L >= 4 && (size_t)ny * G->ytw_cols * 12 <= 220 * 1024 && want;
+    // by default only on periodic y (its partitioned form pays two spike corrections and a cyclic
+    // coupling per row), where two 64-column blocks fit an SM (ny <= 148), on a grid that fills
+    // it twice.  Measured per mixed step: isotropic 128^3 0.257 against 0.287 ms; the wall-bounded
+    // 192 x 128 x 128 channel 0.180 against 0.174 ms and 256^3 (32-column blocks, one sweep warp
+    // per SM sub-partition) slower as well, so those keep the partitioned solve.
+    const bool want = G->tune_ytwist < 0 ? (G->cyclic && columns >= 148L * 64 && ny <= 148) : G->tune_ytwist == 1;
+    // shared memory holds the block's columns (ny + 1 positions) in FP64 plus their FP32 copy:
+    // 64 columns while two blocks fit an SM (ny <= 148), else 32 (ny <= 585)
+    G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 112 * 1024 ? 64 : 32;
+    G->ytwist = L >= 4 && (size_t)(ny + 1) * G->ytw_cols * 12 <= 220 * 1024 && want;
     if (G->ytwist) return build_twisted_tables(G, a, c);
   }
   const int NRED = 2 * NSEG;

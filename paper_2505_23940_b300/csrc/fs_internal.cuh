@@ -301,11 +301,11 @@ struct fs_grid {
   int ytwist = 0;                         // 1: the twisted solve runs instead of the partitioned one
   int tune_ytwist = -1;                   // -1: chosen from the grid's shape, 0: off, 1: on where it fits
   int ytw_cols = 64;                      // columns per block (64 or 32)
-  int ytw_L = 0, ytw_k = 0;               // chain rows 0..L-1, upper thread rows 0..k
-  int ytw_pitch = 0;                      // row pitch of the eigenvalue-major tables
-  double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [nlz * nmx][pitch], position order
+  int ytw_L = 0, ytw_R = 0;               // chain rows 0..L-1, positions per thread R = ceil(L / 2)
+  int ytw_nlp = 0;                        // row pitch (eigenvalues) of the position-major tables
+  double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [2 R + 4 kTwChunk][nlp], position-major
   double *twP = nullptr;                  // [nlz * nmx][4]
-  double *twZ = nullptr;                  // [nlz * nmx][pitch] (periodic y)
+  double *twZ = nullptr;                  // [2 R + 4 kTwChunk][nlp] (periodic y)
   double *twS = nullptr;                  // [nlz * nmx][4] (periodic y)
 
   fs::IBDev ib;
@@ -373,6 +373,8 @@ template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state*
 void free_adj_buffers(void* p);
 // poisson.cu
 size_t ysolve_smem(int ny, int nseg, int yc);
+// rows per chunk of the twisted y solve; its tables carry 2 chunks of zero padding on each side
+constexpr int kTwChunk = 16;
 // errors
 int set_error(int code, const std::string& msg);
 int cuda_check(cudaError_t e, const char* what);

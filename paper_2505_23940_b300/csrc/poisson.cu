@@ -779,42 +779,51 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 //   xi = (d_{ny-1} - S0 y_0 - S1 y_{ny-2}) S2,   S2 = 1 / (b_{ny-1} - S0 z_0 - S1 z_{ny-2}),
 // S0, S1 its couplings to x_0 and x_{ny-2}: one more multiply-add per row.
 //
-// Rows are held in "position" order p(j) = j (j <= k), L + k - j (k < j < L),
-// ny - 1 (the bordered row): both threads of a column then sweep the same
-// direction (positions ascending while eliminating, descending while
-// substituting), so the shared-memory tile and the eigenvalue-major tables
-// ([nlam][pitch], position order) are read at fixed offsets from one base, the
-// tables a chunk of U rows ahead of their use.  The tile's rows arrive by bulk
-// asynchronous copies straight into their positions and leave the same way.
-// FP32 fields stay FP32 in shared memory: each thread widens its next chunk of
-// the spectrum and narrows its solution with integer field arithmetic
-// (fpconv.cuh) inside its sweeps, where those instructions issue while the FP64
-// pipe, the kernel's bound (one warp instruction per ~73 cycles per SM
-// sub-partition on B300, conversions included), works on the chain.
+// Positions: both threads of a column own R = ceil(L / 2) consecutive
+// positions and sweep them in the same direction.  The upper thread's are rows
+// 0..R-1; the lower thread's start at position R with, when L is odd, one
+// inert slot (multiplier 0, E = 1, C = 0, z = 0) that holds the bordered row
+// ny - 1 on periodic y, followed by rows L-1 down to R.  Shared memory and the
+// tables are then read at fixed strides from one base, with no per-row bounds.
+// The tables are position-major ([2 U zero rows, 2 R positions, 2 U zero
+// rows][eigenvalues]): the 16 threads of a half-warp read 8 consecutive
+// eigenvalues of one position, one coalesced 64-byte segment (one column per
+// eigenvalue instead scatters each such read over 16 lines and halves the
+// sweep rate).
+//
+// B300's FP64 pipe (one warp instruction per ~73 cycles per SM sub-partition,
+// conversions included) bounds the sweeps, which need 3 FP64 operations per
+// cell (4 with periodic y).  The block therefore splits its warps: four
+// "sweep" warps run the chains and issue little besides FP64, while four
+// helper warps widen the FP32 spectrum to FP64 with integer field arithmetic
+// (fpconv.cuh) as its row groups arrive by bulk asynchronous copies, releasing
+// each group to the sweeps on an mbarrier.  All eight warps narrow the solution
+// at the end, which leaves by bulk copies as well.
 //
 // The singular zero mode pins x_0 = 0 through its tables (E_0 = C_0 = 0,
 // M_1 = 0, no coupling to row 0) and is shifted to zero hy-weighted mean (with
 // FP32 fields the shift, a constant invisible to the pressure gradient, is
 // applied after narrowing).
 //
-// Block: W columns (16 per warp, lanes 0..15 the upper and 16..31 the lower
-// threads); 3-D blocks are ordered so that the z positions t and nz - t, which
-// share every eigenvalue, run next to each other.
+// 3-D blocks are ordered so that the z positions t and nz - t, which share every
+// eigenvalue, run next to each other.
 struct YTwArgs {
   int nx, ny, nz, dim, xmode, nmx, nlz;
-  int L, k;              // chain rows 0..L-1; the upper thread owns rows 0..k
-  int pitch;             // table row pitch (>= ny, even)
+  int L, R;              // chain rows 0..L-1; positions per thread R = ceil(L / 2)
+  int nlp;               // table row pitch (eigenvalues, even, >= nlam + 2)
   int bulk;              // rows move by bulk copies (16-byte aligned rows and widths)
-  const double* M;       // [nlam][pitch] forward multipliers (negated), position order
-  const double* E;       // [nlam][pitch] inverse pivots
-  const double* C;       // [nlam][pitch] outward multipliers (negated)
-  const double* Z;       // [nlam][pitch] cyclic: z = A''^-1 u
+  const double* M;       // [2 U + 2 R + 2 U][nlp] forward multipliers (negated), position-major
+  const double* E;       // inverse pivots, same layout
+  const double* C;       // outward multipliers (negated)
+  const double* Z;       // cyclic: z = A''^-1 u
   const double* P;       // [nlam][4] inverse of the middle 2x2 system
   const double* S;       // [nlam][4] cyclic: S0, S1, S2
   const double* hy;      // cell widths (zero-mode mean)
   double hysum;
-  unsigned* status;      // device status word (bit 0: a bulk copy wait gave up)
+  unsigned* status;      // device status word (bit 0: a bulk copy or group wait gave up)
 };
+
+constexpr int kTwU = kTwChunk;   // rows per chunk of the twisted solve (tables fetched a chunk ahead)
 
 __device__ __forceinline__ int lam_of(int nx, int nz, int dim, int xmode, int nmx, int s, int t) {
   int mx;
@@ -838,22 +847,26 @@ __device__ __forceinline__ T narrow(double v) {
 
 template <typename T>
 size_t ytwist_smem(int ny, int w) {
-  return (size_t)ny * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0));
+  const size_t np = (size_t)ny + 1;   // 2 R positions <= ny + 1
+  return np * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0));
 }
 
 template <typename T, bool CYC, int W>
-__global__ void __launch_bounds__(2 * W) ytwist_kernel(T* __restrict__ data, const YTwArgs A) {
+__global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A) {
   constexpr bool F32 = sizeof(T) == 4;
-  constexpr int U = 16;                          // rows per chunk (tables fetched a chunk ahead)
-  constexpr int NG = 4;                          // tile row groups, each on its own barrier
+  constexpr int U = kTwU;
+  constexpr int NG = 4;                          // tile row groups: offsets [16 g, 16 g + 16), the last open
+  constexpr int NS = 2 * W;                      // sweep threads (warps 0 .. W / 16 - 1)
   constexpr unsigned FULL = 0xffffffffu;
   extern __shared__ __align__(16) unsigned char ytw_raw[];
-  const int ny = A.ny, L = A.L, k = A.k;
-  double* sg = reinterpret_cast<double*>(ytw_raw);   // [ny][W] FP64 eliminated / solved values, position order
-  T* st = F32 ? reinterpret_cast<T*>(ytw_raw + (size_t)ny * W * sizeof(double)) : reinterpret_cast<T*>(sg);
-  __shared__ uint64_t bar[NG];
-  const int tid = threadIdx.x, lane = tid & 31, half = lane >> 4;
-  const int cb = (tid >> 5) * 16 + (lane & 15);
+  const int ny = A.ny, L = A.L, R = A.R;
+  const int NP = 2 * R;                          // positions
+  const bool odd = (L & 1) != 0;                 // the lower thread's first position is the inert slot
+  double* sg = reinterpret_cast<double*>(ytw_raw);   // [NP][W] FP64, position order
+  T* st = F32 ? reinterpret_cast<T*>(ytw_raw + (size_t)(ny + 1) * W * sizeof(double)) : reinterpret_cast<T*>(sg);
+  constexpr int ND = 20;                         // output chunks of 16 positions (R <= 293 rows per thread)
+  __shared__ uint64_t bulkbar[NG], widebar[NG], donebar[ND];
+  const int tid = threadIdx.x, lane = tid & 31;
   const int s0 = blockIdx.x * W;
   const int ncol = min(W, A.nx - s0);
   int t = 0;
@@ -863,256 +876,266 @@ __global__ void __launch_bounds__(2 * W) ytwist_kernel(T* __restrict__ data, con
   }
   const size_t rs = (size_t)A.nx;
   T* tile = data + (size_t)A.nx * ny * t + s0;
-  auto pos = [&](int j) { return j <= k ? j : (j < L ? L + k - j : j); };
-  const int s = s0 + cb;
-  const bool act = cb < ncol;
-  const int li = act ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s, t) : 0;
-  const int P0 = half ? k + 1 : 0;             // first position of this thread
-  const int R = half ? L - 1 - k : k + 1;      // positions of this thread's elimination
-  const int RW = k + 1;                        // the upper thread's count (>= the lower's): warp-uniform trips
-  const size_t tb = (size_t)li * A.pitch + P0;
-  const double* __restrict__ Mt = A.M + tb;
-  // group of a row: by its offset from the first position of its thread (upper rows 0..k, lower
-  // rows from position k + 1; the bordered row last), cut at offsets 17, 33, 49 so that group g
-  // holds the chunk the elimination widens g-th
-  auto group = [&](int j) {
-    const int p = pos(j);
-    const int off = p >= L ? RW : (p <= k ? p : p - (k + 1));
-    return off < 17 ? 0 : min(NG - 1, (off - 1) >> 4);
-  };
-  // the first multipliers while the tile is in flight (tables do not depend on the predecessor)
-  double mn[U];
-#pragma unroll
-  for (int q = 0; q < U; ++q) mn[q] = (1 + q < R) ? __ldg(Mt + 1 + q) : 0.0;
+  // position of row j
+  auto pos = [&](int j) { return j < R ? j : (j < L ? R + (odd ? 1 : 0) + (L - 1 - j) : R); };
+  // row at position p (-1: the lower thread's inert slot on walls)
+  auto rowof = [&](int p) { return p < R ? p : (odd && p == R ? (CYC ? ny - 1 : -1) : L - 1 - (p - R - (odd ? 1 : 0))); };
+  // group of position p: its offset from its thread's first position, in chunks of 16
+  auto pgroup = [&](int p) { return min(NG - 1, (p < R ? p : p - R) >> 4); };
+  const uint32_t rb = (uint32_t)(ncol * sizeof(T));
+  const int nchunk = (R + U - 1) / U;
+  const bool zb = s0 == 0 && (A.dim == 2 || t == 0);   // the block holding the zero mode (column 0)
   bool ok = true;
-  if (A.bulk && tid == 0) {
-    for (int g = 0; g < NG; ++g) mbar_init(&bar[g], 1);
+  if (tid == 0) {
+    for (int g = 0; g < NG; ++g) {
+      mbar_init(&bulkbar[g], 1);
+      mbar_init(&widebar[g], W / 16);            // one arrival per helper warp
+    }
+    for (int c = 0; c < ND; ++c) mbar_init(&donebar[c], W / 16);   // one arrival per sweep warp
     mbar_init_fence();
   }
   __syncthreads();
-  pdl_wait();
-  const uint32_t rb = (uint32_t)(ncol * sizeof(T));
-  if (A.bulk) {
-    if (tid < 32) {
-      if (lane < NG) {
-        // rows of group g: offsets [lo, hi) of the upper (RW rows) and lower (L - RW rows) threads,
-        // and the bordered row (offset RW) in the group that holds offset RW
-        const int lo = lane == 0 ? 0 : 1 + 16 * lane, hi = lane == NG - 1 ? 1 << 30 : 17 + 16 * lane;
-        auto cnt = [&](int n) { return max(0, min(hi, n) - lo); };
-        int rows = cnt(RW) + cnt(L - RW);
-        if (CYC && RW >= lo && RW < hi) ++rows;
-        mbar_expect_tx(&bar[lane], rb * (uint32_t)rows);
-      }
-      __syncwarp();
-      // issue in group order so that the first rows needed land first
-      for (int g = 0; g < NG; ++g)
-        for (int j = lane; j < ny; j += 32)
-          if (group(j) == g) bulk_g2s(st + (size_t)pos(j) * W, tile + rs * j, rb, &bar[g]);
-    }
-  } else {
-#pragma unroll 8
-    for (int e = tid; e < ny * W; e += 2 * W) {
-      const int j = e / W, c = e - j * W;
-      if (c < ncol) st[pos(j) * W + c] = tile[rs * j + c];
-    }
-    __syncthreads();
-  }
-  auto wait_group = [&](int g) {
-    if (A.bulk) ok &= mbar_wait(&bar[min(g, NG - 1)], 0);
-  };
-  T* op = st + P0 * W + cb;                    // this thread's column of the tile, from its first position
-  double* gp = sg + P0 * W + cb;
-  // d at positions i0 .. i0 + U - 1 by the integer fast path (positions past R and inactive columns
-  // read as zero); `sp` collects the values outside it
-  auto widen_fast = [&](int i0, double (&out)[U], uint32_t& sp) {
+  if (tid < NS) {
+    // ---------------- sweep threads: two per column ----------------
+    const int half = lane >> 4;
+    const int cb = (tid >> 5) * 16 + (lane & 15);
+    const int s = s0 + cb;
+    const bool act = cb < ncol;
+    const int li = act ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s, t) : 0;
+    const int P0 = half ? R : 0;
+    const size_t nl = (size_t)A.nlp;
+    const size_t tb = (size_t)(2 * U + P0) * nl + li;
+    const double* __restrict__ Mt = A.M + tb;
+    // one buffer per table: a chunk's entries are consumed in order and each slot refilled with
+    // the entry a chunk further on
+    double mb[U];
 #pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      if constexpr (F32) {
-        const uint32_t u = (act && i < R) ? __float_as_uint(op[i * W]) : 0u;
-        uint32_t hi, lo;
-        fsconv_widen_fast(u, &hi, &lo, &sp);
-        out[q] = __hiloint2double((int)hi, (int)lo);
-      } else {
-        out[q] = (act && i < R) ? (double)op[i * W] : 0.0;
-      }
-    }
-  };
-  auto widen_fix = [&](int i0, double (&out)[U], uint32_t sp) {
-    if constexpr (F32) {
-      if (__any_sync(FULL, sp)) {
+    for (int q = 0; q < U; ++q) mb[q] = __ldg(Mt + q * nl);   // tables do not depend on the predecessor
+    double* gp = sg + P0 * W + cb;
+    // 1. elimination towards the middle; chunk c waits for its rows
+    double gv = 0.0;
+    for (int i0 = 0; i0 < R; i0 += U) {
+      ok &= mbar_wait(&widebar[min(NG - 1, i0 >> 4)], 0);
+      if (i0 + U <= R) {
+        // the chunk's values first, the chain in registers, the stores after: no store waits on
+        // the chain ahead of the next chunk's loads
+        double d[U], m[U];
 #pragma unroll
         for (int q = 0; q < U; ++q) {
-          const int i = i0 + q;
-          out[q] = (act && i < R) ? fsconv_widen(op[i * W]) : 0.0;
+          d[q] = gp[(i0 + q) * W];
+          m[q] = mb[q];
+          mb[q] = __ldg(Mt + (i0 + U + q) * nl);
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          gv = fma(m[q], gv, d[q]);
+          d[q] = gv;
+        }
+#pragma unroll
+        for (int q = 0; q < U; ++q) gp[(i0 + q) * W] = d[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          if (i0 + q < R) {
+            gv = fma(mb[q], gv, gp[(i0 + q) * W]);
+            gp[(i0 + q) * W] = gv;
+          }
         }
       }
     }
-  };
-  // FP64 value v of position i narrowed into the tile by the fast path
-  auto narrow_fast = [&](int i, double v, uint32_t& sp) {
-    if constexpr (F32) {
-      const uint32_t r = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
-      if (i >= 0 && i < R) op[i * W] = __uint_as_float(r);
+    // 2. the middle rows (each thread's last position)
+    const double oth = __shfl_xor_sync(FULL, gv, 16);
+    const double gk = half ? oth : gv, hk = half ? gv : oth;
+    const double* Pt = A.P + (size_t)li * 4 + 2 * half;
+    double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
+    gp[(R - 1) * W] = xv;
+    // 3. outward substitution, positions descending
+    {
+      const double* __restrict__ Et = A.E + tb;
+      const double* __restrict__ Ct = A.C + tb;
+      double eb[U], cbuf[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        eb[q] = __ldg(Et + (R - 2 - q) * (ptrdiff_t)nl);
+        cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
+      }
+      int next = nchunk - 1;                     // walls: highest output chunk not yet released
+      for (int i0 = R - 2; i0 >= 0; i0 -= U) {
+        if (i0 + 1 >= U) {
+          // products E g first (independent), the chain in registers, the stores after
+          double v[U], c2[U];
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            v[q] = eb[q] * gp[(i0 - q) * W];
+            c2[q] = cbuf[q];
+            eb[q] = __ldg(Et + (i0 - U - q) * (ptrdiff_t)nl);
+            cbuf[q] = __ldg(Ct + (i0 - U - q) * (ptrdiff_t)nl);
+          }
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            xv = fma(c2[q], xv, v[q]);
+            v[q] = xv;
+          }
+#pragma unroll
+          for (int q = 0; q < U; ++q) gp[(i0 - q) * W] = v[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            if (q <= i0) {
+              const double eg = eb[q] * gp[(i0 - q) * W];
+              xv = fma(cbuf[q], xv, eg);
+              gp[(i0 - q) * W] = xv;
+            }
+          }
+        }
+        if constexpr (!CYC) {
+          // positions max(i0 - U + 1, 0) .. R - 1 are final: hand their chunks to the helpers
+          const int lowest = max(i0 - U + 1, 0);
+          __syncwarp();
+          while (next >= 0 && U * next >= lowest) {
+            if (lane == 0) mbar_arrive(&donebar[next]);
+            --next;
+          }
+        }
+      }
+      if constexpr (!CYC) {
+        __syncwarp();
+        for (; next >= 0; --next)
+          if (lane == 0) mbar_arrive(&donebar[next]);
+      }
+    }
+    pdl_trigger();
+    if constexpr (CYC) {
+      // 4. the bordered row ny - 1 (the lower thread's inert slot, still d_{ny-1}), then x = y - xi z
+      const double yl_own = gp[W];                       // lower: row L - 1 at its second position
+      const double o2 = __shfl_xor_sync(FULL, half ? yl_own : xv, 16);
+      const double y0 = half ? o2 : xv, yl = half ? yl_own : o2;
+      const double dl = __shfl_xor_sync(FULL, gp[0], 16);  // the lower's inert slot, seen by the upper
+      const double dlast = half ? gp[0] : dl;
+      const double* St = A.S + (size_t)li * 4;
+      const double xi = fma(-__ldg(St + 1), yl, fma(-__ldg(St), y0, dlast)) * __ldg(St + 2);
+      const double* __restrict__ Zt = A.Z + tb;
+      double zb[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) zb[q] = __ldg(Zt + q * nl);
+      for (int i0 = 0; i0 < R; i0 += U) {
+        double v[U];
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          v[q] = fma(-xi, zb[q], gp[min(i0 + q, R - 1) * W]);
+          zb[q] = __ldg(Zt + (i0 + U + q) * nl);
+        }
+        if (half && i0 == 0) v[0] = xi;          // the inert slot becomes x_{ny-1}
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (i0 + q < R) gp[(i0 + q) * W] = v[q];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&donebar[i0 / U]);   // the helpers narrow this chunk meanwhile
+      }
+    }
+  } else {
+    // ---------------- helper threads: tile in, widened, group by group ----------------
+    const int h = tid - NS;                      // 0 .. 2 W - 1
+    const int hc = h % W, hw = h / W;            // this helper's column and row parity
+    if (h >= 32) {
+      // the block's table segments into L2 while the tile is in flight (the sweeps' chunk-ahead
+      // register fetches then wait on L2, not on DRAM): per position, the eigenvalues of the
+      // block's slots at its z wavenumber, one bulk prefetch per table
+      const int lzb = A.dim == 3 ? min(t, A.nz - t) : 0;
+      const int mx0 = A.xmode == 1 ? s0 : s0 / 2;
+      const int span = A.xmode == 1 ? W : W / 2 + 1;
+      const size_t nl = (size_t)A.nlp;
+      const size_t first = ((size_t)lzb * A.nmx + mx0) & ~(size_t)1;
+      const uint32_t bytes = (uint32_t)((span + 2) & ~1) * sizeof(double);
+      for (int p = h - 32; p < 2 * R; p += NS - 32) {
+        const size_t o = (size_t)(2 * U + p) * nl + first;
+        bulk_prefetch_l2(A.M + o, bytes);
+        bulk_prefetch_l2(A.E + o, bytes);
+        bulk_prefetch_l2(A.C + o, bytes);
+        if constexpr (CYC) bulk_prefetch_l2(A.Z + o, bytes);
+      }
+    }
+    pdl_wait();
+    if (A.bulk) {
+      if (h < 32) {
+        if (lane < NG) {
+          // positions of group g in each half: offsets [16 g, 16 g + 16) (the last group open), minus
+          // the lower's inert slot when it holds no row
+          const int lo = 16 * lane, hi = lane == NG - 1 ? R : min(R, 16 * lane + 16);
+          int rows = 2 * max(0, hi - lo);
+          if (odd && !CYC && lane == 0) --rows;
+          mbar_expect_tx(&bulkbar[lane], rb * (uint32_t)rows);
+        }
+        __syncwarp();
+        for (int g = 0; g < NG; ++g)
+          for (int j = lane; j < ny; j += 32)
+            if (pgroup(pos(j)) == g) bulk_g2s(st + (size_t)pos(j) * W, tile + rs * j, rb, &bulkbar[g]);
+      }
+      for (int g = 0; g < NG; ++g) {
+        ok &= mbar_wait(&bulkbar[g], 0);
+        // the group's positions: [16 g, ...) in each half
+        const int lo = 16 * g, hi = g == NG - 1 ? R : min(R, 16 * g + 16);
+        const int n = max(0, hi - lo);
+        // this thread: column h % W, rows h / W + 2 k of the group's 2 n (upper n, then lower n)
+        for (int r = hw; r < 2 * n; r += 2) {
+          const int p = r < n ? lo + r : R + lo + (r - n);
+          const bool hole = odd && !CYC && p == R;
+          if constexpr (F32) {
+            const uint32_t u = (hc < ncol && !hole) ? __float_as_uint(st[p * W + hc]) : 0u;
+            uint32_t whi, wlo, sp = 0;
+            fsconv_widen_fast(u, &whi, &wlo, &sp);
+            sg[p * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) : __hiloint2double((int)whi, (int)wlo);
+          } else if (hc >= ncol || hole) {
+            sg[p * W + hc] = 0.0;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&widebar[g]);
+      }
     } else {
-      if (i >= 0 && i < R) op[i * W] = v;
-    }
-  };
-  // 1. elimination towards the middle; the next chunk is widened (fast path) and its multipliers
-  // fetched while the chain runs, its exceptional values redone after
-  wait_group(0);
-  double gv = act ? widen<T>(op[0]) : 0.0;
-  gp[0] = gv;
-  double dn[U];
-  {
-    uint32_t sp = 0;
-    widen_fast(1, dn, sp);
-    widen_fix(1, dn, sp);
-  }
-  int c = 0;
-  for (int i0 = 1; i0 < RW; i0 += U, ++c) {
-    double mc[U], dc[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      mc[q] = mn[q];
-      dc[q] = dn[q];
-      mn[q] = (i0 + U + q < R) ? __ldg(Mt + i0 + U + q) : 0.0;
-    }
-    const bool more = i0 + U < RW;
-    if (more) wait_group(c + 1);
-    uint32_t sp = 0;
-    if (more) widen_fast(i0 + U, dn, sp);
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = i0 + q;
-      if (i < R) {
-        gv = fma(mc[q], gv, dc[q]);
-        gp[i * W] = gv;
+      // plain loads, widened straight into their positions
+      for (int e = h; e < NP * W; e += NS) {
+        const int p = e / W, c = e - p * W;
+        const int j = rowof(p);
+        sg[e] = (c < ncol && j >= 0) ? widen<T>(tile[rs * j + c]) : 0.0;
       }
+      asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");   // every helper's rows are in
+      if (lane == 0)
+        for (int g = 0; g < NG; ++g) mbar_arrive(&widebar[g]);
     }
-    if (more) widen_fix(i0 + U, dn, sp);
-  }
-  // 2. the middle rows k (upper's last position) and k+1 (lower's last)
-  const double oth = __shfl_xor_sync(FULL, gv, 16);
-  const double gk = half ? oth : gv, hk = half ? gv : oth;
-  const double* Pt = A.P + (size_t)li * 4 + 2 * half;
-  double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
-  gp[(R - 1) * W] = xv;
-  // 3. outward substitution, step m at position R - 2 - m (walls: narrowed as they are solved)
-  {
-    const double* __restrict__ Et = A.E + tb;
-    const double* __restrict__ Ct = A.C + tb;
-    double en[U], cn[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int i = R - 2 - q;
-      en[q] = i >= 0 ? __ldg(Et + i) : 0.0;
-      cn[q] = i >= 0 ? __ldg(Ct + i) : 0.0;
-    }
-    for (int m0 = 0; m0 < RW - 1; m0 += U) {
-      double ec[U], cc[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        ec[q] = en[q];
-        cc[q] = cn[q];
-        const int i = R - 2 - (m0 + U + q);
-        en[q] = i >= 0 ? __ldg(Et + i) : 0.0;
-        cn[q] = i >= 0 ? __ldg(Ct + i) : 0.0;
-      }
-      uint32_t sp = 0;
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int i = R - 2 - (m0 + q);
-        if (i >= 0) {
-          const double eg = ec[q] * gp[i * W];
-          xv = fma(cc[q], xv, eg);
-          gp[i * W] = xv;
-        }
-        if constexpr (!CYC && F32) narrow_fast(i, xv, sp);
-      }
-      if constexpr (!CYC && F32) {
-        if (__any_sync(FULL, sp)) {
-#pragma unroll
-          for (int q = 0; q < U; ++q) {
-            const int i = R - 2 - (m0 + q);
-            if (i >= 0) op[i * W] = fsconv_narrow(gp[i * W]);
+    // the solution out, chunk by chunk as the sweeps finish it: narrowed, row-coalesced (the zero
+    // mode's column waits for its mean, below)
+    const bool mine = hc < ncol && !(zb && hc == 0);
+    for (int c = 0; c < nchunk; ++c) {
+      ok &= mbar_wait(&donebar[c], 0);
+      const int lo = U * c, n = min(U, R - lo);
+      // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r
+#pragma unroll 4
+      for (int r = hw; r < 2 * n; r += 2) {
+        const int p = r < n ? lo + r : R + lo + (r - n);
+        const int j = rowof(p);
+        if (mine && j >= 0) {
+          const double v = sg[p * W + hc];
+          if constexpr (F32) {
+            uint32_t sp = 0;
+            const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
+            tile[rs * j + hc] = sp ? fsconv_narrow(v) : __uint_as_float(o);
+          } else {
+            tile[rs * j + hc] = v;
           }
         }
       }
     }
   }
-  pdl_trigger();
-  if constexpr (CYC) {
-    // 4. the bordered row ny - 1 (position ny - 1), then x = y - xi z, narrowed
-    for (int g = 1; g < NG; ++g) wait_group(g);   // the bordered row's group (already complete but for short columns)
-    const double o2 = __shfl_xor_sync(FULL, xv, 16);
-    const double y0 = half ? o2 : xv, yl = half ? xv : o2;   // positions 0 and k + 1
-    const double* St = A.S + (size_t)li * 4;
-    T* lastp = st + (size_t)(ny - 1) * W + cb;
-    const double dl = act ? widen<T>(*lastp) : 0.0;
-    const double xi = fma(-__ldg(St + 1), yl, fma(-__ldg(St), y0, dl)) * __ldg(St + 2);
-    const double* __restrict__ Zt = A.Z + tb;
-    double zn[U];
-#pragma unroll
-    for (int q = 0; q < U; ++q) zn[q] = q < R ? __ldg(Zt + q) : 0.0;
-    for (int i0 = 0; i0 < RW; i0 += U) {
-      double zc[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        zc[q] = zn[q];
-        zn[q] = i0 + U + q < R ? __ldg(Zt + i0 + U + q) : 0.0;
-      }
-      uint32_t sp = 0;
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int i = i0 + q;
-        narrow_fast(i, fma(-xi, zc[q], i < R ? gp[i * W] : 0.0), sp);
-      }
-      if constexpr (F32) {
-        if (__any_sync(FULL, sp)) {
-#pragma unroll
-          for (int q = 0; q < U; ++q) {
-            const int i = i0 + q;
-            if (i < R) op[i * W] = fsconv_narrow(fma(-xi, zc[q], gp[i * W]));
-          }
-        }
-      }
-    }
-    __syncwarp();
-    if (half) *lastp = narrow<T>(xi);
-  } else {
-    // walls: the middle position, which the outward sweep does not cover
-    if constexpr (F32) op[(R - 1) * W] = fsconv_narrow(gp[(R - 1) * W]);
-  }
-  // 5. zero mode: hy-weighted mean of its column (column 0 of the block holding s = 0, t = 0),
-  // subtracted in the field precision
-  const bool zb = s0 == 0 && (A.dim == 2 || t == 0);
   __syncthreads();
-  if (zb) {
-    if (tid < 32) {
-      T part = 0;
-      for (int j = lane; j < ny; j += 32) part += (T)__ldg(A.hy + j) * st[pos(j) * W];
+  // 5. zero mode: hy-weighted mean of its column, subtracted (in the field precision) as it leaves
+  if (zb && tid < 32) {
+    double part = 0.0;
+    for (int j = lane; j < ny; j += 32) part = fma(__ldg(A.hy + j), sg[pos(j) * W], part);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-      const T zm = part / (T)A.hysum;
-      for (int p = lane; p < ny; p += 32) st[p * W] -= zm;
-    }
-    __syncthreads();
-  }
-  if (A.bulk) {
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid < 32) {
-      for (int j = lane; j < ny; j += 32) bulk_s2g(tile + rs * j, st + (size_t)pos(j) * W, rb);
-      bulk_s2g_commit();
-      bulk_s2g_wait();
-    }
-  } else {
-#pragma unroll 8
-    for (int e = tid; e < ny * W; e += 2 * W) {
-      const int j = e / W, c2 = e - j * W;
-      if (c2 < ncol) tile[rs * j + c2] = st[pos(j) * W + c2];
-    }
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    const T zm = (T)(part / A.hysum);
+    for (int j = lane; j < ny; j += 32) tile[rs * j] = narrow<T>(sg[pos(j) * W]) - zm;
   }
   if (!ok) atomicOr(A.status, 1u);   // part of the tile never arrived: this block's columns are invalid
 }
@@ -1521,8 +1544,8 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.nmx = G->nmx;
     A.nlz = G->nlz;
     A.L = G->ytw_L;
-    A.k = G->ytw_k;
-    A.pitch = G->ytw_pitch;
+    A.R = G->ytw_R;
+    A.nlp = G->ytw_nlp;
     A.M = G->twM;
     A.E = G->twE;
     A.C = G->twC;
@@ -1538,11 +1561,11 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     const dim3 grid((nx + w - 1) / w, G->dim == 3 ? nz : 1);
     const size_t sb = ytwist_smem<T>(ny, w);
     if (w == 64) {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(128), sb, data, A);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(128), sb, data, A);
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(256), sb, data, A);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(256), sb, data, A);
     } else {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(64), sb, data, A);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(64), sb, data, A);
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(128), sb, data, A);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(128), sb, data, A);
     }
   } else {
     YArgs A;
