@@ -50,7 +50,8 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50367232 + 864768, "src": "8165a552c6a7"},
+    "predictor": {"bytes": 50361856 + 835072, "src": "d0c04e2fd11e"},
+    "ysolve": {"bytes": 27249408 + 0, "src": "b15fd835e28b"},
     "fft_x_fwd_div": {"bytes": 25243392 + 0, "src": "7895d4f893d7"},
     "fft_z_fwd": {"bytes": 8407040 + 0, "src": "7895d4f893d7"},
     "fft_y_solve": {"bytes": 8435200 + 0, "src": "7895d4f893d7"},
@@ -65,6 +66,8 @@ NCU_TRAFFIC = {
 KERNEL_SOURCES = {
     "predictor": ("stencil.cu", "// Staged z-marching predictor", "if (!ok) atomicOr(status, 1u);", ["tma.cuh"]),
     "correct": ("stencil.cu", "__global__ void __launch_bounds__(kThreads) correct4_kernel", "\n}\n", []),
+    "ysolve": ("poisson.cu", "// y solve for grids with many columns", "// Periodic y: the columns",
+               ["fpconv.cuh", "tma.cuh"]),
     "fft": ("fft_reg.cuh", "", "", []),
 }
 
@@ -353,15 +356,20 @@ def run_ours(args, ws, rank, local):
                 "timing": timing, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     if dominant == "ysolve":
-        # the FP64 partitioned tridiagonal is bound by the FP64 rate: 9 flops per cell (forward sweep
-        # 3, backward 2, spike correction 4) against the B300's nominal 1.25 TFLOP/s FP64 (no FP64
-        # peak is measured on this machine)
-        flops = 9.0
+        # the FP64 y solve is bound by the FP64 pipe.  Algorithmic flops per cell of the cyclic
+        # twisted solve (periodic y): forward multiply-add 2, outward multiply + multiply-add 3,
+        # cyclic correction multiply-add 2 = 7 (the wall-bounded chain has no correction: 5).
+        # Peak: B300's nominal FP64 rate, 1.25 TFLOP/s (no FP64 peak is measured on this machine; a
+        # timing probe of independent DFMA chains reached 1.06 TFLOP/s at 2032 MHz)
+        flops = 7.0 if wl.bc[1][0] == S.PERIODIC else 5.0
         ach = flops * cells / (kms / cnt * 1e-3) / 1e12 if cnt else None
+        tr = NCU_TRAFFIC.get(dominant)
         roofline = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
-                    "frac": ach / 1.25 if ach else None, "traffic": None, "flops_per_cell": flops,
+                    "frac": ach / 1.25 if ach else None,
+                    "traffic": tr["bytes"] if tr and tr.get("src") == src_hash(dominant) else None,
+                    "flops_per_cell": flops,
                     "launches": cnt, "avg_launch_us": kms / cnt * 1e3 if cnt else None, "timing": timing,
-                    "peak_source": "nominal FP64 rate (1.25 TFLOP/s)"}
+                    "peak_source": "nominal FP64 rate (1.25 TFLOP/s); a DFMA timing probe reached 1.06"}
     else:
         roofline = hbm_roofline(dominant)
     stencil_roofline = hbm_roofline("predictor") if dominant != "predictor" else None
