@@ -288,6 +288,11 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     128 or 256 the predictor stages its input planes in
  *                     shared memory with bulk asynchronous copies; 0: it reads
  *                     them from global memory (four-cell z-marching kernel)
+ *   "predictor_chunk" staged predictor work split: 0 (default) equal shares of
+ *                     the (row block, plane) units for grids whose three
+ *                     velocity fields fit in 64 MB, else runs of planes aligned
+ *                     across row blocks (about two blocks per SM); -1 equal
+ *                     shares; N > 0 aligned runs of N planes
  *   "y_spectral"      periodic y only: 1 (default) DFT along y in the grid's
  *                     field precision, zero mode exact; 0: the FP64 cyclic
  *                     tridiagonal solve per x/z wavenumber (rebuilds the y

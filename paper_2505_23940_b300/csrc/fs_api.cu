@@ -834,6 +834,9 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "predictor_staged") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "predictor_staged must be 0 or 1");
     G->tune_staged = value == 1;
+  } else if (k == "predictor_chunk") {
+    if (value < -1 || value > G->nz) return set_error(FS_ERR_ARG, "predictor_chunk must be -1 .. nz");
+    G->tune_pred_chunk = value;
   } else if (k == "y_spectral") {
     // periodic y: 1 (default) DFT along y in the field precision with the exact zero mode;
     // 0 the FP64 cyclic tridiagonal solve per x/z wavenumber (the wall-normal path)

@@ -297,6 +297,7 @@ struct fs_grid {
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
   int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
   bool tune_staged = true;                // shared-memory staged predictor where it applies
+  int tune_pred_chunk = 0;                // staged predictor runs: 0 by grid size, -1 equal shares, > 0 aligned runs
   // twisted y solve (grids with many columns): two threads per column, tables per eigenvalue
   int ytwist = 0;                         // 1: the twisted solve runs instead of the partitioned one
   int tune_ytwist = -1;                   // -1: chosen from the grid's shape, 0: off, 1: on where it fits

@@ -324,12 +324,14 @@ def test_mixed_periodic_transform_shapes(n):
     assert d["divmax"] < 1e-3 * d["umax"] * max(n)
 
 
-@pytest.mark.parametrize("n,kz", [((128, 16, 8), 8), ((128, 14, 10), 8), ((128, 10, 12), 5), ((256, 6, 6), 4),
-                                  ((256, 12, 6), 1)])
-def test_mixed_staged_predictor(n, kz):
+@pytest.mark.parametrize("n,kz,chunk", [((128, 16, 8), 8, 0), ((128, 14, 10), 8, 0), ((128, 10, 12), 5, 0),
+                                        ((256, 6, 6), 4, 0), ((256, 12, 6), 1, 0),
+                                        ((128, 14, 10), 8, 3), ((256, 12, 8), 4, 3), ((128, 10, 12), 5, 5)])
+def test_mixed_staged_predictor(n, kz, chunk):
     """The shared-memory staged predictor (bulk asynchronous copies of whole
-    planes; n_x = 128 / 256, ragged y blocks and z chunks, plane ring reuse)
-    against the FP64 oracle and against the unstaged z-marching kernel."""
+    planes; n_x = 128 / 256, ragged y blocks and z chunks, plane ring reuse; equal
+    shares of the units (chunk 0 on these small grids) and runs aligned across row
+    blocks, ragged last run) against the FP64 oracle and the unstaged z-marching kernel."""
     from paper_2505_23940_b300 import grid_from_workload
     L = (1.0, 0.8, 1.2)
     wl = S.box_3d(*n, (P, P), (P, P), L=L, nu=0.001)
@@ -342,6 +344,7 @@ def test_mixed_staged_predictor(n, kz):
         g = grid_from_workload(wl, "mixed")
         g.set_tuning("predictor_zmarch", kz)
         g.set_tuning("predictor_staged", staged)
+        g.set_tuning("predictor_chunk", chunk)
         u = [torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous() for a in wl.u0]
         g.step(u, wl.dt, 3)
         assert g.device_status() == 0
