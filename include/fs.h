@@ -303,6 +303,9 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     (y_spectral = 0) when the grid has at least 148 * 64
  *                     columns (n_x n_z) and ny <= 148.  Rebuilds the y tables
  *                     (synchronises the stream)
+ *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
+ *                     least 32 rows as 32-row tensor-map boxes; 0: one bulk
+ *                     copy per row
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
  *                     grid has fewer 32-column blocks than two per SM, else 4);

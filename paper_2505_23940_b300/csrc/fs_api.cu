@@ -863,6 +863,9 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
     free_ytables(G);
     return build_tables(G);
+  } else if (k == "ysolve_tiled") {
+    if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "ysolve_tiled must be 0 or 1");
+    G->tune_ytile = value == 1;
   } else if (k == "ysolve_twisted") {
     if (value < -1 || value > 1) return set_error(FS_ERR_ARG, "ysolve_twisted must be -1, 0 or 1");
     if (value == G->tune_ytwist) return FS_OK;

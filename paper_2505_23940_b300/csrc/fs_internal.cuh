@@ -302,6 +302,11 @@ struct fs_grid {
   int ytwist = 0;                         // 1: the twisted solve runs instead of the partitioned one
   int tune_ytwist = -1;                   // -1: chosen from the grid's shape, 0: off, 1: on where it fits
   int ytw_cols = 64;                      // columns per block (64 or 32)
+  alignas(64) unsigned char ytw_map[128] = {};   // tensor map of the FP32 spectrum (CUtensorMap bytes)
+  const void* ytw_map_ptr = nullptr;      // array and block width the map was encoded for
+  int ytw_map_w = 0;
+  bool ytw_map_ok = false;
+  bool tune_ytile = true;                 // twisted solve: tensor-map tile loads where they apply
   int ytw_L = 0, ytw_R = 0;               // chain rows 0..L-1, positions per thread R = ceil(L / 2)
   int ytw_nlp = 0;                        // row pitch (eigenvalues) of the position-major tables
   double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [2 R + 4 kTwChunk][nlp], position-major

@@ -19,10 +19,12 @@
 // one complex line per group of butterflies, whole lines resident per CTA.
 // Precision: the field type T for transforms (FP32 in mixed mode), FP64 for the
 // tridiagonal elimination in both modes.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "fs_internal.cuh"
@@ -812,6 +814,7 @@ struct YTwArgs {
   int L, R;              // chain rows 0..L-1; positions per thread R = ceil(L / 2)
   int nlp;               // table row pitch (eigenvalues, even, >= nlam + 2)
   int bulk;              // rows move by bulk copies (16-byte aligned rows and widths)
+  int tiled;             // FP32: the tile arrives as 32-row boxes of the tensor map (row order)
   const double* M;       // [2 U + 2 R + 2 U][nlp] forward multipliers (negated), position-major
   const double* E;       // inverse pivots, same layout
   const double* C;       // outward multipliers (negated)
@@ -848,24 +851,30 @@ __device__ __forceinline__ T narrow(double v) {
 template <typename T>
 size_t ytwist_smem(int ny, int w) {
   const size_t np = (size_t)ny + 1;   // 2 R positions <= ny + 1
-  return np * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0));
+  return np * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0)) + 128;   // + alignment slack
 }
 
+constexpr int kTwBoxRows = 32;   // rows per tensor-map box of the twisted solve's tile
+
 template <typename T, bool CYC, int W>
-__global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A) {
+__global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A,
+                                                          const __grid_constant__ CUtensorMap tmap) {
   constexpr bool F32 = sizeof(T) == 4;
   constexpr int U = kTwU;
   constexpr int NG = 4;                          // tile row groups: offsets [16 g, 16 g + 16), the last open
   constexpr int NS = 2 * W;                      // sweep threads (warps 0 .. W / 16 - 1)
   constexpr unsigned FULL = 0xffffffffu;
-  extern __shared__ __align__(16) unsigned char ytw_raw[];
+  extern __shared__ __align__(128) unsigned char ytw_smem[];
+  // 128-byte aligned base (tensor-map box destinations); the launch adds 128 bytes for it
+  unsigned char* ytw_raw = ytw_smem + ((128u - (smem_u32(ytw_smem) & 127u)) & 127u);
   const int ny = A.ny, L = A.L, R = A.R;
   const int NP = 2 * R;                          // positions
   const bool odd = (L & 1) != 0;                 // the lower thread's first position is the inert slot
   double* sg = reinterpret_cast<double*>(ytw_raw);   // [NP][W] FP64, position order
   T* st = F32 ? reinterpret_cast<T*>(ytw_raw + (size_t)(ny + 1) * W * sizeof(double)) : reinterpret_cast<T*>(sg);
   constexpr int ND = 20;                         // output chunks of 16 positions (R <= 293 rows per thread)
-  __shared__ uint64_t bulkbar[NG], widebar[NG], donebar[ND];
+  constexpr int NB = 20;                         // tensor-map boxes (ny <= 640)
+  __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
   const int tid = threadIdx.x, lane = tid & 31;
   const int s0 = blockIdx.x * W;
   const int ncol = min(W, A.nx - s0);
@@ -884,10 +893,11 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   auto pgroup = [&](int p) { return min(NG - 1, (p < R ? p : p - R) >> 4); };
   const uint32_t rb = (uint32_t)(ncol * sizeof(T));
   const int nchunk = (R + U - 1) / U;
+  const int nbox = (ny + kTwBoxRows - 1) / kTwBoxRows, nlev = (nbox + 1) / 2;
   const bool zb = s0 == 0 && (A.dim == 2 || t == 0);   // the block holding the zero mode (column 0)
   bool ok = true;
   if (tid == 0) {
-    for (int g = 0; g < NG; ++g) {
+    for (int g = 0; g < NB; ++g) {
       mbar_init(&bulkbar[g], 1);
       mbar_init(&widebar[g], W / 16);            // one arrival per helper warp
     }
@@ -915,7 +925,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // 1. elimination towards the middle; chunk c waits for its rows
     double gv = 0.0;
     for (int i0 = 0; i0 < R; i0 += U) {
-      ok &= mbar_wait(&widebar[min(NG - 1, i0 >> 4)], 0);
+      // tiled: level l (two boxes, 32 rows from each end) holds chunks 2 l, 2 l + 1
+      ok &= mbar_wait(&widebar[A.tiled ? min(nlev - 1, i0 >> 5) : min(NG - 1, i0 >> 4)], 0);
       if (i0 + U <= R) {
         // the chunk's values first, the chain in registers, the stores after: no store waits on
         // the chain ahead of the next chunk's loads
@@ -1037,10 +1048,12 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // ---------------- helper threads: tile in, widened, group by group ----------------
     const int h = tid - NS;                      // 0 .. 2 W - 1
     const int hc = h % W, hw = h / W;            // this helper's column and row parity
-    if (h >= 32) {
-      // the block's table segments into L2 while the tile is in flight (the sweeps' chunk-ahead
-      // register fetches then wait on L2, not on DRAM): per position, the eigenvalues of the
-      // block's slots at its z wavenumber, one bulk prefetch per table
+    if (h >= 32 && !A.tiled) {
+      // row copies: the block's table segments into L2 while the tile is in flight (the sweeps'
+      // chunk-ahead register fetches then wait on L2, not on DRAM): per position, the eigenvalues
+      // of the block's slots at its z wavenumber, one bulk prefetch per table.  (With the tile as
+      // tensor-map boxes these requests, sharing the SM's copy engine, delay the boxes more than
+      // they save: 0.269 against 0.259 ms per 128^3 step.)
       const int lzb = A.dim == 3 ? min(t, A.nz - t) : 0;
       const int mx0 = A.xmode == 1 ? s0 : s0 / 2;
       const int span = A.xmode == 1 ? W : W / 2 + 1;
@@ -1056,7 +1069,43 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       }
     }
     pdl_wait();
-    if (A.bulk) {
+    if (A.tiled) {
+      // boxes of 32 rows in row order, from both ends of the column inward (the rows each
+      // thread's elimination needs first): box b is the top (b even) or bottom (b odd) box of
+      // level b / 2; the stage buffer holds the tile in row order
+      auto box_row = [&](int b) {
+        const int l = b >> 1;
+        return (b & 1) ? max(0, ny - kTwBoxRows * (l + 1)) : kTwBoxRows * l;
+      };
+      if (h == 0) {
+        for (int b = 0; b < nbox; ++b) {
+          mbar_expect_tx(&bulkbar[b], (uint32_t)(kTwBoxRows * W * sizeof(T)));
+          const int r0 = box_row(b);
+          tensor_g2s_3d(st + (size_t)r0 * W, &tmap, s0, r0, t, &bulkbar[b]);
+        }
+      }
+      if (odd && !CYC) sg[R * W + (h % W)] = 0.0;   // the lower thread's inert slot holds no row
+      for (int l = 0; l < nlev; ++l) {
+        for (int b = 2 * l; b < min(2 * l + 2, nbox); ++b) {
+          ok &= mbar_wait(&bulkbar[b], 0);
+          // the rows this box is the first to bring (boxes overlap on ragged columns, and a row
+          // the sweeps may already be eliminating in place must not be widened again): the top box
+          // of level l owns [32 l, min(32 l + 32, ny - 32 l)), the bottom box
+          // [max(32 (l + 1), ny - 32 (l + 1)), ny - 32 l)
+          const int a0 = (b & 1) ? max(kTwBoxRows * (l + 1), ny - kTwBoxRows * (l + 1)) : kTwBoxRows * l;
+          const int a1 = (b & 1) ? ny - kTwBoxRows * l : min(kTwBoxRows * (l + 1), ny - kTwBoxRows * l);
+          // this thread: column h % W, rows a0 + h / W + 2 k
+          for (int j = a0 + hw; j < a1; j += 2) {
+            const uint32_t u = __float_as_uint(st[j * W + hc]);
+            uint32_t whi, wlo, sp = 0;
+            fsconv_widen_fast(u, &whi, &wlo, &sp);
+            sg[pos(j) * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) : __hiloint2double((int)whi, (int)wlo);
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&widebar[l]);
+      }
+    } else if (A.bulk) {
       if (h < 32) {
         if (lane < NG) {
           // positions of group g in each half: offsets [16 g, 16 g + 16) (the last group open), minus
@@ -1465,6 +1514,32 @@ size_t ysolve_smem(int ny, int nseg, int yc) {
   return ((size_t)ny * yc + (size_t)yc * 3 * nseg + staged) * sizeof(double);
 }
 
+// 3-D tensor map of an FP32 spectrum array [nz][ny][nx] with boxes of w slots x kTwBoxRows rows,
+// for the twisted y solve's tile loads; false when the driver's encoder is unavailable or rejects it
+bool encode_spectrum_map(CUtensorMap* map, const float* data, int nx, int ny, int nz, int w) {
+  using Encode = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  static Encode enc = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = reinterpret_cast<Encode>(fn);
+  }
+  if (!enc) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)nx * sizeof(float), (cuuint64_t)nx * ny * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)w, (cuuint32_t)kTwBoxRows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(data), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <typename T>
 void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   set_smem_attrs<T>();
@@ -1558,14 +1633,32 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     // rows move by bulk copies when every row start and width is a multiple of 16 bytes
     A.bulk = (nx * (int)sizeof(T)) % 16 == 0 && reinterpret_cast<uintptr_t>(data) % 16 == 0;
     const int w = G->ytw_cols;
+    // FP32 tiles of at least one box of rows arrive as tensor-map boxes (a few large copies
+    // instead of one bulk copy per row); the map is encoded once per spectrum array
+    CUtensorMap tmap;
+    std::memset(&tmap, 0, sizeof(tmap));
+    A.tiled = 0;
+    if (sizeof(T) == 4 && A.bulk && ny >= kTwBoxRows && G->tune_ytile) {
+      const int nzt = G->dim == 3 ? nz : 1;
+      if (G->ytw_map_ptr != (const void*)data || G->ytw_map_w != w) {
+        G->ytw_map_ok = encode_spectrum_map(reinterpret_cast<CUtensorMap*>(G->ytw_map), (const float*)data, nx, ny,
+                                            nzt, w);
+        G->ytw_map_ptr = data;
+        G->ytw_map_w = w;
+      }
+      if (G->ytw_map_ok) {
+        std::memcpy(&tmap, G->ytw_map, sizeof(tmap));
+        A.tiled = 1;
+      }
+    }
     const dim3 grid((nx + w - 1) / w, G->dim == 3 ? nz : 1);
     const size_t sb = ytwist_smem<T>(ny, w);
     if (w == 64) {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(256), sb, data, A);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(256), sb, data, A);
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(256), sb, data, A, tmap);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(256), sb, data, A, tmap);
     } else {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(128), sb, data, A);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(128), sb, data, A);
+      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(128), sb, data, A, tmap);
+      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(128), sb, data, A, tmap);
     }
   } else {
     YArgs A;

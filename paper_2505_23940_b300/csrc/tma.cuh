@@ -48,6 +48,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                : "memory");
 }
 
+// tiled 3-D load of one box of a tensor map (coordinates x innermost; x times the element size a
+// multiple of 16 bytes), completing on an mbarrier; elements outside the tensor read as zero
+__device__ __forceinline__ void tensor_g2s_3d(void* dst, const void* tmap, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::
+          "r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // shared -> global bulk copy (bulk-group completion); the source must not change until
 // bulk_s2g_wait() returns in the issuing thread
 __device__ __forceinline__ void bulk_s2g(void* dst, const void* src, uint32_t bytes) {

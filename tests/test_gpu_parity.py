@@ -227,14 +227,19 @@ def test_solve_pressure_twisted_fp64(wl):
     assert float((out[0] - out[1]).abs().max()) < 1e-11 * scale
 
 
-@pytest.mark.parametrize("wl", [
-    S.isotropic_3d(n=32, steps=5),
-    S.box_3d(16, 24, 8, (P, P), (NS, NS), stretched=1.2),
-    S.box_2d(18, 24, (P, P), (NS, NS), stretched=1.2),    # rows not 16-byte multiples: plain loads
+@pytest.mark.parametrize("tiled", [1, 0])
+@pytest.mark.parametrize("make", [
+    lambda: S.isotropic_3d(n=32, steps=5),
+    lambda: S.box_3d(16, 24, 8, (P, P), (NS, NS), stretched=1.2),
+    lambda: S.box_2d(18, 24, (P, P), (NS, NS), stretched=1.2),    # rows not 16-byte multiples: plain loads
+    lambda: S.box_3d(64, 66, 4, (P, P), (NS, NS), stretched=1.2),  # three 32-row boxes, ragged
+    lambda: S.box_3d(32, 100, 4, (P, P), (P, P)),                  # cyclic, four boxes overlapping
 ])
-def test_mixed_twisted_y_solve(wl):
+def test_mixed_twisted_y_solve(make, tiled):
     """Mixed precision with the twisted FP64 y solve (integer-pipe FP32 <-> FP64
-    conversions, FP32 gauge of the zero mode) against the FP64 oracle over steps."""
+    conversions, FP32 gauge of the zero mode; tiles as tensor-map boxes or row copies)
+    against the FP64 oracle over steps."""
+    wl = make()
     from paper_2505_23940_b300 import grid_from_workload
     if not wl.u0:
         hmin = min(float(np.diff(wl.xf[d]).min()) for d in range(wl.dim))
@@ -246,9 +251,11 @@ def test_mixed_twisted_y_solve(wl):
     if wl.bc[1][0] == P:
         G.set_tuning("y_spectral", 0)
     G.set_tuning("ysolve_twisted", 1)
+    G.set_tuning("ysolve_tiled", tiled)
     u = [torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous() for a in wl.u0]
     G.step(u, wl.dt, n)
     torch.cuda.synchronize()
+    assert G.device_status() == 0
     assert field_err([x.double().cpu() for x in u], st.u) < TOLMIX
 
 
