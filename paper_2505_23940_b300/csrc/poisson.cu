@@ -854,7 +854,7 @@ size_t ytwist_smem(int ny, int w) {
   return np * w * (sizeof(double) + (sizeof(T) == 4 ? sizeof(T) : 0)) + 128;   // + alignment slack
 }
 
-constexpr int kTwBoxRows = 32;   // rows per tensor-map box of the twisted solve's tile
+constexpr int kTwBoxRows = 16;   // rows per tensor-map box of the twisted solve's tile (one chunk)
 
 template <typename T, bool CYC, int W>
 __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A,
@@ -925,8 +925,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // 1. elimination towards the middle; chunk c waits for its rows
     double gv = 0.0;
     for (int i0 = 0; i0 < R; i0 += U) {
-      // tiled: level l (two boxes, 32 rows from each end) holds chunks 2 l, 2 l + 1
-      ok &= mbar_wait(&widebar[A.tiled ? min(nlev - 1, i0 >> 5) : min(NG - 1, i0 >> 4)], 0);
+      // tiled: level l (two boxes, kTwBoxRows rows from each end) holds chunk l
+      ok &= mbar_wait_idle(&widebar[A.tiled ? min(nlev - 1, i0 / kTwBoxRows) : min(NG - 1, i0 >> 4)], 0);
       if (i0 + U <= R) {
         // the chunk's values first, the chain in registers, the stores after: no store waits on
         // the chain ahead of the next chunk's loads
@@ -1070,7 +1070,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     }
     pdl_wait();
     if (A.tiled) {
-      // boxes of 32 rows in row order, from both ends of the column inward (the rows each
+      // boxes of kTwBoxRows rows in row order, from both ends of the column inward (the rows each
       // thread's elimination needs first): box b is the top (b even) or bottom (b odd) box of
       // level b / 2; the stage buffer holds the tile in row order
       auto box_row = [&](int b) {
@@ -1087,20 +1087,23 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       if (odd && !CYC) sg[R * W + (h % W)] = 0.0;   // the lower thread's inert slot holds no row
       for (int l = 0; l < nlev; ++l) {
         for (int b = 2 * l; b < min(2 * l + 2, nbox); ++b) {
-          ok &= mbar_wait(&bulkbar[b], 0);
+          ok &= mbar_wait_idle(&bulkbar[b], 0);
           // the rows this box is the first to bring (boxes overlap on ragged columns, and a row
-          // the sweeps may already be eliminating in place must not be widened again): the top box
-          // of level l owns [32 l, min(32 l + 32, ny - 32 l)), the bottom box
-          // [max(32 (l + 1), ny - 32 (l + 1)), ny - 32 l)
+          // the sweeps may already be eliminating in place must not be widened again): with B rows
+          // per box the top box of level l owns [B l, min(B l + B, ny - B l)), the bottom box
+          // [max(B (l + 1), ny - B (l + 1)), ny - B l)
           const int a0 = (b & 1) ? max(kTwBoxRows * (l + 1), ny - kTwBoxRows * (l + 1)) : kTwBoxRows * l;
           const int a1 = (b & 1) ? ny - kTwBoxRows * l : min(kTwBoxRows * (l + 1), ny - kTwBoxRows * l);
-          // this thread: column h % W, rows a0 + h / W + 2 k
+          // this thread: column h % W, rows a0 + h / W + 2 k, by the fast path; a warp that met
+          // another value redoes its rows with the general routine
+          uint32_t sp = 0;
           for (int j = a0 + hw; j < a1; j += 2) {
-            const uint32_t u = __float_as_uint(st[j * W + hc]);
-            uint32_t whi, wlo, sp = 0;
-            fsconv_widen_fast(u, &whi, &wlo, &sp);
-            sg[pos(j) * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) : __hiloint2double((int)whi, (int)wlo);
+            uint32_t whi, wlo;
+            fsconv_widen_fast(__float_as_uint(st[j * W + hc]), &whi, &wlo, &sp);
+            sg[pos(j) * W + hc] = __hiloint2double((int)whi, (int)wlo);
           }
+          if (__any_sync(FULL, sp))
+            for (int j = a0 + hw; j < a1; j += 2) sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&widebar[l]);
@@ -1156,7 +1159,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // mode's column waits for its mean, below)
     const bool mine = hc < ncol && !(zb && hc == 0);
     for (int c = 0; c < nchunk; ++c) {
-      ok &= mbar_wait(&donebar[c], 0);
+      ok &= mbar_wait_idle(&donebar[c], 0);
       const int lo = U * c, n = min(U, R - lo);
       // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r
 #pragma unroll 4
@@ -1638,7 +1641,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     CUtensorMap tmap;
     std::memset(&tmap, 0, sizeof(tmap));
     A.tiled = 0;
-    if (sizeof(T) == 4 && A.bulk && ny >= kTwBoxRows && G->tune_ytile) {
+    if (sizeof(T) == 4 && A.bulk && ny >= 2 * kTwBoxRows && ny <= 20 * kTwBoxRows && G->tune_ytile) {
       const int nzt = G->dim == 3 ? nz : 1;
       if (G->ytw_map_ptr != (const void*)data || G->ytw_map_w != w) {
         G->ytw_map_ok = encode_spectrum_map(reinterpret_cast<CUtensorMap*>(G->ytw_map), (const float*)data, nx, ny,

@@ -94,4 +94,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
+// The same wait for warps that have nothing else to do meanwhile: between polls the thread sleeps
+// (64 ns), leaving the issue slots of its SM sub-partition to the warps doing the work it waits for.
+__device__ __forceinline__ bool mbar_wait_idle(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity)) {
+    __nanosleep(64);
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+  return true;
+}
+
 }  // namespace fs
