@@ -1161,19 +1161,27 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     for (int c = 0; c < nchunk; ++c) {
       ok &= mbar_wait_idle(&donebar[c], 0);
       const int lo = U * c, n = min(U, R - lo);
-      // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r
+      // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r;
+      // the fast path for every value, the general routine again where a warp met another
+      uint32_t sp = 0;
 #pragma unroll 4
       for (int r = hw; r < 2 * n; r += 2) {
         const int p = r < n ? lo + r : R + lo + (r - n);
         const int j = rowof(p);
-        if (mine && j >= 0) {
-          const double v = sg[p * W + hc];
-          if constexpr (F32) {
-            uint32_t sp = 0;
-            const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
-            tile[rs * j + hc] = sp ? fsconv_narrow(v) : __uint_as_float(o);
-          } else {
-            tile[rs * j + hc] = v;
+        const double v = sg[p * W + hc];
+        if constexpr (F32) {
+          const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
+          if (mine && j >= 0) tile[rs * j + hc] = __uint_as_float(o);
+        } else {
+          if (mine && j >= 0) tile[rs * j + hc] = v;
+        }
+      }
+      if constexpr (F32) {
+        if (__any_sync(FULL, sp)) {
+          for (int r = hw; r < 2 * n; r += 2) {
+            const int p = r < n ? lo + r : R + lo + (r - n);
+            const int j = rowof(p);
+            if (mine && j >= 0) tile[rs * j + hc] = fsconv_narrow(sg[p * W + hc]);
           }
         }
       }
