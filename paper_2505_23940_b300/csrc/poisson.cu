@@ -1097,6 +1097,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           // this thread: column h % W, rows a0 + h / W + 2 k, by the fast path; a warp that met
           // another value redoes its rows with the general routine
           uint32_t sp = 0;
+#pragma unroll 8
           for (int j = a0 + hw; j < a1; j += 2) {
             uint32_t whi, wlo;
             fsconv_widen_fast(__float_as_uint(st[j * W + hc]), &whi, &wlo, &sp);
@@ -1164,7 +1165,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r;
       // the fast path for every value, the general routine again where a warp met another
       uint32_t sp = 0;
-#pragma unroll 4
+#pragma unroll 8
       for (int r = hw; r < 2 * n; r += 2) {
         const int p = r < n ? lo + r : R + lo + (r - n);
         const int j = rowof(p);
