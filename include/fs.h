@@ -303,8 +303,11 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     (y_spectral = 0) when the grid has at least 148 * 64
  *                     columns (n_x n_z) and ny <= 148.  Rebuilds the y tables
  *                     (synchronises the stream)
+ *   "ysolve_twist_columns" columns per block of the twisted solve: 64 or 32
+ *                     (0, the default: 64 while two blocks fit an SM, ny <= 148,
+ *                     else 32); rebuilds the y tables
  *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
- *                     least 32 rows as 32-row tensor-map boxes; 0: one bulk
+ *                     least 32 rows as 16-row tensor-map boxes; 0: one bulk
  *                     copy per row
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the

@@ -311,6 +311,7 @@ int build_tables(fs_grid* G) {
     // shared memory holds the block's columns (ny + 1 positions) in FP64 plus their FP32 copy:
     // 64 columns while two blocks fit an SM (ny <= 148), else 32 (ny <= 585)
     G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 112 * 1024 ? 64 : 32;
+    if (G->tune_ytw_cols > 0) G->ytw_cols = G->tune_ytw_cols;
     G->ytwist = L >= 4 && (size_t)(ny + 1) * G->ytw_cols * 12 <= 220 * 1024 && want;
     if (G->ytwist) return build_twisted_tables(G, a, c);
   }
@@ -859,6 +860,16 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     if (value == G->tune_ynseg) return FS_OK;
     G->tune_ynseg = value;
     if (G->yspec) return FS_OK;   // periodic y has no partitioned solve
+    const cudaError_t e = cudaStreamSynchronize(G->stream);
+    if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
+    free_ytables(G);
+    return build_tables(G);
+  } else if (k == "ysolve_twist_columns") {
+    if (value != 0 && value != 32 && value != 64)
+      return set_error(FS_ERR_ARG, "ysolve_twist_columns must be 0, 32 or 64");
+    if (value == G->tune_ytw_cols) return FS_OK;
+    G->tune_ytw_cols = value;
+    if (G->yspec) return FS_OK;
     const cudaError_t e = cudaStreamSynchronize(G->stream);
     if (e != cudaSuccess) return cuda_check(e, "fs_set_tuning");
     free_ytables(G);

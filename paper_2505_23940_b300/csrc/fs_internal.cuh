@@ -302,6 +302,7 @@ struct fs_grid {
   int ytwist = 0;                         // 1: the twisted solve runs instead of the partitioned one
   int tune_ytwist = -1;                   // -1: chosen from the grid's shape, 0: off, 1: on where it fits
   int ytw_cols = 64;                      // columns per block (64 or 32)
+  int tune_ytw_cols = 0;                  // requested columns per block (0: chosen from ny)
   alignas(64) unsigned char ytw_map[128] = {};   // tensor map of the FP32 spectrum (CUtensorMap bytes)
   const void* ytw_map_ptr = nullptr;      // array and block width the map was encoded for
   int ytw_map_w = 0;

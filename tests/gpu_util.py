@@ -6,9 +6,11 @@ import oracle as O
 from helpers import body_of, grid_of, rel_l2
 
 
-def run_gpu(wl, steps, dt=None, precision="fp64", u0=None, want_p=False):
+def run_gpu(wl, steps, dt=None, precision="fp64", u0=None, want_p=False, tuning=()):
     from paper_2505_23940_b300 import body_tensor, grid_from_workload
     g = grid_from_workload(wl, precision)
+    for key, value in tuning:
+        g.set_tuning(key, value)
     u = [torch.tensor(np.asarray(a), dtype=g.dtype, device="cuda").contiguous() for a in (u0 or wl.u0)]
     body = body_tensor(wl)
     p = torch.zeros(g.shape(-1), dtype=torch.float64, device="cuda") if want_p else None

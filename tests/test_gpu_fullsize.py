@@ -15,6 +15,16 @@ def test_isotropic_128_mixed_full_size():
     assert field_err(gp["u"], st.u) < 1e-5
 
 
+def test_isotropic_128_mixed_fp64_y_full_size():
+    """The benchmark's step: FP32 stencils and x/z transforms, the periodic y part of the
+    Poisson solve as the FP64 cyclic tridiagonal (twisted factorisation, tensor-map tiles)."""
+    wl = S.isotropic_3d(n=128)
+    gp = run_gpu(wl, 2, precision="mixed", tuning=[("y_spectral", 0)])
+    assert gp["grid"].device_status() == 0
+    st, _, _ = run_oracle(wl, 2)
+    assert field_err(gp["u"], st.u) < 1e-5
+
+
 def test_channel_192x128x128_mixed_full_size():
     wl = S.channel_3d()
     gp = run_gpu(wl, 2, precision="mixed")
