@@ -923,10 +923,31 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     for (int q = 0; q < U; ++q) mb[q] = __ldg(Mt + q * nl);   // tables do not depend on the predecessor
     double* gp = sg + P0 * W + cb;
     // 1. elimination towards the middle; chunk c waits for its rows
+    if (F32 && A.tiled) {
+      // chunk 0 is exactly the rows of box 0 (upper thread) or box 1 (lower): widened here, by
+      // the thread that eliminates them, as soon as the box lands
+      ok &= mbar_wait_idle(&bulkbar[half], 0);
+      uint32_t sp = 0;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int j = rowof(P0 + q);
+        uint32_t whi, wlo;
+        fsconv_widen_fast(act && j >= 0 ? __float_as_uint((float)st[j * W + cb]) : 0u, &whi, &wlo, &sp);
+        gp[q * W] = __hiloint2double((int)whi, (int)wlo);
+      }
+      if (__any_sync(FULL, sp)) {
+#pragma unroll
+        for (int q = 0; q < U; ++q) {
+          const int j = rowof(P0 + q);
+          gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) : 0.0;
+        }
+      }
+    }
     double gv = 0.0;
     for (int i0 = 0; i0 < R; i0 += U) {
-      // tiled: level l (two boxes, kTwBoxRows rows from each end) holds chunk l
-      ok &= mbar_wait_idle(&widebar[A.tiled ? min(nlev - 1, i0 / kTwBoxRows) : min(NG - 1, i0 >> 4)], 0);
+      // tiled: level l (two boxes, kTwBoxRows rows from each end) holds chunk l; chunk 0 is ours
+      if (!A.tiled) ok &= mbar_wait_idle(&widebar[min(NG - 1, i0 >> 4)], 0);
+      else if (i0 > 0) ok &= mbar_wait_idle(&widebar[min(nlev - 1, i0 / kTwBoxRows)], 0);
       if (i0 + U <= R) {
         // the chunk's values first, the chain in registers, the stores after: no store waits on
         // the chain ahead of the next chunk's loads
@@ -1084,8 +1105,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           tensor_g2s_3d(st + (size_t)r0 * W, &tmap, s0, r0, t, &bulkbar[b]);
         }
       }
-      if (odd && !CYC) sg[R * W + (h % W)] = 0.0;   // the lower thread's inert slot holds no row
-      for (int l = 0; l < nlev; ++l) {
+      for (int l = 1; l < nlev; ++l) {   // level 0: the sweep threads' own first chunk
         for (int b = 2 * l; b < min(2 * l + 2, nbox); ++b) {
           ok &= mbar_wait_idle(&bulkbar[b], 0);
           // the rows this box is the first to bring (boxes overlap on ragged columns, and a row
