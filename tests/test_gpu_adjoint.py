@@ -60,9 +60,11 @@ def oracle_vjp(wl, u0, lam_u, dt, lam_body=None, dJdF=None):
     return out
 
 
-def gpu_vjp(wl, u0, lam_u, dt, precision, lam_body=None, dJdF=None):
+def gpu_vjp(wl, u0, lam_u, dt, precision, lam_body=None, dJdF=None, tuning=()):
     from paper_2505_23940_b300 import body_tensor, grid_from_workload
     g = grid_from_workload(wl, precision)
+    for key, value in tuning:
+        g.set_tuning(key, value)
     u = [torch.tensor(np.asarray(a), dtype=g.dtype, device="cuda").contiguous() for a in u0]
     lam = [torch.tensor(np.asarray(a), dtype=g.dtype, device="cuda").contiguous() for a in lam_u]
     body = body_tensor(wl)
@@ -146,6 +148,19 @@ def test_adjoint_mixed_isotropic_rk3():
     o = oracle_vjp(wl, wl.u0, lam, wl.dt)
     gp = gpu_vjp(wl, wl.u0, lam, wl.dt, "mixed")
     assert rel_l2(gp["u"], o["u"]) < 1e-5
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("mixed", 1e-5)])
+@pytest.mark.parametrize("twisted", [1, 0])
+def test_adjoint_fp64_periodic_y_solve(precision, tol, twisted):
+    """The adjoint step with the y part of its Poisson solves as the FP64 cyclic tridiagonal
+    (y_spectral = 0), twisted (tensor-map tiles in mixed precision) or partitioned, against
+    the oracle's reverse-mode AD."""
+    wl = S.isotropic_3d(n=32, steps=1)
+    lam = seeds(wl, 7)
+    o = oracle_vjp(wl, wl.u0, lam, wl.dt)
+    gp = gpu_vjp(wl, wl.u0, lam, wl.dt, precision, tuning=[("y_spectral", 0), ("ysolve_twisted", twisted)])
+    assert rel_l2(gp["u"], o["u"]) < tol
 
 
 def test_adjoint_mixed_cylinder():
