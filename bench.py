@@ -51,7 +51,7 @@ KERNEL_BYTES_PER_CELL = {
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50362880 + 839680, "src": "9d68f8187082"},
-    "ysolve": {"bytes": 27197184 + 0, "src": "789db66cebf5"},
+    "ysolve": {"bytes": 27197184 + 0, "src": "62755ef9a23c"},
     "fft_x_fwd_div": {"bytes": 25243392 + 0, "src": "7895d4f893d7"},
     "fft_z_fwd": {"bytes": 8407040 + 0, "src": "7895d4f893d7"},
     "fft_y_solve": {"bytes": 8435200 + 0, "src": "7895d4f893d7"},

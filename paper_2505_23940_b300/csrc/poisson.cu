@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   double* sg = reinterpret_cast<double*>(ytw_raw);   // [NP][W] FP64, position order
   T* st = F32 ? reinterpret_cast<T*>(ytw_raw + (size_t)(ny + 1) * W * sizeof(double)) : reinterpret_cast<T*>(sg);
   constexpr int ND = 20;                         // output chunks of 16 positions (R <= 293 rows per thread)
-  constexpr int NB = 20;                         // tensor-map boxes (ny <= 640)
+  constexpr int NB = 20;                         // tensor-map boxes of kTwBoxRows rows (ny <= 320)
   __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
   const int tid = threadIdx.x, lane = tid & 31;
   const int s0 = blockIdx.x * W;
