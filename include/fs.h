@@ -299,10 +299,9 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     tables; synchronises).  Same discrete solution.
  *   "ysolve_twisted"  FP64 tridiagonal y solve form: 1 twisted factorisation,
  *                     two threads per column (where ny <= 586); 0 the
- *                     partitioned form; -1 (default) twisted on periodic y
- *                     (y_spectral = 0) when the grid has at least 148 * 64
- *                     columns (n_x n_z) and ny <= 148.  Rebuilds the y tables
- *                     (synchronises the stream)
+ *                     partitioned form; -1 (default) twisted when the grid has
+ *                     at least 148 * 64 columns (n_x n_z) and ny <= 148.
+ *                     Rebuilds the y tables (synchronises the stream)
  *   "ysolve_twist_columns" columns per block of the twisted solve: 64 or 32
  *                     (0, the default: 64 while two blocks fit an SM, ny <= 148,
  *                     else 32); rebuilds the y tables

@@ -302,12 +302,11 @@ int build_tables(fs_grid* G) {
   {
     const long columns = (long)nx * (G->dim == 3 ? nz : 1);
     const int L = G->cyclic ? ny - 1 : ny;
-    // by default only on periodic y (its partitioned form pays two spike corrections and a cyclic
-    // coupling per row), where two 64-column blocks fit an SM (ny <= 148), on a grid that fills
-    // it twice.  Measured per mixed step: isotropic 128^3 0.257 against 0.287 ms; the wall-bounded
-    // 192 x 128 x 128 channel 0.180 against 0.174 ms and 256^3 (32-column blocks, one sweep warp
-    // per SM sub-partition) slower as well, so those keep the partitioned solve.
-    const bool want = G->tune_ytwist < 0 ? (G->cyclic && columns >= 148L * 64 && ny <= 148) : G->tune_ytwist == 1;
+    // by default where two 64-column blocks fit an SM (ny <= 148) on a grid that fills it twice.
+    // Measured per mixed step: isotropic 128^3 (periodic y) 0.237-0.242 against 0.286 ms, the
+    // wall-bounded 192 x 129 x 128 channel 0.161-0.165 against 0.173 ms; 256^3 (32-column blocks,
+    // one sweep warp per SM sub-partition) is slower and keeps the partitioned solve.
+    const bool want = G->tune_ytwist < 0 ? (columns >= 148L * 64 && ny <= 148) : G->tune_ytwist == 1;
     // shared memory holds the block's columns (ny + 1 positions) in FP64 plus their FP32 copy:
     // 64 columns while two blocks fit an SM (ny <= 148), else 32 (ny <= 585)
     G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 112 * 1024 ? 64 : 32;
