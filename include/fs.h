@@ -300,10 +300,10 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *   "ysolve_twisted"  FP64 tridiagonal y solve form: 1 twisted factorisation,
  *                     two threads per column (where ny <= 586); 0 the
  *                     partitioned form; -1 (default) twisted when the grid has
- *                     at least 148 * 64 columns (n_x n_z) and ny <= 148.
+ *                     at least 148 * 64 columns (n_x n_z) and ny <= 292.
  *                     Rebuilds the y tables (synchronises the stream)
  *   "ysolve_twist_columns" columns per block of the twisted solve: 64 or 32
- *                     (0, the default: 64 while two blocks fit an SM, ny <= 148,
+ *                     (0, the default: 64 while a block fits an SM, ny <= 292,
  *                     else 32); rebuilds the y tables
  *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
  *                     least 32 rows as 16-row tensor-map boxes; 0: one bulk

@@ -302,14 +302,18 @@ int build_tables(fs_grid* G) {
   {
     const long columns = (long)nx * (G->dim == 3 ? nz : 1);
     const int L = G->cyclic ? ny - 1 : ny;
-    // by default where two 64-column blocks fit an SM (ny <= 148) on a grid that fills it twice.
+    // by default where a 64-column block fits an SM (ny <= 292) on a grid that fills every SM.
     // Measured per mixed step: isotropic 128^3 (periodic y) 0.237-0.242 against 0.286 ms, the
-    // wall-bounded 192 x 129 x 128 channel 0.161-0.165 against 0.173 ms; 256^3 (32-column blocks,
-    // one sweep warp per SM sub-partition) is slower and keeps the partitioned solve.
-    const bool want = G->tune_ytwist < 0 ? (columns >= 148L * 64 && ny <= 148) : G->tune_ytwist == 1;
+    // wall-bounded 192 x 129 x 128 channel 0.161-0.165 against 0.173 ms, 256^3 (periodic y)
+    // 1.88 against 1.91 ms.
+    const bool want = G->tune_ytwist < 0 ? (columns >= 148L * 64 && ny <= 292) : G->tune_ytwist == 1;
     // shared memory holds the block's columns (ny + 1 positions) in FP64 plus their FP32 copy:
-    // 64 columns while two blocks fit an SM (ny <= 148), else 32 (ny <= 585)
-    G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 112 * 1024 ? 64 : 32;
+    // 64 columns (two blocks per SM while ny <= 148, one up to ny = 292), else 32 (ny <= 585).
+    // A block's warp 0 .. 3 run on the SM's four sub-partitions and its first W / 16 warps
+    // sweep: 64 columns keep an FP64 pipe busy on every sub-partition (256^3 periodic, FP64 y:
+    // 1.88 ms per step with one 64-column block per SM, 1.92 with two 32-column blocks, 1.91
+    // partitioned)
+    G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 220 * 1024 ? 64 : 32;
     if (G->tune_ytw_cols > 0) G->ytw_cols = G->tune_ytw_cols;
     G->ytwist = L >= 4 && (size_t)(ny + 1) * G->ytw_cols * 12 <= 220 * 1024 && want;
     if (G->ytwist) return build_twisted_tables(G, a, c);

@@ -194,7 +194,9 @@ _TWIST_CASES = [
     S.box_3d(12, 16, 10, (P, P), (P, P)),                  # periodic y: cyclic, chain of 15
     S.box_2d(24, 6, (P, P), (P, P)),                       # shortest cyclic chain (5 rows)
     S.box_2d(18, 5, (P, P), (NS, NS)),                     # walls, 5 rows
-    S.box_2d(20, 300, (P, P), (NS, NS), stretched=1.1),    # 300 rows
+    S.box_2d(20, 300, (P, P), (NS, NS), stretched=1.1),    # 300 rows (32-column blocks)
+    S.box_2d(24, 200, (P, P), (NS, NS), stretched=1.1),    # 200 rows, one 64-column block per SM
+    S.box_3d(8, 256, 4, (P, P), (P, P)),                   # cyclic, 256 rows
     S.box_2d(16, 400, (P, P), (P, P)),                     # largest twisted column (200 KB tile), cyclic
 ]
 
@@ -234,6 +236,7 @@ def test_solve_pressure_twisted_fp64(wl):
     lambda: S.box_2d(18, 24, (P, P), (NS, NS), stretched=1.2),    # rows not 16-byte multiples: plain loads
     lambda: S.box_3d(64, 66, 4, (P, P), (NS, NS), stretched=1.2),  # three 32-row boxes, ragged
     lambda: S.box_3d(32, 100, 4, (P, P), (P, P)),                  # cyclic, four boxes overlapping
+    lambda: S.box_3d(16, 200, 4, (P, P), (NS, NS), stretched=1.1),  # 200 rows: 13 boxes
 ])
 def test_mixed_twisted_y_solve(make, tiled):
     """Mixed precision with the twisted FP64 y solve (integer-pipe FP32 <-> FP64
