@@ -210,7 +210,8 @@ def run_reference(args, ws, rank):
         "impl": "reference", "metric": "cell-updates/s forward", "value": rate, "unit": "cell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "cells": wl.cells(), "scheme": wl.scheme},
+        "config": {"workload": args.workload, "cells": wl.cells(), "n": wl.n, "scheme": wl.scheme,
+                   "precision": "FP64 throughout (the oracle)", "parallelism": "single"},
         "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": threads, "kind": "oracle",
                          "sample": "%d full time steps of the %s workload (FP64 torch CPU oracle)"
                                    % (args.steps, args.workload)},
