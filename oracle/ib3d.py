@@ -14,7 +14,7 @@ the Lagrangian markers serve the hydrodynamic force of Eq. (20) only.
   delta3           delta_h(x) = d_h(x) d_h(y) d_h(z) (Eq. 21 in 3-D)
   marker_forces    q_i of Eq. (20) and F = rho sum_i q_i dV_i
 
-Readings (recorded in the design doc): the grid is uniform in all three directions
+Readings: the grid is uniform in all three directions
 where the body's kernel supports reach; a face exactly on a box surface is a
 fluid face (open boxes); dV_i is supplied per marker.
 

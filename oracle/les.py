@@ -2,7 +2,7 @@
 (constant Smagorinsky model; its use in the paper's channel LES, §3.4).
 
 The paper states the model (eddy viscosity nu_t = (C_s Delta)^2 |S|, |S| = sqrt(2 S_ij S_ij))
-but not its discretisation; the readings taken here (recorded in the design doc) are:
+but not its discretisation; the readings taken here are:
 * uniform grids periodic in every direction (the decaying-turbulence LES case);
   Delta = (h_x h_y h_z)^(1/3);
 * on the MAC grid the normal strains S_xx = du/dx, ... live at cell centres, the
