@@ -28,6 +28,10 @@ staggered grid); the details below are this project's reading of it:
 Parity: pinned by tests against polynomial exactness, Taylor-Green decay in
 closed form, Poiseuille flow against an independent tridiagonal solve, and
 momentum conservation (tests/test_oracle_operators.py, test_oracle_flows.py).
+The stretched-grid interpolation weights of the transported and transporting
+velocities are pinned by exact linear fields on a tanh-stretched grid (hand
+values from the face coordinates), the upwind direction by step profiles with
+hand-computed first-order fluxes for both signs of the transport velocity.
 """
 import torch
 

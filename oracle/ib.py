@@ -7,12 +7,13 @@
   inside_polygon           solid test of a point against the marker polygon
   classify                 solid faces (Omega_s) and IB faces (Omega_IB, fluid
                            faces with a solid neighbour, §2.2)
+  half_distribution_sum    F_N_i of Eq. (19)
   target_velocity          u_s of Eq. (5): body velocity on solid faces
                            (Eq. 23), normalised marker interpolation on IB
                            faces (Eqs. 18-19)
   marker_forces            q_i of Eq. (20) and the body force F
 
-Readings of the paper taken here (each recorded in the design doc):
+Readings of the paper taken here:
 * epsilon = 1 on solid faces and on IB faces (the direct forcing acts "in
   cells intersecting the immersed region", §2.3.1, and u_s is defined on IB
   points).
@@ -29,7 +30,11 @@ Readings of the paper taken here (each recorded in the design doc):
   integer decision taken in FP64 with each operation rounded separately.
 
 Parity: kernels pinned by their moment conditions; interpolation / spreading
-by the transpose identity and exact reproduction of a uniform velocity
+by the transpose identity and exact reproduction of a uniform velocity; F_N
+by the half-distribution value 1 / (2 h_x h_y) of a marker on a flat wall;
+the normalised interpolation with non-uniform marker velocities by a
+scalar-loop brute force; q_i, F and the torque by uniform (q = -f), rigid-
+rotation (closed-form torque) and radial (zero torque) forcings
 (tests/test_oracle_ib.py).  The coupled FSI trajectory is "parity unpinned"
 against physics (no reference data); only GPU-vs-oracle applies there.
 """
@@ -150,6 +155,12 @@ def weights_matrix(g, c, kind, Xm, Ym):
     return delta(kind, dx, dy, hx, hy)
 
 
+def half_distribution_sum(g, c, kind, Xm, Ym, solid):
+    """F_N_i of Eq. (19) for component c: sum over the c-faces that are not solid of delta_h(x - X_i)."""
+    W = weights_matrix(g, c, kind, Xm, Ym)
+    return (W * (~solid).unsqueeze(0)).sum(dim=(1, 2, 3))
+
+
 def target_velocity(g, body, kind, w, wdot, masks):
     """u_s of Eq. (5) on forced faces and the exact solid velocity u_c of Eq. (8).
 
@@ -167,7 +178,7 @@ def target_velocity(g, body, kind, w, wdot, masks):
         bvx, bvy = body.velocity_at(fx.expand(g.shape(c)), fy.expand(g.shape(c)), w, wdot)
         bv = (bvx, bvy)[c]
         W = weights_matrix(g, c, kind, Xm, Ym)         # (nm, ez, ey, ex)
-        FN = (W * (~solid).unsqueeze(0)).sum(dim=(1, 2, 3))           # Eq. (19)
+        FN = half_distribution_sum(g, c, kind, Xm, Ym, solid)          # Eq. (19)
         FNs = torch.where(FN > 0, FN, torch.ones_like(FN))
         wgt = W * (dV / FNs).reshape(-1, 1, 1, 1)
         num = (wgt * mv[c].reshape(-1, 1, 1, 1)).sum(dim=0)

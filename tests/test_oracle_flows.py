@@ -102,3 +102,43 @@ def test_periodic_step_conserves_momentum():
         st, _ = O.step(g, st, 0.01)
     m1 = [float((st.u[c] * g.face_volume(c)).sum()) for c in range(3)]
     assert max(abs(a - b) for a, b in zip(m0, m1)) < 1e-13
+
+
+def _rk3_order_ratios():
+    """Time-step refinement of SSP-RK3 on one 16^2 periodic grid (so the spatial error is the same in
+    every run and cancels): a random projected field with u ~ 1, nu = 0.02, T = 0.8 with dt = T/8,
+    T/16, T/32, each compared with dt = T/256 on the same grid.  Returns the two error ratios."""
+    from oracle import poisson
+    wl = S.box_2d(16, 16, (S.PERIODIC,) * 2, (S.PERIODIC,) * 2, Lx=2 * math.pi, Ly=2 * math.pi, nu=0.02)
+    g = grid_of(wl)
+    rng = np.random.default_rng(3)
+    u0 = [torch.tensor(rng.uniform(-1, 1, size=g.shape(c))) for c in range(2)]
+    u0, _ = poisson.project(g, u0)
+    T = 0.8
+
+    def run(n):
+        st = O.State([x.clone() for x in u0])
+        for _ in range(n):
+            st, _ = O.step(g, st, T / n, scheme="rk3")
+        return st.u
+
+    ref = run(256)
+    es = [rel_l2(run(n), ref) for n in (8, 16, 32)]
+    return es[0] / es[1], es[1] / es[2]
+
+
+def test_ssp_rk3_is_third_order_in_time():
+    """The explicit Runge-Kutta scheme (§2.5; read as Shu-Osher SSP-RK3 with a projection per stage)
+    converges at third order in dt: error ratios ~8 per halving of dt."""
+    r1, r2 = _rk3_order_ratios()
+    assert 7.0 < r1 < 9.5 and 7.0 < r2 < 9.5, (r1, r2)
+
+
+def test_rk3_order_check_rejects_a_wrong_tableau(monkeypatch):
+    """The order check is sensitive to the stage weights: with the second stage's weights swapped
+    (1/4, 3/4) the scheme drops to about second order and the ratios fall near 2-4."""
+    import sys
+    mod = sys.modules["oracle.step"]
+    monkeypatch.setattr(mod, "SSPRK3", ((0.0, 1.0), (0.25, 0.75), (1.0 / 3.0, 2.0 / 3.0)))
+    r1, r2 = _rk3_order_ratios()
+    assert r1 < 5.0 and r2 < 5.0, (r1, r2)
