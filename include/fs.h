@@ -338,8 +338,10 @@ int fs_profile_end(fs_grid* grid, char* report, int len);
  *   out        device, 2 doubles, written by the GPU (read it after the stream)
  * Allocates nothing: its reduction scratch is a fixed 64 KiB file-scope
  * device array present on every device that loads the library, until exit.
- * The first call on a device looks up that array's address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call in each CUDA context of a device (the primary context, a
+ * driver-API context, the primary context re-created after cudaDeviceReset)
+ * looks up that array's address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
  * Every call shares the scratch: calls that overlap on the GPU (different
  * streams, no ordering between them) race and give wrong results.  Each call
  * overwrites every scratch slot it reads, so nothing needs clearing.

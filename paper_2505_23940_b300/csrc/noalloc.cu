@@ -26,9 +26,21 @@ constexpr int kThreads = 256;
 // Two doubles per chunk: partial sum of 0.5 u^2 w and partial max |u|.  64 KiB.
 static __device__ __align__(256) double g_noalloc_partials[2 * kMaxChunks];
 
+// A symbol's device address belongs to a CUDA context, not to a device: the
+// address is cached per device together with the context it was looked up in,
+// and looked up again when another context is current on that device (a
+// driver-API context, or the primary context re-created after
+// cudaDeviceReset).
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
-double* g_partials_addr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  void* ctx;
+  double* addr;
+};
+ScratchAddr g_partials_addr[kMaxDevices] = {};
+
+typedef int (*CtxGetCurrentFn)(void**);
+CtxGetCurrentFn g_ctx_get_current = nullptr;   // the driver's cuCtxGetCurrent
 
 template <typename T>
 __global__ void chunk_stats_kernel(const T* __restrict__ u, long long n, int ex, int ey, double vol,
@@ -84,20 +96,36 @@ __global__ void finish_stats_kernel(const double* __restrict__ partials, int nch
   }
 }
 
-// Device address of the static scratch for the current device, looked up once per device.
+// Device address of the static scratch in the current context, looked up once per
+// (device, context).
 int scratch_address(double** addr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fs::cuda_check(e, "fs_component_stats_noalloc: cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fs::set_error(FS_ERR_UNSUPPORTED, "device index beyond 63");
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_partials_addr[dev]) {
+  if (!g_ctx_get_current) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fs::set_error(FS_ERR_CUDA, "fs_component_stats_noalloc: cuCtxGetCurrent not found");
+    g_ctx_get_current = reinterpret_cast<CtxGetCurrentFn>(fn);
+  }
+  void* ctx = nullptr;
+  if (g_ctx_get_current(&ctx) != 0) ctx = nullptr;
+  ScratchAddr& a = g_partials_addr[dev];
+  if (!ctx || !a.addr || a.ctx != ctx) {
+    // the lookup also makes the runtime's context current when none is yet
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_partials);
     if (e != cudaSuccess) return fs::cuda_check(e, "fs_component_stats_noalloc: cudaGetSymbolAddress");
-    g_partials_addr[dev] = static_cast<double*>(p);
+    if (g_ctx_get_current(&ctx) != 0 || !ctx)
+      return fs::set_error(FS_ERR_CUDA, "fs_component_stats_noalloc: no current CUDA context");
+    a.ctx = ctx;
+    a.addr = static_cast<double*>(p);
   }
-  *addr = g_partials_addr[dev];
+  *addr = a.addr;
   return FS_OK;
 }
 
@@ -110,11 +138,22 @@ extern "C" int fs_component_stats_noalloc(const void* u, int precision, const in
     return fs::set_error(FS_ERR_ARG, "fs_component_stats_noalloc: unknown precision");
   if (ext[0] < 1 || ext[1] < 1 || ext[2] < 1)
     return fs::set_error(FS_ERR_ARG, "fs_component_stats_noalloc: extents must be >= 1");
-  const long long n = (long long)ext[0] * ext[1] * ext[2];
-  const long long nchunks = (n + kChunk - 1) / kChunk;
-  if (nchunks > kMaxChunks)
+  // the element count, checked against the scratch's capacity before each product
+  constexpr long long kMaxElems = (long long)kChunk * kMaxChunks;
+  long long n = ext[0];
+  bool too_big = n > kMaxElems;
+  if (!too_big) {
+    n *= ext[1];
+    too_big = n > kMaxElems;
+  }
+  if (!too_big) {
+    n *= ext[2];
+    too_big = n > kMaxElems;
+  }
+  if (too_big)
     return fs::set_error(FS_ERR_ARG, "fs_component_stats_noalloc: field has more than 33554432 elements "
                                      "(4096 chunks of 8192), the size of its fixed scratch");
+  const long long nchunks = (n + kChunk - 1) / kChunk;
   double* partials = nullptr;
   int rc = scratch_address(&partials);
   if (rc != FS_OK) return rc;

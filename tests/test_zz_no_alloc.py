@@ -57,6 +57,23 @@ def test_noalloc_stats_match_grid_diagnostics_two_calls(precision):
         assert um == ref["umax"], (call, um, ref["umax"])
 
 
+def test_noalloc_exact_capacity_without_weights_matches_host_sum():
+    """A field of exactly 33,554,432 FP32 elements fills all 4096 scratch slots; with wy = NULL every
+    element has weight vol.  Checked against an FP64 sum and max taken on the host, twice in a row."""
+    from paper_2505_23940_b300 import MIXED, lib
+    L = lib()
+    for seed in (21, 22):
+        gen = torch.Generator().manual_seed(seed)
+        host = torch.rand((2, 4096, 4096), generator=gen, dtype=torch.float64).mul_(2.0).sub_(1.0).float()
+        t = host.to("cuda")
+        o = _stats(L, t, MIXED, 0.25)
+        h64 = host.double()
+        ke = float((0.5 * h64 * h64).sum()) * 0.25
+        assert abs(float(o[0]) - ke) <= 1e-12 * ke, (seed, float(o[0]), ke)
+        assert float(o[1]) == float(h64.abs().max())
+        del t
+
+
 def test_noalloc_rejects_fields_beyond_its_scratch():
     from paper_2505_23940_b300 import FP64, lib
     L = lib()
@@ -67,3 +84,7 @@ def test_noalloc_rejects_fields_beyond_its_scratch():
                                       ctypes.c_void_p(out.data_ptr()), None)
     assert rc == -1
     assert b"33554432" in L.fs_last_error()
+    ext = (ctypes.c_int * 3)(2 ** 30, 2 ** 30, 2 ** 30)   # the product overflows 64 bits without the stepwise check
+    rc = L.fs_component_stats_noalloc(ctypes.c_void_p(t.data_ptr()), FP64, ext, ctypes.c_double(1.0), None,
+                                      ctypes.c_void_p(out.data_ptr()), None)
+    assert rc == -1
