@@ -25,7 +25,11 @@ pinned by Taylor-Green decay, Poiseuille flow, divergence-free projection and
 momentum conservation (tests/test_oracle_flows.py), the SSP-RK3 tableau by
 third-order convergence in dt (error ratios ~8 per halving; a swapped stage
 weight drops it to ~2), and its autograd adjoint by central finite
-differences (tests/test_oracle_adjoint.py).
+differences (tests/test_oracle_adjoint.py).  The implicit-differentiation
+adjoint of the strongly coupled step (step_coupled_adjoint) is pinned by
+central finite differences of the coupled step converged to rounding and by
+reverse-mode AD through the unrolled sub-iterations
+(tests/test_oracle_coupling.py).
 """
 import torch
 
@@ -140,13 +144,59 @@ def step_coupled(g, st, dt, body, kernel=ib.ROMA3, params=None, max_iter=100, to
         new, dg = step(g, State(st.u, w_it, wd_it), dt, "fe", body, kernel, params=None)
         k += 1
         w_new, wd_new = body_mod.rk4(params, st.w, st.wd, dg.F, dt)
-        den = float((w_it * w_it).sum())
-        num = float(((w_new - w_it) ** 2).sum())
+        den = float((w_it * w_it).sum().detach())
+        num = float(((w_new - w_it) ** 2).sum().detach())
         xi = num / den if den > 0.0 else num
         w_it, wd_it = w_new, wd_new
         if xi < tol:
             break
     return State(new.u, w_it, wd_it), dg, k, xi
+
+
+def step_coupled_adjoint(g, st, dt, body, kernel, params, lam_u, lam_body, dJdF, max_iter=100, tol=1e-5):
+    """Reverse of the strongly coupled step by implicit differentiation (§2.4.1) of its fixed point.
+
+    The converged body state s* = (w*, wdot*) of Algorithm 1 satisfies
+        R(s*, theta) = s* - B(s^n, F(u^n, s*), k) = 0,
+    where F(u^n, s) is the force of the fluid step advanced from u^n with the body kinematics s
+    and B the RK4 step of Eq. (12) from the level-n body state s^n; the new velocity is
+    u^{n+1} = U(u^n, s*).  For the loss L(u^{n+1}, s*, F) with adjoint seeds (lam_u, lam_body,
+    dJdF) the paper's adjoint equation reads
+        (dR/ds)^T lam = (dL/ds)^T,  dL/dtheta = (explicit part) - lam^T dR/dtheta,
+    with theta = (u^n, s^n, k).  The fluid step and the body step are linearised at the converged
+    iterate (the body state step_coupled returns); their partial derivatives come from
+    torch.autograd, dR/ds = I - dB/ds is formed column by column (4 x 4) and the 4-unknown system
+    is solved directly.
+
+    Returns (lam_u^n, lam_body^n (4,), dJ/dk) and the sub-iteration count of the forward solve.
+    """
+    with torch.no_grad():
+        new, _, iters, _ = step_coupled(g, State([x.detach() for x in st.u], st.w.detach(), st.wd.detach()), dt,
+                                        body, kernel, params, max_iter, tol)
+    s_star = torch.cat([new.w, new.wd]).detach().clone().requires_grad_(True)
+    u_n = [x.detach().clone().requires_grad_(True) for x in st.u]
+    s_n = torch.cat([st.w, st.wd]).detach().clone().requires_grad_(True)
+    k = torch.tensor(float(params.k), dtype=F64, requires_grad=True)
+    p = body_mod.RigidParams(params.m, k, params.c, params.active)
+    fl, dg = step(g, State(u_n, s_star[:2], s_star[2:]), dt, "fe", body, kernel, params=None)
+    w_b, wd_b = body_mod.rk4(p, s_n[:2], s_n[2:], dg.F, dt)
+    B = torch.cat([w_b, wd_b])
+    seeds_u = [torch.as_tensor(a, dtype=F64) for a in lam_u]
+    sig = torch.as_tensor(lam_body, dtype=F64)
+    fbar = torch.as_tensor(dJdF, dtype=F64)
+    # partial dL/ds at s*: lam_body directly, plus the fluid outputs' dependence on the kinematics
+    dLds = torch.autograd.grad(list(fl.u) + [dg.F], s_star, seeds_u + [fbar], retain_graph=True)[0] + sig
+    # dR/ds = I - dB/ds, row i of dB/ds from the vector-Jacobian product with e_i
+    dBds = torch.stack([torch.autograd.grad(B, s_star, torch.eye(4, dtype=F64)[i], retain_graph=True,
+                                            allow_unused=True)[0] for i in range(4)])
+    lam = torch.linalg.solve((torch.eye(4, dtype=F64) - dBds).T, dLds)
+    # explicit part through U and F, then -lam^T dR/dtheta = lam^T dB/dtheta
+    ex = torch.autograd.grad(list(fl.u) + [dg.F], u_n, seeds_u + [fbar], retain_graph=True)
+    th = torch.autograd.grad(B, u_n + [s_n, k], lam, allow_unused=True)
+    lam_un = [a + (b if b is not None else torch.zeros_like(a)) for a, b in zip(ex, th[:len(u_n)])]
+    lam_sn = th[len(u_n)] if th[len(u_n)] is not None else torch.zeros(4, dtype=F64)
+    dk = th[len(u_n) + 1] if th[len(u_n) + 1] is not None else torch.zeros((), dtype=F64)
+    return [x.detach() for x in lam_un], lam_sn.detach(), dk.detach(), iters
 
 
 def kinetic_energy(g, u):
