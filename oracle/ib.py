@@ -4,7 +4,8 @@
                            kernel of the paper, the 3-point kernel (Roma,
                            Peskin & Berger 1999) is the one the FSI workload asks for
   delta                    tensor product delta_h = d_h(x) d_h(y), Eq. (21)
-  inside_polygon           solid test of a point against the marker polygon
+  inside_polygon           solid test of a point against the marker polygon (one or
+                           several closed contours)
   classify                 solid faces (Omega_s) and IB faces (Omega_IB, fluid
                            faces with a solid neighbour, §2.2)
   half_distribution_sum    F_N_i of Eq. (19)
@@ -72,15 +73,30 @@ def delta(kind, dx, dy, hx, hy):
     return phi(dx / hx) * phi(dy / hy) / (hx * hy)
 
 
-def inside_polygon(px, py, X, Y):
-    """Crossing-number test of points (px, py) against the closed polygon (X, Y).
+def contour_next(nm, starts=None):
+    """Index of the vertex after each vertex: closed contours [starts[k], starts[k+1]) (one contour
+    of all nm markers when starts is None), each closing back to its first vertex."""
+    starts = [0] if starts is None else [int(a) for a in starts]
+    ends = starts[1:] + [nm]
+    nxt = []
+    for a, b in zip(starts, ends):
+        nxt += list(range(a + 1, b)) + [a]
+    return nxt
+
+
+def inside_polygon(px, py, X, Y, nxt=None):
+    """Crossing-number test of points (px, py) against the closed polygon (X, Y), or against a set of
+    closed contours (vertex i joined to vertex nxt[i]): a point is inside when a ray from it crosses
+    the edges an odd number of times, i.e. when it lies inside an odd number of the contours.
 
     Each operation is one IEEE-rounded FP64 operation in the order written."""
     inside = torch.zeros(torch.broadcast_shapes(px.shape, py.shape), dtype=torch.bool)
     nm = X.numel()
+    if nxt is None:
+        nxt = contour_next(nm)
     for i in range(nm):
         ax, ay = X[i], Y[i]
-        bx, by = X[(i + 1) % nm], Y[(i + 1) % nm]
+        bx, by = X[nxt[i]], Y[nxt[i]]
         cond = (ay > py) != (by > py)
         if float(by - ay) == 0.0:
             continue
@@ -94,17 +110,21 @@ class Body:
 
     X0, Y0      marker rest positions, ordered around the closed surface
     ds          arc length per marker
+    contours    first marker of each closed contour when the body is made of several
+                disjoint parts (an array of cylinders moving as one rigid body); None:
+                one contour
     xc0         reference point (rotation centre) at rest
     omega       prescribed angular velocity (surface velocity only; the
                 geometry translates but does not turn)
     """
 
-    def __init__(self, X0, Y0, ds, xc0, omega=0.0):
+    def __init__(self, X0, Y0, ds, xc0, omega=0.0, contours=None):
         self.X0 = torch.as_tensor(X0, dtype=F64)
         self.Y0 = torch.as_tensor(Y0, dtype=F64)
         self.ds = torch.as_tensor(ds, dtype=F64)
         self.xc0 = (float(xc0[0]), float(xc0[1]))
         self.omega = float(omega)
+        self.next = contour_next(self.X0.numel(), contours)
 
     def markers(self, w):
         return self.X0 + w[0], self.Y0 + w[1]
@@ -123,7 +143,7 @@ def classify(g, body, w):
         fx, fy, _ = g.face_coords(c)
         px = (fx - w[0]).expand(g.shape(c))
         py = (fy - w[1]).expand(g.shape(c))
-        solid = inside_polygon(px, py, body.X0, body.Y0)
+        solid = inside_polygon(px, py, body.X0, body.Y0, body.next)
         nb = torch.zeros_like(solid)
         for d in range(2):
             ax = 2 - d

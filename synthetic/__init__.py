@@ -12,6 +12,8 @@ Workloads (sizes and parameters from the paper's cases, §3):
                     profile plus 10 % seeded noise, constant-pressure-gradient forcing (§3.4.1)
   cylinder_2d       cylinder of diameter D = 40 cells in a 16 D x 8 D box, uniform inflow,
                     free-slip sides, outflow, 126 markers (§3.1-3.2)
+  cylinder_array_2d an array of cylinders moving as one elastically mounted body (the
+                    immersed-boundary stress case: 32 x 32 cylinders, 102,400 markers)
   poiseuille_2d     periodic channel with no-slip walls and a uniform body force
 
 The initial fields are not made discretely divergence-free here; the first
@@ -40,6 +42,7 @@ class BodySpec:
     active: tuple = (False, False)
     w0: tuple = (0.0, 0.0)
     wd0: tuple = (0.0, 0.0)
+    contours: Optional[list] = None   # first marker of each closed contour (None: one contour)
 
 
 @dataclass
@@ -245,6 +248,54 @@ def cylinder_2d(nx=640, ny=320, cells_per_d=40, nm=126, re=150.0, mass_ratio=2.0
         rng = np.random.default_rng(seed)
         v[:, 1:-1, :] = perturb * U * rng.uniform(-1.0, 1.0, size=(1, ny - 1, nx))
     return Workload("cylinder_2d", 2, nn, xf, bc, bc_val, U * D / re, dt=dt, steps=steps,
+                    precision=precision, kernel=kernel, body=body, u0=[u, v])
+
+
+def cylinder_array_2d(rows=32, cols=32, cells_per_d=32, pitch_d=2.0, margin_d=(4.0, 1.0), nm_per=None,
+                      re=150.0, mass_ratio=2.0, reduced_velocity=5.0, U=1.0, dt=None, steps=100, kernel=ROMA3,
+                      precision="mixed", seed=5, perturb=0.01):
+    """A rows x cols array of cylinders (diameter D = 1 = cells_per_d cells, centres pitch_d D apart)
+    moving as one elastically mounted rigid body (1-DOF transverse), in the FSI set-up of
+    cylinder_2d: uniform inflow, zero-gradient outflow, free-slip y walls.  The immersed-boundary
+    stress case: nm_per markers per cylinder (default one per grid spacing, pi cells_per_d), each
+    cylinder a closed contour of its own.  Mass and stiffness scale with the number of cylinders
+    (m = m* rho N pi D^2 / 4), so the body has the single cylinder's natural frequency."""
+    D = 1.0
+    h = D / cells_per_d
+    nm_per = int(round(math.pi * cells_per_d)) if nm_per is None else int(nm_per)
+    nx = int(round((2 * margin_d[0] + cols * pitch_d) * cells_per_d))
+    ny = int(round((2 * margin_d[1] + rows * pitch_d) * cells_per_d))
+    nx += nx % 2
+    ny += ny % 2
+    Lx, Ly = nx * h, ny * h
+    xf = [uniform_faces(nx, Lx), uniform_faces(ny, Ly), np.array([0.0, 1.0])]
+    bc = [(INFLOW, OUTFLOW), (FREESLIP, FREESLIP)]
+    bc_val = [[[U, 0.0, 0.0], [0.0, 0.0, 0.0]], [[0.0] * 3, [0.0] * 3]]
+    Xs, Ys, Ss, starts = [], [], [], []
+    for r in range(rows):
+        for q in range(cols):
+            c = ((margin_d[0] + (q + 0.5) * pitch_d) * D, (margin_d[1] + (r + 0.5) * pitch_d) * D)
+            X, Y, ds = circle_markers(nm_per, D, c)
+            starts.append(len(Xs) * nm_per)
+            Xs.append(X)
+            Ys.append(Y)
+            Ss.append(ds)
+    X, Y, ds = np.concatenate(Xs), np.concatenate(Ys), np.concatenate(Ss)
+    ncyl = rows * cols
+    centre = (0.5 * Lx, 0.5 * Ly)
+    m = mass_ratio * ncyl * math.pi * D * D / 4.0
+    fn = U / (reduced_velocity * D)
+    k = m * (2.0 * math.pi * fn) ** 2
+    body = BodySpec(X, Y, ds, centre, mass=m, stiffness=k, damping=0.0, active=(False, True),
+                    contours=starts)
+    u = np.full((1, ny, nx + 1), U)
+    v = np.zeros((1, ny + 1, nx))
+    if seed is not None and perturb > 0:
+        rng = np.random.default_rng(seed)
+        v[:, 1:-1, :] = perturb * U * rng.uniform(-1.0, 1.0, size=(1, ny - 1, nx))
+    if dt is None:
+        dt = 0.2 * h
+    return Workload("cylinder_array_2d", 2, [nx, ny, 1], xf, bc, bc_val, U * D / re, dt=dt, steps=steps,
                     precision=precision, kernel=kernel, body=body, u0=[u, v])
 
 

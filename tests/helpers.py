@@ -29,7 +29,7 @@ def body_of(wl):
     b = wl.body
     if b is None:
         return None, None
-    body = oib.Body(b.X0, b.Y0, b.ds, b.centre, b.omega)
+    body = oib.Body(b.X0, b.Y0, b.ds, b.centre, b.omega, getattr(b, "contours", None))
     params = RigidParams(b.mass, b.stiffness, b.damping, b.active) if b.mass > 0 else None
     return body, params
 

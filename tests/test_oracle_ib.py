@@ -291,3 +291,31 @@ def test_marker_torque_closed_forms(kernel):
     f = [(fxu - cx).expand(g.shape(0)).clone(), (fyv - cy).expand(g.shape(1)).clone()]
     _, _, torque = ib.marker_forces(g, body, kernel, w, f)
     assert abs(float(torque)) < 1e-14
+
+
+def test_inside_test_of_several_contours_is_their_union():
+    """A body of several closed contours (an array of cylinders moving as one): a point is solid when
+    it lies inside one of the cylinders, against the distance to every centre (points within 2e-3 D of
+    a circle, where the 40-gon's chords depart from it, skipped), and the solid faces are the union of the single-cylinder classifications."""
+    wl = S.cylinder_array_2d(rows=2, cols=3, cells_per_d=8, nm_per=40)
+    b = wl.body
+    body = ib.Body(b.X0, b.Y0, b.ds, b.centre, 0.0, b.contours)
+    assert len(set(body.next)) == len(body.next) == b.X0.size
+    rng = np.random.default_rng(3)
+    px = torch.tensor(rng.uniform(3.5, 10.5, 6000))
+    py = torch.tensor(rng.uniform(0.5, 5.5, 6000))
+    cs = [(4.0 + (q + 0.5) * 2.0, 1.0 + (r + 0.5) * 2.0) for r in range(2) for q in range(3)]
+    dmin = torch.stack([torch.sqrt((px - cx) ** 2 + (py - cy) ** 2) for cx, cy in cs]).min(0).values
+    keep = (dmin - 0.5).abs() > 2e-3        # beyond the chords' sagitta 0.5 (1 - cos(pi / 40)) = 1.5e-3
+    inside = ib.inside_polygon(px, py, body.X0, body.Y0, body.next)
+    assert bool((inside[keep] == (dmin[keep] < 0.5)).all()) and int(inside.sum()) > 500
+    g = grid_of(wl)
+    w = torch.tensor([0.0, 0.037], dtype=torch.float64)
+    masks = ib.classify(g, body, w)
+    for c in range(2):
+        union = torch.zeros_like(masks[c][0])
+        for k in range(6):
+            sl = slice(b.contours[k], b.contours[k] + 40)
+            one = ib.Body(b.X0[sl], b.Y0[sl], b.ds[sl], b.centre)
+            union |= ib.classify(g, one, w)[c][0]
+        assert torch.equal(masks[c][0], union)
