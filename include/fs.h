@@ -92,9 +92,9 @@ typedef struct {
   double* body;
 } fs_state;
 
-/* Immersed body (§2.3.3): a closed polygon of Lagrangian markers, rigid,
- * translating with the displacement of fs_state.body, optionally elastically
- * mounted (Eq. 12). */
+/* Immersed body (§2.3.3): a closed polygon of Lagrangian markers, or several
+ * disjoint closed contours (an array of cylinders), rigid, translating with
+ * the displacement of fs_state.body, optionally elastically mounted (Eq. 12). */
 typedef struct {
   int nm;                  /* number of markers (>= 3) */
   const double* X0;        /* host: rest x of each marker, ordered around the surface */
@@ -107,6 +107,10 @@ typedef struct {
   double damping;          /* c */
   int active[2];           /* DOF mask: x, y */
   int delta_kernel;        /* FS_PESKIN4 | FS_ROMA3 */
+  int ncontour;            /* number of closed contours; 0 or 1: all markers form one contour */
+  const int* contour_start;/* host: ncontour increasing first-marker indices (the first 0), each
+                              contour >= 3 markers and closed on its own first marker; NULL when
+                              ncontour <= 1 */
 } fs_body_desc;
 
 /* Parameter-gradient accumulators filled by fs_step_adjoint (added to, never cleared). */
@@ -135,10 +139,17 @@ int fs_field_extent(const fs_grid* grid, int comp, int ext[3]);
 
 /* Attach a rigid body (2-D grids, uniform x and y near the body).  Marker
  * arrays are host memory and are copied.  Replaces any previous body.
- * Eqs. (18)-(23): solid faces (inside the polygon) and IB faces (non-solid
- * faces with a solid same-component neighbour) are forced; the target
- * velocity is the body velocity inside and the half-distribution-normalised
- * marker interpolation on IB faces.  Errors: FS_ERR_ARG, FS_ERR_UNSUPPORTED
+ * Eqs. (18)-(23): solid faces (inside the polygon: an odd number of edge
+ * crossings to their right) and IB faces (non-solid faces with a solid
+ * same-component neighbour) are forced; the target velocity is the body
+ * velocity inside and the half-distribution-normalised marker interpolation
+ * on IB faces.  Every step then classifies the faces row by row from the
+ * edges crossing each row (edges sorted by their lowest point, found by
+ * bisection), computes F_N (Eq. 19) per marker, and forms the interpolation
+ * on each IB face by gathering the markers of the nearby cells (markers
+ * binned by the cell of their rest position; the body only translates): a
+ * fixed summation order per face, so results are bitwise reproducible, with
+ * no atomics.  Errors: FS_ERR_ARG (bad contour list), FS_ERR_UNSUPPORTED
  * (3-D grid, RK3 grid). */
 int fs_set_ib_markers(fs_grid* grid, const fs_body_desc* body);
 
@@ -175,10 +186,30 @@ int fs_step(fs_grid* grid, fs_state* st, double dt, int nsteps);
  * parameter gradients to g.  dJdF: host, dim doubles, the sensitivity of the
  * loss to the hydrodynamic force of this step (may be NULL).  The forward
  * step is recomputed internally.  The epsilon mask is frozen (its derivative
- * is zero almost everywhere).  Errors: FS_ERR_UNSUPPORTED (rotating surface
- * with a body), FS_ERR_ARG, FS_ERR_CUDA. */
+ * is zero almost everywhere).
+ * Strongly coupled steps (fs_set_coupling with max_subiters > 1, elastically
+ * mounted body) are differentiated implicitly (§2.4.1) at the fixed point of
+ * Algorithm 1: the forward sub-iteration is re-run from st_n to its converged
+ * body state s* (synchronising once per sub-iteration, as fs_step does), the
+ * fluid step is linearised at (u^n, s*) and the body ODE at (s^n, F(u^n, s*)),
+ * and mu solves (I - B_F J_s)^T mu = lam_s + U_s^T lam_u + J_s^T dJdF (B the
+ * RK4 step, U the new velocity, J_s the force's dependence on the body
+ * kinematics), a 4 x 4 system solved on the device; then lam_s^n = B_s^T mu,
+ * lam_u^n = U_u^T lam_u + J_u^T (dJdF + B_F^T mu) and dJ/dk += B_k^T mu.  It
+ * costs the forward sub-iterations plus one fluid adjoint for the loss and one
+ * per active DOF, and synchronises the stream at its end (FS_ERR_DIVERGED when
+ * I - dB/ds is singular).  The body-force gradient is not provided there
+ * (FS_ERR_UNSUPPORTED).
+ * Errors: FS_ERR_UNSUPPORTED (rotating surface with a body, Smagorinsky model,
+ * static box body), FS_ERR_ARG, FS_ERR_CUDA. */
 int fs_step_adjoint(fs_grid* grid, const fs_state* st_n, fs_state* lam,
                     const double* dJdF, fs_param_grad* g, double dt);
+
+/* fs_step_adjoint with dJdF in device memory (dim doubles, or NULL): the
+ * reverse sweep of a rollout can then keep the per-step force sensitivities on
+ * the device and needs no host read between adjoint steps. */
+int fs_step_adjoint_dev(fs_grid* grid, const fs_state* st_n, fs_state* lam,
+                        const double* dJdF, fs_param_grad* g, double dt);
 
 /* One RK3 step (fs_step with nsteps = 1 and a fixed dt > 0) that leaves its two
  * intermediate stage states in v1[dim], v2[dim]: caller-owned device arrays
@@ -232,8 +263,8 @@ int fs_set_body_force(fs_grid* grid, const double* fx);
  * xi = |w_k - w_{k-1}|^2 / |w_{k-1}|^2 < tol (|w_k - w_{k-1}|^2 while w_{k-1} = 0)
  * or max_subiters fluid solves.  max_subiters = 1 (the default) is the weakly
  * coupled step.  Each sub-iteration reads xi on the host (one stream
- * synchronisation).  fs_step_adjoint returns FS_ERR_UNSUPPORTED for a grid
- * with max_subiters > 1.  Errors: FS_ERR_ARG (max_subiters < 1, tol <= 0). */
+ * synchronisation).  fs_step_adjoint differentiates such a step implicitly
+ * at its fixed point.  Errors: FS_ERR_ARG (max_subiters < 1, tol <= 0). */
 int fs_set_coupling(fs_grid* grid, int max_subiters, double tol);
 
 /* Constant-coefficient Smagorinsky subgrid model (§2.5; the LES of §3.4):
@@ -245,6 +276,11 @@ int fs_set_coupling(fs_grid* grid, int max_subiters, double tol);
  * fs_step_adjoint returns FS_ERR_UNSUPPORTED while it is on.
  * Errors: FS_ERR_ARG (cs < 0), FS_ERR_UNSUPPORTED, FS_ERR_CUDA. */
 int fs_set_les(fs_grid* grid, double cs);
+
+/* Number of IB faces (both components) classified by the last step of a grid with
+ * a 2-D body (host output; synchronises the grid's stream).  FS_ERR_STATE
+ * without a body. */
+int fs_ib_face_count(fs_grid* grid, int* count);
 
 /* Sub-iterations and final xi of the last strongly coupled step (host outputs, may be NULL). */
 int fs_coupling_stats(const fs_grid* grid, int* subiters, double* xi);

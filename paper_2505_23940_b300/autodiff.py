@@ -206,6 +206,8 @@ class Rollout:
             ops = revolve_schedule(self.n, slots)
         self.used_slots = slots
         lam = [x.clone() for x in lam_u]
+        if lam_forces is not None:
+            lam_forces = lam_forces.to(device=lam[0].device, dtype=torch.float64).contiguous()
         lb = lam_body.clone() if lam_body is not None else (
             torch.zeros(4, dtype=torch.float64, device=lam[0].device) if self.g.has_body else None)
         self.recomputed = 0
@@ -226,9 +228,8 @@ class Rollout:
                 mem[op[1]] = self._clone(work_u, work_b)
             elif op[0] == "adjoint":
                 t = op[1]
-                dJdF = None
-                if lam_forces is not None:
-                    dJdF = [float(x) for x in lam_forces[t, :2].tolist()]
+                # the force sensitivity of step t stays on the device (no host read per step)
+                dJdF = lam_forces[t, :2] if lam_forces is not None else None
                 self.g.step_adjoint(work_u, lam, self.dt, body_n=work_b, lam_body=lb, dJdF=dJdF,
                                     g_body_force=g_body_force, g_stiffness=g_stiffness)
         return lam, lb

@@ -752,6 +752,59 @@ __global__ void ib_force_adj_kernel(const IBAdjGeom G, int nm, const double* __r
   lamX[2 * t + 1] = lq * gy;
 }
 
+// Reverse of the RK4 step of Eq. (12) for one active DOF (FP64): from the adjoints
+// (lw1, lv1) of (w, wdot)^{n+1} to those of (w, wdot)^n (lx0, lv0), the adjoint of the
+// force lF and of the stiffness dk, linearised at the level-n state (x0, v0) and force f.
+__device__ void rk4_reverse_dof(double x0, double v0, double f, double lw1, double lv1, double m, double k, double c,
+                                double h, double& lx0_out, double& lv0_out, double& lF_out, double& dk_out) {
+  auto acc = [&](double x, double v) { return (f - c * v - k * x) / m; };
+  // forward stages
+  const double k1x = v0, k1v = acc(x0, v0);
+  const double x1 = x0 + 0.5 * h * k1x, v1 = v0 + 0.5 * h * k1v;
+  const double k2x = v1, k2v = acc(x1, v1);
+  const double x2 = x0 + 0.5 * h * k2x, v2 = v0 + 0.5 * h * k2v;
+  const double k3x = v2;
+  const double x3 = x0 + h * k3x;
+  double lF = 0.0, dk = 0.0;
+  // reverse
+  double lx0 = lw1, lv0 = lv1;
+  double lk1x = h / 6.0 * lw1, lk2x = h / 3.0 * lw1, lk3x = h / 3.0 * lw1, lk4x = h / 6.0 * lw1;
+  double lk1v = h / 6.0 * lv1, lk2v = h / 3.0 * lv1, lk3v = h / 3.0 * lv1, lk4v = h / 6.0 * lv1;
+  // k4v = acc(x3, v3), k4x = v3
+  double lx3 = -k / m * lk4v, lv3 = -c / m * lk4v + lk4x;
+  lF += lk4v / m;
+  dk += -x3 / m * lk4v;
+  lx0 += lx3;
+  lk3x += h * lx3;
+  lv0 += lv3;
+  lk3v += h * lv3;
+  // k3v = acc(x2, v2), k3x = v2
+  double lx2 = -k / m * lk3v, lv2 = -c / m * lk3v + lk3x;
+  lF += lk3v / m;
+  dk += -x2 / m * lk3v;
+  lx0 += lx2;
+  lk2x += 0.5 * h * lx2;
+  lv0 += lv2;
+  lk2v += 0.5 * h * lv2;
+  // k2v = acc(x1, v1), k2x = v1
+  double lx1 = -k / m * lk2v, lv1s = -c / m * lk2v + lk2x;
+  lF += lk2v / m;
+  dk += -x1 / m * lk2v;
+  lx0 += lx1;
+  lk1x += 0.5 * h * lx1;
+  lv0 += lv1s;
+  lk1v += 0.5 * h * lv1s;
+  // k1v = acc(x0, v0), k1x = v0
+  lx0 += -k / m * lk1v;
+  lv0 += -c / m * lk1v + lk1x;
+  lF += lk1v / m;
+  dk += -x0 / m * lk1v;
+  lx0_out = lx0;
+  lv0_out = lv0;
+  lF_out = lF;
+  dk_out = dk;
+}
+
 // Reverse of the RK4 step of Eq. (12) per active DOF; body state and adjoints in FP64.
 //   lamb:  in lam of (w, wdot)^{n+1}, out: lam of (w, wdot)^n from the ODE
 //   lamF:  out lam of F^n (plus the direct dJ/dF)
@@ -763,7 +816,7 @@ __global__ void rk4_adj_kernel(const double* __restrict__ st, const double* __re
   double dk = 0.0;
   for (int d = 0; d < 2; ++d) {
     const double lw1 = lamb[d], lv1 = lamb[2 + d];
-    double lF = dJdF[d];
+    const double lF = dJdF[d];
     if (!dynamic) {   // static body: state carried through unchanged
       lamF[d] = lF;
       continue;
@@ -774,56 +827,106 @@ __global__ void rk4_adj_kernel(const double* __restrict__ st, const double* __re
       lamF[d] = lF;
       continue;
     }
-    const double f = F[d], h = dt;
-    const double x0 = st[d], v0 = st[2 + d];
-    auto acc = [&](double x, double v) { return (f - c * v - k * x) / m; };
-    // forward stages
-    const double k1x = v0, k1v = acc(x0, v0);
-    const double x1 = x0 + 0.5 * h * k1x, v1 = v0 + 0.5 * h * k1v;
-    const double k2x = v1, k2v = acc(x1, v1);
-    const double x2 = x0 + 0.5 * h * k2x, v2 = v0 + 0.5 * h * k2v;
-    const double k3x = v2, k3v = acc(x2, v2);
-    const double x3 = x0 + h * k3x, v3 = v0 + h * k3v;
-    (void)k3x;
-    (void)v3;
-    // reverse
-    double lx0 = lw1, lv0 = lv1;
-    double lk1x = h / 6.0 * lw1, lk2x = h / 3.0 * lw1, lk3x = h / 3.0 * lw1, lk4x = h / 6.0 * lw1;
-    double lk1v = h / 6.0 * lv1, lk2v = h / 3.0 * lv1, lk3v = h / 3.0 * lv1, lk4v = h / 6.0 * lv1;
-    // k4v = acc(x3, v3), k4x = v3
-    double lx3 = -k / m * lk4v, lv3 = -c / m * lk4v + lk4x;
-    lF += lk4v / m;
-    dk += -x3 / m * lk4v;
-    lx0 += lx3;
-    lk3x += h * lx3;
-    lv0 += lv3;
-    lk3v += h * lv3;
-    // k3v = acc(x2, v2), k3x = v2
-    double lx2 = -k / m * lk3v, lv2 = -c / m * lk3v + lk3x;
-    lF += lk3v / m;
-    dk += -x2 / m * lk3v;
-    lx0 += lx2;
-    lk2x += 0.5 * h * lx2;
-    lv0 += lv2;
-    lk2v += 0.5 * h * lv2;
-    // k2v = acc(x1, v1), k2x = v1
-    double lx1 = -k / m * lk2v, lv1s = -c / m * lk2v + lk2x;
-    lF += lk2v / m;
-    dk += -x1 / m * lk2v;
-    lx0 += lx1;
-    lk1x += 0.5 * h * lx1;
-    lv0 += lv1s;
-    lk1v += 0.5 * h * lv1s;
-    // k1v = acc(x0, v0), k1x = v0
-    lx0 += -k / m * lk1v;
-    lv0 += -c / m * lk1v + lk1x;
-    lF += lk1v / m;
-    dk += -x0 / m * lk1v;
+    double lx0, lv0, lFo, dkd;
+    rk4_reverse_dof(st[d], st[2 + d], F[d], lw1, lv1, m, k, c, dt, lx0, lv0, lFo, dkd);
     lamb[d] = lx0;
     lamb[2 + d] = lv0;
-    lamF[d] = lF;
+    lamF[d] = lF + lFo;
+    dk += dkd;
   }
   if (gk) *gk += dk;
+}
+
+// Implicit-differentiation solve of the strongly coupled step (§2.4.1, the
+// fixed point s* = B(s^n, F(u^n, s*), k) of Algorithm 1), one thread, FP64.
+//   sig    lam of the step's output body state s* (the caller's lam->body)
+//   base   the fluid adjoint's body part for the loss seeds: U_s^T lam_u + J_s^T dJdF
+//   unit   the fluid adjoint's body part for a unit force adjoint e_d: J_s^T e_d (4 per DOF)
+// Forms dB/ds* = B_F J_s (B_F^T from the RK4 reverse of unit adjoints), solves
+// (I - dB/ds*)^T mu = sig + base by Gaussian elimination with partial pivoting,
+// and writes lam of s^n = B_s^T mu into lamb, beta = B_F^T mu (the force adjoint the
+// fluid solves add on top of dJdF) and dJ/dk += B_k^T mu.
+__global__ void coupled_adj_solve_kernel(const double* __restrict__ s_n, const double* __restrict__ F,
+                                         const double* __restrict__ sig, const double* __restrict__ base,
+                                         const double* __restrict__ unit, double m, double k, double c, int ax,
+                                         int ay, double dt, double* __restrict__ lamb, double* __restrict__ beta,
+                                         double* __restrict__ gk, int* __restrict__ singular) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int act[2] = {ax, ay};
+  double BFt[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};   // (B_F^T e_j)_d
+  double Bst[4][4] = {};                              // column j: B_s^T e_j
+  double Bk[4] = {0, 0, 0, 0};
+  for (int j = 0; j < 4; ++j)
+    for (int d = 0; d < 2; ++d) {
+      if (!act[d]) continue;
+      const double lw1 = j == d ? 1.0 : 0.0, lv1 = j == 2 + d ? 1.0 : 0.0;
+      if (lw1 == 0.0 && lv1 == 0.0) continue;
+      double lx0, lv0, lF, dk;
+      rk4_reverse_dof(s_n[d], s_n[2 + d], F[d], lw1, lv1, m, k, c, dt, lx0, lv0, lF, dk);
+      BFt[d][j] = lF;
+      Bst[d][j] = lx0;
+      Bst[2 + d][j] = lv0;
+      Bk[j] = dk;
+    }
+  // A = (I - dB/ds*)^T = I - M, M[i][j] = sum_d unit_d[i] BFt[d][j]
+  double A[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      double mij = 0.0;
+      for (int d = 0; d < 2; ++d)
+        if (act[d]) mij += unit[4 * d + i] * BFt[d][j];
+      A[i][j] = (i == j ? 1.0 : 0.0) - mij;
+    }
+    A[i][4] = sig[i] + base[i];
+  }
+  for (int col = 0; col < 4; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < 4; ++r)
+      if (fabs(A[r][col]) > fabs(A[piv][col])) piv = r;
+    if (!(fabs(A[piv][col]) > 0.0)) {
+      *singular = 1;
+      return;
+    }
+    if (piv != col)
+      for (int q = 0; q < 5; ++q) {
+        const double t = A[col][q];
+        A[col][q] = A[piv][q];
+        A[piv][q] = t;
+      }
+    for (int r = col + 1; r < 4; ++r) {
+      const double f = A[r][col] / A[col][col];
+      for (int q = col; q < 5; ++q) A[r][q] -= f * A[col][q];
+    }
+  }
+  double mu[4];
+  for (int i = 3; i >= 0; --i) {
+    double r = A[i][4];
+    for (int q = i + 1; q < 4; ++q) r -= A[i][q] * mu[q];
+    mu[i] = r / A[i][i];
+  }
+  double dk = 0.0;
+  for (int i = 0; i < 4; ++i) {
+    double r = 0.0;
+    for (int j = 0; j < 4; ++j) r += Bst[i][j] * mu[j];
+    lamb[i] = r;
+    dk += Bk[i] * mu[i];
+  }
+  for (int d = 0; d < 2; ++d) {
+    double r = 0.0;
+    for (int j = 0; j < 4; ++j) r += BFt[d][j] * mu[j];
+    beta[d] = r;
+  }
+  if (gk) *gk += dk;
+  *singular = 0;
+}
+
+// y += (*alpha) x (alpha read on the device)
+template <typename T>
+__global__ void axpy_dev_kernel(T* __restrict__ y, const T* __restrict__ x, const double* __restrict__ alpha,
+                                long long n) {
+  const T a = T(*alpha);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] += a * x[t];
 }
 
 // lam of (w, wdot)^n += position adjoint (sum over markers) + fluid sums of the body velocity.
@@ -1000,6 +1103,11 @@ struct AdjBuffers {
   void* lamf[2] = {nullptr, nullptr};
   void* lamout = nullptr;
   double* scal = nullptr;   // [0..1] lamF, [2..3] wdsum, [4..5] dJdF, [8..] lamX (2 * 2 * nm)
+  // strongly coupled steps: a copy of the state for the forward re-run, the fluid
+  // adjoint of a unit force adjoint per DOF, and the small FP64 work vectors
+  void* cu[3] = {nullptr, nullptr, nullptr};
+  void* ld[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  double* cd = nullptr;
 };
 
 int adj_buffers(fs_grid* G, AdjBuffers** out) {
@@ -1048,12 +1156,113 @@ void free_adj_buffers(void* p) {
   F(B->lamf[1]);
   F(B->lamout);
   F(B->scal);
+  for (int c = 0; c < 3; ++c) {
+    F(B->cu[c]);
+    F(B->ld[0][c]);
+    F(B->ld[1][c]);
+  }
+  F(B->cd);
   delete B;
+}
+
+int coupled_buffers(fs_grid* G, AdjBuffers* B) {
+  if (B->cd) return FS_OK;
+  const size_t es = G->prec == FS_MIXED ? 4 : 8;
+  bool ok = true;
+  for (int c = 0; c < G->dim && ok; ++c) {
+    const size_t n = comp_count(G, c) * es;
+    ok = cudaMalloc(&B->cu[c], n) == cudaSuccess && cudaMalloc(&B->ld[0][c], n) == cudaSuccess &&
+         cudaMalloc(&B->ld[1][c], n) == cudaSuccess;
+  }
+  if (ok) ok = cudaMalloc(&B->cd, 32 * sizeof(double)) == cudaSuccess;
+  if (!ok) return set_error(FS_ERR_CUDA, "allocating the coupled adjoint buffers");
+  return FS_OK;
+}
+
+// Recompute the forward-Euler step's classification, u*, forcing f and force F from
+// the velocity u and the body kinematics s_lin (the point the adjoint is linearised at).
+template <typename T>
+void fe_body_recompute(fs_grid* G, T* const* u, double* s_lin, double dt) {
+  T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
+  ib_prepare<T>(G, s_lin);
+  launch_outflow_flux<T>(G, u);
+  launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, s_lin);
+  ib_forces<T>(G, s_lin);
+}
+
+// Fluid part of the forward-Euler adjoint: lam of u^{n+1} in L is overwritten with
+// lam of u^n.  With a body (s_lin not null; the forward quantities recomputed at
+// s_lin by fe_body_recompute), lamF (device, 2) is the adjoint of the step's force,
+// spread back to the forcing term (Eq. 20 transposed), and lamb (device, 4) receives
+// the fluid's dependence on the body kinematics: the marker-position adjoint and the
+// adjoint of the body velocity imposed on forced faces.
+template <typename T>
+void fe_fluid_adjoint(fs_grid* G, AdjBuffers* B, T* const* u, const double* s_lin, T* const* L, const double* lamF,
+                      double* lamb, double* bfsum, double dt) {
+  const Geom<T> g = G->geom<T>();
+  const int X = G->nx + (G->per[0] ? 0 : 1), Y = G->ny + (G->per[1] ? 0 : 1);
+  const dim3 blk = stencil_block(G), grd = stencil_grid(G, X, Y);
+  T* mu[3] = {(T*)B->mu[0], (T*)B->mu[1], (T*)B->mu[2]};
+  T* ln[3] = {(T*)B->lamn[0], (T*)B->lamn[1], (T*)B->lamn[2]};
+  T* spec = (T*)G->spec;
+  IBDev& ib = G->ib;
+  double* sc = B->scal;
+  const bool body = s_lin != nullptr;
+  if (body) {
+    for (int c = 0; c < 2; ++c) cudaMemsetAsync(B->lamf[c], 0, comp_count(G, c) * sizeof(T), G->stream);
+    cudaMemsetAsync(sc + 2, 0, 2 * sizeof(double), G->stream);
+    // force reverse: lam_f on the grid, marker position adjoint
+    const IBAdjGeom ig = make_ib_adj_geom(G);
+    FS_LAUNCH(G, "ib_force_adjoint", ib_force_adj_kernel<T><<<(2 * ib.nm + 127) / 128, 128, 0, G->stream>>>(
+                                         ig, ib.nm, ib.X0, ib.Y0, ib.ds, s_lin, lamF, G->rho, (const T*)ib.f[0],
+                                         (const T*)ib.f[1], (T*)B->lamf[0], (T*)B->lamf[1], sc + 8));
+  }
+  launch_projection_adjoint_solve<T>(G, L, spec);
+  FaceAdjArgs<T> A{};
+  A.g = g;
+  for (int c = 0; c < 3; ++c) {
+    A.lam1[c] = L[c];
+    A.mu[c] = mu[c];
+    A.lamn[c] = ln[c];
+  }
+  A.y = spec;
+  A.hy = G->hy64;
+  A.dt = (T)dt;
+  A.rk = 0;
+  if (body) {
+    A.flags[0] = ib.flags[0];
+    A.flags[1] = ib.flags[1];
+    A.lamf[0] = (const T*)B->lamf[0];
+    A.lamf[1] = (const T*)B->lamf[1];
+    A.wdsum = sc + 2;
+  }
+  A.bfsum = bfsum;
+  A.lamout = (T*)B->lamout;
+  A.X = X;
+  A.Y = Y;
+  FS_LAUNCH(G, "face_adjoint", face_adj_kernel<T><<<grd, blk, 0, G->stream>>>(A));
+  launch_rhs_adjoint<T>(G, u, mu, ln);
+  if (!G->per[0] && G->bc[0][1] == FS_BC_OUTFLOW) {
+    double q_in = 0.0;
+    if (G->bc[0][0] == FS_BC_INFLOW) {
+      double area = 0.0;
+      for (int j = 0; j < G->ny; ++j) area += G->h[1][j];
+      area *= (G->dim == 3 ? G->hz * G->nz : 1.0);
+      q_in = G->bcv[0][0][0] * area;
+    }
+    FS_LAUNCH(G, "outflow_adjoint", outflow_adj_kernel<T><<<1, kT, 0, G->stream>>>(
+                                        u[0], (const T*)B->lamout, ln[0], G->nx + 1, G->ny, G->nz, G->hy64,
+                                        G->dim == 3 ? G->hz : 1.0, q_in));
+  }
+  if (body)
+    FS_LAUNCH(G, "body_adjoint", body_adj_finish_kernel<<<1, kT, 0, G->stream>>>(ib.nm, sc + 8, sc + 2, lamb));
+  for (int c = 0; c < G->dim; ++c)
+    cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
 }
 
 template <typename T>
 int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJdF, fs_param_grad* pg, double dt,
-                 void* const* rv1, void* const* rv2) {
+                 void* const* rv1, void* const* rv2, bool dJdF_on_device) {
   AdjBuffers* B = nullptr;
   int rc = adj_buffers(G, &B);
   if (rc != FS_OK) return rc;
@@ -1145,81 +1354,132 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
   // ---- forward Euler (optional body) ------------------------------------------
   IBDev& ib = G->ib;
   double* sc = B->scal;
-  const bool body = G->has_body;
-  if (body) {
+  if (G->has_body) {
     // recompute the classification, u*, f and F of the forward step from the state at n
-    T* us[3] = {(T*)G->ustar[0], (T*)G->ustar[1], (T*)G->ustar[2]};
-    ib_prepare<T>(G, st->body);
-    launch_outflow_flux<T>(G, u);
-    launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
-    ib_forces<T>(G, st->body);
-    double h4[4] = {dJdF ? dJdF[0] : 0.0, dJdF ? dJdF[1] : 0.0, 0.0, 0.0};
-    cudaMemcpyAsync(sc + 4, h4, 2 * sizeof(double), cudaMemcpyHostToDevice, G->stream);
-    cudaMemsetAsync(sc + 2, 0, 2 * sizeof(double), G->stream);
+    fe_body_recompute<T>(G, u, st->body, dt);
+    if (dJdF_on_device) {
+      if (dJdF) cudaMemcpyAsync(sc + 4, dJdF, 2 * sizeof(double), cudaMemcpyDeviceToDevice, G->stream);
+      else cudaMemsetAsync(sc + 4, 0, 2 * sizeof(double), G->stream);
+    } else {
+      double h4[2] = {dJdF ? dJdF[0] : 0.0, dJdF ? dJdF[1] : 0.0};
+      cudaMemcpyAsync(sc + 4, h4, 2 * sizeof(double), cudaMemcpyHostToDevice, G->stream);
+    }
     // body ODE reverse: lam of (w, wdot)^{n+1} -> ODE part of lam^n, lam_F, dJ/dk
     FS_LAUNCH(G, "rk4_adjoint", rk4_adj_kernel<<<1, 32, 0, G->stream>>>(
                                     st->body, ib.F, lam->body, sc, sc + 4, ib.mass, ib.k, ib.c, ib.active[0],
                                     ib.active[1], dt, ib.mass > 0 ? 1 : 0, pg ? pg->stiffness : nullptr));
-    // force reverse: lam_f on the grid, marker position adjoint
-    for (int c = 0; c < 2; ++c) cudaMemsetAsync(B->lamf[c], 0, comp_count(G, c) * sizeof(T), G->stream);
-    const IBAdjGeom ig = make_ib_adj_geom(G);
-    FS_LAUNCH(G, "ib_force_adjoint", ib_force_adj_kernel<T><<<(2 * ib.nm + 127) / 128, 128, 0, G->stream>>>(
-                                         ig, ib.nm, ib.X0, ib.Y0, ib.ds, st->body, sc, G->rho, (const T*)ib.f[0],
-                                         (const T*)ib.f[1], (T*)B->lamf[0], (T*)B->lamf[1], sc + 8));
-  } else if (G->bc[0][1] == FS_BC_OUTFLOW && !G->per[0]) {
+    fe_fluid_adjoint<T>(G, B, u, st->body, L, sc, lam->body, bfsum, dt);
+    return cuda_check(cudaGetLastError(), "fs_step_adjoint");
+  }
+  if (G->bc[0][1] == FS_BC_OUTFLOW && !G->per[0]) {
     launch_outflow_flux<T>(G, u);
   } else if (gather_fast(G) && proj_adj_fast<T>(G, L, la, ln)) {
     launch_proj_adj_fast<T>(G, L, 0.0, 1.0, dt, false, bfsum, la, ln);
     launch_rhs_adjoint_gather<T>(G, u, ln, dt, L);
     return cuda_check(cudaGetLastError(), "fs_step_adjoint");
   }
-  launch_projection_adjoint_solve<T>(G, L, spec);
-  FaceAdjArgs<T> A{};
-  A.g = g;
-  for (int c = 0; c < 3; ++c) {
-    A.lam1[c] = L[c];
-    A.mu[c] = mu[c];
-    A.lamn[c] = ln[c];
-  }
-  A.y = spec;
-  A.hy = G->hy64;
-  A.dt = (T)dt;
-  A.rk = 0;
-  if (body) {
-    A.flags[0] = ib.flags[0];
-    A.flags[1] = ib.flags[1];
-    A.lamf[0] = (const T*)B->lamf[0];
-    A.lamf[1] = (const T*)B->lamf[1];
-    A.wdsum = sc + 2;
-  }
-  A.bfsum = bfsum;
-  A.lamout = (T*)B->lamout;
-  A.X = X;
-  A.Y = Y;
-  FS_LAUNCH(G, "face_adjoint", face_adj_kernel<T><<<grd, blk, 0, G->stream>>>(A));
-  launch_rhs_adjoint<T>(G, u, mu, ln);
-  if (!G->per[0] && G->bc[0][1] == FS_BC_OUTFLOW) {
-    double q_in = 0.0;
-    if (G->bc[0][0] == FS_BC_INFLOW) {
-      double area = 0.0;
-      for (int j = 0; j < G->ny; ++j) area += G->h[1][j];
-      area *= (G->dim == 3 ? G->hz * G->nz : 1.0);
-      q_in = G->bcv[0][0][0] * area;
-    }
-    FS_LAUNCH(G, "outflow_adjoint", outflow_adj_kernel<T><<<1, kT, 0, G->stream>>>(
-                                        u[0], (const T*)B->lamout, ln[0], G->nx + 1, G->ny, G->nz, G->hy64,
-                                        G->dim == 3 ? G->hz : 1.0, q_in));
-  }
-  if (body)
-    FS_LAUNCH(G, "body_adjoint", body_adj_finish_kernel<<<1, kT, 0, G->stream>>>(ib.nm, sc + 8, sc + 2, lam->body));
-  for (int c = 0; c < dim; ++c)
-    cudaMemcpyAsync(L[c], ln[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, G->stream);
+  fe_fluid_adjoint<T>(G, B, u, nullptr, L, nullptr, nullptr, bfsum, dt);
   return cuda_check(cudaGetLastError(), "fs_step_adjoint");
 }
 
+// Adjoint of the strongly coupled forward-Euler FSI step (§2.3.3 Algorithm 1,
+// differentiated implicitly as in §2.4.1).  The forward sub-iteration is re-run
+// from st_n to its converged body state s*; the fluid step is linearised at
+// (u^n, s*) and the body step at (s^n, F(u^n, s*)).  With U the fluid's new
+// velocity, F its force, B the RK4 step and J_s, J_u the force's partial
+// derivatives:
+//   mu solves (I - B_F J_s)^T mu = lam_s + U_s^T lam_u + J_s^T dJdF,
+//   lam_u^n = U_u^T lam_u + J_u^T (dJdF + B_F^T mu),  lam_s^n = B_s^T mu,
+//   dJ/dk += B_k^T mu.
+// The fluid adjoint is run once for the loss seeds and once per active DOF for a
+// unit force adjoint (J_u^T e_d, J_s^T e_d); the 4 x 4 system is solved on the device.
+template <typename T>
+int step_adjoint_coupled(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJdF, bool dJdF_on_device,
+                         fs_param_grad* pg, double dt) {
+  AdjBuffers* B = nullptr;
+  int rc = adj_buffers(G, &B);
+  if (rc != FS_OK) return rc;
+  rc = coupled_buffers(G, B);
+  if (rc != FS_OK) return rc;
+  if (pg && pg->body_force)
+    return set_error(FS_ERR_UNSUPPORTED, "body-force gradient of a strongly coupled FSI step");
+  IBDev& ib = G->ib;
+  cudaStream_t s = G->stream;
+  const int dim = G->dim;
+  T* u[3] = {(T*)st->u[0], (T*)st->u[1], nullptr};
+  T* L[3] = {(T*)lam->u[0], (T*)lam->u[1], nullptr};
+  double* d = B->cd;
+  double* s_star = d;          // [0..3]
+  double* sig = d + 4;         // [4..7]
+  double* base = d + 8;        // [8..11]
+  double* unit = d + 12;       // [12..19], 4 per DOF
+  double* fbar = d + 20;       // [20..21]
+  double* e = d + 22;          // [22..25] unit force adjoints e_0, e_1
+  double* beta = d + 26;       // [26..27]
+  int* singular = (int*)(d + 28);
+  // 1. the converged body state of the forward step, from copies of st_n
+  for (int c = 0; c < dim; ++c)
+    cudaMemcpyAsync(B->cu[c], st->u[c], comp_count(G, c) * sizeof(T), cudaMemcpyDeviceToDevice, s);
+  cudaMemcpyAsync(s_star, st->body, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  fs_state tmp{};
+  for (int c = 0; c < dim; ++c) tmp.u[c] = B->cu[c];
+  tmp.body = s_star;
+  const int iters = G->fsi_last_iters;
+  const double xi = G->fsi_last_xi;
+  rc = step_coupled<T>(G, &tmp, dt, false);
+  G->fsi_last_iters = iters;
+  G->fsi_last_xi = xi;
+  if (rc != FS_OK) return rc;
+  // 2. the fluid step at (u^n, s*): classification, u*, f and F*
+  fe_body_recompute<T>(G, u, s_star, dt);
+  // 3. seeds
+  cudaMemcpyAsync(sig, lam->body, 4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  if (dJdF_on_device) {
+    if (dJdF) cudaMemcpyAsync(fbar, dJdF, 2 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(fbar, 0, 2 * sizeof(double), s);
+  } else {
+    const double h2[2] = {dJdF ? dJdF[0] : 0.0, dJdF ? dJdF[1] : 0.0};
+    cudaMemcpyAsync(fbar, h2, 2 * sizeof(double), cudaMemcpyHostToDevice, s);
+  }
+  const double he[4] = {1.0, 0.0, 0.0, 1.0};
+  cudaMemcpyAsync(e, he, 4 * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaMemsetAsync(base, 0, 12 * sizeof(double), s);
+  // 4. fluid adjoints: the loss seeds, then a unit force adjoint per active DOF
+  fe_fluid_adjoint<T>(G, B, u, s_star, L, fbar, base, nullptr, dt);
+  for (int q = 0; q < 2; ++q) {
+    if (!ib.active[q]) continue;
+    T* Lq[3] = {(T*)B->ld[q][0], (T*)B->ld[q][1], nullptr};
+    for (int c = 0; c < dim; ++c) cudaMemsetAsync(Lq[c], 0, comp_count(G, c) * sizeof(T), s);
+    fe_fluid_adjoint<T>(G, B, u, s_star, Lq, e + 2 * q, unit + 4 * q, nullptr, dt);
+  }
+  // 5. the implicit system, then lam_u^n += beta_d J_u^T e_d
+  FS_LAUNCH(G, "coupled_adjoint_solve", coupled_adj_solve_kernel<<<1, 32, 0, s>>>(
+                                            st->body, ib.F, sig, base, unit, ib.mass, ib.k, ib.c, ib.active[0],
+                                            ib.active[1], dt, lam->body, beta, pg ? pg->stiffness : nullptr,
+                                            singular));
+  for (int q = 0; q < 2; ++q) {
+    if (!ib.active[q]) continue;
+    for (int c = 0; c < dim; ++c) {
+      const long long n = (long long)comp_count(G, c);
+      FS_LAUNCH(G, "axpy", axpy_dev_kernel<T><<<(int)std::min<long long>((n + 255) / 256, 148 * 16), 256, 0, s>>>(
+                               L[c], (const T*)B->ld[q][c], beta + q, n));
+    }
+  }
+  int hs = 0;
+  cudaError_t err = cudaMemcpyAsync(&hs, singular, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_check(err, "fs_step_adjoint (strong coupling)");
+  if (hs) return set_error(FS_ERR_DIVERGED, "fs_step_adjoint: singular coupling system (I - dB/ds)");
+  return cuda_check(cudaGetLastError(), "fs_step_adjoint (strong coupling)");
+}
+
 template int step_adjoint<float>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double,
-                                  void* const*, void* const*);
+                                  void* const*, void* const*, bool);
 template int step_adjoint<double>(fs_grid*, const fs_state*, fs_state*, const double*, fs_param_grad*, double,
-                                   void* const*, void* const*);
+                                   void* const*, void* const*, bool);
+template int step_adjoint_coupled<float>(fs_grid*, const fs_state*, fs_state*, const double*, bool, fs_param_grad*,
+                                         double);
+template int step_adjoint_coupled<double>(fs_grid*, const fs_state*, fs_state*, const double*, bool,
+                                          fs_param_grad*, double);
 
 }  // namespace fs

@@ -100,6 +100,34 @@ FSCONV_FN uint32_t fsconv_narrow_fast(uint32_t hi, uint32_t lo, uint32_t* specia
   return zero ? sign : (sign | r);
 }
 
+// The binary64 product RN(e * f) of a binary32 value f (bits u) and a binary64 value e (words
+// ehi, elo), rounded to nearest even once, from integer products of the significands (24 x 53
+// bits, 77 exact bits): the multiply of the twisted y solve's scaled elimination, moved off the
+// FP64 pipe.  Fast path: f and e normal or zero with a normal (or zero) result; `special` is set
+// for every other input, which the caller multiplies in FP64 instead.
+FSCONV_FN void fsconv_scale_fast(uint32_t u, uint32_t ehi, uint32_t elo, uint32_t* hi, uint32_t* lo,
+                                 uint32_t* special) {
+  const uint32_t sign = (u ^ ehi) & 0x80000000u;
+  const uint32_t fm = u & 0x7fffffffu, em = ehi & 0x7fffffffu;
+  const uint32_t e8 = fm >> 23, e11 = em >> 20;
+  const int fz = fm == 0u, ez = (em | elo) == 0u, zero = fz || ez;
+  const uint64_t mf = (uint64_t)((fm & 0x7fffffu) | 0x800000u);
+  const uint64_t p_lo = mf * elo;                                              // < 2^56
+  const uint64_t p_hi = mf * (uint64_t)((em & 0xfffffu) | 0x100000u) + (p_lo >> 32);   // P >> 32 < 2^45
+  const uint32_t p_lw = (uint32_t)p_lo;                                        // P mod 2^32
+  const uint32_t sh = 23u + (uint32_t)(p_hi >> 44);                            // 24 when P >= 2^76
+  uint64_t r = (p_hi << (32u - sh)) | (uint64_t)(p_lw >> sh);                  // P >> sh, 53 bits
+  const uint32_t rem = p_lw & ((1u << sh) - 1u), half = 1u << (sh - 1u);
+  r += (uint64_t)((rem > half) | ((rem == half) & (uint32_t)(r & 1u)));
+  // biased exponent of r / 2^52; a rounding carry to 2^53 steps it (the fraction bits are then 0)
+  const int32_t eb = (int32_t)e8 + (int32_t)e11 + (int32_t)sh - 150 + (int32_t)(r >> 53);
+  const uint64_t bits = ((uint64_t)(uint32_t)eb << 52) + (r & 0xfffffffffffffull);
+  const int fin = (e8 - 1u < 254u || fz) && (e11 - 1u < 2046u || ez);
+  *special |= (uint32_t)(!fin || (!zero && (eb < 1 || eb > 2046)));
+  *hi = zero ? sign : (sign | (uint32_t)(bits >> 32));
+  *lo = zero ? 0u : (uint32_t)bits;
+}
+
 #ifdef __CUDACC__
 __device__ __forceinline__ double fsconv_widen(float f) {
   uint32_t hi, lo;

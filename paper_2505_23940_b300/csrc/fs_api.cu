@@ -155,6 +155,7 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
   auto pos = [&](int j) { return j < R ? j : R + (odd ? 1 : 0) + (L - 1 - j); };
   std::vector<double> M((size_t)rows * nlp, 0.0), E((size_t)rows * nlp, 0.0), C((size_t)rows * nlp, 0.0);
   std::vector<double> P((size_t)4 * nlam, 0.0), Z, S;
+  std::vector<int> K(nlam, 0);
   if (cyc) {
     Z.assign((size_t)rows * nlp, 0.0);
     S.assign((size_t)4 * nlam, 0.0);
@@ -209,10 +210,21 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
       const double det = beta[k] * beta[k + 1] - cc[k] * aa[k + 1];
       const double p[4] = {beta[k + 1] / det, -cc[k] / det, -aa[k + 1] / det, beta[k] / det};
       for (int q = 0; q < 4; ++q) P[(size_t)li * 4 + q] = p[q];
+      // scaled elimination: the sweeps carry g^_j = E_j g_j, so the outward pass is one multiply-add,
+      //   g^_j = s_j d_j + M^_j g^_prev,   x_j = g^_j + C_j x_next,
+      // with s_j = E_j except at the two middle rows (s = 1: the 2 x 2 solve takes the plain g_k, h_k+1)
+      // and M^_j = s_j M_j / s_prev, i.e. -a_j e_j (upper) or -c_j e_j (lower), -a_k / -c_k+1 at the middle
+      // rows and 0 where M_j = 0.  The products s_j d_j are formed as the tile is widened.
       for (int j = 0; j < L; ++j) {
         const size_t o = at(pos(j), li);
-        M[o] = m[j];
-        E[o] = ee[j];
+        const bool mid = j == k || j == k + 1;
+        double mh = 0.0;
+        if (m[j] != 0.0) {
+          if (j <= k) mh = j == k ? -aa[j] : -aa[j] * e[j];
+          else mh = j == k + 1 ? -cc[j] : -cc[j] * e[j];
+        }
+        M[o] = mh;
+        E[o] = mid ? 1.0 : ee[j];
         C[o] = cm[j];
       }
       if (odd) E[at(R, li)] = 1.0;   // the inert slot keeps its value
@@ -230,6 +242,16 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
         for (int j = k - 1; j >= 0; --j) x[j] = ee[j] * gh[j] + cm[j] * x[j + 1];
         for (int j = k + 2; j < L; ++j) x[j] = ee[j] * gh[j] + cm[j] * x[j - 1];
         for (int j = 0; j < L; ++j) Z[at(pos(j), li)] = x[j];
+        // positions (from each thread's first) beyond which |z| < 2^-56 max |z|: the correction
+        // x = y - xi z changes nothing there at FP64 precision and is skipped
+        double zmax = 0.0;
+        for (int j = 0; j < L; ++j) zmax = std::max(zmax, std::fabs(x[j]));
+        int kz = 1;
+        for (int p = 0; p < 2 * R; ++p) {
+          const int j = p < R ? p : (odd && p == R ? -1 : L - 1 - (p - R - (odd ? 1 : 0)));
+          if (j >= 0 && std::fabs(x[j]) > std::ldexp(zmax, -56)) kz = std::max(kz, (p < R ? p : p - R) + 1);
+        }
+        K[li] = kz;
         const double sigma = bb[ny - 1] - cc[ny - 1] * x[0] - aa[ny - 1] * x[L - 1];
         S[(size_t)li * 4 + 0] = cc[ny - 1];
         S[(size_t)li * 4 + 1] = aa[ny - 1];
@@ -238,7 +260,9 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
     }
   }
   if (upload(&G->twM, M) != cudaSuccess || upload(&G->twE, E) != cudaSuccess || upload(&G->twC, C) != cudaSuccess ||
-      upload(&G->twP, P) != cudaSuccess || (cyc && (upload(&G->twZ, Z) != cudaSuccess || upload(&G->twS, S) != cudaSuccess)))
+      upload(&G->twP, P) != cudaSuccess ||
+      (cyc && (upload(&G->twZ, Z) != cudaSuccess || upload(&G->twS, S) != cudaSuccess ||
+               upload(&G->twK, K) != cudaSuccess)))
     return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");
   return FS_OK;
 }
@@ -432,6 +456,8 @@ void free_ytables(fs_grid* G) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
+  if (G->twK) cudaFree(G->twK);
+  G->twK = nullptr;
 }
 
 void free_all(fs_grid* G) {
@@ -451,9 +477,10 @@ void free_all(fs_grid* G) {
   F(G->lamy); F(G->lamxz);
   free_ytables(G);
   IBDev& B = G->ib;
-  F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
+  F(B.X0); F(B.Y0); F(B.ds); F(B.order);
+  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
-  F(B.fn); F(B.q); F(B.F); F(B.ticket);
+  F(B.fn); F(B.q); F(B.part); F(B.F); F(B.ticket);
 }
 
 void free_body(fs_grid* G) {
@@ -461,9 +488,10 @@ void free_body(fs_grid* G) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
   };
-  F(B.X0); F(B.Y0); F(B.ds); F(B.PX); F(B.PY); F(B.order);
+  F(B.X0); F(B.Y0); F(B.ds); F(B.order);
+  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
-  F(B.fn); F(B.q); F(B.F); F(B.ticket);
+  F(B.fn); F(B.q); F(B.part); F(B.F); F(B.ticket);
   B = IBDev();
   G->has_body = false;
 }
@@ -520,6 +548,8 @@ __global__ void couple_kernel(double* __restrict__ st, const double* __restrict_
   for (int q = 0; q < 4; ++q) st[q] = nb[q];
 }
 
+}  // namespace
+
 // Strongly coupled forward-Euler FSI step (§2.3.3, Algorithm 1): sub-iterate the
 // fluid solve (kinematics of the current body iterate, from u^n) and the body
 // ODE (from the body at level n, with the force of that solve) until the
@@ -571,7 +601,9 @@ int step_coupled(fs_grid* G, fs_state* st, double dt, bool want_p) {
   return FS_OK;
 }
 
-}  // namespace
+template int step_coupled<float>(fs_grid*, fs_state*, double, bool);
+template int step_coupled<double>(fs_grid*, fs_state*, double, bool);
+
 }  // namespace fs
 
 using namespace fs;
@@ -968,39 +1000,101 @@ int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
   B.c = b->damping;
   B.active[0] = b->active[0];
   B.active[1] = b->active[1];
-  // polygon in surface order, bounding box with a margin so the early-out never decides a point near an edge
-  std::vector<double> PX(b->X0, b->X0 + b->nm), PY(b->Y0, b->Y0 + b->nm);
-  double xmin = PX[0], xmax = PX[0], ymin = PY[0], ymax = PY[0];
-  for (int m = 0; m < b->nm; ++m) {
-    xmin = std::min(xmin, PX[m]);
-    xmax = std::max(xmax, PX[m]);
-    ymin = std::min(ymin, PY[m]);
-    ymax = std::max(ymax, PY[m]);
+  // contours: vertex m is joined to nxt[m] (each contour closes on its first vertex)
+  const int nm = b->nm;
+  std::vector<int> nxt(nm);
+  {
+    std::vector<int> starts;
+    if (b->ncontour > 1) {
+      if (!b->contour_start) return set_error(FS_ERR_ARG, "ncontour > 1 needs contour_start");
+      starts.assign(b->contour_start, b->contour_start + b->ncontour);
+    } else {
+      starts.push_back(0);
+    }
+    if (starts[0] != 0) return set_error(FS_ERR_ARG, "the first contour must start at marker 0");
+    for (size_t k = 0; k < starts.size(); ++k) {
+      const int a = starts[k], e = k + 1 < starts.size() ? starts[k + 1] : nm;
+      if (e - a < 3 || e > nm) return set_error(FS_ERR_ARG, "contours need increasing starts and >= 3 markers each");
+      for (int m = a; m < e; ++m) nxt[m] = m + 1 < e ? m + 1 : a;
+    }
+  }
+  // bounding box with a margin so the early-out never decides a point near an edge
+  double xmin = b->X0[0], xmax = b->X0[0], ymin = b->Y0[0], ymax = b->Y0[0];
+  for (int m = 0; m < nm; ++m) {
+    xmin = std::min(xmin, b->X0[m]);
+    xmax = std::max(xmax, b->X0[m]);
+    ymin = std::min(ymin, b->Y0[m]);
+    ymax = std::max(ymax, b->Y0[m]);
   }
   const double mg = 1e-6 * (std::fabs(xmax - xmin) + std::fabs(ymax - ymin) + 1.0);
   B.poly_bb[0] = xmin - mg;
   B.poly_bb[1] = xmax + mg;
   B.poly_bb[2] = ymin - mg;
   B.poly_bb[3] = ymax + mg;
-  // markers sorted by the cell that holds their rest position (row-major), for warp-local reductions
-  std::vector<int> order(b->nm);
-  for (int m = 0; m < b->nm; ++m) order[m] = m;
+  // edges sorted by their lowest point (a row at height y is crossed only by edges whose lowest
+  // point lies in [y - ehmax, y])
+  std::vector<int> eo(nm);
+  for (int m = 0; m < nm; ++m) eo[m] = m;
+  auto elo = [&](int m) { return std::min(b->Y0[m], b->Y0[nxt[m]]); };
+  std::stable_sort(eo.begin(), eo.end(), [&](int p, int q) { return elo(p) < elo(q); });
+  std::vector<double> EAX(nm), EAY(nm), EBX(nm), EBY(nm), EY0(nm);
+  B.ehmax = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    const int a = eo[k], c = nxt[a];
+    EAX[k] = b->X0[a];
+    EAY[k] = b->Y0[a];
+    EBX[k] = b->X0[c];
+    EBY[k] = b->Y0[c];
+    EY0[k] = elo(a);
+    B.ehmax = std::max(B.ehmax, std::max(b->Y0[a], b->Y0[c]) - EY0[k]);
+  }
+  // markers sorted by the cell that holds their rest position (row-major), and the cell bins
   const double x0 = G->xf[0][0], y0 = G->xf[1][0], hy = G->h[1][0];
-  auto cell = [&](int m) {
-    const long long ci = (long long)std::floor((b->X0[m] - x0) / G->hx);
-    const long long cj = (long long)std::floor((b->Y0[m] - y0) / hy);
-    return cj * (G->nx + 2) + ci;
-  };
-  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return cell(p) < cell(q); });
-  std::vector<double> X(b->nm), Y(b->nm), S(b->nm);
-  for (int m = 0; m < b->nm; ++m) {
+  std::vector<long long> ci(nm), cj(nm);
+  long long cimin = 0, cimax = 0, cjmin = 0, cjmax = 0;
+  for (int m = 0; m < nm; ++m) {
+    ci[m] = (long long)std::floor((b->X0[m] - x0) / G->hx);
+    cj[m] = (long long)std::floor((b->Y0[m] - y0) / hy);
+    cimin = m ? std::min(cimin, ci[m]) : ci[m];
+    cimax = m ? std::max(cimax, ci[m]) : ci[m];
+    cjmin = m ? std::min(cjmin, cj[m]) : cj[m];
+    cjmax = m ? std::max(cjmax, cj[m]) : cj[m];
+  }
+  if ((cimax - cimin + 1) * (cjmax - cjmin + 1) > (1LL << 28))
+    return set_error(FS_ERR_ARG, "the body's markers span more than 2^28 cells");
+  B.bx0 = (int)cimin;
+  B.by0 = (int)cjmin;
+  B.nbx = (int)(cimax - cimin + 1);
+  B.nby = (int)(cjmax - cjmin + 1);
+  auto key = [&](int m) { return (cj[m] - cjmin) * B.nbx + (ci[m] - cimin); };
+  std::vector<int> order(nm);
+  for (int m = 0; m < nm; ++m) order[m] = m;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) { return key(p) < key(q); });
+  std::vector<double> X(nm), Y(nm), S(nm);
+  for (int m = 0; m < nm; ++m) {
     X[m] = b->X0[order[m]];
     Y[m] = b->Y0[order[m]];
     S[m] = b->ds[order[m]];
   }
+  std::vector<int> bins((size_t)B.nbx * B.nby + 1, 0);
+  {
+    size_t k = 0;
+    for (size_t cell = 0; cell <= (size_t)B.nbx * B.nby; ++cell) {
+      while (k < (size_t)nm && (size_t)key(order[k]) < cell) ++k;
+      bins[cell] = (int)k;
+    }
+  }
   B.horder = order;
   bool ok = upload(&B.X0, X) == cudaSuccess && upload(&B.Y0, Y) == cudaSuccess && upload(&B.ds, S) == cudaSuccess &&
-            upload(&B.PX, PX) == cudaSuccess && upload(&B.PY, PY) == cudaSuccess && upload(&B.order, order) == cudaSuccess;
+            upload(&B.EAX, EAX) == cudaSuccess && upload(&B.EAY, EAY) == cudaSuccess &&
+            upload(&B.EBX, EBX) == cudaSuccess && upload(&B.EBY, EBY) == cudaSuccess &&
+            upload(&B.EY0, EY0) == cudaSuccess && upload(&B.order, order) == cudaSuccess &&
+            upload(&B.bin_start, bins) == cudaSuccess;
+  {
+    const size_t nf = comp_size(G, 0) + comp_size(G, 1);
+    if (ok) ok = dalloc(&B.iblist, nf) == cudaSuccess && dalloc(&B.ibcount, 1) == cudaSuccess &&
+                 cudaMemset(B.ibcount, 0, sizeof(unsigned)) == cudaSuccess;
+  }
   const size_t es = elem_size(G);
   for (int c = 0; c < 2 && ok; ++c) {
     const size_t n = comp_size(G, c);
@@ -1009,6 +1103,7 @@ int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
          cudaMemset(B.num[c], 0, n * es) == cudaSuccess && cudaMemset(B.den[c], 0, n * es) == cudaSuccess &&
          cudaMemset(B.flags[c], 0, n) == cudaSuccess && cudaMemset(B.f[c], 0, n * es) == cudaSuccess;
   }
+  if (ok) ok = dalloc(&B.part, 3 * (size_t)((2 * b->nm * 16 + 255) / 256)) == cudaSuccess;
   if (ok) ok = dalloc(&B.fn, 2 * b->nm) == cudaSuccess && dalloc(&B.q, 2 * b->nm) == cudaSuccess &&
                dalloc(&B.F, 4) == cudaSuccess && cudaMemset(B.F, 0, 4 * sizeof(double)) == cudaSuccess &&
                dalloc(&B.ticket, 1) == cudaSuccess && cudaMemset(B.ticket, 0, sizeof(unsigned)) == cudaSuccess;
@@ -1050,24 +1145,36 @@ int fs_step(fs_grid* G, fs_state* st, double dt, int nsteps) {
   return cuda_check(cudaGetLastError(), "fs_step launch");
 }
 
-int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, fs_param_grad* g,
-                    double dt) {
+namespace {
+int step_adjoint_entry(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, bool dJdF_dev,
+                       fs_param_grad* g, double dt) {
   if (!G || !st_n || !lam) return set_error(FS_ERR_ARG, "NULL argument");
   if (!(dt > 0)) return set_error(FS_ERR_ARG, "the adjoint needs the fixed step dt > 0 of the forward step");
   for (int c = 0; c < G->dim; ++c)
     if (!st_n->u[c] || !lam->u[c]) return set_error(FS_ERR_ARG, "NULL velocity component");
   if (G->has_body) {
     if (!st_n->body || !lam->body) return set_error(FS_ERR_ARG, "a grid with a body needs st_n->body and lam->body");
-    if (G->fsi_iters > 1)
-      return set_error(FS_ERR_UNSUPPORTED, "adjoint of the strongly coupled (sub-iterated) FSI step");
     if (G->ib.omega != 0.0)
       return set_error(FS_ERR_UNSUPPORTED, "adjoint of a body with a prescribed surface rotation");
   }
   if (G->les_cs > 0.0) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a step with the Smagorinsky model");
   if (G->has_ib3) return set_error(FS_ERR_UNSUPPORTED, "adjoint of a grid with a static 3-D box body");
-  const int rc = G->prec == FS_MIXED ? step_adjoint<float>(G, st_n, lam, dJdF, g, dt)
-                                     : step_adjoint<double>(G, st_n, lam, dJdF, g, dt);
-  return rc;
+  if (G->has_body && G->fsi_iters > 1 && G->ib.mass > 0)
+    return G->prec == FS_MIXED ? step_adjoint_coupled<float>(G, st_n, lam, dJdF, dJdF_dev, g, dt)
+                               : step_adjoint_coupled<double>(G, st_n, lam, dJdF, dJdF_dev, g, dt);
+  return G->prec == FS_MIXED ? step_adjoint<float>(G, st_n, lam, dJdF, g, dt, nullptr, nullptr, dJdF_dev)
+                             : step_adjoint<double>(G, st_n, lam, dJdF, g, dt, nullptr, nullptr, dJdF_dev);
+}
+}  // namespace
+
+int fs_step_adjoint(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, fs_param_grad* g,
+                    double dt) {
+  return step_adjoint_entry(G, st_n, lam, dJdF, false, g, dt);
+}
+
+int fs_step_adjoint_dev(fs_grid* G, const fs_state* st_n, fs_state* lam, const double* dJdF, fs_param_grad* g,
+                        double dt) {
+  return step_adjoint_entry(G, st_n, lam, dJdF, true, g, dt);
 }
 
 namespace {
@@ -1161,6 +1268,17 @@ int fs_set_les(fs_grid* G, double cs) {
     }
   }
   G->les_cs = cs;
+  return FS_OK;
+}
+
+int fs_ib_face_count(fs_grid* G, int* count) {
+  if (!G || !count) return set_error(FS_ERR_ARG, "NULL argument");
+  if (!G->has_body) return set_error(FS_ERR_STATE, "no 2-D body attached");
+  unsigned n = 0;
+  cudaError_t e = cudaMemcpyAsync(&n, G->ib.ibcount, sizeof(unsigned), cudaMemcpyDeviceToHost, G->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+  if (e != cudaSuccess) return cuda_check(e, "fs_ib_face_count");
+  *count = (int)n;
   return FS_OK;
 }
 

@@ -215,9 +215,18 @@ struct Plan1D {
 struct IBDev {
   int nm = 0;
   int kernel = FS_ROMA3;
-  double *X0 = nullptr, *Y0 = nullptr, *ds = nullptr;  // device, markers sorted by cell
-  double *PX = nullptr, *PY = nullptr;                 // device, polygon in surface order
+  double *X0 = nullptr, *Y0 = nullptr, *ds = nullptr;  // device, markers sorted by the cell of their rest position
+  // edges of the rest contours, sorted by their lowest y (ey0), each from vertex a to vertex
+  // next(a) in surface order: device arrays of ne = nm entries
+  double *EAX = nullptr, *EAY = nullptr, *EBX = nullptr, *EBY = nullptr, *EY0 = nullptr;
+  double ehmax = 0.0;                                  // largest edge height
   int* order = nullptr;                                // device, sorted position -> caller index
+  // rest-frame cell bins of the sorted markers: bin_start[(cj - by0) * nbx + (ci - bx0)] is the
+  // first sorted marker of cell (ci, cj); nbx * nby + 1 entries
+  int* bin_start = nullptr;
+  int bx0 = 0, by0 = 0, nbx = 0, nby = 0;
+  unsigned* iblist = nullptr;                          // IB faces of the current step: (index << 1) | component
+  unsigned* ibcount = nullptr;                         // their number (device)
   std::vector<int> horder;
   double centre[2] = {0, 0};
   double omega = 0;
@@ -229,6 +238,7 @@ struct IBDev {
   void* f[2] = {nullptr, nullptr};         // direct-forcing term f of Eq. (5) (field precision)
   double* fn = nullptr;                    // F_N per marker and component (2 * nm)
   double* q = nullptr;                     // marker forces (2 * nm)
+  double* part = nullptr;                  // per-block sums of the force kernel (3 per block)
   double* F = nullptr;                     // [Fx, Fy, torque]
   unsigned* ticket = nullptr;              // blocks finished in the force kernel (reset by its last block)
   bool have_forces = false;
@@ -313,6 +323,7 @@ struct fs_grid {
   double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [2 R + 4 kTwChunk][nlp], position-major
   double *twP = nullptr;                  // [nlz * nmx][4]
   double *twZ = nullptr;                  // [2 R + 4 kTwChunk][nlp] (periodic y)
+  int* twK = nullptr;                     // [nlam] positions per thread where z matters (periodic y)
   double *twS = nullptr;                  // [nlz * nmx][4] (periodic y)
 
   fs::IBDev ib;
@@ -374,9 +385,15 @@ template <typename T> void ib3_forces(fs_grid* g);
 void free_ib3(fs_grid* g);
 // adjoint.cu
 // rv1, rv2: the RK3 stage states recorded by the forward step (then nothing is recomputed), or null
+// dJdF_on_device: dJdF is a device pointer (else host)
 template <typename T> int step_adjoint(fs_grid* g, const fs_state* st, fs_state* lam, const double* dJdF,
                                        fs_param_grad* pg, double dt, void* const* rv1 = nullptr,
-                                       void* const* rv2 = nullptr);
+                                       void* const* rv2 = nullptr, bool dJdF_on_device = false);
+// adjoint of the strongly coupled (sub-iterated) FSI step by implicit differentiation
+template <typename T> int step_adjoint_coupled(fs_grid* g, const fs_state* st, fs_state* lam, const double* dJdF,
+                                               bool dJdF_on_device, fs_param_grad* pg, double dt);
+// fs_api.cu: the strongly coupled forward-Euler FSI step (Algorithm 1)
+template <typename T> int step_coupled(fs_grid* g, fs_state* st, double dt, bool want_p);
 void free_adj_buffers(void* p);
 // poisson.cu
 size_t ysolve_smem(int ny, int nseg, int yc);

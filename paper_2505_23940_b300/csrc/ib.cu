@@ -1,17 +1,22 @@
 // Immersed-boundary and rigid-body kernels (§2.3.2-2.3.3 of the paper), 2-D bodies.
 //
 //   classify_solid   solid faces: crossing-number test of (face - w) against the
-//                    rest polygon, every FP64 operation rounded on its own
+//                    rest contours, every FP64 operation rounded on its own
 //                    (__d*_rn) so the integer decision is the oracle's bit for bit;
 //                    one block per face row finds the edges crossing the row's
-//                    height once, then every face of the row counts the crossings
-//                    to its right (both components in one launch)
-//   classify_ib      IB faces: non-solid faces with a solid same-component neighbour
-//   ib_target        F_N of Eq. (19) per marker and component (support nodes that are
-//                    not solid) and the normalised scatter of Eq. (18): numerator and
-//                    denominator of u_IB on IB faces; 16 lanes per (marker, component),
-//                    one support node each, F_N summed by shuffles, one atomicAdd per
-//                    IB node
+//                    height once (edges sorted by their lowest point, the candidates
+//                    found by bisection), then every face of the row counts the
+//                    crossings to its right (both components in one launch)
+//   classify_ib      IB faces: non-solid faces with a solid same-component neighbour,
+//                    appended to a list of the step's IB faces
+//   ib_fn            F_N of Eq. (19) per marker and component (support nodes that are
+//                    not solid): 16 lanes per (marker, component), one support node
+//                    each, summed by shuffles
+//   ib_gather        the normalised interpolation of Eq. (18) on each IB face: the
+//                    markers of the cells around the face (markers binned by the cell of
+//                    their rest position, visited row by row in a fixed order) are summed
+//                    in FP64 registers, so every face has one writer, no atomics, and a
+//                    bitwise reproducible result
 //   ib_force         q_i of Eq. (20) per marker (FP64 sums, 16 lanes per marker and
 //                    component); the last block to finish forms F = rho sum q_i dV_i and
 //                    the torque in a fixed order (FP64) and, in a forward step, the
@@ -33,20 +38,37 @@ namespace {
 
 constexpr int kT = 256;
 
+// Edges of the rest contours, sorted by their lowest y (ey0): edge k runs from (ax, ay)
+// to (bx, by) in surface order.
 struct Poly {
-  const double* X;
-  const double* Y;
+  const double* ax;
+  const double* ay;
+  const double* bx;
+  const double* by;
+  const double* ey0;
   int n;
+  double hmax;     // largest edge height
   double bb[4];
 };
+
+// first edge whose lowest point is >= v (or > v when strict)
+__device__ __forceinline__ int edge_bound(const Poly& P, double v, bool strict) {
+  int lo = 0, hi = P.n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const double e = P.ey0[mid];
+    if (strict ? e <= v : e < v) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ bool inside_polygon(const Poly& P, double px, double py) {
   if (px < P.bb[0] || px > P.bb[1] || py < P.bb[2] || py > P.bb[3]) return false;
   bool in = false;
   for (int e = 0; e < P.n; ++e) {
-    const double ax = P.X[e], ay = P.Y[e];
-    const int f = (e + 1 == P.n) ? 0 : e + 1;
-    const double bx = P.X[f], by = P.Y[f];
+    const double ax = P.ax[e], ay = P.ay[e];
+    const double bx = P.bx[e], by = P.by[e];
     if ((ay > py) != (by > py)) {
       const double xint = __dadd_rn(ax, __ddiv_rn(__dmul_rn(__dsub_rn(py, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
       if (px < xint) in = !in;
@@ -90,13 +112,19 @@ __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0
     for (int i = threadIdx.x; i < ex; i += blockDim.x) row[i] = 0;
     return;
   }
-  if (threadIdx.x == 0) cnt = 0;
+  __shared__ int elo, ehi;
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    // only edges whose lowest point lies in [py - hmax, py] can cross the row (twice the largest
+    // height as the lower bound keeps a rounded edge height from excluding one)
+    elo = edge_bound(P, py - 2.0 * P.hmax, false);
+    ehi = edge_bound(P, py, true);
+  }
   __syncthreads();
   // x where each edge crosses the row's height (the order of the crossings does not matter to the parity)
-  for (int e = threadIdx.x; e < P.n; e += blockDim.x) {
-    const double ax = P.X[e], ay = P.Y[e];
-    const int f = (e + 1 == P.n) ? 0 : e + 1;
-    const double bx = P.X[f], by = P.Y[f];
+  for (int e = elo + threadIdx.x; e < ehi; e += blockDim.x) {
+    const double ax = P.ax[e], ay = P.ay[e];
+    const double bx = P.bx[e], by = P.by[e];
     if ((ay > py) != (by > py)) {
       const double xint = __dadd_rn(ax, __ddiv_rn(__dmul_rn(__dsub_rn(py, ay), __dsub_rn(bx, ax)), __dsub_rn(by, ay)));
       const int k = atomicAdd(&cnt, 1);
@@ -118,35 +146,56 @@ __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0
   }
 }
 
-// grid (blocks, 2 components)
-__global__ void classify_ib_kernel(Flags F, int ex0, int ey0, int ex1, int ey1, int perx, int pery) {
+// marks face t IB when it is not solid and a same-component neighbour is; returns that
+__device__ __forceinline__ bool ib_face(uint8_t* __restrict__ flags, long long t, int ex, int ey, int perx,
+                                        int pery) {
+  const int i = (int)(t % ex), j = (int)(t / ex);
+  const uint8_t me = flags[t];
+  if (me & 1) return false;
+  bool nb = false;
+  const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    int a = i + di[q], b = j + dj[q];
+    if (a < 0 || a >= ex) {
+      if (!perx) continue;
+      a = a < 0 ? a + ex : a - ex;
+    }
+    if (b < 0 || b >= ey) {
+      if (!pery) continue;
+      b = b < 0 ? b + ey : b - ey;
+    }
+    nb = nb || (flags[(size_t)b * ex + a] & 1);
+  }
+  if (nb) flags[t] = me | 2;
+  return nb;
+}
+
+// grid (blocks, 2 components); the IB faces are appended to list as (index << 1) | component
+// (the list's order varies from run to run; nothing computed from it depends on the order)
+__global__ void classify_ib_kernel(Flags F, int ex0, int ey0, int ex1, int ey1, int perx, int pery,
+                                   unsigned* __restrict__ list, unsigned* __restrict__ count) {
   const int c = blockIdx.y;
   const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
   uint8_t* __restrict__ flags = c ? F.p[1] : F.p[0];
   const long long total = (long long)ex * ey;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % ex), j = (int)(t / ex);
-    const uint8_t me = flags[t];
-    if (me & 1) continue;
-    bool nb = false;
-    const int di[4] = {-1, 1, 0, 0}, dj[4] = {0, 0, -1, 1};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int a = i + di[q], b = j + dj[q];
-      if (a < 0 || a >= ex) {
-        if (!perx) continue;
-        a = a < 0 ? a + ex : a - ex;
-      }
-      if (b < 0 || b >= ey) {
-        if (!pery) continue;
-        b = b < 0 ? b + ey : b - ey;
-      }
-      nb = nb || (flags[(size_t)b * ex + a] & 1);
+  const long long span = (long long)gridDim.x * blockDim.x;
+  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += span) {
+    const long long t = t0 + threadIdx.x;
+    bool isib = false;
+    if (t < total) isib = ib_face(flags, t, ex, ey, perx, pery);
+    // warp-aggregated append
+    const unsigned m = __ballot_sync(0xffffffffu, isib);
+    if (m) {
+      const int lane = threadIdx.x & 31;
+      unsigned base = 0;
+      if (lane == __ffs(m) - 1) base = atomicAdd(count, (unsigned)__popc(m));
+      base = __shfl_sync(0xffffffffu, base, __ffs(m) - 1);
+      if (isib) list[base + __popc(m & ((1u << lane) - 1u))] = ((unsigned)t << 1) | (unsigned)c;
     }
-    if (nb) flags[t] = me | 2;
   }
 }
+
 
 template <typename T>
 __device__ __forceinline__ T phi_kernel(int kind, T r) {
@@ -217,45 +266,83 @@ __device__ __forceinline__ double sum16(double s) {
   return s;
 }
 
-// F_N_i of Eq. (19) and the scatter of Eq. (18) in one pass: the 16 lanes of a
-// (marker, component) pair evaluate delta_h at their support node once, sum
-// F_N over the non-solid nodes by shuffles (every lane receives the sum), and
-// the lanes whose node is an IB face add w = delta dV_i / F_N_i and w times the
-// marker velocity to the numerator and denominator of u_IB.
+// F_N_i of Eq. (19): the 16 lanes of a (marker, component) pair evaluate delta_h at
+// their support node and sum it over the nodes that are not solid by shuffles.
 template <typename T>
-__global__ void ib_target_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
-                                 const double* __restrict__ ds, const double* __restrict__ body, double omega,
-                                 double cx, double cy, const Flags flags, double* __restrict__ fn, T* num0, T* den0,
-                                 T* num1, T* den1) {
+__global__ void ib_fn_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
+                             const double* __restrict__ body, const Flags flags, double* __restrict__ fn) {
   const Lane L = lane_of(G, nm);
   double s = 0.0;
-  T d = T(0);
-  long long face = -1;
-  double X = 0.0, Y = 0.0;
   if (L.live && L.b < G.width) {
     const int c = L.c;
-    X = X0[L.m] + body[0];
-    Y = Y0[L.m] + body[1];
+    const double X = X0[L.m] + body[0];
+    const double Y = Y0[L.m] + body[1];
     const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
     if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
       const size_t f = (size_t)j * G.ex[c] + i;
       const uint8_t fl = (c ? flags.p[1] : flags.p[0])[f];
       const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
       const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
-      d = px * py;
-      if (!(fl & 1)) s = (double)d * G.ihxy;   // solid nodes are excluded from F_N
-      if (fl & 2) face = (long long)f;
+      if (!(fl & 1)) s = (double)(px * py) * G.ihxy;   // solid nodes are excluded from F_N
     }
   }
   const double F = sum16(s);
   if (L.live && (threadIdx.x & 15) == 0) fn[L.pair] = F;
-  if (face >= 0 && F > 0.0) {
-    const int c = L.c;
-    const T w = T((double)d * G.ihxy * (ds[L.m] * G.hx) / F);
-    // marker velocity: body translation plus surface rotation
-    const double vm = c == 0 ? body[2] - omega * (Y - (cy + body[1])) : body[3] + omega * (X - (cx + body[0]));
-    atomicAdd(c ? &num1[face] : &num0[face], w * T(vm));
-    atomicAdd(c ? &den1[face] : &den0[face], w);
+}
+
+// Marker bins of the rest positions (see IBDev): markers of cell (ci, cj) are the sorted
+// markers [start[k], start[k + 1]), k = (cj - by0) nbx + (ci - bx0).
+struct Bins {
+  const int* start;
+  int bx0, by0, nbx, nby;
+  double x0, y0;   // grid origin (cell (0, 0) starts there)
+};
+
+// Eq. (18) in normalised form on one IB face per thread: u_IB = sum_i w_i v_i / sum_i w_i,
+// w_i = delta_h(x - X_i) dV_i / F_N_i, over the markers whose support holds the face.  The face's
+// rest-frame position x - w picks the cells whose markers can reach it (the kernel's support
+// plus one cell on each side); within a cell row the markers of consecutive cells are one
+// contiguous run of the sorted markers, visited in order.  FP64 sums, one writer per face.
+template <typename T>
+__global__ void __launch_bounds__(kT) ib_gather_kernel(const IBGeom G, const Bins Bn, const double* __restrict__ X0,
+                                                       const double* __restrict__ Y0, const double* __restrict__ ds,
+                                                       const double* __restrict__ fn,
+                                                       const double* __restrict__ body, double omega, double cx,
+                                                       double cy, const unsigned* __restrict__ list,
+                                                       const unsigned* __restrict__ count, T* num0, T* den0, T* num1,
+                                                       T* den1) {
+  const unsigned n = *count;
+  const double wx = body[0], wy = body[1];
+  const double reach = G.kind == FS_PESKIN4 ? 2.0 : 1.5;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const unsigned code = list[e];
+    const int c = (int)(code & 1u);
+    const size_t f = code >> 1;
+    const int i = (int)(f % (size_t)G.ex[c]), j = (int)(f / (size_t)G.ex[c]);
+    const double xf = node_x(G, c, i), yf = node_y(G, c, j);
+    const double sx = (xf - wx - Bn.x0) * G.ihx, sy = (yf - wy - Bn.y0) * G.ihy;
+    const int ci0 = max((int)floor(sx - reach) - 1, Bn.bx0), ci1 = min((int)floor(sx + reach) + 1, Bn.bx0 + Bn.nbx - 1);
+    const int cj0 = max((int)floor(sy - reach) - 1, Bn.by0), cj1 = min((int)floor(sy + reach) + 1, Bn.by0 + Bn.nby - 1);
+    double num = 0.0, den = 0.0;
+    for (int cj = cj0; cj <= cj1 && ci0 <= ci1; ++cj) {
+      const int row = (cj - Bn.by0) * Bn.nbx - Bn.bx0;
+      const int m0 = Bn.start[row + ci0], m1 = Bn.start[row + ci1 + 1];
+      for (int m = m0; m < m1; ++m) {
+        const double X = X0[m] + wx, Y = Y0[m] + wy;
+        const T py = phi_kernel<T>(G.kind, T((yf - Y) * G.ihy));
+        const T px = phi_kernel<T>(G.kind, T((xf - X) * G.ihx));
+        const T d = px * py;
+        const double F = fn[2 * m + c];
+        if (d == T(0) || !(F > 0.0)) continue;
+        const T w = T((double)d * G.ihxy * (ds[m] * G.hx) / F);
+        // marker velocity: body translation plus surface rotation
+        const double vm = c == 0 ? body[2] - omega * (Y - (cy + wy)) : body[3] + omega * (X - (cx + wx));
+        num += (double)(w * T(vm));
+        den += (double)w;
+      }
+    }
+    (c ? num1 : num0)[f] = T(num);
+    (c ? den1 : den0)[f] = T(den);
   }
 }
 
@@ -293,23 +380,27 @@ struct BodyODE {
 };
 
 // q_i = - sum_x f(x) delta_h(x - X_i) dv(x)   (Eq. 20), 16 lanes per marker and
-// component; then F = rho sum_i q_i dV_i and the torque rho sum_i dV_i (r_i x q_i)
-// by the block that finishes last (the other blocks publish their q before
-// taking a ticket; no block waits), in a fixed summation order, and, when asked,
-// the body ODE step with that force.
+// component; then F = rho sum_i q_i dV_i and the torque rho sum_i dV_i (r_i x q_i): each
+// block sums its markers' terms (a fixed tree) into its slot of part, and the block that
+// finishes last (the others publish their slot before taking a ticket; no block waits) sums
+// the slots in a fixed order and, when asked, takes the body ODE step with that force.
 template <typename T>
 __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const double* __restrict__ X0,
                                                    const double* __restrict__ Y0, const double* __restrict__ ds,
                                                    const double* body, const T* __restrict__ f0,
                                                    const T* __restrict__ f1, double cx, double cy, double rho,
-                                                   double* __restrict__ q, double* __restrict__ F,
-                                                   unsigned* __restrict__ ticket, const BodyODE ode) {
+                                                   double* __restrict__ q, double* __restrict__ part,
+                                                   double* __restrict__ F, unsigned* __restrict__ ticket,
+                                                   const BodyODE ode) {
   const Lane L = lane_of(G, nm);
-  double s = 0.0;
+  double s = 0.0, X = 0.0, Y = 0.0;
+  if (L.live) {
+    X = X0[L.m] + body[0];
+    Y = Y0[L.m] + body[1];
+  }
   if (L.live && L.b < G.width) {
     const int c = L.c;
     const T* f = c == 0 ? f0 : f1;
-    const double X = X0[L.m] + body[0], Y = Y0[L.m] + body[1];
     const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
     if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
       const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
@@ -319,8 +410,40 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
     }
   }
   s = sum16(s);
-  if (L.live && (threadIdx.x & 15) == 0) q[L.pair] = -s;
-  // the last block to finish reduces
+  // this pair's terms of F and the torque (held by the pair's first lane)
+  __shared__ double s0[kT], s1[kT], s2[kT];
+  double a = 0.0, b = 0.0, tq = 0.0;
+  if (L.live && (threadIdx.x & 15) == 0) {
+    const double qv = -s;
+    q[L.pair] = qv;
+    const double dV = ds[L.m] * G.hx;
+    const double rx = X - (cx + body[0]), ry = Y - (cy + body[1]);
+    if (L.c == 0) {
+      a = qv * dV;
+      tq = -dV * ry * qv;
+    } else {
+      b = qv * dV;
+      tq = dV * rx * qv;
+    }
+  }
+  s0[threadIdx.x] = a;
+  s1[threadIdx.x] = b;
+  s2[threadIdx.x] = tq;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s0[threadIdx.x] += s0[threadIdx.x + o];
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+      s2[threadIdx.x] += s2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = s0[0];
+    part[3 * blockIdx.x + 1] = s1[0];
+    part[3 * blockIdx.x + 2] = s2[0];
+  }
+  // the last block to finish reduces the block sums
   __shared__ bool last;
   __threadfence();
   __syncthreads();
@@ -328,17 +451,13 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
   __syncthreads();
   if (!last) return;
   __threadfence();
-  __shared__ double s0[kT], s1[kT], s2[kT];
-  const double bx = body[0], by = body[1];
-  double a = 0, b = 0, tq = 0;
-  for (int m = threadIdx.x; m < nm; m += blockDim.x) {
-    const double dV = ds[m] * G.hx;
-    const double qx = __ldcg(q + 2 * m), qy = __ldcg(q + 2 * m + 1);
-    a += qx * dV;
-    b += qy * dV;
-    const double rx = X0[m] + bx - (cx + bx), ry = Y0[m] + by - (cy + by);
-    tq += dV * (rx * qy - ry * qx);
+  a = b = tq = 0.0;
+  for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+    a += __ldcg(part + 3 * k);
+    b += __ldcg(part + 3 * k + 1);
+    tq += __ldcg(part + 3 * k + 2);
   }
+  __syncthreads();
   s0[threadIdx.x] = a;
   s1[threadIdx.x] = b;
   s2[threadIdx.x] = tq;
@@ -391,9 +510,13 @@ template <typename T>
 void ib_prepare(fs_grid* G, const double* body_state) {
   IBDev& B = G->ib;
   Poly P;
-  P.X = B.PX;
-  P.Y = B.PY;
+  P.ax = B.EAX;
+  P.ay = B.EAY;
+  P.bx = B.EBX;
+  P.by = B.EBY;
+  P.ey0 = B.EY0;
   P.n = B.nm;
+  P.hmax = B.ehmax;
   for (int q = 0; q < 4; ++q) P.bb[q] = B.poly_bb[q];
   Flags dflags;
   dflags.p[0] = B.flags[0];
@@ -405,18 +528,24 @@ void ib_prepare(fs_grid* G, const double* body_state) {
   }
   FS_LAUNCH(G, "classify_solid", classify_solid_kernel<<<dim3(std::max(ey[0], ey[1]), 2), kT, 0, G->stream>>>(
                                      dflags, ex[0], ey[0], ex[1], ey[1], G->xf64[0], G->xf64[1], body_state, P));
+  cudaMemsetAsync(B.ibcount, 0, sizeof(unsigned), G->stream);
   {
     const long long n = (long long)std::max(ex[0] * ey[0], ex[1] * ey[1]);
     int nb = (int)((n + kT - 1) / kT);
     if (nb > 148 * 8) nb = 148 * 8;
-    FS_LAUNCH(G, "classify_ib", classify_ib_kernel<<<dim3(nb, 2), kT, 0, G->stream>>>(dflags, ex[0], ey[0], ex[1], ey[1],
-                                                                                        G->per[0], G->per[1]));
+    FS_LAUNCH(G, "classify_ib", classify_ib_kernel<<<dim3(nb, 2), kT, 0, G->stream>>>(
+                                    dflags, ex[0], ey[0], ex[1], ey[1], G->per[0], G->per[1], B.iblist, B.ibcount));
   }
   const IBGeom g = make_geom(G);
   const int nlane = 2 * B.nm * 16;
-  FS_LAUNCH(G, "ib_target", ib_target_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
-                                g, B.nm, B.X0, B.Y0, B.ds, body_state, B.omega, B.centre[0], B.centre[1], dflags, B.fn,
-                                (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
+  FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state,
+                                                                                     dflags, B.fn));
+  Bins bn{B.bin_start, B.bx0, B.by0, B.nbx, B.nby, G->xf[0][0], G->xf[1][0]};
+  // IB faces: about two per marker and component; the kernel strides over the list's length
+  int nb = (int)std::min<long long>(148LL * 8, (4LL * B.nm + kT - 1) / kT + 1);
+  FS_LAUNCH(G, "ib_gather", ib_gather_kernel<T><<<nb, kT, 0, G->stream>>>(
+                                g, bn, B.X0, B.Y0, B.ds, B.fn, body_state, B.omega, B.centre[0], B.centre[1], B.iblist,
+                                B.ibcount, (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
 }
 
 template <typename T>
@@ -428,7 +557,7 @@ void ib_forces(fs_grid* G, double* body_state, double* advance, double dt) {
   if (advance && B.mass > 0) ode.st = advance;
   FS_LAUNCH(G, "ib_force", force_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
                                g, B.nm, B.X0, B.Y0, B.ds, body_state, (const T*)B.f[0], (const T*)B.f[1], B.centre[0],
-                               B.centre[1], G->rho, B.q, B.F, B.ticket, ode));
+                               B.centre[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
   B.have_forces = true;
 }
 

@@ -771,15 +771,24 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // inverse P after one shuffle between the two threads; each thread then
 // substitutes outward,
 //   x_j = E_j g_j + C_j x_{j+1}   (upper),  x_j = E_j h_j + C_j x_{j-1}   (lower).
-// That is one FP64 multiply-add per row forward and a multiply plus a
-// multiply-add backward: the FP64 work of a plain Thomas solve, spread over
-// twice the threads.  M, E, C are tabulated per eigenvalue (M and C negated).
+// The sweeps carry the scaled values g^_j = E_j g_j instead (E_j -> 1 at the two
+// middle rows, which the 2x2 solve reads unscaled):
+//   g^_j = E_j d_j + M^_j g^_{j-1},   x_j = g^_j + C_j x_{j+1},
+// M^_j = E_j M_j / E_{j-1}.  The products E_j d_j of the FP32 spectrum and the
+// FP64 scales are formed exactly rounded on the integer pipes as the tile is
+// widened (fpconv.cuh), so the sweeps issue one FP64 multiply-add per row in
+// each direction.  M^, E, C are tabulated per eigenvalue (M^ and C negated).
 //
 // Periodic y (cyclic): with xi = x_{ny-1}, rows 0..ny-2 read A'' x' = d' - xi u,
 // u the coupling column of x_{ny-1}; so x' = y - xi z with A'' y = d' (the solve
 // above) and z = A''^-1 u (tabulated), and row ny-1 gives
 //   xi = (d_{ny-1} - S0 y_0 - S1 y_{ny-2}) S2,   S2 = 1 / (b_{ny-1} - S0 z_0 - S1 z_{ny-2}),
-// S0, S1 its couplings to x_0 and x_{ny-2}: one more multiply-add per row.
+// S0, S1 its couplings to x_0 and x_{ny-2}: one more multiply-add per row where
+// z matters.  z decays geometrically away from the chain's ends (faster for the
+// larger x/z eigenvalues); a warp corrects the leading positions of its threads
+// up to the last one where some column's |z| exceeds 2^-56 of its largest
+// (tabulated per eigenvalue, K), beyond which the correction is below FP64
+// rounding of the solution's scale.
 //
 // Positions: both threads of a column own R = ceil(L / 2) consecutive
 // positions and sweep them in the same direction.  The upper thread's are rows
@@ -794,13 +803,14 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // sweep rate).
 //
 // B300's FP64 pipe (one warp instruction per ~73 cycles per SM sub-partition,
-// conversions included) bounds the sweeps, which need 3 FP64 operations per
-// cell (4 with periodic y).  The block therefore splits its warps: four
-// "sweep" warps run the chains and issue little besides FP64, while four
-// helper warps widen the FP32 spectrum to FP64 with integer field arithmetic
-// (fpconv.cuh) as its row groups arrive by bulk asynchronous copies, releasing
-// each group to the sweeps on an mbarrier.  All eight warps narrow the solution
-// at the end, which leaves by bulk copies as well.
+// conversions included) bounds the sweeps, which need 2 FP64 operations per
+// cell (plus the truncated correction with periodic y).  The block therefore
+// splits its warps: four "sweep" warps run the chains and issue little besides
+// FP64, while four helper warps widen and scale the FP32 spectrum to FP64 with
+// integer field arithmetic (fpconv.cuh) as its row groups arrive by bulk
+// asynchronous copies, releasing each group to the sweeps on an mbarrier.  All
+// eight warps narrow the solution at the end, which leaves by bulk copies as
+// well.  With FP64 fields the helpers scale in FP64.
 //
 // The singular zero mode pins x_0 = 0 through its tables (E_0 = C_0 = 0,
 // M_1 = 0, no coupling to row 0) and is shifted to zero hy-weighted mean (with
@@ -821,6 +831,7 @@ struct YTwArgs {
   const double* Z;       // cyclic: z = A''^-1 u
   const double* P;       // [nlam][4] inverse of the middle 2x2 system
   const double* S;       // [nlam][4] cyclic: S0, S1, S2
+  const int* K;          // [nlam] cyclic: positions per thread (from its first) where z matters
   const double* hy;      // cell widths (zero-mode mean)
   double hysum;
   unsigned* status;      // device status word (bit 0: a bulk copy or group wait gave up)
@@ -846,6 +857,15 @@ template <typename T>
 __device__ __forceinline__ T narrow(double v) {
   if constexpr (sizeof(T) == 4) return fsconv_narrow(v);
   else return v;
+}
+
+// s * v for the scaled elimination: v an FP32 spectrum value (bits u), s the row's FP64 scale;
+// the exactly rounded product is formed on the integer pipes (fpconv.cuh), the FP64 multiply
+// only for the inputs the fast path flags (sp).
+__device__ __forceinline__ double scale_fast(uint32_t u, double sv, uint32_t* sp) {
+  uint32_t hi, lo;
+  fsconv_scale_fast(u, (uint32_t)__double2hiint(sv), (uint32_t)__double2loint(sv), &hi, &lo, sp);
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 template <typename T>
@@ -927,19 +947,18 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       // chunk 0 is exactly the rows of box 0 (upper thread) or box 1 (lower): widened here, by
       // the thread that eliminates them, as soon as the box lands
       ok &= mbar_wait_idle(&bulkbar[half], 0);
+      const double* __restrict__ Es = A.E + tb;
       uint32_t sp = 0;
 #pragma unroll
       for (int q = 0; q < U; ++q) {
         const int j = rowof(P0 + q);
-        uint32_t whi, wlo;
-        fsconv_widen_fast(act && j >= 0 ? __float_as_uint((float)st[j * W + cb]) : 0u, &whi, &wlo, &sp);
-        gp[q * W] = __hiloint2double((int)whi, (int)wlo);
+        gp[q * W] = scale_fast(act && j >= 0 ? __float_as_uint((float)st[j * W + cb]) : 0u, __ldg(Es + q * nl), &sp);
       }
       if (__any_sync(FULL, sp)) {
 #pragma unroll
         for (int q = 0; q < U; ++q) {
           const int j = rowof(P0 + q);
-          gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) : 0.0;
+          gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) * __ldg(Es + q * nl) : 0.0;
         }
       }
     }
@@ -981,16 +1000,12 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     const double* Pt = A.P + (size_t)li * 4 + 2 * half;
     double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
     gp[(R - 1) * W] = xv;
-    // 3. outward substitution, positions descending
+    // 3. outward substitution, positions descending (the stored g^ already carry E)
     {
-      const double* __restrict__ Et = A.E + tb;
       const double* __restrict__ Ct = A.C + tb;
-      double eb[U], cbuf[U];
+      double cbuf[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        eb[q] = __ldg(Et + (R - 2 - q) * (ptrdiff_t)nl);
-        cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
-      }
+      for (int q = 0; q < U; ++q) cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
       int next = nchunk - 1;                     // walls: highest output chunk not yet released
       for (int i0 = R - 2; i0 >= 0; i0 -= U) {
         if (i0 + 1 >= U) {
@@ -998,9 +1013,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           double v[U], c2[U];
 #pragma unroll
           for (int q = 0; q < U; ++q) {
-            v[q] = eb[q] * gp[(i0 - q) * W];
+            v[q] = gp[(i0 - q) * W];
             c2[q] = cbuf[q];
-            eb[q] = __ldg(Et + (i0 - U - q) * (ptrdiff_t)nl);
             cbuf[q] = __ldg(Ct + (i0 - U - q) * (ptrdiff_t)nl);
           }
 #pragma unroll
@@ -1014,8 +1028,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
 #pragma unroll
           for (int q = 0; q < U; ++q) {
             if (q <= i0) {
-              const double eg = eb[q] * gp[(i0 - q) * W];
-              xv = fma(cbuf[q], xv, eg);
+              xv = fma(cbuf[q], xv, gp[(i0 - q) * W]);
               gp[(i0 - q) * W] = xv;
             }
           }
@@ -1047,20 +1060,24 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       const double* St = A.S + (size_t)li * 4;
       const double xi = fma(-__ldg(St + 1), yl, fma(-__ldg(St), y0, dlast)) * __ldg(St + 2);
       const double* __restrict__ Zt = A.Z + tb;
+      // the positions where some column of this warp still has a z above 2^-56 of its largest
+      const int kw = __reduce_max_sync(FULL, act ? __ldg(A.K + li) : 1);
       double zb[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) zb[q] = __ldg(Zt + q * nl);
       for (int i0 = 0; i0 < R; i0 += U) {
-        double v[U];
+        if (i0 < kw) {
+          double v[U];
 #pragma unroll
-        for (int q = 0; q < U; ++q) {
-          v[q] = fma(-xi, zb[q], gp[min(i0 + q, R - 1) * W]);
-          zb[q] = __ldg(Zt + (i0 + U + q) * nl);
+          for (int q = 0; q < U; ++q) {
+            v[q] = fma(-xi, zb[q], gp[min(i0 + q, R - 1) * W]);
+            zb[q] = __ldg(Zt + (i0 + U + q) * nl);
+          }
+          if (half && i0 == 0) v[0] = xi;          // the inert slot becomes x_{ny-1}
+#pragma unroll
+          for (int q = 0; q < U; ++q)
+            if (i0 + q < R) gp[(i0 + q) * W] = v[q];
         }
-        if (half && i0 == 0) v[0] = xi;          // the inert slot becomes x_{ny-1}
-#pragma unroll
-        for (int q = 0; q < U; ++q)
-          if (i0 + q < R) gp[(i0 + q) * W] = v[q];
         __syncwarp();
         if (lane == 0) mbar_arrive(&donebar[i0 / U]);   // the helpers narrow this chunk meanwhile
       }
@@ -1069,6 +1086,10 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // ---------------- helper threads: tile in, widened, group by group ----------------
     const int h = tid - NS;                      // 0 .. 2 W - 1
     const int hc = h % W, hw = h / W;            // this helper's column and row parity
+    // the row scales s_j of this helper's column (its eigenvalue's entries, position-major)
+    const size_t nlh = (size_t)A.nlp;
+    const double* __restrict__ Eh =
+        A.E + (size_t)(2 * U) * nlh + (hc < ncol ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s0 + hc, t) : 0);
     if (h >= 32 && !A.tiled) {
       // row copies: the block's table segments into L2 while the tile is in flight (the sweeps'
       // chunk-ahead register fetches then wait on L2, not on DRAM): per position, the eigenvalues
@@ -1118,13 +1139,11 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           // another value redoes its rows with the general routine
           uint32_t sp = 0;
 #pragma unroll 8
-          for (int j = a0 + hw; j < a1; j += 2) {
-            uint32_t whi, wlo;
-            fsconv_widen_fast(__float_as_uint(st[j * W + hc]), &whi, &wlo, &sp);
-            sg[pos(j) * W + hc] = __hiloint2double((int)whi, (int)wlo);
-          }
+          for (int j = a0 + hw; j < a1; j += 2)
+            sg[pos(j) * W + hc] = scale_fast(__float_as_uint(st[j * W + hc]), __ldg(Eh + (size_t)pos(j) * nlh), &sp);
           if (__any_sync(FULL, sp))
-            for (int j = a0 + hw; j < a1; j += 2) sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]);
+            for (int j = a0 + hw; j < a1; j += 2)
+              sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]) * __ldg(Eh + (size_t)pos(j) * nlh);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&widebar[l]);
@@ -1153,13 +1172,16 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
         for (int r = hw; r < 2 * n; r += 2) {
           const int p = r < n ? lo + r : R + lo + (r - n);
           const bool hole = odd && !CYC && p == R;
+          const double sv = __ldg(Eh + (size_t)p * nlh);
           if constexpr (F32) {
             const uint32_t u = (hc < ncol && !hole) ? __float_as_uint(st[p * W + hc]) : 0u;
-            uint32_t whi, wlo, sp = 0;
-            fsconv_widen_fast(u, &whi, &wlo, &sp);
-            sg[p * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) : __hiloint2double((int)whi, (int)wlo);
+            uint32_t sp = 0;
+            const double v = scale_fast(u, sv, &sp);
+            sg[p * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) * sv : v;
           } else if (hc >= ncol || hole) {
             sg[p * W + hc] = 0.0;
+          } else {
+            sg[p * W + hc] *= sv;
           }
         }
         __syncwarp();
@@ -1170,7 +1192,9 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       for (int e = h; e < NP * W; e += NS) {
         const int p = e / W, c = e - p * W;
         const int j = rowof(p);
-        sg[e] = (c < ncol && j >= 0) ? widen<T>(tile[rs * j + c]) : 0.0;
+        const double* Ec =
+            A.E + (size_t)(2 * U + p) * nlh + (c < ncol ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s0 + c, t) : 0);
+        sg[e] = (c < ncol && j >= 0) ? widen<T>(tile[rs * j + c]) * __ldg(Ec) : 0.0;
       }
       asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");   // every helper's rows are in
       if (lane == 0)
@@ -1659,6 +1683,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     A.P = G->twP;
     A.Z = G->twZ;
     A.S = G->twS;
+    A.K = G->twK;
     A.hy = G->hy64;
     A.hysum = G->hysum;
     A.status = G->dstatus;

@@ -43,7 +43,8 @@ class State(ctypes.Structure):
 class BodyDesc(ctypes.Structure):
     _fields_ = [("nm", c_int), ("X0", POINTER(c_double)), ("Y0", POINTER(c_double)), ("ds", POINTER(c_double)),
                 ("centre", c_double * 2), ("omega", c_double), ("mass", c_double), ("stiffness", c_double),
-                ("damping", c_double), ("active", c_int * 2), ("delta_kernel", c_int)]
+                ("damping", c_double), ("active", c_int * 2), ("delta_kernel", c_int), ("ncontour", c_int),
+                ("contour_start", POINTER(c_int))]
 
 
 class ParamGrad(ctypes.Structure):
@@ -71,6 +72,9 @@ def lib():
                                                POINTER(State), POINTER(ParamGrad), c_double]
         L.fs_step_adjoint.argtypes = [c_void_p, POINTER(State), POINTER(State), POINTER(c_double),
                                       POINTER(ParamGrad), c_double]
+        L.fs_ib_face_count.argtypes = [c_void_p, POINTER(c_int)]
+        L.fs_step_adjoint_dev.argtypes = [c_void_p, POINTER(State), POINTER(State), c_void_p,
+                                          POINTER(ParamGrad), c_double]
         L.fs_solve_pressure.argtypes = [c_void_p, c_void_p, c_void_p]
         L.fs_solve_pressure_cg.argtypes = [c_void_p, c_void_p, c_void_p, c_double, c_int, c_int, POINTER(c_int),
                                            POINTER(c_double)]
@@ -173,7 +177,8 @@ class Grid:
         return [torch.zeros(self.shape(c), dtype=self.dtype, device="cuda") for c in range(self.dim)]
 
     def set_body(self, X0, Y0, ds, centre, omega=0.0, mass=0.0, stiffness=0.0, damping=0.0,
-                 active=(False, False), kernel=ROMA3):
+                 active=(False, False), kernel=ROMA3, contours=None):
+        """contours: first marker of each closed contour (several disjoint parts), or None."""
         b = BodyDesc()
         b.nm = len(X0)
         ax, px = _dptr(X0)
@@ -184,6 +189,11 @@ class Grid:
         b.omega, b.mass, b.stiffness, b.damping = float(omega), float(mass), float(stiffness), float(damping)
         b.active[0], b.active[1] = int(bool(active[0])), int(bool(active[1]))
         b.delta_kernel = int(kernel)
+        starts = None
+        if contours is not None and len(contours) > 1:
+            starts = (c_int * len(contours))(*[int(a) for a in contours])
+            b.ncontour = len(contours)
+            b.contour_start = ctypes.cast(starts, POINTER(c_int))
         check(lib().fs_set_ib_markers(self.h, byref(b)))
         self.has_body = True
         self.nm = b.nm
@@ -209,6 +219,12 @@ class Grid:
         g = ParamGrad()
         g.body_force = g_body_force.data_ptr() if g_body_force is not None else None
         g.stiffness = g_stiffness.data_ptr() if g_stiffness is not None else None
+        if torch.is_tensor(dJdF) and dJdF.is_cuda:
+            # device sensitivities (2 contiguous float64 values): no host read
+            assert dJdF.dtype == torch.float64 and dJdF.numel() >= 2 and dJdF.stride(-1) == 1
+            check(lib().fs_step_adjoint_dev(self.h, byref(sn), byref(sl), c_void_p(dJdF.data_ptr()), byref(g),
+                                            float(dt)))
+            return
         dj = None
         if dJdF is not None:
             dj = (c_double * 2)(*[float(x) for x in dJdF])
@@ -298,6 +314,12 @@ class Grid:
     def set_coupling(self, max_subiters, tol=1e-5):
         """Strong FSI coupling: sub-iterate each step up to max_subiters fluid solves (1 = weak)."""
         check(lib().fs_set_coupling(self.h, int(max_subiters), float(tol)))
+
+    def ib_face_count(self):
+        """IB faces classified by the last step (synchronises)."""
+        n = c_int(0)
+        check(lib().fs_ib_face_count(self.h, byref(n)))
+        return n.value
 
     def coupling_stats(self):
         k, xi = c_int(0), c_double(0.0)

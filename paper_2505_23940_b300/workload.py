@@ -15,7 +15,7 @@ def grid_from_workload(wl, precision=None, stream=None):
     b = getattr(wl, "body", None)
     if b is not None:
         g.set_body(b.X0, b.Y0, b.ds, b.centre, b.omega, b.mass, b.stiffness, b.damping, b.active,
-                   kernel=wl.kernel)
+                   kernel=wl.kernel, contours=getattr(b, "contours", None))
     bx = getattr(wl, "boxes", None)
     if bx is not None:
         g.set_boxes(bx.boxes, bx.X, bx.dV, wl.kernel)

@@ -1,9 +1,10 @@
-/* Host check of the integer-pipe FP32 <-> FP64 conversions of the y solve
- * (paper_2505_23940_b300/csrc/fpconv.cuh) against the host's IEEE 754
- * conversions: every binary32 value widened; binary64 values from every
- * exponent of and around the binary32 range, with rounding ties, narrowed;
- * the fast paths agree on every input they do not flag and flag exactly the
- * rest.
+/* Host check of the integer-pipe FP32 <-> FP64 conversions and of the FP32 x
+ * FP64 product of the y solve (paper_2505_23940_b300/csrc/fpconv.cuh) against
+ * the host's IEEE 754 arithmetic: every binary32 value widened; binary64 values
+ * from every exponent of and around the binary32 range, with rounding ties,
+ * narrowed; products over every binary32 exponent, the under- and overflow
+ * boundaries and constructed rounding ties; the fast paths agree on every input
+ * they do not flag and flag exactly the rest.
  * Prints "ok" and exits 0, or the first mismatch and exits 1. */
 #include <math.h>
 #include <stdint.h>
@@ -50,7 +51,80 @@ static int narrow_one(uint64_t b) {
   return 0;
 }
 
+/* binary32 x binary64 product: the fast path agrees with the host's IEEE product (one rounding,
+   to nearest even) wherever it does not flag the input, and flags exactly the inputs that are not
+   normal or zero and the products that are not normal (a product just below the smallest normal
+   that rounds up to it may be flagged as well) */
+static int scale_one(uint32_t u, uint64_t e) {
+  uint32_t hi, lo, sp = 0;
+  fsconv_scale_fast(u, (uint32_t)(e >> 32), (uint32_t)e, &hi, &lo, &sp);
+  const double want = (double)bitsf(u) * bitsd(e);
+  const uint64_t wb = dbits(want), got = ((uint64_t)hi << 32) | lo;
+  const uint32_t e8 = (u >> 23) & 0xffu;
+  const uint64_t e11 = (e >> 52) & 0x7ffu, we = (wb >> 52) & 0x7ffu;
+  const int fz = (u << 1) == 0, ez = (e << 1) == 0;
+  const int fin = ((e8 >= 1u && e8 <= 254u) || fz) && ((e11 >= 1u && e11 <= 2046u) || ez);
+  const int plain = fin && (fz || ez || (we >= 1u && we <= 2046u));
+  if ((!sp && !plain) || (sp && plain && we != 1u) || (!sp && got != wb)) {
+    printf("scale %08x x %016llx: special %u got %016llx want %016llx\n", u, (unsigned long long)e, sp,
+           (unsigned long long)got, (unsigned long long)wb);
+    return 1;
+  }
+  return 0;
+}
+
+static uint64_t inv_mod24(uint64_t a) {   /* a odd: a^-1 mod 2^24 by Newton's iteration */
+  uint64_t x = a;
+  for (int i = 0; i < 5; ++i) x = (x * (2 - a * x)) & 0xffffffull;
+  return x;
+}
+
+static int check_scale(void) {
+  /* every binary32 exponent against sampled binary64 exponents (edges, the ranges where the product
+     leaves the normal range, random), random significands and both signs */
+  for (uint32_t e8 = 0; e8 < 256u; ++e8) {
+    uint64_t exps[80];
+    int ne = 0;
+    const uint64_t edge[] = {0, 1, 2, 1022, 1023, 1024, 2045, 2046, 2047};
+    for (unsigned q = 0; q < sizeof(edge) / sizeof(edge[0]); ++q) exps[ne++] = edge[q];
+    for (int d = -3; d <= 3; ++d) {
+      const long lo_e = 150 - 24 - (long)e8 + d, hi_e = 2046 + 150 - 24 - (long)e8 + d;
+      if (lo_e >= 0 && lo_e < 2048) exps[ne++] = (uint64_t)lo_e;
+      if (hi_e >= 0 && hi_e < 2048) exps[ne++] = (uint64_t)hi_e;
+    }
+    while (ne < 80) exps[ne++] = next() & 0x7ffull;
+    for (int q = 0; q < ne; ++q)
+      for (int r = 0; r < 24; ++r) {
+        const uint32_t u = ((uint32_t)(next() & 1u) << 31) | (e8 << 23) | (uint32_t)(next() & 0x7fffffu);
+        const uint64_t e = ((next() & 1ull) << 63) | (exps[q] << 52) | (next() & 0xfffffffffffffull);
+        if (scale_one(u, e)) return 1;
+        if (scale_one(u & 0x80000000u, e) || scale_one(u, e & 0x8000000000000000ull)) return 1;   /* zeros */
+      }
+  }
+  /* rounding ties and their neighbours at both alignments: significand products with
+     P mod 2^24 = 2^23 (a tie when P >= 2^76) or 2^22 (a tie when P < 2^76) */
+  for (int r = 0; r < 400000; ++r) {
+    const uint64_t mf = (next() & 0x7fffffull) | 0x800001ull;   /* odd */
+    const uint64_t inv = inv_mod24(mf);
+    const uint64_t target = (r & 1) ? (1ull << 23) : (1ull << 22);
+    const uint64_t low = (target * inv) & 0xffffffull;
+    for (int dd = -1; dd <= 1; ++dd) {
+      const uint64_t me = ((next() & 0xfffffffull) << 24) | ((low + (uint64_t)(long long)dd) & 0xffffffull);
+      const uint32_t e8 = 100u + (uint32_t)(next() % 50u);
+      const uint64_t e11 = 900u + next() % 200u;
+      const uint32_t u = (e8 << 23) | (uint32_t)(mf & 0x7fffffu);
+      const uint64_t e = (e11 << 52) | (me & 0xfffffffffffffull);
+      if (scale_one(u, e)) return 1;
+    }
+  }
+  /* random bit patterns (specials included) */
+  for (long r = 0; r < 20000000; ++r)
+    if (scale_one((uint32_t)next(), next())) return 1;
+  return 0;
+}
+
 int main(void) {
+  if (check_scale()) return 1;
   /* widening: all 2^32 inputs */
   for (uint64_t i = 0; i < (1ull << 32); ++i) {
     const uint32_t u = (uint32_t)i;

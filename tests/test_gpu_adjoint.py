@@ -174,3 +174,101 @@ def test_adjoint_mixed_cylinder():
     gp = gpu_vjp(wl, u0, lam, wl.dt, "mixed", lb, [0.0, 1.0])
     assert rel_l2(gp["u"], o["u"]) < 1e-5
     assert rel_l2([gp["body"]], [o["body"]]) < 1e-5
+
+
+def _coupled_case(active, precision):
+    wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, centre_d=(2.0, 2.0), precision=precision,
+                       seed=3, perturb=0.05, mass_ratio=1.0)
+    wl.body.w0 = (0.02, 0.05)
+    wl.body.wd0 = (0.1 if active[0] else 0.0, -0.2)
+    wl.body.active = active
+    return wl
+
+
+@pytest.mark.parametrize("active", [(False, True), (True, True)])
+def test_adjoint_strong_coupling_fp64(active):
+    """Adjoint of the strongly coupled step (Algorithm 1 differentiated implicitly at its fixed point,
+    §2.4.1) against the oracle's implicit differentiation: lam of u^n, of the body state and dJ/dk, both
+    sides converging the sub-iteration to rounding (xi < 1e-28).  dJdF is passed in device memory."""
+    from oracle.step import step_coupled_adjoint
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    wl = _coupled_case(active, "fp64")
+    g = grid_of(wl)
+    body, params = body_of(wl)
+    f64 = torch.float64
+    st = O.State([torch.tensor(a, dtype=f64) for a in wl.u0], torch.tensor(wl.body.w0, dtype=f64),
+                 torch.tensor(wl.body.wd0, dtype=f64))
+    lam_u = seeds(wl, 9)
+    lb, fb = [0.3, -0.7, 0.2, 0.9], [0.4, -1.1]
+    lu, ls, dk, iters = step_coupled_adjoint(g, st, wl.dt, body, wl.kernel, params, lam_u, lb, fb,
+                                             max_iter=200, tol=1e-28)
+    G = grid_from_workload(wl, "fp64")
+    G.set_coupling(200, 1e-28)
+    u = [torch.tensor(a, dtype=f64, device="cuda") for a in wl.u0]
+    lam = [torch.tensor(a, dtype=f64, device="cuda") for a in lam_u]
+    bt = body_tensor(wl)
+    lbt = torch.tensor(lb, dtype=f64, device="cuda")
+    gk = torch.zeros(1, dtype=f64, device="cuda")
+    G.step_adjoint(u, lam, wl.dt, body_n=bt, lam_body=lbt, dJdF=torch.tensor(fb, dtype=f64, device="cuda"),
+                   g_stiffness=gk)
+    torch.cuda.synchronize()
+    eu = rel_l2([x.cpu() for x in lam], lu)
+    eb = float((lbt.cpu() - ls).norm() / ls.norm())
+    ek = abs(float(gk[0]) - float(dk)) / abs(float(dk))
+    print("strong coupling adjoint %s: %d sub-iterations, lam_u %.2e, lam_body %.2e, dJ/dk %.2e"
+          % (active, iters, eu, eb, ek))
+    assert eu < 1e-9 and eb < 1e-9 and ek < 1e-9
+    assert torch.equal(u[0].cpu(), torch.tensor(wl.u0[0], dtype=f64))   # st_n is not modified
+
+
+def test_adjoint_strong_coupling_mixed():
+    """The same in mixed precision (FP32 fluid, FP64 body and coupling system) against the FP64 oracle;
+    the FP32 force limits how far the sub-iteration converges (xi < 1e-12 here)."""
+    from oracle.step import step_coupled_adjoint
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    wl = _coupled_case((True, True), "mixed")
+    g = grid_of(wl)
+    body, params = body_of(wl)
+    f64 = torch.float64
+    st = O.State([torch.tensor(a, dtype=f64) for a in wl.u0], torch.tensor(wl.body.w0, dtype=f64),
+                 torch.tensor(wl.body.wd0, dtype=f64))
+    lam_u = seeds(wl, 9)
+    lb, fb = [0.3, -0.7, 0.2, 0.9], [0.4, -1.1]
+    lu, ls, dk, _ = step_coupled_adjoint(g, st, wl.dt, body, wl.kernel, params, lam_u, lb, fb,
+                                         max_iter=200, tol=1e-28)
+    G = grid_from_workload(wl, "mixed")
+    G.set_coupling(100, 1e-12)
+    u = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in wl.u0]
+    lam = [torch.tensor(a, dtype=torch.float32, device="cuda") for a in lam_u]
+    bt = body_tensor(wl)
+    lbt = torch.tensor(lb, dtype=f64, device="cuda")
+    gk = torch.zeros(1, dtype=f64, device="cuda")
+    G.step_adjoint(u, lam, wl.dt, body_n=bt, lam_body=lbt, dJdF=fb, g_stiffness=gk)
+    torch.cuda.synchronize()
+    eu = rel_l2([x.double().cpu() for x in lam], lu)
+    eb = float((lbt.cpu() - ls).norm() / ls.norm())
+    ek = abs(float(gk[0]) - float(dk)) / abs(float(dk))
+    print("strong coupling adjoint, mixed: lam_u %.2e, lam_body %.2e, dJ/dk %.2e" % (eu, eb, ek))
+    assert eu < 1e-5 and eb < 1e-4 and ek < 1e-4
+
+
+def test_adjoint_device_and_host_force_sensitivity_agree():
+    """fs_step_adjoint_dev (dJ/dF in device memory) gives fs_step_adjoint's result (up to the order of
+    the adjoint's atomic FP64 sums)."""
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, centre_d=(2.0, 2.0), precision="fp64",
+                       seed=3, perturb=0.05)
+    wl.body.w0 = (0.0, 0.05)
+    G = grid_from_workload(wl, "fp64")
+    u = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in wl.u0]
+    out = []
+    for dev in (False, True):
+        lam = [torch.tensor(a, dtype=torch.float64, device="cuda") for a in seeds(wl, 11)]
+        lbt = torch.tensor([0.3, -0.7, 0.2, 0.9], dtype=torch.float64, device="cuda")
+        fb = [0.4, -1.1]
+        G.step_adjoint(u, lam, wl.dt, body_n=body_tensor(wl), lam_body=lbt,
+                       dJdF=torch.tensor(fb, dtype=torch.float64, device="cuda") if dev else fb)
+        torch.cuda.synchronize()
+        out.append([x.cpu() for x in lam] + [lbt.cpu()])
+    for a, b in zip(*out):
+        assert float((a - b).norm()) <= 1e-13 * float(b.norm())

@@ -121,3 +121,45 @@ def test_recorded_stages_match_recomputed_adjoint(precision):
     G.step_adjoint_recorded(u0, v1, v2, lb, wl.dt)
     torch.cuda.synchronize()
     assert all(torch.equal(a, b) for a, b in zip(la, lb))
+
+
+def test_rollout_gradient_stiffness_strong_coupling():
+    """dJ/dk and dJ/du0 of a 3-step strongly coupled FSI rollout (2-DOF, sub-iterations converged to
+    rounding) through FsRollout against the oracle's implicit-differentiation adjoint chained over the
+    same steps (each step reversed at its own converged fixed point)."""
+    from oracle.step import step_coupled, step_coupled_adjoint
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    from paper_2505_23940_b300.autodiff import rollout
+    wl = S.cylinder_2d(nx=48, ny=32, cells_per_d=8, nm=26, dt=0.01, centre_d=(2.0, 2.0), precision="fp64",
+                       seed=3, perturb=0.05, mass_ratio=1.0)
+    wl.body.w0 = (0.02, 0.05)
+    wl.body.active = (True, True)
+    n, tol = 3, 1e-28
+    g = grid_of(wl)
+    body, params = body_of(wl)
+    f64 = torch.float64
+    st = O.State([torch.tensor(a, dtype=f64) for a in wl.u0], torch.tensor(wl.body.w0, dtype=f64),
+                 torch.tensor(wl.body.wd0, dtype=f64))
+    states, Fy = [], []
+    for _ in range(n):
+        states.append(st)
+        st, dg, _, _ = step_coupled(g, st, wl.dt, body, wl.kernel, params, max_iter=200, tol=tol)
+        Fy.append(float(dg.F[1]))
+    J = sum(f * f for f in Fy) + 50.0 * float(st.w[1]) ** 2
+    lam_u = [np.zeros(g.shape(c)) for c in range(2)]
+    lam_b = [0.0, 100.0 * float(st.w[1]), 0.0, 0.0]
+    dk = 0.0
+    for t in range(n - 1, -1, -1):
+        lu, ls, dkt, _ = step_coupled_adjoint(g, states[t], wl.dt, body, wl.kernel, params, lam_u, lam_b,
+                                              [0.0, 2.0 * Fy[t]], max_iter=200, tol=tol)
+        lam_u, lam_b, dk = [x.numpy() for x in lu], ls.tolist(), dk + float(dkt)
+    G = grid_from_workload(wl, "fp64")
+    G.set_coupling(200, tol)
+    u0 = [torch.tensor(a, device="cuda", requires_grad=True) for a in wl.u0]
+    kg = torch.tensor([wl.body.stiffness], dtype=f64, device="cuda", requires_grad=True)
+    uT, bT, forces = rollout(G, u0, wl.dt, n, slots=2, body0=body_tensor(wl), stiffness=kg)
+    Jg = (forces[:, 1] ** 2).sum() + 50.0 * bT[1] ** 2
+    gg = torch.autograd.grad(Jg, [kg] + u0)
+    assert abs(float(Jg) - J) < 1e-10 * abs(J)
+    assert abs(float(gg[0]) - dk) < 1e-9 * abs(dk), (float(gg[0]), dk)
+    assert rel_l2([x.cpu() for x in gg[1:]], [torch.tensor(a) for a in lam_u]) < 1e-9
