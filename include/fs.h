@@ -344,6 +344,14 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
  *                     least 32 rows as 16-row tensor-map boxes; 0: one bulk
  *                     copy per row
+ *   "ysplit"          1: on periodic-z grids whose twisted y solve has two or
+ *                     more column blocks along x, the z transforms and the y
+ *                     solve of the two halves of the x spectrum run as two
+ *                     independent chains on two streams (a second, library-owned
+ *                     stream; fork after the x transform, join before its
+ *                     inverse); 0 (default): one chain.  Same result bit for bit
+ *                     (at 128^3 no faster: each half's y solve, one block per
+ *                     SM, takes nearly the whole solve's time)
  *   "ysolve_segments" segments per column of the partitioned wall-bounded y
  *                     solve: 4, 8 or 16 (default: 8 for ny >= 192 or when the
  *                     grid has fewer 32-column blocks than two per SM, else 4);

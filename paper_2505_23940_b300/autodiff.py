@@ -37,24 +37,29 @@ def revolve_schedule(n, slots):
     Slot 0 holds the initial state.
     """
     ops = []
-
-    def rev(a, b, free, base_slot):
+    # the recursion rev(a, b, free, base) of the binomial schedule, run from an explicit stack (a
+    # schedule with a slot per step nests n levels deep); `free` is always a suffix of the slot list
+    # 1 .. slots - 1, held as its first index k (free slots k + 1 .. slots - 1)
+    nfree0 = slots - 1
+    stack = [(0, n, 0, 0)]
+    while stack:
+        a, b, k, base_slot = stack.pop()
         # the state at a is held in base_slot
         n_ = b - a
         if n_ <= 0:
-            return
+            continue
         if n_ == 1:
             ops.append(("load", base_slot, a))
             ops.append(("adjoint", a))
-            return
-        if not free:
+            continue
+        s = nfree0 - k
+        if s <= 0:
             for t in range(b - 1, a - 1, -1):
                 ops.append(("load", base_slot, a))
                 if t > a:
                     ops.append(("advance", a, t))
                 ops.append(("adjoint", t))
-            return
-        s = len(free)
+            continue
         t = 1
         while _beta(s, t) < n_:
             t += 1
@@ -62,12 +67,10 @@ def revolve_schedule(n, slots):
         m = a + d
         ops.append(("load", base_slot, a))
         ops.append(("advance", a, m))
-        slot = free[0]
+        slot = k + 1
         ops.append(("store", slot, m))
-        rev(m, b, free[1:], slot)
-        rev(a, m, free, base_slot)
-
-    rev(0, n, list(range(1, slots)), 0)
+        stack.append((a, m, k, base_slot))       # second: the first part, with the same slots
+        stack.append((m, b, k + 1, slot))        # first: the rest, from the stored state
     return ops
 
 

@@ -475,14 +475,14 @@ __global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ dat
 // z forward (see zfwd_kernel): complex lines of slot pairs along z at one y row.
 template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
-                                                           const cplx<T>* __restrict__ tw) {
+                                                           const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
   const int j = blockIdx.y;
-  const int pair0 = blockIdx.x * kRegLines;
+  const int pair0 = (blockIdx.x + tile0) * kRegLines;
   const int np = min(kRegLines, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ dat
 // rebuilds Z = Y0 + i Y1 into line 0.
 template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
-                                                           const cplx<T>* __restrict__ tw) {
+                                                           const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
   constexpr int P = rpitch<N>();
   extern __shared__ unsigned char smem_raw[];
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ dat
   cplx<T>* tws = S + kRegLines * P;
   cplx<T>* X = tws + N;   // scratch line (pair 0)
   const int j = blockIdx.y;
-  const int pair0 = blockIdx.x * kRegLines;
+  const int pair0 = (blockIdx.x + tile0) * kRegLines;
   const int np = min(kRegLines, nx / 2 - pair0);
   const size_t plane = (size_t)nx * ny;
   T* base = data + (size_t)nx * j + 2 * pair0;

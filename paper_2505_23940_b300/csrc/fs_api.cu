@@ -210,21 +210,10 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
       const double det = beta[k] * beta[k + 1] - cc[k] * aa[k + 1];
       const double p[4] = {beta[k + 1] / det, -cc[k] / det, -aa[k + 1] / det, beta[k] / det};
       for (int q = 0; q < 4; ++q) P[(size_t)li * 4 + q] = p[q];
-      // scaled elimination: the sweeps carry g^_j = E_j g_j, so the outward pass is one multiply-add,
-      //   g^_j = s_j d_j + M^_j g^_prev,   x_j = g^_j + C_j x_next,
-      // with s_j = E_j except at the two middle rows (s = 1: the 2 x 2 solve takes the plain g_k, h_k+1)
-      // and M^_j = s_j M_j / s_prev, i.e. -a_j e_j (upper) or -c_j e_j (lower), -a_k / -c_k+1 at the middle
-      // rows and 0 where M_j = 0.  The products s_j d_j are formed as the tile is widened.
       for (int j = 0; j < L; ++j) {
         const size_t o = at(pos(j), li);
-        const bool mid = j == k || j == k + 1;
-        double mh = 0.0;
-        if (m[j] != 0.0) {
-          if (j <= k) mh = j == k ? -aa[j] : -aa[j] * e[j];
-          else mh = j == k + 1 ? -cc[j] : -cc[j] * e[j];
-        }
-        M[o] = mh;
-        E[o] = mid ? 1.0 : ee[j];
+        M[o] = m[j];
+        E[o] = ee[j];
         C[o] = cm[j];
       }
       if (odd) E[at(R, li)] = 1.0;   // the inert slot keeps its value
@@ -464,6 +453,11 @@ void free_all(fs_grid* G) {
   auto F = [](void* p) {
     if (p) cudaFree(p);
   };
+  if (G->yev[0]) cudaEventDestroy(G->yev[0]);
+  if (G->yev[1]) cudaEventDestroy(G->yev[1]);
+  if (G->ystream2) cudaStreamDestroy(G->ystream2);
+  G->yev[0] = G->yev[1] = nullptr;
+  G->ystream2 = nullptr;
   F(G->ihy64); F(G->ihfy64); F(G->thy64); F(G->bf64);
   F(G->ihy32); F(G->ihfy32); F(G->thy32); F(G->bf32);
   for (int d = 0; d < 3; ++d) F(G->xf64[d]);
@@ -478,7 +472,8 @@ void free_all(fs_grid* G) {
   free_ytables(G);
   IBDev& B = G->ib;
   F(B.X0); F(B.Y0); F(B.ds); F(B.order);
-  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount);
+  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount); F(B.ebin);
+  F(B.gi); F(B.gf); F(B.rel); F(B.wfac); F(B.dsh);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
   F(B.fn); F(B.q); F(B.part); F(B.F); F(B.ticket);
 }
@@ -489,7 +484,8 @@ void free_body(fs_grid* G) {
     if (p) cudaFree(p);
   };
   F(B.X0); F(B.Y0); F(B.ds); F(B.order);
-  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount);
+  F(B.EAX); F(B.EAY); F(B.EBX); F(B.EBY); F(B.EY0); F(B.bin_start); F(B.iblist); F(B.ibcount); F(B.ebin);
+  F(B.gi); F(B.gf); F(B.rel); F(B.wfac); F(B.dsh);
   for (int c = 0; c < 2; ++c) { F(B.flags[c]); F(B.num[c]); F(B.den[c]); F(B.f[c]); }
   F(B.fn); F(B.q); F(B.part); F(B.F); F(B.ticket);
   B = IBDev();
@@ -806,6 +802,9 @@ int fs_create_grid(const fs_grid_desc* D, void* stream, fs_grid** out) {
                                    : (make_twiddles<double>(G->px) == cudaSuccess &&
                                       (G->dim == 2 || make_twiddles<double>(G->pz) == cudaSuccess) &&
                                       (!G->yspec || make_twiddles<double>(G->py) == cudaSuccess));
+  if (ok) ok = cudaStreamCreateWithFlags(&G->ystream2, cudaStreamNonBlocking) == cudaSuccess &&
+               cudaEventCreateWithFlags(&G->yev[0], cudaEventDisableTiming) == cudaSuccess &&
+               cudaEventCreateWithFlags(&G->yev[1], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     free_all(G);
     delete G;
@@ -864,6 +863,9 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
   } else if (k == "predictor_zmarch") {
     if (value < 0 || value > 64) return set_error(FS_ERR_ARG, "predictor_zmarch must be in 0..64");
     G->tune_zmarch = value;
+  } else if (k == "ysplit") {
+    if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "ysplit must be 0 or 1");
+    G->tune_ysplit = value;
   } else if (k == "pdl") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "pdl must be 0 or 1");
     G->use_pdl = value == 1;
@@ -1048,6 +1050,22 @@ int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
     EY0[k] = elo(a);
     B.ehmax = std::max(B.ehmax, std::max(b->Y0[a], b->Y0[c]) - EY0[k]);
   }
+  // bins of the sorted edges over their lowest y, one grid spacing high
+  {
+    B.ebin0 = EY0[0];
+    B.ebinh = G->h[1][0];
+    B.nebin = (int)std::ceil((EY0[nm - 1] - EY0[0]) / B.ebinh) + 1;
+    if (B.nebin > (1 << 26)) return set_error(FS_ERR_ARG, "the body's edges span too many rows");
+  }
+  std::vector<int> ebin((size_t)B.nebin + 1, nm);
+  {
+    int k = 0;
+    for (int b = 0; b <= B.nebin; ++b) {
+      const double lo = B.ebin0 + b * B.ebinh;
+      while (k < nm && EY0[k] < lo) ++k;
+      ebin[b] = k;
+    }
+  }
   // markers sorted by the cell that holds their rest position (row-major), and the cell bins
   const double x0 = G->xf[0][0], y0 = G->xf[1][0], hy = G->h[1][0];
   std::vector<long long> ci(nm), cj(nm);
@@ -1084,12 +1102,40 @@ int fs_set_ib_markers(fs_grid* G, const fs_body_desc* b) {
       bins[cell] = (int)k;
     }
   }
+  // grid units of the sorted markers (the cells of the bins above)
+  std::vector<int2> GI(nm);
+  std::vector<double> GF(2 * (size_t)nm), REL(2 * (size_t)nm);
+  for (int m = 0; m < nm; ++m) {
+    GI[m] = make_int2((int)ci[order[m]], (int)cj[order[m]]);
+    GF[2 * m] = (X[m] - x0) / G->hx - (double)ci[order[m]];
+    GF[2 * m + 1] = (Y[m] - y0) / hy - (double)cj[order[m]];
+    REL[2 * m] = X[m] - b->centre[0];
+    REL[2 * m + 1] = Y[m] - b->centre[1];
+  }
   B.horder = order;
-  bool ok = upload(&B.X0, X) == cudaSuccess && upload(&B.Y0, Y) == cudaSuccess && upload(&B.ds, S) == cudaSuccess &&
+  bool ok = upload(&B.gi, GI) == cudaSuccess;
+  std::vector<double> DSH(nm);
+  for (int m = 0; m < nm; ++m) DSH[m] = S[m] * G->hx;
+  if (G->prec == FS_MIXED) {
+    float *gf = nullptr, *rel = nullptr, *dsh = nullptr;
+    ok = ok && upload(&gf, cast<float>(GF)) == cudaSuccess && upload(&rel, cast<float>(REL)) == cudaSuccess &&
+         upload(&dsh, cast<float>(DSH)) == cudaSuccess;
+    B.gf = gf;
+    B.rel = rel;
+    B.dsh = dsh;
+  } else {
+    double *gf = nullptr, *rel = nullptr, *dsh = nullptr;
+    ok = ok && upload(&gf, GF) == cudaSuccess && upload(&rel, REL) == cudaSuccess && upload(&dsh, DSH) == cudaSuccess;
+    B.gf = gf;
+    B.rel = rel;
+    B.dsh = dsh;
+  }
+  ok = ok && cudaMalloc(&B.wfac, 2 * (size_t)nm * elem_size(G)) == cudaSuccess;
+  ok = ok && upload(&B.X0, X) == cudaSuccess && upload(&B.Y0, Y) == cudaSuccess && upload(&B.ds, S) == cudaSuccess &&
             upload(&B.EAX, EAX) == cudaSuccess && upload(&B.EAY, EAY) == cudaSuccess &&
             upload(&B.EBX, EBX) == cudaSuccess && upload(&B.EBY, EBY) == cudaSuccess &&
             upload(&B.EY0, EY0) == cudaSuccess && upload(&B.order, order) == cudaSuccess &&
-            upload(&B.bin_start, bins) == cudaSuccess;
+            upload(&B.bin_start, bins) == cudaSuccess && upload(&B.ebin, ebin) == cudaSuccess;
   {
     const size_t nf = comp_size(G, 0) + comp_size(G, 1);
     if (ok) ok = dalloc(&B.iblist, nf) == cudaSuccess && dalloc(&B.ibcount, 1) == cudaSuccess &&

@@ -220,10 +220,21 @@ struct IBDev {
   // next(a) in surface order: device arrays of ne = nm entries
   double *EAX = nullptr, *EAY = nullptr, *EBX = nullptr, *EBY = nullptr, *EY0 = nullptr;
   double ehmax = 0.0;                                  // largest edge height
+  int* ebin = nullptr;                                 // first edge with ey0 >= ebin0 + k ebinh (nebin + 1)
+  double ebin0 = 0.0, ebinh = 1.0;
+  int nebin = 0;
   int* order = nullptr;                                // device, sorted position -> caller index
   // rest-frame cell bins of the sorted markers: bin_start[(cj - by0) * nbx + (ci - bx0)] is the
   // first sorted marker of cell (ci, cj); nbx * nby + 1 entries
   int* bin_start = nullptr;
+  // sorted markers in grid units: rest cell (gi) and fraction in it (gf, field precision, x and y),
+  // rest position minus the rotation centre (rel, field precision), and per (marker, component) the
+  // interpolation weight factor dV_i / (F_N_i h_x h_y) of the step (wfac, field precision)
+  int2* gi = nullptr;
+  void* gf = nullptr;
+  void* rel = nullptr;
+  void* wfac = nullptr;
+  void* dsh = nullptr;                                 // dV_i = ds_i h_x per sorted marker, field precision
   int bx0 = 0, by0 = 0, nbx = 0, nby = 0;
   unsigned* iblist = nullptr;                          // IB faces of the current step: (index << 1) | component
   unsigned* ibcount = nullptr;                         // their number (device)
@@ -256,6 +267,10 @@ struct IB3Dev {
   void* f[3] = {nullptr, nullptr, nullptr}; // direct-forcing term f of Eq. (5) (field precision)
   double* q = nullptr;                      // marker forces (3 * nm, SoA)
   double* F = nullptr;                      // [Fx, Fy, Fz]
+  int* gi = nullptr;                        // marker cell index per direction (3 * nm, SoA)
+  void* gf = nullptr;                       // fraction in the cell, field precision (3 * nm, SoA)
+  double* part = nullptr;                   // per-block sums of the force gather
+  unsigned* ticket = nullptr;               // blocks of the force gather finished
   bool have_forces = false;
 };
 
@@ -272,6 +287,11 @@ struct fs_grid {
   std::vector<double> xf[3], h[3], hf[3], th[3];
   std::vector<double> bforce;
   cudaStream_t stream = nullptr;
+  // second stream and fork / join events of the split periodic-z Poisson solve (two halves of the
+  // x spectrum as independent z / y / z chains)
+  cudaStream_t ystream2 = nullptr;
+  cudaEvent_t yev[2] = {nullptr, nullptr};
+  int tune_ysplit = 0;
   long long launches = 0;
 
   // device metrics (both precisions)

@@ -49,19 +49,12 @@ struct Poly {
   int n;
   double hmax;     // largest edge height
   double bb[4];
+  // edge bins: ybin[k] is the first edge whose lowest point is >= ybin0 + k / iybin (nybin + 1 entries)
+  const int* ybin;
+  double ybin0, iybin;
+  int nybin;
+  double ihx;      // 1 / h_x of the grid
 };
-
-// first edge whose lowest point is >= v (or > v when strict)
-__device__ __forceinline__ int edge_bound(const Poly& P, double v, bool strict) {
-  int lo = 0, hi = P.n;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    const double e = P.ey0[mid];
-    if (strict ? e <= v : e < v) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
 
 __device__ __forceinline__ bool inside_polygon(const Poly& P, double px, double py) {
   if (px < P.bb[0] || px > P.bb[1] || py < P.bb[2] || py > P.bb[3]) return false;
@@ -101,7 +94,8 @@ __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0
                                                              const double* __restrict__ yf,
                                                              const double* __restrict__ body, Poly P) {
   __shared__ double xs[kRowCross];
-  __shared__ int cnt;
+  __shared__ int xi[kRowCross];
+  __shared__ int cnt, elo, ehi;
   const int c = blockIdx.y, j = blockIdx.x;
   const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
   if (j >= ey) return;
@@ -112,13 +106,19 @@ __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0
     for (int i = threadIdx.x; i < ex; i += blockDim.x) row[i] = 0;
     return;
   }
-  __shared__ int elo, ehi;
+  // the face x of index i, minus the displacement, as the oracle forms it
+  auto px_of = [&](int i) {
+    return __dsub_rn(c == 0 ? xf[i] : __dmul_rn(0.5, __dadd_rn(xf[i], xf[i + 1])), wx);
+  };
   if (threadIdx.x == 0) {
     cnt = 0;
-    // only edges whose lowest point lies in [py - hmax, py] can cross the row (twice the largest
-    // height as the lower bound keeps a rounded edge height from excluding one)
-    elo = edge_bound(P, py - 2.0 * P.hmax, false);
-    ehi = edge_bound(P, py, true);
+    // only edges whose lowest point lies in [py - hmax, py] can cross the row: their range from the
+    // edge bins (twice the largest height as the lower bound keeps a rounded height from excluding one)
+    const double b0 = (py - 2.0 * P.hmax - P.ybin0) * P.iybin, b1 = (py - P.ybin0) * P.iybin;
+    const int k0 = (int)fmin(fmax(floor(b0), 0.0), (double)P.nybin);
+    const int k1 = (int)fmin(fmax(floor(b1) + 1.0, 0.0), (double)P.nybin);
+    elo = P.ybin[k0];
+    ehi = P.ybin[k1];
   }
   __syncthreads();
   // x where each edge crosses the row's height (the order of the crossings does not matter to the parity)
@@ -133,16 +133,51 @@ __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0
   }
   __syncthreads();
   const int nc = cnt;
-  for (int i = threadIdx.x; i < ex; i += blockDim.x) {
-    const double px = __dsub_rn(c == 0 ? xf[i] : __dmul_rn(0.5, __dadd_rn(xf[i], xf[i + 1])), wx);
-    bool in = false;
-    if (nc > kRowCross) {
-      in = inside_polygon(P, px, py);
-    } else if (px >= P.bb[0] && px <= P.bb[1]) {
-      for (int k = 0; k < nc; ++k)
-        if (px < xs[k]) in = !in;
+  if (nc > kRowCross) {
+    for (int i = threadIdx.x; i < ex; i += blockDim.x) row[i] = inside_polygon(P, px_of(i), py) ? 1 : 0;
+    return;
+  }
+  // per crossing: the number of faces left of it (px < xint; px grows with i), from an estimate
+  // corrected by exact comparisons; a face is solid when an odd number of crossings lie to its right
+  int npow = 1;
+  while (npow < nc) npow <<= 1;
+  for (int k = threadIdx.x; k < npow; k += blockDim.x) {
+    int idx = 0x7fffffff;
+    if (k < nc) {
+      const double xint = xs[k];
+      const double x0 = c == 0 ? xf[0] : 0.5 * (xf[0] + xf[1]);
+      const double gs = ceil((xint + wx - x0) * P.ihx);
+      idx = (int)fmin(fmax(gs, 0.0), (double)ex);
+      while (idx > 0 && !(px_of(idx - 1) < xint)) --idx;
+      while (idx < ex && px_of(idx) < xint) ++idx;
     }
-    row[i] = in ? 1 : 0;
+    xi[k] = idx;
+  }
+  __syncthreads();
+  // bitonic sort of the npow entries (padding sorts last)
+  for (int kk = 2; kk <= npow; kk <<= 1)
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      for (int i = threadIdx.x; i < npow; i += blockDim.x) {
+        const int l = i ^ jj;
+        if (l > i) {
+          const int a = xi[i], b = xi[l];
+          if ((a > b) == ((i & kk) == 0)) {
+            xi[i] = b;
+            xi[l] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int i = threadIdx.x; i < ex; i += blockDim.x) {
+    // crossings with idx > i lie to the right of face i: nc - (first position with idx > i)
+    int lo = 0, hi = nc;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (xi[mid] <= i) lo = mid + 1;
+      else hi = mid;
+    }
+    row[i] = ((nc - lo) & 1) ? 1 : 0;
   }
 }
 
@@ -266,28 +301,71 @@ __device__ __forceinline__ double sum16(double s) {
   return s;
 }
 
-// F_N_i of Eq. (19): the 16 lanes of a (marker, component) pair evaluate delta_h at
-// their support node and sum it over the nodes that are not solid by shuffles.
+// Markers in grid units.  A marker's rest position in cell units from the grid origin,
+// g = (X0 - x0) / h, is held as an integer part gi = floor(g) and a fraction gf in [0, 1)
+// (host-computed in FP64 when the body is attached, gf stored in the field precision T);
+// the step's displacement in cell units, W = w / h, splits the same way.  The offset of a
+// node from a marker in grid units, r = (node - X) / h, is then an integer difference plus a
+// difference of fractions, formed in T: no FP64 arithmetic per node, which on B300's narrow
+// FP64 pipe would bound every immersed-boundary kernel.  Node i of component c sits at
+// (i + o_c) h from the origin: o = 0 along the component's own direction, 1/2 across.
 template <typename T>
-__global__ void ib_fn_kernel(const IBGeom G, int nm, const double* __restrict__ X0, const double* __restrict__ Y0,
-                             const double* __restrict__ body, const Flags flags, double* __restrict__ fn) {
+struct Shift {
+  int wi[2];   // floor(W) per direction
+  T wf[2];     // W - floor(W)
+};
+
+template <typename T>
+__device__ __forceinline__ Shift<T> shift_of(const double* body, double ihx, double ihy) {
+  Shift<T> S;
+  const double W[2] = {body[0] * ihx, body[1] * ihy};
+  for (int d = 0; d < 2; ++d) {
+    const double f = floor(W[d]);
+    S.wi[d] = (int)f;
+    S.wf[d] = T(W[d] - f);
+  }
+  return S;
+}
+
+// first support node of a marker (integer part gi, fraction gf) along one direction for nodes at
+// offset o, and the marker's position relative to that direction's node 0 as (sint, sfr)
+template <typename T>
+__device__ __forceinline__ int first_node_units(int kind, int gi, T gf, int wi, T wf, T o, int& sint, T& sfr) {
+  T t = gf + wf - o;                 // in [-1/2, 2)
+  const T k = floor(t);
+  sint = gi + wi + (int)k;
+  sfr = t - k;                       // in [0, 1)
+  return kind == FS_PESKIN4 ? sint - 1 : sint + (int)floor(sfr + T(0.5)) - 1;
+}
+
+// F_N_i of Eq. (19): the 16 lanes of a (marker, component) pair evaluate delta_h at their
+// support node and sum it over the nodes that are not solid by shuffles; the pair's first lane
+// stores the interpolation weight factor of Eq. (18), wfac = dV_i / (F_N_i h_x h_y) (then
+// w_i(x) = phi phi wfac), with dsh = dV_i = ds_i h_x.
+template <typename T>
+__global__ void ib_fn_kernel(const IBGeom G, int nm, const int2* __restrict__ gi, const T* __restrict__ gf,
+                             const T* __restrict__ dsh, const double* __restrict__ body, const Flags flags,
+                             T* __restrict__ wfac) {
+  __shared__ Shift<T> S;
+  if (threadIdx.x == 0) S = shift_of<T>(body, G.ihx, G.ihy);
+  __syncthreads();
   const Lane L = lane_of(G, nm);
-  double s = 0.0;
+  T s = T(0);
   if (L.live && L.b < G.width) {
     const int c = L.c;
-    const double X = X0[L.m] + body[0];
-    const double Y = Y0[L.m] + body[1];
-    const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
+    const int2 mi = gi[L.m];
+    int sx, sy;
+    T fx, fy;
+    const int i = first_node_units<T>(G.kind, mi.x, gf[2 * L.m], S.wi[0], S.wf[0], c ? T(0.5) : T(0), sx, fx) + L.a;
+    const int j = first_node_units<T>(G.kind, mi.y, gf[2 * L.m + 1], S.wi[1], S.wf[1], c ? T(0) : T(0.5), sy, fy) + L.b;
     if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
-      const size_t f = (size_t)j * G.ex[c] + i;
-      const uint8_t fl = (c ? flags.p[1] : flags.p[0])[f];
-      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
-      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
-      if (!(fl & 1)) s = (double)(px * py) * G.ihxy;   // solid nodes are excluded from F_N
+      const uint8_t fl = (c ? flags.p[1] : flags.p[0])[(size_t)j * G.ex[c] + i];
+      if (!(fl & 1)) s = phi_kernel<T>(G.kind, T(i - sx) - fx) * phi_kernel<T>(G.kind, T(j - sy) - fy);
     }
   }
-  const double F = sum16(s);
-  if (L.live && (threadIdx.x & 15) == 0) fn[L.pair] = F;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (L.live && (threadIdx.x & 15) == 0) wfac[L.pair] = s > T(0) ? dsh[L.m] / s : T(0);
 }
 
 // Marker bins of the rest positions (see IBDev): markers of cell (ci, cj) are the sorted
@@ -298,51 +376,116 @@ struct Bins {
   double x0, y0;   // grid origin (cell (0, 0) starts there)
 };
 
-// Eq. (18) in normalised form on one IB face per thread: u_IB = sum_i w_i v_i / sum_i w_i,
+// Eq. (18) in normalised form, one warp per IB face: u_IB = sum_i w_i v_i / sum_i w_i,
 // w_i = delta_h(x - X_i) dV_i / F_N_i, over the markers whose support holds the face.  The face's
-// rest-frame position x - w picks the cells whose markers can reach it (the kernel's support
-// plus one cell on each side); within a cell row the markers of consecutive cells are one
-// contiguous run of the sorted markers, visited in order.  FP64 sums, one writer per face.
-template <typename T>
-__global__ void __launch_bounds__(kT) ib_gather_kernel(const IBGeom G, const Bins Bn, const double* __restrict__ X0,
-                                                       const double* __restrict__ Y0, const double* __restrict__ ds,
-                                                       const double* __restrict__ fn,
-                                                       const double* __restrict__ body, double omega, double cx,
-                                                       double cy, const unsigned* __restrict__ list,
+// rest-frame position x - w picks the rows of rest cells that can hold such a marker; within a
+// row the markers of consecutive cells are one contiguous run of the sorted markers.  The runs
+// of the (at most 5) rows are laid end to end and the warp's lanes take one marker each (all
+// loads in flight at once), then the lanes' sums are reduced by shuffles in a fixed tree: one
+// writer per face, no atomics, the same result on every run.
+template <typename T, bool WARP>
+__global__ void __launch_bounds__(kT) ib_gather_kernel(const IBGeom G, const Bins Bn, const int2* __restrict__ gi,
+                                                       const T* __restrict__ gf, const T* __restrict__ rel,
+                                                       const T* __restrict__ wfac, const double* __restrict__ body,
+                                                       double omega, const unsigned* __restrict__ list,
                                                        const unsigned* __restrict__ count, T* num0, T* den0, T* num1,
                                                        T* den1) {
+  __shared__ Shift<T> S;
+  __shared__ T vbs[2];
+  if (threadIdx.x == 0) {
+    S = shift_of<T>(body, G.ihx, G.ihy);
+    vbs[0] = T(body[2]);
+    vbs[1] = T(body[3]);
+  }
+  __syncthreads();
   const unsigned n = *count;
-  const double wx = body[0], wy = body[1];
-  const double reach = G.kind == FS_PESKIN4 ? 2.0 : 1.5;
-  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+  constexpr int reach = 2;   // cells on each side of the face's own that can hold a marker within the support
+  const int lane = WARP ? (int)(threadIdx.x & 31) : 0;
+  const unsigned stride = WARP ? (gridDim.x * blockDim.x) >> 5 : gridDim.x * blockDim.x;
+  const unsigned first = WARP ? (blockIdx.x * blockDim.x + threadIdx.x) >> 5 : blockIdx.x * blockDim.x + threadIdx.x;
+  for (unsigned e = first; e < n; e += stride) {
     const unsigned code = list[e];
     const int c = (int)(code & 1u);
     const size_t f = code >> 1;
     const int i = (int)(f % (size_t)G.ex[c]), j = (int)(f / (size_t)G.ex[c]);
-    const double xf = node_x(G, c, i), yf = node_y(G, c, j);
-    const double sx = (xf - wx - Bn.x0) * G.ihx, sy = (yf - wy - Bn.y0) * G.ihy;
-    const int ci0 = max((int)floor(sx - reach) - 1, Bn.bx0), ci1 = min((int)floor(sx + reach) + 1, Bn.bx0 + Bn.nbx - 1);
-    const int cj0 = max((int)floor(sy - reach) - 1, Bn.by0), cj1 = min((int)floor(sy + reach) + 1, Bn.by0 + Bn.nby - 1);
-    double num = 0.0, den = 0.0;
-    for (int cj = cj0; cj <= cj1 && ci0 <= ci1; ++cj) {
-      const int row = (cj - Bn.by0) * Bn.nbx - Bn.bx0;
-      const int m0 = Bn.start[row + ci0], m1 = Bn.start[row + ci1 + 1];
-      for (int m = m0; m < m1; ++m) {
-        const double X = X0[m] + wx, Y = Y0[m] + wy;
-        const T py = phi_kernel<T>(G.kind, T((yf - Y) * G.ihy));
-        const T px = phi_kernel<T>(G.kind, T((xf - X) * G.ihx));
-        const T d = px * py;
-        const double F = fn[2 * m + c];
-        if (d == T(0) || !(F > 0.0)) continue;
-        const T w = T((double)d * G.ihxy * (ds[m] * G.hx) / F);
-        // marker velocity: body translation plus surface rotation
-        const double vm = c == 0 ? body[2] - omega * (Y - (cy + wy)) : body[3] + omega * (X - (cx + wx));
-        num += (double)(w * T(vm));
-        den += (double)w;
+    // the face's offsets from a marker with (gi, gf): (i - gi - wi) + (ox - gf - wf), likewise in y
+    const int ai = i - S.wi[0], aj = j - S.wi[1];
+    const T afx = (c ? T(0.5) : T(0)) - S.wf[0], afy = (c ? T(0) : T(0.5)) - S.wf[1];
+    // rest cells that can hold a marker with |face - marker| < 2 cells (Peskin) or 1.5 (Roma): a marker
+    // left out at the rounded window's edge would sit where the kernel vanishes
+    const int fcx = ai + (int)floor(afx), fcy = aj + (int)floor(afy);
+    const int ci0 = max(fcx - reach, Bn.bx0), ci1 = min(fcx + reach, Bn.bx0 + Bn.nbx - 1);
+    const int cj0 = max(fcy - reach, Bn.by0), cj1 = min(fcy + reach, Bn.by0 + Bn.nby - 1);
+    int roff[2 * reach + 1], rm0[2 * reach + 1];   // every row's run: offset in the candidate list, first marker
+    int total = 0;
+    if constexpr (WARP) {
+      // lane r < 2 reach + 1: the run of row cj0 + r
+      int m0 = 0, len = 0;
+      if (lane <= 2 * reach && cj0 + lane <= cj1 && ci0 <= ci1) {
+        const int row = (cj0 + lane - Bn.by0) * Bn.nbx - Bn.bx0;
+        m0 = Bn.start[row + ci0];
+        len = Bn.start[row + ci1 + 1] - m0;
+      }
+      // runs end to end: start offset of each row's run
+      int off = len;
+#pragma unroll
+      for (int o = 1; o < 8; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+      }
+      total = __shfl_sync(0xffffffffu, off, 2 * reach);
+      off -= len;                                   // exclusive
+#pragma unroll
+      for (int q = 0; q <= 2 * reach; ++q) {
+        roff[q] = __shfl_sync(0xffffffffu, off, q);
+        rm0[q] = __shfl_sync(0xffffffffu, m0, q);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q <= 2 * reach; ++q) {
+        int m0 = 0, len = 0;
+        if (cj0 + q <= cj1 && ci0 <= ci1) {
+          const int row = (cj0 + q - Bn.by0) * Bn.nbx - Bn.bx0;
+          m0 = Bn.start[row + ci0];
+          len = Bn.start[row + ci1 + 1] - m0;
+        }
+        roff[q] = total;
+        rm0[q] = m0;
+        total += len;
       }
     }
-    (c ? num1 : num0)[f] = T(num);
-    (c ? den1 : den0)[f] = T(den);
+    T num = T(0), den = T(0);
+    const T vb = vbs[c];
+    for (int k = lane; k < total; k += WARP ? 32 : 1) {
+      // the row holding candidate k (empty rows have the next row's offset and are passed over)
+      int m = rm0[0] + k;
+#pragma unroll
+      for (int q = 1; q <= 2 * reach; ++q)
+        if (k >= roff[q]) m = rm0[q] + (k - roff[q]);
+      const int2 mi = gi[m];
+      const T rx = T(ai - mi.x) + (afx - gf[2 * m]);
+      const T ry = T(aj - mi.y) + (afy - gf[2 * m + 1]);
+      const T d = phi_kernel<T>(G.kind, rx) * phi_kernel<T>(G.kind, ry);
+      const T wf = wfac[2 * m + c];
+      if (d != T(0) && wf > T(0)) {
+        const T w = d * wf;
+        // marker velocity: body translation plus surface rotation (rel: rest position - centre)
+        const T vm = omega == 0.0 ? vb : (c == 0 ? vb - T(omega) * rel[2 * m + 1] : vb + T(omega) * rel[2 * m]);
+        num += w * vm;
+        den += w;
+      }
+    }
+    if constexpr (WARP) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+      }
+    }
+    if (lane == 0) {
+      (c ? num1 : num0)[f] = num;
+      (c ? den1 : den0)[f] = den;
+    }
   }
 }
 
@@ -385,33 +528,43 @@ struct BodyODE {
 // finishes last (the others publish their slot before taking a ticket; no block waits) sums
 // the slots in a fixed order and, when asked, takes the body ODE step with that force.
 template <typename T>
-__global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const double* __restrict__ X0,
+__global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const int2* __restrict__ gi,
+                                                   const T* __restrict__ gf, const double* __restrict__ X0,
                                                    const double* __restrict__ Y0, const double* __restrict__ ds,
                                                    const double* body, const T* __restrict__ f0,
                                                    const T* __restrict__ f1, double cx, double cy, double rho,
                                                    double* __restrict__ q, double* __restrict__ part,
                                                    double* __restrict__ F, unsigned* __restrict__ ticket,
                                                    const BodyODE ode) {
+  __shared__ Shift<T> S;
+  if (threadIdx.x == 0) S = shift_of<T>(body, G.ihx, G.ihy);
+  __syncthreads();
   const Lane L = lane_of(G, nm);
-  double s = 0.0, X = 0.0, Y = 0.0;
-  if (L.live) {
-    X = X0[L.m] + body[0];
-    Y = Y0[L.m] + body[1];
-  }
+  // per node: f delta_h dv in the field precision (the grid is uniform near the body, so dv / (h_x h_y)
+  // is 1); the 16 lanes' sum, q_i, in FP64
+  T sp = T(0);
   if (L.live && L.b < G.width) {
     const int c = L.c;
     const T* f = c == 0 ? f0 : f1;
-    const int i = first_node(G, X, G.x0c[c], G.hx) + L.a, j = first_node(G, Y, G.y0c[c], G.hy) + L.b;
-    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
-      const T py = phi_kernel<T>(G.kind, T((node_y(G, c, j) - Y) * G.ihy));
-      const T px = phi_kernel<T>(G.kind, T((node_x(G, c, i) - X) * G.ihx));
-      const double dvy = c == 0 ? G.hyv[j] : G.hfyv[j];
-      s = (double)f[(size_t)j * G.ex[c] + i] * ((double)(px * py) * G.ihxy) * (G.hfx * dvy);
-    }
+    const int2 mi = gi[L.m];
+    int sx, sy;
+    T fx, fy;
+    const int i = first_node_units<T>(G.kind, mi.x, gf[2 * L.m], S.wi[0], S.wf[0], c ? T(0.5) : T(0), sx, fx) + L.a;
+    const int j = first_node_units<T>(G.kind, mi.y, gf[2 * L.m + 1], S.wi[1], S.wf[1], c ? T(0) : T(0.5), sy, fy) + L.b;
+    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c])
+      sp = f[(size_t)j * G.ex[c] + i] * (phi_kernel<T>(G.kind, T(i - sx) - fx) * phi_kernel<T>(G.kind, T(j - sy) - fy));
   }
-  s = sum16(s);
-  // this pair's terms of F and the torque (held by the pair's first lane)
-  __shared__ double s0[kT], s1[kT], s2[kT];
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+  const double s = (double)sp;
+  double X = 0.0, Y = 0.0;
+  if (L.live && (threadIdx.x & 15) == 0) {
+    X = X0[L.m] + body[0];
+    Y = Y0[L.m] + body[1];
+  }
+  // this pair's terms of F and the torque (held by the pair's first lane): only those lanes add,
+  // the two pair leaders of a warp by one shuffle, then one thread per block over its warps
+  __shared__ double s0[kT / 32], s1[kT / 32], s2[kT / 32];
   double a = 0.0, b = 0.0, tq = 0.0;
   if (L.live && (threadIdx.x & 15) == 0) {
     const double qv = -s;
@@ -426,25 +579,30 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
       tq = dV * rx * qv;
     }
   }
-  s0[threadIdx.x] = a;
-  s1[threadIdx.x] = b;
-  s2[threadIdx.x] = tq;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      s0[threadIdx.x] += s0[threadIdx.x + o];
-      s1[threadIdx.x] += s1[threadIdx.x + o];
-      s2[threadIdx.x] += s2[threadIdx.x + o];
+  {
+    const double a2 = __shfl_down_sync(0xffffffffu, a, 16), b2 = __shfl_down_sync(0xffffffffu, b, 16),
+                 t2 = __shfl_down_sync(0xffffffffu, tq, 16);
+    if ((threadIdx.x & 31) == 0) {
+      s0[threadIdx.x >> 5] = a + a2;
+      s1[threadIdx.x >> 5] = b + b2;
+      s2[threadIdx.x >> 5] = tq + t2;
     }
-    __syncthreads();
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    part[3 * blockIdx.x] = s0[0];
-    part[3 * blockIdx.x + 1] = s1[0];
-    part[3 * blockIdx.x + 2] = s2[0];
+    double sa = 0.0, sb = 0.0, st = 0.0;
+    for (int w = 0; w < kT / 32; ++w) {
+      sa += s0[w];
+      sb += s1[w];
+      st += s2[w];
+    }
+    part[3 * blockIdx.x] = sa;
+    part[3 * blockIdx.x + 1] = sb;
+    part[3 * blockIdx.x + 2] = st;
   }
   // the last block to finish reduces the block sums
   __shared__ bool last;
+  __shared__ double r0[kT], r1[kT], r2[kT];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -457,23 +615,22 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
     b += __ldcg(part + 3 * k + 1);
     tq += __ldcg(part + 3 * k + 2);
   }
-  __syncthreads();
-  s0[threadIdx.x] = a;
-  s1[threadIdx.x] = b;
-  s2[threadIdx.x] = tq;
+  r0[threadIdx.x] = a;
+  r1[threadIdx.x] = b;
+  r2[threadIdx.x] = tq;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) {
-      s0[threadIdx.x] += s0[threadIdx.x + o];
-      s1[threadIdx.x] += s1[threadIdx.x + o];
-      s2[threadIdx.x] += s2[threadIdx.x + o];
+      r0[threadIdx.x] += r0[threadIdx.x + o];
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o];
     }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    F[0] = rho * s0[0];
-    F[1] = rho * s1[0];
-    F[2] = rho * s2[0];
+    F[0] = rho * r0[0];
+    F[1] = rho * r1[0];
+    F[2] = rho * r2[0];
     *ticket = 0u;
     if (ode.st) rk4_body(ode.st, F, ode.m, ode.k, ode.c, ode.ax, ode.ay, ode.dt);
   }
@@ -518,6 +675,11 @@ void ib_prepare(fs_grid* G, const double* body_state) {
   P.n = B.nm;
   P.hmax = B.ehmax;
   for (int q = 0; q < 4; ++q) P.bb[q] = B.poly_bb[q];
+  P.ybin = B.ebin;
+  P.ybin0 = B.ebin0;
+  P.iybin = 1.0 / B.ebinh;
+  P.nybin = B.nebin;
+  P.ihx = 1.0 / G->hx;
   Flags dflags;
   dflags.p[0] = B.flags[0];
   dflags.p[1] = B.flags[1];
@@ -538,14 +700,22 @@ void ib_prepare(fs_grid* G, const double* body_state) {
   }
   const IBGeom g = make_geom(G);
   const int nlane = 2 * B.nm * 16;
-  FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(g, B.nm, B.X0, B.Y0, body_state,
-                                                                                     dflags, B.fn));
+  FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
+                            g, B.nm, B.gi, (const T*)B.gf, (const T*)B.dsh, body_state, dflags, (T*)B.wfac));
   Bins bn{B.bin_start, B.bx0, B.by0, B.nbx, B.nby, G->xf[0][0], G->xf[1][0]};
-  // IB faces: about two per marker and component; the kernel strides over the list's length
-  int nb = (int)std::min<long long>(148LL * 8, (4LL * B.nm + kT - 1) / kT + 1);
-  FS_LAUNCH(G, "ib_gather", ib_gather_kernel<T><<<nb, kT, 0, G->stream>>>(
-                                g, bn, B.X0, B.Y0, B.ds, B.fn, body_state, B.omega, B.centre[0], B.centre[1], B.iblist,
-                                B.ibcount, (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
+  // IB faces: about two per marker and component.  Small bodies take a warp per face (the candidate
+  // markers' loads all in flight: latency), large ones a thread per face (throughput); the kernel
+  // strides over the list
+  const bool warp = 4LL * B.nm * 32 <= 148LL * 2048;
+  const int nb = (int)std::min<long long>(148LL * 8, (4LL * B.nm * (warp ? 32 : 1) + kT - 1) / kT + 1);
+  if (warp)
+    FS_LAUNCH(G, "ib_gather", ib_gather_kernel<T, true><<<nb, kT, 0, G->stream>>>(
+                                  g, bn, B.gi, (const T*)B.gf, (const T*)B.rel, (const T*)B.wfac, body_state, B.omega,
+                                  B.iblist, B.ibcount, (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
+  else
+    FS_LAUNCH(G, "ib_gather", ib_gather_kernel<T, false><<<nb, kT, 0, G->stream>>>(
+                                  g, bn, B.gi, (const T*)B.gf, (const T*)B.rel, (const T*)B.wfac, body_state, B.omega,
+                                  B.iblist, B.ibcount, (T*)B.num[0], (T*)B.den[0], (T*)B.num[1], (T*)B.den[1]));
 }
 
 template <typename T>
@@ -556,8 +726,8 @@ void ib_forces(fs_grid* G, double* body_state, double* advance, double dt) {
   BodyODE ode{nullptr, B.mass, B.k, B.c, dt, B.active[0], B.active[1]};
   if (advance && B.mass > 0) ode.st = advance;
   FS_LAUNCH(G, "ib_force", force_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
-                               g, B.nm, B.X0, B.Y0, B.ds, body_state, (const T*)B.f[0], (const T*)B.f[1], B.centre[0],
-                               B.centre[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
+                               g, B.nm, B.gi, (const T*)B.gf, B.X0, B.Y0, B.ds, body_state, (const T*)B.f[0],
+                               (const T*)B.f[1], B.centre[0], B.centre[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
   B.have_forces = true;
 }
 

@@ -104,41 +104,58 @@ __device__ __forceinline__ T phi3(int kind, T r) {
 
 struct GatherArgs {
   int nm, kind, w;           // markers, kernel, support width
-  const double* X;           // SoA x, y, z
+  const int* gi;             // SoA 3 * nm: marker cell index per direction, floor((X - x0) / h)
+  const void* gf;            // SoA 3 * nm: its fraction in the cell, in the field precision
   const double* dV;
-  double h[3], x0[3];        // uniform spacing and domain origin
+  double h[3];               // uniform spacing
   int ext[3][3];             // extents per component
   int per[3];
   double dv, rho;
   double* q;                 // SoA 3 * nm
+  double* part;              // per-block sums of F (3 per block)
+  unsigned* ticket;          // blocks finished (reset by the last one)
   double* F;
 };
 
 // One thread per marker: the separable weights of the two face families of
 // every direction (a component's own faces, offset 0, and the faces across,
-// offset 1/2) are formed once and serve the three components; the support sums
-// run in the field precision, q and the body force in FP64.
+// offset 1/2) are formed once and serve the three components.  The marker's
+// position in grid units comes as a cell index and a fraction (computed in FP64
+// once, when the body is attached: the body is static), so the weights take no
+// FP64 arithmetic; the support sums run in the field precision, q and the body
+// force in FP64.  F is summed per block in a fixed tree and the block that
+// finishes last adds the block sums in a fixed order (no block waits): the
+// force is bitwise reproducible.
 template <typename T, int W>
 __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs A, const T* __restrict__ f0,
                                                      const T* __restrict__ f1, const T* __restrict__ f2) {
   __shared__ double red[3][8];
+  __shared__ bool last;
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   double contrib[3] = {0.0, 0.0, 0.0};
   if (m < A.nm) {
+    const T* gf = static_cast<const T*>(A.gf);
     int base[3][2];
     T wgt[3][2][W];
 #pragma unroll
-    for (int d = 0; d < 3; ++d)
+    for (int d = 0; d < 3; ++d) {
+      const int gi = A.gi[d * A.nm + m];
+      const T fr = gf[d * A.nm + m];
+      const T ih = T(1.0 / A.h[d]);
 #pragma unroll
       for (int fam = 0; fam < 2; ++fam) {
-        const double s = (A.X[d * A.nm + m] - A.x0[d]) / A.h[d] - (fam ? 0.5 : 0.0);
+        // position s = gi + fr - off in units of this family's nodes (off = 1/2 across the component)
+        T t = fr - (fam ? T(0.5) : T(0));
+        const T k = floor(t);
+        const int si = gi + (int)k;
+        t -= k;                                    // in [0, 1)
         // faces within the support |s - i| < W / 2
-        const int b0 = W == 4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
+        const int b0 = W == 4 ? si - 1 : si + (int)floor(t + T(0.5)) - 1;
         base[d][fam] = b0;
-        const T ih = T(1.0 / A.h[d]);
 #pragma unroll
-        for (int a = 0; a < W; ++a) wgt[d][fam][a] = phi3<T>(A.kind, T(s - (b0 + a))) * ih;
+        for (int a = 0; a < W; ++a) wgt[d][fam][a] = phi3<T>(A.kind, T(si - (b0 + a)) + t) * ih;
       }
+    }
     const T* fs[3] = {f0, f1, f2};
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -189,8 +206,30 @@ __global__ void __launch_bounds__(256) gather_kernel(const GatherArgs A, const T
   if (threadIdx.x < 3) {
     double v = 0.0;
     for (int q = 0; q < (int)(blockDim.x / 32); ++q) v += red[threadIdx.x][q];
-    if (v != 0.0) atomicAdd(&A.F[threadIdx.x], v);
+    A.part[3 * blockIdx.x + threadIdx.x] = v;
   }
+  // the last block to finish adds the block sums in block order
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(A.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    for (int cc = 0; cc < 3; ++cc) v[cc] += __ldcg(A.part + 3 * b + cc);
+  for (int cc = 0; cc < 3; ++cc)
+    for (int o = 16; o > 0; o >>= 1) v[cc] += __shfl_down_sync(0xffffffffu, v[cc], o);
+  __syncthreads();
+  if (l == 0)
+    for (int cc = 0; cc < 3; ++cc) red[cc][w] = v[cc];
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[threadIdx.x][q];
+    A.F[threadIdx.x] = t;
+  }
+  if (threadIdx.x == 0) *A.ticket = 0u;
 }
 
 }  // namespace
@@ -209,6 +248,10 @@ void free_ib3(fs_grid* G) {
   }
   F(B.q);
   F(B.F);
+  F(B.gi);
+  F(B.gf);
+  F(B.part);
+  F(B.ticket);
   B = IB3Dev();
   G->has_ib3 = false;
 }
@@ -221,12 +264,12 @@ void ib3_forces(fs_grid* G) {
   A.nm = B.nm;
   A.kind = B.kernel;
   A.w = B.kernel == FS_PESKIN4 ? 4 : 3;
-  A.X = B.X;
+  A.gi = B.gi;
+  A.gf = B.gf;
   A.dV = B.dV;
   const int n[3] = {G->nx, G->ny, G->nz};
   for (int d = 0; d < 3; ++d) {
     A.h[d] = G->h[d][0];
-    A.x0[d] = G->xf[d][0];
     A.per[d] = G->per[d];
     for (int c = 0; c < 3; ++c) A.ext[c][d] = n[d] + ((c == d && !G->per[d]) ? 1 : 0);
   }
@@ -234,7 +277,8 @@ void ib3_forces(fs_grid* G) {
   A.rho = G->rho;
   A.q = B.q;
   A.F = B.F;
-  cudaMemsetAsync(B.F, 0, 3 * sizeof(double), G->stream);
+  A.part = B.part;
+  A.ticket = B.ticket;
   const int nb = (B.nm + 255) / 256;
   if (A.w == 4)
     FS_LAUNCH(G, "ib3_force_gather", gather_kernel<T, 4><<<nb, 256, 0, G->stream>>>(
@@ -288,9 +332,33 @@ extern "C" int fs_set_ib_boxes(fs_grid* G, int nbox, const double* boxes, int nm
   std::vector<double> bx(boxes, boxes + 6 * (size_t)nbox), xs(3 * (size_t)nm), dv(dV, dV + nm);
   for (int m = 0; m < nm; ++m)
     for (int d = 0; d < 3; ++d) xs[(size_t)d * nm + m] = X[3 * (size_t)m + d];
+  // marker positions in grid units: cell index and fraction per direction (FP64 here, once)
+  std::vector<int> gi(3 * (size_t)nm);
+  std::vector<double> gfr(3 * (size_t)nm);
+  for (int d = 0; d < 3; ++d)
+    for (int m = 0; m < nm; ++m) {
+      const double g = (xs[(size_t)d * nm + m] - G->xf[d][0]) / G->h[d][0];
+      const double fl = std::floor(g);
+      gi[(size_t)d * nm + m] = (int)fl;
+      gfr[(size_t)d * nm + m] = g - fl;
+    }
+  const int nblk = std::max(1, (nm + 255) / 256);
   bool ok = upload_vec(&B.boxes, bx) == cudaSuccess && upload_vec(&B.X, xs) == cudaSuccess &&
             upload_vec(&B.dV, dv) == cudaSuccess && cudaMalloc(&B.q, std::max(3 * nm, 1) * sizeof(double)) == cudaSuccess &&
-            cudaMalloc(&B.F, 3 * sizeof(double)) == cudaSuccess;
+            cudaMalloc(&B.F, 3 * sizeof(double)) == cudaSuccess && upload_vec(&B.gi, gi) == cudaSuccess &&
+            cudaMalloc(&B.part, 3 * (size_t)nblk * sizeof(double)) == cudaSuccess &&
+            cudaMalloc(&B.ticket, sizeof(unsigned)) == cudaSuccess &&
+            cudaMemset(B.ticket, 0, sizeof(unsigned)) == cudaSuccess;
+  if (ok && G->prec == FS_MIXED) {
+    std::vector<float> g32(gfr.begin(), gfr.end());
+    float* p = nullptr;
+    ok = upload_vec(&p, g32) == cudaSuccess;
+    B.gf = p;
+  } else if (ok) {
+    double* p = nullptr;
+    ok = upload_vec(&p, gfr) == cudaSuccess;
+    B.gf = p;
+  }
   const size_t es = G->prec == FS_MIXED ? sizeof(float) : sizeof(double);
   const int n[3] = {G->nx, G->ny, G->nz};
   for (int c = 0; c < 3 && ok; ++c) {

@@ -771,13 +771,9 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // inverse P after one shuffle between the two threads; each thread then
 // substitutes outward,
 //   x_j = E_j g_j + C_j x_{j+1}   (upper),  x_j = E_j h_j + C_j x_{j-1}   (lower).
-// The sweeps carry the scaled values g^_j = E_j g_j instead (E_j -> 1 at the two
-// middle rows, which the 2x2 solve reads unscaled):
-//   g^_j = E_j d_j + M^_j g^_{j-1},   x_j = g^_j + C_j x_{j+1},
-// M^_j = E_j M_j / E_{j-1}.  The products E_j d_j of the FP32 spectrum and the
-// FP64 scales are formed exactly rounded on the integer pipes as the tile is
-// widened (fpconv.cuh), so the sweeps issue one FP64 multiply-add per row in
-// each direction.  M^, E, C are tabulated per eigenvalue (M^ and C negated).
+// That is one FP64 multiply-add per row forward and a multiply plus a
+// multiply-add backward: the FP64 work of a plain Thomas solve, spread over
+// twice the threads.  M, E, C are tabulated per eigenvalue (M and C negated).
 //
 // Periodic y (cyclic): with xi = x_{ny-1}, rows 0..ny-2 read A'' x' = d' - xi u,
 // u the coupling column of x_{ny-1}; so x' = y - xi z with A'' y = d' (the solve
@@ -803,14 +799,13 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // sweep rate).
 //
 // B300's FP64 pipe (one warp instruction per ~73 cycles per SM sub-partition,
-// conversions included) bounds the sweeps, which need 2 FP64 operations per
-// cell (plus the truncated correction with periodic y).  The block therefore
-// splits its warps: four "sweep" warps run the chains and issue little besides
-// FP64, while four helper warps widen and scale the FP32 spectrum to FP64 with
-// integer field arithmetic (fpconv.cuh) as its row groups arrive by bulk
-// asynchronous copies, releasing each group to the sweeps on an mbarrier.  All
-// eight warps narrow the solution at the end, which leaves by bulk copies as
-// well.  With FP64 fields the helpers scale in FP64.
+// conversions included) bounds the sweeps, which need 3 FP64 operations per
+// cell (4 with periodic y).  The block therefore splits its warps: four
+// "sweep" warps run the chains and issue little besides FP64, while four
+// helper warps widen the FP32 spectrum to FP64 with integer field arithmetic
+// (fpconv.cuh) as its row groups arrive by bulk asynchronous copies, releasing
+// each group to the sweeps on an mbarrier.  All eight warps narrow the solution
+// at the end, which leaves by bulk copies as well.
 //
 // The singular zero mode pins x_0 = 0 through its tables (E_0 = C_0 = 0,
 // M_1 = 0, no coupling to row 0) and is shifted to zero hy-weighted mean (with
@@ -835,6 +830,7 @@ struct YTwArgs {
   const double* hy;      // cell widths (zero-mode mean)
   double hysum;
   unsigned* status;      // device status word (bit 0: a bulk copy or group wait gave up)
+  int xblk0;             // first block of columns along x (blockIdx.x + xblk0)
 };
 
 constexpr int kTwU = kTwChunk;   // rows per chunk of the twisted solve (tables fetched a chunk ahead)
@@ -857,15 +853,6 @@ template <typename T>
 __device__ __forceinline__ T narrow(double v) {
   if constexpr (sizeof(T) == 4) return fsconv_narrow(v);
   else return v;
-}
-
-// s * v for the scaled elimination: v an FP32 spectrum value (bits u), s the row's FP64 scale;
-// the exactly rounded product is formed on the integer pipes (fpconv.cuh), the FP64 multiply
-// only for the inputs the fast path flags (sp).
-__device__ __forceinline__ double scale_fast(uint32_t u, double sv, uint32_t* sp) {
-  uint32_t hi, lo;
-  fsconv_scale_fast(u, (uint32_t)__double2hiint(sv), (uint32_t)__double2loint(sv), &hi, &lo, sp);
-  return __hiloint2double((int)hi, (int)lo);
 }
 
 template <typename T>
@@ -896,7 +883,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   constexpr int NB = 20;                         // tensor-map boxes of kTwBoxRows rows (ny <= 320)
   __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
   const int tid = threadIdx.x, lane = tid & 31;
-  const int s0 = blockIdx.x * W;
+  const int s0 = (blockIdx.x + A.xblk0) * W;
   const int ncol = min(W, A.nx - s0);
   int t = 0;
   if (A.dim == 3) {
@@ -947,18 +934,19 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       // chunk 0 is exactly the rows of box 0 (upper thread) or box 1 (lower): widened here, by
       // the thread that eliminates them, as soon as the box lands
       ok &= mbar_wait_idle(&bulkbar[half], 0);
-      const double* __restrict__ Es = A.E + tb;
       uint32_t sp = 0;
 #pragma unroll
       for (int q = 0; q < U; ++q) {
         const int j = rowof(P0 + q);
-        gp[q * W] = scale_fast(act && j >= 0 ? __float_as_uint((float)st[j * W + cb]) : 0u, __ldg(Es + q * nl), &sp);
+        uint32_t whi, wlo;
+        fsconv_widen_fast(act && j >= 0 ? __float_as_uint((float)st[j * W + cb]) : 0u, &whi, &wlo, &sp);
+        gp[q * W] = __hiloint2double((int)whi, (int)wlo);
       }
       if (__any_sync(FULL, sp)) {
 #pragma unroll
         for (int q = 0; q < U; ++q) {
           const int j = rowof(P0 + q);
-          gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) * __ldg(Es + q * nl) : 0.0;
+          gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) : 0.0;
         }
       }
     }
@@ -1000,12 +988,16 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     const double* Pt = A.P + (size_t)li * 4 + 2 * half;
     double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
     gp[(R - 1) * W] = xv;
-    // 3. outward substitution, positions descending (the stored g^ already carry E)
+    // 3. outward substitution, positions descending
     {
+      const double* __restrict__ Et = A.E + tb;
       const double* __restrict__ Ct = A.C + tb;
-      double cbuf[U];
+      double eb[U], cbuf[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
+      for (int q = 0; q < U; ++q) {
+        eb[q] = __ldg(Et + (R - 2 - q) * (ptrdiff_t)nl);
+        cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
+      }
       int next = nchunk - 1;                     // walls: highest output chunk not yet released
       for (int i0 = R - 2; i0 >= 0; i0 -= U) {
         if (i0 + 1 >= U) {
@@ -1013,8 +1005,9 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           double v[U], c2[U];
 #pragma unroll
           for (int q = 0; q < U; ++q) {
-            v[q] = gp[(i0 - q) * W];
+            v[q] = eb[q] * gp[(i0 - q) * W];
             c2[q] = cbuf[q];
+            eb[q] = __ldg(Et + (i0 - U - q) * (ptrdiff_t)nl);
             cbuf[q] = __ldg(Ct + (i0 - U - q) * (ptrdiff_t)nl);
           }
 #pragma unroll
@@ -1028,7 +1021,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
 #pragma unroll
           for (int q = 0; q < U; ++q) {
             if (q <= i0) {
-              xv = fma(cbuf[q], xv, gp[(i0 - q) * W]);
+              const double eg = eb[q] * gp[(i0 - q) * W];
+              xv = fma(cbuf[q], xv, eg);
               gp[(i0 - q) * W] = xv;
             }
           }
@@ -1086,10 +1080,6 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     // ---------------- helper threads: tile in, widened, group by group ----------------
     const int h = tid - NS;                      // 0 .. 2 W - 1
     const int hc = h % W, hw = h / W;            // this helper's column and row parity
-    // the row scales s_j of this helper's column (its eigenvalue's entries, position-major)
-    const size_t nlh = (size_t)A.nlp;
-    const double* __restrict__ Eh =
-        A.E + (size_t)(2 * U) * nlh + (hc < ncol ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s0 + hc, t) : 0);
     if (h >= 32 && !A.tiled) {
       // row copies: the block's table segments into L2 while the tile is in flight (the sweeps'
       // chunk-ahead register fetches then wait on L2, not on DRAM): per position, the eigenvalues
@@ -1139,11 +1129,13 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           // another value redoes its rows with the general routine
           uint32_t sp = 0;
 #pragma unroll 8
-          for (int j = a0 + hw; j < a1; j += 2)
-            sg[pos(j) * W + hc] = scale_fast(__float_as_uint(st[j * W + hc]), __ldg(Eh + (size_t)pos(j) * nlh), &sp);
+          for (int j = a0 + hw; j < a1; j += 2) {
+            uint32_t whi, wlo;
+            fsconv_widen_fast(__float_as_uint(st[j * W + hc]), &whi, &wlo, &sp);
+            sg[pos(j) * W + hc] = __hiloint2double((int)whi, (int)wlo);
+          }
           if (__any_sync(FULL, sp))
-            for (int j = a0 + hw; j < a1; j += 2)
-              sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]) * __ldg(Eh + (size_t)pos(j) * nlh);
+            for (int j = a0 + hw; j < a1; j += 2) sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&widebar[l]);
@@ -1172,16 +1164,13 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
         for (int r = hw; r < 2 * n; r += 2) {
           const int p = r < n ? lo + r : R + lo + (r - n);
           const bool hole = odd && !CYC && p == R;
-          const double sv = __ldg(Eh + (size_t)p * nlh);
           if constexpr (F32) {
             const uint32_t u = (hc < ncol && !hole) ? __float_as_uint(st[p * W + hc]) : 0u;
-            uint32_t sp = 0;
-            const double v = scale_fast(u, sv, &sp);
-            sg[p * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) * sv : v;
+            uint32_t whi, wlo, sp = 0;
+            fsconv_widen_fast(u, &whi, &wlo, &sp);
+            sg[p * W + hc] = sp ? fsconv_widen(__uint_as_float(u)) : __hiloint2double((int)whi, (int)wlo);
           } else if (hc >= ncol || hole) {
             sg[p * W + hc] = 0.0;
-          } else {
-            sg[p * W + hc] *= sv;
           }
         }
         __syncwarp();
@@ -1192,9 +1181,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       for (int e = h; e < NP * W; e += NS) {
         const int p = e / W, c = e - p * W;
         const int j = rowof(p);
-        const double* Ec =
-            A.E + (size_t)(2 * U + p) * nlh + (c < ncol ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s0 + c, t) : 0);
-        sg[e] = (c < ncol && j >= 0) ? widen<T>(tile[rs * j + c]) * __ldg(Ec) : 0.0;
+        sg[e] = (c < ncol && j >= 0) ? widen<T>(tile[rs * j + c]) : 0.0;
       }
       asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");   // every helper's rows are in
       if (lane == 0)
@@ -1500,15 +1487,16 @@ struct RegLaunch {
     launch_pdl(G, "fft_x_inv", xinv_reg_kernel<T, N>, dim3(nb), dim3(kRegBlock), reg_smem_bytes<T, N>(0), data, rows,
                G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw);
   }
-  static void zfwd(fs_grid* G, T* data) {
-    const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
-    launch_pdl(G, "fft_z_fwd", zfwd_reg_kernel<T, N>, grid, dim3(kRegBlock), reg_smem_bytes<T, N>(0), data, G->nx, G->ny,
-               (const cplx<T>*)G->pz.tw);
+  // tiles [tile0, tile0 + ntiles) of kRegLines slot pairs (ntiles <= 0: every tile)
+  static void zfwd(fs_grid* G, T* data, int tile0 = 0, int ntiles = 0) {
+    const int nt = ntiles > 0 ? ntiles : (G->nx / 2 + kRegLines - 1) / kRegLines;
+    launch_pdl(G, "fft_z_fwd", zfwd_reg_kernel<T, N>, dim3(nt, G->ny), dim3(kRegBlock), reg_smem_bytes<T, N>(0), data,
+               G->nx, G->ny, (const cplx<T>*)G->pz.tw, tile0);
   }
-  static void zinv(fs_grid* G, T* data) {
-    const dim3 grid((G->nx / 2 + kRegLines - 1) / kRegLines, G->ny);
-    launch_pdl(G, "fft_z_inv", zinv_reg_kernel<T, N>, grid, dim3(kRegBlock), reg_smem_bytes<T, N>(1), data, G->nx, G->ny,
-               (const cplx<T>*)G->pz.tw);
+  static void zinv(fs_grid* G, T* data, int tile0 = 0, int ntiles = 0) {
+    const int nt = ntiles > 0 ? ntiles : (G->nx / 2 + kRegLines - 1) / kRegLines;
+    launch_pdl(G, "fft_z_inv", zinv_reg_kernel<T, N>, dim3(nt, G->ny), dim3(kRegBlock), reg_smem_bytes<T, N>(1), data,
+               G->nx, G->ny, (const cplx<T>*)G->pz.tw, tile0);
   }
   static void yspec(fs_grid* G, T* data, const YSpecArgs& A) {
     const dim3 grid((G->nx + 31) / 32, G->dim == 3 ? G->nz : 1);
@@ -1596,6 +1584,64 @@ bool encode_spectrum_map(CUtensorMap* map, const float* data, int nx, int ny, in
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The twisted y solve over column blocks [xblk0, xblk0 + nxblk) along x (nxblk <= 0: all).
+template <typename T>
+void launch_ytwist(fs_grid* G, T* data, int xblk0, int nxblk) {
+  const int nx = G->nx, ny = G->ny, nz = G->nz;
+  YTwArgs A;
+  A.nx = nx;
+  A.ny = ny;
+  A.nz = nz;
+  A.dim = G->dim;
+  A.xmode = G->xmode;
+  A.nmx = G->nmx;
+  A.nlz = G->nlz;
+  A.L = G->ytw_L;
+  A.R = G->ytw_R;
+  A.nlp = G->ytw_nlp;
+  A.M = G->twM;
+  A.E = G->twE;
+  A.C = G->twC;
+  A.P = G->twP;
+  A.Z = G->twZ;
+  A.S = G->twS;
+  A.K = G->twK;
+  A.hy = G->hy64;
+  A.hysum = G->hysum;
+  A.status = G->dstatus;
+  A.xblk0 = xblk0;
+  // rows move by bulk copies when every row start and width is a multiple of 16 bytes
+  A.bulk = (nx * (int)sizeof(T)) % 16 == 0 && reinterpret_cast<uintptr_t>(data) % 16 == 0;
+  const int w = G->ytw_cols;
+  // FP32 tiles of at least one box of rows arrive as tensor-map boxes (a few large copies
+  // instead of one bulk copy per row); the map is encoded once per spectrum array
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof(tmap));
+  A.tiled = 0;
+  if (sizeof(T) == 4 && A.bulk && ny >= 2 * kTwBoxRows && ny <= 20 * kTwBoxRows && G->tune_ytile) {
+    const int nzt = G->dim == 3 ? nz : 1;
+    if (G->ytw_map_ptr != (const void*)data || G->ytw_map_w != w) {
+      G->ytw_map_ok = encode_spectrum_map(reinterpret_cast<CUtensorMap*>(G->ytw_map), (const float*)data, nx, ny,
+                                          nzt, w);
+      G->ytw_map_ptr = data;
+      G->ytw_map_w = w;
+    }
+    if (G->ytw_map_ok) {
+      std::memcpy(&tmap, G->ytw_map, sizeof(tmap));
+      A.tiled = 1;
+    }
+  }
+  const dim3 grid(nxblk > 0 ? nxblk : (nx + w - 1) / w, G->dim == 3 ? nz : 1);
+  const size_t sb = ytwist_smem<T>(ny, w);
+  if (w == 64) {
+    if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(256), sb, data, A, tmap);
+    else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(256), sb, data, A, tmap);
+  } else {
+    if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(128), sb, data, A, tmap);
+    else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(128), sb, data, A, tmap);
+  }
+}
+
 template <typename T>
 void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   set_smem_attrs<T>();
@@ -1618,150 +1664,129 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
                                                                     (const cplx<T>*)G->px.tw,
                                                                     (const cplx<T>*)G->px.dtw, dv ? *dv : none));
   }
-  int ppb = 0;
-  const bool zreg = G->dim == 3 && is_reg_length(nz);
-  if (zreg) {
-    with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data); });
-  } else if (G->dim == 3) {
-    if (is_fixed_length<T>(G->pz.n)) {
-      ppb = kMaxLines;   // the compile-time-length z kernels map 32 slots x 8 rows onto 256 threads
-    } else {
-      ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
-      const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : kMaxLines;
-      ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
-      if (ppb > nx / 2) ppb = nx / 2;
-    }
-    dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
-    auto k = fft_kernels<T>(G->pz).zfwd;
-    FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
-                                                            (const cplx<T>*)G->pz.tw));
-  }
-  if (G->yspec && is_reg_length(ny)) {
-    YSpecArgs A;
-    A.nx = nx;
-    A.ny = ny;
-    A.nz = nz;
-    A.dim = G->dim;
-    A.xmode = G->xmode;
-    A.nmx = G->nmx;
-    A.spb = 32;
-    with_reg_length<T>(ny, [&](auto L) { L.yspec(G, data, A); });
-  } else if (G->yspec) {
-    YSpecArgs A;
-    A.nx = nx;
-    A.ny = ny;
-    A.nz = nz;
-    A.dim = G->dim;
-    A.xmode = G->xmode;
-    A.nmx = G->nmx;
-    // slots per block: an even count whose two ping-pong buffers fit the budget
-    const size_t line_bytes = 2ull * (ny + 1) * sizeof(cplx<T>);
-    int spb = 2 * (int)std::min<size_t>(kMaxLines, kYSpecBudget / line_bytes);
-    if (is_fixed_length<T>(ny)) spb = 2 * kMaxLines;   // compile-time lengths map 32 slots x 8 rows onto 256 threads
-    else if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
-    A.spb = spb;
-    dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);
-    auto k = fft_kernels<T>(G->py).yspec;
-    FS_LAUNCH(G, "fft_y_solve", k<<<grid, 256, (size_t)(spb / 2) * line_bytes, G->stream>>>(
-                                    data, A, radices_of(G->py), (const cplx<T>*)G->py.tw, (const T*)G->lamy,
-                                    (const T*)G->lamxz));
-  } else if (G->ytwist) {
-    YTwArgs A;
-    A.nx = nx;
-    A.ny = ny;
-    A.nz = nz;
-    A.dim = G->dim;
-    A.xmode = G->xmode;
-    A.nmx = G->nmx;
-    A.nlz = G->nlz;
-    A.L = G->ytw_L;
-    A.R = G->ytw_R;
-    A.nlp = G->ytw_nlp;
-    A.M = G->twM;
-    A.E = G->twE;
-    A.C = G->twC;
-    A.P = G->twP;
-    A.Z = G->twZ;
-    A.S = G->twS;
-    A.K = G->twK;
-    A.hy = G->hy64;
-    A.hysum = G->hysum;
-    A.status = G->dstatus;
-    // rows move by bulk copies when every row start and width is a multiple of 16 bytes
-    A.bulk = (nx * (int)sizeof(T)) % 16 == 0 && reinterpret_cast<uintptr_t>(data) % 16 == 0;
-    const int w = G->ytw_cols;
-    // FP32 tiles of at least one box of rows arrive as tensor-map boxes (a few large copies
-    // instead of one bulk copy per row); the map is encoded once per spectrum array
-    CUtensorMap tmap;
-    std::memset(&tmap, 0, sizeof(tmap));
-    A.tiled = 0;
-    if (sizeof(T) == 4 && A.bulk && ny >= 2 * kTwBoxRows && ny <= 20 * kTwBoxRows && G->tune_ytile) {
-      const int nzt = G->dim == 3 ? nz : 1;
-      if (G->ytw_map_ptr != (const void*)data || G->ytw_map_w != w) {
-        G->ytw_map_ok = encode_spectrum_map(reinterpret_cast<CUtensorMap*>(G->ytw_map), (const float*)data, nx, ny,
-                                            nzt, w);
-        G->ytw_map_ptr = data;
-        G->ytw_map_w = w;
-      }
-      if (G->ytw_map_ok) {
-        std::memcpy(&tmap, G->ytw_map, sizeof(tmap));
-        A.tiled = 1;
-      }
-    }
-    const dim3 grid((nx + w - 1) / w, G->dim == 3 ? nz : 1);
-    const size_t sb = ytwist_smem<T>(ny, w);
-    if (w == 64) {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 64>, grid, dim3(256), sb, data, A, tmap);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 64>, grid, dim3(256), sb, data, A, tmap);
-    } else {
-      if (G->cyclic) launch_pdl(G, "ysolve", ytwist_kernel<T, true, 32>, grid, dim3(128), sb, data, A, tmap);
-      else launch_pdl(G, "ysolve", ytwist_kernel<T, false, 32>, grid, dim3(128), sb, data, A, tmap);
-    }
+  // Periodic-z grids with the twisted y solve in two or more column blocks along x: the z
+  // transforms and the y solve of the two halves of the x spectrum are independent, so they run as
+  // two chains on two streams (fork after the x transform, join before its inverse).  The y solve is
+  // bound by the FP64 pipe and the z transforms by memory, so each half's y solve runs beside the
+  // other half's transforms; each y-solve half also holds one block per SM instead of two.
+  const bool zreg2 = G->dim == 3 && is_reg_length(nz);
+  const int wcol = G->ytw_cols;
+  const int nxb = (nx + wcol - 1) / wcol;
+  const int tiles_per_blk = (wcol / 2) / kRegLines;
+  const bool split = G->tune_ysplit && zreg2 && G->ytwist && !G->yspec && G->ystream2 && nxb >= 2 &&
+                     nx % wcol == 0 && (wcol / 2) % kRegLines == 0;
+  if (split) {
+    const int hb = nxb / 2;
+    const int nt = (nx / 2) / kRegLines;
+    cudaEventRecord(G->yev[0], G->stream);
+    cudaStreamWaitEvent(G->ystream2, G->yev[0], 0);
+    with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data, 0, hb * tiles_per_blk); });
+    launch_ytwist<T>(G, data, 0, hb);
+    with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data, 0, hb * tiles_per_blk); });
+    cudaStream_t main = G->stream;
+    G->stream = G->ystream2;
+    with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data, hb * tiles_per_blk, nt - hb * tiles_per_blk); });
+    launch_ytwist<T>(G, data, hb, nxb - hb);
+    with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data, hb * tiles_per_blk, nt - hb * tiles_per_blk); });
+    cudaEventRecord(G->yev[1], G->stream);
+    G->stream = main;
+    cudaStreamWaitEvent(G->stream, G->yev[1], 0);
   } else {
-    YArgs A;
-    A.nx = nx;
-    A.ny = ny;
-    A.nz = nz;
-    A.dim = G->dim;
-    A.xmode = G->xmode;
-    A.nmx = G->nmx;
-    A.nlz = G->nlz;
-    A.cyclic = G->cyclic;
-    A.a = G->ya;
-    A.E = G->tE;
-    A.CP = G->tCP;
-    A.ZV = G->tZV;
-    A.WV = G->tWV;
-    A.MI = G->tMI;
-    A.hy = G->hy64;
-    A.hysum = G->hysum;
-    A.pitch = G->ypitch;
-    A.status = G->dstatus;
-    // narrow blocks with staged tables when 32-column blocks would leave SMs idle
-    const int tz = G->dim == 3 ? nz : 1;
-    const int yc = G->ynarrow ? 8 : YCOLS;
-    const dim3 grid((nx + yc - 1) / yc, tz);
-    const int ns = G->ynseg;
-    const size_t sb = ysolve_smem(ny, ns, yc);
-    if (yc == 8) {
-      if (ns == 16) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, 8><<<grid, dim3(8, 16), sb, G->stream>>>(data, A));
-      else if (ns == 8) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, 8><<<grid, dim3(8, 8), sb, G->stream>>>(data, A));
-      else FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, 8><<<grid, dim3(8, 4), sb, G->stream>>>(data, A));
-    } else if (ns == 16) {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, YCOLS><<<grid, dim3(YCOLS, 16), sb, G->stream>>>(data, A));
-    } else if (ns == 8) {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, YCOLS><<<grid, dim3(YCOLS, 8), sb, G->stream>>>(data, A));
-    } else {
-      FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, YCOLS><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
+    int ppb = 0;
+    const bool zreg = G->dim == 3 && is_reg_length(nz);
+    if (zreg) {
+      with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data); });
+    } else if (G->dim == 3) {
+      if (is_fixed_length<T>(G->pz.n)) {
+        ppb = kMaxLines;   // the compile-time-length z kernels map 32 slots x 8 rows onto 256 threads
+      } else {
+        ppb = (int)(kSmemBudget / fft_smem_bytes_z<T>(nz, 1));
+        const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : kMaxLines;
+        ppb = ppb > want ? want : (ppb < 1 ? 1 : ppb);
+        if (ppb > nx / 2) ppb = nx / 2;
+      }
+      dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
+      auto k = fft_kernels<T>(G->pz).zfwd;
+      FS_LAUNCH(G, "fft_z_fwd", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+                                                              (const cplx<T>*)G->pz.tw));
     }
-  }
-  if (zreg) {
-    with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data); });
-  } else if (G->dim == 3) {
-    dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
-    auto k = fft_kernels<T>(G->pz).zinv;
-    FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
-                                                            (const cplx<T>*)G->pz.tw));
+    if (G->yspec && is_reg_length(ny)) {
+      YSpecArgs A;
+      A.nx = nx;
+      A.ny = ny;
+      A.nz = nz;
+      A.dim = G->dim;
+      A.xmode = G->xmode;
+      A.nmx = G->nmx;
+      A.spb = 32;
+      with_reg_length<T>(ny, [&](auto L) { L.yspec(G, data, A); });
+    } else if (G->yspec) {
+      YSpecArgs A;
+      A.nx = nx;
+      A.ny = ny;
+      A.nz = nz;
+      A.dim = G->dim;
+      A.xmode = G->xmode;
+      A.nmx = G->nmx;
+      // slots per block: an even count whose two ping-pong buffers fit the budget
+      const size_t line_bytes = 2ull * (ny + 1) * sizeof(cplx<T>);
+      int spb = 2 * (int)std::min<size_t>(kMaxLines, kYSpecBudget / line_bytes);
+      if (is_fixed_length<T>(ny)) spb = 2 * kMaxLines;   // compile-time lengths map 32 slots x 8 rows onto 256 threads
+      else if (G->tune_fft_lines > 0) spb = std::min(spb, 2 * G->tune_fft_lines);
+      A.spb = spb;
+      dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);
+      auto k = fft_kernels<T>(G->py).yspec;
+      FS_LAUNCH(G, "fft_y_solve", k<<<grid, 256, (size_t)(spb / 2) * line_bytes, G->stream>>>(
+                                      data, A, radices_of(G->py), (const cplx<T>*)G->py.tw, (const T*)G->lamy,
+                                      (const T*)G->lamxz));
+    } else if (G->ytwist) {
+      launch_ytwist<T>(G, data, 0, 0);
+    } else {
+      YArgs A;
+      A.nx = nx;
+      A.ny = ny;
+      A.nz = nz;
+      A.dim = G->dim;
+      A.xmode = G->xmode;
+      A.nmx = G->nmx;
+      A.nlz = G->nlz;
+      A.cyclic = G->cyclic;
+      A.a = G->ya;
+      A.E = G->tE;
+      A.CP = G->tCP;
+      A.ZV = G->tZV;
+      A.WV = G->tWV;
+      A.MI = G->tMI;
+      A.hy = G->hy64;
+      A.hysum = G->hysum;
+      A.pitch = G->ypitch;
+      A.status = G->dstatus;
+      // narrow blocks with staged tables when 32-column blocks would leave SMs idle
+      const int tz = G->dim == 3 ? nz : 1;
+      const int yc = G->ynarrow ? 8 : YCOLS;
+      const dim3 grid((nx + yc - 1) / yc, tz);
+      const int ns = G->ynseg;
+      const size_t sb = ysolve_smem(ny, ns, yc);
+      if (yc == 8) {
+        if (ns == 16) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, 8><<<grid, dim3(8, 16), sb, G->stream>>>(data, A));
+        else if (ns == 8) FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, 8><<<grid, dim3(8, 8), sb, G->stream>>>(data, A));
+        else FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, 8><<<grid, dim3(8, 4), sb, G->stream>>>(data, A));
+      } else if (ns == 16) {
+        FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 16, YCOLS><<<grid, dim3(YCOLS, 16), sb, G->stream>>>(data, A));
+      } else if (ns == 8) {
+        FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 8, YCOLS><<<grid, dim3(YCOLS, 8), sb, G->stream>>>(data, A));
+      } else {
+        FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, YCOLS><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
+      }
+    }
+    if (zreg) {
+      with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data); });
+    } else if (G->dim == 3) {
+      dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
+      auto k = fft_kernels<T>(G->pz).zinv;
+      FS_LAUNCH(G, "fft_z_inv", k<<<grid, 256, fft_smem_bytes_z<T>(nz, ppb), G->stream>>>(data, nx, ny, nz, ppb, radices_of(G->pz),
+                                                              (const cplx<T>*)G->pz.tw));
+    }
   }
   if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xinv(G, data, rows); });

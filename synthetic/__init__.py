@@ -13,7 +13,7 @@ Workloads (sizes and parameters from the paper's cases, §3):
   cylinder_2d       cylinder of diameter D = 40 cells in a 16 D x 8 D box, uniform inflow,
                     free-slip sides, outflow, 126 markers (§3.1-3.2)
   cylinder_array_2d an array of cylinders moving as one elastically mounted body (the
-                    immersed-boundary stress case: 32 x 32 cylinders, 102,400 markers)
+                    immersed-boundary stress case: 12 x 116 cylinders, 104,400 markers)
   poiseuille_2d     periodic channel with no-slip walls and a uniform body force
 
 The initial fields are not made discretely divergence-free here; the first
@@ -251,7 +251,7 @@ def cylinder_2d(nx=640, ny=320, cells_per_d=40, nm=126, re=150.0, mass_ratio=2.0
                     precision=precision, kernel=kernel, body=body, u0=[u, v])
 
 
-def cylinder_array_2d(rows=32, cols=32, cells_per_d=32, pitch_d=2.0, margin_d=(4.0, 1.0), nm_per=None,
+def cylinder_array_2d(rows=12, cols=116, cells_per_d=24, pitch_d=2.0, margin_d=(4.0, 1.0), nm_per=None,
                       re=150.0, mass_ratio=2.0, reduced_velocity=5.0, U=1.0, dt=None, steps=100, kernel=ROMA3,
                       precision="mixed", seed=5, perturb=0.01):
     """A rows x cols array of cylinders (diameter D = 1 = cells_per_d cells, centres pitch_d D apart)
