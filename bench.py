@@ -179,6 +179,12 @@ def workload(name):
         return S.taylor_green_2d()
     if name == "cylinder_2d":
         return S.cylinder_2d(seed=2, perturb=0.01)
+    if name == "cylinder_array_2d":
+        return S.cylinder_array_2d()
+    if name == "rough_channel_3d_128":
+        # the rough-wall case of the static-box stress leg at 128^3 (cubes of 4 cells every 6, both
+        # walls, markers every h/2)
+        return S.rough_channel_3d(128, 128, 128, cube=4, pitch=6, both_walls=True, marker_spacing=0.5)
     raise ValueError(name)
 
 
@@ -290,7 +296,38 @@ def ensemble_leg(args, flush):
     torch.cuda.synchronize()
     g_ms = e2.elapsed_time(e3)
     sizes = sorted({tuple(w.n[:2]) for w in wls})
-    return {"members": len(wls), "cells": cells, "steps": k, "grid_sizes": len(sizes),
+    # forward + adjoint over the workload's 500 steps (windows of 20: a checkpoint per window, each
+    # window's forward recomputed in the reverse sweep); loss: the members' final kinetic energy
+    window, windows = 20, 25
+    weights = [[torch.tensor((w.xf[0][1] - w.xf[0][0]) ** 2, dtype=torch.float32, device="cuda")] * 2
+               for w in wls]
+    ens.restore(snap)
+    ens.setup_adjoint(window, windows, weights)
+    ens.capture_windows()
+    ens.fwd_adj_graph()   # upload replays
+    torch.cuda.synchronize()
+    flush.fill_(5)
+    e4, e5, e6 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e4.record(stream)
+    ens.fwd_adj_graph()
+    e5.record(stream)
+    torch.cuda.synchronize()
+    lam_graph = [[x.double().clone() for x in lu] for lu, _ in ens.lam_v]
+    ens.fwd_adj_sequential()
+    e6.record(stream)
+    torch.cuda.synchronize()
+    ga_ms, sa_ms = e4.elapsed_time(e5), e5.elapsed_time(e6)
+    num = sum(float(((a - b.double()) ** 2).sum()) for la, (lu, _) in zip(lam_graph, ens.lam_v) for a, b in zip(la, lu))
+    den = sum(float((b.double() ** 2).sum()) for lu, _ in ens.lam_v for b in lu)
+    nfa = window * windows
+    fwd_adj = {"steps": nfa, "window": window, "graph_launches": 2 * windows,
+               "graph": {"value": cells * nfa / (ga_ms * 1e-3), "unit": "cell-updates/s fwd+adj", "ms": ga_ms},
+               "one_by_one": {"value": cells * nfa / (sa_ms * 1e-3), "unit": "cell-updates/s fwd+adj", "ms": sa_ms},
+               "speedup": sa_ms / ga_ms, "graph_vs_one_by_one_grad_rel_l2": (num / den) ** 0.5,
+               "note": "every member's 500 steps forward (a checkpoint per 20-step window), then the reverse "
+                       "sweep: per window its forward recomputed keeping each state and its 20 adjoint steps; "
+                       "graph = 2 graphs over all members on 32 branches, 50 launches"}
+    return {"members": len(wls), "cells": cells, "steps": k, "grid_sizes": len(sizes), "fwd_adj": fwd_adj,
             "graph": {"value": cells * k / (g_ms * 1e-3), "unit": "cell-updates/s", "ms": g_ms,
                       "launches": 1},
             "one_by_one": {"value": cells * k / (seq_ms * 1e-3), "unit": "cell-updates/s", "ms": seq_ms},
@@ -307,24 +344,30 @@ def run_ours(args, ws, rank, local):
     wl = workload(args.workload)
     cells = wl.cells()
     stream = torch.cuda.current_stream()
-    g = grid_from_workload(wl, "mixed", stream=stream)
+    g = grid_from_workload(wl, args.precision, stream=stream)
     # "FP32 stencils / FP64 Poisson": on a periodic y the y part of the Poisson solve is the FP64
     # cyclic tridiagonal per x/z wavenumber (x and z transforms in FP32, zero mode exact)
     fp64_y = args.y_solve == "fp64" and wl.bc[1][0] == S.PERIODIC
     if fp64_y:
         g.set_tuning("y_spectral", 0)
-    u0 = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
+    u0 = [torch.tensor(np.asarray(a), dtype=g.dtype, device=dev).contiguous() for a in wl.u0]
     u = [x.clone() for x in u0]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    if args.precision != "mixed":
+        args.quick = True        # the comparison legs are defined for the mixed-precision headline
+    from paper_2505_23940_b300 import body_tensor
+    body = body_tensor(wl)   # FSI workloads (forward legs only)
+    if body is not None:
+        args.quick = True
 
     for _ in range(args.warmup):
-        g.step(u, wl.dt, 1)
+        g.step(u, wl.dt, 1, body=body)
     torch.cuda.synchronize()
     barrier(ws)
     torch.cuda.synchronize()
     launches0 = g.launches()
     with Clocks(local) as clk:
-        ms = timed_steps(g, u, wl.dt, args.steps, flush, stream)
+        ms = timed_steps(g, u, wl.dt, args.steps, flush, stream, body=body)
     launches = g.launches() - launches0
     barrier(ws)
     total_ms = max_over_ranks(ws, sum(ms), dev)
@@ -332,7 +375,7 @@ def run_ours(args, ws, rank, local):
 
     # every kernel's launches timed by CUDA events on the grid's stream over the same K flushed
     # steps again: the dominant kernel and its roofline
-    allk = kernel_times(g, u, wl.dt, args.steps, flush, stream, "")
+    allk = kernel_times(g, u, wl.dt, args.steps, flush, stream, "", body=body)
     dominant = max(allk, key=lambda k: allk[k][1])
     cnt, kms = allk.get(dominant, (0, 0.0))
     peaks = measured_peaks()
@@ -378,10 +421,11 @@ def run_ours(args, ws, rank, local):
     line = {
         "metric": "cell-updates/s forward", "value": value, "unit": "cell-updates/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "cells": cells, "n": wl.n, "scheme": wl.scheme,
-                   "precision": ("mixed: FP32 stencils and x/z transforms; FP64 Poisson along y (cyclic "
+                   "precision": ("FP64 throughout" if args.precision == "fp64" else
+                                 "mixed: FP32 stencils and x/z transforms; FP64 Poisson along y (cyclic "
                                  "tridiagonal per wavenumber), zero mode and reductions" if fp64_y else
                                  "mixed (FP32 stencils/transforms, FP64 tridiagonal/zero mode/reductions)"),
                    "l2": "flushed before every timed step (256 MB write outside the timed events)",
@@ -511,16 +555,29 @@ def run_ours(args, ws, rank, local):
         line["fwd_adj"]["speedup_mixed_over_fp64"] = line["fwd_adj"]["value"] / line["fwd_adj"]["fp64_gpu"]["value"]
         del g64, u64, ro64
 
+    def leg(key, fn):
+        # a leg that fails records its error instead of ending the run without the headline line
+        try:
+            line[key] = fn()
+        except Exception as e:   # noqa: BLE001
+            line[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+            torch.cuda.synchronize()
+            torch.cuda.empty_cache()
+
+    if not args.quick and args.gradients:
+        leg("gradients", lambda: gradient_legs(stream, flush))
+
     if not args.quick and args.ensemble > 0:
-        line["ensemble"] = ensemble_leg(args, flush)
+        leg("ensemble", lambda: ensemble_leg(args, flush))
 
     if not args.quick:
-        line["krylov"] = krylov_leg(wl, stream)
+        leg("krylov", lambda: krylov_leg(wl, stream))
     if not args.quick and args.ib_stress:
-        line["ib_stress"] = ib_stress_leg(stream, flush)
+        leg("ib_stress", lambda: ib_stress_leg(stream, flush))
+        leg("ib2_stress", lambda: ib2_stress_leg(stream, flush))
 
     if not args.quick and args.sweep:
-        line["hbm_sweep"] = [sweep_leg(n, stream, flush) for n in args.sweep.split(",") if n]
+        leg("hbm_sweep", lambda: [sweep_leg(n, stream, flush) for n in args.sweep.split(",") if n])
 
     if rank == 0 and not args.quick and args.cpu_steps > 0:
         rate, secs = cpu_oracle_rate(wl, args.cpu_steps)
@@ -528,8 +585,231 @@ def run_ours(args, ws, rank, local):
                                 "kind": "oracle",
                                 "sample": "%d full time step(s) of the %s workload, FP64 torch CPU oracle, %.1f s"
                                           % (args.cpu_steps, args.workload, secs)}
+    line["summary"] = summary_of(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _face_weights(wl, dev, dtype):
+    """Face control volumes per velocity component (x-fastest tensors): the weights of the
+    kinetic energy 1/2 sum_c sum_faces u_c^2 V_c."""
+    h = [np.diff(np.asarray(wl.xf[d], dtype=np.float64)) for d in range(wl.dim)]
+    out = []
+    for c in range(wl.dim):
+        per = wl.bc[c][0] == S.PERIODIC
+        ws = []
+        for d in range(wl.dim):
+            if d != c:
+                ws.append(h[d])
+            else:
+                xc = 0.5 * (np.asarray(wl.xf[d][:-1]) + np.asarray(wl.xf[d][1:]))
+                if per:
+                    hf = np.empty_like(h[d])
+                    hf[1:] = np.diff(xc)
+                    hf[0] = xc[0] - (xc[-1] - (wl.xf[d][-1] - wl.xf[d][0]))
+                else:
+                    hf = np.empty(h[d].size + 1)
+                    hf[1:-1] = np.diff(xc)
+                    hf[0], hf[-1] = h[d][0], h[d][-1]
+                ws.append(hf)
+        w = ws[0][None, None, :] * ws[1][None, :, None]
+        if wl.dim == 3:
+            w = w * ws[2][:, None, None]
+        out.append(torch.tensor(np.ascontiguousarray(w), dtype=dtype, device=dev))
+    return out
+
+
+def _fd_best(Jf, ad, steps):
+    """Best relative agreement of central differences (J(+e) - J(-e)) / 2e with ad over steps e."""
+    best, at = float("inf"), None
+    for e in steps:
+        fd = (Jf(e) - Jf(-e)) / (2.0 * e)
+        r = abs(fd - ad) / max(abs(ad), 1e-300)
+        if r < best:
+            best, at = r, e
+    return best, at
+
+
+def gradient_legs(stream, flush):
+    """The three gradient runs of the paper's workloads at full size (§2.4.1), forward + reverse
+    through the revolve-checkpointed rollout, timed with CUDA events; each gradient checked along a
+    seeded random direction against central differences of the FP64 GPU forward (best over a scan of
+    steps), and the mixed gradient against the FP64 one.
+      isotropic 128^3, SSP-RK3, 500 steps: J = final kinetic energy, dJ/du_0
+      channel 192x129x128, forward Euler, 200 steps with 20 snapshot slots (revolve recomputation):
+        J = final kinetic energy, dJ/df_x(y) (128 values)
+      cylinder 640x320 FSI, 20000 steps: J = mean over the last 5000 steps of C_L^2, dJ/dk."""
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    from paper_2505_23940_b300.autodiff import Rollout
+    dev = torch.device("cuda")
+    out = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        r = fn()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        return r, ev[0].elapsed_time(ev[1])
+
+    # ---- isotropic turbulence 128^3, dJ/du_0 over 500 steps ----
+    wl = S.isotropic_3d(n=128)
+    n = 500
+    cells = wl.cells()
+    grads, res = {}, {}
+    for prec in ("mixed", "fp64"):
+        g = grid_from_workload(wl, prec, stream=stream)
+        g.set_tuning("y_spectral", 0)
+        dt_ = torch.float32 if prec == "mixed" else torch.float64
+        u0 = [torch.tensor(np.asarray(a), dtype=dt_, device=dev).contiguous() for a in wl.u0]
+        V = _face_weights(wl, dev, dt_)
+        ro = Rollout(g, wl.dt, n)
+
+        def run():
+            uT = ro.forward(u0)[0]
+            lam0, _ = ro.backward(u0, None, [x * v for x, v in zip(uT, V)])
+            return lam0
+        lam0, ms = timed(run)
+        grads[prec] = [x.double() for x in lam0]
+        res[prec] = {"ms": ms, "value": cells * n / (ms * 1e-3), "slots": ro.used_slots,
+                     "recorded_stages": ro.recorded, "recomputed_steps": ro.recomputed}
+        if prec == "fp64":
+            V64 = V
+            g64 = g
+        else:
+            del ro, g
+        flush.fill_(1)
+    rng = np.random.default_rng(11)
+    d = [torch.tensor(rng.uniform(-1.0, 1.0, size=np.asarray(a).shape), device=dev) for a in wl.u0]
+    u00 = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev) for a in wl.u0]
+
+    def J_iso(e):
+        u = [(a + e * b).contiguous() for a, b in zip(u00, d)]
+        g64.step(u, wl.dt, n)
+        return float(sum(0.5 * (x * x * v).sum() for x, v in zip(u, V64)))
+    ad64 = float(sum((a * b).sum() for a, b in zip(grads["fp64"], d)))
+    admx = float(sum((a * b).sum() for a, b in zip(grads["mixed"], d)))
+    fd, at = _fd_best(J_iso, ad64, (1e-5, 1e-6, 1e-7, 1e-8))
+    num = sum(float(((a - b) ** 2).sum()) for a, b in zip(grads["mixed"], grads["fp64"]))
+    den = sum(float((b ** 2).sum()) for b in grads["fp64"])
+    out["isotropic_128_500_steps"] = {
+        "value": res["mixed"]["value"], "unit": "cell-updates/s fwd+adj", "ms": res["mixed"]["ms"],
+        "fp64_value": res["fp64"]["value"], "mixed_slots": res["mixed"]["slots"],
+        "recorded_stages": res["mixed"]["recorded_stages"], "recomputed_steps": res["mixed"]["recomputed_steps"],
+        "fd_rel_err_fp64": fd, "fd_step": at,
+        "fd_rel_err_mixed": abs(admx - ad64) / abs(ad64) if fd < 1e-4 else None,
+        "mixed_vs_fp64_grad_rel_l2": (num / den) ** 0.5}
+    del g64, grads, u00, d
+    torch.cuda.empty_cache()
+
+    # ---- channel 192x129x128, dJ/df_x(y) over 200 steps with 20 snapshot slots ----
+    wl = S.channel_3d()
+    n = 200
+    cells = wl.cells()
+    gf, res = {}, {}
+    for prec in ("mixed", "fp64"):
+        g = grid_from_workload(wl, prec, stream=stream)
+        dt_ = torch.float32 if prec == "mixed" else torch.float64
+        u0 = [torch.tensor(np.asarray(a), dtype=dt_, device=dev).contiguous() for a in wl.u0]
+        V = _face_weights(wl, dev, dt_)
+        ro = Rollout(g, wl.dt, n, slots=20)
+        gfx = torch.zeros(wl.n[1], dtype=torch.float64, device=dev)
+
+        def run():
+            uT = ro.forward(u0)[0]
+            ro.backward(u0, None, [x * v for x, v in zip(uT, V)], g_body_force=gfx)
+            return gfx
+        _, ms = timed(run)
+        gf[prec] = gfx.clone()
+        res[prec] = {"ms": ms, "value": cells * n / (ms * 1e-3), "recomputed_steps": ro.recomputed}
+        if prec == "fp64":
+            g64, V64 = g, V
+        else:
+            del ro, g
+    dfx = torch.tensor(rng.uniform(-1.0, 1.0, size=wl.n[1]), device=dev)
+    fx0 = torch.tensor(np.asarray(wl.body_force), device=dev)
+    u00 = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev) for a in wl.u0]
+
+    def J_ch(e):
+        g64.set_body_force((fx0 + e * dfx).contiguous())
+        u = [a.clone() for a in u00]
+        g64.step(u, wl.dt, n)
+        return float(sum(0.5 * (x * x * v).sum() for x, v in zip(u, V64)))
+    ad64 = float((gf["fp64"] * dfx).sum())
+    admx = float((gf["mixed"] * dfx).sum())
+    fd, at = _fd_best(J_ch, ad64, (1e-2, 1e-3, 1e-4, 1e-5))
+    out["channel_200_steps"] = {
+        "value": res["mixed"]["value"], "unit": "cell-updates/s fwd+adj", "ms": res["mixed"]["ms"],
+        "fp64_value": res["fp64"]["value"], "slots": 20, "recomputed_steps": res["mixed"]["recomputed_steps"],
+        "fd_rel_err_fp64": fd, "fd_step": at, "fd_rel_err_mixed": abs(admx - ad64) / abs(ad64),
+        "mixed_vs_fp64_grad_rel_l2": float((gf["mixed"] - gf["fp64"]).norm() / gf["fp64"].norm())}
+    del g64, u00
+    torch.cuda.empty_cache()
+
+    # ---- cylinder FSI 640x320, dJ/dk over 20000 steps, J = mean of C_L^2 over the last 5000 ----
+    wl = S.cylinder_2d(seed=2, perturb=0.01)
+    n, m = 20000, 5000
+    cells = wl.cells()
+    k0 = float(wl.body.stiffness)
+    gk, res, Jv = {}, {}, {}
+    for prec in ("mixed", "fp64"):
+        g = grid_from_workload(wl, prec, stream=stream)
+        dt_ = torch.float32 if prec == "mixed" else torch.float64
+        u0 = [torch.tensor(np.asarray(a), dtype=dt_, device=dev).contiguous() for a in wl.u0]
+        b0 = body_tensor(wl)
+        ro = Rollout(g, wl.dt, n)
+        kk = torch.zeros(1, dtype=torch.float64, device=dev)
+
+        def run():
+            uT, bT, forces = ro.forward(u0, b0)
+            lamF = torch.zeros_like(forces)
+            lamF[n - m:, 1] = 8.0 * forces[n - m:, 1] / m        # J = (1/m) sum (2 F_y)^2
+            ro.backward(u0, b0, [torch.zeros_like(x) for x in uT], torch.zeros_like(bT), lamF, g_stiffness=kk)
+            return forces
+        forces, ms = timed(run)
+        Jv[prec] = float((4.0 * forces[n - m:, 1] ** 2).mean())
+        gk[prec] = float(kk[0])
+        res[prec] = {"ms": ms, "value": cells * n / (ms * 1e-3), "slots": ro.used_slots,
+                     "recomputed_steps": ro.recomputed}
+        if prec == "fp64":
+            g64 = g
+        else:
+            del ro, g
+        del forces
+
+    # central differences over 20000 steps would see the epsilon mask flip at shifted steps (the
+    # adjoint freezes it, A17); the FD pin runs the same FSI over 2000 steps, J over the last 1000
+    nf, mf = 2000, 1000
+
+    def J_cyl(e, want_grad=False):
+        g64.set_stiffness(k0 + e)
+        u = [torch.tensor(np.asarray(a), dtype=torch.float64, device=dev).contiguous() for a in wl.u0]
+        ro = Rollout(g64, wl.dt, nf, slots=None if want_grad else 2)
+        b0 = body_tensor(wl)
+        _, bT, forces = ro.forward(u, b0)
+        J = float((4.0 * forces[nf - mf:, 1] ** 2).mean())
+        if not want_grad:
+            return J
+        kk = torch.zeros(1, dtype=torch.float64, device=dev)
+        lamF = torch.zeros_like(forces)
+        lamF[nf - mf:, 1] = 8.0 * forces[nf - mf:, 1] / mf
+        ro.backward(u, b0, [torch.zeros_like(x) for x in u], torch.zeros_like(bT), lamF, g_stiffness=kk)
+        return J, float(kk[0])
+    _, gk_short = J_cyl(0.0, want_grad=True)
+    fd, at = _fd_best(J_cyl, gk_short, (1e-4 * k0, 1e-5 * k0, 1e-6 * k0, 1e-7 * k0))
+    g64.set_stiffness(k0)
+    out["cylinder_fsi_20000_steps"] = {
+        "value": res["mixed"]["value"], "unit": "cell-updates/s fwd+adj", "ms": res["mixed"]["ms"],
+        "fp64_value": res["fp64"]["value"], "J": Jv["mixed"], "dJdk": gk["mixed"], "dJdk_fp64": gk["fp64"],
+        "mixed_vs_fp64_dJdk_rel": abs(gk["mixed"] - gk["fp64"]) / abs(gk["fp64"]),
+        "fd_rel_err_fp64": fd, "fd_step": at, "fd_horizon_steps": nf,
+        "slots": res["mixed"]["slots"], "recomputed_steps": res["mixed"]["recomputed_steps"],
+        "note": "FD pin (FP64 adjoint vs central differences of the FP64 forward) over 2000 steps, J over the "
+                "last 1000; the 20000-step gradients are compared mixed vs FP64"}
+    del g64
+    torch.cuda.empty_cache()
+    return out
 
 
 def krylov_leg(wl, stream):
@@ -563,6 +843,86 @@ def krylov_leg(wl, stream):
     return out
 
 
+def support_faces(P, h, origin, ext, kind):
+    """Number of distinct grid nodes of one face family (node k of direction d at origin[d] + k h[d],
+    ext[d] nodes) in the union of the markers' delta-kernel supports (the nodes an IB kernel must
+    read once): P (nm, d) marker positions."""
+    width = 4 if kind == S.PESKIN4 else 3
+    d = P.shape[1]
+    first = []
+    for a in range(d):
+        sx = (P[:, a] - origin[a]) / h[a]
+        first.append((np.floor(sx) - 1 if kind == S.PESKIN4 else np.floor(sx + 0.5) - 1).astype(np.int64))
+    mask = np.zeros(int(np.prod(ext)), dtype=bool)
+    offs = np.stack(np.meshgrid(*[np.arange(width)] * d, indexing="ij"), -1).reshape(-1, d)
+    for o in offs:
+        idx = [first[a] + o[a] for a in range(d)]
+        ok = np.ones(P.shape[0], dtype=bool)
+        for a in range(d):
+            ok &= (idx[a] >= 0) & (idx[a] < ext[a])
+        flat = np.zeros(int(ok.sum()), dtype=np.int64)
+        stride = 1
+        for a in range(d):
+            flat += idx[a][ok] * stride
+            stride *= ext[a]
+        mask[flat] = True
+    return int(mask.sum())
+
+
+def ib2_stress_leg(stream, flush):
+    """Moving 2-D immersed boundary at scale: a 12 x 116 array of cylinders (D = 24 cells, 75
+    markers each: 104,400 markers, 1392 closed contours) moving as one elastically mounted body on a
+    5760 x 624 grid, mixed precision, forward Euler.  Per IB kernel: time per launch and compulsory
+    DRAM bytes (each array the kernel must touch, read or written once), hence achieved GB/s."""
+    from paper_2505_23940_b300 import body_tensor, grid_from_workload
+    dev = torch.device("cuda")
+    wl = S.cylinder_array_2d()
+    wl.body.w0 = (0.0, 0.01)
+    nm = wl.body.X0.size
+    nx, ny = wl.n[0], wl.n[1]
+    h = wl.xf[0][1] - wl.xf[0][0]
+    g = grid_from_workload(wl, "mixed", stream=stream)
+    u = [torch.tensor(np.asarray(a), dtype=torch.float32, device=dev).contiguous() for a in wl.u0]
+    body = body_tensor(wl)
+    for _ in range(2):
+        g.step(u, wl.dt, 1, body=body)
+    steps = 5
+    ms = timed_steps(g, u, wl.dt, steps, flush, stream, body=body)
+    prof = kernel_times(g, u, wl.dt, 2, flush, stream, "", body=body)
+    peak = measured_peaks().get("hbm_gbs", 6400.0)
+    # compulsory bytes per launch
+    faces = (nx + 1) * ny + nx * (ny + 1)
+    P = np.stack([wl.body.X0, wl.body.Y0 + wl.body.w0[1]], 1)
+    x0 = wl.xf[0][0]
+    sup = [support_faces(P, (h, h), (x0, x0 + 0.5 * h), (nx + 1, ny), wl.kernel),
+           support_faces(P, (h, h), (x0 + 0.5 * h, x0), (nx, ny + 1), wl.kernel)]
+    nib = int(g.ib_face_count())
+    byt = {
+        "classify_solid": faces * 1.0,                          # the flags written
+        "classify_ib": faces * 1.0 + nib * (1.0 + 4.0),         # flags read, IB bits and the list written
+        "ib_fn": sum(sup) * 1.0 + nm * (16.0 + 16.0),           # support flags, marker x, y, F_N out
+        "ib_gather": nib * (4.0 + 8.0) + nm * (24.0 + 16.0),    # list, num/den out; markers x, y, ds, F_N
+        "ib_force": sum(sup) * 4.0 + nm * (24.0 + 16.0),        # f on the supports; markers, q out
+    }
+    kern = {}
+    for k, b in byt.items():
+        if k not in prof:
+            continue
+        cnt, tot = prof[k]
+        us = tot / cnt * 1e3
+        kern[k] = {"us": us, "bytes": b, "GBs": b / (us * 1e-6) / 1e9, "frac": b / (us * 1e-6) / 1e9 / peak}
+    out = {"n": [nx, ny], "cells": nx * ny, "markers": nm, "contours": len(wl.body.contours), "ib_faces": nib,
+           "ms_per_step": sum(ms) / steps, "value": nx * ny * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
+           "markers_per_s_gather": nm / (kern["ib_gather"]["us"] * 1e-6) if "ib_gather" in kern else None,
+           "ib_kernels": kern, "peak_GBs": peak,
+           "kernels_ms_per_step": {k: v[1] / 2 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+           "note": "compulsory bytes per launch: every array a kernel must touch, read or written once; the "
+                   "support sets are the distinct faces within the markers' kernel supports"}
+    del g, u
+    torch.cuda.empty_cache()
+    return out
+
+
 def ib_stress_leg(stream, flush):
     """Static 3-D immersed boxes at scale: 256^3 rough-wall channel (cubes of 8 cells every 12 cells
     on both walls, markers every h/2: about 1.35 M markers), mixed precision, forward Euler."""
@@ -587,15 +947,26 @@ def ib_stress_leg(stream, flush):
     prof = kernel_times(g, u, wl.dt, 2, flush, stream, "")
     cnt, tot = prof["ib3_force_gather"]
     gather_us = tot / cnt * 1e3
-    # algorithmic bytes of the gather: 27 four-byte reads of f per marker and component (3-point
-    # kernel), the marker position and volume (32 B) and q (24 B) per marker
-    gbytes = nm * (3 * 27 * 4 + 32 + 24)
+    # compulsory bytes of the gather: f (FP32) once on every face within some marker's kernel support
+    # (neighbouring markers share most of them), the marker position and volume (32 B) and q (24 B)
+    h = 2.0 / 256
+    sup = 0
+    for c in range(3):
+        origin = [wl.xf[d][0] + (0.0 if d == c else 0.5 * h) for d in range(3)]
+        ext = [256, 256, 256]
+        if c == 1:
+            ext[1] = 257
+        sup += support_faces(wl.boxes.X, (h, h, h), origin, ext, wl.kernel)
+    gbytes = sup * 4.0 + nm * (32 + 24)
+    peak = measured_peaks().get("hbm_gbs", 6400.0)
     F = g.box_forces()
     out = {"n": [256, 256, 256], "cells": 256 ** 3, "markers": nm, "boxes": int(wl.boxes.boxes.shape[0]),
            "classify_ms": classify_ms, "ms_per_step": sum(ms) / steps,
            "value": 256 ** 3 * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
            "force_gather_us": gather_us, "force_gather_markers_per_s": nm / (gather_us * 1e-6),
+           "force_gather_bytes": gbytes, "support_faces": sup,
            "force_gather_GBs": gbytes / (gather_us * 1e-6) / 1e9,
+           "force_gather_frac": gbytes / (gather_us * 1e-6) / 1e9 / peak,
            "kernels_ms_per_step": {k: v[1] / 2 for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
            "F": list(F)}
     del g, u
@@ -664,6 +1035,49 @@ def sweep_leg(spec, stream, flush):
     return out
 
 
+def summary_of(line):
+    """The headline numbers of every leg in a few hundred bytes, printed last in the JSON line so
+    that a truncated tail of the output still shows them."""
+    def r(v, d=3):
+        return None if v is None else float("%.*g" % (d, v))
+
+    out = {"fwd": r(line.get("value")), "ms_step": r(line.get("ms_per_step")),
+           "ysolve_frac": r((line.get("roofline") or {}).get("frac")),
+           "stencil_frac": r((line.get("stencil_roofline") or {}).get("frac"))}
+    if "spectral_y" in line:
+        out["spectral_y"] = r(line["spectral_y"]["value"])
+    if "fp64_gpu" in line:
+        out["fp64"] = r(line["fp64_gpu"]["value"])
+        out["mixed_vs_fp64_l2"] = r(line["fp64_gpu"]["mixed_vs_fp64_rel_l2_after_10_steps"], 2)
+    if "e2e" in line:
+        out["e2e"] = r(line["e2e"]["value"])
+    if "fwd_adj" in line:
+        fa = line["fwd_adj"]
+        out["fwd_adj"] = r(fa["value"])
+        out["fwd_adj_fp64"] = r(fa["fp64_gpu"]["value"])
+        out["grad_mixed_vs_fp64"] = r(fa["fp64_gpu"]["mixed_vs_fp64_grad_rel_l2"], 2)
+    line = {k: v for k, v in line.items() if not (isinstance(v, dict) and "error" in v)}
+    for k, v in (line.get("gradients") or {}).items():
+        out["grad_" + k] = {"v": r(v["value"]), "v64": r(v["fp64_value"]), "fd64": r(v["fd_rel_err_fp64"], 2),
+                            "mx": r(v.get("fd_rel_err_mixed", v.get("mixed_vs_fp64_dJdk_rel")), 2)}
+    if "ensemble" in line:
+        e = line["ensemble"]
+        out["ensemble"] = {"graph": r(e["graph"]["value"]), "one_by_one": r(e["one_by_one"]["value"]),
+                           "speedup": r(e["speedup"]), "fa_graph": r(e["fwd_adj"]["graph"]["value"]),
+                           "fa_one_by_one": r(e["fwd_adj"]["one_by_one"]["value"]),
+                           "fa_speedup": r(e["fwd_adj"]["speedup"])}
+    if "krylov" in line:
+        out["cg_ms"] = r(line["krylov"]["cg"]["ms"])
+    if "ib_stress" in line:
+        out["ib3_gather_frac"] = r(line["ib_stress"].get("force_gather_frac"))
+    if "ib2_stress" in line:
+        out["ib2"] = {k: r(v["frac"]) for k, v in line["ib2_stress"]["ib_kernels"].items()}
+        out["ib2_ms_step"] = r(line["ib2_stress"]["ms_per_step"])
+    if "cpu_baseline" in line:
+        out["cpu"] = r(line["cpu_baseline"]["value"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -674,12 +1088,16 @@ def main():
     ap.add_argument("--y-solve", default="fp64", choices=["fp64", "spectral"],
                     help="periodic y: FP64 cyclic tridiagonal (the FP64 Poisson of the 128^3 configuration) "
                          "or the FP32 DFT (also reported as the spectral_y leg)")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="precision of the timed forward steps (fp64 implies --quick)")
     ap.add_argument("--cpu-steps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="timed forward steps only (for profiler runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="members of the batched-ensemble leg (0: skip)")
     ap.add_argument("--sweep", default="256,384,512,4096x4096",
                     help="comma-separated out-of-L2 grids: n for n^3, AxB for a 2-D A x B box ('' to skip)")
     ap.add_argument("--ib-stress", type=int, default=1, help="run the 256^3 static-box leg (0: skip)")
+    ap.add_argument("--gradients", type=int, default=1,
+                    help="run the full-size gradient legs (isotropic 500 steps, channel 200, cylinder 20000; 0: skip)")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

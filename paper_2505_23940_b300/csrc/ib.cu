@@ -262,45 +262,6 @@ struct IBGeom {
   double hfx;              // uniform x spacing
 };
 
-// first support node along one direction for marker coordinate X
-__device__ __forceinline__ int first_node(const IBGeom& G, double X, double x0, double h) {
-  const double s = (X - x0) / h;
-  return G.kind == FS_PESKIN4 ? (int)floor(s) - 1 : (int)floor(s + 0.5) - 1;
-}
-
-__device__ __forceinline__ double node_x(const IBGeom& G, int c, int i) {
-  return c == 0 ? G.xf[i] : __dmul_rn(0.5, __dadd_rn(G.xf[i], G.xf[i + 1]));
-}
-__device__ __forceinline__ double node_y(const IBGeom& G, int c, int j) {
-  return c == 1 ? G.yf[j] : __dmul_rn(0.5, __dadd_rn(G.yf[j], G.yf[j + 1]));
-}
-
-// Support node of one lane: 16 lanes per (marker, component) pair, lane l -> node
-// (a, b) = (l mod width, l / width); lanes with b >= width hold no node.
-struct Lane {
-  int pair, m, c, a, b;
-  bool live;
-};
-
-__device__ __forceinline__ Lane lane_of(const IBGeom& G, int nm) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  Lane L;
-  L.pair = t >> 4;
-  const int l = t & 15;
-  L.m = L.pair >> 1;
-  L.c = L.pair & 1;
-  L.a = l % G.width;
-  L.b = l / G.width;
-  L.live = L.pair < 2 * nm;
-  return L;
-}
-
-__device__ __forceinline__ double sum16(double s) {
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
 // Markers in grid units.  A marker's rest position in cell units from the grid origin,
 // g = (X0 - x0) / h, is held as an integer part gi = floor(g) and a fraction gf in [0, 1)
 // (host-computed in FP64 when the body is attached, gf stored in the field precision T);
@@ -338,34 +299,55 @@ __device__ __forceinline__ int first_node_units(int kind, int gi, T gf, int wi, 
   return kind == FS_PESKIN4 ? sint - 1 : sint + (int)floor(sfr + T(0.5)) - 1;
 }
 
-// F_N_i of Eq. (19): the 16 lanes of a (marker, component) pair evaluate delta_h at their
-// support node and sum it over the nodes that are not solid by shuffles; the pair's first lane
-// stores the interpolation weight factor of Eq. (18), wfac = dV_i / (F_N_i h_x h_y) (then
-// w_i(x) = phi phi wfac), with dsh = dV_i = ds_i h_x.
-template <typename T>
-__global__ void ib_fn_kernel(const IBGeom G, int nm, const int2* __restrict__ gi, const T* __restrict__ gf,
-                             const T* __restrict__ dsh, const double* __restrict__ body, const Flags flags,
-                             T* __restrict__ wfac) {
+// The W x W support of a (marker, component) pair: first nodes (i0, j0) and the 1-D kernel
+// weights of its W columns (px) and W rows (py), in the field precision.
+template <typename T, int W>
+__device__ __forceinline__ void support_of(const IBGeom& G, const Shift<T>& S, int2 mi, T gfx, T gfy, int c, int& i0,
+                                           int& j0, T (&px)[W], T (&py)[W]) {
+  int sx, sy;
+  T fx, fy;
+  i0 = first_node_units<T>(G.kind, mi.x, gfx, S.wi[0], S.wf[0], c ? T(0.5) : T(0), sx, fx);
+  j0 = first_node_units<T>(G.kind, mi.y, gfy, S.wi[1], S.wf[1], c ? T(0) : T(0.5), sy, fy);
+#pragma unroll
+  for (int a = 0; a < W; ++a) {
+    px[a] = phi_kernel<T>(G.kind, T(i0 + a - sx) - fx);
+    py[a] = phi_kernel<T>(G.kind, T(j0 + a - sy) - fy);
+  }
+}
+
+// F_N_i of Eq. (19), one thread per (marker, component): delta_h summed over the support nodes
+// that are not solid; stores the interpolation weight factor of Eq. (18),
+// wfac = dV_i / (F_N_i h_x h_y) (then w_i(x) = phi phi wfac), with dsh = dV_i = ds_i h_x.
+template <typename T, int W>
+__global__ void __launch_bounds__(kT) ib_fn_kernel(const IBGeom G, int nm, const int2* __restrict__ gi,
+                                                   const T* __restrict__ gf, const T* __restrict__ dsh,
+                                                   const double* __restrict__ body, const Flags flags,
+                                                   T* __restrict__ wfac) {
   __shared__ Shift<T> S;
   if (threadIdx.x == 0) S = shift_of<T>(body, G.ihx, G.ihy);
   __syncthreads();
-  const Lane L = lane_of(G, nm);
+  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pair >= 2 * nm) return;
+  const int m = pair >> 1, c = pair & 1;
+  int i0, j0;
+  T px[W], py[W];
+  support_of<T, W>(G, S, gi[m], gf[2 * m], gf[2 * m + 1], c, i0, j0, px, py);
+  const uint8_t* fl = c ? flags.p[1] : flags.p[0];
+  const int ex = G.ex[c], ey = G.ey[c];
   T s = T(0);
-  if (L.live && L.b < G.width) {
-    const int c = L.c;
-    const int2 mi = gi[L.m];
-    int sx, sy;
-    T fx, fy;
-    const int i = first_node_units<T>(G.kind, mi.x, gf[2 * L.m], S.wi[0], S.wf[0], c ? T(0.5) : T(0), sx, fx) + L.a;
-    const int j = first_node_units<T>(G.kind, mi.y, gf[2 * L.m + 1], S.wi[1], S.wf[1], c ? T(0) : T(0.5), sy, fy) + L.b;
-    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c]) {
-      const uint8_t fl = (c ? flags.p[1] : flags.p[0])[(size_t)j * G.ex[c] + i];
-      if (!(fl & 1)) s = phi_kernel<T>(G.kind, T(i - sx) - fx) * phi_kernel<T>(G.kind, T(j - sy) - fy);
-    }
-  }
 #pragma unroll
-  for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (L.live && (threadIdx.x & 15) == 0) wfac[L.pair] = s > T(0) ? dsh[L.m] / s : T(0);
+  for (int b = 0; b < W; ++b) {
+    const int j = j0 + b;
+    if (j < 0 || j >= ey) continue;
+    T r = T(0);
+#pragma unroll
+    for (int a = 0; a < W; ++a) {
+      const int i = i0 + a;
+      if (i >= 0 && i < ex && !(fl[(size_t)j * ex + i] & 1)) r += px[a];   // solid nodes are left out of F_N
+    }
+    s += r * py[b];
+  }
+  wfac[pair] = s > T(0) ? dsh[m] / s : T(0);
 }
 
 // Marker bins of the rest positions (see IBDev): markers of cell (ci, cj) are the sorted
@@ -522,71 +504,64 @@ struct BodyODE {
   int ax, ay;
 };
 
-// q_i = - sum_x f(x) delta_h(x - X_i) dv(x)   (Eq. 20), 16 lanes per marker and
-// component; then F = rho sum_i q_i dV_i and the torque rho sum_i dV_i (r_i x q_i): each
-// block sums its markers' terms (a fixed tree) into its slot of part, and the block that
-// finishes last (the others publish their slot before taking a ticket; no block waits) sums
-// the slots in a fixed order and, when asked, takes the body ODE step with that force.
-template <typename T>
+// q_i = - sum_x f(x) delta_h(x - X_i) dv(x)   (Eq. 20), one thread per (marker, component), in
+// the field precision (the grid is uniform near the body, so dv / (h_x h_y) = 1); then
+// F = rho sum_i q_i dV_i and the torque rho sum_i dV_i (r_i x q_i) in FP64: each block sums its
+// pairs' terms in a fixed tree into its slot of part, and the block that finishes last (the others
+// publish their slot before taking a ticket; no block waits) sums the slots in a fixed order and,
+// when asked, takes the body ODE step with that force.
+template <typename T, int W>
 __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const int2* __restrict__ gi,
-                                                   const T* __restrict__ gf, const double* __restrict__ X0,
-                                                   const double* __restrict__ Y0, const double* __restrict__ ds,
-                                                   const double* body, const T* __restrict__ f0,
-                                                   const T* __restrict__ f1, double cx, double cy, double rho,
+                                                   const T* __restrict__ gf, const T* __restrict__ rel,
+                                                   const T* __restrict__ dsh, const double* body,
+                                                   const T* __restrict__ f0, const T* __restrict__ f1, double rho,
                                                    double* __restrict__ q, double* __restrict__ part,
                                                    double* __restrict__ F, unsigned* __restrict__ ticket,
                                                    const BodyODE ode) {
   __shared__ Shift<T> S;
+  __shared__ double s0[kT / 32], s1[kT / 32], s2[kT / 32];
+  __shared__ bool last;
   if (threadIdx.x == 0) S = shift_of<T>(body, G.ihx, G.ihy);
   __syncthreads();
-  const Lane L = lane_of(G, nm);
-  // per node: f delta_h dv in the field precision (the grid is uniform near the body, so dv / (h_x h_y)
-  // is 1); the 16 lanes' sum, q_i, in FP64
-  T sp = T(0);
-  if (L.live && L.b < G.width) {
-    const int c = L.c;
-    const T* f = c == 0 ? f0 : f1;
-    const int2 mi = gi[L.m];
-    int sx, sy;
-    T fx, fy;
-    const int i = first_node_units<T>(G.kind, mi.x, gf[2 * L.m], S.wi[0], S.wf[0], c ? T(0.5) : T(0), sx, fx) + L.a;
-    const int j = first_node_units<T>(G.kind, mi.y, gf[2 * L.m + 1], S.wi[1], S.wf[1], c ? T(0) : T(0.5), sy, fy) + L.b;
-    if (i >= 0 && i < G.ex[c] && j >= 0 && j < G.ey[c])
-      sp = f[(size_t)j * G.ex[c] + i] * (phi_kernel<T>(G.kind, T(i - sx) - fx) * phi_kernel<T>(G.kind, T(j - sy) - fy));
-  }
-#pragma unroll
-  for (int o = 8; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-  const double s = (double)sp;
-  double X = 0.0, Y = 0.0;
-  if (L.live && (threadIdx.x & 15) == 0) {
-    X = X0[L.m] + body[0];
-    Y = Y0[L.m] + body[1];
-  }
-  // this pair's terms of F and the torque (held by the pair's first lane): only those lanes add,
-  // the two pair leaders of a warp by one shuffle, then one thread per block over its warps
-  __shared__ double s0[kT / 32], s1[kT / 32], s2[kT / 32];
+  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
   double a = 0.0, b = 0.0, tq = 0.0;
-  if (L.live && (threadIdx.x & 15) == 0) {
-    const double qv = -s;
-    q[L.pair] = qv;
-    const double dV = ds[L.m] * G.hx;
-    const double rx = X - (cx + body[0]), ry = Y - (cy + body[1]);
-    if (L.c == 0) {
-      a = qv * dV;
-      tq = -dV * ry * qv;
-    } else {
-      b = qv * dV;
-      tq = dV * rx * qv;
+  if (pair < 2 * nm) {
+    const int m = pair >> 1, c = pair & 1;
+    int i0, j0;
+    T px[W], py[W];
+    support_of<T, W>(G, S, gi[m], gf[2 * m], gf[2 * m + 1], c, i0, j0, px, py);
+    const T* f = c ? f1 : f0;
+    const int ex = G.ex[c], ey = G.ey[c];
+    T sum = T(0);
+#pragma unroll
+    for (int bb = 0; bb < W; ++bb) {
+      const int j = j0 + bb;
+      if (j < 0 || j >= ey) continue;
+      T r = T(0);
+#pragma unroll
+      for (int aa = 0; aa < W; ++aa) {
+        const int i = i0 + aa;
+        if (i >= 0 && i < ex) r += f[(size_t)j * ex + i] * px[aa];
+      }
+      sum += r * py[bb];
     }
+    const T qv = -sum;
+    q[pair] = (double)qv;
+    // this pair's terms of F and of the torque (r = rest position - centre: the body only translates)
+    const T dV = dsh[m];
+    const T t = c == 0 ? -dV * rel[2 * m + 1] * qv : dV * rel[2 * m] * qv;
+    (c == 0 ? a : b) = (double)(qv * dV);
+    tq = (double)t;
   }
-  {
-    const double a2 = __shfl_down_sync(0xffffffffu, a, 16), b2 = __shfl_down_sync(0xffffffffu, b, 16),
-                 t2 = __shfl_down_sync(0xffffffffu, tq, 16);
-    if ((threadIdx.x & 31) == 0) {
-      s0[threadIdx.x >> 5] = a + a2;
-      s1[threadIdx.x >> 5] = b + b2;
-      s2[threadIdx.x >> 5] = tq + t2;
-    }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    tq += __shfl_down_sync(0xffffffffu, tq, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s0[threadIdx.x >> 5] = a;
+    s1[threadIdx.x >> 5] = b;
+    s2[threadIdx.x >> 5] = tq;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -601,8 +576,6 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
     part[3 * blockIdx.x + 2] = st;
   }
   // the last block to finish reduces the block sums
-  __shared__ bool last;
-  __shared__ double r0[kT], r1[kT], r2[kT];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
@@ -615,22 +588,28 @@ __global__ void __launch_bounds__(kT) force_kernel(const IBGeom G, int nm, const
     b += __ldcg(part + 3 * k + 1);
     tq += __ldcg(part + 3 * k + 2);
   }
-  r0[threadIdx.x] = a;
-  r1[threadIdx.x] = b;
-  r2[threadIdx.x] = tq;
-  __syncthreads();
-  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) {
-      r0[threadIdx.x] += r0[threadIdx.x + o];
-      r1[threadIdx.x] += r1[threadIdx.x + o];
-      r2[threadIdx.x] += r2[threadIdx.x + o];
-    }
-    __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    tq += __shfl_down_sync(0xffffffffu, tq, o);
   }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+    s0[threadIdx.x >> 5] = a;
+    s1[threadIdx.x >> 5] = b;
+    s2[threadIdx.x >> 5] = tq;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    F[0] = rho * r0[0];
-    F[1] = rho * r1[0];
-    F[2] = rho * r2[0];
+    double sa = 0.0, sb = 0.0, st = 0.0;
+    for (int w = 0; w < kT / 32; ++w) {
+      sa += s0[w];
+      sb += s1[w];
+      st += s2[w];
+    }
+    F[0] = rho * sa;
+    F[1] = rho * sb;
+    F[2] = rho * st;
     *ticket = 0u;
     if (ode.st) rk4_body(ode.st, F, ode.m, ode.k, ode.c, ode.ax, ode.ay, ode.dt);
   }
@@ -699,9 +678,15 @@ void ib_prepare(fs_grid* G, const double* body_state) {
                                     dflags, ex[0], ey[0], ex[1], ey[1], G->per[0], G->per[1], B.iblist, B.ibcount));
   }
   const IBGeom g = make_geom(G);
-  const int nlane = 2 * B.nm * 16;
-  FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
-                            g, B.nm, B.gi, (const T*)B.gf, (const T*)B.dsh, body_state, dflags, (T*)B.wfac));
+  const int npb = (2 * B.nm + kT - 1) / kT;
+  if (g.width == 4)
+    FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T, 4><<<npb, kT, 0, G->stream>>>(g, B.nm, B.gi, (const T*)B.gf,
+                                                                          (const T*)B.dsh, body_state, dflags,
+                                                                          (T*)B.wfac));
+  else
+    FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T, 3><<<npb, kT, 0, G->stream>>>(g, B.nm, B.gi, (const T*)B.gf,
+                                                                          (const T*)B.dsh, body_state, dflags,
+                                                                          (T*)B.wfac));
   Bins bn{B.bin_start, B.bx0, B.by0, B.nbx, B.nby, G->xf[0][0], G->xf[1][0]};
   // IB faces: about two per marker and component.  Small bodies take a warp per face (the candidate
   // markers' loads all in flight: latency), large ones a thread per face (throughput); the kernel
@@ -722,12 +707,17 @@ template <typename T>
 void ib_forces(fs_grid* G, double* body_state, double* advance, double dt) {
   IBDev& B = G->ib;
   const IBGeom g = make_geom(G);
-  const int nlane = 2 * B.nm * 16;
   BodyODE ode{nullptr, B.mass, B.k, B.c, dt, B.active[0], B.active[1]};
   if (advance && B.mass > 0) ode.st = advance;
-  FS_LAUNCH(G, "ib_force", force_kernel<T><<<(nlane + kT - 1) / kT, kT, 0, G->stream>>>(
-                               g, B.nm, B.gi, (const T*)B.gf, B.X0, B.Y0, B.ds, body_state, (const T*)B.f[0],
-                               (const T*)B.f[1], B.centre[0], B.centre[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
+  const int npb = (2 * B.nm + kT - 1) / kT;
+  if (g.width == 4)
+    FS_LAUNCH(G, "ib_force", force_kernel<T, 4><<<npb, kT, 0, G->stream>>>(
+                                 g, B.nm, B.gi, (const T*)B.gf, (const T*)B.rel, (const T*)B.dsh, body_state,
+                                 (const T*)B.f[0], (const T*)B.f[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
+  else
+    FS_LAUNCH(G, "ib_force", force_kernel<T, 3><<<npb, kT, 0, G->stream>>>(
+                                 g, B.nm, B.gi, (const T*)B.gf, (const T*)B.rel, (const T*)B.dsh, body_state,
+                                 (const T*)B.f[0], (const T*)B.f[1], G->rho, B.q, B.part, B.F, B.ticket, ode));
   B.have_forces = true;
 }
 

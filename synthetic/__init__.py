@@ -303,7 +303,10 @@ def ensemble_cylinders(members=64, seed=2, steps=500, precision="mixed", kmin=12
     """Members of the batched-ensemble workload: 2-D cylinder flows (16 D x 8 D boxes) with
     nx drawn uniformly from the multiples of 32 in [kmin, kmax], ny = nx / 2, D = nx / 16
     cells, Re uniform in [50, 200], 1 % seeded noise on the initial cross-flow velocity,
-    elastically mounted (m* = 2, U_r = 5) as in the FSI workload, dt = 0.2 h."""
+    elastically mounted (m* = 2, U_r = 5) as in the FSI workload.  dt = min(0.2 h, 0.6 / Re) (D = U = 1):
+    0.2 h keeps the advective CFL number at 0.2, and forward Euler with central convection also
+    needs dt < 2 nu / |u|^2 (|u| up to about 1.5 U near the cylinder), which 0.2 h breaks on the
+    coarse, high-Re members (those diverged within 500 steps)."""
     rng = np.random.default_rng(seed)
     sizes = np.arange(kmin, kmax + 1, 32)
     out = []
@@ -312,7 +315,7 @@ def ensemble_cylinders(members=64, seed=2, steps=500, precision="mixed", kmin=12
         re = float(rng.uniform(50.0, 200.0))
         cpd = nx // 16
         nm = int(round(math.pi * cpd))
-        wl = cylinder_2d(nx=nx, ny=nx // 2, cells_per_d=cpd, nm=nm, re=re, dt=0.2 / cpd, steps=steps,
+        wl = cylinder_2d(nx=nx, ny=nx // 2, cells_per_d=cpd, nm=nm, re=re, dt=min(0.2 / cpd, 0.6 / re), steps=steps,
                          precision=precision, seed=int(seed * 1000 + m), perturb=0.01)
         wl.name = "cylinder_2d_member_%d" % m
         out.append(wl)
