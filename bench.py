@@ -51,7 +51,7 @@ KERNEL_BYTES_PER_CELL = {
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50362880 + 839680, "src": "9d68f8187082"},
-    "ysolve": {"bytes": 27197184 + 0, "src": "62755ef9a23c"},
+    "ysolve": {"bytes": 26267392 + 0, "src": "f6da4e81d3a5"},
     "fft_x_fwd_div": {"bytes": 25243392 + 0, "src": "7895d4f893d7"},
     "fft_z_fwd": {"bytes": 8407040 + 0, "src": "7895d4f893d7"},
     "fft_y_solve": {"bytes": 8435200 + 0, "src": "7895d4f893d7"},
@@ -899,10 +899,10 @@ def ib2_stress_leg(stream, flush):
     nib = int(g.ib_face_count())
     byt = {
         "classify_solid": faces * 1.0,                          # the flags written
-        "classify_ib": faces * 1.0 + nib * (1.0 + 4.0),         # flags read, IB bits and the list written
-        "ib_fn": sum(sup) * 1.0 + nm * (16.0 + 16.0),           # support flags, marker x, y, F_N out
-        "ib_gather": nib * (4.0 + 8.0) + nm * (24.0 + 16.0),    # list, num/den out; markers x, y, ds, F_N
-        "ib_force": sum(sup) * 4.0 + nm * (24.0 + 16.0),        # f on the supports; markers, q out
+        # flags read, IB bits and the list written; F_N: support flags, marker cell and fraction, wfac out
+        "classify_ib_fn": faces * 1.0 + nib * (1.0 + 4.0) + sum(sup) * 1.0 + nm * (8.0 + 8.0 + 4.0 + 8.0),
+        "ib_gather": nib * (4.0 + 8.0) + nm * (8.0 + 8.0 + 8.0),   # list, num/den out; marker cell, fraction, wfac
+        "ib_force": sum(sup) * 4.0 + nm * (8.0 + 8.0 + 8.0 + 4.0 + 16.0),   # f on the supports; markers, q out
     }
     kern = {}
     for k, b in byt.items():
