@@ -92,11 +92,13 @@ struct Flags {
 __global__ void __launch_bounds__(kT) classify_solid_kernel(Flags flags, int ex0, int ey0, int ex1, int ey1,
                                                              const double* __restrict__ xf,
                                                              const double* __restrict__ yf,
-                                                             const double* __restrict__ body, Poly P) {
+                                                             const double* __restrict__ body, Poly P,
+                                                             unsigned* __restrict__ ibcount) {
   __shared__ double xs[kRowCross];
   __shared__ int xi[kRowCross];
   __shared__ int cnt, elo, ehi;
   const int c = blockIdx.y, j = blockIdx.x;
+  if (j == 0 && c == 0 && threadIdx.x == 0) *ibcount = 0u;   // the step's IB face list starts empty
   const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
   if (j >= ey) return;
   uint8_t* row = (c ? flags.p[1] : flags.p[0]) + (size_t)j * ex;
@@ -206,19 +208,27 @@ __device__ __forceinline__ bool ib_face(uint8_t* __restrict__ flags, long long t
   return nb;
 }
 
-// grid (blocks, 2 components); the IB faces are appended to list as (index << 1) | component
-// (the list's order varies from run to run; nothing computed from it depends on the order)
-__global__ void classify_ib_kernel(Flags F, int ex0, int ey0, int ex1, int ey1, int perx, int pery,
-                                   unsigned* __restrict__ list, unsigned* __restrict__ count) {
-  const int c = blockIdx.y;
+// Block bx of nbx of the IB classification of component c; the IB faces are appended to list as
+// (index << 1) | component (the list's order varies from run to run; nothing computed from it
+// depends on the order)
+// Only faces of the index box ilo..ihi x jlo..jhi (the body's displaced bounding box plus two faces)
+// can be solid or next to a solid face.
+__device__ __forceinline__ void classify_ib_block(Flags F, int ex0, int ey0, int ex1, int ey1, int perx, int pery,
+                                                  unsigned* __restrict__ list, unsigned* __restrict__ count, int c,
+                                                  int bx, int nbx, int ilo, int ihi, int jlo, int jhi) {
   const int ex = c ? ex1 : ex0, ey = c ? ey1 : ey0;
   uint8_t* __restrict__ flags = c ? F.p[1] : F.p[0];
-  const long long total = (long long)ex * ey;
-  const long long span = (long long)gridDim.x * blockDim.x;
-  for (long long t0 = (long long)blockIdx.x * blockDim.x; t0 < total; t0 += span) {
-    const long long t = t0 + threadIdx.x;
+  // (a periodic direction is visited whole: IB faces may sit across its seam)
+  const int i0 = perx ? 0 : max(ilo, 0), i1 = perx ? ex - 1 : min(ihi, ex - 1);
+  const int j0 = pery ? 0 : max(jlo, 0), j1 = pery ? ey - 1 : min(jhi, ey - 1);
+  const int w = i1 - i0 + 1;
+  const long long total = (w > 0 && j1 >= j0) ? (long long)w * (j1 - j0 + 1) : 0;
+  const long long span = (long long)nbx * blockDim.x;
+  for (long long t0 = (long long)bx * blockDim.x; t0 < total; t0 += span) {
+    const long long tl = t0 + threadIdx.x;
+    const long long t = tl < total ? (long long)(j0 + tl / w) * ex + (i0 + tl % w) : 0;
     bool isib = false;
-    if (t < total) isib = ib_face(flags, t, ex, ey, perx, pery);
+    if (tl < total) isib = ib_face(flags, t, ex, ey, perx, pery);
     // warp-aggregated append
     const unsigned m = __ballot_sync(0xffffffffu, isib);
     if (m) {
@@ -230,7 +240,6 @@ __global__ void classify_ib_kernel(Flags F, int ex0, int ey0, int ex1, int ey1, 
     }
   }
 }
-
 
 template <typename T>
 __device__ __forceinline__ T phi_kernel(int kind, T r) {
@@ -315,18 +324,43 @@ __device__ __forceinline__ void support_of(const IBGeom& G, const Shift<T>& S, i
   }
 }
 
+// the rest polygon's bounding box: xmin, xmax, ymin, ymax
+struct Box4 {
+  double v[4];
+  __host__ __device__ double operator[](int i) const { return v[i]; }
+};
+
 // F_N_i of Eq. (19), one thread per (marker, component): delta_h summed over the support nodes
 // that are not solid; stores the interpolation weight factor of Eq. (18),
 // wfac = dV_i / (F_N_i h_x h_y) (then w_i(x) = phi phi wfac), with dsh = dV_i = ds_i h_x.
+// F_N needs only the solid faces, so it runs in the same launch as the IB classification: blocks
+// [0, 2 nbc) classify (component = block / nbc), the rest take F_N.
 template <typename T, int W>
-__global__ void __launch_bounds__(kT) ib_fn_kernel(const IBGeom G, int nm, const int2* __restrict__ gi,
-                                                   const T* __restrict__ gf, const T* __restrict__ dsh,
-                                                   const double* __restrict__ body, const Flags flags,
-                                                   T* __restrict__ wfac) {
+__global__ void __launch_bounds__(kT) ib_classify_fn_kernel(Flags flags, int ex0, int ey0, int ex1, int ey1,
+                                                            int perx, int pery, unsigned* __restrict__ list,
+                                                            unsigned* __restrict__ count, int nbc, const IBGeom G,
+                                                            int nm, const int2* __restrict__ gi,
+                                                            const T* __restrict__ gf, const T* __restrict__ dsh,
+                                                            const double* __restrict__ body, T* __restrict__ wfac,
+                                                            const Box4 bbox) {
+  if ((int)blockIdx.x < 2 * nbc) {
+    // the displaced bounding box in face indices (uniform spacing near the body), with a margin
+    __shared__ int box[4];
+    if (threadIdx.x == 0) {
+      box[0] = (int)floor((bbox[0] + body[0] - G.xf[0]) * G.ihx) - 2;
+      box[1] = (int)ceil((bbox[1] + body[0] - G.xf[0]) * G.ihx) + 2;
+      box[2] = (int)floor((bbox[2] + body[1] - G.yf[0]) * G.ihy) - 2;
+      box[3] = (int)ceil((bbox[3] + body[1] - G.yf[0]) * G.ihy) + 2;
+    }
+    __syncthreads();
+    classify_ib_block(flags, ex0, ey0, ex1, ey1, perx, pery, list, count, blockIdx.x / nbc, blockIdx.x % nbc, nbc,
+                      box[0], box[1], box[2], box[3]);
+    return;
+  }
   __shared__ Shift<T> S;
   if (threadIdx.x == 0) S = shift_of<T>(body, G.ihx, G.ihy);
   __syncthreads();
-  const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pair = (blockIdx.x - 2 * nbc) * blockDim.x + threadIdx.x;
   if (pair >= 2 * nm) return;
   const int m = pair >> 1, c = pair & 1;
   int i0, j0;
@@ -668,25 +702,30 @@ void ib_prepare(fs_grid* G, const double* body_state) {
     ey[c] = G->ny + ((c == 1 && !G->per[1]) ? 1 : 0);
   }
   FS_LAUNCH(G, "classify_solid", classify_solid_kernel<<<dim3(std::max(ey[0], ey[1]), 2), kT, 0, G->stream>>>(
-                                     dflags, ex[0], ey[0], ex[1], ey[1], G->xf64[0], G->xf64[1], body_state, P));
-  cudaMemsetAsync(B.ibcount, 0, sizeof(unsigned), G->stream);
-  {
-    const long long n = (long long)std::max(ex[0] * ey[0], ex[1] * ey[1]);
-    int nb = (int)((n + kT - 1) / kT);
-    if (nb > 148 * 8) nb = 148 * 8;
-    FS_LAUNCH(G, "classify_ib", classify_ib_kernel<<<dim3(nb, 2), kT, 0, G->stream>>>(
-                                    dflags, ex[0], ey[0], ex[1], ey[1], G->per[0], G->per[1], B.iblist, B.ibcount));
-  }
+                                     dflags, ex[0], ey[0], ex[1], ey[1], G->xf64[0], G->xf64[1], body_state, P,
+                                     B.ibcount));
   const IBGeom g = make_geom(G);
-  const int npb = (2 * B.nm + kT - 1) / kT;
-  if (g.width == 4)
-    FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T, 4><<<npb, kT, 0, G->stream>>>(g, B.nm, B.gi, (const T*)B.gf,
-                                                                          (const T*)B.dsh, body_state, dflags,
-                                                                          (T*)B.wfac));
-  else
-    FS_LAUNCH(G, "ib_fn", ib_fn_kernel<T, 3><<<npb, kT, 0, G->stream>>>(g, B.nm, B.gi, (const T*)B.gf,
-                                                                          (const T*)B.dsh, body_state, dflags,
-                                                                          (T*)B.wfac));
+  Box4 bbox;
+  for (int q = 0; q < 4; ++q) bbox.v[q] = B.poly_bb[q];
+  {
+    // faces in the body's bounding box (plus margins), which the kernel visits
+    const double bw = (B.poly_bb[1] - B.poly_bb[0]) / G->hx + 6.0, bh = (B.poly_bb[3] - B.poly_bb[2]) / G->h[1][0] + 6.0;
+    const long long all = (long long)std::max(ex[0] * ey[0], ex[1] * ey[1]);
+    const long long n = (G->per[0] || G->per[1]) ? all : std::min(all, (long long)(bw * bh) + 1);
+    int nbc = (int)((n + kT - 1) / kT);
+    if (nbc > 148 * 8) nbc = 148 * 8;
+    const int nb = 2 * nbc + (2 * B.nm + kT - 1) / kT;
+    if (g.width == 4)
+      FS_LAUNCH(G, "classify_ib_fn", ib_classify_fn_kernel<T, 4><<<nb, kT, 0, G->stream>>>(
+                                         dflags, ex[0], ey[0], ex[1], ey[1], G->per[0], G->per[1], B.iblist,
+                                         B.ibcount, nbc, g, B.nm, B.gi, (const T*)B.gf, (const T*)B.dsh, body_state,
+                                         (T*)B.wfac, bbox));
+    else
+      FS_LAUNCH(G, "classify_ib_fn", ib_classify_fn_kernel<T, 3><<<nb, kT, 0, G->stream>>>(
+                                         dflags, ex[0], ey[0], ex[1], ey[1], G->per[0], G->per[1], B.iblist,
+                                         B.ibcount, nbc, g, B.nm, B.gi, (const T*)B.gf, (const T*)B.dsh, body_state,
+                                         (T*)B.wfac, bbox));
+  }
   Bins bn{B.bin_start, B.bx0, B.by0, B.nbx, B.nby, G->xf[0][0], G->xf[1][0]};
   // IB faces: about two per marker and component.  Small bodies take a warp per face (the candidate
   // markers' loads all in flight: latency), large ones a thread per face (throughput); the kernel
