@@ -71,9 +71,16 @@ class Ensemble:
         """Record n steps of every member into one CUDA graph (members on parallel branches)."""
         main = torch.cuda.Stream()
         branches = [torch.cuda.Stream() for _ in range(self.nstreams)]
-        # warm-up on the capture streams (kernel attributes, lazily created state)
+        # warm-up: one step of every member on its capture stream (kernel attributes, lazily
+        # created state), then the states restored
+        snap = self.snapshot()
         for i, m in enumerate(self.members):
-            m.grid.set_stream(branches[i % self.nstreams])
+            st = branches[i % self.nstreams]
+            m.grid.set_stream(st)
+            with torch.cuda.stream(st):
+                m.step(1)
+        torch.cuda.synchronize()
+        self.restore(snap)
         torch.cuda.synchronize()
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g, stream=main):
