@@ -400,12 +400,15 @@ def run_ours(args, ws, rank, local):
                 "timing": timing, "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
 
     if dominant == "ysolve":
-        # the FP64 y solve is bound by the FP64 pipe.  Algorithmic flops per cell of the cyclic
-        # twisted solve (periodic y): forward multiply-add 2, outward multiply + multiply-add 3,
-        # cyclic correction multiply-add 2 = 7 (the wall-bounded chain has no correction: 5).
-        # Peak: B300's nominal FP64 rate, 1.25 TFLOP/s (no FP64 peak is measured on this machine; a
-        # timing probe of independent DFMA chains reached 1.06 TFLOP/s at 2032 MHz)
-        flops = 7.0 if wl.bc[1][0] == S.PERIODIC else 5.0
+        # the FP64 y solve is bound by the FP64 pipe.  Algorithmic FP64 flops per cell of the
+        # cyclic twisted solve (periodic y): forward multiply-add 2, outward substitution 2 (FP32
+        # fields: one multiply-add on the scaled rows, the scale applied in FP32 as the result is
+        # narrowed; FP64 fields: multiply + multiply-add, 3), cyclic correction multiply-add 2 (an
+        # upper bound: it is skipped where z is below FP64 rounding) = 6 (7); the wall-bounded
+        # chain has no correction: 4 (5).  Peak: B300's nominal FP64 rate, 1.25 TFLOP/s (no FP64
+        # peak is measured on this machine; a timing probe of independent DFMA chains reached
+        # 1.06 TFLOP/s at 2032 MHz)
+        flops = (2.0 if wl.bc[1][0] == S.PERIODIC else 0.0) + (4.0 if args.precision == "mixed" else 5.0)
         ach = flops * cells / (kms / cnt * 1e-3) / 1e12 if cnt else None
         tr = NCU_TRAFFIC.get(dominant)
         roofline = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",

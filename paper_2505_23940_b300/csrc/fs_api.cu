@@ -139,6 +139,14 @@ size_t elem_size(const fs_grid* G) { return G->prec == FS_MIXED ? sizeof(float) 
 // then rows L-1 down to R.  The rows are 2 kTwChunk zero rows, the 2 R positions, 2 kTwChunk
 // zero rows; nlp >= nlam + 72 leaves room for the kernel's L2 prefetch of a block's segment.
 // P and S are [nlam][4].
+// FP32 fields (mixed precision) take the outward pass in scaled form: with sigma_p = E_p (1 at
+// each thread's last position, whose x the 2x2 system gives, and at the inert slot; 0 at the
+// zero mode's pinned row) and y_p = x_p / sigma_p, the substitution x_p = E_p g_p + C_p x_{p+1}
+// becomes y_p = g_p + C'_p y_{p+1}, C'_p = C_p s_{p+1} / s_p (s = sigma, 1 where sigma = 0):
+// one multiply-add per row instead of a multiply and a multiply-add.  The cyclic correction
+// x = sigma (y - xi z / sigma) then uses z / sigma, and S0, S1 absorb sigma at rows 0 and L - 1.
+// sigma is tabulated in FP32 and applied in FP32 to the narrowed solution (the zero mode's
+// column in FP64, for its mean); E is not stored for such grids.
 int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::vector<double>& c) {
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int nlam = G->nmx * G->nlz;
@@ -159,6 +167,13 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
   if (cyc) {
     Z.assign((size_t)rows * nlp, 0.0);
     S.assign((size_t)4 * nlam, 0.0);
+  }
+  const bool yform = G->prec == FS_MIXED;
+  std::vector<float> SG;
+  std::vector<double> SG0, sc(2 * R), sig(2 * R);
+  if (yform) {
+    SG.assign((size_t)rows * nlp, 0.0f);
+    SG0.assign(2 * R, 0.0);
   }
   std::vector<double> aa(ny), cc(ny), bb(ny), beta(ny), e(ny), rhs(ny), x(ny), gh(ny);
   std::vector<double> m(ny), ee(ny), cm(ny);
@@ -246,9 +261,36 @@ int build_twisted_tables(fs_grid* G, const std::vector<double>& a, const std::ve
         S[(size_t)li * 4 + 1] = aa[ny - 1];
         S[(size_t)li * 4 + 2] = 1.0 / sigma;
       }
+      if (yform) {
+        for (int p = 0; p < 2 * R; ++p) {
+          const double ev = E[at(p, li)];
+          const bool last = p == R - 1 || p == 2 * R - 1;
+          sig[p] = last ? 1.0 : ev;
+          sc[p] = sig[p] != 0.0 ? sig[p] : 1.0;
+        }
+        // the outward pass of each thread: local positions R - 2 .. 0, each coupled to the next
+        for (int half = 0; half < 2; ++half)
+          for (int i = 0; i + 1 < R; ++i) {
+            const int p = half * R + i;
+            C[at(p, li)] = C[at(p, li)] * sc[p + 1] / sc[p];
+          }
+        for (int p = 0; p < 2 * R; ++p) {
+          SG[at(p, li)] = (float)sig[p];
+          E[at(p, li)] = 0.0;
+          if (cyc) Z[at(p, li)] = sig[p] != 0.0 ? Z[at(p, li)] / sig[p] : 0.0;
+        }
+        if (cyc) {
+          S[(size_t)li * 4 + 0] *= sig[pos(0)];
+          S[(size_t)li * 4 + 1] *= sig[pos(L - 1)];
+        }
+        if (li == 0) SG0 = sig;
+      }
     }
   }
-  if (upload(&G->twM, M) != cudaSuccess || upload(&G->twE, E) != cudaSuccess || upload(&G->twC, C) != cudaSuccess ||
+  if (yform && (upload(&G->twSig, SG) != cudaSuccess || upload(&G->twSig0, SG0) != cudaSuccess))
+    return set_error(FS_ERR_CUDA, "allocating tridiagonal tables");
+  if (upload(&G->twM, M) != cudaSuccess || (!yform && upload(&G->twE, E) != cudaSuccess) ||
+      upload(&G->twC, C) != cudaSuccess ||
       upload(&G->twP, P) != cudaSuccess ||
       (cyc && (upload(&G->twZ, Z) != cudaSuccess || upload(&G->twS, S) != cudaSuccess ||
                upload(&G->twK, K) != cudaSuccess)))
@@ -302,6 +344,7 @@ int build_tables(fs_grid* G) {
   const std::vector<double>& hf = G->hf[1];
   G->hysum = 0.0;
   for (int j = 0; j < ny; ++j) G->hysum += h[j];
+  G->yuniform = uniform(h) ? 1 : 0;
   std::vector<double> a(ny), c(ny);
   for (int j = 0; j < ny; ++j) {
     a[j] = 1.0 / (hf[j] * h[j]);        // coupling of row j to j - 1 (row 0: wraps to ny - 1)
@@ -447,6 +490,10 @@ void free_ytables(fs_grid* G) {
   }
   if (G->twK) cudaFree(G->twK);
   G->twK = nullptr;
+  if (G->twSig) cudaFree(G->twSig);
+  G->twSig = nullptr;
+  if (G->twSig0) cudaFree(G->twSig0);
+  G->twSig0 = nullptr;
 }
 
 void free_all(fs_grid* G) {

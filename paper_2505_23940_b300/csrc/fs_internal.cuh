@@ -325,6 +325,7 @@ struct fs_grid {
   int ynarrow = 0;                        // 1: 8-column blocks; tE, tCP, tZV, tWV are then [nlam][ypitch]
   int ypitch = 0;                         // row count of the eigenvalue-major tables (ny rounded up to even)
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
+  int yuniform = 0;                       // the y cells are all of one width
   int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
   bool tune_staged = true;                // shared-memory staged predictor where it applies
   int tune_pred_chunk = 0;                // staged predictor runs: 0 by grid size, -1 equal shares, > 0 aligned runs
@@ -345,6 +346,10 @@ struct fs_grid {
   double *twZ = nullptr;                  // [2 R + 4 kTwChunk][nlp] (periodic y)
   int* twK = nullptr;                     // [nlam] positions per thread where z matters (periodic y)
   double *twS = nullptr;                  // [nlz * nmx][4] (periodic y)
+  // FP32 fields: the outward pass carries y = x / sigma (one multiply-add per row), sigma applied
+  // in FP32 as the solution is narrowed
+  float* twSig = nullptr;                 // [2 R + 4 kTwChunk][nlp] sigma per position, position-major
+  double* twSig0 = nullptr;               // [2 R] sigma of the zero mode's column, FP64
 
   fs::IBDev ib;
   bool has_body = false;

@@ -774,13 +774,18 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // That is one FP64 multiply-add per row forward and a multiply plus a
 // multiply-add backward: the FP64 work of a plain Thomas solve, spread over
 // twice the threads.  M, E, C are tabulated per eigenvalue (M and C negated).
+// With FP32 fields the backward pass carries y_j = x_j / sigma_j instead
+// (sigma_j = E_j; 1 at each thread's last row, 0 at the zero mode's pinned row):
+//   y_j = g_j + C'_j y_{j+1},   C'_j = C_j sigma_{j+1} / sigma_j,
+// one multiply-add per row; sigma is applied in FP32 as the result is narrowed
+// (x = sigma y: two FP32 roundings of the FP64 solution instead of one).
 //
 // Periodic y (cyclic): with xi = x_{ny-1}, rows 0..ny-2 read A'' x' = d' - xi u,
 // u the coupling column of x_{ny-1}; so x' = y - xi z with A'' y = d' (the solve
 // above) and z = A''^-1 u (tabulated), and row ny-1 gives
 //   xi = (d_{ny-1} - S0 y_0 - S1 y_{ny-2}) S2,   S2 = 1 / (b_{ny-1} - S0 z_0 - S1 z_{ny-2}),
 // S0, S1 its couplings to x_0 and x_{ny-2}: one more multiply-add per row where
-// z matters.  z decays geometrically away from the chain's ends (faster for the
+// z matters (FP32 fields: z / sigma, and S0, S1 times sigma).  z decays geometrically away from the chain's ends (faster for the
 // larger x/z eigenvalues); a warp corrects the leading positions of its threads
 // up to the last one where some column's |z| exceeds 2^-56 of its largest
 // (tabulated per eigenvalue, K), beyond which the correction is below FP64
@@ -799,13 +804,15 @@ __global__ void __launch_bounds__(YC * NSEG) ysolve_kernel(T* __restrict__ data,
 // sweep rate).
 //
 // B300's FP64 pipe (one warp instruction per ~73 cycles per SM sub-partition,
-// conversions included) bounds the sweeps, which need 3 FP64 operations per
-// cell (4 with periodic y).  The block therefore splits its warps: four
-// "sweep" warps run the chains and issue little besides FP64, while four
-// helper warps widen the FP32 spectrum to FP64 with integer field arithmetic
-// (fpconv.cuh) as its row groups arrive by bulk asynchronous copies, releasing
-// each group to the sweeps on an mbarrier.  All eight warps narrow the solution
-// at the end, which leaves by bulk copies as well.
+// conversions included) bounds the sweeps, which need 2 FP64 operations per
+// cell with FP32 fields (3 with FP64 fields; one more with periodic y where z
+// matters).  The block therefore splits its warps: four "sweep" warps run the
+// chains and issue little besides FP64, while four helper warps widen the FP32
+// spectrum to FP64 with integer field arithmetic (fpconv.cuh) as its row groups
+// arrive by tensor-map copies, releasing each group to the sweeps on an
+// mbarrier, then stage sigma in the freed FP32 tile, and narrow the solution
+// chunk by chunk as the sweeps finish it: the chunks nearest the middle first,
+// during the outward pass where no z reaches them.
 //
 // The singular zero mode pins x_0 = 0 through its tables (E_0 = C_0 = 0,
 // M_1 = 0, no coupling to row 0) and is shifted to zero hy-weighted mean (with
@@ -821,14 +828,17 @@ struct YTwArgs {
   int bulk;              // rows move by bulk copies (16-byte aligned rows and widths)
   int tiled;             // FP32: the tile arrives as 32-row boxes of the tensor map (row order)
   const double* M;       // [2 U + 2 R + 2 U][nlp] forward multipliers (negated), position-major
-  const double* E;       // inverse pivots, same layout
-  const double* C;       // outward multipliers (negated)
+  const double* E;       // inverse pivots, same layout (FP64 fields)
+  const double* C;       // outward multipliers (negated; FP32 fields: of the scaled pass)
+  const float* sig;      // FP32 fields: sigma per position (x = sigma y), same layout
+  const double* sig0;    // FP32 fields: sigma of the zero mode's column [2 R]
   const double* Z;       // cyclic: z = A''^-1 u
   const double* P;       // [nlam][4] inverse of the middle 2x2 system
   const double* S;       // [nlam][4] cyclic: S0, S1, S2
   const int* K;          // [nlam] cyclic: positions per thread (from its first) where z matters
   const double* hy;      // cell widths (zero-mode mean)
-  double hysum;
+  double hysum_inv;      // 1 / their sum
+  int hy_uniform;        // uniform y cells (the mean is then unweighted)
   unsigned* status;      // device status word (bit 0: a bulk copy or group wait gave up)
   int xblk0;             // first block of columns along x (blockIdx.x + xblk0)
 };
@@ -882,6 +892,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   constexpr int ND = 20;                         // output chunks of 16 positions (R <= 293 rows per thread)
   constexpr int NB = 20;                         // tensor-map boxes of kTwBoxRows rows (ny <= 320)
   __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
+  __shared__ uint64_t stfree;                    // tiled FP32: the sweeps are done with the stage buffer
   const int tid = threadIdx.x, lane = tid & 31;
   const int s0 = (blockIdx.x + A.xblk0) * W;
   const int ncol = min(W, A.nx - s0);
@@ -909,6 +920,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       mbar_init(&widebar[g], W / 16);            // one arrival per helper warp
     }
     for (int c = 0; c < ND; ++c) mbar_init(&donebar[c], W / 16);   // one arrival per sweep warp
+    mbar_init(&stfree, W / 16);
     mbar_init_fence();
   }
   __syncthreads();
@@ -928,6 +940,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     double mb[U];
 #pragma unroll
     for (int q = 0; q < U; ++q) mb[q] = __ldg(Mt + q * nl);   // tables do not depend on the predecessor
+    // periodic y: positions per thread (from its first) where z matters, for this column
+    const int kwl = CYC && act ? __ldg(A.K + li) : 1;
     double* gp = sg + P0 * W + cb;
     // 1. elimination towards the middle; chunk c waits for its rows
     if (F32 && A.tiled) {
@@ -949,6 +963,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           gp[q * W] = act && j >= 0 ? widen<T>(st[j * W + cb]) : 0.0;
         }
       }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&stfree);      // the stage buffer's rows of chunk 0 are read
     }
     double gv = 0.0;
     for (int i0 = 0; i0 < R; i0 += U) {
@@ -988,26 +1004,40 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     const double* Pt = A.P + (size_t)li * 4 + 2 * half;
     double xv = fma(__ldg(Pt), gk, __ldg(Pt + 1) * hk);
     gp[(R - 1) * W] = xv;
-    // 3. outward substitution, positions descending
+    // 3. outward substitution, positions descending (FP32 fields: y = x / sigma, one multiply-add
+    // per row; FP64 fields: x = E g + C x_next)
+    if constexpr (CYC) {
+      // the cyclic correction's first table entries into L2 meanwhile (its start waits on them)
+#pragma unroll
+      for (int q = 0; q < U; ++q) prefetch_l2(A.Z + tb + q * nl);
+      prefetch_l2(A.S + (size_t)li * 4);
+    }
+    // periodic y: the chunks the cyclic correction touches in some column of this warp; the
+    // outward pass hands every later chunk to the helpers as soon as it is final
+    const int nkw = CYC ? (__reduce_max_sync(FULL, kwl) + U - 1) / U : 0;
     {
       const double* __restrict__ Et = A.E + tb;
       const double* __restrict__ Ct = A.C + tb;
-      double eb[U], cbuf[U];
+      double eb[F32 ? 1 : U], cbuf[U];
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        eb[q] = __ldg(Et + (R - 2 - q) * (ptrdiff_t)nl);
+        if constexpr (!F32) eb[q] = __ldg(Et + (R - 2 - q) * (ptrdiff_t)nl);
         cbuf[q] = __ldg(Ct + (R - 2 - q) * (ptrdiff_t)nl);
       }
-      int next = nchunk - 1;                     // walls: highest output chunk not yet released
+      int next = nchunk - 1;                     // highest output chunk not yet released
       for (int i0 = R - 2; i0 >= 0; i0 -= U) {
         if (i0 + 1 >= U) {
           // products E g first (independent), the chain in registers, the stores after
           double v[U], c2[U];
 #pragma unroll
           for (int q = 0; q < U; ++q) {
-            v[q] = eb[q] * gp[(i0 - q) * W];
+            if constexpr (F32) {
+              v[q] = gp[(i0 - q) * W];
+            } else {
+              v[q] = eb[q] * gp[(i0 - q) * W];
+              eb[q] = __ldg(Et + (i0 - U - q) * (ptrdiff_t)nl);
+            }
             c2[q] = cbuf[q];
-            eb[q] = __ldg(Et + (i0 - U - q) * (ptrdiff_t)nl);
             cbuf[q] = __ldg(Ct + (i0 - U - q) * (ptrdiff_t)nl);
           }
 #pragma unroll
@@ -1021,17 +1051,20 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
 #pragma unroll
           for (int q = 0; q < U; ++q) {
             if (q <= i0) {
-              const double eg = eb[q] * gp[(i0 - q) * W];
+              double eg;
+              if constexpr (F32) eg = gp[(i0 - q) * W];
+              else eg = eb[q] * gp[(i0 - q) * W];
               xv = fma(cbuf[q], xv, eg);
               gp[(i0 - q) * W] = xv;
             }
           }
         }
-        if constexpr (!CYC) {
-          // positions max(i0 - U + 1, 0) .. R - 1 are final: hand their chunks to the helpers
+        {
+          // positions max(i0 - U + 1, 0) .. R - 1 are final (periodic y: where no z reaches them):
+          // hand their chunks to the helpers
           const int lowest = max(i0 - U + 1, 0);
           __syncwarp();
-          while (next >= 0 && U * next >= lowest) {
+          while (next >= nkw && U * next >= lowest) {
             if (lane == 0) mbar_arrive(&donebar[next]);
             --next;
           }
@@ -1054,26 +1087,25 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       const double* St = A.S + (size_t)li * 4;
       const double xi = fma(-__ldg(St + 1), yl, fma(-__ldg(St), y0, dlast)) * __ldg(St + 2);
       const double* __restrict__ Zt = A.Z + tb;
-      // the positions where some column of this warp still has a z above 2^-56 of its largest
-      const int kw = __reduce_max_sync(FULL, act ? __ldg(A.K + li) : 1);
-      double zb[U];
+      // the chunks some z of this warp's columns reaches (the later ones went to the helpers in the
+      // outward pass), corrected from the middle outward: the helpers narrow in the same order
+      double zv[U];
 #pragma unroll
-      for (int q = 0; q < U; ++q) zb[q] = __ldg(Zt + q * nl);
-      for (int i0 = 0; i0 < R; i0 += U) {
-        if (i0 < kw) {
-          double v[U];
+      for (int q = 0; q < U; ++q) zv[q] = __ldg(Zt + ((nkw - 1) * U + q) * nl);
+      for (int c = nkw - 1; c >= 0; --c) {
+        const int i0 = c * U;
+        double v[U];
 #pragma unroll
-          for (int q = 0; q < U; ++q) {
-            v[q] = fma(-xi, zb[q], gp[min(i0 + q, R - 1) * W]);
-            zb[q] = __ldg(Zt + (i0 + U + q) * nl);
-          }
-          if (half && i0 == 0) v[0] = xi;          // the inert slot becomes x_{ny-1}
-#pragma unroll
-          for (int q = 0; q < U; ++q)
-            if (i0 + q < R) gp[(i0 + q) * W] = v[q];
+        for (int q = 0; q < U; ++q) {
+          v[q] = fma(-xi, zv[q], gp[min(i0 + q, R - 1) * W]);
+          zv[q] = __ldg(Zt + (i0 - U + q) * nl);   // the table's zero rows ahead of position 0
         }
+        if (half && i0 == 0) v[0] = xi;            // the inert slot becomes x_{ny-1}
+#pragma unroll
+        for (int q = 0; q < U; ++q)
+          if (i0 + q < R) gp[(i0 + q) * W] = v[q];
         __syncwarp();
-        if (lane == 0) mbar_arrive(&donebar[i0 / U]);   // the helpers narrow this chunk meanwhile
+        if (lane == 0) mbar_arrive(&donebar[c]);   // the helpers narrow this chunk meanwhile
       }
     }
   } else {
@@ -1095,7 +1127,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       for (int p = h - 32; p < 2 * R; p += NS - 32) {
         const size_t o = (size_t)(2 * U + p) * nl + first;
         bulk_prefetch_l2(A.M + o, bytes);
-        bulk_prefetch_l2(A.E + o, bytes);
+        if constexpr (!F32) bulk_prefetch_l2(A.E + o, bytes);
         bulk_prefetch_l2(A.C + o, bytes);
         if constexpr (CYC) bulk_prefetch_l2(A.Z + o, bytes);
       }
@@ -1127,12 +1159,22 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
           const int a1 = (b & 1) ? ny - kTwBoxRows * l : min(kTwBoxRows * (l + 1), ny - kTwBoxRows * l);
           // this thread: column h % W, rows a0 + h / W + 2 k, by the fast path; a warp that met
           // another value redoes its rows with the general routine
-          uint32_t sp = 0;
-#pragma unroll 8
-          for (int j = a0 + hw; j < a1; j += 2) {
-            uint32_t whi, wlo;
-            fsconv_widen_fast(__float_as_uint(st[j * W + hc]), &whi, &wlo, &sp);
-            sg[pos(j) * W + hc] = __hiloint2double((int)whi, (int)wlo);
+          // (all of a box's loads first: the stage buffer and the FP64 rows share one array, so
+          // the compiler would otherwise keep every load behind the previous row's store)
+          uint32_t sp = 0, raw[kTwBoxRows / 2];
+#pragma unroll
+          for (int k = 0; k < kTwBoxRows / 2; ++k) {
+            const int j = a0 + hw + 2 * k;
+            raw[k] = j < a1 ? __float_as_uint(st[j * W + hc]) : 0u;
+          }
+#pragma unroll
+          for (int k = 0; k < kTwBoxRows / 2; ++k) {
+            const int j = a0 + hw + 2 * k;
+            if (j < a1) {
+              uint32_t whi, wlo;
+              fsconv_widen_fast(raw[k], &whi, &wlo, &sp);
+              sg[pos(j) * W + hc] = __hiloint2double((int)whi, (int)wlo);
+            }
           }
           if (__any_sync(FULL, sp))
             for (int j = a0 + hw; j < a1; j += 2) sg[pos(j) * W + hc] = fsconv_widen(st[j * W + hc]);
@@ -1189,45 +1231,101 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     }
     // the solution out, chunk by chunk as the sweeps finish it: narrowed, row-coalesced (the zero
     // mode's column waits for its mean, below)
-    const bool mine = hc < ncol && !(zb && hc == 0);
-    for (int c = 0; c < nchunk; ++c) {
-      ok &= mbar_wait_idle(&donebar[c], 0);
+    const bool zcol = zb && hc == 0, mine = hc < ncol && !zcol;
+    // FP32 fields: sigma (x = sigma y) of every position of the block's columns, into the stage
+    // buffer once no thread reads the tile there any more ([2 R][W]; 2 R <= ny + 1 rows), by
+    // asynchronous copies issued long before the first chunk is narrowed
+    float* const ssg = reinterpret_cast<float*>(st);
+    if constexpr (F32) {
+      if (A.tiled) ok &= mbar_wait_idle(&stfree, 0);
+      asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");   // every helper is done with the tile
+      const int lih = hc < ncol ? lam_of(A.nx, A.nz, A.dim, A.xmode, A.nmx, s0 + hc, t) : 0;
+      const float* __restrict__ sgt = A.sig + (size_t)2 * U * A.nlp + lih;
+      for (int p = hw; p < NP; p += 2) cp_async4(ssg + p * W + hc, sgt + (size_t)p * A.nlp);
+      cp_async_wait_all();
+      asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");
+    }
+    // the chunks as the sweeps finish them, the last first: the outward pass (walls) and the
+    // cyclic correction (periodic y) both release the positions nearest the middle first
+    for (int ci = 0; ci < nchunk; ++ci) {
+      const int c = nchunk - 1 - ci;
       const int lo = U * c, n = min(U, R - lo);
+      ok &= mbar_wait_idle(&donebar[c], 0);
       // rows h / W + 2 k of the chunk's 2 n: the upper positions lo + r, then the lower R + lo + r;
-      // the fast path for every value, the general routine again where a warp met another
+      // the fast path for every value, the general routine again where a warp met another.  The
+      // chunk's shared-memory reads come first, all of them: the compiler cannot tell them apart
+      // from the global stores and would otherwise chain each row behind the previous store.
       uint32_t sp = 0;
-#pragma unroll 8
-      for (int r = hw; r < 2 * n; r += 2) {
+      double vv[U];
+      float sgm[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int r = hw + 2 * k;
         const int p = r < n ? lo + r : R + lo + (r - n);
-        const int j = rowof(p);
-        const double v = sg[p * W + hc];
-        if constexpr (F32) {
-          const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
-          if (mine && j >= 0) tile[rs * j + hc] = __uint_as_float(o);
-        } else {
-          if (mine && j >= 0) tile[rs * j + hc] = v;
+        const bool in = r < 2 * n;
+        vv[k] = in ? sg[p * W + hc] : 0.0;
+        if constexpr (F32) sgm[k] = in ? ssg[p * W + hc] : 0.0f;
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int r = hw + 2 * k;
+        if (r < 2 * n) {
+          const int p = r < n ? lo + r : R + lo + (r - n);
+          const int j = rowof(p);
+          const double v = vv[k];
+          if constexpr (F32) {
+            const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
+            const float x = __uint_as_float(o) * sgm[k];
+            if (mine && j >= 0) tile[rs * j + hc] = x;
+            else if (zcol) ssg[p * W + hc] = x;    // the zero mode's column: kept for its mean
+          } else {
+            if (mine && j >= 0) tile[rs * j + hc] = v;
+          }
         }
       }
       if constexpr (F32) {
         if (__any_sync(FULL, sp)) {
-          for (int r = hw; r < 2 * n; r += 2) {
-            const int p = r < n ? lo + r : R + lo + (r - n);
-            const int j = rowof(p);
-            if (mine && j >= 0) tile[rs * j + hc] = fsconv_narrow(sg[p * W + hc]);
+#pragma unroll 1
+          for (int k = 0; k < U; ++k) {
+            const int r = hw + 2 * k;
+            if (r < 2 * n) {
+              const int p = r < n ? lo + r : R + lo + (r - n);
+              const int j = rowof(p);
+              const float x = fsconv_narrow(sg[p * W + hc]) * ssg[p * W + hc];
+              if (mine && j >= 0) tile[rs * j + hc] = x;
+              else if (zcol) ssg[p * W + hc] = x;
+            }
           }
         }
       }
     }
   }
   __syncthreads();
-  // 5. zero mode: hy-weighted mean of its column, subtracted (in the field precision) as it leaves
+  // 5. zero mode: hy-weighted mean of its column, subtracted as it leaves.  FP32 fields: the column
+  // narrowed and scaled by the helpers like every other (x = sigma y in FP32), its mean taken in
+  // FP32 (a gauge constant, exact to FP32 rounding; the weights only on stretched y); FP64 fields
+  // in FP64.
   if (zb && tid < 32) {
-    double part = 0.0;
-    for (int j = lane; j < ny; j += 32) part = fma(__ldg(A.hy + j), sg[pos(j) * W], part);
+    if constexpr (F32) {
+      // the helpers left the column's FP32 values where its sigma was staged
+      const float* const xs = reinterpret_cast<const float*>(st);
+      float part = 0.0f;
+      for (int j = lane; j < ny; j += 32) {
+        const float x = xs[pos(j) * W];
+        part += A.hy_uniform ? x : (float)__ldg(A.hy + j) * x;
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-    const T zm = (T)(part / A.hysum);
-    for (int j = lane; j < ny; j += 32) tile[rs * j] = narrow<T>(sg[pos(j) * W]) - zm;
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      const float zm = part * (A.hy_uniform ? 1.0f / (float)ny : (float)A.hysum_inv);
+      for (int j = lane; j < ny; j += 32) tile[rs * j] = xs[pos(j) * W] - zm;
+    } else {
+      double part = 0.0;
+      for (int j = lane; j < ny; j += 32) part = fma(__ldg(A.hy + j), sg[pos(j) * W], part);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+      const T zm = (T)(part * A.hysum_inv);
+      for (int j = lane; j < ny; j += 32) tile[rs * j] = sg[pos(j) * W] - zm;
+    }
   }
   if (!ok) atomicOr(A.status, 1u);   // part of the tile never arrived: this block's columns are invalid
 }
@@ -1602,12 +1700,15 @@ void launch_ytwist(fs_grid* G, T* data, int xblk0, int nxblk) {
   A.M = G->twM;
   A.E = G->twE;
   A.C = G->twC;
+  A.sig = G->twSig;
+  A.sig0 = G->twSig0;
   A.P = G->twP;
   A.Z = G->twZ;
   A.S = G->twS;
   A.K = G->twK;
   A.hy = G->hy64;
-  A.hysum = G->hysum;
+  A.hysum_inv = 1.0 / G->hysum;
+  A.hy_uniform = G->yuniform;
   A.status = G->dstatus;
   A.xblk0 = xblk0;
   // rows move by bulk copies when every row start and width is a multiple of 16 bytes
