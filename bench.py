@@ -50,14 +50,13 @@ KERNEL_BYTES_PER_CELL = {
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50362880 + 839680, "src": "9d68f8187082"},
-    "ysolve": {"bytes": 26267392 + 0, "src": "f6da4e81d3a5"},
-    "fft_x_fwd_div": {"bytes": 25243392 + 0, "src": "7895d4f893d7"},
-    "fft_z_fwd": {"bytes": 8407040 + 0, "src": "7895d4f893d7"},
-    "fft_y_solve": {"bytes": 8435200 + 0, "src": "7895d4f893d7"},
-    "fft_z_inv": {"bytes": 8410880 + 0, "src": "7895d4f893d7"},
-    "fft_x_inv": {"bytes": 8414720 + 0, "src": "7895d4f893d7"},
-    "correct": {"bytes": 33560576 + 256, "src": "96276b6b63ca"},
+    "predictor": {"bytes": 50361344 + 924416, "src": "4d5c344d8f7c"},
+    "ysolve": {"bytes": 24111872 + 0, "src": "70822cb45082"},
+    "fft_x_fwd_div": {"bytes": 25243648 + 0, "src": "63900357a1f5"},
+    "fft_z_fwd": {"bytes": 8407296 + 0, "src": "63900357a1f5"},
+    "fft_z_inv": {"bytes": 8410880 + 0, "src": "63900357a1f5"},
+    "fft_x_inv": {"bytes": 8414720 + 0, "src": "63900357a1f5"},
+    "correct": {"bytes": 33560320 + 3072, "src": "96276b6b63ca"},
 }
 
 
