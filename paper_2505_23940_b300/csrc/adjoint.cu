@@ -1290,12 +1290,15 @@ int step_adjoint(fs_grid* G, const fs_state* st, fs_state* lam, const double* dJ
         v2[c] = c < dim ? (T*)rv2[c] : nullptr;
       }
     } else {
+      // as the forward step took them (its stage solves leave the pressure's gauge unset)
+      G->ygauge = false;
       launch_predictor<T>(G, u, u, us, dt, Ac[0], Bc[0], nullptr);
       poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
       launch_correct<T>(G, us, spec, v1);
       launch_predictor<T>(G, v1, u, us, dt, Ac[1], Bc[1], nullptr);
       poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
       launch_correct<T>(G, us, spec, v2);
+      G->ygauge = true;
     }
     T* const* vs[3] = {u, v1, v2};
     for (int c = 0; c < dim; ++c) cudaMemsetAsync(la[c], 0, comp_count(G, c) * sizeof(T), G->stream);

@@ -559,7 +559,9 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p, void* const* re
     for (int s = 0; s < 3; ++s) {
       T* const* in = s == 0 ? u : (s == 1 ? v1 : v2);
       launch_predictor<T>(G, in, u, us, dt, A[s], Bc[s], nullptr);
+      G->ygauge = want_p && s == 2;              // only the written-out pressure needs its gauge
       poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, nullptr), spec);
+      G->ygauge = true;
       launch_correct<T>(G, us, spec, s == 2 ? u : (s == 0 ? v1 : v2));
     }
     if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / (Bc[2] * dt));
@@ -568,7 +570,9 @@ void step_once(fs_grid* G, fs_state* st, double dt, bool want_p, void* const* re
   if (G->has_body) ib_prepare<T>(G, st->body);
   launch_outflow_flux<T>(G, u);
   launch_predictor<T>(G, u, nullptr, us, dt, 0.0, 1.0, st->body);
+  G->ygauge = want_p;
   poisson_solve_from_velocity<T>(G, make_div_args<T>(G, us, st->body), spec);
+  G->ygauge = true;
   launch_correct<T>(G, us, spec, u);
   if (want_p) launch_to_pressure<T>(G, spec, st->p, G->rho / dt);
   if (G->has_body) {

@@ -326,6 +326,10 @@ struct fs_grid {
   int ypitch = 0;                         // row count of the eigenvalue-major tables (ny rounded up to even)
   double hysum = 0.0;                     // sum of the y cell widths (zero-mode mean of the y solve)
   int yuniform = 0;                       // the y cells are all of one width
+  // the twisted y solve shifts the zero mode's column to zero hy-weighted mean (the pressure's
+  // gauge); off in the Poisson solves whose pressure is not written out, where only its gradient
+  // is used and the column keeps the gauge of its factorisation (x = 0 at row 0)
+  bool ygauge = true;
   int tune_ynseg = 0;                     // requested segment count (0: chosen from the grid's shape)
   bool tune_staged = true;                // shared-memory staged predictor where it applies
   int tune_pred_chunk = 0;                // staged predictor runs: 0 by grid size, -1 equal shares, > 0 aligned runs

@@ -839,6 +839,7 @@ struct YTwArgs {
   const double* hy;      // cell widths (zero-mode mean)
   double hysum_inv;      // 1 / their sum
   int hy_uniform;        // uniform y cells (the mean is then unweighted)
+  int gauge;             // shift the zero mode's column to zero hy-weighted mean
   unsigned* status;      // device status word (bit 0: a bulk copy or group wait gave up)
   int xblk0;             // first block of columns along x (blockIdx.x + xblk0)
 };
@@ -912,7 +913,8 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   const uint32_t rb = (uint32_t)(ncol * sizeof(T));
   const int nchunk = (R + U - 1) / U;
   const int nbox = (ny + kTwBoxRows - 1) / kTwBoxRows, nlev = (nbox + 1) / 2;
-  const bool zb = s0 == 0 && (A.dim == 2 || t == 0);   // the block holding the zero mode (column 0)
+  // the block holding the zero mode (column 0), when its gauge is to be set
+  const bool zb = A.gauge && s0 == 0 && (A.dim == 2 || t == 0);
   bool ok = true;
   if (tid == 0) {
     for (int g = 0; g < NB; ++g) {
@@ -1709,6 +1711,7 @@ void launch_ytwist(fs_grid* G, T* data, int xblk0, int nxblk) {
   A.hy = G->hy64;
   A.hysum_inv = 1.0 / G->hysum;
   A.hy_uniform = G->yuniform;
+  A.gauge = G->ygauge ? 1 : 0;
   A.status = G->dstatus;
   A.xblk0 = xblk0;
   // rows move by bulk copies when every row start and width is a multiple of 16 bytes
