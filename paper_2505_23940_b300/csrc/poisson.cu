@@ -894,6 +894,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   constexpr int NB = 20;                         // tensor-map boxes of kTwBoxRows rows (ny <= 320)
   __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
   __shared__ uint64_t stfree;                    // tiled FP32: the sweeps are done with the stage buffer
+  __shared__ uint64_t sigbar;                    // FP32: sigma is staged
   const int tid = threadIdx.x, lane = tid & 31;
   const int s0 = (blockIdx.x + A.xblk0) * W;
   const int ncol = min(W, A.nx - s0);
@@ -923,6 +924,7 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
     }
     for (int c = 0; c < ND; ++c) mbar_init(&donebar[c], W / 16);   // one arrival per sweep warp
     mbar_init(&stfree, W / 16);
+    mbar_init(&sigbar, W / 16);                  // one arrival per helper warp
     mbar_init_fence();
   }
   __syncthreads();
@@ -1110,6 +1112,48 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
         if (lane == 0) mbar_arrive(&donebar[c]);   // the helpers narrow this chunk meanwhile
       }
     }
+    // 5. the chunk nearest the chain's ends, the last to be final: narrowed by the sweep threads
+    // themselves (each its own rows) while the helpers narrow the chunk before it
+    {
+      const int n0 = min(U, R);
+      const bool zc = zb && cb == 0;             // the zero mode's column: kept for its gauge
+      float* const ssg = reinterpret_cast<float*>(st) + P0 * W + cb;
+      float sv[U];
+      if constexpr (F32) {
+        ok &= mbar_wait_idle(&sigbar, 0);
+#pragma unroll
+        for (int q = 0; q < U; ++q) sv[q] = q < n0 ? ssg[q * W] : 0.0f;
+      }
+      uint32_t sp = 0;
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int j = rowof(P0 + q);
+        if (q < n0 && act) {
+          const double v = gp[q * W];
+          if constexpr (F32) {
+            const uint32_t o = fsconv_narrow_fast((uint32_t)__double2hiint(v), (uint32_t)__double2loint(v), &sp);
+            const float x = __uint_as_float(o) * sv[q];
+            if (zc) ssg[q * W] = x;
+            else if (j >= 0) tile[rs * j + cb] = x;
+          } else if (!zc && j >= 0) {
+            tile[rs * j + cb] = v;
+          }
+        }
+      }
+      if constexpr (F32) {
+        if (__any_sync(FULL, sp)) {
+#pragma unroll
+          for (int q = 0; q < U; ++q) {
+            const int j = rowof(P0 + q);
+            if (q < n0 && act) {
+              const float x = fsconv_narrow(gp[q * W]) * sv[q];
+              if (zc) ssg[q * W] = x;
+              else if (j >= 0) tile[rs * j + cb] = x;
+            }
+          }
+        }
+      }
+    }
   } else {
     // ---------------- helper threads: tile in, widened, group by group ----------------
     const int h = tid - NS;                      // 0 .. 2 W - 1
@@ -1246,10 +1290,11 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
       for (int p = hw; p < NP; p += 2) cp_async4(ssg + p * W + hc, sgt + (size_t)p * A.nlp);
       cp_async_wait_all();
       asm volatile("bar.sync 1, %0;" ::"r"(NS) : "memory");
+      if (lane == 0) mbar_arrive(&sigbar);
     }
     // the chunks as the sweeps finish them, the last first: the outward pass (walls) and the
     // cyclic correction (periodic y) both release the positions nearest the middle first
-    for (int ci = 0; ci < nchunk; ++ci) {
+    for (int ci = 0; ci < nchunk - 1; ++ci) {   // (chunk 0: the sweeps)
       const int c = nchunk - 1 - ci;
       const int lo = U * c, n = min(U, R - lo);
       ok &= mbar_wait_idle(&donebar[c], 0);
