@@ -51,7 +51,7 @@ KERNEL_BYTES_PER_CELL = {
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50361344 + 924416, "src": "4d5c344d8f7c"},
-    "ysolve": {"bytes": 24111872 + 0, "src": "70822cb45082"},
+    "ysolve": {"bytes": 24119808 + 0, "src": "91361bff4f2b"},
     "fft_x_fwd_div": {"bytes": 25243648 + 0, "src": "63900357a1f5"},
     "fft_z_fwd": {"bytes": 8407296 + 0, "src": "63900357a1f5"},
     "fft_z_inv": {"bytes": 8410880 + 0, "src": "63900357a1f5"},
