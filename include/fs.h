@@ -314,7 +314,8 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *   "stencil_bx"      x threads of the 256-thread stencil blocks: 32, 64, 128, 256
  *   "fft_lines"       complex lines per block of the mixed-radix transforms
  *                     (lengths other than 64, 128, 256): 1..16
- *   "predictor_cells" cells per thread of the FP32 3-D predictor: 2 or 4 (default)
+ *   "predictor_cells" cells per thread of the FP32 predictor: 1 (the one-cell kernel), 2 (3-D) or
+ *                    4 (default; 2-D: fully periodic grids without a body)
  *   "predictor_zmarch" z planes per thread of the four-cell predictor: 1 (no
  *                     march) .. 64; default 8
  *   "pdl"             1 (default): step kernels use programmatic dependent

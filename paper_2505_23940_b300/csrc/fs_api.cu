@@ -909,7 +909,8 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     if (value < 0 || value > 16) return set_error(FS_ERR_ARG, "fft_lines must be in 1..16");
     G->tune_fft_lines = value;
   } else if (k == "predictor_cells") {
-    if (value != 0 && value != 2 && value != 4) return set_error(FS_ERR_ARG, "predictor_cells must be 2 or 4");
+    if (value != 0 && value != 1 && value != 2 && value != 4)
+      return set_error(FS_ERR_ARG, "predictor_cells must be 1, 2 or 4");
     G->tune_pred_vw = value;
   } else if (k == "predictor_zmarch") {
     if (value < 0 || value > 64) return set_error(FS_ERR_ARG, "predictor_zmarch must be in 0..64");

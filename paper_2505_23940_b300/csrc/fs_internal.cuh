@@ -373,7 +373,7 @@ struct fs_grid {
   int tune_stencil_bx = 0;     // x threads of the 2-D stencil blocks (32, 64, 128); blocks hold 256 threads
   int tune_fft_lines = 0;      // complex lines per FFT block (1..16)
   bool use_pdl = true;         // programmatic dependent launch of the step kernels
-  int tune_pred_vw = 0;        // cells per thread of the FP32 3-D predictor (2 or 4; 0 = 4)
+  int tune_pred_vw = 0;        // cells per thread of the FP32 predictor (1, 2 or 4; 0 = 4)
   int tune_zmarch = 0;         // planes per thread of the z-marching FP32 predictor (0: 8, 1: no march)
   // Smagorinsky LES (fs_set_les): constant, nu_t at centres and xy / xz / yz edges (field precision)
   double les_cs = 0.0;

@@ -667,6 +667,72 @@ __global__ void __launch_bounds__(kThreads, 3) predictor3v_kernel(const PredArgs
   stw<VW>(A.out[1] + v00 + i0, o3[1]);
 }
 
+// The 2-D counterpart for fully periodic uniform FP32 grids (no body): VW cells
+// per thread along x, the arithmetic of Eq. (4) on the x- and y-faces with the
+// uniform metrics (interpolation weights 1/2), six row segments per thread.
+template <int VW>
+__global__ void __launch_bounds__(kThreads) predictor2v_kernel(const PredArgs<float> A) {
+  pdl_wait();
+  const Geom<float>& g = A.g;
+  const int nx = g.nx, ny = g.ny;
+  const int i0 = VW * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i0 >= nx || j >= ny) return;
+  const int jm = j > 0 ? j - 1 : ny - 1, jp = j < ny - 1 ? j + 1 : 0;
+  const int r0 = nx * j, rm = nx * jm, rp = nx * jp;
+  const float* __restrict__ U = A.uin[0];
+  const float* __restrict__ V = A.uin[1];
+  constexpr int L = VW + 2;   // index e + 1 is cell i0 + e
+  float U0[L], UM[L], UP[L], V0[L], VM[L], VP[L];
+  ld_seg<true, true, VW>(U + r0, i0, nx, U0);
+  ld_seg<false, true, VW>(U + rm, i0, nx, UM);
+  ld_seg<false, false, VW>(U + rp, i0, nx, UP);
+  ld_seg<true, true, VW>(V + r0, i0, nx, V0);
+  ld_seg<false, false, VW>(V + rm, i0, nx, VM);
+  ld_seg<true, false, VW>(V + rp, i0, nx, VP);
+  const float ihx = g.ihx, ihy = A.ihy0, nu = g.nu, h = 0.5f;
+  const float bf = g.bforce ? g.bforce[j] : 0.f;
+  const float a = A.a, b = A.b, dt = A.dt;
+  float o2[2][VW];
+#pragma unroll
+  for (int e = 0; e < VW; ++e) {
+    const int c = e + 1;
+    const float u = U0[c], uW = U0[c - 1], uE = U0[c + 1], uS = UM[c], uN = UP[c], uSE = UM[c + 1];
+    const float v = V0[c], vW = V0[c - 1], vE = V0[c + 1], vS = VM[c], vN = VP[c], vNW = VP[c - 1];
+    // u on the x-face
+    float TE = h * (u + uE), TW = h * (uW + u);
+    float cv = (TE * TE - TW * TW) * ihx;
+    float df = ((uE - u) * ihx - (u - uW) * ihx) * ihx;
+    float TN = h * (vNW + vN), TS = h * (vW + v);
+    cv += (TN * (h * (u + uN)) - TS * (h * (uS + u))) * ihy;
+    df += ((uN - u) * ihy - (u - uS) * ihy) * ihy;
+    const float Ru = -cv + nu * df + bf;
+    // v on the y-face
+    TE = h * (v + vN);
+    TW = h * (vS + v);
+    cv = (TE * TE - TW * TW) * ihy;
+    df = ((vN - v) * ihy - (v - vS) * ihy) * ihy;
+    TN = h * (uSE + uE);
+    TS = h * (uS + u);
+    cv += (TN * (h * (v + vE)) - TS * (h * (vW + v))) * ihx;
+    df += ((vE - v) * ihx - (v - vW) * ihx) * ihx;
+    const float Rv = -cv + nu * df;
+    o2[0][e] = b * (u + dt * Ru);
+    o2[1][e] = b * (v + dt * Rv);
+  }
+  if (a != 0.f) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float pn[VW];
+      ldw<VW>(A.un[c] + r0 + i0, pn);
+#pragma unroll
+      for (int e = 0; e < VW; ++e) o2[c][e] += a * pn[e];
+    }
+  }
+  stw<VW>(A.out[0] + r0 + i0, o2[0]);
+  stw<VW>(A.out[1] + r0 + i0, o2[1]);
+}
+
 // The four-cell FP32 predictor marching in z: a thread computes the cells
 // (i0 .. i0+3, j) of KZ consecutive planes, keeping the rows shared by
 // neighbouring planes (the z neighbours of the stencil) in registers, so a plane
@@ -1323,7 +1389,7 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
     }
     if constexpr (std::is_same<T, float>::value) {
       const int vw = G->tune_pred_vw > 0 ? G->tune_pred_vw : 4;
-      bool vec = G->nx % vw == 0;
+      bool vec = vw > 1 && G->nx % vw == 0;   // 1: the one-cell kernel
       for (int c = 0; c < 3; ++c) {
         vec = vec && (uintptr_t)uin[c] % (4 * vw) == 0 && (uintptr_t)out[c] % (4 * vw) == 0;
         if (un) vec = vec && (uintptr_t)un[c] % (4 * vw) == 0;
@@ -1395,6 +1461,21 @@ void launch_predictor(fs_grid* G, T* const* uin, T* const* un, T* const* out, do
     else
       launch_pdl(G, "predictor", predictor3_kernel<T, false>, grd, blk, 0, A);
     return;
+  }
+  if constexpr (std::is_same<T, float>::value) {
+    if (G->dim == 2 && G->per[0] && G->per[1] && G->conv == FS_CENTRAL2 && !G->has_body && G->nx % 4 == 0 &&
+        G->tune_pred_vw != 1) {
+      bool vec = true;
+      for (int c = 0; c < 2; ++c) {
+        vec = vec && (uintptr_t)uin[c] % 16 == 0 && (uintptr_t)out[c] % 16 == 0;
+        if (un) vec = vec && (uintptr_t)un[c] % 16 == 0;
+      }
+      if (vec) {
+        const dim3 vb(32, 8), vg((G->nx / 4 + 31) / 32, (G->ny + 7) / 8);
+        launch_pdl(G, "predictor", predictor2v_kernel<4>, vg, vb, 0, A);
+        return;
+      }
+    }
   }
   launch_pdl(G, "predictor", predictor_kernel<T>, grd, blk, 0, A);
 }

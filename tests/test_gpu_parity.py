@@ -510,3 +510,47 @@ def test_split_two_stream_poisson_matches_single_stream(precision):
     assert all(torch.equal(x, y) for x, y in zip(a["u"], b["u"]))
     st, _, _ = run_oracle(wl, 3)
     assert field_err(a["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+@pytest.mark.parametrize("scheme", ["fe", "rk3"])
+@pytest.mark.parametrize("n", [(64, 48), (36, 20)])
+def test_2d_periodic_four_cell_predictor_mixed(n, scheme):
+    """The four-cell 2-D predictor of fully periodic FP32 grids (a row of 36 cells: a partial
+    warp) against the FP64 oracle over steps, and against the one-cell kernel it replaces."""
+    wl = S.box_2d(n[0], n[1], (P, P), (P, P), Lx=1.3, nu=0.02)
+    wl.scheme = scheme
+    wl.dt = 0.002
+    wl.body_force = np.linspace(0.2, 0.8, n[1])
+    wl.u0 = S.random_fields(wl, 7, 1.0)
+    st, _, _ = run_oracle(wl, 6)
+    a = run_gpu(wl, 6, precision="mixed")
+    b = run_gpu(wl, 6, precision="mixed", tuning=[("predictor_cells", 1)])
+    assert field_err(a["u"], st.u) < TOLMIX
+    assert field_err(a["u"], b["u"]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("make", [
+    lambda: S.box_3d(16, 24, 8, (P, P), (P, P)),                     # cyclic y
+    lambda: S.box_3d(16, 24, 8, (P, P), (NS, NS), stretched=1.3),    # walls, stretched y
+])
+def test_twisted_pressure_gauge(make, precision):
+    """The twisted y solve sets the zero mode's gauge (zero hy-weighted mean, the oracle's) in the
+    solve whose pressure is written out, and only there: the written pressure matches the
+    oracle's, and the velocity does not depend on whether the pressure was asked for (the stage
+    solves keep the factorisation's gauge, which the pressure gradient does not see)."""
+    wl = make()
+    wl.dt = 0.002
+    wl.u0 = S.random_fields(wl, 5, 1.0)
+    tune = [("ysolve_twisted", 1)] + ([("y_spectral", 0)] if wl.bc[1][0] == P else [])
+    a = run_gpu(wl, 4, precision=precision, want_p=True, tuning=tune)
+    b = run_gpu(wl, 4, precision=precision, tuning=tune)
+    st, dg, g = run_oracle(wl, 4)
+    fp64 = precision == "fp64"
+    assert field_err(a["u"], st.u) < (TOL64 if fp64 else TOLMIX)
+    assert field_err(a["u"], b["u"]) < (1e-13 if fp64 else 1e-6)
+    p_or = dg.phi * g.rho / wl.dt
+    # FP32 fields: the pressure carries the FP32 rounding of u* through the solve; a wrong gauge
+    # would be off by the column's mean, O(1) of max |p|
+    tol = 1e-9 if fp64 else 1e-4
+    assert float((a["p"] - p_or).abs().max()) < tol * float(p_or.abs().max())
