@@ -1,4 +1,4 @@
-// Register-resident FFT kernels for the transform lengths 64, 128 and 256
+// Register-resident FFT kernels for the transform lengths 64, 128, 256 and 512
 // (included by poisson.cu inside its anonymous namespace; uses cplx, cmul,
 // DivArgs, div_at, div4_at, YSpecArgs and lam_index_spec from there).
 //
@@ -8,7 +8,7 @@
 //   pass 1: thread t takes x[t + TPL m], m < R1, forms the R1-point DFT over m
 //           and multiplies entry q by W_N^{t q};
 //   pass 2: for each q, the TPL-point DFT over t gives X[q + R1 s], s < TPL.
-// The small DFTs (4, 8, 16 points) are straight-line code with constant
+// The small DFTs (4, 8, 16, 32 points) are straight-line code with constant
 // twiddles.  Lines live in shared memory with one pad element every R1 entries
 // so that both passes are free of bank conflicts.  Each block holds kRegLines
 // lines; kRegLines * TPL of its threads run the transform (a line never spans
@@ -30,6 +30,10 @@ struct RegPlan<128> {
 template <>
 struct RegPlan<256> {
   static constexpr int R1 = 16, TPL = 16;
+};
+template <>
+struct RegPlan<512> {
+  static constexpr int R1 = 32, TPL = 16;   // pass 2: two 16-point DFTs per thread
 };
 
 constexpr int kRegLines = 16;
@@ -139,10 +143,45 @@ __device__ __forceinline__ void dft16(cplx<T>* v) {
   }
 }
 
+// cos and sin of pi/16 and 3 pi/16
+constexpr double kC16 = 0.98078528040323044913, kS16 = 0.19509032201612826785;
+constexpr double kC316 = 0.83146961230254523708, kS316 = 0.55557023301960222474;
+
+// exp(-+ 2 pi i k / 32), k < 16
+template <typename T, bool INV>
+__device__ __forceinline__ cplx<T> w32(int k) {
+  const T sg = INV ? T(1) : T(-1);
+  const double c[16] = {1.0,  kC16,   kC8,  kC316,  kR2,  kS316,  kS8,  kS16,
+                        0.0, -kS16, -kS8, -kS316, -kR2, -kC316, -kC8, -kC16};
+  const double s[16] = {0.0, kS16, kS8, kS316, kR2, kC316, kC8, kC16,
+                        1.0, kC16, kC8, kC316, kR2, kS316, kS8, kS16};
+  return {T(c[k]), sg * T(s[k])};
+}
+
+// 32 points: the 16-point DFTs of the even and odd entries, combined (radix 2)
+template <typename T, bool INV>
+__device__ __forceinline__ void dft32(cplx<T>* v) {
+  cplx<T> e[16], o[16];
+#pragma unroll
+  for (int n = 0; n < 16; ++n) {
+    e[n] = v[2 * n];
+    o[n] = v[2 * n + 1];
+  }
+  dft16<T, INV>(e);
+  dft16<T, INV>(o);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const cplx<T> t = k == 0 ? o[0] : cmul(o[k], w32<T, INV>(k));
+    v[k] = cadd(e[k], t);
+    v[k + 16] = csub(e[k], t);
+  }
+}
+
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void dft_small(cplx<T>* v) {
   if constexpr (R == 8) dft8<T, INV>(v);
-  else dft16<T, INV>(v);
+  else if constexpr (R == 16) dft16<T, INV>(v);
+  else dft32<T, INV>(v);
 }
 
 // Transform the line L (padded layout) in place with the TPL threads t of its

@@ -554,3 +554,20 @@ def test_twisted_pressure_gauge(make, precision):
     # would be off by the column's mean, O(1) of max |p|
     tol = 1e-9 if fp64 else 1e-4
     assert float((a["p"] - p_or).abs().max()) < tol * float(p_or.abs().max())
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("make", [
+    lambda: S.box_3d(512, 6, 4, (P, P), (NS, NS), stretched=1.2),     # x: 512-point register DFT
+    lambda: S.box_3d(8, 6, 512, (P, P), (NS, NS), L=(1.0, 1.0, 4.0)),  # z: 512 points
+    lambda: S.box_3d(8, 512, 4, (P, P), (P, P), L=(1.0, 4.0, 1.0)),    # y spectral: 512 points
+])
+def test_register_fft_512(make, precision):
+    """The 512-point register transforms (a 32-point first pass, two 16-point DFTs per thread in
+    the second) in every direction, through whole steps against the FP64 oracle."""
+    wl = make()
+    wl.dt = 0.001
+    wl.u0 = S.random_fields(wl, 9, 1.0)
+    gp = run_gpu(wl, 3, precision=precision)
+    st, _, _ = run_oracle(wl, 3)
+    assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
