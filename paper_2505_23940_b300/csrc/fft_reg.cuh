@@ -1,4 +1,4 @@
-// Register-resident FFT kernels for the transform lengths 64, 128, 256 and 512
+// Register-resident FFT kernels for the transform lengths 64, 128, 256, 384 and 512
 // (included by poisson.cu inside its anonymous namespace; uses cplx, cmul,
 // DivArgs, div_at, div4_at, YSpecArgs and lam_index_spec from there).
 //
@@ -9,7 +9,8 @@
 //           and multiplies entry q by W_N^{t q};
 //   pass 2: for each q, the TPL-point DFT over t gives X[q + R1 s], s < TPL.
 // The small DFTs (4, 8, 16, 32 points) are straight-line code with constant
-// twiddles.  Lines live in shared memory with one pad element every R1 entries
+// twiddles; the 48-point first pass of N = 384 is three 16-point DFTs and
+// sixteen 3-point DFTs, its twiddles read from the line's table.  Lines live in shared memory with one pad element every R1 entries
 // so that both passes are free of bank conflicts.  Each block holds kRegLines
 // lines; kRegLines * TPL of its threads run the transform (a line never spans
 // two warps, so the exchange needs only __syncwarp) and all kRegBlock threads
@@ -30,6 +31,10 @@ struct RegPlan<128> {
 template <>
 struct RegPlan<256> {
   static constexpr int R1 = 16, TPL = 16;
+};
+template <>
+struct RegPlan<384> {
+  static constexpr int R1 = 48, TPL = 8;    // pass 2: six 8-point DFTs per thread
 };
 template <>
 struct RegPlan<512> {
@@ -177,6 +182,47 @@ __device__ __forceinline__ void dft32(cplx<T>* v) {
   }
 }
 
+// 3 points: y0 = a0 + a1 + a2, y1,2 = a0 - (a1 + a2) / 2 -+ i sqrt(3)/2 (a1 - a2) (forward)
+constexpr double kR3h = 0.86602540378443864676;   // sqrt(3) / 2
+template <typename T, bool INV>
+__device__ __forceinline__ void dft3(cplx<T>& a0, cplx<T>& a1, cplx<T>& a2) {
+  const cplx<T> s = cadd(a1, a2), d = csub(a1, a2);
+  const cplx<T> t = {a0.x - T(0.5) * s.x, a0.y - T(0.5) * s.y};
+  const cplx<T> m0 = mul_mi<T, INV>(d);
+  const cplx<T> m = {T(kR3h) * m0.x, T(kR3h) * m0.y};
+  a0 = cadd(a0, s);
+  a1 = cadd(t, m);
+  a2 = csub(t, m);
+}
+
+// 48 points (n = 3 n1 + n2, k = k1 + 16 k2): 16-point DFTs over n1, twiddles W_48^{n2 k1}
+// (entries st * n2 * k1 of the line's table, st = N / 48), 3-point DFTs over n2
+template <typename T, bool INV>
+__device__ __forceinline__ void dft48(cplx<T>* v, const cplx<T>* __restrict__ tws, int st) {
+  cplx<T> a[3][16];
+#pragma unroll
+  for (int n2 = 0; n2 < 3; ++n2) {
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) a[n2][n1] = v[3 * n1 + n2];
+    dft16<T, INV>(a[n2]);
+  }
+#pragma unroll
+  for (int n2 = 1; n2 < 3; ++n2)
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) {
+      cplx<T> w = tws[st * n2 * k1];
+      if (INV) w.y = -w.y;
+      a[n2][k1] = cmul(a[n2][k1], w);
+    }
+#pragma unroll
+  for (int k1 = 0; k1 < 16; ++k1) {
+    dft3<T, INV>(a[0][k1], a[1][k1], a[2][k1]);
+    v[k1] = a[0][k1];
+    v[k1 + 16] = a[1][k1];
+    v[k1 + 32] = a[2][k1];
+  }
+}
+
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void dft_small(cplx<T>* v) {
   if constexpr (R == 8) dft8<T, INV>(v);
@@ -192,7 +238,8 @@ __device__ __forceinline__ void fft_reg_line(cplx<T>* L, int t, const cplx<T>* _
   cplx<T> v[R1];
 #pragma unroll
   for (int m = 0; m < R1; ++m) v[m] = L[rpad<N>(t + TPL * m)];
-  dft_small<T, R1, INV>(v);
+  if constexpr (R1 == 48) dft48<T, INV>(v, tws, N / 48);
+  else dft_small<T, R1, INV>(v);
 #pragma unroll
   for (int q = 1; q < R1; ++q) {
     cplx<T> w = tws[t * q];

@@ -1600,7 +1600,7 @@ void set_smem_attrs_reg() {
   cudaFuncSetAttribute(yspec_reg_kernel<T, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
-bool is_reg_length(int n) { return n == 64 || n == 128 || n == 256 || n == 512; }
+bool is_reg_length(int n) { return n == 64 || n == 128 || n == 256 || n == 384 || n == 512; }
 
 // Lines per block of the mixed-radix x transforms: up to 16, fewer when the
 // grid has too few lines to give every SM two blocks (2-D grids).
@@ -1655,6 +1655,7 @@ void with_reg_length(int n, F&& f) {
   if (n == 64) f(RegLaunch<T, 64>());
   else if (n == 128) f(RegLaunch<T, 128>());
   else if (n == 256) f(RegLaunch<T, 256>());
+  else if (n == 384) f(RegLaunch<T, 384>());
   else f(RegLaunch<T, 512>());
 }
 
@@ -1665,6 +1666,7 @@ void set_smem_attrs() {
   set_smem_attrs_reg<T, 64>();
   set_smem_attrs_reg<T, 128>();
   set_smem_attrs_reg<T, 256>();
+  set_smem_attrs_reg<T, 384>();
   set_smem_attrs_reg<T, 512>();
   set_smem_attrs_plan<T, 0>();
   set_smem_attrs_plan<T, 1>();

@@ -557,15 +557,18 @@ def test_twisted_pressure_gauge(make, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("make", [
-    lambda: S.box_3d(512, 6, 4, (P, P), (NS, NS), stretched=1.2),     # x: 512-point register DFT
-    lambda: S.box_3d(8, 6, 512, (P, P), (NS, NS), L=(1.0, 1.0, 4.0)),  # z: 512 points
-    lambda: S.box_3d(8, 512, 4, (P, P), (P, P), L=(1.0, 4.0, 1.0)),    # y spectral: 512 points
-])
-def test_register_fft_512(make, precision):
-    """The 512-point register transforms (a 32-point first pass, two 16-point DFTs per thread in
-    the second) in every direction, through whole steps against the FP64 oracle."""
-    wl = make()
+@pytest.mark.parametrize("axis", ["x", "z", "y"])
+@pytest.mark.parametrize("n", [384, 512])
+def test_register_fft_384_512(n, axis, precision):
+    """The 384- and 512-point register transforms (first pass: three 16-point and sixteen 3-point
+    DFTs, or two 16-point DFTs and a radix-2 step; second pass: 8- or 16-point DFTs) along x, z
+    and the spectral y, through whole steps against the FP64 oracle."""
+    if axis == "x":
+        wl = S.box_3d(n, 6, 4, (P, P), (NS, NS), stretched=1.2)
+    elif axis == "z":
+        wl = S.box_3d(8, 6, n, (P, P), (NS, NS), L=(1.0, 1.0, 4.0))
+    else:
+        wl = S.box_3d(8, n, 4, (P, P), (P, P), L=(1.0, 4.0, 1.0))
     wl.dt = 0.001
     wl.u0 = S.random_fields(wl, 9, 1.0)
     gp = run_gpu(wl, 3, precision=precision)
