@@ -43,6 +43,9 @@ struct RegPlan<512> {
 
 constexpr int kRegLines = 16;
 constexpr int kRegBlock = 256;
+// the 384- and 512-point kernels are held to two blocks per SM (at most 128 registers)
+template <int N>
+constexpr int kRegMinBlocks = N >= 384 ? 2 : 1;
 
 // Line pitch: the padded length plus one, so that the 16 lines of a block start
 // in 16 different bank pairs (2 * pitch = 2 mod 32 words up to a multiple of 16):
@@ -344,7 +347,7 @@ __device__ __forceinline__ void store_pair_tile(T* __restrict__ base, size_t rs,
 // ---------------------------------------------------------------------------
 // x forward (see xfwd_kernel): rows of length N, two rows per complex line.
 template <typename T, int N, bool DIV>
-__global__ void __launch_bounds__(kRegBlock) xfwd_reg_kernel(T* __restrict__ data, int rows, int mode,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T* __restrict__ data, int rows, int mode,
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
   pdl_wait();
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(kRegBlock) xfwd_reg_kernel(T* __restrict__ dat
 
 // x inverse (see xinv_kernel)
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw) {
   pdl_wait();
@@ -560,7 +563,7 @@ __global__ void __launch_bounds__(kRegBlock) xinv_reg_kernel(T* __restrict__ dat
 
 // z forward (see zfwd_kernel): complex lines of slot pairs along z at one y row.
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
   constexpr int P = rpitch<N>();
@@ -594,7 +597,7 @@ __global__ void __launch_bounds__(kRegBlock) zfwd_reg_kernel(T* __restrict__ dat
 // slots 0 and 1; the first block stages that line in a scratch line and
 // rebuilds Z = Y0 + i Y1 into line 0.
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
   constexpr int P = rpitch<N>();
@@ -649,7 +652,7 @@ __global__ void __launch_bounds__(kRegBlock) zinv_reg_kernel(T* __restrict__ dat
 
 // Periodic y (see yspec_kernel): y DFT of slot pairs, eigenvalue division, inverse DFT.
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegBlock) yspec_reg_kernel(T* __restrict__ data, const YSpecArgs A,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(T* __restrict__ data, const YSpecArgs A,
                                                             const cplx<T>* __restrict__ tw,
                                                             const T* __restrict__ lamy,
                                                             const T* __restrict__ lamxz) {
