@@ -1402,8 +1402,8 @@ __device__ __forceinline__ int lam_index_spec(const YSpecArgs& A, int s, int t) 
   return min(l, A.nz - l) * A.nmx + mx;
 }
 
-template <typename T, int PL>
-__global__ void __launch_bounds__(256) yspec_kernel(T* __restrict__ data, const YSpecArgs A, Radices rad,
+template <typename T, int PL, int NT = 256>
+__global__ void __launch_bounds__(NT) yspec_kernel(T* __restrict__ data, const YSpecArgs A, Radices rad,
                                                     const cplx<T>* __restrict__ tw, const T* __restrict__ lamy,
                                                     const T* __restrict__ lamxz) {
   extern __shared__ unsigned char smem_raw[];
@@ -1526,6 +1526,8 @@ void set_smem_attrs_plan() {
   cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
+  if constexpr (PL == 0)
+    cudaFuncSetAttribute(yspec_kernel<T, 0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
 }
 
 // Kernel instances by plan: compile-time lengths first, generic plans otherwise.
@@ -1889,7 +1891,14 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
       A.spb = spb;
       dim3 grid((nx + spb - 1) / spb, G->dim == 3 ? nz : 1);
       auto k = fft_kernels<T>(G->py).yspec;
-      FS_LAUNCH(G, "fft_y_solve", k<<<grid, 256, (size_t)(spb / 2) * line_bytes, G->stream>>>(
+      // long columns (a few lines per block, one block per SM): 1024 threads instead of 256 keep
+      // more butterflies of each stage in flight (radices up to 5)
+      int nt = 256;
+      if (k == yspec_kernel<T, 0> && spb <= 8) {
+        k = yspec_kernel<T, 0, 1024>;
+        nt = 1024;
+      }
+      FS_LAUNCH(G, "fft_y_solve", k<<<grid, nt, (size_t)(spb / 2) * line_bytes, G->stream>>>(
                                       data, A, radices_of(G->py), (const cplx<T>*)G->py.tw, (const T*)G->lamy,
                                       (const T*)G->lamxz));
     } else if (G->ytwist) {

@@ -574,3 +574,16 @@ def test_register_fft_384_512(n, axis, precision):
     gp = run_gpu(wl, 3, precision=precision)
     st, _, _ = run_oracle(wl, 3)
     assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+@pytest.mark.parametrize("precision,ny", [("mixed", 4096), ("fp64", 2000), ("mixed", 2000)])
+def test_long_periodic_y_spectral(precision, ny):
+    """Periodic y transformed by the mixed-radix kernels on long columns (a few lines per block:
+    1024 threads per block where the block holds at most four lines) against the FP64 oracle."""
+    # square cells of h = 8 / ny; |u| <= 1, CFL <= 0.1 and nu dt / h^2 <= 0.01 (stable steps)
+    wl = S.box_2d(16, ny, (P, P), (P, P), Lx=16 * 8.0 / ny, Ly=8.0, nu=1e-4)
+    wl.dt = 0.0002
+    wl.u0 = S.random_fields(wl, 4, 1.0)
+    gp = run_gpu(wl, 3, precision=precision)
+    st, _, _ = run_oracle(wl, 3)
+    assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
