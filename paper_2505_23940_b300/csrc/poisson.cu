@@ -1520,14 +1520,17 @@ constexpr size_t kYSpecBudget = 200 * 1024;
 template <typename T, int PL>
 void set_smem_attrs_plan() {
   const int zb = (int)(PL >= 2 ? kFixedBudget : kSmemBudget);
-  cudaFuncSetAttribute(xfwd_kernel<T, PL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(xfwd_kernel<T, PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
-  cudaFuncSetAttribute(xinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBudget);
+  // (x lines are sized against kSmemBudget; a single line longer than that, FP64 rows beyond 3072
+  // points, takes up to kFixedBudget)
+  cudaFuncSetAttribute(xfwd_kernel<T, PL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+  cudaFuncSetAttribute(xfwd_kernel<T, PL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+  cudaFuncSetAttribute(xinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
   cudaFuncSetAttribute(zfwd_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   cudaFuncSetAttribute(zinv_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
-  if constexpr (PL == 0)
+  if constexpr (PL == 0) {
     cudaFuncSetAttribute(yspec_kernel<T, 0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
+  }
 }
 
 // Kernel instances by plan: compile-time lengths first, generic plans otherwise.
