@@ -1530,6 +1530,9 @@ void set_smem_attrs_plan() {
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
   if constexpr (PL == 0) {
     cudaFuncSetAttribute(yspec_kernel<T, 0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
+    cudaFuncSetAttribute(xfwd_kernel<T, 4096, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xfwd_kernel<T, 4096, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xinv_kernel<T, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
   }
 }
 
@@ -1592,6 +1595,21 @@ FftKernels<T> fft_kernels(const Plan1D& p) {
   for (int i = 0; i < p.nst; ++i)
     if (p.radix[i] > 5) return fft_kernels_of<T, 1>();
   return fft_kernels_of<T, 0>();
+}
+
+// x rows of 4096 points (2-D grids) take a compile-time plan for the x transforms alone (one
+// line per block; the z and y kernels of that length, which stage 16 lines, are not built)
+constexpr int kXLong = 4096;
+template <typename T>
+FftKernels<T> fft_kernels_x(const Plan1D& p) {
+  if (p.n == kXLong) {
+    FftKernels<T> K = fft_kernels_of<T, 0>();
+    K.xfwd = xfwd_kernel<T, kXLong, false>;
+    K.xfwd_div = xfwd_kernel<T, kXLong, true>;
+    K.xinv = xinv_kernel<T, kXLong>;
+    return K;
+  }
+  return fft_kernels<T>(p);
 }
 
 template <typename T, int N>
@@ -1814,7 +1832,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : default_lines(lines);
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int nb = (lines + lpb - 1) / lpb;
-    const FftKernels<T> K = fft_kernels<T>(G->px);
+    const FftKernels<T> K = fft_kernels_x<T>(G->px);
     auto k = dv ? K.xfwd_div : K.xfwd;
     const DivArgs<T> none{};
     FS_LAUNCH(G, dv ? "fft_x_fwd_div" : "fft_x_fwd",
@@ -1961,7 +1979,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
     const int want = G->tune_fft_lines > 0 ? G->tune_fft_lines : default_lines(lines);
     lpb = lpb > want ? want : (lpb < 1 ? 1 : lpb);
     const int nb = (lines + lpb - 1) / lpb;
-    auto k = fft_kernels<T>(G->px).xinv;
+    auto k = fft_kernels_x<T>(G->px).xinv;
     FS_LAUNCH(G, "fft_x_inv", k<<<nb, 256, fft_smem_bytes<T>(nx, lpb), G->stream>>>(data, nx, rows, lpb, G->xmode, radices_of(G->px),
                                                           (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw));
   }

@@ -590,11 +590,13 @@ def test_long_periodic_y_spectral(precision, ny):
 
 
 @pytest.mark.parametrize("precision,nx,bcx", [("mixed", 4096, (P, P)), ("fp64", 4096, (P, P)),
-                                              ("fp64", 2000, (IN, OUT)), ("mixed", 2000, (IN, OUT))])
+                                              ("fp64", 4096, (IN, OUT)), ("fp64", 2000, (IN, OUT)),
+                                              ("mixed", 2000, (IN, OUT))])
 def test_long_x_lines(precision, nx, bcx):
-    """x transforms of long rows by the mixed-radix kernels with one line per block (FP64 rows of
-    4096 points: one line beyond the usual shared-memory budget): the periodic DFT with the
-    divergence fused, and the DCT-II of an inflow/outflow channel, against the FP64 oracle."""
+    """x transforms of long rows with one line per block (4096 points: the compile-time plan of the
+    x transforms; FP64: one line beyond the usual shared-memory budget; 2000 points: the runtime
+    plan): the periodic DFT with the divergence fused, and the DCT-II of an inflow/outflow
+    channel, against the FP64 oracle."""
     h = 1.0 / 256
     bcy = (NS, NS) if bcx == (P, P) else (FS, FS)
     bc_val = None if bcx == (P, P) else [[[1.0, 0, 0], [0, 0, 0]], [[0, 0, 0], [0, 0, 0]]]
