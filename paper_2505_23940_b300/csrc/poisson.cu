@@ -1407,6 +1407,9 @@ __global__ void __launch_bounds__(NT) yspec_kernel(T* __restrict__ data, const Y
                                                     const cplx<T>* __restrict__ tw, const T* __restrict__ lamy,
                                                     const T* __restrict__ lamxz) {
   extern __shared__ unsigned char smem_raw[];
+  // compile-time lengths up to 640 move 32-slot tiles (spb == 32); 4096 (a few lines per block)
+  // moves its slots with the generic loops
+  constexpr bool TILE32 = PL >= 2 && PL <= 640;
   const int N = PL >= 2 ? PL : A.ny;
   const int P = N + 1;                          // padded line pitch
   cplx<T>* B0 = reinterpret_cast<cplx<T>*>(smem_raw);
@@ -1419,7 +1422,7 @@ __global__ void __launch_bounds__(NT) yspec_kernel(T* __restrict__ data, const Y
   const size_t rs = (size_t)A.nx;
   if (ns & 1)   // odd tail: the missing partner slot is zero
     for (int j = threadIdx.x; j < N; j += blockDim.x) B0[(nl - 1) * P + j].y = T(0);
-  if constexpr (PL >= 2) {
+  if constexpr (TILE32) {
     // spb == 32: thread = (slot c, rows j0 + 8 q)
     const int c = threadIdx.x & 31, j0 = threadIdx.x >> 5;
     if (c < ns) {
@@ -1474,7 +1477,7 @@ __global__ void __launch_bounds__(NT) yspec_kernel(T* __restrict__ data, const Y
   __syncthreads();
   cplx<T>* W = fft_any<T, PL>(Z, Z == B0 ? B1 : B0, N, P, nl, rad, tw, true);
   const T inv_n = T(1) / T(N);
-  if constexpr (PL >= 2) {
+  if constexpr (TILE32) {
     const int c = threadIdx.x & 31, j0 = threadIdx.x >> 5;
     if (c < ns) {
 #pragma unroll 4
@@ -1530,6 +1533,7 @@ void set_smem_attrs_plan() {
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
   if constexpr (PL == 0) {
     cudaFuncSetAttribute(yspec_kernel<T, 0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
+    cudaFuncSetAttribute(yspec_kernel<T, 4096, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
     cudaFuncSetAttribute(xfwd_kernel<T, 4096, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xfwd_kernel<T, 4096, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xinv_kernel<T, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
@@ -1597,8 +1601,9 @@ FftKernels<T> fft_kernels(const Plan1D& p) {
   return fft_kernels_of<T, 0>();
 }
 
-// x rows of 4096 points (2-D grids) take a compile-time plan for the x transforms alone (one
-// line per block; the z and y kernels of that length, which stage 16 lines, are not built)
+// Rows and periodic-y columns of 4096 points (2-D grids) take a compile-time plan in the x
+// transforms (one line per block) and in the 1024-thread periodic-y kernel (a few lines per block);
+// the 16-line z and y kernels of that length are not built
 constexpr int kXLong = 4096;
 template <typename T>
 FftKernels<T> fft_kernels_x(const Plan1D& p) {
@@ -1916,7 +1921,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
       // more butterflies of each stage in flight (radices up to 5)
       int nt = 256;
       if (k == yspec_kernel<T, 0> && spb <= 8) {
-        k = yspec_kernel<T, 0, 1024>;
+        k = ny == kXLong ? yspec_kernel<T, kXLong, 1024> : yspec_kernel<T, 0, 1024>;   // 4096: compile-time plan
         nt = 1024;
       }
       FS_LAUNCH(G, "fft_y_solve", k<<<grid, nt, (size_t)(spb / 2) * line_bytes, G->stream>>>(
