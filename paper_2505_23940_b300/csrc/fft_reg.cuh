@@ -43,9 +43,13 @@ struct RegPlan<512> {
 
 constexpr int kRegLines = 16;
 constexpr int kRegBlock = 256;
-// the 384- and 512-point kernels are held to two blocks per SM (at most 128 registers)
+// the 384- and 512-point kernels are held to two blocks per SM (at most 128 registers), the
+// shorter ones to four (64 registers: 512 blocks of a 128^3 transform in one wave of 148 x 4)
 template <int N>
-constexpr int kRegMinBlocks = N >= 384 ? 2 : 1;
+constexpr int kRegMinBlocks = N >= 384 ? 2 : 4;
+// the inverse x transform (real-packed or DCT output: more live values) of 256 points: three
+template <int N>
+constexpr int kRegMinBlocksXinv = N >= 384 ? 2 : (N >= 256 ? 3 : 4);
 
 // Line pitch: the padded length plus one, so that the 16 lines of a block start
 // in 16 different bank pairs (2 * pitch = 2 mod 32 words up to a multiple of 16):
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
 
 // x inverse (see xinv_kernel)
 template <typename T, int N>
-__global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
+__global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kernel(T* __restrict__ data, int rows, int mode,
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw) {
   pdl_wait();
