@@ -1537,6 +1537,9 @@ void set_smem_attrs_plan() {
     cudaFuncSetAttribute(xfwd_kernel<T, 4096, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xfwd_kernel<T, 4096, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xinv_kernel<T, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xfwd_kernel<T, 5760, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xfwd_kernel<T, 5760, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xinv_kernel<T, 5760>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
   }
 }
 
@@ -1601,19 +1604,23 @@ FftKernels<T> fft_kernels(const Plan1D& p) {
   return fft_kernels_of<T, 0>();
 }
 
-// Rows and periodic-y columns of 4096 points (2-D grids) take a compile-time plan in the x
-// transforms (one line per block) and in the 1024-thread periodic-y kernel (a few lines per block);
-// the 16-line z and y kernels of that length are not built
+// Rows of 4096 and 5760 points and periodic-y columns of 4096 points (2-D grids) take a
+// compile-time plan in the x transforms (one line per block) and in the 1024-thread periodic-y
+// kernel (a few lines per block); the 16-line z and y kernels of those lengths are not built
 constexpr int kXLong = 4096;
+constexpr int kXLong2 = 5760;   // 2^7 3^2 5: the rows of the 2-D cylinder-array workload
+template <typename T, int N>
+FftKernels<T> fft_kernels_xlong() {
+  FftKernels<T> K = fft_kernels_of<T, 0>();
+  K.xfwd = xfwd_kernel<T, N, false>;
+  K.xfwd_div = xfwd_kernel<T, N, true>;
+  K.xinv = xinv_kernel<T, N>;
+  return K;
+}
 template <typename T>
 FftKernels<T> fft_kernels_x(const Plan1D& p) {
-  if (p.n == kXLong) {
-    FftKernels<T> K = fft_kernels_of<T, 0>();
-    K.xfwd = xfwd_kernel<T, kXLong, false>;
-    K.xfwd_div = xfwd_kernel<T, kXLong, true>;
-    K.xinv = xinv_kernel<T, kXLong>;
-    return K;
-  }
+  if (p.n == kXLong) return fft_kernels_xlong<T, kXLong>();
+  if (p.n == kXLong2) return fft_kernels_xlong<T, kXLong2>();
   return fft_kernels<T>(p);
 }
 
