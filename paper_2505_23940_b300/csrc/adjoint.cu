@@ -1013,7 +1013,11 @@ void launch_projection_adjoint_solve(fs_grid* G, T* const* lam, T* spec) {
   const dim3 blk = stencil_block(G), grd = stencil_grid(G, G->nx, G->ny);
   FS_LAUNCH(G, "adj_rhs", adj_rhs_kernel<T><<<grd, blk, 0, G->stream>>>(g, lam[0], lam[1], G->dim == 3 ? lam[2] : lam[1],
                                                                         G->hy64, spec));
+  // the adjoint uses the solution through its gradient and D^T (boundary faces are imposed), so
+  // the zero mode's gauge is not set
+  G->ygauge = false;
   poisson_solve_inplace<T>(G, spec);
+  G->ygauge = true;
 }
 
 // Fully periodic 3-D grids with central convection and no body: the gather
@@ -1040,7 +1044,9 @@ template <typename T>
 void launch_proj_adj_fast(fs_grid* G, T* const* lam, double a, double b, double dt, bool rk, double* bfsum,
                           T* const* la, T* const* ln) {
   T* spec = (T*)G->spec;
+  G->ygauge = false;   // only the gradient of the solution is used
   poisson_solve_from_velocity<T>(G, make_div_args<T>(G, lam, nullptr), spec);
+  G->ygauge = true;
   ProjAdjArgs<T> A;
   A.g = G->geom<T>();
   for (int c = 0; c < 3; ++c) {
