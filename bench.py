@@ -49,6 +49,7 @@ KERNEL_BYTES_PER_CELL = {
 # in L2 at kernel end are not counted; the predictor launch is an RK3 stage 2 or 3,
 # which also reads u^n), keyed by kernel with the hash of the source files it was
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
+NCU_WORKLOAD = "isotropic_3d_128"   # the workload the traffic below was captured on
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50361344 + 924416, "src": "4d5c344d8f7c"},
     "ysolve": {"bytes": 24119808 + 0, "src": "91361bff4f2b"},
@@ -180,6 +181,8 @@ def workload(name):
         return S.cylinder_2d(seed=2, perturb=0.01)
     if name == "cylinder_array_2d":
         return S.cylinder_array_2d()
+    if name.startswith("sweep_"):   # an HBM-sweep point ("sweep_384", "sweep_4096x4096")
+        return sweep_workload(name[len("sweep_"):])[0]
     if name == "rough_channel_3d_128":
         # the rough-wall case of the static-box stress leg at 128^3 (cubes of 4 cells every 6, both
         # walls, markers every h/2)
@@ -391,7 +394,7 @@ def run_ours(args, ws, rank, local):
         if name.startswith("predictor"):
             b = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
         ach = b * cells / (t / c * 1e-3) / 1e9 if (c and b) else None
-        tr = NCU_TRAFFIC.get(name)
+        tr = NCU_TRAFFIC.get(name) if args.workload == NCU_WORKLOAD else None
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak if ach else None,
                 "traffic": tr["bytes"] if tr and tr.get("src") == src_hash(name) else None,
@@ -409,7 +412,7 @@ def run_ours(args, ws, rank, local):
         # 1.06 TFLOP/s at 2032 MHz)
         flops = (2.0 if wl.bc[1][0] == S.PERIODIC else 0.0) + (4.0 if args.precision == "mixed" else 5.0)
         ach = flops * cells / (kms / cnt * 1e-3) / 1e12 if cnt else None
-        tr = NCU_TRAFFIC.get(dominant)
+        tr = NCU_TRAFFIC.get(dominant) if args.workload == NCU_WORKLOAD else None
         roofline = {"kernel": dominant, "bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s",
                     "frac": ach / 1.25 if ach else None,
                     "traffic": tr["bytes"] if tr and tr.get("src") == src_hash(dominant) else None,
@@ -976,13 +979,10 @@ def ib_stress_leg(stream, flush):
     return out
 
 
-def sweep_leg(spec, stream, flush):
-    """The RK3 step on a periodic grid whose working set exceeds L2: per-kernel times and the
-    predictor's achieved HBM bandwidth.  spec "n": n^3 (the isotropic field up to 256^3, uniform
+def sweep_workload(spec):
+    """The workload of one HBM-sweep point: spec "n": n^3 (the isotropic field up to 256^3, uniform
     random faces beyond, where the spectral generator costs minutes on the host); "AxB": a 2-D
-    A x B box with uniform random faces."""
-    from paper_2505_23940_b300 import grid_from_workload
-    dev = torch.device("cuda")
+    A x B periodic box with uniform random faces.  Returns (workload, [nx, ny, nz], field)."""
     if "x" in spec:
         nx, ny = (int(a) for a in spec.split("x"))
         wl = S.box_2d(nx, ny, (S.PERIODIC, S.PERIODIC), (S.PERIODIC, S.PERIODIC), Lx=2 * math.pi,
@@ -1002,6 +1002,15 @@ def sweep_leg(spec, stream, flush):
         wl.u0 = S.random_fields(wl, 5, 1.0)
         wl.scheme = "rk3"
         wl.dt = 0.25 * 2 * math.pi / dims[0]
+    return wl, dims, field
+
+
+def sweep_leg(spec, stream, flush):
+    """The RK3 step on a periodic grid whose working set exceeds L2 (`sweep_workload`): per-kernel
+    times and the predictor's achieved HBM bandwidth."""
+    from paper_2505_23940_b300 import grid_from_workload
+    dev = torch.device("cuda")
+    wl, dims, field = sweep_workload(spec)
     dim = wl.dim
     cells = dims[0] * dims[1] * dims[2]
     g = grid_from_workload(wl, "mixed", stream=stream)
@@ -1044,7 +1053,8 @@ def summary_of(line):
         return None if v is None else float("%.*g" % (d, v))
 
     out = {"fwd": r(line.get("value")), "ms_step": r(line.get("ms_per_step")),
-           "ysolve_frac": r((line.get("roofline") or {}).get("frac")),
+           ("ysolve_frac" if (line.get("roofline") or {}).get("kernel") == "ysolve" else "roofline_frac"):
+               r((line.get("roofline") or {}).get("frac")),
            "stencil_frac": r((line.get("stencil_roofline") or {}).get("frac"))}
     if "spectral_y" in line:
         out["spectral_y"] = r(line["spectral_y"]["value"])
