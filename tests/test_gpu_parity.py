@@ -2,7 +2,8 @@
 
 Tolerances: relative L2 over all velocity components <= 1e-11 for FP64 grids,
 <= 1e-5 for mixed-precision grids (FP32 stencils / transforms, FP64 tridiagonal,
-reductions and body ODE), as the north star of this hot path states."""
+reductions and body ODE): FP64 to the rounding of a few steps, mixed precision to the FP32
+rounding of the stencils and transforms, unless a test states a reason for another bound."""
 import math
 
 import numpy as np
