@@ -875,7 +875,7 @@ size_t ytwist_smem(int ny, int w) {
 constexpr int kTwBoxRows = 16;   // rows per tensor-map box of the twisted solve's tile (one chunk)
 
 template <typename T, bool CYC, int W>
-__global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A,
+__global__ void __launch_bounds__(4 * W, W == 32 ? 4 : 2) ytwist_kernel(T* __restrict__ data, const YTwArgs A,
                                                           const __grid_constant__ CUtensorMap tmap) {
   constexpr bool F32 = sizeof(T) == 4;
   constexpr int U = kTwU;
@@ -895,7 +895,10 @@ __global__ void __launch_bounds__(4 * W, 2) ytwist_kernel(T* __restrict__ data, 
   __shared__ uint64_t bulkbar[NB], widebar[NB], donebar[ND];
   __shared__ uint64_t stfree;                    // tiled FP32: the sweeps are done with the stage buffer
   __shared__ uint64_t sigbar;                    // FP32: sigma is staged
-  const int tid = threadIdx.x, lane = tid & 31;
+  // 32-column blocks: the sweep and helper warps trade places in every other block, so that
+  // the sweeps of neighbouring blocks on an SM sit on different sub-partitions (FP64 pipes)
+  const int tid = (W == 32 && ((blockIdx.x + blockIdx.y) & 1)) ? (int)(threadIdx.x ^ (2 * W)) : (int)threadIdx.x;
+  const int lane = tid & 31;
   const int s0 = (blockIdx.x + A.xblk0) * W;
   const int ncol = min(W, A.nx - s0);
   int t = 0;

@@ -230,7 +230,7 @@ def test_solve_pressure_twisted_fp64(wl):
     assert float((out[0] - out[1]).abs().max()) < 1e-11 * scale
 
 
-@pytest.mark.parametrize("tiled", [1, 0])
+@pytest.mark.parametrize("tiled", [1, 0, "cols32"])
 @pytest.mark.parametrize("make", [
     lambda: S.isotropic_3d(n=32, steps=5),
     lambda: S.box_3d(16, 24, 8, (P, P), (NS, NS), stretched=1.2),
@@ -255,7 +255,10 @@ def test_mixed_twisted_y_solve(make, tiled):
     if wl.bc[1][0] == P:
         G.set_tuning("y_spectral", 0)
     G.set_tuning("ysolve_twisted", 1)
-    G.set_tuning("ysolve_tiled", tiled)
+    if tiled == "cols32":   # 32-column blocks (sweep and helper warps trading places in every other block)
+        G.set_tuning("ysolve_twist_columns", 32)
+    else:
+        G.set_tuning("ysolve_tiled", tiled)
     u = [torch.tensor(np.asarray(a), dtype=torch.float32, device="cuda").contiguous() for a in wl.u0]
     G.step(u, wl.dt, n)
     torch.cuda.synchronize()
