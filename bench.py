@@ -52,7 +52,7 @@ KERNEL_BYTES_PER_CELL = {
 NCU_WORKLOAD = "isotropic_3d_128"   # the workload the traffic below was captured on
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50361344 + 924416, "src": "4d5c344d8f7c"},
-    "ysolve": {"bytes": 24119808 + 0, "src": "91361bff4f2b"},
+    "ysolve": {"bytes": 24118016 + 0, "src": "af343e7d574b"},
     "fft_x_fwd_div": {"bytes": 25243648 + 0, "src": "63900357a1f5"},
     "fft_z_fwd": {"bytes": 8407296 + 0, "src": "63900357a1f5"},
     "fft_z_inv": {"bytes": 8410880 + 0, "src": "63900357a1f5"},
