@@ -335,7 +335,8 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     tridiagonal solve per x/z wavenumber (rebuilds the y
  *                     tables; synchronises).  Same discrete solution.
  *   "ysolve_twisted"  FP64 tridiagonal y solve form: 1 twisted factorisation,
- *                     two threads per column (where ny <= 586); 0 the
+ *                     two threads per column (where ny <= 586, and on periodic
+ *                     y where ny is even; elsewhere the partitioned form); 0 the
  *                     partitioned form; -1 (default) twisted when the grid has
  *                     at least 148 * 64 columns (n_x n_z) and ny <= 292.
  *                     Rebuilds the y tables (synchronises the stream)
@@ -343,8 +344,8 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *                     (0, the default: 64 while a block fits an SM, ny <= 292,
  *                     else 32); rebuilds the y tables
  *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
- *                     least 32 rows as 16-row tensor-map boxes; 0: one bulk
- *                     copy per row
+ *                     least 32 rows as 16-row tensor-map boxes (not on walls
+ *                     with ny odd); 0: one bulk copy per row
  *   "ysplit"          1: on periodic-z grids whose twisted y solve has two or
  *                     more column blocks along x, the z transforms and the y
  *                     solve of the two halves of the x spectrum run as two

@@ -371,7 +371,8 @@ int build_tables(fs_grid* G) {
     // partitioned)
     G->ytw_cols = (size_t)(ny + 1) * 64 * 12 <= 220 * 1024 ? 64 : 32;
     if (G->tune_ytw_cols > 0) G->ytw_cols = G->tune_ytw_cols;
-    G->ytwist = L >= 4 && (size_t)(ny + 1) * G->ytw_cols * 12 <= 220 * 1024 && want;
+    // periodic y needs an odd chain (ny even): the lower thread's first slot holds the bordered row
+    G->ytwist = L >= 4 && (size_t)(ny + 1) * G->ytw_cols * 12 <= 220 * 1024 && want && !(G->cyclic && (ny & 1));
     if (G->ytwist) return build_twisted_tables(G, a, c);
   }
   const int NRED = 2 * NSEG;

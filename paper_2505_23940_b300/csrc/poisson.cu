@@ -1809,7 +1809,10 @@ void launch_ytwist(fs_grid* G, T* data, int xblk0, int nxblk) {
   CUtensorMap tmap;
   std::memset(&tmap, 0, sizeof(tmap));
   A.tiled = 0;
-  if (sizeof(T) == 4 && A.bulk && ny >= 2 * kTwBoxRows && ny <= 20 * kTwBoxRows && G->tune_ytile) {
+  // (odd chains on walls, ny odd, keep the row copies: the lower thread's first slot is then the
+  // inert one, and its first chunk no longer covers the bottom box's rows)
+  if (sizeof(T) == 4 && A.bulk && ny >= 2 * kTwBoxRows && ny <= 20 * kTwBoxRows && G->tune_ytile &&
+      !(!G->cyclic && (ny & 1))) {
     const int nzt = G->dim == 3 ? nz : 1;
     if (G->ytw_map_ptr != (const void*)data || G->ytw_map_w != w) {
       G->ytw_map_ok = encode_spectrum_map(reinterpret_cast<CUtensorMap*>(G->ytw_map), (const float*)data, nx, ny,

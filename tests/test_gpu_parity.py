@@ -614,3 +614,20 @@ def test_long_x_lines(precision, nx, bcx):
     # 640 points and 1.2e-5 at 2000 (the same with one or two lines per block)
     tol_mixed = 2.5e-5 * nx / 2000 if bcx != (P, P) else TOLMIX
     assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else tol_mixed)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("ny,bcy", [(37, (NS, NS)), (33, (NS, NS)), (25, (P, P))])
+def test_twisted_requested_on_odd_ny(precision, ny, bcy):
+    """The twisted y solve requested on odd ny: on walls it runs with row copies (the tensor-map
+    boxes assume the lower thread's first chunk covers the bottom box), on periodic y the
+    partitioned form takes over (the cyclic twisted form needs an odd chain, ny even)."""
+    wl = S.box_3d(16, ny, 4, (P, P), bcy, stretched=0.0 if bcy == (P, P) else 1.2)
+    wl.dt = 0.002
+    wl.u0 = S.random_fields(wl, 5, 1.0)
+    tune = [("ysolve_twisted", 1), ("ysolve_tiled", 1)] + ([("y_spectral", 0)] if bcy == (P, P) else [])
+    gp = run_gpu(wl, 3, precision=precision, tuning=tune)
+    st, _, _ = run_oracle(wl, 3)
+    assert gp["grid"].device_status() == 0
+    assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
+
