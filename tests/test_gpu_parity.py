@@ -631,3 +631,18 @@ def test_twisted_requested_on_odd_ny(precision, ny, bcy):
     assert gp["grid"].device_status() == 0
     assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
 
+
+
+@pytest.mark.parametrize("bcy", [(NS, NS), (P, P)])
+def test_twisted_mixed_long_columns(bcy):
+    """Mixed precision, the twisted y solve on 300-row columns: 32-column blocks (the sweep and
+    helper warps trading places in every other block), tensor-map tiles of 19 boxes, the scaled
+    outward pass; walls (stretched) and periodic y, against the FP64 oracle."""
+    wl = S.box_3d(16, 300, 4, (P, P), bcy, stretched=1.1 if bcy == (NS, NS) else 0.0, L=(1.0, 3.0, 1.0))
+    wl.dt = 0.001
+    wl.u0 = S.random_fields(wl, 8, 1.0)
+    tune = [("ysolve_twisted", 1)] + ([("y_spectral", 0)] if bcy == (P, P) else [])
+    gp = run_gpu(wl, 3, precision="mixed", tuning=tune)
+    st, _, _ = run_oracle(wl, 3)
+    assert gp["grid"].device_status() == 0
+    assert field_err(gp["u"], st.u) < TOLMIX
