@@ -1126,6 +1126,7 @@ template <typename T>
 __global__ void outflow_scale_kernel(const T* __restrict__ u0, int ex, int ny, int nz, const double* __restrict__ hy,
                                      double hz, double q_in, double* scale) {
   __shared__ double sh[kThreads];
+  pdl_wait();
   double s = 0.0;
   for (int t = threadIdx.x; t < ny * nz; t += blockDim.x) {
     const int j = t % ny, k = t / ny;
@@ -1490,8 +1491,8 @@ void launch_outflow_flux(fs_grid* G, T* const* uin) {
     area *= (G->dim == 3 ? G->hz * G->nz : 1.0);
     q_in = G->bcv[0][0][0] * area;
   }
-  FS_LAUNCH(G, "outflow_scale", outflow_scale_kernel<T><<<1, kThreads, 0, G->stream>>>(uin[0], G->nx + 1, G->ny, G->nz, G->hy64,
-                                                         G->dim == 3 ? G->hz : 1.0, q_in, G->scal));
+  launch_pdl(G, "outflow_scale", outflow_scale_kernel<T>, dim3(1), dim3(kThreads), 0, (const T*)uin[0], G->nx + 1,
+             G->ny, G->nz, (const double*)G->hy64, G->dim == 3 ? G->hz : 1.0, q_in, (double*)G->scal);
 }
 
 template <typename T>
