@@ -39,10 +39,26 @@ import synthetic as S  # noqa: E402
 # of the 3-D mixed-precision step: FP32 fields and spectrum.  The predictor reads
 # u (12) and writes u* (12), plus u^n (12) in RK3 stages 2 and 3; the y solve adds
 # its FP64 tables (computed in roofline()).
-KERNEL_BYTES_PER_CELL = {
-    "fft_x_fwd_div": 12.0 + 4.0, "fft_x_fwd": 8.0, "fft_z_fwd": 8.0, "fft_z_inv": 8.0, "fft_x_inv": 8.0,
-    "correct": 12.0 + 4.0 + 12.0, "divergence": 16.0,
-}
+def kernel_bytes_per_cell(name, dim, es, rk3):
+    """Algorithmic bytes per cell of one launch: every array the kernel must touch read or written
+    once (dim velocity fields and one scalar, es bytes per value).  The predictor of an RK3 step
+    reads u^n as well in stages 2 and 3 (the average over the three stages); a transform pass or
+    the spectral y solve reads and writes the scalar once.  The spectral y solve of 4096-row
+    columns runs in three launches (fft_y_fwd, fft_y_solve, fft_y_inv): the solve's bytes are
+    counted once, on fft_y_solve, and the two outer passes of its decomposition count none."""
+    vb = es * dim
+    if name in ("fft_y_fwd", "fft_y_inv"):
+        return 0.0
+    if name.startswith("predictor"):
+        return (2 * vb + 3 * vb + 3 * vb) / 3.0 if rk3 else 2 * vb
+    if name == "fft_x_fwd_div" or name == "divergence":
+        return vb + es
+    if name == "correct":
+        return 2 * vb + es
+    if name.startswith("fft_"):
+        return 2.0 * es
+    return None
+
 
 # DRAM bytes (read + write) per launch from one ncu capture of the 128^3 mixed RK3
 # workload (ncu flushes caches before each captured launch; writes still resident
@@ -382,17 +398,14 @@ def run_ours(args, ws, rank, local):
     cnt, kms = allk.get(dominant, (0, 0.0))
     peaks = measured_peaks()
     peak = peaks.get("hbm_gbs", 6400.0)
-    bpc = KERNEL_BYTES_PER_CELL.get(dominant)
-    if dominant.startswith("predictor"):
-        bpc = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
+    es = 4 if args.precision == "mixed" else 8
+    bpc = kernel_bytes_per_cell(dominant, wl.dim, es, wl.scheme == "rk3")
     timing = ("CUDA events around every launch of the kernel over a second pass of the K timed "
               "steps (L2 flushed per step, programmatic dependent launch off in that pass)")
 
     def hbm_roofline(name):
         c, t = allk.get(name, (0, 0.0))
-        b = KERNEL_BYTES_PER_CELL.get(name)
-        if name.startswith("predictor"):
-            b = (24.0 + 36.0 + 36.0) / 3.0 if wl.scheme == "rk3" else 24.0
+        b = kernel_bytes_per_cell(name, wl.dim, es, wl.scheme == "rk3")
         ach = b * cells / (t / c * 1e-3) / 1e9 if (c and b) else None
         tr = NCU_TRAFFIC.get(name) if args.workload == NCU_WORKLOAD else None
         return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -1024,8 +1037,7 @@ def sweep_leg(spec, stream, flush):
     peak = measured_peaks().get("hbm_gbs", 6400.0)
     kms = {k: v[1] / 2 for k, v in prof.items()}
     cnt, tot = prof["predictor"]
-    vb = 4.0 * dim   # bytes of one FP32 velocity field per cell
-    bpc = (2 * vb + 3 * vb + 3 * vb) / 3.0
+    bpc = kernel_bytes_per_cell("predictor", dim, 4, True)
     ach = bpc * cells / (tot / cnt * 1e-3) / 1e9
     out = {"n": dims, "cells": cells, "field": field, "ms_per_step": sum(ms) / steps,
            "value": cells * steps / (sum(ms) * 1e-3), "unit": "cell-updates/s",
@@ -1033,11 +1045,7 @@ def sweep_leg(spec, stream, flush):
            "predictor": {"avg_launch_us": tot / cnt * 1e3, "bytes_per_cell": bpc, "achieved_GBs": ach,
                          "peak_GBs": peak, "frac": ach / peak}}
     # every kernel's algorithmic bytes per cell (FP32 fields, FP32 spectrum)
-    per_kernel = {"predictor": bpc, "correct": 2 * vb + 4.0, "fft_x_fwd_div": vb + 4.0}
-    for k in kms:
-        if k.startswith("fft_") and k not in per_kernel:
-            per_kernel[k] = 8.0
-    step_bytes = sum(per_kernel.get(k, 0.0) * cells * prof[k][0] / 2 for k in kms)
+    step_bytes = sum((kernel_bytes_per_cell(k, dim, 4, True) or 0.0) * cells * prof[k][0] / 2 for k in kms)
     out["step_algorithmic_bytes"] = step_bytes
     out["step_GBs"] = step_bytes / (sum(ms) / steps * 1e-3) / 1e9
     out["step_frac"] = out["step_GBs"] / peak

@@ -710,3 +710,379 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(
     return {v.x * inv_n, v.y * inv_n};
   });
 }
+
+// ---------------------------------------------------------------------------
+// Periodic y of 4096-row columns in three launches (the four-step decomposition
+// 4096 = 64 x 64 across launches: n = 64 n1 + n2, k = k1 + 64 k2):
+//   y4_outer<fwd>: for each n2, the 64-point DFT over n1 of rows 64 n1 + n2,
+//                  times W_4096^{n2 k1}, back to row 64 k1 + n2;
+//   y4_mid:        for each k1, the 64-point DFT over n2 of rows 64 k1 + n2
+//                  gives X(k1 + 64 k2) in sub-line position k2; the eigenvalue
+//                  division (see yspec_kernel) pairs X(k) with X(4096 - k),
+//                  whose k1 is 64 - k1 (0 and 32 pair with themselves), so a
+//                  block holds the sub-lines of k1 and 64 - k1 (block 0: 0 and
+//                  32); the inverse 64-point DFT over k2 returns row 64 k1 + n2;
+//   y4_outer<inv>: for each n2, times W_4096^{-n2 k1}, the inverse 64-point DFT
+//                  over k1 and the factor 1/4096, back to row 64 n1 + n2.
+// Every block moves 32 consecutive slots (16 slot pairs, 128 B of FP32 per row)
+// of 128 rows: whole row segments instead of the few-slot columns that one
+// block per 4096-row line would read.  Each launch holds 32 sub-lines of 64
+// points (two row groups x 16 slot pairs), 8 transform threads per sub-line.
+constexpr int kY4 = 64;   // 4096 = kY4 * kY4
+constexpr int kY4Sub = 32;
+
+template <typename T>
+size_t y4_smem_bytes() {
+  return (size_t)(kY4Sub * rpitch<kY4>() + kY4) * sizeof(cplx<T>);
+}
+
+// Slot-pair tile of the block: sub-line 16 g + m (g < 2) entry e (< 64) <-> global row row(g, e),
+// slots 2m, 2m + 1; thread = (pair m, entries r0 + 16 q).
+template <typename T, typename RowF, typename Mul>
+__device__ __forceinline__ void y4_load(cplx<T>* S, const T* __restrict__ base, size_t rs, int nslots, RowF row,
+                                        Mul mul) {
+  constexpr int P = rpitch<kY4>();
+  const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+  if (2 * m >= nslots) return;
+  const bool whole = 2 * m + 1 < nslots;
+  using V = typename Pair2<T>::V;
+  cplx<T> v[2][4];
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T* a = base + rs * row(g, r0 + 16 * q) + 2 * m;
+      if (whole) {
+        const V w = *reinterpret_cast<const V*>(a);
+        v[g][q] = {w.x, w.y};
+      } else {
+        v[g][q] = {a[0], T(0)};
+      }
+    }
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) S[(16 * g + m) * P + rpad<kY4>(r0 + 16 * q)] = mul(g, r0 + 16 * q, v[g][q]);
+}
+
+template <typename T, typename RowF, typename Val>
+__device__ __forceinline__ void y4_store(T* __restrict__ base, size_t rs, int nslots, RowF row, Val value) {
+  const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
+  if (2 * m >= nslots) return;
+  const bool whole = 2 * m + 1 < nslots;
+  using V = typename Pair2<T>::V;
+#pragma unroll
+  for (int g = 0; g < 2; ++g)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const cplx<T> o = value(g, m, r0 + 16 * q);
+      T* a = base + rs * row(g, r0 + 16 * q) + 2 * m;
+      if (whole) {
+        V w;
+        w.x = o.x;
+        w.y = o.y;
+        *reinterpret_cast<V*>(a) = w;
+      } else {
+        a[0] = o.x;
+      }
+    }
+}
+
+// tw: the 4096-entry table exp(-2 pi i e / 4096); blocks (slot tile, n2 pair, z position)
+template <typename T, bool INV>
+__global__ void __launch_bounds__(kRegBlock, 4) y4_outer_kernel(T* __restrict__ data, int nx,
+                                                                const cplx<T>* __restrict__ tw) {
+  pdl_wait();
+  constexpr int P = rpitch<kY4>();
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kY4Sub * P;
+  const int s0 = blockIdx.x * 32;
+  const int n2a = 2 * blockIdx.y;
+  const int ns = min(32, nx - s0);
+  T* base = data + s0 + (size_t)nx * (kY4 * kY4) * blockIdx.z;
+  const size_t rs = (size_t)nx;
+  if (threadIdx.x < kY4) tws[threadIdx.x] = tw[kY4 * threadIdx.x];
+  auto row = [&](int g, int e) { return kY4 * e + n2a + g; };
+  y4_load<T>(S, base, rs, ns, row, [&](int g, int e, cplx<T> v) {
+    if (!INV) return v;
+    cplx<T> w = tw[(n2a + g) * e];
+    w.y = -w.y;
+    return cmul(v, w);
+  });
+  __syncthreads();
+  fft_reg_line<T, kY4, INV>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  __syncthreads();
+  pdl_trigger();
+  const T inv_n = T(1) / T(kY4 * kY4);
+  y4_store<T>(base, rs, ns, row, [&](int g, int m, int e) -> cplx<T> {
+    const cplx<T> v = S[(16 * g + m) * P + rpad<kY4>(e)];
+    if (INV) return {v.x * inv_n, v.y * inv_n};
+    return cmul(v, tw[(n2a + g) * e]);
+  });
+}
+
+// blocks (slot tile, k1 pair b < 32, z position)
+template <typename T>
+__global__ void __launch_bounds__(kRegBlock, 4) y4_mid_kernel(T* __restrict__ data, const YSpecArgs A,
+                                                              const cplx<T>* __restrict__ tw,
+                                                              const T* __restrict__ lamy,
+                                                              const T* __restrict__ lamxz) {
+  pdl_wait();
+  constexpr int P = rpitch<kY4>(), N = kY4 * kY4;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* tws = S + kY4Sub * P;
+  __shared__ T Lab[32];
+  const int s0 = blockIdx.x * 32;
+  const int b = blockIdx.y;
+  const int t = blockIdx.z;
+  const int k1g0 = b, k1g1 = b == 0 ? kY4 / 2 : kY4 - b;
+  const int ns = min(32, A.nx - s0);
+  const int nl = (ns + 1) / 2;
+  T* base = data + s0 + (size_t)A.nx * N * t;
+  const size_t rs = (size_t)A.nx;
+  if (threadIdx.x < kY4) tws[threadIdx.x] = tw[kY4 * threadIdx.x];
+  if (threadIdx.x < 2 * nl) {
+    const int sa = s0 + threadIdx.x;
+    const int sl = sa < A.nx ? sa : sa - 1;   // the odd tail's missing partner takes its neighbour's value
+    Lab[threadIdx.x] = lamxz[lam_index_spec<T>(A, sl, t)];
+  }
+  auto row = [&](int g, int e) { return kY4 * (g ? k1g1 : k1g0) + e; };
+  y4_load<T>(S, base, rs, ns, row, [](int, int, cplx<T> v) { return v; });
+  __syncthreads();
+  fft_reg_line<T, kY4, false>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  __syncthreads();
+  // sub-line 16 g + l position k2 holds X(k1_g + 64 k2); each pair (k, 4096 - k) once, by its lower k
+  for (int e = threadIdx.x; e < nl * 2 * kY4; e += blockDim.x) {
+    const int l = e >> 7, g = (e >> 6) & 1, k2 = e & (kY4 - 1);
+    const int k1 = g ? k1g1 : k1g0;
+    const int k = k1 + kY4 * k2;
+    const int kk = (N - k) & (N - 1);
+    if (k > kk) continue;
+    const int gg = (kk & (kY4 - 1)) == k1 ? g : 1 - g;
+    const T La = Lab[2 * l], Lb = Lab[2 * l + 1];
+    const T ly = lamy[k];
+    const T ma = ly + La, mb = ly + Lb;
+    const T ia = ma != T(0) ? T(1) / ma : T(0);
+    const T ib = mb != T(0) ? T(1) / mb : T(0);
+    const T cp = T(0.5) * (ia + ib), cm = T(0.5) * (ia - ib);
+    cplx<T>* p1 = S + (16 * g + l) * P + rpad<kY4>(k2);
+    cplx<T>* p2 = S + (16 * gg + l) * P + rpad<kY4>(kk / kY4);
+    const cplx<T> z1 = *p1, z2 = *p2;
+    *p1 = {cp * z1.x + cm * z2.x, cp * z1.y - cm * z2.y};
+    if (kk != k) *p2 = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
+  }
+  __syncthreads();
+  fft_reg_line<T, kY4, true>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  __syncthreads();
+  pdl_trigger();
+  y4_store<T>(base, rs, ns, row, [&](int g, int m, int e) { return S[(16 * g + m) * P + rpad<kY4>(e)]; });
+}
+
+// ---------------------------------------------------------------------------
+// x transforms of 4096-point rows: one complex line (two rows) per block of 256
+// threads, held in shared memory with one pad entry every 16 (entry i at
+// i + i / 16) and transformed in place by three radix-16 Stockham passes
+// (sub-transform sizes 1, 16, 256).  Thread j takes entries j + 256 r, r < 16,
+// twiddles them by W^{r (j mod Ns)} of the 16 Ns-point stage, forms their
+// 16-point DFT and, after the whole block has read its entries, writes them to
+// (j / Ns) 16 Ns + (j mod Ns) + r Ns.  With the pad every read and every write
+// of a half-warp touches 16 different bank pairs.
+constexpr int kX4 = 4096;
+__host__ __device__ constexpr int x4pad(int i) { return i + (i >> 4); }
+template <typename T>
+constexpr size_t x4_smem_bytes() {
+  return (size_t)x4pad(kX4) * sizeof(cplx<T>);
+}
+
+template <typename T, bool INV>
+__device__ __forceinline__ void fft4096_line(cplx<T>* L, const cplx<T>* __restrict__ tw) {
+  const int j = threadIdx.x;
+#pragma unroll
+  for (int pass = 0; pass < 3; ++pass) {
+    const int lg = 4 * pass;   // log2 of the sub-transform size Ns
+    const int k = j & ((1 << lg) - 1);
+    cplx<T> v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) v[r] = L[x4pad(j + 256 * r)];
+    if (pass > 0) {
+#pragma unroll
+      for (int r = 1; r < 16; ++r) {
+        cplx<T> w = tw[(k * r) << (8 - lg)];   // exp(-2 pi i r k / (16 Ns))
+        if (INV) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft16<T, INV>(v);
+    __syncthreads();   // every entry of the pass read
+    const int d = ((j >> lg) << (lg + 4)) + k;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) L[x4pad(d + (r << lg))] = v[r];
+    __syncthreads();
+  }
+}
+
+// x forward of 4096-point rows (see xfwd_kernel: mode 0 real-packed DFT, 1 DCT-II; DIV forms the
+// rows as the divergence of the predicted velocity)
+template <typename T, bool DIV>
+__global__ void __launch_bounds__(256, 3) xfwd4k_kernel(T* __restrict__ data, int rows, int mode,
+                                                        const cplx<T>* __restrict__ tw,
+                                                        const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
+  pdl_wait();
+  constexpr int N = kX4;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* L = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+  const bool two = r1 < rows;
+  int ja = 0, ka = 0, jb = 0, kb = 0;
+  if constexpr (DIV) {
+    ka = r0 / dv.g.ny;
+    ja = r0 - ka * dv.g.ny;
+    kb = r1 / dv.g.ny;
+    jb = r1 - kb * dv.g.ny;
+  }
+  bool done = false;
+  if constexpr (DIV) {
+    if (dv.vec4 && mode == 0) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int i0 = 4 * (threadIdx.x + 256 * u);
+        const Vec4<T> da = div4_at(dv, i0, ja, ka);
+        Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
+        if (two) db = div4_at(dv, i0, jb, kb);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) L[x4pad(i0 + e)] = {da.v[e], db.v[e]};
+      }
+      done = true;
+    }
+  }
+  if (!done) {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+      const int i = threadIdx.x + 256 * q;
+      T va, vb = T(0);
+      if constexpr (DIV) {
+        va = div_at(dv, i, ja, ka);
+        if (two) vb = div_at(dv, i, jb, kb);
+      } else {
+        va = data[(size_t)r0 * N + i];
+        if (two) vb = data[(size_t)r1 * N + i];
+      }
+      const int dst = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;   // DCT: even forward, odd reversed
+      L[x4pad(dst)] = {va, vb};
+    }
+  }
+  __syncthreads();
+  fft4096_line<T, false>(L, tw);
+  pdl_trigger();
+  using V = typename Pair2<T>::V;
+  for (int t = threadIdx.x; t < N / 2; t += 256) {
+    const int s0 = 2 * t;
+    T oa[2], ob[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = s0 + h;
+      int m;
+      bool im = false;
+      if (mode == 0) {
+        m = s == 0 ? 0 : (s == 1 ? N / 2 : s >> 1);
+        im = s >= 2 && (s & 1);
+      } else {
+        m = s;
+      }
+      const cplx<T> z = L[x4pad(m)], zr = L[x4pad(m == 0 ? 0 : N - m)];
+      const cplx<T> xa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};
+      const cplx<T> xb = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};
+      if (mode == 0) {
+        oa[h] = im ? xa.y : xa.x;
+        ob[h] = im ? xb.y : xb.x;
+      } else {
+        const cplx<T> w = dtw[m];
+        oa[h] = w.x * xa.x - w.y * xa.y;
+        ob[h] = w.x * xb.x - w.y * xb.y;
+      }
+    }
+    V wa, wb;
+    wa.x = oa[0];
+    wa.y = oa[1];
+    wb.x = ob[0];
+    wb.y = ob[1];
+    *reinterpret_cast<V*>(data + (size_t)r0 * N + s0) = wa;
+    if (two) *reinterpret_cast<V*>(data + (size_t)r1 * N + s0) = wb;
+  }
+}
+
+// x inverse of 4096-point rows (see xinv_kernel)
+template <typename T>
+__global__ void __launch_bounds__(256, 3) xinv4k_kernel(T* __restrict__ data, int rows, int mode,
+                                                        const cplx<T>* __restrict__ tw,
+                                                        const cplx<T>* __restrict__ dtw) {
+  pdl_wait();
+  constexpr int N = kX4;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* L = reinterpret_cast<cplx<T>*>(smem_raw);
+  const int r0 = 2 * blockIdx.x, r1 = r0 + 1;
+  const bool two = r1 < rows;
+  const T* ra = data + (size_t)r0 * N;
+  const T* rb = data + (size_t)r1 * N;
+  using V = typename Pair2<T>::V;
+#pragma unroll 4
+  for (int q = 0; q < 16; ++q) {
+    const int k = threadIdx.x + 256 * q;
+    cplx<T> xa, xb = {T(0), T(0)};
+    if (mode == 0) {
+      // Hermitian spectra from real-packed rows: slot pair (2k', 2k' + 1) read as one vector
+      const int kk = 2 * k <= N ? k : N - k;
+      const int off = 2 * (2 * kk == N ? 0 : kk);
+      const V pa = *reinterpret_cast<const V*>(ra + off);
+      V pb;
+      pb.x = pb.y = T(0);
+      if (two) pb = *reinterpret_cast<const V*>(rb + off);
+      if (k == 0) {
+        xa = {pa.x, T(0)};
+        xb = {pb.x, T(0)};
+      } else if (2 * k == N) {
+        xa = {pa.y, T(0)};
+        xb = {pb.y, T(0)};
+      } else if (2 * k < N) {
+        xa = {pa.x, pa.y};
+        xb = {pb.x, pb.y};
+      } else {
+        xa = {pa.x, -pa.y};
+        xb = {pb.x, -pb.y};
+      }
+    } else {
+      // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
+      const cplx<T> w = cconj(dtw[k]);
+      const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
+      xa = cmul(w, cplx<T>{a1, -a2});
+      if (two) {
+        const T b1 = rb[k], b2 = k ? rb[N - k] : T(0);
+        xb = cmul(w, cplx<T>{b1, -b2});
+      }
+    }
+    L[x4pad(k)] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
+  }
+  __syncthreads();
+  fft4096_line<T, true>(L, tw);
+  pdl_trigger();
+  const T inv_n = T(1) / T(N);
+  for (int t = threadIdx.x; t < N / 2; t += 256) {
+    const int i0 = 2 * t;
+    cplx<T> v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = i0 + h;
+      const int src = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
+      v[h] = L[x4pad(src)];
+    }
+    V wa, wb;
+    wa.x = v[0].x * inv_n;
+    wa.y = v[1].x * inv_n;
+    wb.x = v[0].y * inv_n;
+    wb.y = v[1].y * inv_n;
+    *reinterpret_cast<V*>(data + (size_t)r0 * N + i0) = wa;
+    if (two) *reinterpret_cast<V*>(data + (size_t)r1 * N + i0) = wb;
+  }
+}

@@ -1410,8 +1410,8 @@ __global__ void __launch_bounds__(NT) yspec_kernel(T* __restrict__ data, const Y
                                                     const cplx<T>* __restrict__ tw, const T* __restrict__ lamy,
                                                     const T* __restrict__ lamxz) {
   extern __shared__ unsigned char smem_raw[];
-  // compile-time lengths up to 640 move 32-slot tiles (spb == 32); 4096 (a few lines per block)
-  // moves its slots with the generic loops
+  // compile-time lengths up to 640 move 32-slot tiles (spb == 32); longer columns (a few lines
+  // per block) move their slots with the generic loops
   constexpr bool TILE32 = PL >= 2 && PL <= 640;
   const int N = PL >= 2 ? PL : A.ny;
   const int P = N + 1;                          // padded line pitch
@@ -1536,10 +1536,9 @@ void set_smem_attrs_plan() {
   cudaFuncSetAttribute(yspec_kernel<T, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
   if constexpr (PL == 0) {
     cudaFuncSetAttribute(yspec_kernel<T, 0, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
-    cudaFuncSetAttribute(yspec_kernel<T, 4096, 1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kYSpecBudget);
-    cudaFuncSetAttribute(xfwd_kernel<T, 4096, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
-    cudaFuncSetAttribute(xfwd_kernel<T, 4096, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
-    cudaFuncSetAttribute(xinv_kernel<T, 4096>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
+    cudaFuncSetAttribute(xfwd4k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
+    cudaFuncSetAttribute(xfwd4k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
+    cudaFuncSetAttribute(xinv4k_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
     cudaFuncSetAttribute(xfwd_kernel<T, 5760, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xfwd_kernel<T, 5760, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xinv_kernel<T, 5760>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
@@ -1607,10 +1606,10 @@ FftKernels<T> fft_kernels(const Plan1D& p) {
   return fft_kernels_of<T, 0>();
 }
 
-// Rows of 4096 and 5760 points and periodic-y columns of 4096 points (2-D grids) take a
-// compile-time plan in the x transforms (one line per block) and in the 1024-thread periodic-y
-// kernel (a few lines per block); the 16-line z and y kernels of those lengths are not built
-constexpr int kXLong = 4096;
+// Rows of 5760 points take a compile-time plan in the x transforms (one line per block); the
+// 16-line z and y kernels of that length are not built.  Rows of 4096 points have their own
+// radix-16 kernels (xfwd4k_kernel, xinv4k_kernel) and periodic-y columns of 4096 points the
+// three-launch four-step solve (y4_outer_kernel, y4_mid_kernel).
 constexpr int kXLong2 = 5760;   // 2^7 3^2 5: the rows of the 2-D cylinder-array workload
 template <typename T, int N>
 FftKernels<T> fft_kernels_xlong() {
@@ -1622,7 +1621,6 @@ FftKernels<T> fft_kernels_xlong() {
 }
 template <typename T>
 FftKernels<T> fft_kernels_x(const Plan1D& p) {
-  if (p.n == kXLong) return fft_kernels_xlong<T, kXLong>();
   if (p.n == kXLong2) return fft_kernels_xlong<T, kXLong2>();
   return fft_kernels<T>(p);
 }
@@ -1844,6 +1842,11 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   // x forward
   if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xfwd(G, data, rows, dv); });
+  } else if (nx == kX4) {
+    const DivArgs<T> none{};
+    launch_pdl(G, dv ? "fft_x_fwd_div" : "fft_x_fwd", dv ? xfwd4k_kernel<T, true> : xfwd4k_kernel<T, false>,
+               dim3((rows + 1) / 2), dim3(256), x4_smem_bytes<T>(), data, rows, G->xmode, (const cplx<T>*)G->px.tw,
+               (const cplx<T>*)G->px.dtw, dv ? *dv : none);
   } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
     const int lines = (rows + 1) / 2;
@@ -1914,6 +1917,21 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
       A.nmx = G->nmx;
       A.spb = 32;
       with_reg_length<T>(ny, [&](auto L) { L.yspec(G, data, A); });
+    } else if (G->yspec && ny == kY4 * kY4) {
+      YSpecArgs A;
+      A.nx = nx;
+      A.ny = ny;
+      A.nz = nz;
+      A.dim = G->dim;
+      A.xmode = G->xmode;
+      A.nmx = G->nmx;
+      A.spb = 32;
+      const dim3 grid((nx + 31) / 32, kY4 / 2, G->dim == 3 ? nz : 1);
+      const cplx<T>* tw = (const cplx<T>*)G->py.tw;
+      launch_pdl(G, "fft_y_fwd", y4_outer_kernel<T, false>, grid, dim3(kRegBlock), y4_smem_bytes<T>(), data, nx, tw);
+      launch_pdl(G, "fft_y_solve", y4_mid_kernel<T>, grid, dim3(kRegBlock), y4_smem_bytes<T>(), data, A, tw,
+                 (const T*)G->lamy, (const T*)G->lamxz);
+      launch_pdl(G, "fft_y_inv", y4_outer_kernel<T, true>, grid, dim3(kRegBlock), y4_smem_bytes<T>(), data, nx, tw);
     } else if (G->yspec) {
       YSpecArgs A;
       A.nx = nx;
@@ -1934,7 +1952,7 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
       // more butterflies of each stage in flight (radices up to 5)
       int nt = 256;
       if (k == yspec_kernel<T, 0> && spb <= 8) {
-        k = ny == kXLong ? yspec_kernel<T, kXLong, 1024> : yspec_kernel<T, 0, 1024>;   // 4096: compile-time plan
+        k = yspec_kernel<T, 0, 1024>;
         nt = 1024;
       }
       FS_LAUNCH(G, "fft_y_solve", k<<<grid, nt, (size_t)(spb / 2) * line_bytes, G->stream>>>(
@@ -1991,6 +2009,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   }
   if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xinv(G, data, rows); });
+  } else if (nx == kX4) {
+    launch_pdl(G, "fft_x_inv", xinv4k_kernel<T>, dim3((rows + 1) / 2), dim3(256), x4_smem_bytes<T>(), data, rows,
+               G->xmode, (const cplx<T>*)G->px.tw, (const cplx<T>*)G->px.dtw);
   } else {
     int lpb = (int)(kSmemBudget / fft_smem_bytes<T>(nx, 1));
     const int lines = (rows + 1) / 2;

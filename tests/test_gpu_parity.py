@@ -582,8 +582,9 @@ def test_register_fft_384_512(n, axis, precision):
 
 @pytest.mark.parametrize("precision,ny", [("mixed", 4096), ("fp64", 2000), ("mixed", 2000)])
 def test_long_periodic_y_spectral(precision, ny):
-    """Periodic y transformed by the mixed-radix kernels on long columns (a few lines per block:
-    1024 threads per block where the block holds at most four lines) against the FP64 oracle."""
+    """Periodic y on long columns against the FP64 oracle: 2000 rows by the mixed-radix kernels (a
+    few lines per block, 1024 threads per block where the block holds at most four lines), 4096
+    rows by the three-launch four-step form."""
     # square cells of h = 8 / ny; |u| <= 1, CFL <= 0.1 and nu dt / h^2 <= 0.01 (stable steps)
     wl = S.box_2d(16, ny, (P, P), (P, P), Lx=16 * 8.0 / ny, Ly=8.0, nu=1e-4)
     wl.dt = 0.0002
@@ -593,19 +594,40 @@ def test_long_periodic_y_spectral(precision, ny):
     assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
 
 
-@pytest.mark.parametrize("precision,nx,bcx", [("mixed", 4096, (P, P)), ("fp64", 4096, (P, P)),
-                                              ("fp64", 4096, (IN, OUT)), ("fp64", 2000, (IN, OUT)),
-                                              ("mixed", 2000, (IN, OUT)), ("fp64", 5760, (IN, OUT)),
-                                              ("mixed", 5760, (IN, OUT))])
-def test_long_x_lines(precision, nx, bcx):
-    """x transforms of long rows with one line per block (4096 and 5760 points: the compile-time
-    plans of the x transforms; FP64: one line beyond the usual shared-memory budget; 2000 points:
-    the runtime plan): the periodic DFT with the divergence fused, and the DCT-II of an
-    inflow/outflow channel, against the FP64 oracle."""
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("shape", [(40, 4096), (8, 4096, 4)])
+def test_four_step_periodic_y(precision, shape):
+    """Periodic y of 4096-row columns in three launches (64-point DFTs over the rows of each
+    residue class mod 64 with the 4096-point twiddles; the eigenvalue division in the middle
+    launch, whose blocks hold the row groups k1 and 64 - k1): two slot tiles, the second
+    holding 8 slots, in 2-D, and four z planes in 3-D, against the FP64 oracle."""
+    h = 8.0 / 4096   # square cells; |u| <= 1, CFL <= 0.1, nu dt / h^2 <= 0.01
+    if len(shape) == 2:
+        wl = S.box_2d(shape[0], 4096, (P, P), (P, P), Lx=shape[0] * h, Ly=8.0, nu=1e-4)
+    else:
+        wl = S.box_3d(shape[0], 4096, shape[2], (P, P), (P, P), L=(shape[0] * h, 8.0, shape[2] * h), nu=1e-4)
+    wl.dt = 0.0002
+    wl.u0 = S.random_fields(wl, 7, 1.0)
+    gp = run_gpu(wl, 3, precision=precision)
+    st, _, _ = run_oracle(wl, 3)
+    assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
+
+
+@pytest.mark.parametrize("precision,nx,bcx,ny", [("mixed", 4096, (P, P), 16), ("fp64", 4096, (P, P), 16),
+                                                 ("fp64", 4096, (P, P), 15), ("fp64", 4096, (IN, OUT), 16),
+                                                 ("mixed", 4096, (IN, OUT), 15), ("fp64", 2000, (IN, OUT), 16),
+                                                 ("mixed", 2000, (IN, OUT), 16), ("fp64", 5760, (IN, OUT), 16),
+                                                 ("mixed", 5760, (IN, OUT), 16)])
+def test_long_x_lines(precision, nx, bcx, ny):
+    """x transforms of long rows with one line per block (4096 points: the radix-16 kernels;
+    5760: the compile-time plan; 2000: the runtime plan; FP64: lines beyond the usual
+    shared-memory budget): the periodic DFT with the divergence fused, and the DCT-II of an
+    inflow/outflow channel, with an odd row count (the last line's second row empty), against
+    the FP64 oracle."""
     h = 1.0 / 256
     bcy = (NS, NS) if bcx == (P, P) else (FS, FS)
     bc_val = None if bcx == (P, P) else [[[1.0, 0, 0], [0, 0, 0]], [[0, 0, 0], [0, 0, 0]]]
-    wl = S.box_2d(nx, 16, bcx, bcy, Lx=nx * h, Ly=16 * h, nu=1e-4, bc_val=bc_val)
+    wl = S.box_2d(nx, ny, bcx, bcy, Lx=nx * h, Ly=ny * h, nu=1e-4, bc_val=bc_val)
     wl.dt = 0.1 * h
     wl.u0 = S.random_fields(wl, 6, 1.0)
     gp = run_gpu(wl, 3, precision=precision)
