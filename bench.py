@@ -51,7 +51,7 @@ def kernel_bytes_per_cell(name, dim, es, rk3):
         return 0.0
     if name.startswith("predictor"):
         return (2 * vb + 3 * vb + 3 * vb) / 3.0 if rk3 else 2 * vb
-    if name == "fft_x_fwd_div" or name == "divergence":
+    if name in ("fft_x_fwd_div", "fft_xz_fwd_div", "divergence"):
         return vb + es
     if name == "correct":
         return 2 * vb + es
@@ -67,13 +67,11 @@ def kernel_bytes_per_cell(name, dim, es, rk3):
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_WORKLOAD = "isotropic_3d_128"   # the workload the traffic below was captured on
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50361344 + 924416, "src": "4d5c344d8f7c"},
-    "ysolve": {"bytes": 24118016 + 0, "src": "af343e7d574b"},
-    "fft_x_fwd_div": {"bytes": 25243648 + 0, "src": "63900357a1f5"},
-    "fft_z_fwd": {"bytes": 8407296 + 0, "src": "63900357a1f5"},
-    "fft_z_inv": {"bytes": 8410880 + 0, "src": "63900357a1f5"},
-    "fft_x_inv": {"bytes": 8414720 + 0, "src": "63900357a1f5"},
-    "correct": {"bytes": 33560320 + 3072, "src": "96276b6b63ca"},
+    "predictor": {"bytes": 50363136 + 882944, "src": "4d5c344d8f7c"},
+    "ysolve": {"bytes": 24119040 + 0, "src": "af343e7d574b"},
+    "fft_xz_fwd_div": {"bytes": 25195520 + 2048, "src": "d8e0c8babe2e"},
+    "fft_xz_inv": {"bytes": 8412416 + 0, "src": "d8e0c8babe2e"},
+    "correct": {"bytes": 33560320 + 768, "src": "96276b6b63ca"},
 }
 
 

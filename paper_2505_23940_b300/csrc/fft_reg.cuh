@@ -1086,3 +1086,191 @@ __global__ void __launch_bounds__(256, 3) xinv4k_kernel(T* __restrict__ data, in
     if (two) *reinterpret_cast<V*>(data + (size_t)r1 * N + i0) = wb;
   }
 }
+
+// ---------------------------------------------------------------------------
+// x and z transforms of one y position j per block (3-D, FP32 fields, nx = nz = N
+// of 64 or 128, periodic x and z).  The x-z plane of a y position (N rows k of N
+// values, 16 or 64 KB) fits in shared memory, so both directions are done in one
+// pass over the field instead of the two of the x and z kernels:
+//   forward: rows (divergence formed on the fly, or read) -> N/2 row-pair lines
+//            (rows 2l, 2l + 1 as real and imaginary parts), x DFT, real-packed
+//            split written as N/2 slot-pair lines along z, z DFT, written out in
+//            the layout of zfwd_reg_kernel (pair 0 split into two real-packed z
+//            spectra);
+//   inverse: the mirror image (zinv_reg_kernel, then xinv_reg_kernel with the
+//            rows paired along z instead of along y), one 1 / N^2 at the end.
+// Each line is transformed by 8 threads (fft_reg_line); 8 N threads per block,
+// half of them transform while the other half idles, all of them move data.
+template <int N>
+constexpr size_t plane_smem_bytes() {
+  return (size_t)(N * rpitch<N>() + N) * sizeof(cplx<float>);
+}
+
+template <int N, bool DIV>
+__global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict__ data, int ny,
+                                                               const cplx<float>* __restrict__ tw,
+                                                               const DivArgs<float> dv) {
+  pdl_wait();
+  using T = float;
+  constexpr int P = rpitch<N>(), NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // z lines: slot pair c, entry k
+  cplx<T>* B = A + NL * P;                              // x lines: row pair l, entry i
+  cplx<T>* tws = B + NL * P;
+  const int j = blockIdx.x;
+  const size_t rs = (size_t)N * ny;   // between z positions
+  T* base = data + (size_t)N * j;
+  for (int e = threadIdx.x; e < N; e += NT) tws[e] = tw[e];
+  // rows k of the plane as quads of x positions
+  constexpr int NQ = N * N / 4 / NT;   // quads per thread
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / (N / 4), i0 = 4 * (e - k * (N / 4));
+    float v[4];
+    if constexpr (DIV) {
+      const Vec4<T> d = div4_at(dv, i0, j, k);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = d.v[c];
+    } else {
+      const float4 d = *reinterpret_cast<const float4*>(base + rs * k + i0);
+      v[0] = d.x; v[1] = d.y; v[2] = d.z; v[3] = d.w;
+    }
+    T* dst = reinterpret_cast<T*>(B + (k >> 1) * P);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dst[2 * rpad<N>(i0 + c) + (k & 1)] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  // real-packed split of rows 2l, 2l + 1: slot pair c (slots 2c, 2c + 1) of row k -> A[c][k]
+  for (int e = threadIdx.x; e < NL * NL; e += NT) {
+    const int l = e / NL, c = e - l * NL;
+    const cplx<T>* line = B + l * P;
+    cplx<T> oa, ob;
+    if (c == 0) {   // slots 0 and 1: the real modes 0 and N / 2
+      const cplx<T> z0 = line[rpad<N>(0)], zh = line[rpad<N>(N / 2)];
+      oa = {z0.x, zh.x};
+      ob = {z0.y, zh.y};
+    } else {
+      const cplx<T> z = line[rpad<N>(c)], zr = line[rpad<N>(N - c)];
+      oa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};   // XA = (Z + conj Zr) / 2
+      ob = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};   // XB = (Z - conj Zr) / (2 i)
+    }
+    A[c * P + rpad<N>(2 * l)] = oa;
+    A[c * P + rpad<N>(2 * l + 1)] = ob;
+  }
+  __syncthreads();
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  pdl_trigger();
+  constexpr int NE = N * NL / NT;   // slot pairs per thread
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NL, c = e - k * NL;
+    cplx<T> o;
+    if (c > 0) {
+      o = A[c * P + rpad<N>(k)];
+    } else {   // pair 0 holds two real sequences: split into two real-packed z spectra
+      const int m = k == 0 ? 0 : (k == 1 ? N / 2 : k >> 1);
+      const bool im = k >= 2 && (k & 1);
+      const cplx<T> z = A[rpad<N>(m)], zr = A[rpad<N>(m == 0 ? 0 : N - m)];
+      o = im ? cplx<T>{T(0.5) * (z.y - zr.y), T(0.5) * (zr.x - z.x)}
+             : cplx<T>{T(0.5) * (z.x + zr.x), T(0.5) * (z.y + zr.y)};
+    }
+    *reinterpret_cast<float2*>(base + rs * k + 2 * c) = make_float2(o.x, o.y);
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict__ data, int ny,
+                                                               const cplx<float>* __restrict__ tw) {
+  pdl_wait();
+  using T = float;
+  constexpr int P = rpitch<N>(), NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // z lines: slot pair c, entry k
+  cplx<T>* B = A + NL * P;                              // x lines: row pair l, entry i
+  cplx<T>* tws = B + NL * P;
+  const int j = blockIdx.x;
+  const size_t rs = (size_t)N * ny;
+  T* base = data + (size_t)N * j;
+  for (int e = threadIdx.x; e < N; e += NT) tws[e] = tw[e];
+  constexpr int NE = N * NL / NT;
+  float2 v[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NL, c = e - k * NL;
+    v[q] = *reinterpret_cast<const float2*>(base + rs * k + 2 * c);
+  }
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NL, c = e - k * NL;
+    A[c * P + rpad<N>(k)] = {v[q].x, v[q].y};
+    if (c == 0) B[rpad<N>(k)] = {v[q].x, v[q].y};   // pair 0 kept aside for its rebuild
+  }
+  __syncthreads();
+  // pair 0: the two real-packed z spectra Y0 (slot 0), Y1 (slot 1) -> Z = Y0 + i Y1
+  for (int l = threadIdx.x; l < N; l += NT) {
+    cplx<T> y0, y1;
+    if (l == 0 || 2 * l == N) {
+      const cplx<T> a = B[rpad<N>(l == 0 ? 0 : 1)];
+      y0 = {a.x, T(0)};
+      y1 = {a.y, T(0)};
+    } else {
+      const int q = 2 * l < N ? l : N - l;
+      const T sg = 2 * l < N ? T(1) : T(-1);
+      const cplx<T> a = B[rpad<N>(2 * q)], b = B[rpad<N>(2 * q + 1)];
+      y0 = {a.x, sg * b.x};
+      y1 = {a.y, sg * b.y};
+    }
+    A[rpad<N>(l)] = {y0.x - y1.y, y0.y + y1.x};
+  }
+  __syncthreads();
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  // x lines: row pair l (rows 2l, 2l + 1), entry kx = XA + i XB, the Hermitian spectra of the two
+  // rows from their real-packed slots (slots 2c, 2c + 1 of row k are A[c][k])
+  for (int e = threadIdx.x; e < NL * N; e += NT) {
+    const int l = e / N, kx = e - l * N;
+    const int kk = 2 * kx <= N ? kx : N - kx;
+    const int c = 2 * kk == N ? 0 : kk;
+    const cplx<T> pa = A[c * P + rpad<N>(2 * l)], pb = A[c * P + rpad<N>(2 * l + 1)];
+    cplx<T> xa, xb;
+    if (kx == 0) {
+      xa = {pa.x, T(0)};
+      xb = {pb.x, T(0)};
+    } else if (2 * kx == N) {
+      xa = {pa.y, T(0)};
+      xb = {pb.y, T(0)};
+    } else if (2 * kx < N) {
+      xa = pa;
+      xb = pb;
+    } else {
+      xa = {pa.x, -pa.y};
+      xb = {pb.x, -pb.y};
+    }
+    B[l * P + rpad<N>(kx)] = {xa.x - xb.y, xa.y + xb.x};
+  }
+  __syncthreads();
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  pdl_trigger();
+  const T sc = T(1) / T(N * N);
+  constexpr int NQ = N * N / 4 / NT;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / (N / 4), i0 = 4 * (e - k * (N / 4));
+    const T* src = reinterpret_cast<const T*>(B + (k >> 1) * P);
+    float4 o;
+    o.x = src[2 * rpad<N>(i0) + (k & 1)] * sc;
+    o.y = src[2 * rpad<N>(i0 + 1) + (k & 1)] * sc;
+    o.z = src[2 * rpad<N>(i0 + 2) + (k & 1)] * sc;
+    o.w = src[2 * rpad<N>(i0 + 3) + (k & 1)] * sc;
+    *reinterpret_cast<float4*>(base + rs * k + i0) = o;
+  }
+}

@@ -1721,6 +1721,11 @@ void set_smem_attrs() {
   set_smem_attrs_plan<T, 480>();
   set_smem_attrs_plan<T, 512>();
   set_smem_attrs_plan<T, 640>();
+  if constexpr (std::is_same<T, float>::value) {
+    cudaFuncSetAttribute(xzfwd_plane_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
+    cudaFuncSetAttribute(xzfwd_plane_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
+    cudaFuncSetAttribute(zxinv_plane_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
+  }
   cudaFuncSetAttribute(ysolve_kernel<T, 4, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 8, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 16, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -1834,13 +1839,63 @@ void launch_ytwist(fs_grid* G, T* data, int xblk0, int nxblk) {
   }
 }
 
+// The x and z transforms fused per y position (xzfwd_plane_kernel, zxinv_plane_kernel): FP32
+// fields, nx = nz of 64 or 128, periodic x, the divergence formed from row quads.
+template <typename T>
+bool xz_plane(const fs_grid* G, const DivArgs<T>* dv) {
+  if constexpr (!std::is_same<T, float>::value) {
+    return false;
+  } else {
+    return G->tune_xzplane && G->dim == 3 && G->nx == G->nz && (G->nx == 64 || G->nx == 128) && G->xmode == 0 &&
+           (!dv || dv->vec4);
+  }
+}
+
+template <typename T>
+void launch_xz_plane(fs_grid* G, T* data, const DivArgs<T>* dv, bool inverse) {
+  if constexpr (std::is_same<T, float>::value) {
+    const DivArgs<float> none{};
+    const cplx<float>* tw = (const cplx<float>*)G->px.tw;
+    const dim3 grid(G->ny);
+    if (G->nx == 128) {
+      if (inverse)
+        launch_pdl(G, "fft_xz_inv", zxinv_plane_kernel<128>, grid, dim3(1024), plane_smem_bytes<128>(), data, G->ny, tw);
+      else
+        launch_pdl(G, dv ? "fft_xz_fwd_div" : "fft_xz_fwd",
+                   dv ? xzfwd_plane_kernel<128, true> : xzfwd_plane_kernel<128, false>, grid, dim3(1024),
+                   plane_smem_bytes<128>(), data, G->ny, tw, dv ? *dv : none);
+    } else {
+      if (inverse)
+        launch_pdl(G, "fft_xz_inv", zxinv_plane_kernel<64>, grid, dim3(512), plane_smem_bytes<64>(), data, G->ny, tw);
+      else
+        launch_pdl(G, dv ? "fft_xz_fwd_div" : "fft_xz_fwd",
+                   dv ? xzfwd_plane_kernel<64, true> : xzfwd_plane_kernel<64, false>, grid, dim3(512),
+                   plane_smem_bytes<64>(), data, G->ny, tw, dv ? *dv : none);
+    }
+  }
+}
+
 template <typename T>
 void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   set_smem_attrs<T>();
   const int nx = G->nx, ny = G->ny, nz = G->nz;
   const int rows = ny * nz;
-  // x forward
-  if (x_reg(G)) {
+  // Periodic-z grids with the twisted y solve in two or more column blocks along x: the z
+  // transforms and the y solve of the two halves of the x spectrum are independent, so they run as
+  // two chains on two streams (fork after the x transform, join before its inverse).  The y solve is
+  // bound by the FP64 pipe and the z transforms by memory, so each half's y solve runs beside the
+  // other half's transforms; each y-solve half also holds one block per SM instead of two.
+  const bool zreg2 = G->dim == 3 && is_reg_length(nz);
+  const int wcol = G->ytw_cols;
+  const int nxb = (nx + wcol - 1) / wcol;
+  const int tiles_per_blk = (wcol / 2) / kRegLines;
+  const bool split = G->tune_ysplit && zreg2 && G->ytwist && !G->yspec && G->ystream2 && nxb >= 2 &&
+                     nx % wcol == 0 && (wcol / 2) % kRegLines == 0;
+  const bool plane = !split && xz_plane<T>(G, dv);
+  // x forward (and z forward in the fused form)
+  if (plane) {
+    launch_xz_plane<T>(G, data, dv, false);
+  } else if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xfwd(G, data, rows, dv); });
   } else if (nx == kX4) {
     const DivArgs<T> none{};
@@ -1861,17 +1916,6 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
                                                                     (const cplx<T>*)G->px.tw,
                                                                     (const cplx<T>*)G->px.dtw, dv ? *dv : none));
   }
-  // Periodic-z grids with the twisted y solve in two or more column blocks along x: the z
-  // transforms and the y solve of the two halves of the x spectrum are independent, so they run as
-  // two chains on two streams (fork after the x transform, join before its inverse).  The y solve is
-  // bound by the FP64 pipe and the z transforms by memory, so each half's y solve runs beside the
-  // other half's transforms; each y-solve half also holds one block per SM instead of two.
-  const bool zreg2 = G->dim == 3 && is_reg_length(nz);
-  const int wcol = G->ytw_cols;
-  const int nxb = (nx + wcol - 1) / wcol;
-  const int tiles_per_blk = (wcol / 2) / kRegLines;
-  const bool split = G->tune_ysplit && zreg2 && G->ytwist && !G->yspec && G->ystream2 && nxb >= 2 &&
-                     nx % wcol == 0 && (wcol / 2) % kRegLines == 0;
   if (split) {
     const int hb = nxb / 2;
     const int nt = (nx / 2) / kRegLines;
@@ -1891,7 +1935,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
   } else {
     int ppb = 0;
     const bool zreg = G->dim == 3 && is_reg_length(nz);
-    if (zreg) {
+    if (plane) {
+      // z forward done with the x forward
+    } else if (zreg) {
       with_reg_length<T>(nz, [&](auto L) { L.zfwd(G, data); });
     } else if (G->dim == 3) {
       if (is_fixed_length<T>(G->pz.n)) {
@@ -1998,7 +2044,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
         FS_LAUNCH(G, "ysolve", ysolve_kernel<T, 4, YCOLS><<<grid, dim3(YCOLS, 4), sb, G->stream>>>(data, A));
       }
     }
-    if (zreg) {
+    if (plane) {
+      // z inverse done with the x inverse
+    } else if (zreg) {
       with_reg_length<T>(nz, [&](auto L) { L.zinv(G, data); });
     } else if (G->dim == 3) {
       dim3 grid((nx / 2 + ppb - 1) / ppb, ny);
@@ -2007,7 +2055,9 @@ void poisson_solve(fs_grid* G, T* data, const DivArgs<T>* dv) {
                                                               (const cplx<T>*)G->pz.tw));
     }
   }
-  if (x_reg(G)) {
+  if (plane) {
+    launch_xz_plane<T>(G, data, dv, true);
+  } else if (x_reg(G)) {
     with_reg_length<T>(nx, [&](auto L) { L.xinv(G, data, rows); });
   } else if (nx == kX4) {
     launch_pdl(G, "fft_x_inv", xinv4k_kernel<T>, dim3((rows + 1) / 2), dim3(256), x4_smem_bytes<T>(), data, rows,
