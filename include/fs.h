@@ -346,12 +346,14 @@ int fs_device_status(fs_grid* grid, unsigned* bits);
  *   "ysolve_tiled"    1 (default): the twisted solve loads FP32 tiles of at
  *                     least 32 rows as 16-row tensor-map boxes (not on walls
  *                     with ny odd); 0: one bulk copy per row
- *   "xz_plane"        1 (default): on 3-D FP32 grids with nx = nz of 64 or 128
- *                     and periodic x (no immersed body), the x and z transforms
- *                     of the Poisson solve run fused, one block per y position
- *                     holding its x-z plane in shared memory (one pass over the
- *                     field each way instead of two; not where "ysplit" applies);
- *                     0: separate x and z kernels
+ *   "xz_plane"        on 3-D FP32 grids with nx = nz of 64 or 128 and periodic
+ *                     x (no immersed body) the x and z transforms of the
+ *                     Poisson solve run fused per y position, its x-z plane in
+ *                     shared memory (one pass over the field each way instead
+ *                     of two; not where "ysplit" applies): 1 (default) one
+ *                     block per plane, 2 the plane split over a cluster of two
+ *                     blocks (slower at 128^3: 0.288 against 0.219 ms per
+ *                     step); 0: separate x and z kernels
  *   "ysplit"          1: on periodic-z grids whose twisted y solve has two or
  *                     more column blocks along x, the z transforms and the y
  *                     solve of the two halves of the x spectrum run as two

@@ -1274,3 +1274,222 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
     *reinterpret_cast<float4*>(base + rs * k + i0) = o;
   }
 }
+
+// The same fused x and z transforms with each y position's plane split over a
+// cluster of two blocks (rank r): block r holds the row pairs l and the slot
+// pairs c of its half (N / 4 lines of each kind) and transforms them with all
+// of its 2 N threads (8 per line).  Forward: the block's rows through the x
+// DFT, the real-packed split stored into the slot-pair lines of whichever
+// block owns the slot pair (the peer's through distributed shared memory),
+// a cluster barrier, the z DFT of its own slot pairs.  Inverse: its slot pairs
+// through the z DFT, a cluster barrier, each row pair gathered from both
+// blocks' slot-pair lines, the x DFT of its own rows.  Twice the blocks of
+// the one-block form (all SMs busy at 128^3) and no idle threads in the
+// transform passes, yet slower at 128^3 (20.5 and 25 us per launch against
+// 16.5 and 14.4, and less overlap between launches): the one-block form is
+// the default.
+template <int N>
+constexpr size_t plane_pair_smem_bytes() {
+  return (size_t)(N / 2 * rpitch<N>() + N) * sizeof(cplx<float>);
+}
+
+template <int N, bool DIV>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(2 * N)
+    xzfwd_pair_kernel(float* __restrict__ data, int ny, const cplx<float>* __restrict__ tw, const DivArgs<float> dv) {
+  cluster_arrive_relaxed();   // this block runs: its shared memory may take the peer's stores
+  pdl_wait();
+  using T = float;
+  constexpr int P = rpitch<N>(), NL = N / 2, NH = N / 4, NT = 2 * N, TPL = RegPlan<N>::TPL;
+  static_assert(NH * TPL == NT, "one transform thread group per line");
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // own slot pairs c = NH r + cl, entry k
+  cplx<T>* B = A + NH * P;                              // own row pairs l = NH r + ll, entry i
+  cplx<T>* tws = B + NH * P;
+  const int r = (int)cluster_rank();
+  const int j = blockIdx.x >> 1;
+  const size_t rs = (size_t)N * ny;
+  T* base = data + (size_t)N * j;
+  for (int e = threadIdx.x; e < N; e += NT) tws[e] = tw[e];
+  // own rows k = N r / 2 + kk as quads of x positions
+  constexpr int NQ = N / 16;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int kk = e / (N / 4), i0 = 4 * (e - kk * (N / 4));
+    const int k = NL * r + kk;
+    float v[4];
+    if constexpr (DIV) {
+      const Vec4<T> d = div4_at(dv, i0, j, k);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) v[c] = d.v[c];
+    } else {
+      const float4 d = *reinterpret_cast<const float4*>(base + rs * k + i0);
+      v[0] = d.x; v[1] = d.y; v[2] = d.z; v[3] = d.w;
+    }
+    T* dst = reinterpret_cast<T*>(B + (kk >> 1) * P);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) dst[2 * rpad<N>(i0 + c) + (kk & 1)] = v[c];
+  }
+  __syncthreads();
+  fft_reg_line<T, N, false>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  cluster_wait();   // the peer runs: its slot-pair lines may be written
+  const uint32_t A_own = smem_u32(A), A_peer = map_peer(A_own, (uint32_t)(r ^ 1));
+  for (int e = threadIdx.x; e < NH * NL; e += NT) {
+    const int ll = e / NL, c = e - ll * NL;
+    const int l = NH * r + ll;
+    const cplx<T>* line = B + ll * P;
+    cplx<T> oa, ob;
+    if (c == 0) {
+      const cplx<T> z0 = line[rpad<N>(0)], zh = line[rpad<N>(N / 2)];
+      oa = {z0.x, zh.x};
+      ob = {z0.y, zh.y};
+    } else {
+      const cplx<T> z = line[rpad<N>(c)], zr = line[rpad<N>(N - c)];
+      oa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};
+      ob = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};
+    }
+    const int owner = c / NH, cl = c - owner * NH;
+    const uint32_t at = (owner == r ? A_own : A_peer) + (uint32_t)((cl * P + rpad<N>(2 * l)) * sizeof(cplx<T>));
+    st_cluster_f2(at, oa.x, oa.y);
+    st_cluster_f2(at + (uint32_t)((rpad<N>(2 * l + 1) - rpad<N>(2 * l)) * sizeof(cplx<T>)), ob.x, ob.y);
+  }
+  cluster_arrive();   // this block's stores into both blocks' lines are done
+  cluster_wait();     // and the peer's
+  fft_reg_line<T, N, false>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  pdl_trigger();
+  constexpr int NE = N / 8;   // slot pairs per thread
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NH, cl = e - k * NH;
+    const int c = NH * r + cl;
+    cplx<T> o;
+    if (c > 0) {
+      o = A[cl * P + rpad<N>(k)];
+    } else {   // pair 0: two real-packed z spectra
+      const int m = k == 0 ? 0 : (k == 1 ? N / 2 : k >> 1);
+      const bool im = k >= 2 && (k & 1);
+      const cplx<T> z = A[rpad<N>(m)], zr = A[rpad<N>(m == 0 ? 0 : N - m)];
+      o = im ? cplx<T>{T(0.5) * (z.y - zr.y), T(0.5) * (zr.x - z.x)}
+             : cplx<T>{T(0.5) * (z.x + zr.x), T(0.5) * (z.y + zr.y)};
+    }
+    *reinterpret_cast<float2*>(base + rs * k + 2 * c) = make_float2(o.x, o.y);
+  }
+}
+
+template <int N>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(2 * N)
+    zxinv_pair_kernel(float* __restrict__ data, int ny, const cplx<float>* __restrict__ tw) {
+  pdl_wait();
+  using T = float;
+  constexpr int P = rpitch<N>(), NL = N / 2, NH = N / 4, NT = 2 * N, TPL = RegPlan<N>::TPL;
+  static_assert(NH * TPL == NT, "one transform thread group per line");
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // own slot pairs c = NH r + cl, entry k
+  cplx<T>* B = A + NH * P;                              // own row pairs l = NH r + ll, entry i
+  cplx<T>* tws = B + NH * P;
+  const int r = (int)cluster_rank();
+  const int j = blockIdx.x >> 1;
+  const size_t rs = (size_t)N * ny;
+  T* base = data + (size_t)N * j;
+  for (int e = threadIdx.x; e < N; e += NT) tws[e] = tw[e];
+  constexpr int NE = N / 8;
+  float2 v[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NH, cl = e - k * NH;
+    v[q] = *reinterpret_cast<const float2*>(base + rs * k + 2 * (NH * r + cl));
+  }
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int k = e / NH, cl = e - k * NH;
+    A[cl * P + rpad<N>(k)] = {v[q].x, v[q].y};
+    if (r == 0 && cl == 0) B[rpad<N>(k)] = {v[q].x, v[q].y};   // pair 0 kept aside for its rebuild
+  }
+  __syncthreads();
+  if (r == 0) {   // pair 0: Y0 (slot 0), Y1 (slot 1) real-packed -> Z = Y0 + i Y1
+    for (int l = threadIdx.x; l < N; l += NT) {
+      cplx<T> y0, y1;
+      if (l == 0 || 2 * l == N) {
+        const cplx<T> a = B[rpad<N>(l == 0 ? 0 : 1)];
+        y0 = {a.x, T(0)};
+        y1 = {a.y, T(0)};
+      } else {
+        const int q = 2 * l < N ? l : N - l;
+        const T sg = 2 * l < N ? T(1) : T(-1);
+        const cplx<T> a = B[rpad<N>(2 * q)], b = B[rpad<N>(2 * q + 1)];
+        y0 = {a.x, sg * b.x};
+        y1 = {a.y, sg * b.y};
+      }
+      A[rpad<N>(l)] = {y0.x - y1.y, y0.y + y1.x};
+    }
+  }
+  __syncthreads();
+  fft_reg_line<T, N, true>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  cluster_arrive();   // this block's slot-pair lines are final
+  cluster_wait();     // and the peer's
+  const uint32_t A_own = smem_u32(A), A_peer = map_peer(A_own, (uint32_t)(r ^ 1));
+  constexpr int RE = NH * N / NT, RB = 4;   // entries per thread, in batches of RB loads in flight
+  static_assert(RE % RB == 0, "whole batches");
+#pragma unroll
+  for (int q0 = 0; q0 < RE; q0 += RB) {
+    float2 pa[RB], pb[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int e = threadIdx.x + NT * (q0 + u);
+      const int ll = e / N, kx = e - ll * N;
+      const int l = NH * r + ll;
+      const int kk = 2 * kx <= N ? kx : N - kx;
+      const int c = 2 * kk == N ? 0 : kk;
+      const int owner = c / NH, cl = c - owner * NH;
+      const uint32_t at = (owner == r ? A_own : A_peer) + (uint32_t)((cl * P + rpad<N>(2 * l)) * sizeof(cplx<T>));
+      pa[u] = ld_cluster_f2(at);
+      pb[u] = ld_cluster_f2(at + (uint32_t)((rpad<N>(2 * l + 1) - rpad<N>(2 * l)) * sizeof(cplx<T>)));
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const int e = threadIdx.x + NT * (q0 + u);
+      const int ll = e / N, kx = e - ll * N;
+      cplx<T> xa, xb;
+      if (kx == 0) {
+        xa = {pa[u].x, T(0)};
+        xb = {pb[u].x, T(0)};
+      } else if (2 * kx == N) {
+        xa = {pa[u].y, T(0)};
+        xb = {pb[u].y, T(0)};
+      } else if (2 * kx < N) {
+        xa = {pa[u].x, pa[u].y};
+        xb = {pb[u].x, pb[u].y};
+      } else {
+        xa = {pa[u].x, -pa[u].y};
+        xb = {pb[u].x, -pb[u].y};
+      }
+      B[ll * P + rpad<N>(kx)] = {xa.x - xb.y, xa.y + xb.x};
+    }
+  }
+  cluster_arrive();   // the peer's lines are no longer read by this block
+  __syncthreads();
+  fft_reg_line<T, N, true>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  __syncthreads();
+  pdl_trigger();
+  const T sc = T(1) / T(N * N);
+  constexpr int NQ = N / 16;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int e = threadIdx.x + NT * q;
+    const int kk = e / (N / 4), i0 = 4 * (e - kk * (N / 4));
+    const int k = NL * r + kk;
+    const T* src = reinterpret_cast<const T*>(B + (kk >> 1) * P);
+    float4 o;
+    o.x = src[2 * rpad<N>(i0) + (kk & 1)] * sc;
+    o.y = src[2 * rpad<N>(i0 + 1) + (kk & 1)] * sc;
+    o.z = src[2 * rpad<N>(i0 + 2) + (kk & 1)] * sc;
+    o.w = src[2 * rpad<N>(i0 + 3) + (kk & 1)] * sc;
+    *reinterpret_cast<float4*>(base + rs * k + i0) = o;
+  }
+  cluster_wait();   // the peer no longer reads this block's lines: its shared memory may go
+}

@@ -965,8 +965,8 @@ int fs_set_tuning(fs_grid* G, const char* key, int value) {
     free_ytables(G);
     return build_tables(G);
   } else if (k == "xz_plane") {
-    if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "xz_plane must be 0 or 1");
-    G->tune_xzplane = value == 1;
+    if (value < 0 || value > 2) return set_error(FS_ERR_ARG, "xz_plane must be 0, 1 or 2");
+    G->tune_xzplane = value;
   } else if (k == "ysolve_tiled") {
     if (value != 0 && value != 1) return set_error(FS_ERR_ARG, "ysolve_tiled must be 0 or 1");
     G->tune_ytile = value == 1;

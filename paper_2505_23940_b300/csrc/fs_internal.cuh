@@ -343,7 +343,7 @@ struct fs_grid {
   int ytw_map_w = 0;
   bool ytw_map_ok = false;
   bool tune_ytile = true;                 // twisted solve: tensor-map tile loads where they apply
-  bool tune_xzplane = true;               // FP32 nx = nz of 64 or 128: x and z transforms fused per y position
+  int tune_xzplane = 1;                   // FP32 nx = nz of 64 or 128: x and z transforms fused per y position (1: one block, 2: a two-block cluster)
   int ytw_L = 0, ytw_R = 0;               // chain rows 0..L-1, positions per thread R = ceil(L / 2)
   int ytw_nlp = 0;                        // row pitch (eigenvalues) of the position-major tables
   double *twM = nullptr, *twE = nullptr, *twC = nullptr;   // [2 R + 4 kTwChunk][nlp], position-major

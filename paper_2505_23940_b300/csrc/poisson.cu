@@ -1725,6 +1725,9 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(xzfwd_plane_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
     cudaFuncSetAttribute(xzfwd_plane_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
     cudaFuncSetAttribute(zxinv_plane_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
+    cudaFuncSetAttribute(xzfwd_pair_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
+    cudaFuncSetAttribute(xzfwd_pair_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
+    cudaFuncSetAttribute(zxinv_pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
   }
   cudaFuncSetAttribute(ysolve_kernel<T, 4, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   cudaFuncSetAttribute(ysolve_kernel<T, 8, YCOLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
@@ -1857,6 +1860,26 @@ void launch_xz_plane(fs_grid* G, T* data, const DivArgs<T>* dv, bool inverse) {
     const DivArgs<float> none{};
     const cplx<float>* tw = (const cplx<float>*)G->px.tw;
     const dim3 grid(G->ny);
+    if (G->tune_xzplane == 2) {   // two-block clusters: grid of 2 ny blocks
+      const dim3 g2(2 * G->ny);
+      if (G->nx == 128) {
+        if (inverse)
+          launch_pdl(G, "fft_xz_inv", zxinv_pair_kernel<128>, g2, dim3(256), plane_pair_smem_bytes<128>(), data, G->ny,
+                     tw);
+        else
+          launch_pdl(G, dv ? "fft_xz_fwd_div" : "fft_xz_fwd",
+                     dv ? xzfwd_pair_kernel<128, true> : xzfwd_pair_kernel<128, false>, g2, dim3(256),
+                     plane_pair_smem_bytes<128>(), data, G->ny, tw, dv ? *dv : none);
+      } else {
+        if (inverse)
+          launch_pdl(G, "fft_xz_inv", zxinv_pair_kernel<64>, g2, dim3(128), plane_pair_smem_bytes<64>(), data, G->ny, tw);
+        else
+          launch_pdl(G, dv ? "fft_xz_fwd_div" : "fft_xz_fwd",
+                     dv ? xzfwd_pair_kernel<64, true> : xzfwd_pair_kernel<64, false>, g2, dim3(128),
+                     plane_pair_smem_bytes<64>(), data, G->ny, tw, dv ? *dv : none);
+      }
+      return;
+    }
     if (G->nx == 128) {
       if (inverse)
         launch_pdl(G, "fft_xz_inv", zxinv_plane_kernel<128>, grid, dim3(1024), plane_smem_bytes<128>(), data, G->ny, tw);

@@ -594,19 +594,21 @@ def test_long_periodic_y_spectral(precision, ny):
     assert field_err(gp["u"], st.u) < (TOL64 if precision == "fp64" else TOLMIX)
 
 
+@pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("n,ny,bcy,yspec", [(64, 24, (NS, NS), None), (128, 16, (P, P), 0),
                                              (128, 16, (P, P), 1), (64, 64, (P, P), 0)])
-def test_xz_plane_transforms(n, ny, bcy, yspec):
+def test_xz_plane_transforms(n, ny, bcy, yspec, form):
     """Mixed precision, the x and z transforms fused per y position (nx = nz of 64 or 128: the
-    x-z plane in shared memory, one pass each way, the divergence formed on the fly): whole RK3
-    steps against the FP64 oracle, and against the separate x and z kernels (xz_plane off) to
-    FP32 rounding; walls in y (stretched) and periodic y by the FP64 twisted solve and by the
-    FP32 DFT."""
+    x-z plane in shared memory, one pass each way, the divergence formed on the fly; form 1 one
+    block per plane, form 2 the plane split over a two-block cluster exchanging its halves
+    through distributed shared memory): whole RK3 steps against the FP64 oracle, and against
+    the separate x and z kernels (xz_plane off) to FP32 rounding; walls in y (stretched) and
+    periodic y by the FP64 twisted solve and by the FP32 DFT."""
     wl = S.box_3d(n, ny, n, (P, P), bcy, stretched=1.2 if bcy == (NS, NS) else 0.0, nu=1e-3)
     wl.dt = 0.002
     wl.u0 = S.random_fields(wl, 11, 1.0)
     tune = [] if yspec is None else [("y_spectral", yspec)]
-    gp = run_gpu(wl, 3, precision="mixed", tuning=tune)
+    gp = run_gpu(wl, 3, precision="mixed", tuning=tune + [("xz_plane", form)])
     gs = run_gpu(wl, 3, precision="mixed", tuning=tune + [("xz_plane", 0)])
     st, _, _ = run_oracle(wl, 3)
     assert field_err(gp["u"], st.u) < TOLMIX
