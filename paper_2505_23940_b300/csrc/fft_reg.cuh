@@ -1121,24 +1121,51 @@ __global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict
   const size_t rs = (size_t)N * ny;   // between z positions
   T* base = data + (size_t)N * j;
   for (int e = threadIdx.x; e < N; e += NT) tws[e] = tw[e];
-  // rows k of the plane as quads of x positions
-  constexpr int NQ = N * N / 4 / NT;   // quads per thread
+  // row pairs (2l, 2l + 1) of the plane as quads of x positions, stored as complex pairs
+  constexpr int NQ = N * N / 8 / NT;   // row-pair quads per thread
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const int e = threadIdx.x + NT * q;
-    const int k = e / (N / 4), i0 = 4 * (e - k * (N / 4));
-    float v[4];
+    const int l = e / (N / 4), i0 = 4 * (e - l * (N / 4));
+    float va[4], vb[4];
     if constexpr (DIV) {
-      const Vec4<T> d = div4_at(dv, i0, j, k);
+      // D u* at rows k0 = 2l and k1 = 2l + 1 (as div4_at): the rows share the w quad of k1, and the
+      // x neighbour of a quad's last cell is the next lane's first (a row's quads fill N / 4
+      // consecutive lanes, periodic in x)
+      const Geom<T>& g = dv.g;
+      const int k0 = 2 * l, k1 = k0 + 1, k2 = k1 + 1 < g.nz ? k1 + 1 : 0;
+      const Vec4<T> ua = ld4(dv.u[0] + rs * k0 + (size_t)N * j + i0);
+      const Vec4<T> ub = ld4(dv.u[0] + rs * k1 + (size_t)N * j + i0);
+      const int ey = g.ext(1, 1);
+      const int jp = j + 1 < ey ? j + 1 : 0;
+      const T* vp = dv.u[1] + i0;
+      const size_t vs = (size_t)N * ey;
+      const Vec4<T> v0a = ld4(vp + vs * k0 + (size_t)N * j), v1a = ld4(vp + vs * k0 + (size_t)N * jp);
+      const Vec4<T> v0b = ld4(vp + vs * k1 + (size_t)N * j), v1b = ld4(vp + vs * k1 + (size_t)N * jp);
+      const T* wp = dv.u[2] + (size_t)N * j + i0;
+      const Vec4<T> w0 = ld4(wp + rs * k0), w1 = ld4(wp + rs * k1), w2 = ld4(wp + rs * k2);
+      constexpr int Q = N / 4;
+      const int lane = threadIdx.x & 31;
+      const int nb = (lane & ~(Q - 1)) | ((lane + 1) & (Q - 1));
+      const T ea = __shfl_sync(0xffffffffu, ua.v[0], nb), eb = __shfl_sync(0xffffffffu, ub.v[0], nb);
+      const T ih = g.ihy[j];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) v[c] = d.v[c];
+      for (int c = 0; c < 4; ++c) {
+        va[c] = ((c < 3 ? ua.v[c + 1] : ea) - ua.v[c]) * g.ihx;
+        vb[c] = ((c < 3 ? ub.v[c + 1] : eb) - ub.v[c]) * g.ihx;
+        va[c] += (v1a.v[c] - v0a.v[c]) * ih;
+        vb[c] += (v1b.v[c] - v0b.v[c]) * ih;
+        va[c] += (w1.v[c] - w0.v[c]) * g.ihz;
+        vb[c] += (w2.v[c] - w1.v[c]) * g.ihz;
+      }
     } else {
-      const float4 d = *reinterpret_cast<const float4*>(base + rs * k + i0);
-      v[0] = d.x; v[1] = d.y; v[2] = d.z; v[3] = d.w;
+      const float4 da = *reinterpret_cast<const float4*>(base + rs * (2 * l) + i0);
+      const float4 db = *reinterpret_cast<const float4*>(base + rs * (2 * l + 1) + i0);
+      va[0] = da.x; va[1] = da.y; va[2] = da.z; va[3] = da.w;
+      vb[0] = db.x; vb[1] = db.y; vb[2] = db.z; vb[3] = db.w;
     }
-    T* dst = reinterpret_cast<T*>(B + (k >> 1) * P);
 #pragma unroll
-    for (int c = 0; c < 4; ++c) dst[2 * rpad<N>(i0 + c) + (k & 1)] = v[c];
+    for (int c = 0; c < 4; ++c) B[l * P + rpad<N>(i0 + c)] = {va[c], vb[c]};
   }
   __syncthreads();
   if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
@@ -1260,18 +1287,18 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
   __syncthreads();
   pdl_trigger();
   const T sc = T(1) / T(N * N);
-  constexpr int NQ = N * N / 4 / NT;
+  constexpr int NQ = N * N / 8 / NT;   // row-pair quads per thread
 #pragma unroll
   for (int q = 0; q < NQ; ++q) {
     const int e = threadIdx.x + NT * q;
-    const int k = e / (N / 4), i0 = 4 * (e - k * (N / 4));
-    const T* src = reinterpret_cast<const T*>(B + (k >> 1) * P);
-    float4 o;
-    o.x = src[2 * rpad<N>(i0) + (k & 1)] * sc;
-    o.y = src[2 * rpad<N>(i0 + 1) + (k & 1)] * sc;
-    o.z = src[2 * rpad<N>(i0 + 2) + (k & 1)] * sc;
-    o.w = src[2 * rpad<N>(i0 + 3) + (k & 1)] * sc;
-    *reinterpret_cast<float4*>(base + rs * k + i0) = o;
+    const int l = e / (N / 4), i0 = 4 * (e - l * (N / 4));
+    cplx<T> z[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) z[c] = B[l * P + rpad<N>(i0 + c)];
+    *reinterpret_cast<float4*>(base + rs * (2 * l) + i0) =
+        make_float4(z[0].x * sc, z[1].x * sc, z[2].x * sc, z[3].x * sc);
+    *reinterpret_cast<float4*>(base + rs * (2 * l + 1) + i0) =
+        make_float4(z[0].y * sc, z[1].y * sc, z[2].y * sc, z[3].y * sc);
   }
 }
 
