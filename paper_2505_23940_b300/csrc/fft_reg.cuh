@@ -790,7 +790,7 @@ __device__ __forceinline__ void y4_store(T* __restrict__ base, size_t rs, int ns
 
 // tw: the 4096-entry table exp(-2 pi i e / 4096); blocks (slot tile, n2 pair, z position)
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kRegBlock, 4) y4_outer_kernel(T* __restrict__ data, int nx,
+__global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_outer_kernel(T* __restrict__ data, int nx,
                                                                 const cplx<T>* __restrict__ tw) {
   pdl_wait();
   constexpr int P = rpitch<kY4>();
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(kRegBlock, 4) y4_outer_kernel(T* __restrict__ 
 
 // blocks (slot tile, k1 pair b < 32, z position)
 template <typename T>
-__global__ void __launch_bounds__(kRegBlock, 4) y4_mid_kernel(T* __restrict__ data, const YSpecArgs A,
+__global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_mid_kernel(T* __restrict__ data, const YSpecArgs A,
                                                               const cplx<T>* __restrict__ tw,
                                                               const T* __restrict__ lamy,
                                                               const T* __restrict__ lamxz) {
@@ -926,7 +926,7 @@ __device__ __forceinline__ void fft4096_line(cplx<T>* L, const cplx<T>* __restri
 // x forward of 4096-point rows (see xfwd_kernel: mode 0 real-packed DFT, 1 DCT-II; DIV forms the
 // rows as the divergence of the predicted velocity)
 template <typename T, bool DIV>
-__global__ void __launch_bounds__(256, 3) xfwd4k_kernel(T* __restrict__ data, int rows, int mode,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) xfwd4k_kernel(T* __restrict__ data, int rows, int mode,
                                                         const cplx<T>* __restrict__ tw,
                                                         const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
   pdl_wait();
@@ -1015,7 +1015,7 @@ __global__ void __launch_bounds__(256, 3) xfwd4k_kernel(T* __restrict__ data, in
 
 // x inverse of 4096-point rows (see xinv_kernel)
 template <typename T>
-__global__ void __launch_bounds__(256, 3) xinv4k_kernel(T* __restrict__ data, int rows, int mode,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) xinv4k_kernel(T* __restrict__ data, int rows, int mode,
                                                         const cplx<T>* __restrict__ tw,
                                                         const cplx<T>* __restrict__ dtw) {
   pdl_wait();
