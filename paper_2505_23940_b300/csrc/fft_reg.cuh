@@ -1,4 +1,6 @@
-// Register-resident FFT kernels for the transform lengths 64, 128, 256, 384 and 512
+// Register-resident FFT kernels for the transform lengths 64, 128, 256, 384 and 512,
+// the x and z transforms fused per y position (nx = nz of 64 or 128), and the
+// 4096-point transforms (periodic y in three launches, x rows by radix-16 passes)
 // (included by poisson.cu inside its anonymous namespace; uses cplx, cmul,
 // DivArgs, div_at, div4_at, YSpecArgs and lam_index_spec from there).
 //
