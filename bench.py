@@ -67,10 +67,10 @@ def kernel_bytes_per_cell(name, dim, es, rk3):
 # measured on (see KERNEL_SOURCES): a changed kernel reports traffic null until re-captured.
 NCU_WORKLOAD = "isotropic_3d_128"   # the workload the traffic below was captured on
 NCU_TRAFFIC = {
-    "predictor": {"bytes": 50363136 + 1117952, "src": "4d5c344d8f7c"},
-    "ysolve": {"bytes": 24119296 + 0, "src": "af343e7d574b"},
-    "fft_xz_fwd_div": {"bytes": 25208576 + 0, "src": "3a7b4fcf6430"},
-    "fft_xz_inv": {"bytes": 8412416 + 0, "src": "3a7b4fcf6430"},
+    "predictor": {"bytes": 50363136 + 1117952, "src": "787d2c94fc89"},
+    "ysolve": {"bytes": 24119296 + 0, "src": "193f4010f1a6"},
+    "fft_xz_fwd_div": {"bytes": 25208576 + 0, "src": "1cc92d96aeb7"},
+    "fft_xz_inv": {"bytes": 8412416 + 0, "src": "1cc92d96aeb7"},
     "correct": {"bytes": 33560576 + 1024, "src": "96276b6b63ca"},
 }
 
@@ -82,6 +82,8 @@ KERNEL_SOURCES = {
     "correct": ("stencil.cu", "__global__ void __launch_bounds__(kThreads) correct4_kernel", "\n}\n", []),
     "ysolve": ("poisson.cu", "// y solve for grids with many columns", "// Periodic y: the columns",
                ["fpconv.cuh", "tma.cuh"]),
+    "fft_xz": ("fft_reg.cuh", "// x and z transforms of one y position j per block",
+               "// The same fused x and z transforms with each y position's plane split", []),
     "fft": ("fft_reg.cuh", "", "", []),
 }
 
