@@ -378,16 +378,79 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
     if (dv.vec4 && mode == 0) {
       constexpr int NQ = N / 4;
       constexpr int PER = kRegLines * NQ / kRegBlock;   // quads per thread
+      if constexpr (N >= 384 && sizeof(T) == 4) {
+        // two blocks per SM (128 registers): the raw loads of two quads of both rows of a line
+        // are issued together before any arithmetic (the divergence as div4_at forms it; FP64
+        // rows keep the one-quad form, whose registers hold without spilling)
+        constexpr int BT = 2;
+        static_assert(PER % BT == 0, "whole batches");
+        const Geom<T>& g = dv.g;
+        const bool d3 = g.dim == 3;
+        const int ey = g.ext(1, 1);
+        const size_t pu = (size_t)N * g.ny, pv = (size_t)N * ey;
 #pragma unroll
-      for (int u = 0; u < PER; ++u) {
-        const int Q = threadIdx.x + kRegBlock * u;
-        const int l = Q / NQ, i0 = 4 * (Q - l * NQ);
-        if (l < nl) {
-          const Vec4<T> da = div4_at(dv, i0, rowj[2 * l], rowk[2 * l]);
-          Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
-          if (2 * (line0 + l) + 1 < rows) db = div4_at(dv, i0, rowj[2 * l + 1], rowk[2 * l + 1]);
+        for (int u0 = 0; u0 < PER; u0 += BT) {
+          Vec4<T> x[BT][2][5];   // row a, b of the line: u, v at j and j + 1, w at k and k + 1
+          T xe[BT][2];           // u right of the quad
 #pragma unroll
-          for (int e = 0; e < 4; ++e) S[l * P + rpad<N>(i0 + e)] = {da.v[e], db.v[e]};
+          for (int b = 0; b < BT; ++b) {
+            const int Q = threadIdx.x + kRegBlock * (u0 + b);
+            const int l = min(Q / NQ, nl - 1);   // past the block's lines: line nl - 1 again, not stored
+            const int i0 = 4 * (Q % NQ);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const bool in = h == 0 || 2 * (line0 + l) + 1 < rows;
+              const int j = rowj[2 * l + (in ? h : 0)], k = rowk[2 * l + (in ? h : 0)];
+              const T* ur = dv.u[0] + (size_t)N * j + pu * k;
+              x[b][h][0] = ld4(ur + i0);
+              xe[b][h] = __ldg(ur + (i0 + 4 < N ? i0 + 4 : 0));
+              const int jp = j + 1 < ey ? j + 1 : 0;
+              const T* vr = dv.u[1] + pv * k + i0;
+              x[b][h][1] = ld4(vr + (size_t)N * j);
+              x[b][h][2] = ld4(vr + (size_t)N * jp);
+              if (d3) {
+                const int kp = k + 1 < g.nz ? k + 1 : 0;
+                const T* wr = dv.u[2] + (size_t)N * j + i0;
+                x[b][h][3] = ld4(wr + pu * k);
+                x[b][h][4] = ld4(wr + pu * kp);
+              }
+            }
+          }
+#pragma unroll
+          for (int b = 0; b < BT; ++b) {
+            const int Q = threadIdx.x + kRegBlock * (u0 + b);
+            const int l = Q / NQ, i0 = 4 * (Q % NQ);
+            if (l < nl) {
+              T d[2][4];
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const bool in = h == 0 || 2 * (line0 + l) + 1 < rows;
+                const T ih = g.ihy[rowj[2 * l + (in ? h : 0)]];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  T sv = ((c < 3 ? x[b][h][0].v[c + 1] : xe[b][h]) - x[b][h][0].v[c]) * g.ihx;
+                  sv += (x[b][h][2].v[c] - x[b][h][1].v[c]) * ih;
+                  if (d3) sv += (x[b][h][4].v[c] - x[b][h][3].v[c]) * g.ihz;
+                  d[h][c] = in ? sv : T(0);
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c) S[l * P + rpad<N>(i0 + c)] = {d[0][c], d[1][c]};
+            }
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int Q = threadIdx.x + kRegBlock * u;
+          const int l = Q / NQ, i0 = 4 * (Q - l * NQ);
+          if (l < nl) {
+            const Vec4<T> da = div4_at(dv, i0, rowj[2 * l], rowk[2 * l]);
+            Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
+            if (2 * (line0 + l) + 1 < rows) db = div4_at(dv, i0, rowj[2 * l + 1], rowk[2 * l + 1]);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) S[l * P + rpad<N>(i0 + e)] = {da.v[e], db.v[e]};
+          }
         }
       }
       done = true;
