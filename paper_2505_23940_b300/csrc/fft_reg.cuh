@@ -542,13 +542,19 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
   load_twiddles<T, N>(tws, tw);
   using V = typename Pair2<T>::V;
   constexpr int KB = kRegLines * N / kRegBlock;
-  cplx<T> z[KB];
+  // entries per thread converted together: all of them up to 256 points; chunks of 8 for the
+  // 384- and 512-point rows, whose 24 or 32 pairs of both rows would not fit 128 registers
+  constexpr int CH = N >= 384 ? 8 : KB;
+  static_assert(KB % CH == 0, "whole chunks");
+#pragma unroll
+  for (int q0 = 0; q0 < KB; q0 += CH) {
+  cplx<T> z[CH];
   if (mode == 0) {
     // Hermitian spectra from real-packed rows: slot pair (2k', 2k' + 1) read as one vector
-    V pa[KB], pb[KB];
+    V pa[CH], pb[CH];
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = threadIdx.x + q * kRegBlock;
+    for (int q = 0; q < CH; ++q) {
+      const int t = threadIdx.x + (q0 + q) * kRegBlock;
       const int l = t / N, k = t - l * N;
       const int kk = 2 * k <= N ? k : N - k;
       pa[q].x = pa[q].y = pb[q].x = pb[q].y = T(0);
@@ -559,8 +565,8 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
       }
     }
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = threadIdx.x + q * kRegBlock;
+    for (int q = 0; q < CH; ++q) {
+      const int t = threadIdx.x + (q0 + q) * kRegBlock;
       const int k = t - (t / N) * N;
       cplx<T> xa, xb;
       if (k == 0) {
@@ -580,8 +586,8 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
     }
   } else {
 #pragma unroll
-    for (int q = 0; q < KB; ++q) {
-      const int t = threadIdx.x + q * kRegBlock;
+    for (int q = 0; q < CH; ++q) {
+      const int t = threadIdx.x + (q0 + q) * kRegBlock;
       const int l = t / N, k = t - l * N;
       z[q] = {T(0), T(0)};
       if (l < nl) {
@@ -599,10 +605,11 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
     }
   }
 #pragma unroll
-  for (int q = 0; q < KB; ++q) {
-    const int t = threadIdx.x + q * kRegBlock;
+  for (int q = 0; q < CH; ++q) {
+    const int t = threadIdx.x + (q0 + q) * kRegBlock;
     const int l = t / N, k = t - l * N;
     S[l * P + rpad<N>(k)] = z[q];
+  }
   }
   __syncthreads();
   fft_reg_block<T, N, true>(S, tws);
