@@ -1016,7 +1016,50 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) xfwd4k_kernel(T* 
   }
   bool done = false;
   if constexpr (DIV) {
-    if (dv.vec4 && mode == 0) {
+    if (dv.vec4 && mode == 0 && dv.g.dim == 2 && sizeof(T) == 4) {
+      // 2-D FP32 rows: the raw loads of two quads of both rows (u with its right neighbour, v at
+      // j and j + 1) issued together before any arithmetic (the divergence as div4_at forms it)
+      const Geom<T>& g = dv.g;
+      const int ey = g.ext(1, 1);
+      const int jb2 = two ? jb : ja;
+      const int jr[2] = {ja, jb2};
+      const T ih[2] = {g.ihy[ja], g.ihy[jb2]};
+#pragma unroll
+      for (int u0 = 0; u0 < 4; u0 += 2) {
+        Vec4<T> xu[2][2], xv0[2][2], xv1[2][2];
+        T xe[2][2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int i0 = 4 * (threadIdx.x + 256 * (u0 + b));
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = jr[h];
+            const T* ur = dv.u[0] + (size_t)N * j;
+            xu[b][h] = ld4(ur + i0);
+            xe[b][h] = __ldg(ur + (i0 + 4 < N ? i0 + 4 : 0));
+            const int jp = j + 1 < ey ? j + 1 : 0;
+            xv0[b][h] = ld4(dv.u[1] + (size_t)N * j + i0);
+            xv1[b][h] = ld4(dv.u[1] + (size_t)N * jp + i0);
+          }
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int i0 = 4 * (threadIdx.x + 256 * (u0 + b));
+          T d[2][4];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              T sv = ((c < 3 ? xu[b][h].v[c + 1] : xe[b][h]) - xu[b][h].v[c]) * g.ihx;
+              sv += (xv1[b][h].v[c] - xv0[b][h].v[c]) * ih[h];
+              d[h][c] = (h == 0 || two) ? sv : T(0);
+            }
+#pragma unroll
+          for (int c = 0; c < 4; ++c) L[x4pad(i0 + c)] = {d[0][c], d[1][c]};
+        }
+      }
+      done = true;
+    } else if (dv.vec4 && mode == 0) {
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i0 = 4 * (threadIdx.x + 256 * u);
