@@ -1142,42 +1142,47 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) xinv4k_kernel(T* 
   const T* ra = data + (size_t)r0 * N;
   const T* rb = data + (size_t)r1 * N;
   using V = typename Pair2<T>::V;
-#pragma unroll 4
-  for (int q = 0; q < 16; ++q) {
-    const int k = threadIdx.x + 256 * q;
-    cplx<T> xa, xb = {T(0), T(0)};
-    if (mode == 0) {
-      // Hermitian spectra from real-packed rows: slot pair (2k', 2k' + 1) read as one vector
-      const int kk = 2 * k <= N ? k : N - k;
-      const int off = 2 * (2 * kk == N ? 0 : kk);
-      const V pa = *reinterpret_cast<const V*>(ra + off);
-      V pb;
-      pb.x = pb.y = T(0);
-      if (two) pb = *reinterpret_cast<const V*>(rb + off);
-      if (k == 0) {
-        xa = {pa.x, T(0)};
-        xb = {pb.x, T(0)};
-      } else if (2 * k == N) {
-        xa = {pa.y, T(0)};
-        xb = {pb.y, T(0)};
-      } else if (2 * k < N) {
-        xa = {pa.x, pa.y};
-        xb = {pb.x, pb.y};
-      } else {
-        xa = {pa.x, -pa.y};
-        xb = {pb.x, -pb.y};
+  if (mode == 0) {
+    // Hermitian spectra from real-packed rows: the slot pair (2k, 2k + 1), 0 < k < N/2, read once
+    // as one vector gives entries k and N - k (complex conjugates of each other); slot pair 0
+    // holds the real X[0] and X[N/2].  Four pairs of both rows are loaded before any is stored.
+#pragma unroll
+    for (int q0 = 0; q0 < 8; q0 += 4) {
+      V pa[4], pb[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = threadIdx.x + 256 * (q0 + c);
+        pa[c] = *reinterpret_cast<const V*>(ra + 2 * k);
+        pb[c].x = pb[c].y = T(0);
+        if (two) pb[c] = *reinterpret_cast<const V*>(rb + 2 * k);
       }
-    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int k = threadIdx.x + 256 * (q0 + c);
+        if (k == 0) {
+          L[x4pad(0)] = {pa[c].x, pb[c].x};          // XA + i XB, both real
+          L[x4pad(N / 2)] = {pa[c].y, pb[c].y};
+        } else {
+          L[x4pad(k)] = {pa[c].x - pb[c].y, pa[c].y + pb[c].x};
+          L[x4pad(N - k)] = {pa[c].x + pb[c].y, pb[c].x - pa[c].y};
+        }
+      }
+    }
+  } else {
+#pragma unroll 4
+    for (int q = 0; q < 16; ++q) {
+      const int k = threadIdx.x + 256 * q;
       // V[k] = exp(i pi k / 2N) (X[k] - i X[N-k]), X[N] = 0
       const cplx<T> w = cconj(dtw[k]);
       const T a1 = ra[k], a2 = k ? ra[N - k] : T(0);
-      xa = cmul(w, cplx<T>{a1, -a2});
+      const cplx<T> xa = cmul(w, cplx<T>{a1, -a2});
+      cplx<T> xb = {T(0), T(0)};
       if (two) {
         const T b1 = rb[k], b2 = k ? rb[N - k] : T(0);
         xb = cmul(w, cplx<T>{b1, -b2});
       }
+      L[x4pad(k)] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
     }
-    L[x4pad(k)] = {xa.x - xb.y, xa.y + xb.x};   // XA + i XB
   }
   __syncthreads();
   fft4096_line<T, true>(L, tw);
