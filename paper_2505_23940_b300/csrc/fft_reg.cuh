@@ -802,10 +802,17 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(
 // points (two row groups x 16 slot pairs), 8 transform threads per sub-line.
 constexpr int kY4 = 64;   // 4096 = kY4 * kY4
 constexpr int kY4Sub = 32;
+// Sub-line s of the tile starts at 96 s + 8 (s mod 2) + s / 2 (complex entries; the padded
+// 64-point line spans 71).  The 16 sub-lines a warp transposes start in 16 different 8-byte bank
+// pairs, and the four lines a warp transforms pair up 8 bank pairs apart, so with FP32 entries
+// neither the transposition nor the two in-line passes replay (a plain pitch of 73 put the lines'
+// starts on the in-line stride of 9 and replayed the passes up to four times).
+constexpr int kY4Pitch = 96;
+__device__ __forceinline__ int y4line(int s) { return kY4Pitch * s + 8 * (s & 1) + (s >> 1); }
 
 template <typename T>
 size_t y4_smem_bytes() {
-  return (size_t)(kY4Sub * rpitch<kY4>() + kY4) * sizeof(cplx<T>);
+  return (size_t)(kY4Sub * kY4Pitch + kY4) * sizeof(cplx<T>);
 }
 
 // Slot-pair tile of the block: sub-line 16 g + m (g < 2) entry e (< 64) <-> global row row(g, e),
@@ -813,7 +820,6 @@ size_t y4_smem_bytes() {
 template <typename T, typename RowF, typename Mul>
 __device__ __forceinline__ void y4_load(cplx<T>* S, const T* __restrict__ base, size_t rs, int nslots, RowF row,
                                         Mul mul) {
-  constexpr int P = rpitch<kY4>();
   const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
   if (2 * m >= nslots) return;
   const bool whole = 2 * m + 1 < nslots;
@@ -834,7 +840,7 @@ __device__ __forceinline__ void y4_load(cplx<T>* S, const T* __restrict__ base, 
 #pragma unroll
   for (int g = 0; g < 2; ++g)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) S[(16 * g + m) * P + rpad<kY4>(r0 + 16 * q)] = mul(g, r0 + 16 * q, v[g][q]);
+    for (int q = 0; q < 4; ++q) S[y4line(16 * g + m) + rpad<kY4>(r0 + 16 * q)] = mul(g, r0 + 16 * q, v[g][q]);
 }
 
 template <typename T, typename RowF, typename Val>
@@ -865,10 +871,9 @@ template <typename T, bool INV>
 __global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_outer_kernel(T* __restrict__ data, int nx,
                                                                 const cplx<T>* __restrict__ tw) {
   pdl_wait();
-  constexpr int P = rpitch<kY4>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* tws = S + kY4Sub * P;
+  cplx<T>* tws = S + kY4Sub * kY4Pitch;
   const int s0 = blockIdx.x * 32;
   const int n2a = 2 * blockIdx.y;
   const int ns = min(32, nx - s0);
@@ -883,12 +888,12 @@ __global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_outer_ke
     return cmul(v, w);
   });
   __syncthreads();
-  fft_reg_line<T, kY4, INV>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  fft_reg_line<T, kY4, INV>(S + y4line(threadIdx.x >> 3), threadIdx.x & 7, tws);
   __syncthreads();
   pdl_trigger();
   const T inv_n = T(1) / T(kY4 * kY4);
   y4_store<T>(base, rs, ns, row, [&](int g, int m, int e) -> cplx<T> {
-    const cplx<T> v = S[(16 * g + m) * P + rpad<kY4>(e)];
+    const cplx<T> v = S[y4line(16 * g + m) + rpad<kY4>(e)];
     if (INV) return {v.x * inv_n, v.y * inv_n};
     return cmul(v, tw[(n2a + g) * e]);
   });
@@ -901,10 +906,10 @@ __global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_mid_kern
                                                               const T* __restrict__ lamy,
                                                               const T* __restrict__ lamxz) {
   pdl_wait();
-  constexpr int P = rpitch<kY4>(), N = kY4 * kY4;
+  constexpr int N = kY4 * kY4;
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* tws = S + kY4Sub * P;
+  cplx<T>* tws = S + kY4Sub * kY4Pitch;
   __shared__ T Lab[32];
   const int s0 = blockIdx.x * 32;
   const int b = blockIdx.y;
@@ -920,36 +925,44 @@ __global__ void __launch_bounds__(kRegBlock, sizeof(T) == 4 ? 5 : 4) y4_mid_kern
     const int sl = sa < A.nx ? sa : sa - 1;   // the odd tail's missing partner takes its neighbour's value
     Lab[threadIdx.x] = lamxz[lam_index_spec<T>(A, sl, t)];
   }
+  static_assert(kRegBlock == 256, "the eigenvalue step maps 256 threads to (k2 < 32, group, sub-line)");
+  const T ly_own = lamy[((threadIdx.x >> 5) & 1 ? k1g1 : k1g0) + kY4 * (threadIdx.x & 31)];
+  const T ly_mid = lamy[N / 2];
   auto row = [&](int g, int e) { return kY4 * (g ? k1g1 : k1g0) + e; };
   y4_load<T>(S, base, rs, ns, row, [](int, int, cplx<T> v) { return v; });
   __syncthreads();
-  fft_reg_line<T, kY4, false>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  fft_reg_line<T, kY4, false>(S + y4line(threadIdx.x >> 3), threadIdx.x & 7, tws);
   __syncthreads();
-  // sub-line 16 g + l position k2 holds X(k1_g + 64 k2); each pair (k, 4096 - k) once, by its lower k
-  for (int e = threadIdx.x; e < nl * 2 * kY4; e += blockDim.x) {
-    const int l = e >> 7, g = (e >> 6) & 1, k2 = e & (kY4 - 1);
-    const int k1 = g ? k1g1 : k1g0;
-    const int k = k1 + kY4 * k2;
-    const int kk = (N - k) & (N - 1);
-    if (k > kk) continue;
-    const int gg = (kk & (kY4 - 1)) == k1 ? g : 1 - g;
+  // sub-line 16 g + l position k2 holds X(k1_g + 64 k2); each pair (k, 4096 - k) is updated once,
+  // by its lower k: every k2 < 32 of both groups, and k2 = 32 of group 0 when b = 0 (k = 2048).
+  // Thread (k2, g) = (t mod 32, t / 32 mod 2) takes sub-lines l = t / 64 + 4 i; with its k fixed,
+  // lamy[k] is read once.
+  auto pair_update = [&](int l, int g, int gg, int k2, int q2, bool both, T ly) {
     const T La = Lab[2 * l], Lb = Lab[2 * l + 1];
-    const T ly = lamy[k];
     const T ma = ly + La, mb = ly + Lb;
     const T ia = ma != T(0) ? T(1) / ma : T(0);
     const T ib = mb != T(0) ? T(1) / mb : T(0);
     const T cp = T(0.5) * (ia + ib), cm = T(0.5) * (ia - ib);
-    cplx<T>* p1 = S + (16 * g + l) * P + rpad<kY4>(k2);
-    cplx<T>* p2 = S + (16 * gg + l) * P + rpad<kY4>(kk / kY4);
+    cplx<T>* p1 = S + y4line(16 * g + l) + rpad<kY4>(k2);
+    cplx<T>* p2 = S + y4line(16 * gg + l) + rpad<kY4>(q2);
     const cplx<T> z1 = *p1, z2 = *p2;
     *p1 = {cp * z1.x + cm * z2.x, cp * z1.y - cm * z2.y};
-    if (kk != k) *p2 = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
+    if (both) *p2 = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
+  };
+  {
+    const int k2 = threadIdx.x & 31, g = (threadIdx.x >> 5) & 1;
+    const int k1 = g ? k1g1 : k1g0;
+    const int k = k1 + kY4 * k2;
+    const int kk = (N - k) & (N - 1);
+    const int gg = (kk & (kY4 - 1)) == k1 ? g : 1 - g;
+    for (int l = threadIdx.x >> 6; l < nl; l += kRegBlock / 64) pair_update(l, g, gg, k2, kk / kY4, kk != k, ly_own);
+    if (b == 0 && threadIdx.x < nl) pair_update(threadIdx.x, 0, 0, kY4 / 2, kY4 / 2, false, ly_mid);
   }
   __syncthreads();
-  fft_reg_line<T, kY4, true>(S + (threadIdx.x >> 3) * P, threadIdx.x & 7, tws);
+  fft_reg_line<T, kY4, true>(S + y4line(threadIdx.x >> 3), threadIdx.x & 7, tws);
   __syncthreads();
   pdl_trigger();
-  y4_store<T>(base, rs, ns, row, [&](int g, int m, int e) { return S[(16 * g + m) * P + rpad<kY4>(e)]; });
+  y4_store<T>(base, rs, ns, row, [&](int g, int m, int e) { return S[y4line(16 * g + m) + rpad<kY4>(e)]; });
 }
 
 // ---------------------------------------------------------------------------

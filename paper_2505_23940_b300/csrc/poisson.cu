@@ -1539,6 +1539,10 @@ void set_smem_attrs_plan() {
     cudaFuncSetAttribute(xfwd4k_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
     cudaFuncSetAttribute(xfwd4k_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
     cudaFuncSetAttribute(xinv4k_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)x4_smem_bytes<T>());
+    // (FP64 tiles of the 4096-row y solve exceed the 48 KB default)
+    cudaFuncSetAttribute(y4_outer_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y4_smem_bytes<T>());
+    cudaFuncSetAttribute(y4_outer_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y4_smem_bytes<T>());
+    cudaFuncSetAttribute(y4_mid_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)y4_smem_bytes<T>());
     cudaFuncSetAttribute(xfwd_kernel<T, 5760, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xfwd_kernel<T, 5760, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
     cudaFuncSetAttribute(xinv_kernel<T, 5760>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFixedBudget);
