@@ -1234,9 +1234,22 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) xinv4k_kernel(T* 
 //            rows paired along z instead of along y), one 1 / N^2 at the end.
 // Each line is transformed by 8 threads (fft_reg_line); 8 N threads per block,
 // half of them transform while the other half idles, all of them move data.
+// Line s of each half of the plane starts at xzpitch s + 8 (s mod 2) + (s / 2 mod 16): lines
+// 32 apart repeat the skew, every 32 consecutive lines start twice in each of the 16 8-byte bank
+// pairs (the slot-pair transpositions stay conflict-free) and the four lines a warp transforms
+// start 8 bank pairs apart, so the in-line FFT passes do not replay either (with the plain pitch
+// N + N / R1 + 1 = 9 mod 16 they replayed up to three times)
+template <int N>
+__host__ __device__ constexpr int xzpitch() {
+  return (N + N / RegPlan<N>::R1 + 23 + 15) / 16 * 16;   // padded line + largest skew, 16-aligned
+}
+template <int N>
+__device__ __forceinline__ int xzline(int s) {
+  return xzpitch<N>() * s + 8 * (s & 1) + ((s >> 1) & 15);
+}
 template <int N>
 constexpr size_t plane_smem_bytes() {
-  return (size_t)(N * rpitch<N>() + N) * sizeof(cplx<float>);
+  return (size_t)(N * xzpitch<N>() + N) * sizeof(cplx<float>);
 }
 
 template <int N, bool DIV>
@@ -1245,11 +1258,11 @@ __global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict
                                                                const DivArgs<float> dv) {
   pdl_wait();
   using T = float;
-  constexpr int P = rpitch<N>(), NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
+  constexpr int NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // z lines: slot pair c, entry k
-  cplx<T>* B = A + NL * P;                              // x lines: row pair l, entry i
-  cplx<T>* tws = B + NL * P;
+  cplx<T>* B = A + NL * xzpitch<N>();   // x lines: row pair l, entry i
+  cplx<T>* tws = B + NL * xzpitch<N>();
   const int j = blockIdx.x;
   const size_t rs = (size_t)N * ny;   // between z positions
   T* base = data + (size_t)N * j;
@@ -1298,15 +1311,15 @@ __global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict
       vb[0] = db.x; vb[1] = db.y; vb[2] = db.z; vb[3] = db.w;
     }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) B[l * P + rpad<N>(i0 + c)] = {va[c], vb[c]};
+    for (int c = 0; c < 4; ++c) B[xzline<N>(l) + rpad<N>(i0 + c)] = {va[c], vb[c]};
   }
   __syncthreads();
-  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(B + xzline<N>(threadIdx.x / TPL), threadIdx.x % TPL, tws);
   __syncthreads();
   // real-packed split of rows 2l, 2l + 1: slot pair c (slots 2c, 2c + 1) of row k -> A[c][k]
   for (int e = threadIdx.x; e < NL * NL; e += NT) {
     const int l = e / NL, c = e - l * NL;
-    const cplx<T>* line = B + l * P;
+    const cplx<T>* line = B + xzline<N>(l);
     cplx<T> oa, ob;
     if (c == 0) {   // slots 0 and 1: the real modes 0 and N / 2
       const cplx<T> z0 = line[rpad<N>(0)], zh = line[rpad<N>(N / 2)];
@@ -1317,11 +1330,11 @@ __global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict
       oa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};   // XA = (Z + conj Zr) / 2
       ob = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};   // XB = (Z - conj Zr) / (2 i)
     }
-    A[c * P + rpad<N>(2 * l)] = oa;
-    A[c * P + rpad<N>(2 * l + 1)] = ob;
+    A[xzline<N>(c) + rpad<N>(2 * l)] = oa;
+    A[xzline<N>(c) + rpad<N>(2 * l + 1)] = ob;
   }
   __syncthreads();
-  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, false>(A + xzline<N>(threadIdx.x / TPL), threadIdx.x % TPL, tws);
   __syncthreads();
   pdl_trigger();
   constexpr int NE = N * NL / NT;   // slot pairs per thread
@@ -1331,7 +1344,7 @@ __global__ void __launch_bounds__(8 * N, 1) xzfwd_plane_kernel(float* __restrict
     const int k = e / NL, c = e - k * NL;
     cplx<T> o;
     if (c > 0) {
-      o = A[c * P + rpad<N>(k)];
+      o = A[xzline<N>(c) + rpad<N>(k)];
     } else {   // pair 0 holds two real sequences: split into two real-packed z spectra
       const int m = k == 0 ? 0 : (k == 1 ? N / 2 : k >> 1);
       const bool im = k >= 2 && (k & 1);
@@ -1348,11 +1361,11 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
                                                                const cplx<float>* __restrict__ tw) {
   pdl_wait();
   using T = float;
-  constexpr int P = rpitch<N>(), NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
+  constexpr int NL = N / 2, NT = 8 * N, TPL = RegPlan<N>::TPL;
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* A = reinterpret_cast<cplx<T>*>(smem_raw);   // z lines: slot pair c, entry k
-  cplx<T>* B = A + NL * P;                              // x lines: row pair l, entry i
-  cplx<T>* tws = B + NL * P;
+  cplx<T>* B = A + NL * xzpitch<N>();   // x lines: row pair l, entry i
+  cplx<T>* tws = B + NL * xzpitch<N>();
   const int j = blockIdx.x;
   const size_t rs = (size_t)N * ny;
   T* base = data + (size_t)N * j;
@@ -1369,7 +1382,7 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
   for (int q = 0; q < NE; ++q) {
     const int e = threadIdx.x + NT * q;
     const int k = e / NL, c = e - k * NL;
-    A[c * P + rpad<N>(k)] = {v[q].x, v[q].y};
+    A[xzline<N>(c) + rpad<N>(k)] = {v[q].x, v[q].y};
     if (c == 0) B[rpad<N>(k)] = {v[q].x, v[q].y};   // pair 0 kept aside for its rebuild
   }
   __syncthreads();
@@ -1390,7 +1403,7 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
     A[rpad<N>(l)] = {y0.x - y1.y, y0.y + y1.x};
   }
   __syncthreads();
-  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(A + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(A + xzline<N>(threadIdx.x / TPL), threadIdx.x % TPL, tws);
   __syncthreads();
   // x lines: row pair l (rows 2l, 2l + 1), entry kx = XA + i XB, the Hermitian spectra of the two
   // rows from their real-packed slots (slots 2c, 2c + 1 of row k are A[c][k])
@@ -1398,7 +1411,7 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
     const int l = e / N, kx = e - l * N;
     const int kk = 2 * kx <= N ? kx : N - kx;
     const int c = 2 * kk == N ? 0 : kk;
-    const cplx<T> pa = A[c * P + rpad<N>(2 * l)], pb = A[c * P + rpad<N>(2 * l + 1)];
+    const cplx<T> pa = A[xzline<N>(c) + rpad<N>(2 * l)], pb = A[xzline<N>(c) + rpad<N>(2 * l + 1)];
     cplx<T> xa, xb;
     if (kx == 0) {
       xa = {pa.x, T(0)};
@@ -1413,10 +1426,10 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
       xa = {pa.x, -pa.y};
       xb = {pb.x, -pb.y};
     }
-    B[l * P + rpad<N>(kx)] = {xa.x - xb.y, xa.y + xb.x};
+    B[xzline<N>(l) + rpad<N>(kx)] = {xa.x - xb.y, xa.y + xb.x};
   }
   __syncthreads();
-  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(B + (threadIdx.x / TPL) * P, threadIdx.x % TPL, tws);
+  if (threadIdx.x < NL * TPL) fft_reg_line<T, N, true>(B + xzline<N>(threadIdx.x / TPL), threadIdx.x % TPL, tws);
   __syncthreads();
   pdl_trigger();
   const T sc = T(1) / T(N * N);
@@ -1427,7 +1440,7 @@ __global__ void __launch_bounds__(8 * N, 1) zxinv_plane_kernel(float* __restrict
     const int l = e / (N / 4), i0 = 4 * (e - l * (N / 4));
     cplx<T> z[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) z[c] = B[l * P + rpad<N>(i0 + c)];
+    for (int c = 0; c < 4; ++c) z[c] = B[xzline<N>(l) + rpad<N>(i0 + c)];
     *reinterpret_cast<float4*>(base + rs * (2 * l) + i0) =
         make_float4(z[0].x * sc, z[1].x * sc, z[2].x * sc, z[3].x * sc);
     *reinterpret_cast<float4*>(base + rs * (2 * l + 1) + i0) =

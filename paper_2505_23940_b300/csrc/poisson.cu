@@ -1729,6 +1729,9 @@ void set_smem_attrs() {
     cudaFuncSetAttribute(xzfwd_plane_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
     cudaFuncSetAttribute(xzfwd_plane_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
     cudaFuncSetAttribute(zxinv_plane_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<128>());
+    cudaFuncSetAttribute(xzfwd_plane_kernel<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<64>());
+    cudaFuncSetAttribute(xzfwd_plane_kernel<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<64>());
+    cudaFuncSetAttribute(zxinv_plane_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_smem_bytes<64>());
     cudaFuncSetAttribute(xzfwd_pair_kernel<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
     cudaFuncSetAttribute(xzfwd_pair_kernel<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
     cudaFuncSetAttribute(zxinv_pair_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane_pair_smem_bytes<128>());
