@@ -64,6 +64,25 @@ template <int N>
 __device__ __forceinline__ int rpad(int i) {
   return i + i / RegPlan<N>::R1;
 }
+// Line s of a 16-line block tile.  With FP32 entries and 8 threads per line (64, 128 and 384
+// points) a warp transforms four lines at once, and the plain pitch (9 mod 16 bank pairs) put their
+// starts on the in-line stride of 9, so the passes replayed up to three times: those tiles start
+// line s at regpitch s + 8 (s mod 2) + s / 2, which keeps the 16 lines of a tile in 16 different
+// bank pairs and starts the four lines of a warp 8 bank pairs apart.  With 16 threads per line, or
+// 16-byte FP64 entries, the plain pitch is already conflict-free.
+template <typename T, int N>
+__host__ __device__ constexpr bool reg_skewed() {
+  return sizeof(T) == 4 && RegPlan<N>::TPL == 8;
+}
+template <typename T, int N>
+__host__ __device__ constexpr int regpitch() {
+  return reg_skewed<T, N>() ? (N + N / RegPlan<N>::R1 + 23 + 15) / 16 * 16 : rpitch<N>();
+}
+template <typename T, int N>
+__device__ __forceinline__ int regline(int s) {
+  if constexpr (reg_skewed<T, N>()) return regpitch<T, N>() * s + 8 * (s & 1) + (s >> 1);
+  return rpitch<N>() * s;
+}
 template <int N>
 constexpr int reg_threads() {
   return kRegLines * RegPlan<N>::TPL;
@@ -279,7 +298,7 @@ __device__ __forceinline__ void load_twiddles(cplx<T>* tws, const cplx<T>* __res
 
 template <typename T, int N>
 size_t reg_smem_bytes(int extra_lines) {
-  return (size_t)((kRegLines + extra_lines) * rpitch<N>() + N) * sizeof(cplx<T>);
+  return (size_t)((kRegLines + extra_lines) * regpitch<T, N>() + N) * sizeof(cplx<T>);
 }
 
 // The transform threads of the block run the line FFT of their line.
@@ -287,7 +306,7 @@ template <typename T, int N, bool INV>
 __device__ __forceinline__ void fft_reg_block(cplx<T>* S, const cplx<T>* __restrict__ tws) {
   constexpr int TPL = RegPlan<N>::TPL;
   if (threadIdx.x < reg_threads<N>())
-    fft_reg_line<T, N, INV>(S + (threadIdx.x / TPL) * rpitch<N>(), threadIdx.x % TPL, tws);
+    fft_reg_line<T, N, INV>(S + regline<T, N>(threadIdx.x / TPL), threadIdx.x % TPL, tws);
 }
 
 template <typename T>
@@ -307,7 +326,7 @@ struct Pair2<double> {
 // (the missing partner reads as zero and is not written).
 template <typename T, int N>
 __device__ __forceinline__ void load_pair_tile(cplx<T>* S, const T* __restrict__ base, size_t rs, int nslots) {
-  constexpr int P = rpitch<N>(), NQ = N / 16;
+  constexpr int NQ = N / 16;
   const int m = threadIdx.x & 15, r0 = threadIdx.x >> 4;
   if (2 * m >= nslots) return;
   const bool whole = 2 * m + 1 < nslots;
@@ -324,7 +343,7 @@ __device__ __forceinline__ void load_pair_tile(cplx<T>* S, const T* __restrict__
     }
   }
 #pragma unroll
-  for (int q = 0; q < NQ; ++q) S[m * P + rpad<N>(r0 + 16 * q)] = v[q];
+  for (int q = 0; q < NQ; ++q) S[regline<T, N>(m) + rpad<N>(r0 + 16 * q)] = v[q];
 }
 
 template <typename T, int N, typename F>
@@ -357,7 +376,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw, const DivArgs<T> dv) {
   pdl_wait();
-  constexpr int P = rpitch<N>();
+  constexpr int P = regpitch<T, N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
@@ -435,7 +454,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
                 }
               }
 #pragma unroll
-              for (int c = 0; c < 4; ++c) S[l * P + rpad<N>(i0 + c)] = {d[0][c], d[1][c]};
+              for (int c = 0; c < 4; ++c) S[regline<T, N>(l) + rpad<N>(i0 + c)] = {d[0][c], d[1][c]};
             }
           }
         }
@@ -449,7 +468,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
             Vec4<T> db = {{T(0), T(0), T(0), T(0)}};
             if (2 * (line0 + l) + 1 < rows) db = div4_at(dv, i0, rowj[2 * l + 1], rowk[2 * l + 1]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) S[l * P + rpad<N>(i0 + e)] = {da.v[e], db.v[e]};
+            for (int e = 0; e < 4; ++e) S[regline<T, N>(l) + rpad<N>(i0 + e)] = {da.v[e], db.v[e]};
           }
         }
       }
@@ -480,7 +499,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
       const int t = threadIdx.x + q * kRegBlock;
       const int l = t / N, i = t - l * N;
       const int dst = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
-      S[l * P + rpad<N>(dst)] = {va[q], vb[q]};
+      S[regline<T, N>(l) + rpad<N>(dst)] = {va[q], vb[q]};
     }
   }
   __syncthreads();
@@ -504,7 +523,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) xfwd_reg_kernel(T
       } else {
         m = s;
       }
-      const cplx<T> z = S[l * P + rpad<N>(m)], zr = S[l * P + rpad<N>(m == 0 ? 0 : N - m)];
+      const cplx<T> z = S[regline<T, N>(l) + rpad<N>(m)], zr = S[regline<T, N>(l) + rpad<N>(m == 0 ? 0 : N - m)];
       const cplx<T> xa = {T(0.5) * (z.x + zr.x), T(0.5) * (z.y - zr.y)};
       const cplx<T> xb = {T(0.5) * (z.y + zr.y), T(0.5) * (zr.x - z.x)};
       if (mode == 0) {
@@ -533,7 +552,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
                                                            const cplx<T>* __restrict__ tw,
                                                            const cplx<T>* __restrict__ dtw) {
   pdl_wait();
-  constexpr int P = rpitch<N>();
+  constexpr int P = regpitch<T, N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
@@ -608,7 +627,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
   for (int q = 0; q < CH; ++q) {
     const int t = threadIdx.x + (q0 + q) * kRegBlock;
     const int l = t / N, k = t - l * N;
-    S[l * P + rpad<N>(k)] = z[q];
+    S[regline<T, N>(l) + rpad<N>(k)] = z[q];
   }
   }
   __syncthreads();
@@ -625,7 +644,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocksXinv<N>) xinv_reg_kern
     for (int h = 0; h < 2; ++h) {
       const int i = i0 + h;
       const int src = mode == 1 ? ((i & 1) ? N - 1 - (i >> 1) : (i >> 1)) : i;
-      v[h] = S[l * P + rpad<N>(src)];
+      v[h] = S[regline<T, N>(l) + rpad<N>(src)];
     }
     V wa, wb;
     wa.x = v[0].x * inv_n;
@@ -642,7 +661,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zfwd_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
-  constexpr int P = rpitch<N>();
+  constexpr int P = regpitch<T, N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
@@ -658,7 +677,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zfwd_reg_kernel(T
   __syncthreads();
   pdl_trigger();
   store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int p) -> cplx<T> {
-    const cplx<T>* Z = S + line * P;
+    const cplx<T>* Z = S + regline<T, N>(line);
     if (pair0 + line > 0) return Z[rpad<N>(p)];
     // pair 0 holds two real sequences: split into two real-packed z spectra
     const int l = p == 0 ? 0 : (p == 1 ? N / 2 : p >> 1);
@@ -676,7 +695,7 @@ template <typename T, int N>
 __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zinv_reg_kernel(T* __restrict__ data, int nx, int ny,
                                                            const cplx<T>* __restrict__ tw, int tile0) {
   pdl_wait();
-  constexpr int P = rpitch<N>();
+  constexpr int P = regpitch<T, N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
@@ -721,7 +740,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) zinv_reg_kernel(T
   pdl_trigger();
   const T inv_n = T(1) / T(N);
   store_pair_tile<T, N>(base, plane, 2 * np, [&](int line, int k) -> cplx<T> {
-    const cplx<T> v = S[line * P + rpad<N>(k)];
+    const cplx<T> v = S[regline<T, N>(line) + rpad<N>(k)];
     return {v.x * inv_n, v.y * inv_n};
   });
 }
@@ -733,7 +752,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(
                                                             const T* __restrict__ lamy,
                                                             const T* __restrict__ lamxz) {
   pdl_wait();
-  constexpr int P = rpitch<N>();
+  constexpr int P = regpitch<T, N>();
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* S = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* tws = S + kRegLines * P;
@@ -767,7 +786,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(
     const T ia = ma != T(0) ? T(1) / ma : T(0);
     const T ib = mb != T(0) ? T(1) / mb : T(0);
     const T cp = T(0.5) * (ia + ib), cm = T(0.5) * (ia - ib);
-    cplx<T>* line = S + l * P;
+    cplx<T>* line = S + regline<T, N>(l);
     const cplx<T> z1 = line[rpad<N>(k)], z2 = line[rpad<N>(kk)];
     line[rpad<N>(k)] = {cp * z1.x + cm * z2.x, cp * z1.y - cm * z2.y};
     if (kk != k) line[rpad<N>(kk)] = {cp * z2.x + cm * z1.x, cp * z2.y - cm * z1.y};
@@ -778,7 +797,7 @@ __global__ void __launch_bounds__(kRegBlock, kRegMinBlocks<N>) yspec_reg_kernel(
   pdl_trigger();
   const T inv_n = T(1) / T(N);
   store_pair_tile<T, N>(base, rs, ns, [&](int line, int jj) -> cplx<T> {
-    const cplx<T> v = S[line * P + rpad<N>(jj)];
+    const cplx<T> v = S[regline<T, N>(line) + rpad<N>(jj)];
     return {v.x * inv_n, v.y * inv_n};
   });
 }
