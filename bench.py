@@ -69,8 +69,8 @@ NCU_WORKLOAD = "isotropic_3d_128"   # the workload the traffic below was capture
 NCU_TRAFFIC = {
     "predictor": {"bytes": 50363136 + 1117952, "src": "787d2c94fc89"},
     "ysolve": {"bytes": 24119296 + 0, "src": "193f4010f1a6"},
-    "fft_xz_fwd_div": {"bytes": 25208576 + 0, "src": "1cc92d96aeb7"},
-    "fft_xz_inv": {"bytes": 8412416 + 0, "src": "1cc92d96aeb7"},
+    "fft_xz_fwd_div": {"bytes": 25194752 + 0, "src": "7e6f0662b6fd"},
+    "fft_xz_inv": {"bytes": 8411904 + 0, "src": "7e6f0662b6fd"},
     "correct": {"bytes": 33560576 + 1024, "src": "96276b6b63ca"},
 }
 
